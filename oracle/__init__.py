@@ -1,0 +1,114 @@
+"""FP64 CPU oracle for shadow accumulation -- TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and the benchmark's CPU-baseline leg may import
+this package.  The product path (the CUDA library and its binding) never does.
+
+The C source `sa_oracle.c` holds the definitions (see its header for the citations);
+this module compiles it with gcc/OpenMP on first use (in-tree, `_build/`) and wraps it
+for numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sa_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libsa_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, -O2, OpenMP); returns its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ct.CDLL(build())
+            P = ct.c_void_p
+            i64, i32, f64, ci = ct.c_int64, ct.c_int32, ct.c_double, ct.c_int
+            L.sao_shadow_bits.argtypes = [P, P, i64, P, P, i64, P, i32, P, ci]
+            L.sao_near_boundary.argtypes = [P, P, i64, P, P, i64, P, P, i32, f64, P, P, ci]
+            L.sao_reduce.argtypes = [P, i64, P, i32, P, P]
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def _f32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.int32)
+
+
+def default_threads() -> int:
+    return int(os.environ.get("SA_ORACLE_THREADS", os.cpu_count() or 1))
+
+
+def shadow_bits(tri9, tri_building, pos, nrm, dirs, nthreads: int | None = None) -> np.ndarray:
+    """uint8 [R, S]: 1 where the receiver is in shadow at that step (FP64 brute force)."""
+    tri9, tb, pos, nrm, dirs = _f32(tri9), _i32(tri_building), _f32(pos), _f32(nrm), _f32(dirs)
+    T, R, S = tri9.shape[0], pos.shape[0], dirs.shape[0]
+    out = np.zeros((R, S), dtype=np.uint8)
+    rc = lib().sao_shadow_bits(_ptr(tri9), _ptr(tb), T, _ptr(pos), _ptr(nrm), R, _ptr(dirs), S,
+                               _ptr(out), nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"sao_shadow_bits failed: {rc}")
+    return out
+
+
+def near_boundary(tri9, tri_building, pos, nrm, dirs, day_start, status, eps=1e-4,
+                  nthreads: int | None = None) -> np.ndarray:
+    """uint8 [R, S]: 1 where rotating d_j by +-eps along the sun arc flips the status."""
+    tri9, tb, pos, nrm, dirs = _f32(tri9), _i32(tri_building), _f32(pos), _f32(nrm), _f32(dirs)
+    ds = _i32(day_start)
+    status = np.ascontiguousarray(status, dtype=np.uint8)
+    T, R = tri9.shape[0], pos.shape[0]
+    near = np.zeros_like(status)
+    rc = lib().sao_near_boundary(_ptr(tri9), _ptr(tb), T, _ptr(pos), _ptr(nrm), R, _ptr(dirs),
+                                 _ptr(ds), ds.shape[0] - 1, float(eps), _ptr(status), _ptr(near),
+                                 nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"sao_near_boundary failed: {rc}")
+    return near
+
+
+def reduce(bits, day_start):
+    """(gross int32 [R], continuous int32 [R]) from per-step bits grouped by day."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    ds = _i32(day_start)
+    R = bits.shape[0]
+    g = np.zeros(R, np.int32)
+    c = np.zeros(R, np.int32)
+    rc = lib().sao_reduce(_ptr(bits), R, _ptr(ds), ds.shape[0] - 1, _ptr(g), _ptr(c))
+    if rc != 0:
+        raise RuntimeError(f"sao_reduce failed: {rc}")
+    return g, c
+
+
+def accumulate(tri9, tri_building, pos, nrm, dirs, day_start, step_minutes,
+               nthreads: int | None = None):
+    """Oracle gross steps, gross minutes (gross x step length) and continuous steps."""
+    bits = shadow_bits(tri9, tri_building, pos, nrm, dirs, nthreads)
+    g, c = reduce(bits, day_start)
+    return g, (g.astype(np.float64) * step_minutes).astype(np.float32), c, bits

@@ -1,0 +1,89 @@
+"""The synthetic workloads, by name (seeded, deterministic).
+
+  boxes16     4 x 4 boxes, 64 x 64 ground receivers at 2 m, 21 Jun 09-17 h @ 2 min (241 steps)
+  district    2,000 convex buildings (~60k triangles), 2048^2 ground at 1 m + 1M facade
+              samples, 21 Jun 09-17 h @ 1 min (481 steps)
+  season      50,000 buildings (~1.5M triangles), central 4096^2 ground at 1 m,
+              92 days (21 Jun - 20 Sep) x 481 steps
+  park        500 x 300 m park at 0.5 m (600k receivers) ringed by 200 buildings
+              (median 60 m), equinox 09-17 h @ 1 min
+  district_small / facade_small   parity-sized cases with ragged tails
+
+All at latitude 40.7 N.  The paper's Manhattan mesh is not available; these stand in
+for it (same building count and triangle scale for `season`).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import city as C
+from .sun import SunTable, sun_table
+
+LAT = 40.7
+
+
+@dataclass
+class Workload:
+    name: str
+    city: C.City
+    mesh: C.Mesh
+    ground: C.GroundGrid | None
+    facade_pos: np.ndarray | None      # float32 [Rf, 3]
+    facade_nrm: np.ndarray | None      # float32 [Rf, 3]
+    sun: SunTable
+
+    @property
+    def R(self) -> int:
+        g = self.ground.R if self.ground is not None else 0
+        f = 0 if self.facade_pos is None else int(self.facade_pos.shape[0])
+        return g + f
+
+
+def boxes16(seed_off: int = 1) -> Workload:
+    city = C.city_boxes(C.SEED_BASE + seed_off)
+    extent = 4 * 55.0 - 15.0
+    g = C.GroundGrid(x0=extent / 2 - 64.0, y0=extent / 2 - 64.0, dx=2.0, nx=64, ny=64)
+    sun = sun_table(LAT, [172], 9.0, 17.0, 2.0)
+    return Workload("boxes16", city, C.extrude(city), g, None, None, sun)
+
+
+def district(n_facade: int = 1_000_000, with_ground: bool = True, seed_off: int = 2) -> Workload:
+    city = C.city_district(C.SEED_BASE + seed_off)
+    g = C.GroundGrid(x0=0.0, y0=0.0, dx=1.0, nx=2048, ny=2048) if with_ground else None
+    fp, fn = (C.facade_samples(city, n_facade, C.SEED_BASE + 100 + seed_off)
+              if n_facade else (None, None))
+    sun = sun_table(LAT, [172], 9.0, 17.0, 1.0)
+    return Workload("district", city, C.extrude(city), g, fp, fn, sun)
+
+
+def season(n_days: int = 92, ground_n: int = 4096) -> Workload:
+    city = C.city_district(C.SEED_BASE + 3, extent=10240.0, n_buildings=50_000)
+    off = (10240.0 - ground_n) / 2
+    g = C.GroundGrid(x0=off, y0=off, dx=1.0, nx=ground_n, ny=ground_n)
+    sun = sun_table(LAT, list(range(172, 172 + n_days)), 9.0, 17.0, 1.0)
+    return Workload("season", city, C.extrude(city), g, None, None, sun)
+
+
+def park() -> Workload:
+    city = C.city_ring_around_park(C.SEED_BASE + 5)
+    g = C.GroundGrid(x0=0.0, y0=0.0, dx=0.5, nx=1000, ny=600)
+    sun = sun_table(LAT, [79], 9.0, 17.0, 1.0)
+    return Workload("park", city, C.extrude(city), g, None, None, sun)
+
+
+def district_small(seed_off: int = 6, n_buildings: int = 120, extent: float = 520.0,
+                   nx: int = 200, ny: int = 150, dx: float = 2.5, n_facade: int = 3001,
+                   doys=(172,), t0: float = 9.0, t1: float = 17.0, step: float = 4.0) -> Workload:
+    """A few hundred metres of district: several 32 x 32 tiles with ragged edges."""
+    city = C.city_district(C.SEED_BASE + seed_off, extent=extent, n_buildings=n_buildings)
+    g = C.GroundGrid(x0=8.25, y0=6.75, dx=dx, nx=nx, ny=ny)
+    fp, fn = (C.facade_samples(city, n_facade, C.SEED_BASE + 200 + seed_off)
+              if n_facade else (None, None))
+    sun = sun_table(LAT, list(doys), t0, t1, step)
+    return Workload("district_small", city, C.extrude(city), g, fp, fn, sun)
+
+
+BY_NAME = {"boxes16": boxes16, "district": district, "season": season, "park": park,
+           "district_small": district_small}
