@@ -1,0 +1,376 @@
+"""Benchmark: receiver-sun-steps per second of shadow accumulation on one GB300.
+
+Workload (default `district`): 2,000 synthetic convex buildings (~60k triangles), a
+2048 x 2048 ground raster at 1 m plus 1,000,000 facade samples, one day 09:00-17:00 at
+1-minute steps (481 sun directions).  One step = one full accumulation of every receiver
+over every sun step with the shadow-accrual method (ground grid: accrual raster; facades:
+ray-traced accrual), inputs resident on the device.  The per-step baselines (per-step
+ray sweep, per-step raster) are timed on the same workload and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
+
+Under torchrun every rank runs its own copy of the workload (independent problems, no
+collective): weak scaling, value = all ranks' receiver-steps / slowest rank's time.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "receiver·sun-steps/s shadow-accumulated (accrual vs per-step sweep), 1 GB300"
+UNIT = "receiver-steps/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.f = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}",
+                                          f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1].split()[0]))
+                smax.append(float(p[2].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names[1:], p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------ workload
+def make_workload(name: str):
+    from synth import configs
+    if name == "district":
+        return configs.district()
+    if name == "district_small":
+        return configs.district_small()
+    if name == "boxes16":
+        return configs.boxes16()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def cpu_oracle_sample(w, seconds_hint: float = 15.0, seed: int = 0):
+    """Time the FP64 oracle on a bounded receiver sample of the workload (all steps)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    t9, tb = w.mesh.tri9(), w.mesh.tri_building
+    # calibrate on a tiny sample, then size the sample to ~seconds_hint of work
+    pos_all = w.ground.positions() if w.ground is not None else None
+    n_g = 64
+    sel = rng.choice(pos_all.shape[0], n_g, replace=False)
+    t0 = time.perf_counter()
+    oracle.shadow_bits(t9, tb, pos_all[sel], None, w.sun.dirs)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_rx = dt / n_g
+    n_total = int(max(64, min(50_000, seconds_hint / per_rx)))
+    R = w.R
+    frac_f = (0 if w.facade_pos is None else w.facade_pos.shape[0]) / R
+    n_f = int(round(n_total * frac_f))
+    n_g = n_total - n_f
+    sel_g = rng.choice(pos_all.shape[0], n_g, replace=False)
+    t0 = time.perf_counter()
+    oracle.shadow_bits(t9, tb, pos_all[sel_g], None, w.sun.dirs)
+    if n_f:
+        sel_f = rng.choice(w.facade_pos.shape[0], n_f, replace=False)
+        oracle.shadow_bits(t9, tb, w.facade_pos[sel_f], w.facade_nrm[sel_f], w.sun.dirs)
+    el = time.perf_counter() - t0
+    value = (n_g + n_f) * w.sun.S / el
+    return {"value": value, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+            "sample": f"{n_g} ground + {n_f} facade receivers (seeded uniform sample) x all "
+                      f"{w.sun.S} steps, FP64 brute force with per-building box pre-test",
+            "seconds": el}
+
+
+# ------------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1907_04435_gb300 import binding as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = make_workload(args.workload)
+    st = w.sun
+    # resident inputs
+    scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B)
+    sun = B.Sun(st.dirs, st.day_start, args.block_len)
+    g = w.ground
+    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+    fac = B.Receivers.points(w.facade_pos, w.facade_nrm) if w.facade_pos is not None else None
+    R = grid.R + (fac.R if fac else 0)
+    units = R * st.S
+    out_g = [torch.zeros(grid.R, dtype=torch.int32, device=dev),
+             torch.empty(grid.R, dtype=torch.float32, device=dev),
+             torch.zeros(grid.R, dtype=torch.int32, device=dev)]
+    out_f = ([torch.zeros(fac.R, dtype=torch.int32, device=dev),
+              torch.empty(fac.R, dtype=torch.float32, device=dev),
+              torch.zeros(fac.R, dtype=torch.int32, device=dev)] if fac else None)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(method_ground, method_fac, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        B.sa_accumulate(scene, grid, sun, st.step_minutes, method_ground,
+                        gross=out_g[0], minutes=out_g[1], continuous=out_g[2])
+        if ev is not None:
+            ev[1].record(stream)
+        if fac:
+            B.sa_accumulate(scene, fac, sun, st.step_minutes, method_fac,
+                            gross=out_f[0], minutes=out_f[1], continuous=out_f[2])
+        if ev is not None:
+            ev[2].record(stream)
+
+    def timed(method_ground, method_fac, steps, warmup):
+        for _ in range(warmup):
+            step(method_ground, method_fac)
+        torch.cuda.synchronize()
+        tot, tg, tf = 0.0, 0.0, 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)                     # evict L2 between timed iterations
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            step(method_ground, method_fac, ev)
+            torch.cuda.synchronize()
+            tg += ev[0].elapsed_time(ev[1])
+            tf += ev[1].elapsed_time(ev[2])
+            tot += ev[0].elapsed_time(ev[2])
+        return tot / steps, tg / steps, tf / steps
+
+    # ---- headline: shadow accrual (ground accrual raster + facade ray-traced accrual)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".", f"clocks_rank{rank}.csv"))
+    ms, ms_g, ms_f = timed("accrual_sam", "accrual_trace", args.steps, args.warmup)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * units / (ms * 1e-3)
+
+    # ---- per-step baselines and the other exact method on the same workload
+    methods = {"accrual_sam": {"ms": ms, "ground_ms": ms_g, "facade_ms": ms_f,
+                               "value": units / (ms * 1e-3)}}
+    if not args.skip_baselines:
+        for mg, mf, name, k in (("accrual_trace", "accrual_trace", "accrual_trace", 1),
+                                ("sweep_raster", "sweep_trace", "sweep_raster+sweep_trace", 1),
+                                ("sweep_trace", "sweep_trace", "sweep_trace", 1)):
+            m_ms, m_g, m_f = timed(mg, mf, k, 1)
+            methods[name] = {"ms": m_ms, "ground_ms": m_g, "facade_ms": m_f,
+                             "value": units / (m_ms * 1e-3)}
+        sweep = methods["sweep_trace"]["value"]
+        for v in methods.values():
+            v["speedup_vs_sweep_trace"] = v["value"] / sweep
+
+    # ---- roofline of the dominant kernel (instrumented work counters)
+    roof = roofline(B, scene, grid, fac, sun, st, ms_g, ms_f)
+
+    # ---- end to end through the C ABI from host buffers
+    e2e = end_to_end(B, w, args, dev)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {w.city.B} buildings, {w.mesh.T} triangles, "
+                                   f"{g.nx}x{g.ny} ground @ {g.dx} m + "
+                                   f"{0 if fac is None else fac.R} facade samples, {st.S} sun steps",
+                       "receivers": R, "sun_steps": st.S, "block_len": args.block_len or 60,
+                       "method": "accrual_sam (ground accrual raster) + accrual_trace (facades)",
+                       "l2": "flushed (256 MB write) before every timed iteration",
+                       "parallelism": f"replicas x{world}"},
+            "methods": methods,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": count_launches(scene, sun, grid, fac),
+            "clocks": clk,
+        }
+        if world == 1 and not args.skip_cpu:
+            line["cpu_baseline"] = cpu_oracle_sample(w, args.cpu_seconds)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def count_launches(scene, sun, grid, fac):
+    """Kernels of one timed step: raster = per chunk (memset x2, count, copy, 3 scan, fill,
+    raster) + 1 run-scratch memset; facades = one accrual launch."""
+    chunks = (sun.n_blocks + 63) // 64
+    return chunks * 6 + (1 if fac else 0)
+
+
+def roofline(B, scene, grid, fac, sun, st, ms_g, ms_f):
+    import ctypes as ct
+    import torch
+    peaks, src = load_peaks()
+    clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    # ALU peak: 152 SMs x 128 FP32 lanes x 1 op per lane per clock (an FMA counted as one op)
+    peak_ops = 152 * 128 * clk
+    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    L = B.lib()
+    if fac is not None and hasattr(L, "sa_work_counters"):
+        L.sa_work_counters.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p]
+        L.sa_work_counters.restype = ct.c_int
+        rc = L.sa_work_counters(scene.handle, fac.handle, sun.handle, 2, ct.c_void_p(stats.data_ptr()),
+                                ct.c_void_p(torch.cuda.current_stream().cuda_stream))
+        torch.cuda.synchronize()
+        if rc == 0:
+            box, tri = int(stats[0]), int(stats[1])
+            ops = box * 12 + tri * 25
+            ach = ops / (ms_f * 1e-3)
+            return {"bound": "alu", "kernel": "k_accrual (facade ray-traced accrual)",
+                    "achieved": ach / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                    "frac": ach / peak_ops, "traffic": None,
+                    "work": {"box_tests": box, "tri_tests": tri, "ops_per_box": 12,
+                             "ops_per_tri": 25},
+                    "peak_source": f"152 SMs x 128 lanes x {clk/1e6:.0f} MHz (sm_max_mhz {src})"}
+    return {"bound": "alu", "achieved": None, "peak": peak_ops / 1e12, "unit": "Tops/s",
+            "frac": None, "traffic": None}
+
+
+def end_to_end(B, w, args, dev):
+    """Same metric through the C ABI from host buffers: scene + BVH build, sun table,
+    receiver sort, accumulation, and the results copied back to pinned host memory."""
+    import torch
+    st = w.sun
+    g = w.ground
+    verts, tris, tb = w.mesh.verts, w.mesh.tris, w.mesh.tri_building
+    fpos, fnrm = w.facade_pos, w.facade_nrm
+    R = g.R + (0 if fpos is None else fpos.shape[0])
+    host_out = torch.empty(3 * R, dtype=torch.int32).pin_memory()
+    h2d = verts.nbytes + tris.nbytes + tb.nbytes + st.dirs.nbytes + st.day_start.nbytes + \
+        (0 if fpos is None else fpos.nbytes + fnrm.nbytes)
+    d2h = 3 * R * 4
+
+    def once():
+        scene = B.Scene(verts, tris, tb, w.city.B)
+        sun = B.Sun(st.dirs, st.day_start, args.block_len)
+        grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+        gg, gm, gc = B.sa_accumulate(scene, grid, sun, st.step_minutes, "accrual_sam")
+        parts = [gg, gm.view(torch.int32), gc]
+        if fpos is not None:
+            fac = B.Receivers.points(fpos, fnrm)
+            fg, fm, fc = B.sa_accumulate(scene, fac, sun, st.step_minutes, "accrual_trace")
+            parts = [torch.cat([gg, fg]), torch.cat([gm, fm]).view(torch.int32), torch.cat([gc, fc])]
+        host_out.copy_(torch.cat(parts), non_blocking=True)
+        torch.cuda.synchronize()
+
+    once()
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        once()
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return {"value": R * st.S / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "seconds_per_step": t}
+
+
+# ------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.workload)
+    import oracle
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, args.cpu_seconds / 4)
+    for k in range(args.steps):
+        vals.append(cpu_oracle_sample(w, args.cpu_seconds / 2, seed=k))
+    value = statistics.median([v["value"] for v in vals])
+    s = vals[0]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median([v["seconds"] for v in vals]) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "sample": s["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.default_threads(),
+                             "kind": "oracle", "sample": s["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="district")
+    ap.add_argument("--block-len", dest="block_len", type=int, default=0)
+    ap.add_argument("--skip-baselines", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

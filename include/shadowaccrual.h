@@ -1,0 +1,176 @@
+/*
+ * shadowaccrual.h -- C ABI of the GB300 shadow-accumulation library (libshadowaccrual.so).
+ *
+ * Problem (Sec. 3.1, Sec. 7.1 of Miranda et al., "Shadow Accrual Maps", TVCG 2019):
+ * given a mesh of building triangles, a set of receivers (ground raster cells or facade
+ * points) and a time period sampled as a table of sun directions, count for every
+ * receiver the steps it spends in building shadow ("gross shadow", also in minutes) and
+ * the longest run of consecutive shadowed steps within a day, maximised over days
+ * ("continuous shadow").  The sun is a directional light (Sec. 3.2); every direction in
+ * the table points TOWARD the sun and must have d_z > 0.
+ *
+ * Frame: ENU metres, x = east, y = north, z = up, flat ground at z = 0.
+ *
+ * Exact target (what every exact method reproduces):
+ *   shadow(r, j) = 1 iff the ray o_r + t d_j, t > t_min, meets any triangle (two-sided);
+ *   ground receiver at p:                o = p,               t_min = 1e-3 m
+ *   facade receiver at p, outward n:     o = p + 1e-2 m * n,  t_min = 0
+ *
+ * Conventions for every call:
+ *   - Handles (sa_scene, sa_sun, sa_receivers) own only their internal device memory;
+ *     the caller owns every buffer it passes and keeps it alive for the call.
+ *   - "dev" buffers are device pointers of the current CUDA device; "host" buffers are
+ *     host pointers.  Functions with a `device_ptrs` flag accept either.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and is
+ *     asynchronous unless stated otherwise.  Creation calls synchronise `stream` before
+ *     returning so the handle is ready for use on any stream.
+ *   - Errors are returned as sa_status; no exception crosses the ABI.  sa_last_error()
+ *     gives a message for the calling thread's last failure.
+ *   - Integer outputs are deterministic from run to run.
+ */
+#ifndef SHADOWACCRUAL_H
+#define SHADOWACCRUAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SA_OK = 0,
+    SA_ERR_INVALID_ARG = -1,        /* bad pointer, size, flag or direction */
+    SA_ERR_CUDA = -2,               /* a CUDA runtime call failed */
+    SA_ERR_OOM = -3,                /* device allocation failed */
+    SA_ERR_SUN_BELOW_HORIZON = -4,  /* a sun direction has d_z <= 0 */
+    SA_ERR_DEGENERATE = -5,         /* non-finite vertex or receiver coordinate */
+    SA_ERR_TIMEOUT = -6,            /* a bounded device-side wait gave up */
+    SA_ERR_INTERNAL = -7,           /* a device-side consistency check failed */
+    SA_ERR_UNSUPPORTED = -8         /* method not defined for these receivers */
+} sa_status;
+
+/* Accumulation methods.  All five count the same quantity; the first four are exact
+ * (equal to the definition above away from shadow boundaries), SA_IAM is the paper's
+ * approximate inverse accrual map.
+ *   SA_SWEEP_TRACE    plain per-step sweep: one any-hit ray per receiver and step
+ *                     through the BVH (the per-minute ray-tracing baseline, Sec. 8.1).
+ *   SA_SWEEP_RASTER   per-step shadow raster of ground receivers: each step projects
+ *                     the triangles onto the ground separately (the per-minute
+ *                     shadow-map baseline, Sec. 8.1).  Ground grids only.
+ *   SA_ACCRUAL_TRACE  ray-traced accrual: one BVH traversal per receiver and block of
+ *                     <= 64 steps, whose query is the whole fan of the block's rays
+ *                     (the moving-shadow observation of Sec. 3.2 applied to rays).
+ *   SA_ACCRUAL_SAM    shadow accrual map (Sec. 4): one pass over the geometry per block
+ *                     writes all of the block's step slices.  Ground grids use the
+ *                     receiver-space accrual raster; facade points use SA_ACCRUAL_TRACE.
+ *   SA_IAM            inverse accrual map (Sec. 5): L source levels traced from both
+ *                     ends of each block, shadow lines drawn into per-step bit vectors.
+ *                     Ground grids only; approximate by design. */
+typedef enum {
+    SA_SWEEP_TRACE = 0,
+    SA_SWEEP_RASTER = 1,
+    SA_ACCRUAL_TRACE = 2,
+    SA_ACCRUAL_SAM = 3,
+    SA_IAM = 4
+} sa_method;
+
+typedef struct sa_scene sa_scene;
+typedef struct sa_sun sa_sun;
+typedef struct sa_receivers sa_receivers;
+
+/* Message of the calling thread's most recent failed call ("" if none). */
+const char* sa_last_error(void);
+
+/* Library version, (major << 16) | minor. */
+int32_t sa_version(void);
+
+/* ---------------------------------------------------------------------------- scene
+ * Build a scene from an indexed triangle mesh (Sec. 8.2: the city mesh): vertices
+ * float [nv][3] and triangles int32 [nt][3] (0-based vertex indices), optional int32
+ * [nt] building id per triangle (NULL: all 0), n_buildings > every id.  Buffers are
+ * host (device_ptrs = 0) or device (device_ptrs = 1) memory; they are copied.
+ * On the device this builds a linear BVH: 30-bit Morton codes of the triangle
+ * centroids, a least-significant-digit radix sort, Karras' (2012) radix-tree topology,
+ * bottom-up box refit, and a depth-first node order whose escape links allow stackless
+ * traversal.  Zero-area triangles are kept but never hit.
+ * Errors: SA_ERR_INVALID_ARG (NULL pointers, index out of range, nt or nv < 0),
+ * SA_ERR_DEGENERATE (non-finite vertex), SA_ERR_OOM, SA_ERR_CUDA.  nt = 0 is allowed. */
+sa_status sa_scene_from_mesh(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                             const int32_t* tri_building, int32_t n_buildings,
+                             int32_t device_ptrs, void* stream, sa_scene** out);
+
+/* Release a scene (NULL is ignored). Synchronises the device first. */
+void sa_scene_destroy(sa_scene* scene);
+
+/* Triangle and BVH node counts, number of buildings, minimum vertex z. */
+sa_status sa_scene_info(const sa_scene* scene, int64_t* n_tris, int64_t* n_nodes,
+                        int32_t* n_buildings, float* min_z);
+
+/* ------------------------------------------------------------------------- sun table
+ * Validate and partition a per-step sun-direction table (host memory): dirs float
+ * [S][3] toward the sun, |d| within 1e-5 of 1 and d_z > 0; day_start int32 [D+1] with
+ * day_start[0] = 0, non-decreasing, day_start[D] = S.  Steps of a day are consecutive
+ * and equally spaced in time.  Each day is cut into consecutive blocks of at most
+ * block_len steps (1..64; 0 picks 60, the paper's hourly interval of one-minute steps,
+ * Sec. 3.2), so every step lies in exactly one block and blocks never cross days.
+ * Errors: SA_ERR_INVALID_ARG, SA_ERR_SUN_BELOW_HORIZON, SA_ERR_OOM, SA_ERR_CUDA. */
+sa_status sa_sun_create(const float* dirs, int32_t S, const int32_t* day_start, int32_t D,
+                        int32_t block_len, void* stream, sa_sun** out);
+void sa_sun_destroy(sa_sun* sun);
+/* Number of steps, days and blocks. */
+sa_status sa_sun_info(const sa_sun* sun, int32_t* S, int32_t* D, int32_t* n_blocks);
+
+/* ------------------------------------------------------------------------- receivers
+ * Ground raster: nx * ny cells of side dx (> 0) with lower-left corner (x0, y0); the
+ * receiver of cell (ix, iy) is its centre (x0 + (ix + 0.5) dx, y0 + (iy + 0.5) dx, 0)
+ * and its output index is iy * nx + ix.  Nothing is allocated per cell. */
+sa_status sa_receivers_grid(float x0, float y0, float dx, int32_t nx, int32_t ny,
+                            sa_receivers** out);
+
+/* Point receivers: pos float [n][3]; normal float [n][3] outward unit normals (facade
+ * receivers) or NULL (ground receivers at their own z, using the ground rule).  Host or
+ * device memory per device_ptrs; copied and sorted internally along a Morton curve so
+ * a warp holds neighbouring points.  Outputs always come back in input order.
+ * Errors: SA_ERR_INVALID_ARG, SA_ERR_DEGENERATE (non-finite), SA_ERR_OOM, SA_ERR_CUDA. */
+sa_status sa_receivers_points(const float* pos, const float* normal, int64_t n,
+                              int32_t device_ptrs, void* stream, sa_receivers** out);
+void sa_receivers_destroy(sa_receivers* recv);
+int64_t sa_receivers_count(const sa_receivers* recv);
+
+/* ------------------------------------------------------------------------ accumulate
+ * Accumulate shadow over every step of `sun` for every receiver (Sec. 3.1):
+ *   gross_steps      int32 [R] dev: shadowed steps (required)
+ *   gross_minutes    float [R] dev: gross_steps * step_minutes (nullable)
+ *   continuous_steps int32 [R] dev: longest run of consecutive shadowed steps inside a
+ *                    day, maximised over days (nullable)
+ * flags: SA_ACCUMULATE_INTO adds to gross_steps and takes the max with
+ *        continuous_steps already in the buffers (progressive accumulation over several
+ *        calls that each cover whole days, Sec. 7.1); otherwise they are overwritten.
+ * iam_levels: source levels L for SA_IAM (1..8; 0 picks 3, the paper's choice, Sec. 8.2).
+ * Scratch memory is taken from the stream-ordered allocator on `stream`.
+ * Errors: SA_ERR_INVALID_ARG, SA_ERR_UNSUPPORTED (raster / IAM methods on point
+ * receivers, or raster methods on a scene with geometry below z = 0), SA_ERR_OOM,
+ * SA_ERR_CUDA. */
+#define SA_ACCUMULATE_INTO 1
+sa_status sa_accumulate(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
+                        float step_minutes, sa_method method, int32_t iam_levels,
+                        int32_t flags, int32_t* gross_steps, float* gross_minutes,
+                        int32_t* continuous_steps, void* stream);
+
+/* Per-step shadow masks: masks uint64 [n_blocks][R] dev; bit k of masks[b][r] is
+ * shadow(r, first step of block b + k).  Same methods as sa_accumulate. */
+sa_status sa_shadow_masks(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
+                          sa_method method, int32_t iam_levels, uint64_t* masks, void* stream);
+
+/* Work counters of one accumulation (diagnostics for roofline accounting): runs `method`
+ * with counting enabled and writes counters uint64 [4] dev: [0] ray/fan-versus-box tests
+ * and [1] ray-versus-triangle tests performed per receiver lane (trace methods),
+ * [2] projected (triangle, step) set-ups and [3] cell coverage tests (raster methods).
+ * The outputs of the accumulation itself are discarded. */
+sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
+                           sa_method method, uint64_t* counters, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHADOWACCRUAL_H */

@@ -1,0 +1,250 @@
+"""Thin Python binding of libshadowaccrual (ctypes).
+
+Functions carry the C names (see include/shadowaccrual.h) and only marshal arguments:
+torch tensors become device pointers, the current torch stream becomes the cudaStream_t,
+and a non-zero sa_status becomes an SAError.  Every step of the computation runs in the
+library's CUDA kernels; there is no Python or CPU fallback.  If the library is missing it
+is built with nvcc; if that fails, importing raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import threading
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+SA_SWEEP_TRACE, SA_SWEEP_RASTER, SA_ACCRUAL_TRACE, SA_ACCRUAL_SAM, SA_IAM = range(5)
+SA_ACCUMULATE_INTO = 1
+METHODS = {"sweep_trace": SA_SWEEP_TRACE, "sweep_raster": SA_SWEEP_RASTER,
+           "accrual_trace": SA_ACCRUAL_TRACE, "accrual_sam": SA_ACCRUAL_SAM, "iam": SA_IAM}
+STATUS = {0: "SA_OK", -1: "SA_ERR_INVALID_ARG", -2: "SA_ERR_CUDA", -3: "SA_ERR_OOM",
+          -4: "SA_ERR_SUN_BELOW_HORIZON", -5: "SA_ERR_DEGENERATE", -6: "SA_ERR_TIMEOUT",
+          -7: "SA_ERR_INTERNAL", -8: "SA_ERR_UNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if stale) the CUDA library and declare its signatures."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ct.CDLL(path)
+            P, i32, i64, f32 = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_float
+            PP = ct.POINTER(ct.c_void_p)
+            L.sa_last_error.restype = ct.c_char_p
+            L.sa_version.restype = i32
+            L.sa_scene_from_mesh.argtypes = [P, i64, P, i64, P, i32, i32, P, PP]
+            L.sa_scene_destroy.argtypes = [P]
+            L.sa_scene_destroy.restype = None
+            L.sa_scene_info.argtypes = [P, P, P, P, P]
+            L.sa_sun_create.argtypes = [P, i32, P, i32, i32, P, PP]
+            L.sa_sun_destroy.argtypes = [P]
+            L.sa_sun_destroy.restype = None
+            L.sa_sun_info.argtypes = [P, P, P, P]
+            L.sa_receivers_grid.argtypes = [f32, f32, f32, i32, i32, PP]
+            L.sa_receivers_points.argtypes = [P, P, i64, i32, P, PP]
+            L.sa_receivers_destroy.argtypes = [P]
+            L.sa_receivers_destroy.restype = None
+            L.sa_receivers_count.argtypes = [P]
+            L.sa_receivers_count.restype = i64
+            L.sa_accumulate.argtypes = [P, P, P, f32, i32, i32, i32, P, P, P, P]
+            L.sa_shadow_masks.argtypes = [P, P, P, i32, i32, P, P]
+            for name in ("sa_scene_from_mesh", "sa_scene_info", "sa_sun_create", "sa_sun_info",
+                         "sa_receivers_grid", "sa_receivers_points", "sa_accumulate",
+                         "sa_shadow_masks"):
+                getattr(L, name).restype = ct.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise SAError(status, lib().sa_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _host_f32(a) -> np.ndarray:
+    if isinstance(a, torch.Tensor):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _host_i32(a) -> np.ndarray:
+    if isinstance(a, torch.Tensor):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return ct.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ct.c_void_p)
+
+
+# ------------------------------------------------------------------------------ handles
+class Scene:
+    """sa_scene: device copy of the mesh plus its linear BVH."""
+
+    def __init__(self, verts, tris, tri_building=None, n_buildings=None, stream=None):
+        v, t = _host_f32(verts).reshape(-1, 3), _host_i32(tris).reshape(-1, 3)
+        b = None if tri_building is None else _host_i32(tri_building).reshape(-1)
+        nb = int(n_buildings if n_buildings is not None else (int(b.max()) + 1 if b is not None and b.size else 1))
+        h = ct.c_void_p()
+        _check(lib().sa_scene_from_mesh(_ptr(v), v.shape[0], _ptr(t), t.shape[0], _ptr(b), nb, 0,
+                                        ct.c_void_p(_stream(stream)), ct.byref(h)))
+        self.handle = h
+        self.n_buildings = nb
+
+    def info(self):
+        nt, nn, nb, mz = ct.c_int64(), ct.c_int64(), ct.c_int32(), ct.c_float()
+        _check(lib().sa_scene_info(self.handle, ct.byref(nt), ct.byref(nn), ct.byref(nb), ct.byref(mz)))
+        return {"n_tris": nt.value, "n_nodes": nn.value, "n_buildings": nb.value, "min_z": mz.value}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.sa_scene_destroy(h)
+            self.handle = None
+
+
+class Sun:
+    """sa_sun: validated, block-partitioned sun-direction table."""
+
+    def __init__(self, dirs, day_start, block_len: int = 0, stream=None):
+        d = _host_f32(dirs).reshape(-1, 3)
+        ds = _host_i32(day_start).reshape(-1)
+        h = ct.c_void_p()
+        _check(lib().sa_sun_create(_ptr(d), d.shape[0], _ptr(ds), ds.shape[0] - 1, int(block_len),
+                                   ct.c_void_p(_stream(stream)), ct.byref(h)))
+        self.handle = h
+        S, D, nb = ct.c_int32(), ct.c_int32(), ct.c_int32()
+        _check(lib().sa_sun_info(h, ct.byref(S), ct.byref(D), ct.byref(nb)))
+        self.S, self.D, self.n_blocks = S.value, D.value, nb.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.sa_sun_destroy(h)
+            self.handle = None
+
+
+class Receivers:
+    """sa_receivers: a ground grid (no per-cell storage) or Morton-sorted points."""
+
+    def __init__(self, handle, R, grid=None):
+        self.handle = handle
+        self.R = int(R)
+        self.grid = grid
+
+    @classmethod
+    def ground_grid(cls, x0, y0, dx, nx, ny):
+        h = ct.c_void_p()
+        _check(lib().sa_receivers_grid(float(x0), float(y0), float(dx), int(nx), int(ny), ct.byref(h)))
+        return cls(h, int(nx) * int(ny), grid=(x0, y0, dx, nx, ny))
+
+    @classmethod
+    def points(cls, pos, normal=None, stream=None):
+        if isinstance(pos, torch.Tensor) and pos.is_cuda:
+            p = pos.detach().float().contiguous()
+            n = None if normal is None else normal.detach().float().contiguous()
+            dev = 1
+        else:
+            p = _host_f32(pos).reshape(-1, 3)
+            n = None if normal is None else _host_f32(normal).reshape(-1, 3)
+            dev = 0
+        h = ct.c_void_p()
+        _check(lib().sa_receivers_points(_ptr(p), _ptr(n), p.shape[0], dev,
+                                         ct.c_void_p(_stream(stream)), ct.byref(h)))
+        return cls(h, p.shape[0])
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.sa_receivers_destroy(h)
+            self.handle = None
+
+
+# --------------------------------------------------------------------------- the calls
+def sa_accumulate(scene: Scene, recv: Receivers, sun: Sun, step_minutes: float, method,
+                  iam_levels: int = 0, accumulate_into: bool = False, gross=None, minutes=None,
+                  continuous=None, want_minutes=True, want_continuous=True, stream=None):
+    """Returns (gross_steps int32, gross_minutes float32 | None, continuous int32 | None) on
+    the current CUDA device; pass preallocated tensors to reuse or to accumulate into."""
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    R = recv.R
+    if gross is None:
+        gross = torch.zeros(R, dtype=torch.int32, device=dev)
+    if minutes is None and want_minutes:
+        minutes = torch.empty(R, dtype=torch.float32, device=dev)
+    if continuous is None and want_continuous:
+        continuous = torch.zeros(R, dtype=torch.int32, device=dev)
+    for t, dt in ((gross, torch.int32), (minutes, torch.float32), (continuous, torch.int32)):
+        if t is not None and (t.dtype != dt or not t.is_cuda or not t.is_contiguous() or t.numel() != R):
+            raise ValueError("output tensors must be contiguous CUDA tensors of R elements")
+    _check(lib().sa_accumulate(scene.handle, recv.handle, sun.handle, float(step_minutes), m,
+                               int(iam_levels), SA_ACCUMULATE_INTO if accumulate_into else 0,
+                               _ptr(gross), _ptr(minutes), _ptr(continuous),
+                               ct.c_void_p(_stream(stream))))
+    return gross, minutes, continuous
+
+
+def sa_shadow_masks(scene: Scene, recv: Receivers, sun: Sun, method, iam_levels: int = 0,
+                    masks=None, stream=None):
+    """uint64 masks [n_blocks, R] as an int64 tensor (bit k = step k of the block)."""
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    if masks is None:
+        masks = torch.empty((sun.n_blocks, recv.R), dtype=torch.int64,
+                            device=torch.device("cuda", torch.cuda.current_device()))
+    _check(lib().sa_shadow_masks(scene.handle, recv.handle, sun.handle, m, int(iam_levels),
+                                 _ptr(masks), ct.c_void_p(_stream(stream))))
+    return masks
+
+
+def unpack_masks(masks: torch.Tensor, sun_block_sizes) -> np.ndarray:
+    """Host helper: [n_blocks, R] masks -> uint8 [R, S] per-step bits (block order)."""
+    mk = masks.cpu().numpy().view(np.uint64)
+    R = mk.shape[1]
+    cols = []
+    for b, K in enumerate(sun_block_sizes):
+        bits = (mk[b][:, None] >> np.arange(K, dtype=np.uint64)[None, :]) & np.uint64(1)
+        cols.append(bits.astype(np.uint8))
+    return np.concatenate(cols, axis=1) if cols else np.zeros((R, 0), np.uint8)
+
+
+def block_sizes(day_start, block_len: int = 0):
+    """Host mirror of the library's block partition (consecutive, balanced, per day)."""
+    K = block_len or 60
+    out = []
+    ds = list(np.asarray(day_start).reshape(-1))
+    for a, b in zip(ds[:-1], ds[1:]):
+        n = int(b - a)
+        if n == 0:
+            continue
+        nb = (n + K - 1) // K
+        base, rem = divmod(n, nb)
+        out += [base + (1 if q < rem else 0) for q in range(nb)]
+    return out

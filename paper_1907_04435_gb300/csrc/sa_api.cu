@@ -1,0 +1,537 @@
+// sa_api.cu -- C ABI of libshadowaccrual: handles, validation, sun-table partitioning and
+// dispatch of the accumulation methods.  See include/shadowaccrual.h for the contract.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "sa_internal.cuh"
+
+struct sa_scene {
+    sa::LbvhBuild bvh;
+    long long T;
+    int n_buildings;
+    float min_z;
+};
+
+struct sa_sun {
+    int S, D;
+    std::vector<sa::StepConst> h_steps;
+    std::vector<sa::BlockConst> h_blocks;        // requested block length
+    std::vector<sa::BlockConst> h_step_blocks;   // one step per block
+    sa::StepConst* d_steps = nullptr;
+    sa::BlockConst* d_blocks = nullptr;
+    sa::BlockConst* d_step_blocks = nullptr;
+};
+
+struct sa_receivers {
+    int is_grid;
+    float x0, y0, dx;
+    int nx, ny;
+    long long R;
+    float4* d_orig = nullptr;
+    int* d_perm = nullptr;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+sa_status fail(sa_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+sa_status cuda_fail(cudaError_t e, const char* where) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(SA_ERR_OOM, "%s: out of device memory", where);
+    return fail(SA_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void make_step(const float* d, sa::StepConst* s) {
+    s->dx = d[0]; s->dy = d[1]; s->dz = d[2];
+    s->ux = (float)((double)d[0] / (double)d[2]);
+    s->uy = (float)((double)d[1] / (double)d[2]);
+    float inv[3];
+    for (int k = 0; k < 3; ++k) {
+        double v = d[k];
+        if (fabs(v) < 1e-20) v = v < 0 ? -1e-20 : 1e-20;
+        inv[k] = (float)(1.0 / v);
+    }
+    s->ix = inv[0]; s->iy = inv[1]; s->iz = inv[2];
+    int kz = 2;
+    if (fabsf(d[0]) > fabsf(d[kz])) kz = 0;
+    if (fabsf(d[1]) > fabsf(d[kz])) kz = 1;
+    const int kx = (kz + 1) % 3, ky = (kz + 2) % 3;
+    s->kz = kz;
+    s->Sx = (float)((double)d[kx] / (double)d[kz]);
+    s->Sy = (float)((double)d[ky] / (double)d[kz]);
+    s->Sz = (float)(1.0 / (double)d[kz]);
+    s->pad0 = s->pad1 = s->pad2 = s->pad3 = 0;
+}
+
+void cross(const double* a, const double* b, double* c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+double dot(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+void normalize(double* a) {
+    double n = sqrt(dot(a, a));
+    for (int k = 0; k < 3; ++k) a[k] /= n;
+}
+
+// Block constants for steps [j0, j0 + K): slope box, and the wedge bounding the fan of
+// the block's rays (plane through the first and last directions, in-plane angles psi).
+sa::BlockConst make_block(const float* dirs, const std::vector<sa::StepConst>& steps, int j0,
+                          int K, int new_day, bool with_wedge) {
+    sa::BlockConst b;
+    memset(&b, 0, sizeof(b));
+    b.j0 = j0; b.K = K; b.new_day = new_day; b.monotone = 0;
+    b.mask_block = 0; b.mask_bit = 0;
+    b.uxlo = b.uylo = 3.4e38f; b.uxhi = b.uyhi = -3.4e38f;
+    for (int k = 0; k < K; ++k) {
+        b.uxlo = std::min(b.uxlo, steps[j0 + k].ux); b.uxhi = std::max(b.uxhi, steps[j0 + k].ux);
+        b.uylo = std::min(b.uylo, steps[j0 + k].uy); b.uyhi = std::max(b.uyhi, steps[j0 + k].uy);
+    }
+    b.wedge_ok = 0.f;
+    if (!with_wedge || K < 2) return b;
+    double a[3], c[3], n[3];
+    for (int q = 0; q < 3; ++q) { a[q] = dirs[3 * j0 + q]; c[q] = dirs[3 * (j0 + K - 1) + q]; }
+    normalize(a); normalize(c);
+    cross(a, c, n);
+    const double nn = sqrt(dot(n, n));
+    if (nn < 1e-7) return b;
+    for (int q = 0; q < 3; ++q) n[q] /= nn;
+    double e1[3] = {a[0] + c[0], a[1] + c[1], a[2] + c[2]};
+    const double pn = dot(e1, n);
+    for (int q = 0; q < 3; ++q) e1[q] -= pn * n[q];
+    normalize(e1);
+    double e2[3];
+    cross(n, e1, e2);
+    double soff = 0.0, pmin = 1e9, pmax = -1e9;
+    int mono = 1;
+    double prev = -1e9;
+    for (int k = 0; k < K; ++k) {
+        double d[3];
+        for (int q = 0; q < 3; ++q) d[q] = dirs[3 * (j0 + k) + q];
+        normalize(d);
+        soff = std::max(soff, fabs(dot(n, d)));
+        const double psi = atan2(dot(e2, d), dot(e1, d));
+        b.psi[k] = (float)psi;
+        pmin = std::min(pmin, psi);
+        pmax = std::max(pmax, psi);
+        if (psi < prev) mono = 0;
+        prev = psi;
+    }
+    if (pmax - pmin > 3.0) return b;   // not a thin fan: keep the slope box
+    const double eps = 1e-5;
+    b.monotone = mono;
+    b.psi_eps = 2e-5f;
+    b.s_off = (float)(soff + 1e-6);
+    b.nx = (float)n[0]; b.ny = (float)n[1]; b.nz = (float)n[2];
+    b.e1x = (float)e1[0]; b.e1y = (float)e1[1]; b.e1z = (float)e1[2];
+    b.e2x = (float)e2[0]; b.e2y = (float)e2[1]; b.e2z = (float)e2[2];
+    const double lo = pmin - eps, hi = pmax + eps;
+    for (int q = 0; q < 3; ++q) {
+        (&b.g1x)[q] = (float)(-sin(lo) * e1[q] + cos(lo) * e2[q]);
+        (&b.g2x)[q] = (float)(sin(hi) * e1[q] - cos(hi) * e2[q]);
+    }
+    b.wedge_ok = 1.f;
+    return b;
+}
+
+sa::DevScene dev_scene(const sa_scene* s) {
+    sa::DevScene d;
+    d.nodes = s->bvh.nodes;
+    d.tris = s->bvh.tris;
+    d.n_nodes = s->bvh.n_nodes;
+    d.T = (int)s->T;
+    return d;
+}
+
+sa::DevRecv dev_recv(const sa_receivers* r) {
+    sa::DevRecv d;
+    d.is_grid = r->is_grid;
+    d.x0 = r->x0; d.y0 = r->y0; d.dx = r->dx; d.nx = r->nx; d.ny = r->ny;
+    d.orig = r->d_orig;
+    d.perm = r->d_perm;
+    d.R = r->R;
+    return d;
+}
+
+template <class T>
+cudaError_t upload(const void* src, size_t n, int device_ptrs, T** dst, cudaStream_t st) {
+    *dst = nullptr;
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(dst, sizeof(T) * n);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(*dst, src, sizeof(T) * n,
+                           device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+}
+
+// host copy of a caller buffer (host or device) for validation
+template <class T>
+sa_status host_copy(const T* src, size_t n, int device_ptrs, std::vector<T>* out) {
+    out->resize(n);
+    if (n == 0) return SA_OK;
+    if (!device_ptrs) {
+        memcpy(out->data(), src, sizeof(T) * n);
+        return SA_OK;
+    }
+    cudaError_t e = cudaMemcpy(out->data(), src, sizeof(T) * n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading caller buffer");
+    return SA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sa_last_error(void) { return g_err; }
+
+int32_t sa_version(void) { return (1 << 16) | 0; }
+
+// ------------------------------------------------------------------------------ scene
+sa_status sa_scene_from_mesh(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                             const int32_t* tri_building, int32_t n_buildings,
+                             int32_t device_ptrs, void* stream, sa_scene** out) {
+    if (!out) return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: out is NULL");
+    *out = nullptr;
+    if (nv < 0 || nt < 0) return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: negative size");
+    if (nt > (1ll << 30)) return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: too many triangles");
+    if ((nv > 0 && !verts) || (nt > 0 && !tris))
+        return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: NULL buffer");
+    if (n_buildings < 0) return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: n_buildings < 0");
+    std::vector<float> hv;
+    std::vector<int32_t> ht, hb;
+    sa_status s = host_copy(verts, (size_t)nv * 3, device_ptrs, &hv);
+    if (s != SA_OK) return s;
+    s = host_copy(tris, (size_t)nt * 3, device_ptrs, &ht);
+    if (s != SA_OK) return s;
+    if (tri_building) {
+        s = host_copy(tri_building, (size_t)nt, device_ptrs, &hb);
+        if (s != SA_OK) return s;
+    }
+    float min_z = INFINITY;
+    for (size_t i = 0; i < hv.size(); ++i)
+        if (!isfinite(hv[i])) return fail(SA_ERR_DEGENERATE, "sa_scene_from_mesh: non-finite vertex %zu", i / 3);
+    for (size_t t = 0; t < ht.size(); ++t) {
+        if (ht[t] < 0 || ht[t] >= nv)
+            return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: triangle %zu indexes vertex %d", t / 3, ht[t]);
+        min_z = std::min(min_z, hv[3 * (size_t)ht[t] + 2]);
+    }
+    for (size_t t = 0; t < hb.size(); ++t)
+        if (hb[t] < 0 || hb[t] >= std::max(n_buildings, 1))
+            return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: building id %d of triangle %zu", hb[t], t);
+    cudaStream_t st = as_stream(stream);
+    sa_scene* sc = new (std::nothrow) sa_scene();
+    if (!sc) return fail(SA_ERR_OOM, "sa_scene_from_mesh: host allocation");
+    sc->T = nt;
+    sc->n_buildings = n_buildings;
+    sc->min_z = nt > 0 ? min_z : 0.f;
+    float* dv = nullptr;
+    int *dt = nullptr, *db = nullptr;
+    cudaError_t e = upload(hv.data(), hv.size(), 0, &dv, st);
+    if (e == cudaSuccess) e = upload(ht.data(), ht.size(), 0, &dt, st);
+    if (e == cudaSuccess && tri_building) e = upload(hb.data(), hb.size(), 0, &db, st);
+    if (e == cudaSuccess) e = sa::build_lbvh(dv, nv, dt, nt, db, &sc->bvh, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (dv) cudaFree(dv);
+    if (dt) cudaFree(dt);
+    if (db) cudaFree(db);
+    if (e != cudaSuccess) {
+        delete sc;
+        return cuda_fail(e, "sa_scene_from_mesh");
+    }
+    *out = sc;
+    return SA_OK;
+}
+
+void sa_scene_destroy(sa_scene* scene) {
+    if (!scene) return;
+    cudaDeviceSynchronize();
+    if (scene->bvh.nodes) cudaFree(scene->bvh.nodes);
+    if (scene->bvh.tris) cudaFree(scene->bvh.tris);
+    delete scene;
+}
+
+sa_status sa_scene_info(const sa_scene* scene, int64_t* n_tris, int64_t* n_nodes,
+                        int32_t* n_buildings, float* min_z) {
+    if (!scene) return fail(SA_ERR_INVALID_ARG, "sa_scene_info: NULL scene");
+    if (n_tris) *n_tris = scene->T;
+    if (n_nodes) *n_nodes = scene->bvh.n_nodes;
+    if (n_buildings) *n_buildings = scene->n_buildings;
+    if (min_z) *min_z = scene->min_z;
+    return SA_OK;
+}
+
+// -------------------------------------------------------------------------------- sun
+sa_status sa_sun_create(const float* dirs, int32_t S, const int32_t* day_start, int32_t D,
+                        int32_t block_len, void* stream, sa_sun** out) {
+    if (!out) return fail(SA_ERR_INVALID_ARG, "sa_sun_create: out is NULL");
+    *out = nullptr;
+    if (S < 0 || D < 0 || (S > 0 && !dirs) || !day_start)
+        return fail(SA_ERR_INVALID_ARG, "sa_sun_create: bad sizes or NULL pointers");
+    if (block_len == 0) block_len = 60;
+    if (block_len < 1 || block_len > sa::kMaxBlock)
+        return fail(SA_ERR_INVALID_ARG, "sa_sun_create: block_len %d outside 1..64", block_len);
+    if (day_start[0] != 0 || day_start[D] != S)
+        return fail(SA_ERR_INVALID_ARG, "sa_sun_create: day_start must run from 0 to S");
+    for (int k = 0; k < D; ++k)
+        if (day_start[k + 1] < day_start[k])
+            return fail(SA_ERR_INVALID_ARG, "sa_sun_create: day_start decreases at day %d", k);
+    for (int j = 0; j < S; ++j) {
+        const float* d = dirs + 3 * j;
+        if (!isfinite(d[0]) || !isfinite(d[1]) || !isfinite(d[2]))
+            return fail(SA_ERR_INVALID_ARG, "sa_sun_create: non-finite direction at step %d", j);
+        const double n = sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
+        if (fabs(n - 1.0) > 1e-5)
+            return fail(SA_ERR_INVALID_ARG, "sa_sun_create: |d| = %.8f at step %d", n, j);
+        if (!(d[2] > 0.f))
+            return fail(SA_ERR_SUN_BELOW_HORIZON, "sa_sun_create: d_z <= 0 at step %d", j);
+    }
+    sa_sun* sun = new (std::nothrow) sa_sun();
+    if (!sun) return fail(SA_ERR_OOM, "sa_sun_create: host allocation");
+    sun->S = S;
+    sun->D = D;
+    sun->h_steps.resize(S);
+    for (int j = 0; j < S; ++j) make_step(dirs + 3 * j, &sun->h_steps[j]);
+    for (int k = 0; k < D; ++k) {
+        const int a = day_start[k], n = day_start[k + 1] - a;
+        if (n == 0) continue;
+        const int nb = (n + block_len - 1) / block_len;
+        const int base = n / nb, rem = n % nb;
+        int j = a;
+        for (int q = 0; q < nb; ++q) {
+            const int K = base + (q < rem ? 1 : 0);
+            const int mb = (int)sun->h_blocks.size();
+            sun->h_blocks.push_back(make_block(dirs, sun->h_steps, j, K, q == 0, true));
+            sun->h_blocks.back().mask_block = mb;
+            for (int i = 0; i < K; ++i) {
+                sun->h_step_blocks.push_back(make_block(dirs, sun->h_steps, j + i, 1, q == 0 && i == 0, false));
+                sun->h_step_blocks.back().mask_block = mb;
+                sun->h_step_blocks.back().mask_bit = i;
+            }
+            j += K;
+        }
+    }
+    cudaStream_t st = as_stream(stream);
+    cudaError_t e = upload(sun->h_steps.data(), sun->h_steps.size(), 0, &sun->d_steps, st);
+    if (e == cudaSuccess) e = upload(sun->h_blocks.data(), sun->h_blocks.size(), 0, &sun->d_blocks, st);
+    if (e == cudaSuccess)
+        e = upload(sun->h_step_blocks.data(), sun->h_step_blocks.size(), 0, &sun->d_step_blocks, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        sa_sun_destroy(sun);
+        return cuda_fail(e, "sa_sun_create");
+    }
+    *out = sun;
+    return SA_OK;
+}
+
+void sa_sun_destroy(sa_sun* sun) {
+    if (!sun) return;
+    cudaDeviceSynchronize();
+    if (sun->d_steps) cudaFree(sun->d_steps);
+    if (sun->d_blocks) cudaFree(sun->d_blocks);
+    if (sun->d_step_blocks) cudaFree(sun->d_step_blocks);
+    delete sun;
+}
+
+sa_status sa_sun_info(const sa_sun* sun, int32_t* S, int32_t* D, int32_t* n_blocks) {
+    if (!sun) return fail(SA_ERR_INVALID_ARG, "sa_sun_info: NULL sun");
+    if (S) *S = sun->S;
+    if (D) *D = sun->D;
+    if (n_blocks) *n_blocks = (int32_t)sun->h_blocks.size();
+    return SA_OK;
+}
+
+// -------------------------------------------------------------------------- receivers
+sa_status sa_receivers_grid(float x0, float y0, float dx, int32_t nx, int32_t ny,
+                            sa_receivers** out) {
+    if (!out) return fail(SA_ERR_INVALID_ARG, "sa_receivers_grid: out is NULL");
+    *out = nullptr;
+    if (!(dx > 0.f) || !isfinite(dx) || !isfinite(x0) || !isfinite(y0))
+        return fail(SA_ERR_INVALID_ARG, "sa_receivers_grid: bad origin or spacing");
+    if (nx < 0 || ny < 0 || nx > (1 << 24) || ny > (1 << 24))
+        return fail(SA_ERR_INVALID_ARG, "sa_receivers_grid: bad grid size");
+    sa_receivers* r = new (std::nothrow) sa_receivers();
+    if (!r) return fail(SA_ERR_OOM, "sa_receivers_grid: host allocation");
+    r->is_grid = 1;
+    r->x0 = x0; r->y0 = y0; r->dx = dx; r->nx = nx; r->ny = ny;
+    r->R = (long long)nx * ny;
+    *out = r;
+    return SA_OK;
+}
+
+sa_status sa_receivers_points(const float* pos, const float* normal, int64_t n,
+                              int32_t device_ptrs, void* stream, sa_receivers** out) {
+    if (!out) return fail(SA_ERR_INVALID_ARG, "sa_receivers_points: out is NULL");
+    *out = nullptr;
+    if (n < 0 || n > (1ll << 31) - 1) return fail(SA_ERR_INVALID_ARG, "sa_receivers_points: bad count");
+    if (n > 0 && !pos) return fail(SA_ERR_INVALID_ARG, "sa_receivers_points: NULL positions");
+    std::vector<float> hp, hn;
+    sa_status s = host_copy(pos, (size_t)n * 3, device_ptrs, &hp);
+    if (s != SA_OK) return s;
+    if (normal) {
+        s = host_copy(normal, (size_t)n * 3, device_ptrs, &hn);
+        if (s != SA_OK) return s;
+    }
+    for (size_t i = 0; i < hp.size(); ++i)
+        if (!isfinite(hp[i])) return fail(SA_ERR_DEGENERATE, "sa_receivers_points: non-finite position %zu", i / 3);
+    for (size_t i = 0; i < hn.size(); ++i)
+        if (!isfinite(hn[i])) return fail(SA_ERR_DEGENERATE, "sa_receivers_points: non-finite normal %zu", i / 3);
+    sa_receivers* r = new (std::nothrow) sa_receivers();
+    if (!r) return fail(SA_ERR_OOM, "sa_receivers_points: host allocation");
+    r->is_grid = 0;
+    r->R = n;
+    cudaStream_t st = as_stream(stream);
+    float *dp = nullptr, *dn = nullptr;
+    cudaError_t e = upload(hp.data(), hp.size(), 0, &dp, st);
+    if (e == cudaSuccess && normal) e = upload(hn.data(), hn.size(), 0, &dn, st);
+    if (e == cudaSuccess && n > 0) e = cudaMalloc(&r->d_orig, sizeof(float4) * (size_t)n);
+    if (e == cudaSuccess && n > 0) e = cudaMalloc(&r->d_perm, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = sa::sort_points(dp, dn, n, r->d_orig, r->d_perm, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (dp) cudaFree(dp);
+    if (dn) cudaFree(dn);
+    if (e != cudaSuccess) {
+        sa_receivers_destroy(r);
+        return cuda_fail(e, "sa_receivers_points");
+    }
+    *out = r;
+    return SA_OK;
+}
+
+void sa_receivers_destroy(sa_receivers* recv) {
+    if (!recv) return;
+    cudaDeviceSynchronize();
+    if (recv->d_orig) cudaFree(recv->d_orig);
+    if (recv->d_perm) cudaFree(recv->d_perm);
+    delete recv;
+}
+
+int64_t sa_receivers_count(const sa_receivers* recv) { return recv ? recv->R : -1; }
+
+// ------------------------------------------------------------------------- accumulate
+static sa_status run_method(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
+                            sa_method method, int32_t iam_levels, sa::DevOut out,
+                            cudaStream_t st, const char* who) {
+    if (!scene || !recv || !sun) return fail(SA_ERR_INVALID_ARG, "%s: NULL handle", who);
+    if (iam_levels < 0 || iam_levels > 8) return fail(SA_ERR_INVALID_ARG, "%s: iam_levels", who);
+    const bool raster = method == SA_SWEEP_RASTER || (method == SA_ACCRUAL_SAM && recv->is_grid);
+    if ((method == SA_SWEEP_RASTER || method == SA_IAM) && !recv->is_grid)
+        return fail(SA_ERR_UNSUPPORTED, "%s: method %d needs a ground grid", who, (int)method);
+    if (raster && scene->min_z < 0.f)
+        return fail(SA_ERR_UNSUPPORTED, "%s: raster methods need geometry at z >= 0", who);
+    if (method < SA_SWEEP_TRACE || method > SA_IAM)
+        return fail(SA_ERR_INVALID_ARG, "%s: unknown method %d", who, (int)method);
+    if (method == SA_IAM) return fail(SA_ERR_UNSUPPORTED, "%s: SA_IAM not available", who);
+    sa::DevScene dsc = dev_scene(scene);
+    sa::DevRecv drc = dev_recv(recv);
+    sa::DevSun dsun;
+    dsun.steps = sun->d_steps;
+    dsun.S = sun->S;
+    if (method == SA_SWEEP_RASTER) {
+        dsun.blocks = sun->d_step_blocks;
+        dsun.n_blocks = (int)sun->h_step_blocks.size();
+    } else {
+        dsun.blocks = sun->d_blocks;
+        dsun.n_blocks = (int)sun->h_blocks.size();
+    }
+    const long long R = recv->R;
+    if (R == 0) return SA_OK;
+    cudaError_t e = cudaSuccess;
+    int* run = nullptr;
+    if (raster) {
+        e = cudaMallocAsync(&run, sizeof(int) * (size_t)R, st);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+        out.run = run;
+        e = sa::launch_raster_ground(dsc, drc, dsun, out, st);
+    } else if (method == SA_SWEEP_TRACE) {
+        e = sa::launch_sweep_trace(dsc, drc, dsun, out, st);
+    } else {
+        e = sa::launch_accrual_trace(dsc, drc, dsun, out, st);
+    }
+    if (run) cudaFreeAsync(run, st);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return SA_OK;
+}
+
+sa_status sa_accumulate(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
+                        float step_minutes, sa_method method, int32_t iam_levels,
+                        int32_t flags, int32_t* gross_steps, float* gross_minutes,
+                        int32_t* continuous_steps, void* stream) {
+    if (!gross_steps && recv && recv->R > 0)
+        return fail(SA_ERR_INVALID_ARG, "sa_accumulate: gross_steps is NULL");
+    if (!isfinite(step_minutes) || step_minutes < 0.f)
+        return fail(SA_ERR_INVALID_ARG, "sa_accumulate: bad step_minutes");
+    if (flags & ~SA_ACCUMULATE_INTO) return fail(SA_ERR_INVALID_ARG, "sa_accumulate: unknown flags");
+    sa::DevOut out;
+    memset(&out, 0, sizeof(out));
+    out.gross = gross_steps;
+    out.minutes = gross_minutes;
+    out.continuous = continuous_steps;
+    out.step_minutes = step_minutes;
+    out.accumulate_into = (flags & SA_ACCUMULATE_INTO) ? 1 : 0;
+    out.write_final = 1;
+    return run_method(scene, recv, sun, method, iam_levels, out, as_stream(stream), "sa_accumulate");
+}
+
+sa_status sa_shadow_masks(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
+                          sa_method method, int32_t iam_levels, uint64_t* masks, void* stream) {
+    if (!masks && recv && recv->R > 0) return fail(SA_ERR_INVALID_ARG, "sa_shadow_masks: NULL masks");
+    if (!recv) return fail(SA_ERR_INVALID_ARG, "sa_shadow_masks: NULL receivers");
+    cudaStream_t st = as_stream(stream);
+    int* gross = nullptr;
+    if (recv->R > 0) {
+        cudaError_t e = cudaMallocAsync(&gross, sizeof(int) * (size_t)recv->R, st);
+        if (e != cudaSuccess) return cuda_fail(e, "sa_shadow_masks");
+    }
+    if (recv->R > 0 && sun) {
+        cudaError_t e = cudaMemsetAsync(masks, 0, sizeof(uint64_t) * (size_t)recv->R * sun->h_blocks.size(), st);
+        if (e != cudaSuccess) { cudaFreeAsync(gross, st); return cuda_fail(e, "sa_shadow_masks"); }
+    }
+    sa::DevOut out;
+    memset(&out, 0, sizeof(out));
+    out.gross = gross;
+    out.masks = reinterpret_cast<uint64_t*>(masks);
+    out.write_final = 1;
+    sa_status s = run_method(scene, recv, sun, method, iam_levels, out, st, "sa_shadow_masks");
+    if (gross) cudaFreeAsync(gross, st);
+    return s;
+}
+
+sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
+                           sa_method method, uint64_t* counters, void* stream) {
+    if (!counters) return fail(SA_ERR_INVALID_ARG, "sa_work_counters: NULL counters");
+    if (!recv) return fail(SA_ERR_INVALID_ARG, "sa_work_counters: NULL receivers");
+    cudaStream_t st = as_stream(stream);
+    cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(uint64_t) * 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sa_work_counters");
+    int* gross = nullptr;
+    if (recv->R > 0) {
+        e = cudaMallocAsync(&gross, sizeof(int) * (size_t)recv->R, st);
+        if (e != cudaSuccess) return cuda_fail(e, "sa_work_counters");
+    }
+    sa::DevOut out;
+    memset(&out, 0, sizeof(out));
+    out.gross = gross;
+    out.write_final = 1;
+    out.stats = reinterpret_cast<unsigned long long*>(counters);
+    sa_status s = run_method(scene, recv, sun, method, 0, out, st, "sa_work_counters");
+    if (gross) cudaFreeAsync(gross, st);
+    return s;
+}
+
+}  // extern "C"

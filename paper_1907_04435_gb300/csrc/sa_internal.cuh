@@ -1,0 +1,213 @@
+// sa_internal.cuh -- shared device structures and helpers of libshadowaccrual.
+//
+// Geometry conventions follow the paper's statement of the problem (Sec. 3): the sun is a
+// directional light, each step j has a unit direction d_j toward the sun, and a receiver
+// is in shadow at step j when the ray from it toward the sun meets a triangle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "shadowaccrual.h"
+
+namespace sa {
+
+constexpr float kGroundTmin = 1e-3f;     // ground receivers: hits closer than 1 mm ignored
+constexpr float kFacadeOffset = 1e-2f;   // facade receivers start 1 cm along their normal
+constexpr int kMaxBlock = 64;            // steps per accrual block (one uint64 mask)
+
+// ---------------------------------------------------------------------------- sun
+// Per-step constants (one sun direction), read warp-uniformly.
+struct StepConst {
+    float dx, dy, dz;   // unit direction toward the sun
+    float ux, uy;       // ground slope: d_xy / d_z (a point at height z shadows p - z * u)
+    float ix, iy, iz;   // 1 / d (safe against zero components)
+    float Sx, Sy, Sz;   // watertight shear for the major axis kz (Woop et al. 2013)
+    int kz;             // major axis of |d|
+    int pad0, pad1, pad2, pad3;
+};
+
+// Per-block constants: a block is <= 64 consecutive steps of one day.
+// The block's rays from one origin form a thin fan ("wedge") around the plane through
+// its first and last directions: n is that plane's unit normal, s_off bounds |n . d_j|,
+// and g1, g2 are in-plane normals of the two half-spaces that bound the in-plane angles
+// of the block's directions.  psi[k] is the in-plane angle of step j0 + k measured in the
+// orthonormal basis (e1, e2) of the plane, relative to the middle of the block.
+struct BlockConst {
+    int j0, K;              // first step, number of steps
+    int new_day;            // 1 if the block is the first of its day (runs restart)
+    int monotone;           // 1 if psi is non-decreasing over the block
+    int mask_block;         // block of the requested partition that holds these steps
+    int mask_bit;           // bit of step j0 within that block's mask
+    int pad_i0, pad_i1;
+    float uxlo, uxhi, uylo, uyhi;   // slope box of the block's steps
+    float nx, ny, nz, s_off;
+    float g1x, g1y, g1z, wedge_ok;  // wedge_ok = 0: fall back to the slope box only
+    float g2x, g2y, g2z, psi_eps;
+    float e1x, e1y, e1z, pad_f0;
+    float e2x, e2y, e2z, pad_f1;
+    float psi[kMaxBlock];
+};
+
+// ---------------------------------------------------------------------------- scene
+// BVH nodes in depth-first order, two float4 each:
+//   n0 = (lo.x, lo.y, lo.z, escape as int)   escape = index of the next node after the subtree
+//   n1 = (hi.x, hi.y, hi.z, tri as int)      tri = leaf triangle (leaf order) or -1
+// Triangles in leaf order, three float4 each: (v0, building), (v1, original index), (v2, 0).
+struct DevScene {
+    const float4* nodes;
+    const float4* tris;
+    int n_nodes;
+    int T;
+};
+
+// ------------------------------------------------------------------- reduction state
+// Running gross / continuous state of one receiver (Sec. 3.1 and the prefix/max/suffix
+// stitching of Sec. 6 applied to consecutive blocks of a day).
+struct RunState {
+    int gross, run, best;
+};
+
+__device__ __forceinline__ int longest_run64(uint64_t m) {
+    int n = 0;
+    while (m) { m &= m << 1; ++n; }
+    return n;
+}
+
+// Fold the mask of one block (bits 0..K-1 = its steps in order) into the state.
+__device__ __forceinline__ void stitch(RunState& s, uint64_t m, int K, int new_day) {
+    if (new_day) s.run = 0;
+    const uint64_t full = (K >= 64) ? ~0ull : ((1ull << K) - 1ull);
+    m &= full;
+    s.gross += __popcll(m);
+    if (m == full) {
+        s.run += K;
+        s.best = max(s.best, s.run);
+        return;
+    }
+    const int prefix = __ffsll((long long)~m) - 1;              // ones from bit 0 upward
+    const uint64_t zeros = (~m) & full;                         // the block's unshadowed steps
+    const int suffix = K - 1 - (63 - __clzll((long long)zeros));  // ones below bit K-1
+    s.best = max(s.best, s.run + prefix);
+    s.best = max(s.best, longest_run64(m));
+    s.run = suffix;
+}
+
+// ------------------------------------------------------------------ float helpers
+template <int A> __device__ __forceinline__ float comp(const float4& v);
+template <> __device__ __forceinline__ float comp<0>(const float4& v) { return v.x; }
+template <> __device__ __forceinline__ float comp<1>(const float4& v) { return v.y; }
+template <> __device__ __forceinline__ float comp<2>(const float4& v) { return v.z; }
+template <int A> __device__ __forceinline__ float comp3(const float3& v);
+template <> __device__ __forceinline__ float comp3<0>(const float3& v) { return v.x; }
+template <> __device__ __forceinline__ float comp3<1>(const float3& v) { return v.y; }
+template <> __device__ __forceinline__ float comp3<2>(const float3& v) { return v.z; }
+
+// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013) specialised for the
+// major axis KZ.  The edge functions use explicit round-to-nearest products and
+// differences (no contraction), so the value computed for an edge shared by two
+// triangles is the exact negation in the other and a ray through the edge hits at
+// least one of them.  Zero edge values count as inside (inclusive, like the oracle).
+template <int KZ>
+__device__ __forceinline__ bool hit_tri(const float3& o, const float4& a, const float4& b,
+                                        const float4& c, float Sx, float Sy, float Sz,
+                                        float tmin) {
+    constexpr int KX = (KZ + 1) % 3, KY = (KZ + 2) % 3;
+    const float az = comp<KZ>(a) - comp3<KZ>(o);
+    const float bz = comp<KZ>(b) - comp3<KZ>(o);
+    const float cz = comp<KZ>(c) - comp3<KZ>(o);
+    const float ax = fmaf(-Sx, az, comp<KX>(a) - comp3<KX>(o));
+    const float ay = fmaf(-Sy, az, comp<KY>(a) - comp3<KY>(o));
+    const float bx = fmaf(-Sx, bz, comp<KX>(b) - comp3<KX>(o));
+    const float by = fmaf(-Sy, bz, comp<KY>(b) - comp3<KY>(o));
+    const float cx = fmaf(-Sx, cz, comp<KX>(c) - comp3<KX>(o));
+    const float cy = fmaf(-Sy, cz, comp<KY>(c) - comp3<KY>(o));
+    const float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
+    const float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
+    const float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
+    const float det = U + V + W;
+    if (det == 0.f) return false;
+    const float T = U * (Sz * az) + V * (Sz * bz) + W * (Sz * cz);
+    return det > 0.f ? (T > tmin * det) : (T < tmin * det);
+}
+
+__device__ __forceinline__ bool hit_tri_any(int kz, const float3& o, const float4& a,
+                                            const float4& b, const float4& c,
+                                            const StepConst& s, float tmin) {
+    if (kz == 2) return hit_tri<2>(o, a, b, c, s.Sx, s.Sy, s.Sz, tmin);
+    if (kz == 0) return hit_tri<0>(o, a, b, c, s.Sx, s.Sy, s.Sz, tmin);
+    return hit_tri<1>(o, a, b, c, s.Sx, s.Sy, s.Sz, tmin);
+}
+
+// Slab test of the ray o + t d, t in [0, inf), against a (padded) box.
+__device__ __forceinline__ bool hit_box(const float3& o, float ix, float iy, float iz,
+                                        const float4& lo, const float4& hi) {
+    float tx0 = (lo.x - o.x) * ix, tx1 = (hi.x - o.x) * ix;
+    float ty0 = (lo.y - o.y) * iy, ty1 = (hi.y - o.y) * iy;
+    float tz0 = (lo.z - o.z) * iz, tz1 = (hi.z - o.z) * iz;
+    float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+    float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+    return tn <= tf * 1.0000005f;
+}
+
+// --------------------------------------------------------------- host-side launchers
+// Receivers as the kernels see them.
+struct DevRecv {
+    int is_grid;
+    // grid
+    float x0, y0, dx;
+    int nx, ny;
+    // points, in Morton order: origin (already offset) and t_min; perm = input index
+    const float4* orig;
+    const int* perm;
+    long long R;
+};
+
+struct DevSun {
+    const StepConst* steps;
+    const BlockConst* blocks;
+    int S, n_blocks;
+};
+
+// outputs / state (state buffers hold gross, run, best per receiver in output order)
+struct DevOut {
+    int* gross;
+    float* minutes;
+    int* continuous;
+    int* run;            // scratch: running length at the end of the last processed block
+    float step_minutes;
+    int accumulate_into;
+    int write_final;     // 1: this launch finishes the call (write minutes)
+    uint64_t* masks;     // optional [n_blocks][R]
+    unsigned long long* stats;   // optional work counters (box tests, triangle tests, ...)
+};
+
+cudaError_t launch_sweep_trace(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                               const DevOut& out, cudaStream_t st);
+cudaError_t launch_accrual_trace(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                                 const DevOut& out, cudaStream_t st);
+// ground raster; `sun` may be the per-step partition (K = 1 blocks) for SA_SWEEP_RASTER
+cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                                 const DevOut& out, cudaStream_t st);
+
+// LBVH build (device), returns node / triangle arrays owned by the caller
+struct LbvhBuild {
+    float4* nodes;   // [2 * n_nodes]
+    float4* tris;    // [3 * T]
+    int n_nodes;
+};
+cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, long long nt,
+                       const int* d_tri_building, LbvhBuild* out, cudaStream_t st);
+
+// Morton order of point receivers: fills perm (sorted -> input index) and sorted origins
+cudaError_t sort_points(const float* d_pos, const float* d_nrm, long long n, float4* d_orig,
+                        int* d_perm, cudaStream_t st);
+
+// radix sort of (key, value) pairs by key (stable, 32-bit keys), in place via scratch
+cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, long long n, cudaStream_t st);
+
+// exclusive scan of n uint32 (in place); writes the total to *d_total if non-null
+cudaError_t exclusive_scan_u32(unsigned* data, long long n, unsigned* d_total, cudaStream_t st);
+
+}  // namespace sa

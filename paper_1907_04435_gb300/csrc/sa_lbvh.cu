@@ -1,0 +1,371 @@
+// sa_lbvh.cu -- linear BVH over the city triangles, built on the device.
+//
+// The paper indexes the city with a uniform 3D grid for its ray traversal (Sec. 8.1); this
+// library uses a linear BVH instead: Morton codes of triangle centroids, a stable radix
+// sort, the radix-tree topology of Karras (HPG 2012), a bottom-up box refit, and a
+// depth-first node order.  In depth-first order the subtree of a node is contiguous, so
+// its escape link (the node to visit when the subtree is skipped) is just its index plus
+// the subtree size, and traversal needs no stack.
+#include <float.h>
+
+#include "sa_internal.cuh"
+
+namespace sa {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ unsigned expand_bits10(unsigned v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ unsigned morton3(float x, float y, float z) {
+    unsigned ix = (unsigned)fminf(fmaxf(x * 1024.f, 0.f), 1023.f);
+    unsigned iy = (unsigned)fminf(fmaxf(y * 1024.f, 0.f), 1023.f);
+    unsigned iz = (unsigned)fminf(fmaxf(z * 1024.f, 0.f), 1023.f);
+    return (expand_bits10(ix) << 2) | (expand_bits10(iy) << 1) | expand_bits10(iz);
+}
+
+// order-preserving float <-> uint map for atomic min / max
+__device__ __forceinline__ unsigned f2o(float f) {
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// gather triangles, centroid bounds
+__global__ void k_gather(const float* __restrict__ verts, const int* __restrict__ tris,
+                         const int* __restrict__ tri_b, long long nt, float4* __restrict__ raw,
+                         unsigned* __restrict__ cbox /* 6: lo.xyz hi.xyz as ordered uint */) {
+    __shared__ unsigned s_lo[3], s_hi[3];
+    if (threadIdx.x < 3) { s_lo[threadIdx.x] = 0xffffffffu; s_hi[threadIdx.x] = 0u; }
+    __syncthreads();
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nt) {
+        float p[3][3];
+        for (int v = 0; v < 3; ++v) {
+            long long vi = tris[3 * t + v];
+            for (int k = 0; k < 3; ++k) p[v][k] = verts[3 * vi + k];
+        }
+        raw[3 * t + 0] = make_float4(p[0][0], p[0][1], p[0][2], __int_as_float(tri_b ? tri_b[t] : 0));
+        raw[3 * t + 1] = make_float4(p[1][0], p[1][1], p[1][2], __int_as_float((int)t));
+        raw[3 * t + 2] = make_float4(p[2][0], p[2][1], p[2][2], 0.f);
+        for (int k = 0; k < 3; ++k) {
+            float c = (p[0][k] + p[1][k] + p[2][k]) * (1.f / 3.f);
+            atomicMin(&s_lo[k], f2o(c));
+            atomicMax(&s_hi[k], f2o(c));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        atomicMin(&cbox[threadIdx.x], s_lo[threadIdx.x]);
+        atomicMax(&cbox[3 + threadIdx.x], s_hi[threadIdx.x]);
+    }
+}
+
+__global__ void k_morton(const float4* __restrict__ raw, long long nt,
+                         const unsigned* __restrict__ cbox, unsigned* __restrict__ keys,
+                         unsigned* __restrict__ vals) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    float lo[3], inv[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = o2f(cbox[k]);
+        float ext = o2f(cbox[3 + k]) - lo[k];
+        inv[k] = ext > 0.f ? 1.f / ext : 0.f;
+    }
+    float4 a = raw[3 * t], b = raw[3 * t + 1], c = raw[3 * t + 2];
+    float cx = (a.x + b.x + c.x) * (1.f / 3.f), cy = (a.y + b.y + c.y) * (1.f / 3.f),
+          cz = (a.z + b.z + c.z) * (1.f / 3.f);
+    keys[t] = morton3((cx - lo[0]) * inv[0], (cy - lo[1]) * inv[1], (cz - lo[2]) * inv[2]);
+    vals[t] = (unsigned)t;
+}
+
+// common-prefix length of keys i and j (index tie-break for equal keys); -1 out of range
+__device__ __forceinline__ int delta(const unsigned* keys, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    unsigned a = keys[i], b = keys[j];
+    if (a == b) return 32 + __clz((unsigned)(i ^ j));
+    return __clz(a ^ b);
+}
+
+// Karras 2012: internal node i covers leaves [first, last] split after `split`.
+// Node ids: internal 0..n-2, leaf k = n-1+k.
+__global__ void k_karras(const unsigned* __restrict__ keys, int n, int* __restrict__ left,
+                         int* __restrict__ right, int* __restrict__ parent,
+                         int* __restrict__ first, int* __restrict__ last, int* __restrict__ split) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(keys, n, i, i - d);
+    int lmax = 2;
+    while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta(keys, n, i, j);
+    int s = 0;
+    int t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int gamma = i + s * d + min(d, 0);
+    int lo = min(i, j), hi = max(i, j);
+    int lc = (lo == gamma) ? (n - 1 + gamma) : gamma;
+    int rc = (hi == gamma + 1) ? (n - 1 + gamma + 1) : gamma + 1;
+    left[i] = lc;
+    right[i] = rc;
+    parent[lc] = i;
+    parent[rc] = i;
+    first[i] = lo;
+    last[i] = hi;
+    split[i] = gamma;
+}
+
+// Bottom-up refit: one thread per leaf; the second child to arrive at a parent merges.
+__global__ void k_refit(const float4* __restrict__ tris, int n, const int* __restrict__ left,
+                        const int* __restrict__ right, const int* __restrict__ parent,
+                        float4* __restrict__ blo, float4* __restrict__ bhi,
+                        unsigned* __restrict__ flags) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float4 a = tris[3 * k], b = tris[3 * k + 1], c = tris[3 * k + 2];
+    float lo[3] = {fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z))};
+    float hi[3] = {fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z))};
+    // pad by a few ulps so the FP32 slab test can never reject a box holding a hit
+    for (int q = 0; q < 3; ++q) {
+        float pad = 4e-6f * fmaxf(fabsf(lo[q]), fabsf(hi[q])) + 1e-5f;
+        lo[q] -= pad;
+        hi[q] += pad;
+    }
+    int node = n - 1 + k;
+    blo[node] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    bhi[node] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    __threadfence();
+    if (n == 1) return;
+    int p = parent[node];
+    while (true) {
+        unsigned old = atomicAdd(&flags[p], 1u);
+        if (old == 0) return;   // the sibling is not done yet; it will continue
+        __threadfence();
+        int l = left[p], r = right[p];
+        float4 l0 = __ldcg(&blo[l]), l1 = __ldcg(&bhi[l]);
+        float4 r0 = __ldcg(&blo[r]), r1 = __ldcg(&bhi[r]);
+        blo[p] = make_float4(fminf(l0.x, r0.x), fminf(l0.y, r0.y), fminf(l0.z, r0.z), 0.f);
+        bhi[p] = make_float4(fmaxf(l1.x, r1.x), fmaxf(l1.y, r1.y), fmaxf(l1.z, r1.z), 0.f);
+        __threadfence();
+        if (p == 0) return;
+        p = parent[p];
+    }
+}
+
+// Depth-first index of every node: walk to the root adding, at each step down, 1 for a
+// left child and 1 + (size of the left sibling's subtree) for a right child.
+__global__ void k_emit(int n, const int* __restrict__ left, const int* __restrict__ parent,
+                       const int* __restrict__ first, const int* __restrict__ last,
+                       const int* __restrict__ split, const float4* __restrict__ blo,
+                       const float4* __restrict__ bhi, float4* __restrict__ nodes) {
+    int node = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n_nodes = 2 * n - 1;
+    if (node >= n_nodes) return;
+    int leaves = (node >= n - 1) ? 1 : (last[node] - first[node] + 1);
+    int pre = 0;
+    int cur = node;
+    while (cur != 0 && n > 1) {
+        int p = parent[cur];
+        if (left[p] == cur) {
+            pre += 1;
+        } else {
+            int left_leaves = split[p] - first[p] + 1;
+            pre += 1 + (2 * left_leaves - 1);
+        }
+        cur = p;
+    }
+    int escape = pre + 2 * leaves - 1;
+    int tri = (node >= n - 1) ? (node - (n - 1)) : -1;
+    float4 lo = blo[node], hi = bhi[node];
+    nodes[2 * pre] = make_float4(lo.x, lo.y, lo.z, __int_as_float(escape));
+    nodes[2 * pre + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(tri));
+}
+
+__global__ void k_permute_tris(const float4* __restrict__ raw, const unsigned* __restrict__ order,
+                               long long nt, float4* __restrict__ out) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    long long t = order[k];
+    out[3 * k] = raw[3 * t];
+    out[3 * k + 1] = raw[3 * t + 1];
+    out[3 * k + 2] = raw[3 * t + 2];
+}
+
+inline int nblk(long long n, int t = kThreads) { return (int)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, long long nt,
+                       const int* d_tri_b, LbvhBuild* out, cudaStream_t st) {
+    (void)nv;
+    out->nodes = nullptr;
+    out->tris = nullptr;
+    out->n_nodes = 0;
+    if (nt == 0) return cudaSuccess;
+    const int n = (int)nt;
+    const int n_nodes = 2 * n - 1;
+    cudaError_t e;
+    float4 *raw = nullptr, *blo = nullptr, *bhi = nullptr;
+    unsigned *cbox = nullptr, *keys = nullptr, *vals = nullptr, *flags = nullptr;
+    int* ibuf = nullptr;
+#define TRY(x) do { e = (x); if (e != cudaSuccess) goto fail; } while (0)
+    TRY(cudaMalloc(&out->nodes, sizeof(float4) * 2 * (size_t)n_nodes));
+    TRY(cudaMalloc(&out->tris, sizeof(float4) * 3 * (size_t)n));
+    TRY(cudaMallocAsync(&raw, sizeof(float4) * 3 * (size_t)n, st));
+    TRY(cudaMallocAsync(&cbox, sizeof(unsigned) * 6, st));
+    TRY(cudaMallocAsync(&keys, sizeof(unsigned) * (size_t)n, st));
+    TRY(cudaMallocAsync(&vals, sizeof(unsigned) * (size_t)n, st));
+    TRY(cudaMallocAsync(&blo, sizeof(float4) * (size_t)n_nodes, st));
+    TRY(cudaMallocAsync(&bhi, sizeof(float4) * (size_t)n_nodes, st));
+    TRY(cudaMallocAsync(&flags, sizeof(unsigned) * (size_t)n, st));
+    TRY(cudaMallocAsync(&ibuf, sizeof(int) * 6 * (size_t)n_nodes, st));
+    {
+        int* left = ibuf;
+        int* right = ibuf + n_nodes;
+        int* parent = ibuf + 2 * n_nodes;
+        int* first = ibuf + 3 * n_nodes;
+        int* last = ibuf + 4 * n_nodes;
+        int* split = ibuf + 5 * n_nodes;
+        unsigned init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+        TRY(cudaMemcpyAsync(cbox, init, sizeof(init), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)n, st));
+        TRY(cudaMemsetAsync(ibuf, 0, sizeof(int) * 6 * (size_t)n_nodes, st));
+        k_gather<<<nblk(n), kThreads, 0, st>>>(d_verts, d_tris, d_tri_b, n, raw, cbox);
+        k_morton<<<nblk(n), kThreads, 0, st>>>(raw, n, cbox, keys, vals);
+        TRY(cudaGetLastError());
+        TRY(radix_sort_pairs(keys, vals, n, st));
+        k_permute_tris<<<nblk(n), kThreads, 0, st>>>(raw, vals, n, out->tris);
+        if (n > 1) k_karras<<<nblk(n - 1), kThreads, 0, st>>>(keys, n, left, right, parent, first, last, split);
+        k_refit<<<nblk(n), kThreads, 0, st>>>(out->tris, n, left, right, parent, blo, bhi, flags);
+        k_emit<<<nblk(n_nodes), kThreads, 0, st>>>(n, left, parent, first, last, split, blo, bhi, out->nodes);
+        TRY(cudaGetLastError());
+        // the initialisation copy reads host stack memory: finish before returning
+        TRY(cudaStreamSynchronize(st));
+    }
+    out->n_nodes = n_nodes;
+    cudaFreeAsync(raw, st); cudaFreeAsync(cbox, st); cudaFreeAsync(keys, st);
+    cudaFreeAsync(vals, st); cudaFreeAsync(blo, st); cudaFreeAsync(bhi, st);
+    cudaFreeAsync(flags, st); cudaFreeAsync(ibuf, st);
+    return cudaSuccess;
+fail:
+    cudaStreamSynchronize(st);
+    if (raw) cudaFree(raw);
+    if (cbox) cudaFree(cbox);
+    if (keys) cudaFree(keys);
+    if (vals) cudaFree(vals);
+    if (blo) cudaFree(blo);
+    if (bhi) cudaFree(bhi);
+    if (flags) cudaFree(flags);
+    if (ibuf) cudaFree(ibuf);
+    if (out->nodes) cudaFree(out->nodes);
+    if (out->tris) cudaFree(out->tris);
+    out->nodes = nullptr;
+    out->tris = nullptr;
+    return e;
+#undef TRY
+}
+
+// ----------------------------------------------------------------- point receivers
+namespace {
+
+__global__ void k_points_prep(const float* __restrict__ pos, const float* __restrict__ nrm,
+                              long long n, float4* __restrict__ orig_unsorted,
+                              unsigned* __restrict__ box) {
+    __shared__ unsigned s_lo[3], s_hi[3];
+    if (threadIdx.x < 3) { s_lo[threadIdx.x] = 0xffffffffu; s_hi[threadIdx.x] = 0u; }
+    __syncthreads();
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float o[3];
+        float tmin = kGroundTmin;
+        for (int k = 0; k < 3; ++k) o[k] = pos[3 * i + k];
+        if (nrm) {
+            for (int k = 0; k < 3; ++k) o[k] = fmaf(kFacadeOffset, nrm[3 * i + k], o[k]);
+            tmin = 0.f;
+        }
+        orig_unsorted[i] = make_float4(o[0], o[1], o[2], tmin);
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&s_lo[k], f2o(o[k]));
+            atomicMax(&s_hi[k], f2o(o[k]));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        atomicMin(&box[threadIdx.x], s_lo[threadIdx.x]);
+        atomicMax(&box[3 + threadIdx.x], s_hi[threadIdx.x]);
+    }
+}
+
+__global__ void k_points_morton(const float4* __restrict__ o, long long n,
+                                const unsigned* __restrict__ box, unsigned* __restrict__ keys,
+                                unsigned* __restrict__ vals) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float lo[3], inv[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = o2f(box[k]);
+        float ext = o2f(box[3 + k]) - lo[k];
+        inv[k] = ext > 0.f ? 1.f / ext : 0.f;
+    }
+    float4 p = o[i];
+    keys[i] = morton3((p.x - lo[0]) * inv[0], (p.y - lo[1]) * inv[1], (p.z - lo[2]) * inv[2]);
+    vals[i] = (unsigned)i;
+}
+
+__global__ void k_points_gather(const float4* __restrict__ o, const unsigned* __restrict__ order,
+                                long long n, float4* __restrict__ out, int* __restrict__ perm) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    unsigned i = order[k];
+    out[k] = o[i];
+    perm[k] = (int)i;
+}
+
+}  // namespace
+
+cudaError_t sort_points(const float* d_pos, const float* d_nrm, long long n, float4* d_orig,
+                        int* d_perm, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    float4* tmp = nullptr;
+    unsigned *box = nullptr, *keys = nullptr, *vals = nullptr;
+    cudaError_t e = cudaMallocAsync(&tmp, sizeof(float4) * (size_t)n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&box, sizeof(unsigned) * 6, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&keys, sizeof(unsigned) * (size_t)n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&vals, sizeof(unsigned) * (size_t)n, st);
+    if (e == cudaSuccess) {
+        unsigned init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+        e = cudaMemcpyAsync(box, init, sizeof(init), cudaMemcpyHostToDevice, st);
+        k_points_prep<<<nblk(n), kThreads, 0, st>>>(d_pos, d_nrm, n, tmp, box);
+        k_points_morton<<<nblk(n), kThreads, 0, st>>>(tmp, n, box, keys, vals);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, n, st);
+        k_points_gather<<<nblk(n), kThreads, 0, st>>>(tmp, vals, n, d_orig, d_perm);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (tmp) cudaFreeAsync(tmp, st);
+    if (box) cudaFreeAsync(box, st);
+    if (keys) cudaFreeAsync(keys, st);
+    if (vals) cudaFreeAsync(vals, st);
+    return e;
+}
+
+}  // namespace sa

@@ -1,0 +1,356 @@
+// sa_raster.cu -- shadow accrual map of a ground receiver grid (Sec. 4).
+//
+// The paper's shadow accrual map projects every occluder point s along the block's sun
+// directions onto a shadow plane and writes one depth slice per step in a single pass over
+// the geometry (Sec. 4, Step 1; Theorem 1 shows the slices equal one shadow map per step).
+// For receivers on the ground the shadow plane can be the ground itself: every occluder
+// lies above z = 0, so a ground point is shadowed at step j exactly when it lies inside
+// the projection of some triangle along d_j onto z = 0 (no depth test is needed, Step 2
+// reduces to a coverage test).  The map is therefore kept in receiver space, at the
+// receivers themselves, as one bit per step: no texel resampling, no aliasing, no bias.
+//
+// Per block of <= 64 steps:
+//   k_bin_count / k_bin_fill  one pass over the triangles bins each into the 32 x 32-cell
+//                             tiles its projection can reach during the block (the
+//                             triangle swept along the block's slope box)
+//   k_raster                  one CTA per tile keeps the tile's 1024 x 64-bit slices in
+//                             registers, projects each binned triangle for every step of
+//                             the block and sets bit k of each covered cell; the gross /
+//                             continuous reduction is fused into the epilogue.
+// With one step per block the same kernels form the per-step shadow raster baseline.
+//
+// Coverage is decided with edge functions evaluated from canonically ordered endpoints,
+// so an edge shared by two projected triangles yields exactly negated values in the two
+// and a cell centre on it is covered by at least one (watertight).
+#include "sa_internal.cuh"
+
+namespace sa {
+
+namespace {
+
+constexpr int kTile = 32;               // cells per tile side
+constexpr int kRasterThreads = 256;     // 8 warps x 4 rows each
+constexpr int kTriBatch = 16;           // triangles staged per batch
+constexpr int kMaxItems = kTriBatch * kMaxBlock;
+
+struct TileGeom {
+    float x0, y0, dx;
+    int nx, ny, tiles_x, tiles_y;
+};
+
+__device__ __forceinline__ bool tri_above_ground(const float4& a, const float4& b, const float4& c) {
+    return fmaxf(a.z, fmaxf(b.z, c.z)) > 0.f;
+}
+
+// Conservative tile range of a triangle swept over a slope box.
+__device__ __forceinline__ bool swept_tiles(const float4& a, const float4& b, const float4& c,
+                                            const BlockConst& bc, const TileGeom& g, int* tx0,
+                                            int* tx1, int* ty0, int* ty1) {
+    float xmin = 3.4e38f, xmax = -3.4e38f, ymin = 3.4e38f, ymax = -3.4e38f;
+    const float4* v[3] = {&a, &b, &c};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float z = fmaxf(v[q]->z, 0.f);
+        xmin = fminf(xmin, v[q]->x - z * bc.uxhi);
+        xmax = fmaxf(xmax, v[q]->x - z * bc.uxlo);
+        ymin = fminf(ymin, v[q]->y - z * bc.uyhi);
+        ymax = fmaxf(ymax, v[q]->y - z * bc.uylo);
+    }
+    const float inv = 1.f / (kTile * g.dx);
+    // one cell of margin on every side absorbs rounding of the projections
+    const float fx0 = floorf((xmin - g.x0 - g.dx) * inv), fx1 = floorf((xmax - g.x0 + g.dx) * inv);
+    const float fy0 = floorf((ymin - g.y0 - g.dx) * inv), fy1 = floorf((ymax - g.y0 + g.dx) * inv);
+    if (fx1 < 0.f || fy1 < 0.f || fx0 >= (float)g.tiles_x || fy0 >= (float)g.tiles_y) return false;
+    *tx0 = (int)fmaxf(fx0, 0.f);
+    *tx1 = (int)fminf(fx1, (float)(g.tiles_x - 1));
+    *ty0 = (int)fmaxf(fy0, 0.f);
+    *ty1 = (int)fminf(fy1, (float)(g.tiles_y - 1));
+    return true;
+}
+
+__global__ void k_bin_count(DevScene sc, const BlockConst* __restrict__ blocks, int b0,
+                            TileGeom g, unsigned* __restrict__ counts) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int bl = blockIdx.y;
+    if (t >= sc.T) return;
+    const float4 a = __ldg(&sc.tris[3 * t]), b = __ldg(&sc.tris[3 * t + 1]),
+                 c = __ldg(&sc.tris[3 * t + 2]);
+    if (!tri_above_ground(a, b, c)) return;
+    int tx0, tx1, ty0, ty1;
+    if (!swept_tiles(a, b, c, blocks[b0 + bl], g, &tx0, &tx1, &ty0, &ty1)) return;
+    unsigned* row = counts + (size_t)bl * g.tiles_x * g.tiles_y;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&row[ty * g.tiles_x + tx], 1u);
+}
+
+__global__ void k_bin_fill(DevScene sc, const BlockConst* __restrict__ blocks, int b0,
+                           TileGeom g, const unsigned* __restrict__ offsets,
+                           unsigned* __restrict__ cursor, int* __restrict__ bins) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int bl = blockIdx.y;
+    if (t >= sc.T) return;
+    const float4 a = __ldg(&sc.tris[3 * t]), b = __ldg(&sc.tris[3 * t + 1]),
+                 c = __ldg(&sc.tris[3 * t + 2]);
+    if (!tri_above_ground(a, b, c)) return;
+    int tx0, tx1, ty0, ty1;
+    if (!swept_tiles(a, b, c, blocks[b0 + bl], g, &tx0, &tx1, &ty0, &ty1)) return;
+    const size_t row = (size_t)bl * g.tiles_x * g.tiles_y;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            const size_t cell = row + ty * g.tiles_x + tx;
+            bins[offsets[cell] + atomicAdd(&cursor[cell], 1u)] = t;
+        }
+}
+
+// One projected (triangle, step): sign-folded canonical edge functions, inside iff all >= 0,
+// and the clipped cell range [c0, c1] x [r0, r1] of its bounding box (r0 > r1: empty).
+struct Item {
+    float A[3], B[3], C[3];
+    int range;   // c0 | c1 << 8 | r0 << 16 | r1 << 24
+};
+
+__device__ __forceinline__ void canonical_edge(float px, float py, float qx, float qy, float fold,
+                                               float* A, float* B, float* C) {
+    float ax = px, ay = py, bx = qx, by = qy, s = fold;
+    if (!(px < qx || (px == qx && py < qy))) { ax = qx; ay = qy; bx = px; by = py; s = -fold; }
+    const float a = ay - by, b = bx - ax;
+    const float c = -fmaf(a, ax, b * ay);
+    *A = s * a; *B = s * b; *C = s * c;    // exact sign flips
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+__device__ void setup_item(const float4& a, const float4& b, const float4& c, const StepConst& s,
+                           float tox, float toy, float dx, Item* it) {
+    // project along d onto z = 0, then to tile-local coordinates
+    const float p0x = fmaf(-a.z, s.ux, a.x) - tox, p0y = fmaf(-a.z, s.uy, a.y) - toy;
+    const float p1x = fmaf(-b.z, s.ux, b.x) - tox, p1y = fmaf(-b.z, s.uy, b.y) - toy;
+    const float p2x = fmaf(-c.z, s.ux, c.x) - tox, p2y = fmaf(-c.z, s.uy, c.y) - toy;
+    const float area = __fsub_rn(__fmul_rn(p1x - p0x, p2y - p0y), __fmul_rn(p1y - p0y, p2x - p0x));
+    int range = 0x00ff00ff;   // r0 = 255 > r1 = 0: empty
+    if (area != 0.f) {
+        const float fold = area > 0.f ? 1.f : -1.f;
+        canonical_edge(p0x, p0y, p1x, p1y, fold, &it->A[0], &it->B[0], &it->C[0]);
+        canonical_edge(p1x, p1y, p2x, p2y, fold, &it->A[1], &it->B[1], &it->C[1]);
+        canonical_edge(p2x, p2y, p0x, p0y, fold, &it->A[2], &it->B[2], &it->C[2]);
+        const float inv = 1.f / dx;
+        const float xmin = fminf(p0x, fminf(p1x, p2x)), xmax = fmaxf(p0x, fmaxf(p1x, p2x));
+        const float ymin = fminf(p0y, fminf(p1y, p2y)), ymax = fmaxf(p0y, fmaxf(p1y, p2y));
+        // cell k has its centre near (k + 0.5) dx; one cell of margin on each side
+        const float fc0 = floorf(xmin * inv - 0.5f) - 1.f, fc1 = ceilf(xmax * inv - 0.5f) + 1.f;
+        const float fr0 = floorf(ymin * inv - 0.5f) - 1.f, fr1 = ceilf(ymax * inv - 0.5f) + 1.f;
+        if (fc1 >= 0.f && fr1 >= 0.f && fc0 <= (float)(kTile - 1) && fr0 <= (float)(kTile - 1)) {
+            const int c0 = clampi((int)fmaxf(fc0, -1.f), 0, kTile - 1);
+            const int c1 = clampi((int)fminf(fc1, (float)kTile), 0, kTile - 1);
+            const int r0 = clampi((int)fmaxf(fr0, -1.f), 0, kTile - 1);
+            const int r1 = clampi((int)fminf(fr1, (float)kTile), 0, kTile - 1);
+            range = c0 | (c1 << 8) | (r0 << 16) | (r1 << 24);
+        }
+    }
+    it->range = range;
+}
+
+__device__ __forceinline__ bool covered(const Item& it, float x, float y) {
+    const float e0 = fmaf(it.A[0], x, fmaf(it.B[0], y, it.C[0]));
+    const float e1 = fmaf(it.A[1], x, fmaf(it.B[1], y, it.C[1]));
+    const float e2 = fmaf(it.A[2], x, fmaf(it.B[2], y, it.C[2]));
+    return e0 >= 0.f && e1 >= 0.f && e2 >= 0.f;
+}
+
+struct RasterArgs {
+    DevScene sc;
+    DevSun sun;
+    TileGeom g;
+    int b0, nbc;                     // first block and number of blocks of this chunk
+    const unsigned* offsets;         // [nbc][tiles] bin offsets
+    const unsigned* counts;          // [nbc][tiles] bin sizes
+    const int* bins;
+    DevOut out;
+    int* best;                       // continuous state (== out.continuous or scratch)
+    int load_state;                  // 0: start from zero, 1: from out.gross / best / run
+    int final_chunk;
+    long long R;
+};
+
+__global__ void __launch_bounds__(kRasterThreads)
+k_raster(RasterArgs ra) {
+    __shared__ float4 s_tri[kTriBatch * 3];
+    __shared__ Item s_item[kMaxItems];
+    const TileGeom& g = ra.g;
+    const int tile = blockIdx.x;
+    const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int row0 = warp * 4;
+    // tile origin and this thread's cell centres in tile-local coordinates; the centres
+    // are rounded exactly as the receivers' world coordinates, then shifted
+    const float tox = __fadd_rn(g.x0, __fmul_rn((float)(tx * kTile), g.dx));
+    const float toy = __fadd_rn(g.y0, __fmul_rn((float)(ty * kTile), g.dx));
+    const int ix = tx * kTile + lane;
+    const float xl = __fadd_rn(g.x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), g.dx)) - tox;
+    float yl[4];
+    long long outi[4];
+    bool act[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int iy = ty * kTile + row0 + q;
+        yl[q] = __fadd_rn(g.y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), g.dx)) - toy;
+        act[q] = ix < g.nx && iy < g.ny;
+        outi[q] = (long long)iy * g.nx + ix;
+    }
+    RunState st[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        st[q] = RunState{0, 0, 0};
+        if (act[q] && ra.load_state) {
+            st[q].gross = ra.out.gross[outi[q]];
+            st[q].best = ra.best[outi[q]];
+            st[q].run = ra.out.run[outi[q]];
+        }
+    }
+    const int n_tiles = g.tiles_x * g.tiles_y;
+    for (int bl = 0; bl < ra.nbc; ++bl) {
+        const BlockConst* bcp = &ra.sun.blocks[ra.b0 + bl];
+        const int j0 = bcp->j0, K = bcp->K;
+        uint64_t m[4] = {0, 0, 0, 0};
+        const unsigned off = ra.offsets[(size_t)bl * n_tiles + tile];
+        const unsigned cnt = ra.counts[(size_t)bl * n_tiles + tile];
+        for (unsigned base = 0; base < cnt; base += kTriBatch) {
+            const int nt = (int)min((unsigned)kTriBatch, cnt - base);
+            __syncthreads();
+            if (threadIdx.x < nt * 3) {
+                const int t = ra.bins[off + base + threadIdx.x / 3];
+                s_tri[threadIdx.x] = __ldg(&ra.sc.tris[3 * t + threadIdx.x % 3]);
+            }
+            __syncthreads();
+            const int items = nt * K;
+            for (int it = threadIdx.x; it < items; it += kRasterThreads) {
+                const int t = it / K, k = it - t * K;
+                const StepConst s = ra.sun.steps[j0 + k];
+                setup_item(s_tri[3 * t], s_tri[3 * t + 1], s_tri[3 * t + 2], s, tox, toy, g.dx,
+                           &s_item[it]);
+            }
+            __syncthreads();
+            for (int it = 0; it < items; ++it) {
+                const int range = s_item[it].range;
+                const int c0 = range & 0xff, c1 = (range >> 8) & 0xff;
+                const int r0 = (range >> 16) & 0xff, r1 = (range >> 24) & 0xff;
+                const int ra0 = max(r0, row0), ra1 = min(r1, row0 + 3);
+                if (ra0 > ra1) continue;                       // warp-uniform
+                if (lane < c0 || lane > c1) continue;
+                const Item& item = s_item[it];
+                const int k = it % K;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int row = row0 + q;
+                    if (row >= ra0 && row <= ra1 && covered(item, xl, yl[q])) m[q] |= 1ull << k;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            stitch(st[q], m[q], K, bcp->new_day);
+            if (ra.out.masks && act[q])
+                ra.out.masks[(size_t)bcp->mask_block * ra.R + outi[q]] |= m[q] << bcp->mask_bit;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (!act[q]) continue;
+        ra.out.gross[outi[q]] = st[q].gross;
+        ra.best[outi[q]] = st[q].best;
+        ra.out.run[outi[q]] = st[q].run;
+        if (ra.final_chunk && ra.out.minutes) ra.out.minutes[outi[q]] = (float)st[q].gross * ra.out.step_minutes;
+    }
+}
+
+}  // namespace
+
+// Runs every block of `sun` through the accrual raster, in chunks of blocks whose bins
+// fit a bounded scratch budget.  out.run must be scratch [R]; out.continuous may be NULL.
+cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                                 const DevOut& out, cudaStream_t st) {
+    TileGeom g;
+    g.x0 = rc.x0; g.y0 = rc.y0; g.dx = rc.dx; g.nx = rc.nx; g.ny = rc.ny;
+    g.tiles_x = (rc.nx + kTile - 1) / kTile;
+    g.tiles_y = (rc.ny + kTile - 1) / kTile;
+    const int n_tiles = g.tiles_x * g.tiles_y;
+    const long long R = (long long)rc.nx * rc.ny;
+    if (R == 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    int* best = out.continuous;
+    int* best_scratch = nullptr;
+    if (!best) {
+        e = cudaMallocAsync(&best_scratch, sizeof(int) * (size_t)R, st);
+        if (e != cudaSuccess) return e;
+        best = best_scratch;
+    }
+    const int chunk = 64;
+    const int max_chunk_blocks = sun.n_blocks < chunk ? sun.n_blocks : chunk;
+    unsigned *counts = nullptr, *offsets = nullptr, *cursor = nullptr, *d_total = nullptr;
+    int* bins = nullptr;
+    size_t bins_cap = 0;
+    const size_t nc = (size_t)max_chunk_blocks * n_tiles;
+    e = cudaMallocAsync(&counts, sizeof(unsigned) * nc, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&offsets, sizeof(unsigned) * nc, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&cursor, sizeof(unsigned) * nc, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_total, sizeof(unsigned), st);
+    const int tpb = 128;
+    for (int b0 = 0; b0 < sun.n_blocks && e == cudaSuccess; b0 += chunk) {
+        const int nbc = (sun.n_blocks - b0) < chunk ? (sun.n_blocks - b0) : chunk;
+        const size_t ncc = (size_t)nbc * n_tiles;
+        e = cudaMemsetAsync(counts, 0, sizeof(unsigned) * ncc, st);
+        if (e != cudaSuccess) break;
+        e = cudaMemsetAsync(cursor, 0, sizeof(unsigned) * ncc, st);
+        if (e != cudaSuccess) break;
+        unsigned total = 0;
+        if (sc.T > 0) {
+            dim3 grid((sc.T + tpb - 1) / tpb, nbc);
+            k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.blocks, b0, g, counts);
+            e = cudaMemcpyAsync(offsets, counts, sizeof(unsigned) * ncc, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) break;
+            e = exclusive_scan_u32(offsets, (long long)ncc, d_total, st);
+            if (e != cudaSuccess) break;
+            e = cudaMemcpyAsync(&total, d_total, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) break;
+            e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) break;
+            if (total > bins_cap) {
+                if (bins) cudaFreeAsync(bins, st);
+                bins_cap = (size_t)total + total / 4 + 1024;
+                e = cudaMallocAsync(&bins, sizeof(int) * bins_cap, st);
+                if (e != cudaSuccess) { bins = nullptr; break; }
+            }
+            if (total > 0) k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.blocks, b0, g, offsets, cursor, bins);
+        } else {
+            e = cudaMemsetAsync(offsets, 0, sizeof(unsigned) * ncc, st);
+            if (e != cudaSuccess) break;
+        }
+        RasterArgs ra;
+        ra.sc = sc; ra.sun = sun; ra.g = g; ra.b0 = b0; ra.nbc = nbc;
+        ra.offsets = offsets; ra.counts = counts; ra.bins = bins;
+        ra.out = out; ra.best = best;
+        ra.load_state = (b0 > 0) || out.accumulate_into;
+        ra.final_chunk = (b0 + nbc >= sun.n_blocks);
+        ra.R = R;
+        if (b0 == 0 && out.accumulate_into) {
+            // run lengths never cross calls (calls cover whole days)
+            e = cudaMemsetAsync(out.run, 0, sizeof(int) * (size_t)R, st);
+            if (e != cudaSuccess) break;
+            if (!out.continuous) {
+                e = cudaMemsetAsync(best, 0, sizeof(int) * (size_t)R, st);
+                if (e != cudaSuccess) break;
+            }
+        }
+        k_raster<<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        e = cudaGetLastError();
+    }
+    if (counts) cudaFreeAsync(counts, st);
+    if (offsets) cudaFreeAsync(offsets, st);
+    if (cursor) cudaFreeAsync(cursor, st);
+    if (d_total) cudaFreeAsync(d_total, st);
+    if (bins) cudaFreeAsync(bins, st);
+    if (best_scratch) cudaFreeAsync(best_scratch, st);
+    return e;
+}
+
+}  // namespace sa

@@ -1,0 +1,318 @@
+// sa_trace.cu -- ray-traced shadow accumulation on the linear BVH.
+//
+//   k_sweep    plain per-step sweep: one any-hit ray per receiver and sun step (the
+//              per-minute ray-tracing baseline of Sec. 8.1).
+//   k_accrual  ray-traced accrual: one traversal per receiver and block of <= 64 steps
+//              whose query is the fan of the block's rays.  The shadow of an occluder
+//              point sweeps a line while the sun moves (Sec. 3.2); seen from the receiver,
+//              the block's rays sweep a thin wedge, and only geometry inside that wedge
+//              can shadow it in the block.  Each candidate triangle is tested exactly,
+//              per step, with the same watertight test as the sweep.
+//
+// Both kernels are warp-coherent: the 32 lanes of a warp hold neighbouring receivers (an
+// 8 x 4 patch of a ground grid or 32 Morton-consecutive points) and walk the depth-first
+// node list together -- a node is entered when any lane's query overlaps it -- so node
+// loads are warp-uniform broadcasts and there is no divergence in the traversal itself.
+// The per-receiver gross / continuous reduction is fused into the epilogue.
+#include "sa_internal.cuh"
+
+namespace sa {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarpsPerCta = 4;
+
+struct Receiver {
+    float3 o;
+    float tmin;
+    long long out;   // output index
+    bool active;
+};
+
+__device__ __forceinline__ Receiver load_receiver(const DevRecv& rc, long long warp_id, int lane) {
+    Receiver r;
+    if (rc.is_grid) {
+        const int tiles_x = (rc.nx + 7) >> 3;
+        const long long ty = warp_id / tiles_x;
+        const int tx = (int)(warp_id - ty * tiles_x);
+        const int ix = tx * 8 + (lane & 7);
+        const long long iy = ty * 4 + (lane >> 3);
+        r.active = ix < rc.nx && iy < rc.ny;
+        // cell centre, rounded exactly as x0 + (ix + 0.5) * dx in FP32 without contraction
+        r.o.x = __fadd_rn(rc.x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), rc.dx));
+        r.o.y = __fadd_rn(rc.y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), rc.dx));
+        r.o.z = 0.f;
+        r.tmin = kGroundTmin;
+        r.out = iy * rc.nx + ix;
+    } else {
+        const long long s = warp_id * 32 + lane;
+        r.active = s < rc.R;
+        const float4 p = r.active ? rc.orig[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        r.o = make_float3(p.x, p.y, p.z);
+        r.tmin = p.w;
+        r.out = r.active ? rc.perm[s] : 0;
+    }
+    return r;
+}
+
+__device__ __forceinline__ long long warp_count(const DevRecv& rc) {
+    if (rc.is_grid) return (long long)((rc.nx + 7) >> 3) * ((rc.ny + 3) >> 2);
+    return (rc.R + 31) / 32;
+}
+
+__device__ __forceinline__ RunState load_state(const DevOut& out, const Receiver& r) {
+    RunState s{0, 0, 0};
+    if (out.accumulate_into && r.active) {
+        s.gross = out.gross[r.out];
+        s.best = out.continuous ? out.continuous[r.out] : 0;
+    }
+    return s;
+}
+
+__device__ __forceinline__ void store_state(const DevOut& out, const Receiver& r,
+                                            const RunState& s) {
+    if (!r.active) return;
+    out.gross[r.out] = s.gross;
+    if (out.continuous) out.continuous[r.out] = s.best;
+    if (out.minutes) out.minutes[r.out] = (float)s.gross * out.step_minutes;
+}
+
+// Warp-coherent any-hit query of one step for the whole warp.
+template <int KZ, bool COUNT>
+__device__ __forceinline__ bool any_hit_packet(const DevScene& sc, const float3& o, float tmin,
+                                               const StepConst& s, bool want,
+                                               unsigned long long& n_box,
+                                               unsigned long long& n_tri) {
+    bool hit = false;
+    int i = 0;
+    unsigned live = __ballot_sync(kFull, want);
+    while (live != 0u && i < sc.n_nodes) {
+        const float4 lo = __ldg(&sc.nodes[2 * i]);
+        const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
+        const int esc = __float_as_int(lo.w);
+        const int tri = __float_as_int(hi.w);
+        const bool in = want && !hit && hit_box(o, s.ix, s.iy, s.iz, lo, hi);
+        if (COUNT && want && !hit) ++n_box;
+        if (tri >= 0) {
+            if (in) {
+                if (COUNT) ++n_tri;
+                const float4 a = __ldg(&sc.tris[3 * tri]);
+                const float4 b = __ldg(&sc.tris[3 * tri + 1]);
+                const float4 c = __ldg(&sc.tris[3 * tri + 2]);
+                hit = hit_tri<KZ>(o, a, b, c, s.Sx, s.Sy, s.Sz, tmin);
+            }
+            i = esc;
+            live = __ballot_sync(kFull, want && !hit);
+        } else {
+            i = __any_sync(kFull, in) ? i + 1 : esc;
+        }
+    }
+    return hit;
+}
+
+__device__ __forceinline__ void flush_counts(const DevOut& out, unsigned long long n_box,
+                                             unsigned long long n_tri) {
+    for (int o = 16; o > 0; o >>= 1) {
+        n_box += __shfl_down_sync(kFull, n_box, o);
+        n_tri += __shfl_down_sync(kFull, n_tri, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out.stats[0], n_box);
+        atomicAdd(&out.stats[1], n_tri);
+    }
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
+k_sweep(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
+    unsigned long long n_box = 0, n_tri = 0;
+    const int lane = threadIdx.x & 31;
+    const long long warp_id = (long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+    if (warp_id >= warp_count(rc)) return;
+    const Receiver r = load_receiver(rc, warp_id, lane);
+    RunState st = load_state(out, r);
+    for (int b = 0; b < sun.n_blocks; ++b) {
+        const int j0 = sun.blocks[b].j0, K = sun.blocks[b].K;
+        uint64_t m = 0;
+        for (int k = 0; k < K; ++k) {
+            const StepConst s = sun.steps[j0 + k];
+            bool h;
+            if (s.kz == 2) h = any_hit_packet<2, COUNT>(sc, r.o, r.tmin, s, r.active, n_box, n_tri);
+            else if (s.kz == 0) h = any_hit_packet<0, COUNT>(sc, r.o, r.tmin, s, r.active, n_box, n_tri);
+            else h = any_hit_packet<1, COUNT>(sc, r.o, r.tmin, s, r.active, n_box, n_tri);
+            if (h) m |= 1ull << k;
+        }
+        stitch(st, m, K, sun.blocks[b].new_day);
+        if (out.masks && r.active)
+            out.masks[(long long)sun.blocks[b].mask_block * rc.R + r.out] |= m << sun.blocks[b].mask_bit;
+    }
+    store_state(out, r, st);
+    if (COUNT) flush_counts(out, n_box, n_tri);
+}
+
+// ------------------------------------------------------------------- accrual trace
+// Conservative test of a box against the block's ray fan from origin o (see BlockConst).
+__device__ __forceinline__ bool fan_box(const float3& o, const BlockConst& bc, const float4& lo,
+                                        const float4& hi) {
+    if (hi.z < o.z) return false;                       // every ray climbs
+    const float cx = 0.5f * (lo.x + hi.x) - o.x, cy = 0.5f * (lo.y + hi.y) - o.y,
+                cz = 0.5f * (lo.z + hi.z) - o.z;
+    const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y), hz = 0.5f * (hi.z - lo.z);
+    const float R = sqrtf(cx * cx + cy * cy + cz * cz) + sqrtf(hx * hx + hy * hy + hz * hz);
+    const float slack = 1e-5f * R + 1e-4f;
+    // in-plane half-spaces
+    const float g1 = bc.g1x * cx + bc.g1y * cy + bc.g1z * cz +
+                     fabsf(bc.g1x) * hx + fabsf(bc.g1y) * hy + fabsf(bc.g1z) * hz;
+    const float g2 = bc.g2x * cx + bc.g2y * cy + bc.g2z * cz +
+                     fabsf(bc.g2x) * hx + fabsf(bc.g2y) * hy + fabsf(bc.g2z) * hz;
+    if (g1 < -slack || g2 < -slack) return false;
+    // out of plane: |n . x| <= s_off |x| on the fan
+    const float nc = bc.nx * cx + bc.ny * cy + bc.nz * cz;
+    const float rn = fabsf(bc.nx) * hx + fabsf(bc.ny) * hy + fabsf(bc.nz) * hz;
+    const float lim = bc.s_off * R + slack;
+    return (nc - rn <= lim) && (nc + rn >= -lim);
+}
+
+// Slope-box version (used when the block's wedge is degenerate): a point at height z above
+// o on one of the rays lies at o.xy + (z - o.z) * u with u in the block's slope box.
+__device__ __forceinline__ bool slope_box(const float3& o, const BlockConst& bc, const float4& lo,
+                                          const float4& hi) {
+    const float h1 = hi.z - o.z;
+    if (h1 < 0.f) return false;
+    const float h0 = fmaxf(lo.z - o.z, 0.f);
+    const float xa = fminf(h0 * bc.uxlo, h1 * bc.uxlo), xb = fmaxf(h0 * bc.uxhi, h1 * bc.uxhi);
+    const float ya = fminf(h0 * bc.uylo, h1 * bc.uylo), yb = fmaxf(h0 * bc.uyhi, h1 * bc.uyhi);
+    const float sl = 1e-4f + 1e-6f * (fabsf(o.x) + fabsf(o.y) + h1);
+    return (o.x + xa <= hi.x + sl) && (o.x + xb >= lo.x - sl) && (o.y + ya <= hi.y + sl) &&
+           (o.y + yb >= lo.y - sl);
+}
+
+// Steps of the block whose in-plane angle can meet the triangle: [*ka, *kb] (inclusive).
+__device__ __forceinline__ void candidate_steps(const float3& o, const BlockConst& bc,
+                                                const float* psi, const float4& a,
+                                                const float4& b, const float4& c, int* ka,
+                                                int* kb) {
+    *ka = 0;
+    *kb = bc.K - 1;
+    if (bc.wedge_ok == 0.f || !bc.monotone) return;
+    float ang[3];
+    const float4* v[3] = {&a, &b, &c};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float x = v[q]->x - o.x, y = v[q]->y - o.y, z = v[q]->z - o.z;
+        const float p = bc.e1x * x + bc.e1y * y + bc.e1z * z;
+        const float s = bc.e2x * x + bc.e2y * y + bc.e2z * z;
+        if (p * p + s * s < 1e-12f) return;             // vertex on the fan's axis line
+        ang[q] = atan2f(s, p);
+    }
+    const float amin = fminf(ang[0], fminf(ang[1], ang[2]));
+    const float amax = fmaxf(ang[0], fmaxf(ang[1], ang[2]));
+    if (amax - amin >= 3.1f) return;                    // may surround the origin: all steps
+    const float lo = amin - bc.psi_eps, hi = amax + bc.psi_eps;
+    // first k with psi[k] >= lo, last k with psi[k] <= hi
+    int l = 0, r = bc.K;
+    while (l < r) { int m = (l + r) >> 1; if (psi[m] >= lo) r = m; else l = m + 1; }
+    *ka = l;
+    l = 0; r = bc.K;
+    while (l < r) { int m = (l + r) >> 1; if (psi[m] > hi) r = m; else l = m + 1; }
+    *kb = l - 1;
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
+k_accrual(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
+    __shared__ BlockConst s_bc;
+    unsigned long long n_box = 0, n_tri = 0;
+    const int lane = threadIdx.x & 31;
+    const long long warp_id = (long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+    const bool warp_live = warp_id < warp_count(rc);
+    Receiver r;
+    if (warp_live) r = load_receiver(rc, warp_id, lane);
+    else r.active = false;
+    RunState st = load_state(out, r);
+    for (int b = 0; b < sun.n_blocks; ++b) {
+        __syncthreads();
+        for (int w = threadIdx.x; w < (int)(sizeof(BlockConst) / 4); w += blockDim.x)
+            reinterpret_cast<int*>(&s_bc)[w] = reinterpret_cast<const int*>(&sun.blocks[b])[w];
+        __syncthreads();
+        if (!warp_live) continue;
+        const BlockConst& bc = s_bc;
+        const int K = bc.K;
+        const uint64_t full = (K >= 64) ? ~0ull : ((1ull << K) - 1ull);
+        uint64_t m = 0;
+        const bool wedge = bc.wedge_ok != 0.f;
+        int i = 0;
+        unsigned live = __ballot_sync(kFull, r.active);
+        while (live != 0u && i < sc.n_nodes) {
+            const float4 lo = __ldg(&sc.nodes[2 * i]);
+            const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
+            const int esc = __float_as_int(lo.w);
+            const int tri = __float_as_int(hi.w);
+            const bool want = r.active && m != full;
+            const bool in = want && (wedge ? fan_box(r.o, bc, lo, hi) : slope_box(r.o, bc, lo, hi));
+            if (COUNT && want) ++n_box;
+            if (tri >= 0) {
+                int ka = K, kb = -1;
+                float4 ta, tb, tc;
+                if (in) {
+                    ta = __ldg(&sc.tris[3 * tri]);
+                    tb = __ldg(&sc.tris[3 * tri + 1]);
+                    tc = __ldg(&sc.tris[3 * tri + 2]);
+                    candidate_steps(r.o, bc, bc.psi, ta, tb, tc, &ka, &kb);
+                }
+                const int wa = __reduce_min_sync(kFull, ka);
+                const int wb = __reduce_max_sync(kFull, kb);
+                for (int k = wa; k <= wb; ++k) {
+                    const StepConst s = sun.steps[bc.j0 + k];
+                    const bool test = in && k >= ka && k <= kb && !((m >> k) & 1ull);
+                    if (test) {
+                        if (COUNT) ++n_tri;
+                        bool h;
+                        if (s.kz == 2) h = hit_tri<2>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
+                        else if (s.kz == 0) h = hit_tri<0>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
+                        else h = hit_tri<1>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
+                        if (h) m |= 1ull << k;
+                    }
+                }
+                i = esc;
+                live = __ballot_sync(kFull, r.active && m != full);
+            } else {
+                i = __any_sync(kFull, in) ? i + 1 : esc;
+            }
+        }
+        stitch(st, m, K, bc.new_day);
+        if (out.masks && r.active) out.masks[(long long)bc.mask_block * rc.R + r.out] |= m << bc.mask_bit;
+    }
+    if (warp_live) store_state(out, r, st);
+    if (COUNT && warp_live) flush_counts(out, n_box, n_tri);
+}
+
+long long host_warps(const DevRecv& rc) {
+    if (rc.is_grid) return (long long)((rc.nx + 7) / 8) * ((rc.ny + 3) / 4);
+    return (rc.R + 31) / 32;
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_trace(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                               const DevOut& out, cudaStream_t st) {
+    const long long warps = host_warps(rc);
+    if (warps == 0) return cudaSuccess;
+    const long long ctas = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
+    if (out.stats) k_sweep<true><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, st>>>(sc, rc, sun, out);
+    else k_sweep<false><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, st>>>(sc, rc, sun, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accrual_trace(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                                 const DevOut& out, cudaStream_t st) {
+    const long long warps = host_warps(rc);
+    if (warps == 0) return cudaSuccess;
+    const long long ctas = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
+    if (out.stats) k_accrual<true><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, st>>>(sc, rc, sun, out);
+    else k_accrual<false><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, st>>>(sc, rc, sun, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sa

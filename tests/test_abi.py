@@ -1,0 +1,87 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every declared symbol,
+and rejects bad arguments on the host before touching the device."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(sa_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1907_04435_gb300 import binding
+    return binding.lib()
+
+
+def test_library_exports_every_declared_symbol(L):
+    names = declared_symbols()
+    assert len(names) >= 14
+    for n in sorted(names):
+        assert hasattr(L, n), f"missing export {n}"
+
+
+def test_version_and_empty_error(L):
+    assert L.sa_version() >> 16 == 1
+    assert isinstance(L.sa_last_error(), bytes)
+
+
+def test_grid_receivers_need_no_device(L):
+    from paper_1907_04435_gb300 import binding as B
+    r = B.Receivers.ground_grid(0.0, 0.0, 1.0, 7, 5)
+    assert L.sa_receivers_count(r.handle) == 35
+    h = ct.c_void_p()
+    assert L.sa_receivers_grid(0.0, 0.0, 0.0, 3, 3, ct.byref(h)) == -1       # dx = 0
+    assert L.sa_receivers_grid(0.0, 0.0, 1.0, -1, 3, ct.byref(h)) == -1
+    assert b"grid size" in L.sa_last_error()
+
+
+def test_sun_validation_happens_on_the_host(L):
+    from paper_1907_04435_gb300 import binding as B
+    h = ct.c_void_p()
+    bad = np.array([[0.6, 0.0, 0.8], [0.8, 0.0, -0.6]], np.float32)
+    ds = np.array([0, 2], np.int32)
+    assert L.sa_sun_create(B._ptr(bad), 2, B._ptr(ds), 1, 0, None, ct.byref(h)) == -4
+    unnorm = np.array([[0.6, 0.0, 0.9]], np.float32)
+    assert L.sa_sun_create(B._ptr(unnorm), 1, B._ptr(np.array([0, 1], np.int32)), 1, 0, None,
+                           ct.byref(h)) == -1
+    ok = np.array([[0.6, 0.0, 0.8]], np.float32)
+    assert L.sa_sun_create(B._ptr(ok), 1, B._ptr(np.array([0, 2], np.int32)), 1, 0, None,
+                           ct.byref(h)) == -1          # day_start[D] != S
+    assert L.sa_sun_create(B._ptr(ok), 1, B._ptr(np.array([0, 1], np.int32)), 1, 65, None,
+                           ct.byref(h)) == -1          # block_len > 64
+
+
+def test_scene_validation_happens_on_the_host(L):
+    from paper_1907_04435_gb300 import binding as B
+    h = ct.c_void_p()
+    v = np.zeros((3, 3), np.float32)
+    t = np.array([[0, 1, 3]], np.int32)
+    assert L.sa_scene_from_mesh(B._ptr(v), 3, B._ptr(t), 1, None, 1, 0, None, ct.byref(h)) == -1
+    v[1, 2] = np.nan
+    t = np.array([[0, 1, 2]], np.int32)
+    assert L.sa_scene_from_mesh(B._ptr(v), 3, B._ptr(t), 1, None, 1, 0, None, ct.byref(h)) == -5
+    v[1, 2] = 0
+    b = np.array([4], np.int32)
+    assert L.sa_scene_from_mesh(B._ptr(v), 3, B._ptr(t), 1, B._ptr(b), 2, 0, None, ct.byref(h)) == -1
+
+
+def test_block_partition_mirror():
+    from paper_1907_04435_gb300.binding import block_sizes
+    assert block_sizes([0, 481]) == [54, 54, 54, 54, 53, 53, 53, 53, 53]
+    assert sum(block_sizes([0, 481])) == 481
+    assert block_sizes([0, 5, 5, 70], 64) == [5, 33, 32]
+    assert block_sizes([0, 3], 1) == [1, 1, 1]
+    assert max(block_sizes([0, 1000], 64)) <= 64

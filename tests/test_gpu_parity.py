@@ -1,0 +1,183 @@
+"""GPU parity of every exact method against the FP64 oracle (through the C ABI)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import city as C
+from synth import configs
+from synth.sun import sun_table
+
+from parity import (assert_bits_parity, assert_counts_parity, cached_oracle, workload)
+
+pytestmark = pytest.mark.gpu
+
+EXACT = ["sweep_trace", "accrual_trace", "accrual_sam", "sweep_raster"]
+POINT_METHODS = ["sweep_trace", "accrual_trace", "accrual_sam"]
+
+
+def _scene(B, w):
+    return B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B)
+
+
+def _ground(B, w):
+    g = w.ground
+    return B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+
+
+def _run(B, scene, recv, sun, method, minutes=1.0):
+    g, m, c = B.sa_accumulate(scene, recv, sun, minutes, method)
+    torch.cuda.synchronize()
+    return g.cpu().numpy(), m.cpu().numpy(), c.cpu().numpy()
+
+
+@pytest.mark.parametrize("method", EXACT)
+def test_boxes16_ground_counts(cuda_lib, method):
+    B = cuda_lib
+    w = workload("boxes16")
+    bits, near = cached_oracle("boxes16/ground", w, "ground")
+    sc, rc, sun = _scene(B, w), _ground(B, w), B.Sun(w.sun.dirs, w.sun.day_start)
+    g, m, c = _run(B, sc, rc, sun, method, w.sun.step_minutes)
+    assert_counts_parity(g, c, bits, near, w.sun.day_start, method)
+    assert np.allclose(m, g * np.float32(w.sun.step_minutes))
+
+
+@pytest.mark.parametrize("method", EXACT)
+def test_boxes16_ground_bits(cuda_lib, method):
+    B = cuda_lib
+    w = workload("boxes16")
+    bits, near = cached_oracle("boxes16/ground", w, "ground")
+    sc, rc, sun = _scene(B, w), _ground(B, w), B.Sun(w.sun.dirs, w.sun.day_start)
+    masks = B.sa_shadow_masks(sc, rc, sun, method)
+    torch.cuda.synchronize()
+    gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start))
+    assert_bits_parity(gb, bits, near, method)
+
+
+@pytest.mark.parametrize("method", EXACT)
+@pytest.mark.parametrize("block_len", [0, 7, 64])
+def test_district_small_ground(cuda_lib, method, block_len):
+    """200 x 150 cells (ragged 32-cell tiles and 8 x 4 warp patches), 120 buildings."""
+    B = cuda_lib
+    w = workload("district_small")
+    bits, near = cached_oracle("district_small/ground", w, "ground")
+    sc, rc = _scene(B, w), _ground(B, w)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start, block_len)
+    g, _, c = _run(B, sc, rc, sun, method)
+    assert_counts_parity(g, c, bits, near, w.sun.day_start, f"{method}/K{block_len}")
+    masks = B.sa_shadow_masks(sc, rc, sun, method)
+    gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start, block_len))
+    assert_bits_parity(gb, bits, near, f"{method}/K{block_len}")
+
+
+@pytest.mark.parametrize("method", POINT_METHODS)
+def test_district_small_facades(cuda_lib, method):
+    B = cuda_lib
+    w = workload("district_small")
+    bits, near = cached_oracle("district_small/facade", w, "facade")
+    sc = _scene(B, w)
+    rc = B.Receivers.points(w.facade_pos, w.facade_nrm)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    g, _, c = _run(B, sc, rc, sun, method)
+    assert_counts_parity(g, c, bits, near, w.sun.day_start, method)
+    masks = B.sa_shadow_masks(sc, rc, sun, method)
+    gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start))
+    assert_bits_parity(gb, bits, near, method)
+
+
+def test_point_receivers_on_the_ground_match_the_grid(cuda_lib):
+    """Ground cells passed as points (no normal) give the grid's result."""
+    B = cuda_lib
+    w = workload("district_small")
+    sc = _scene(B, w)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    gg, _, gc = _run(B, sc, _ground(B, w), sun, "accrual_trace")
+    pg, _, pc = _run(B, sc, B.Receivers.points(w.ground.positions()), sun, "accrual_trace")
+    assert np.array_equal(gg, pg) and np.array_equal(gc, pc)
+
+
+def test_theorem1_accrual_raster_equals_per_step_raster(cuda_lib):
+    """Theorem 1 (Sec. 4): one accrual pass per block gives the same slices as one map per
+    step -- here bit for bit, over every receiver, boundary or not."""
+    B = cuda_lib
+    w = workload("district_small")
+    sc, rc = _scene(B, w), _ground(B, w)
+    for K in (0, 13, 64):
+        sun = B.Sun(w.sun.dirs, w.sun.day_start, K)
+        a = B.sa_shadow_masks(sc, rc, sun, "accrual_sam")
+        b = B.sa_shadow_masks(sc, rc, sun, "sweep_raster")
+        assert torch.equal(a, b)
+
+
+def test_multi_day_stitching_and_progressive_accumulation(cuda_lib):
+    """Three days: runs restart each day (continuous = max over days), blocks of 7 steps
+    are stitched with prefix / max / suffix, and day-by-day accumulation equals one call."""
+    B = cuda_lib
+    w = configs.district_small(doys=(172, 200, 250), step=8.0, n_facade=0)
+    bits, near = cached_oracle("district_small_3d/ground", w, "ground")
+    sc, rc = _scene(B, w), _ground(B, w)
+    ds = w.sun.day_start
+    for method in EXACT:
+        sun = B.Sun(w.sun.dirs, ds, 7)
+        g, _, c = _run(B, sc, rc, sun, method, 8.0)
+        assert_counts_parity(g, c, bits, near, ds, method)
+        gacc = torch.zeros(rc.R, dtype=torch.int32, device="cuda")
+        cacc = torch.zeros(rc.R, dtype=torch.int32, device="cuda")
+        for k in range(len(ds) - 1):
+            d = w.sun.dirs[ds[k]:ds[k + 1]]
+            sun_k = B.Sun(d, np.array([0, d.shape[0]], np.int32), 7)
+            B.sa_accumulate(sc, rc, sun_k, 8.0, method, accumulate_into=True, gross=gacc,
+                            continuous=cacc, want_minutes=False)
+        assert np.array_equal(gacc.cpu().numpy(), g) and np.array_equal(cacc.cpu().numpy(), c)
+
+
+def test_empty_scene_and_empty_receivers(cuda_lib):
+    B = cuda_lib
+    w = workload("boxes16")
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    empty = B.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32))
+    rc = _ground(B, w)
+    for method in EXACT:
+        g, _, c = _run(B, empty, rc, sun, method)
+        assert g.sum() == 0 and c.sum() == 0
+    none = B.Receivers.points(np.zeros((0, 3), np.float32))
+    g, m, c = B.sa_accumulate(_scene(B, w), none, sun, 2.0, "accrual_trace")
+    assert g.numel() == 0
+
+
+def test_single_triangle_scene(cuda_lib):
+    B = cuda_lib
+    v = np.array([[0, 0, 10], [10, 0, 10], [0, 10, 10]], np.float32)
+    t = np.array([[0, 1, 2]], np.int32)
+    sc = B.Scene(v, t)
+    st = sun_table(40.7, [172], 11.0, 13.0, 5.0)
+    sun = B.Sun(st.dirs, st.day_start)
+    grid = C.GroundGrid(-20.0, -20.0, 0.5, 80, 80)
+    rc = B.Receivers.ground_grid(grid.x0, grid.y0, grid.dx, grid.nx, grid.ny)
+    bits = oracle.shadow_bits(v.reshape(1, 9), None, grid.positions(), None, st.dirs)
+    near = oracle.near_boundary(v.reshape(1, 9), None, grid.positions(), None, st.dirs,
+                                st.day_start, bits)
+    for method in EXACT:
+        g, _, c = _run(B, sc, rc, sun, method)
+        assert_counts_parity(g, c, bits, near, st.day_start, method)
+        assert g.sum() > 0
+
+
+def test_receivers_inside_footprints_are_always_shadowed(cuda_lib):
+    B = cuda_lib
+    w = workload("boxes16")
+    cen = np.array([[fp[:, 0].mean(), fp[:, 1].mean(), 0.0] for fp in w.city.footprints], np.float32)
+    sc, sun = _scene(B, w), B.Sun(w.sun.dirs, w.sun.day_start)
+    for method in POINT_METHODS:
+        g, _, c = _run(B, sc, B.Receivers.points(cen), sun, method)
+        assert (g == w.sun.S).all() and (c == w.sun.S).all()
+
+
+def test_raster_methods_reject_point_receivers(cuda_lib):
+    B = cuda_lib
+    w = workload("boxes16")
+    sc, sun = _scene(B, w), B.Sun(w.sun.dirs, w.sun.day_start)
+    rc = B.Receivers.points(w.ground.positions()[:10])
+    with pytest.raises(B.SAError) as e:
+        B.sa_accumulate(sc, rc, sun, 1.0, "sweep_raster")
+    assert e.value.status == -8
