@@ -91,6 +91,13 @@ def make_workload(name: str):
     from synth import configs
     if name == "district":
         return configs.district()
+    if name == "district_1k":
+        # the district's city with a 1024 x 1024 ground grid over its centre and 250k
+        # facade samples: a quarter-size case for detailed profiles
+        w = configs.district(n_facade=250_000)
+        from synth.city import GroundGrid
+        w.ground = GroundGrid(x0=512.0, y0=512.0, dx=1.0, nx=1024, ny=1024)
+        return w
     if name == "district_small":
         return configs.district_small()
     if name == "boxes16":
@@ -191,6 +198,14 @@ def run_gpu(args):
             tf += ev[1].elapsed_time(ev[2])
             tot += ev[0].elapsed_time(ev[2])
         return tot / steps, tg / steps, tf / steps
+
+    if args.only_step:
+        # profiling mode: W warm-up steps and K timed steps of the headline method only
+        ms, ms_g, ms_f = timed("accrual_sam", "accrual_trace", args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"only_step": True, "workload": args.workload, "ms_per_step": ms,
+                              "ground_ms": ms_g, "facade_ms": ms_f}))
+        return
 
     # ---- headline: shadow accrual (ground accrual raster + facade ray-traced accrual)
     if world > 1:
@@ -363,6 +378,8 @@ def main():
     ap.add_argument("--workload", default="district")
     ap.add_argument("--block-len", dest="block_len", type=int, default=0)
     ap.add_argument("--skip-baselines", action="store_true")
+    ap.add_argument("--only-step", action="store_true",
+                    help="time the headline method only (for profiler runs); prints one JSON line")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
