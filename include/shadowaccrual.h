@@ -170,6 +170,39 @@ sa_status sa_shadow_masks(const sa_scene* scene, const sa_receivers* recv, const
 sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
                            sa_method method, uint64_t* counters, void* stream);
 
+/* ------------------------------------------------------------ allocation-free variant
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate
+ * device memory while they run -- for example a host application that reserved the
+ * device's memory for itself before loading this library, or a loop that must not pay
+ * the allocator's synchronisation and latency.
+ *
+ * Same result as sa_accumulate(..., SA_ACCRUAL_SAM, ...) on a ground grid (the ground
+ * accrual raster), but it calls no cudaMalloc, cudaMallocAsync, cudaFree or other
+ * allocating routine: every scratch buffer (run state, tile bins, scan partials) comes
+ * from one fixed device array of SA_NOALLOC_SCRATCH_BYTES (64 MiB) compiled into the
+ * library, which every GPU that loads the library keeps until the process exits.  The
+ * caller still passes the outputs (as for sa_accumulate; gross_minutes and
+ * continuous_steps may be NULL).
+ *   - grid must come from sa_receivers_grid with at most SA_NOALLOC_MAX_CELLS cells
+ *     (2048 x 2048); larger grids are rejected with SA_ERR_INVALID_ARG.  If a single
+ *     block's triangle-tile bins do not fit the remaining scratch the call also returns
+ *     SA_ERR_INVALID_ARG (use a shorter block_len or a smaller grid).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture.
+ *   - All calls in the process share the one array per device and it keeps the previous
+ *     call's contents (each call clears what it needs).  Calls that can overlap on the GPU
+ *     -- on different streams or threads of the same device -- race on it: serialise them.
+ *   - Like the other raster methods it needs scene geometry at z >= 0
+ *     (SA_ERR_UNSUPPORTED otherwise) and synchronises `stream` once per chunk of blocks to
+ *     size the bins. */
+#define SA_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+#define SA_NOALLOC_MAX_CELLS 4194304
+sa_status sa_accumulate_grid_noalloc(const sa_scene* scene, const sa_receivers* grid,
+                                     const sa_sun* sun, float step_minutes, int32_t flags,
+                                     int32_t* gross_steps, float* gross_minutes,
+                                     int32_t* continuous_steps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,9 +65,11 @@ def lib():
             L.sa_receivers_count.restype = i64
             L.sa_accumulate.argtypes = [P, P, P, f32, i32, i32, i32, P, P, P, P]
             L.sa_shadow_masks.argtypes = [P, P, P, i32, i32, P, P]
+            L.sa_accumulate_grid_noalloc.argtypes = [P, P, P, f32, i32, P, P, P, P]
+            L.sa_work_counters.argtypes = [P, P, P, i32, P, P]
             for name in ("sa_scene_from_mesh", "sa_scene_info", "sa_sun_create", "sa_sun_info",
                          "sa_receivers_grid", "sa_receivers_points", "sa_accumulate",
-                         "sa_shadow_masks"):
+                         "sa_shadow_masks", "sa_accumulate_grid_noalloc", "sa_work_counters"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
     return _lib
@@ -210,6 +212,29 @@ def sa_accumulate(scene: Scene, recv: Receivers, sun: Sun, step_minutes: float, 
                                _ptr(gross), _ptr(minutes), _ptr(continuous),
                                ct.c_void_p(_stream(stream))))
     return gross, minutes, continuous
+
+
+def sa_accumulate_grid_noalloc(scene: Scene, grid: Receivers, sun: Sun, step_minutes: float,
+                               gross, minutes=None, continuous=None, accumulate_into=False,
+                               stream=None):
+    """The ground accrual raster with no device allocation: the caller passes every output
+    tensor (already allocated); the library's scratch is a fixed array compiled into it."""
+    _check(lib().sa_accumulate_grid_noalloc(scene.handle, grid.handle, sun.handle,
+                                            float(step_minutes),
+                                            SA_ACCUMULATE_INTO if accumulate_into else 0,
+                                            _ptr(gross), _ptr(minutes), _ptr(continuous),
+                                            ct.c_void_p(_stream(stream))))
+    return gross, minutes, continuous
+
+
+def sa_work_counters(scene: Scene, recv: Receivers, sun: Sun, method, stream=None):
+    """Work counters of one accumulation: (box tests, triangle tests, raster set-ups,
+    raster cell tests), as Python ints."""
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    c = torch.zeros(4, dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device()))
+    _check(lib().sa_work_counters(scene.handle, recv.handle, sun.handle, m, _ptr(c),
+                                  ct.c_void_p(_stream(stream))))
+    return [int(x) for x in c.cpu().tolist()]
 
 
 def sa_shadow_masks(scene: Scene, recv: Receivers, sun: Sun, method, iam_levels: int = 0,

@@ -9,33 +9,7 @@
 #include <new>
 #include <vector>
 
-#include "sa_internal.cuh"
-
-struct sa_scene {
-    sa::LbvhBuild bvh;
-    long long T;
-    int n_buildings;
-    float min_z;
-};
-
-struct sa_sun {
-    int S, D;
-    std::vector<sa::StepConst> h_steps;
-    std::vector<sa::BlockConst> h_blocks;        // requested block length
-    std::vector<sa::BlockConst> h_step_blocks;   // one step per block
-    sa::StepConst* d_steps = nullptr;
-    sa::BlockConst* d_blocks = nullptr;
-    sa::BlockConst* d_step_blocks = nullptr;
-};
-
-struct sa_receivers {
-    int is_grid;
-    float x0, y0, dx;
-    int nx, ny;
-    long long R;
-    float4* d_orig = nullptr;
-    int* d_perm = nullptr;
-};
+#include "sa_handles.cuh"
 
 namespace {
 
@@ -194,6 +168,10 @@ sa_status host_copy(const T* src, size_t n, int device_ptrs, std::vector<T>* out
 }
 
 }  // namespace
+
+namespace sa {
+sa_status report_error(sa_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace sa
 
 extern "C" {
 

@@ -209,5 +209,16 @@ cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, long long n, cudaSt
 
 // exclusive scan of n uint32 (in place); writes the total to *d_total if non-null
 cudaError_t exclusive_scan_u32(unsigned* data, long long n, unsigned* d_total, cudaStream_t st);
+// the same scan with caller-provided partials (scan_partials(n) words); allocates nothing
+long long scan_partials(long long n);
+cudaError_t exclusive_scan_u32_with(unsigned* data, long long n, unsigned* partial,
+                                    unsigned* d_total, cudaStream_t st);
+
+// The ground accrual raster with every scratch buffer carved from `scratch` (bytes long,
+// 256-byte aligned); allocates nothing.  *capacity_error is set to 1 (and cudaSuccess
+// returned) when the receivers' state or a single block's bins do not fit.
+cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                                    const DevOut& out, cudaStream_t st, unsigned char* scratch,
+                                    size_t bytes, int* capacity_error);
 
 }  // namespace sa

@@ -353,4 +353,95 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
     return e;
 }
 
+namespace {
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+}  // namespace
+
+cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                                    const DevOut& out, cudaStream_t st, unsigned char* scratch,
+                                    size_t bytes, int* capacity_error) {
+    *capacity_error = 0;
+    TileGeom g;
+    g.x0 = rc.x0; g.y0 = rc.y0; g.dx = rc.dx; g.nx = rc.nx; g.ny = rc.ny;
+    g.tiles_x = (rc.nx + kTile - 1) / kTile;
+    g.tiles_y = (rc.ny + kTile - 1) / kTile;
+    const int n_tiles = g.tiles_x * g.tiles_y;
+    const long long R = (long long)rc.nx * rc.ny;
+    if (R == 0) return cudaSuccess;
+    const int max_chunk = 16;
+    const size_t nc = (size_t)max_chunk * n_tiles;
+    // carve: run [R], best [R] (when the caller passes no continuous buffer), total,
+    // counts / offsets / cursor [max_chunk * tiles], scan partials, bins (the rest)
+    size_t off = 0;
+    int* run = reinterpret_cast<int*>(scratch + off);
+    off += align256(sizeof(int) * (size_t)R);
+    int* best = out.continuous;
+    if (!best) {
+        best = reinterpret_cast<int*>(scratch + off);
+        off += align256(sizeof(int) * (size_t)R);
+    }
+    unsigned* d_total = reinterpret_cast<unsigned*>(scratch + off);
+    off += 256;
+    unsigned* counts = reinterpret_cast<unsigned*>(scratch + off);
+    off += align256(sizeof(unsigned) * nc);
+    unsigned* offsets = reinterpret_cast<unsigned*>(scratch + off);
+    off += align256(sizeof(unsigned) * nc);
+    unsigned* cursor = reinterpret_cast<unsigned*>(scratch + off);
+    off += align256(sizeof(unsigned) * nc);
+    unsigned* partial = reinterpret_cast<unsigned*>(scratch + off);
+    off += align256(sizeof(unsigned) * (size_t)scan_partials((long long)nc));
+    if (off >= bytes) { *capacity_error = 1; return cudaSuccess; }
+    int* bins = reinterpret_cast<int*>(scratch + off);
+    const size_t bins_cap = (bytes - off) / sizeof(int);
+    DevOut o = out;
+    o.run = run;
+    cudaError_t e = cudaSuccess;
+    if (out.accumulate_into) {
+        e = cudaMemsetAsync(run, 0, sizeof(int) * (size_t)R, st);
+        if (e == cudaSuccess && !out.continuous) e = cudaMemsetAsync(best, 0, sizeof(int) * (size_t)R, st);
+        if (e != cudaSuccess) return e;
+    }
+    const int tpb = 128;
+    int b0 = 0;
+    int nbc = sun.n_blocks < max_chunk ? sun.n_blocks : max_chunk;
+    while (b0 < sun.n_blocks) {
+        if (b0 + nbc > sun.n_blocks) nbc = sun.n_blocks - b0;
+        const size_t ncc = (size_t)nbc * n_tiles;
+        e = cudaMemsetAsync(counts, 0, sizeof(unsigned) * ncc, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(unsigned) * ncc, st);
+        if (e != cudaSuccess) return e;
+        unsigned total = 0;
+        dim3 grid((sc.T + tpb - 1) / tpb, nbc);
+        if (sc.T > 0) {
+            k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.blocks, b0, g, counts);
+            e = cudaMemcpyAsync(offsets, counts, sizeof(unsigned) * ncc, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = exclusive_scan_u32_with(offsets, (long long)ncc, partial, d_total, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
+        } else {
+            e = cudaMemsetAsync(offsets, 0, sizeof(unsigned) * ncc, st);
+            if (e != cudaSuccess) return e;
+        }
+        if ((size_t)total > bins_cap) {
+            if (nbc == 1) { *capacity_error = 1; return cudaSuccess; }
+            nbc = (nbc + 1) / 2;          // retry this chunk with fewer blocks
+            continue;
+        }
+        if (total > 0) k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.blocks, b0, g, offsets, cursor, bins);
+        RasterArgs ra;
+        ra.sc = sc; ra.sun = sun; ra.g = g; ra.b0 = b0; ra.nbc = nbc;
+        ra.offsets = offsets; ra.counts = counts; ra.bins = bins;
+        ra.out = o; ra.best = best;
+        ra.load_state = (b0 > 0) || out.accumulate_into;
+        ra.final_chunk = (b0 + nbc >= sun.n_blocks);
+        ra.R = R;
+        k_raster<<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        b0 += nbc;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace sa

@@ -179,6 +179,21 @@ cudaError_t exclusive_scan_u32(unsigned* data, long long n, unsigned* d_total, c
     return e != cudaSuccess ? e : e2;
 }
 
+long long scan_partials(long long n) { return (n + kScanTile - 1) / kScanTile; }
+
+cudaError_t exclusive_scan_u32_with(unsigned* data, long long n, unsigned* partial,
+                                    unsigned* d_total, cudaStream_t st) {
+    if (n <= 0) {
+        if (d_total) return cudaMemsetAsync(d_total, 0, sizeof(unsigned), st);
+        return cudaSuccess;
+    }
+    const int np = (int)scan_partials(n);
+    k_scan_reduce<<<np, kScanThreads, 0, st>>>(data, n, partial);
+    k_scan_partials<<<1, kScanThreads, 0, st>>>(partial, np, d_total);
+    k_scan_apply<<<np, kScanThreads, 0, st>>>(data, n, partial);
+    return cudaGetLastError();
+}
+
 cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, long long n, cudaStream_t st) {
     if (n <= 1) return cudaSuccess;
     const int n_tiles = (int)((n + kSortTile - 1) / kSortTile);
