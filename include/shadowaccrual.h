@@ -99,6 +99,25 @@ sa_status sa_scene_from_mesh(const float* verts, int64_t nv, const int32_t* tris
                              const int32_t* tri_building, int32_t n_buildings,
                              int32_t device_ptrs, void* stream, sa_scene** out);
 
+/* Build a scene from extruded building footprints (Sec. 8.2: the city is a mesh of extruded
+ * OpenStreetMap footprints).  xy float [nv][2]: vertices of every footprint, each a convex
+ * counter-clockwise polygon of >= 3 vertices; poly_off int32 [n_buildings + 1]: footprint b
+ * is xy[poly_off[b] .. poly_off[b+1]); heights float [n_buildings] (> 0 m).  Building b
+ * becomes a closed prism: walls split into nb = max(1, ceil(h_b / band_height)) bands
+ * (band_height 0: one band), two triangles per band and edge, a roof fan and a bottom fan
+ * at z = 0; triangle building ids are b.  Extrusion and BVH build run on the device.  The
+ * band counts are fixed here, so sa_scene_set_heights keeps the topology.
+ * Errors: SA_ERR_INVALID_ARG (sizes, non-convex or clockwise footprints, heights <= 0),
+ * SA_ERR_DEGENERATE, SA_ERR_OOM, SA_ERR_CUDA. */
+sa_status sa_scene_from_footprints(const float* xy, const int32_t* poly_off, int32_t n_buildings,
+                                   const float* heights, float band_height, int32_t device_ptrs,
+                                   void* stream, sa_scene** out);
+
+/* Replace the heights of a footprint scene (host or device float [n_buildings]) and
+ * rebuild its mesh and BVH (synchronises `stream`).  SA_ERR_UNSUPPORTED for mesh scenes. */
+sa_status sa_scene_set_heights(sa_scene* scene, const float* heights, int32_t device_ptrs,
+                               void* stream);
+
 /* Release a scene (NULL is ignored). Synchronises the device first. */
 void sa_scene_destroy(sa_scene* scene);
 
@@ -161,6 +180,21 @@ sa_status sa_accumulate(const sa_scene* scene, const sa_receivers* recv, const s
  * shadow(r, first step of block b + k).  Same methods as sa_accumulate. */
 sa_status sa_shadow_masks(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
                           sa_method method, int32_t iam_levels, uint64_t* masks, void* stream);
+
+/* Height gradient of the shadow-minutes of a ground grid (no counterpart in the paper, which
+ * motivates height trade-offs in its case studies, Sec. 9).  Objective: between consecutive
+ * steps of a day the sun moves on the great circle through their directions, at constant
+ * rate over step_minutes; a receiver counts step_minutes * chi over an interval whose end
+ * statuses agree, and the shadowed part of it where its status flips once.
+ *   S = sum_r w_r * (those minutes),  w_r = weights[r] (dev float [R], NULL = 1).
+ * Writes dS_dh (dev float [n_buildings]) and, if S_out is non-NULL, S (dev double [1]).
+ * Flips come from the forward step masks (ground accrual raster); each flip time and its
+ * derivative with respect to the height of the building whose roof edge casts it are
+ * computed in FP64.  Needs a scene from sa_scene_from_footprints and a ground grid.
+ * Errors: SA_ERR_INVALID_ARG, SA_ERR_UNSUPPORTED, SA_ERR_OOM, SA_ERR_CUDA. */
+sa_status sa_height_grad(const sa_scene* scene, const sa_receivers* grid, const sa_sun* sun,
+                         float step_minutes, const float* weights, float* dS_dh, double* S_out,
+                         void* stream);
 
 /* Work counters of one accumulation (diagnostics for roofline accounting): runs `method`
  * with counting enabled and writes counters uint64 [4] dev: [0] ray/fan-versus-box tests

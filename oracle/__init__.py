@@ -45,6 +45,10 @@ def lib():
             L.sao_shadow_bits.argtypes = [P, P, i64, P, P, i64, P, i32, P, ci]
             L.sao_near_boundary.argtypes = [P, P, i64, P, P, i64, P, P, i32, f64, P, P, ci]
             L.sao_reduce.argtypes = [P, i64, P, i32, P, P]
+            f32 = ct.c_float
+            L.sao_shadow_integral.argtypes = [P, P, i64, P, i64, P, P, i32, f64, P, i32, P, P, ci]
+            L.sao_iam.argtypes = [P, P, i64, f32, f32, f32, i32, i32, P, P, P, i32, i32, f64,
+                                  i32, i32, P, ci]
             _lib = L
     return _lib
 
@@ -104,6 +108,66 @@ def reduce(bits, day_start):
     if rc != 0:
         raise RuntimeError(f"sao_reduce failed: {rc}")
     return g, c
+
+
+def block_partition(day_start, block_len: int = 0):
+    """Blocks of <= block_len (0: 60) consecutive steps per day, balanced: (j0 [], K [])."""
+    K = block_len or 60
+    j0s, Ks = [], []
+    ds = [int(x) for x in np.asarray(day_start).reshape(-1)]
+    for a, b in zip(ds[:-1], ds[1:]):
+        n = b - a
+        if n <= 0:
+            continue
+        nb = (n + K - 1) // K
+        base, rem = divmod(n, nb)
+        j = a
+        for q in range(nb):
+            k = base + (1 if q < rem else 0)
+            j0s.append(j)
+            Ks.append(k)
+            j += k
+    return np.asarray(j0s, np.int32), np.asarray(Ks, np.int32)
+
+
+IAM_LINE_SUPERCOVER, IAM_LINE_THIN = 0, 1
+
+
+def iam_bits(tri9, tri_building, grid, dirs, day_start, block_len=0, levels=3,
+             tmin_src=1.0, line_mode=IAM_LINE_THIN, nthreads: int | None = None) -> np.ndarray:
+    """uint8 [R, S]: the inverse-accrual-map bits (Sec. 5) of a ground grid (x0, y0, dx,
+    nx, ny), from L = `levels` source levels traced at both ends of every block."""
+    tri9, tb, dirs = _f32(tri9), _i32(tri_building), _f32(dirs)
+    x0, y0, dx, nx, ny = grid
+    j0, K = block_partition(day_start, block_len)
+    S = dirs.shape[0]
+    out = np.zeros((int(nx) * int(ny), S), np.uint8)
+    rc = lib().sao_iam(_ptr(tri9), _ptr(tb), tri9.shape[0], float(x0), float(y0), float(dx),
+                       int(nx), int(ny), _ptr(dirs), _ptr(j0), _ptr(K), j0.shape[0], int(levels),
+                       float(tmin_src), int(line_mode), S, _ptr(out), nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"sao_iam failed: {rc}")
+    return out
+
+
+def shadow_integral(tri9, tri_building, pos, dirs, day_start, step_minutes, weights=None,
+                    bisect_iters: int = 60, per_receiver: bool = False,
+                    nthreads: int | None = None):
+    """Continuous-time shadow-minutes S of ground receivers (sun slerped between steps,
+    status flips found by bisection), summed with optional per-receiver weights."""
+    tri9, tb, pos, dirs = _f32(tri9), _i32(tri_building), _f32(pos), _f32(dirs)
+    ds = _i32(day_start)
+    R = pos.shape[0]
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    S = ct.c_double()
+    per = np.zeros(R, np.float64) if per_receiver else None
+    rc = lib().sao_shadow_integral(_ptr(tri9), _ptr(tb), tri9.shape[0], _ptr(pos), R, _ptr(dirs),
+                                   _ptr(ds), ds.shape[0] - 1, float(step_minutes), _ptr(w),
+                                   int(bisect_iters), ct.byref(S), _ptr(per),
+                                   nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"sao_shadow_integral failed: {rc}")
+    return (S.value, per) if per_receiver else S.value
 
 
 def accumulate(tri9, tri_building, pos, nrm, dirs, day_start, step_minutes,

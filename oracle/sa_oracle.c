@@ -295,3 +295,235 @@ int sao_reduce(const uint8_t* bits, int64_t R, const int32_t* day_start, int32_t
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------
+ * Inverse accrual map (Sec. 5), in the paper's steps, FP64.  An approximation by design.
+ *
+ * For each block of steps [j0, j0 + K) and each ground cell centre p of the grid:
+ *   1. Forward map (t_1 -> t_n): cast the ray from p toward the sun at the block's first
+ *      step; each intersection farther than `tmin_src` (the paper's 100 cm) is a source
+ *      of shadow; keep the L closest (source levels l = 1..L).
+ *   2. For each source s, its shadow at step k is q_k, the projection of s along d_k onto
+ *      the ground.  The shadow line from p (= q_0) to q_{K-1} is cut into K - 1 pieces
+ *      [q_k, q_{k+1}]; bit k of every cell the piece touches is set, and bit K-1 of the
+ *      cell(s) of q_{K-1}.
+ *   3. Reverse map (t_n -> t_1): the same from the block's last step, the pieces running
+ *      backwards: [q_k, q_{k-1}] sets bit k, and bit 0 is set at q_0.
+ * Cells are closed squares of side dx around the centres ("touches" includes edges and
+ * corners).  Gross and continuous shadow then follow from the bits as in Sec. 3.1.
+ * ------------------------------------------------------------------------------------ */
+
+typedef struct { double t; } ohit;
+
+/* all hits with t > tmin along o + t d; keeps the L smallest t in ascending order */
+static int nearest_hits(const oscene* s, const double* o, const double* d, double tmin, int L,
+                        double* best) {
+    int n = 0;
+    for (int32_t g = 0; g < s->G; ++g) {
+        if (!ray_box(o, d, s->gbox + 6 * g)) continue;
+        for (int64_t i = s->goff[g]; i < s->goff[g + 1]; ++i) {
+            double t;
+            if (!ray_tri(o, d, &s->tri[s->gtri[i]], tmin, &t)) continue;
+            if (n < L) {
+                int k = n++;
+                while (k > 0 && best[k - 1] > t) { best[k] = best[k - 1]; --k; }
+                best[k] = t;
+            } else if (t < best[L - 1]) {
+                int k = L - 1;
+                while (k > 0 && best[k - 1] > t) { best[k] = best[k - 1]; --k; }
+                best[k] = t;
+            }
+        }
+    }
+    return n;
+}
+
+typedef struct {
+    double x0, y0, dx;
+    int32_t nx, ny;
+} ogrid;
+
+static void set_bit_cell(uint8_t* blk, int32_t K, int64_t cell, int32_t k) {
+    uint8_t* b = blk + cell * K + k;
+#pragma omp atomic write
+    *b = 1;
+}
+
+/* thin line: m = ceil(max(|dx|, |dy|) / cell) + 1 equally spaced samples from P to Q
+ * (both ends included); the cell holding each sample (half-open cells) gets bit k */
+static void draw_thin(const ogrid* g, double px, double py, double qx, double qy,
+                      uint8_t* blk, int32_t K, int32_t k) {
+    const double len = fmax(fabs(qx - px), fabs(qy - py)) / g->dx;
+    const int64_t m = (int64_t)ceil(len) + 1;
+    for (int64_t i = 0; i < m; ++i) {
+        const double a = m > 1 ? (double)i / (double)(m - 1) : 0.0;
+        const double x = px + a * (qx - px), y = py + a * (qy - py);
+        const double fx = floor((x - g->x0) / g->dx), fy = floor((y - g->y0) / g->dx);
+        if (fx < 0 || fy < 0 || fx >= g->nx || fy >= g->ny) continue;
+        set_bit_cell(blk, K, (int64_t)fy * g->nx + (int64_t)fx, k);
+    }
+}
+
+/* every closed cell touched by the segment P -> Q gets bit k */
+static void draw_segment(const ogrid* g, double px, double py, double qx, double qy,
+                         uint8_t* blk, int32_t K, int32_t k) {
+    const double ymin = fmin(py, qy), ymax = fmax(py, qy);
+    int64_t iy0 = (int64_t)ceil((ymin - g->y0) / g->dx) - 1;
+    int64_t iy1 = (int64_t)floor((ymax - g->y0) / g->dx);
+    if (iy0 < 0) iy0 = 0;
+    if (iy1 > g->ny - 1) iy1 = g->ny - 1;
+    for (int64_t iy = iy0; iy <= iy1; ++iy) {
+        const double b0 = g->y0 + (double)iy * g->dx, b1 = b0 + g->dx;
+        double xa, xb;
+        if (py == qy) {
+            if (py < b0 || py > b1) continue;
+            xa = fmin(px, qx); xb = fmax(px, qx);
+        } else {
+            double ta = (b0 - py) / (qy - py), tb = (b1 - py) / (qy - py);
+            double lo = fmax(fmin(ta, tb), 0.0), hi = fmin(fmax(ta, tb), 1.0);
+            if (lo > hi) continue;
+            double x1 = px + lo * (qx - px), x2 = px + hi * (qx - px);
+            xa = fmin(x1, x2); xb = fmax(x1, x2);
+        }
+        int64_t ix0 = (int64_t)ceil((xa - g->x0) / g->dx) - 1;
+        int64_t ix1 = (int64_t)floor((xb - g->x0) / g->dx);
+        if (ix0 < 0) ix0 = 0;
+        if (ix1 > g->nx - 1) ix1 = g->nx - 1;
+        for (int64_t ix = ix0; ix <= ix1; ++ix) set_bit_cell(blk, K, iy * g->nx + ix, k);
+    }
+}
+
+int sao_iam(const float* tri9, const int32_t* tri_building, int64_t T,
+            float x0, float y0, float dx, int32_t nx, int32_t ny,
+            const float* dirs, const int32_t* block_j0, const int32_t* block_K, int32_t n_blocks,
+            int32_t L, double tmin_src, int32_t line_mode, int32_t S, uint8_t* out, int nthreads) {
+    if (T < 0 || nx < 0 || ny < 0 || L < 1 || L > 16 || n_blocks < 0) return -1;
+    void (*draw)(const ogrid*, double, double, double, double, uint8_t*, int32_t, int32_t) =
+        line_mode == 1 ? draw_thin : draw_segment;
+    oscene sc;
+    if (scene_init(&sc, tri9, tri_building, T) != 0) { scene_free(&sc); return -3; }
+    set_threads(nthreads);
+    const int64_t R = (int64_t)nx * ny;
+    ogrid g = {(double)x0, (double)y0, (double)dx, nx, ny};
+    int32_t Kmax = 1;
+    for (int32_t b = 0; b < n_blocks; ++b) if (block_K[b] > Kmax) Kmax = block_K[b];
+    uint8_t* blk = (uint8_t*)malloc((size_t)(R > 0 ? R : 1) * (size_t)Kmax);
+    if (!blk) { scene_free(&sc); return -3; }
+    for (int32_t b = 0; b < n_blocks; ++b) {
+        const int32_t j0 = block_j0[b], K = block_K[b];
+        memset(blk, 0, (size_t)R * (size_t)K);
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t r = 0; r < R; ++r) {
+            const int64_t ix = r % nx, iy = r / nx;
+            /* cell centre rounded in FP32 exactly as the receivers are defined */
+            const float cxf = x0 + ((float)ix + 0.5f) * dx;
+            const float cyf = y0 + ((float)iy + 0.5f) * dx;
+            const double o[3] = {(double)cxf, (double)cyf, 0.0};
+            for (int dir = 0; dir < 2; ++dir) {
+                const int32_t js = dir == 0 ? j0 : j0 + K - 1;
+                double d[3] = {dirs[3 * js], dirs[3 * js + 1], dirs[3 * js + 2]};
+                double best[16];
+                const int n = nearest_hits(&sc, o, d, tmin_src, L, best);
+                for (int l = 0; l < n; ++l) {
+                    const double s[3] = {o[0] + best[l] * d[0], o[1] + best[l] * d[1], o[2] + best[l] * d[2]};
+                    double qx[64], qy[64];
+                    for (int32_t k = 0; k < K; ++k) {
+                        const double dk[3] = {dirs[3 * (j0 + k)], dirs[3 * (j0 + k) + 1], dirs[3 * (j0 + k) + 2]};
+                        qx[k] = s[0] - s[2] * dk[0] / dk[2];
+                        qy[k] = s[1] - s[2] * dk[1] / dk[2];
+                    }
+                    if (dir == 0) {
+                        for (int32_t k = 0; k + 1 < K; ++k)
+                            draw(&g, qx[k], qy[k], qx[k + 1], qy[k + 1], blk, K, k);
+                        draw(&g, qx[K - 1], qy[K - 1], qx[K - 1], qy[K - 1], blk, K, K - 1);
+                    } else {
+                        for (int32_t k = K - 1; k >= 1; --k)
+                            draw(&g, qx[k], qy[k], qx[k - 1], qy[k - 1], blk, K, k);
+                        draw(&g, qx[0], qy[0], qx[0], qy[0], blk, K, 0);
+                    }
+                }
+            }
+        }
+        for (int64_t r = 0; r < R; ++r)
+            for (int32_t k = 0; k < K; ++k) out[r * S + j0 + k] = blk[r * K + k];
+    }
+    free(blk);
+    scene_free(&sc);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Continuous-time shadow integral (the objective of the height gradient; the paper
+ * motivates height trade-offs but gives no formula, so this is the stated reading).
+ *
+ * Between consecutive steps j, j+1 of a day the sun direction is the great-circle
+ * interpolation d(a) = slerp(d_j, d_{j+1}, a), a in [0, 1], and time runs linearly over
+ * the step length.  A receiver's shadow time over the interval is
+ *     chi(0)                                  if chi(0) == chi(1)
+ *     a*        (shadow -> lit at a*)         otherwise, a* the status flip, found by
+ *     1 - a*    (lit -> shadow at a*)         bisection on the exact ray test
+ * (a second flip inside one interval is not looked for).  S = sum_r w_r * step_minutes *
+ * sum over intervals -- shadow-minutes of the region, weighted per receiver.
+ * ------------------------------------------------------------------------------------ */
+static void slerp_dir(const double* a, const double* b, double theta, double alpha, double* out) {
+    if (theta < 1e-12) {
+        for (int k = 0; k < 3; ++k) out[k] = a[k] + alpha * (b[k] - a[k]);
+    } else {
+        const double s = sin(theta), wa = sin((1.0 - alpha) * theta) / s, wb = sin(alpha * theta) / s;
+        for (int k = 0; k < 3; ++k) out[k] = wa * a[k] + wb * b[k];
+    }
+    const double n = sqrt(dot3(out, out));
+    for (int k = 0; k < 3; ++k) out[k] /= n;
+}
+
+int sao_shadow_integral(const float* tri9, const int32_t* tri_building, int64_t T,
+                        const float* pos, int64_t R, const float* dirs,
+                        const int32_t* day_start, int32_t D, double step_minutes,
+                        const double* weights, int32_t bisect_iters, double* S_out,
+                        double* per_receiver, int nthreads) {
+    if (T < 0 || R < 0 || D < 0 || !S_out) return -1;
+    oscene sc;
+    if (scene_init(&sc, tri9, tri_building, T) != 0) { scene_free(&sc); return -3; }
+    set_threads(nthreads);
+    double total = 0.0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : total)
+    for (int64_t r = 0; r < R; ++r) {
+        double o[3], tmin;
+        receiver_origin(pos, NULL, r, o, &tmin);
+        double acc = 0.0;
+        for (int32_t k = 0; k < D; ++k) {
+            int prev = -1;
+            for (int32_t j = day_start[k]; j + 1 < day_start[k + 1]; ++j) {
+                double a[3] = {dirs[3 * j], dirs[3 * j + 1], dirs[3 * j + 2]};
+                double b[3] = {dirs[3 * j + 3], dirs[3 * j + 4], dirs[3 * j + 5]};
+                const double na = sqrt(dot3(a, a)), nb = sqrt(dot3(b, b));
+                for (int q = 0; q < 3; ++q) { a[q] /= na; b[q] /= nb; }
+                const int c0 = prev >= 0 ? prev : any_hit(&sc, o, a, tmin);
+                const int c1 = any_hit(&sc, o, b, tmin);
+                prev = c1;
+                if (c0 == c1) {
+                    acc += c0;
+                    continue;
+                }
+                double cd = dot3(a, b);
+                if (cd > 1.0) cd = 1.0;
+                const double theta = acos(cd);
+                double lo = 0.0, hi = 1.0;
+                for (int it = 0; it < bisect_iters; ++it) {
+                    const double mid = 0.5 * (lo + hi);
+                    double d[3];
+                    slerp_dir(a, b, theta, mid, d);
+                    if (any_hit(&sc, o, d, tmin) == c0) lo = mid; else hi = mid;
+                }
+                const double astar = 0.5 * (lo + hi);
+                acc += c0 ? astar : 1.0 - astar;
+            }
+        }
+        const double v = acc * step_minutes * (weights ? weights[r] : 1.0);
+        if (per_receiver) per_receiver[r] = v;
+        total += v;
+    }
+    *S_out = total;
+    scene_free(&sc);
+    return 0;
+}

@@ -67,9 +67,13 @@ def lib():
             L.sa_shadow_masks.argtypes = [P, P, P, i32, i32, P, P]
             L.sa_accumulate_grid_noalloc.argtypes = [P, P, P, f32, i32, P, P, P, P]
             L.sa_work_counters.argtypes = [P, P, P, i32, P, P]
+            L.sa_scene_from_footprints.argtypes = [P, P, i32, P, f32, i32, P, PP]
+            L.sa_scene_set_heights.argtypes = [P, P, i32, P]
+            L.sa_height_grad.argtypes = [P, P, P, f32, P, P, P, P]
             for name in ("sa_scene_from_mesh", "sa_scene_info", "sa_sun_create", "sa_sun_info",
                          "sa_receivers_grid", "sa_receivers_points", "sa_accumulate",
-                         "sa_shadow_masks", "sa_accumulate_grid_noalloc", "sa_work_counters"):
+                         "sa_shadow_masks", "sa_accumulate_grid_noalloc", "sa_work_counters",
+                         "sa_scene_from_footprints", "sa_scene_set_heights", "sa_height_grad"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
     return _lib
@@ -119,6 +123,33 @@ class Scene:
                                         ct.c_void_p(_stream(stream)), ct.byref(h)))
         self.handle = h
         self.n_buildings = nb
+
+    @classmethod
+    def from_footprints(cls, footprints, heights, band_height: float = 0.0, stream=None):
+        """Extruded convex CCW footprints (list of [v, 2] arrays) with heights [B]."""
+        xy = np.ascontiguousarray(np.concatenate([np.asarray(f, np.float32).reshape(-1, 2)
+                                                  for f in footprints]) if len(footprints)
+                                  else np.zeros((0, 2), np.float32), dtype=np.float32)
+        off = np.zeros(len(footprints) + 1, np.int32)
+        off[1:] = np.cumsum([len(f) for f in footprints])
+        hs = _host_f32(heights).reshape(-1)
+        h = ct.c_void_p()
+        _check(lib().sa_scene_from_footprints(_ptr(xy), _ptr(off), len(footprints), _ptr(hs),
+                                              float(band_height), 0, ct.c_void_p(_stream(stream)),
+                                              ct.byref(h)))
+        obj = cls.__new__(cls)
+        obj.handle = h
+        obj.n_buildings = len(footprints)
+        return obj
+
+    def set_heights(self, heights, stream=None):
+        """New heights (host array or CUDA tensor [B]); rebuilds mesh and BVH."""
+        if isinstance(heights, torch.Tensor) and heights.is_cuda:
+            hs = heights.detach().float().contiguous()
+            _check(lib().sa_scene_set_heights(self.handle, _ptr(hs), 1, ct.c_void_p(_stream(stream))))
+        else:
+            hs = _host_f32(heights).reshape(-1)
+            _check(lib().sa_scene_set_heights(self.handle, _ptr(hs), 0, ct.c_void_p(_stream(stream))))
 
     def info(self):
         nt, nn, nb, mz = ct.c_int64(), ct.c_int64(), ct.c_int32(), ct.c_float()
@@ -235,6 +266,18 @@ def sa_work_counters(scene: Scene, recv: Receivers, sun: Sun, method, stream=Non
     _check(lib().sa_work_counters(scene.handle, recv.handle, sun.handle, m, _ptr(c),
                                   ct.c_void_p(_stream(stream))))
     return [int(x) for x in c.cpu().tolist()]
+
+
+def sa_height_grad(scene: Scene, grid: Receivers, sun: Sun, step_minutes: float, weights=None,
+                   stream=None):
+    """(dS/dh float32 [B], S float64 scalar tensor) on the current device."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.empty(scene.n_buildings, dtype=torch.float32, device=dev)
+    S = torch.empty(1, dtype=torch.float64, device=dev)
+    w = None if weights is None else torch.as_tensor(weights, dtype=torch.float32, device=dev).contiguous()
+    _check(lib().sa_height_grad(scene.handle, grid.handle, sun.handle, float(step_minutes), _ptr(w),
+                                _ptr(g), _ptr(S), ct.c_void_p(_stream(stream))))
+    return g, S[0]
 
 
 def sa_shadow_masks(scene: Scene, recv: Receivers, sun: Sun, method, iam_levels: int = 0,

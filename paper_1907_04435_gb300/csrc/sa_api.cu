@@ -240,7 +240,153 @@ void sa_scene_destroy(sa_scene* scene) {
     cudaDeviceSynchronize();
     if (scene->bvh.nodes) cudaFree(scene->bvh.nodes);
     if (scene->bvh.tris) cudaFree(scene->bvh.tris);
+    if (scene->d_fp_mem) cudaFree(scene->d_fp_mem);
+    if (scene->d_heights) cudaFree(scene->d_heights);
     delete scene;
+}
+
+// Extrude the footprint set with the scene's current device heights and rebuild the BVH.
+static cudaError_t rebuild_from_footprints(sa_scene* sc, cudaStream_t st) {
+    const sa::FootprintSet& fs = sc->fs;
+    float* dv = nullptr;
+    int *dt = nullptr, *db = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (fs.n_tris > 0) {
+        e = cudaMalloc(&dv, sizeof(float) * 3 * (size_t)fs.n_verts);
+        if (e == cudaSuccess) e = cudaMalloc(&dt, sizeof(int) * 3 * (size_t)fs.n_tris);
+        if (e == cudaSuccess) e = cudaMalloc(&db, sizeof(int) * (size_t)fs.n_tris);
+        if (e == cudaSuccess) e = sa::extrude_footprints(fs, sc->d_heights, dv, dt, db, st);
+    }
+    sa::LbvhBuild nb{};
+    if (e == cudaSuccess) e = sa::build_lbvh(dv, fs.n_verts, dt, fs.n_tris, db, &nb, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (dv) cudaFree(dv);
+    if (dt) cudaFree(dt);
+    if (db) cudaFree(db);
+    if (e != cudaSuccess) return e;
+    if (sc->bvh.nodes) cudaFree(sc->bvh.nodes);
+    if (sc->bvh.tris) cudaFree(sc->bvh.tris);
+    sc->bvh = nb;
+    sc->T = fs.n_tris;
+    return cudaSuccess;
+}
+
+static sa_status check_heights(const std::vector<float>& h, const char* who) {
+    for (size_t b = 0; b < h.size(); ++b)
+        if (!isfinite(h[b]) || !(h[b] > 0.f))
+            return fail(SA_ERR_INVALID_ARG, "%s: height of building %zu must be finite and > 0", who, b);
+    return SA_OK;
+}
+
+sa_status sa_scene_from_footprints(const float* xy, const int32_t* poly_off, int32_t n_buildings,
+                                   const float* heights, float band_height, int32_t device_ptrs,
+                                   void* stream, sa_scene** out) {
+    const char* who = "sa_scene_from_footprints";
+    if (!out) return fail(SA_ERR_INVALID_ARG, "%s: out is NULL", who);
+    *out = nullptr;
+    if (n_buildings < 0 || (n_buildings > 0 && (!xy || !poly_off || !heights)))
+        return fail(SA_ERR_INVALID_ARG, "%s: bad sizes or NULL pointers", who);
+    if (!isfinite(band_height) || band_height < 0.f) return fail(SA_ERR_INVALID_ARG, "%s: band_height", who);
+    std::vector<int32_t> off;
+    sa_status s = host_copy(poly_off, (size_t)n_buildings + 1, device_ptrs, &off);
+    if (s != SA_OK) return s;
+    if (off[0] != 0) return fail(SA_ERR_INVALID_ARG, "%s: poly_off[0] must be 0", who);
+    for (int b = 0; b < n_buildings; ++b)
+        if (off[b + 1] - off[b] < 3)
+            return fail(SA_ERR_INVALID_ARG, "%s: building %d has fewer than 3 vertices", who, b);
+    const int nv = off[n_buildings];
+    std::vector<float> hxy, hh;
+    s = host_copy(xy, (size_t)nv * 2, device_ptrs, &hxy);
+    if (s == SA_OK) s = host_copy(heights, (size_t)n_buildings, device_ptrs, &hh);
+    if (s != SA_OK) return s;
+    s = check_heights(hh, who);
+    if (s != SA_OK) return s;
+    for (size_t i = 0; i < hxy.size(); ++i)
+        if (!isfinite(hxy[i])) return fail(SA_ERR_DEGENERATE, "%s: non-finite footprint vertex", who);
+    // convex, counter-clockwise footprints
+    for (int b = 0; b < n_buildings; ++b) {
+        const int a = off[b], v = off[b + 1] - a;
+        double area = 0.0;
+        for (int i = 0; i < v; ++i) {
+            const int i1 = a + (i + 1) % v, i2 = a + (i + 2) % v;
+            const double e1x = (double)hxy[2 * i1] - hxy[2 * (a + i)], e1y = (double)hxy[2 * i1 + 1] - hxy[2 * (a + i) + 1];
+            const double e2x = (double)hxy[2 * i2] - hxy[2 * i1], e2y = (double)hxy[2 * i2 + 1] - hxy[2 * i1 + 1];
+            if (e1x * e2y - e1y * e2x < 0.0)
+                return fail(SA_ERR_INVALID_ARG, "%s: footprint %d is not convex and counter-clockwise", who, b);
+            area += (double)hxy[2 * (a + i)] * hxy[2 * i1 + 1] - (double)hxy[2 * i1] * hxy[2 * (a + i) + 1];
+        }
+        if (!(area > 0.0)) return fail(SA_ERR_INVALID_ARG, "%s: footprint %d has no positive area", who, b);
+    }
+    std::vector<int32_t> bands(n_buildings), voff(n_buildings + 1, 0), toff(n_buildings + 1, 0);
+    for (int b = 0; b < n_buildings; ++b) {
+        const int v = off[b + 1] - off[b];
+        int nb = 1;
+        if (band_height > 0.f) nb = std::max(1, (int)ceil((double)hh[b] / (double)band_height));
+        bands[b] = nb;
+        voff[b + 1] = voff[b] + (nb + 1) * v;
+        toff[b + 1] = toff[b] + 2 * v * nb + 2 * (v - 2);
+    }
+    sa_scene* sc = new (std::nothrow) sa_scene();
+    if (!sc) return fail(SA_ERR_OOM, "%s: host allocation", who);
+    sc->n_buildings = n_buildings;
+    sc->min_z = 0.f;
+    sc->has_footprints = 1;
+    cudaStream_t st = as_stream(stream);
+    // one device block: xy (float2) | fp_off | bands | vert_off | tri_off
+    const size_t b_xy = sizeof(float) * 2 * (size_t)std::max(nv, 1);
+    const size_t b_i = sizeof(int) * (size_t)(n_buildings + 1);
+    cudaError_t e = cudaMalloc(&sc->d_fp_mem, b_xy + 4 * b_i);
+    if (e == cudaSuccess) e = cudaMalloc(&sc->d_heights, sizeof(float) * (size_t)std::max(n_buildings, 1));
+    if (e == cudaSuccess) {
+        char* base = static_cast<char*>(sc->d_fp_mem);
+        float2* dxy = reinterpret_cast<float2*>(base);
+        int* doff = reinterpret_cast<int*>(base + b_xy);
+        int* dband = doff + (n_buildings + 1);
+        int* dvoff = dband + (n_buildings + 1);
+        int* dtoff = dvoff + (n_buildings + 1);
+        if (nv > 0) e = cudaMemcpyAsync(dxy, hxy.data(), sizeof(float) * 2 * nv, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(doff, off.data(), b_i, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && n_buildings > 0)
+            e = cudaMemcpyAsync(dband, bands.data(), sizeof(int) * n_buildings, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dvoff, voff.data(), b_i, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dtoff, toff.data(), b_i, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && n_buildings > 0)
+            e = cudaMemcpyAsync(sc->d_heights, hh.data(), sizeof(float) * n_buildings, cudaMemcpyHostToDevice, st);
+        sc->fs.B = n_buildings;
+        sc->fs.xy = dxy;
+        sc->fs.fp_off = doff;
+        sc->fs.bands = dband;
+        sc->fs.vert_off = dvoff;
+        sc->fs.tri_off = dtoff;
+        sc->fs.n_verts = voff[n_buildings];
+        sc->fs.n_tris = toff[n_buildings];
+    }
+    if (e == cudaSuccess) e = rebuild_from_footprints(sc, st);
+    if (e != cudaSuccess) {
+        sa_scene_destroy(sc);
+        return cuda_fail(e, who);
+    }
+    *out = sc;
+    return SA_OK;
+}
+
+sa_status sa_scene_set_heights(sa_scene* scene, const float* heights, int32_t device_ptrs,
+                               void* stream) {
+    const char* who = "sa_scene_set_heights";
+    if (!scene || !heights) return fail(SA_ERR_INVALID_ARG, "%s: NULL argument", who);
+    if (!scene->has_footprints) return fail(SA_ERR_UNSUPPORTED, "%s: scene was not built from footprints", who);
+    std::vector<float> hh;
+    sa_status s = host_copy(heights, (size_t)scene->n_buildings, device_ptrs, &hh);
+    if (s != SA_OK) return s;
+    s = check_heights(hh, who);
+    if (s != SA_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    cudaError_t e = scene->n_buildings > 0
+        ? cudaMemcpyAsync(scene->d_heights, hh.data(), sizeof(float) * scene->n_buildings, cudaMemcpyHostToDevice, st)
+        : cudaSuccess;
+    if (e == cudaSuccess) e = rebuild_from_footprints(scene, st);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return SA_OK;
 }
 
 sa_status sa_scene_info(const sa_scene* scene, int64_t* n_tris, int64_t* n_nodes,
@@ -414,7 +560,6 @@ static sa_status run_method(const sa_scene* scene, const sa_receivers* recv, con
         return fail(SA_ERR_UNSUPPORTED, "%s: raster methods need geometry at z >= 0", who);
     if (method < SA_SWEEP_TRACE || method > SA_IAM)
         return fail(SA_ERR_INVALID_ARG, "%s: unknown method %d", who, (int)method);
-    if (method == SA_IAM) return fail(SA_ERR_UNSUPPORTED, "%s: SA_IAM not available", who);
     sa::DevScene dsc = dev_scene(scene);
     sa::DevRecv drc = dev_recv(recv);
     sa::DevSun dsun;
@@ -430,8 +575,22 @@ static sa_status run_method(const sa_scene* scene, const sa_receivers* recv, con
     const long long R = recv->R;
     if (R == 0) return SA_OK;
     cudaError_t e = cudaSuccess;
+    if (dsun.n_blocks == 0) {
+        // no steps: counts are zero (or unchanged when accumulating)
+        if (!out.accumulate_into) {
+            e = cudaMemsetAsync(out.gross, 0, sizeof(int) * (size_t)R, st);
+            if (e == cudaSuccess && out.continuous) e = cudaMemsetAsync(out.continuous, 0, sizeof(int) * (size_t)R, st);
+            if (e == cudaSuccess && out.minutes) e = cudaMemsetAsync(out.minutes, 0, sizeof(float) * (size_t)R, st);
+        }
+        return e == cudaSuccess ? SA_OK : cuda_fail(e, who);
+    }
     int* run = nullptr;
-    if (raster) {
+    if (method == SA_IAM) {
+        e = cudaMallocAsync(&run, sizeof(int) * (size_t)R, st);
+        if (e != cudaSuccess) return cuda_fail(e, who);
+        out.run = run;
+        e = sa::launch_iam(dsc, drc, dsun, sun->h_blocks.data(), iam_levels ? iam_levels : 3, out, st);
+    } else if (raster) {
         e = cudaMallocAsync(&run, sizeof(int) * (size_t)R, st);
         if (e != cudaSuccess) return cuda_fail(e, who);
         out.run = run;
@@ -488,6 +647,26 @@ sa_status sa_shadow_masks(const sa_scene* scene, const sa_receivers* recv, const
     sa_status s = run_method(scene, recv, sun, method, iam_levels, out, st, "sa_shadow_masks");
     if (gross) cudaFreeAsync(gross, st);
     return s;
+}
+
+sa_status sa_height_grad(const sa_scene* scene, const sa_receivers* grid, const sa_sun* sun,
+                         float step_minutes, const float* weights, float* dS_dh, double* S_out,
+                         void* stream) {
+    const char* who = "sa_height_grad";
+    if (!scene || !grid || !sun) return fail(SA_ERR_INVALID_ARG, "%s: NULL handle", who);
+    if (!scene->has_footprints) return fail(SA_ERR_UNSUPPORTED, "%s: scene was not built from footprints", who);
+    if (!grid->is_grid) return fail(SA_ERR_UNSUPPORTED, "%s: receivers must be a ground grid", who);
+    if (scene->n_buildings > 0 && !dS_dh) return fail(SA_ERR_INVALID_ARG, "%s: dS_dh is NULL", who);
+    if (!isfinite(step_minutes) || step_minutes < 0.f) return fail(SA_ERR_INVALID_ARG, "%s: step_minutes", who);
+    sa::DevSun dsun;
+    dsun.steps = sun->d_steps;
+    dsun.blocks = sun->d_blocks;
+    dsun.S = sun->S;
+    dsun.n_blocks = (int)sun->h_blocks.size();
+    cudaError_t e = sa::launch_height_grad(dev_scene(scene), scene->fs, scene->d_heights, dev_recv(grid), dsun,
+                                           step_minutes, weights, dS_dh, S_out, as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return SA_OK;
 }
 
 sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,

@@ -10,6 +10,11 @@ struct sa_scene {
     long long T;
     int n_buildings;
     float min_z;
+    // scenes built from footprints keep them (height changes, height gradient)
+    int has_footprints = 0;
+    sa::FootprintSet fs{};
+    float* d_heights = nullptr;
+    void* d_fp_mem = nullptr;          // one allocation behind the FootprintSet arrays
 };
 
 struct sa_sun {

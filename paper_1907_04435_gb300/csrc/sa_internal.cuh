@@ -191,6 +191,27 @@ cudaError_t launch_accrual_trace(const DevScene& sc, const DevRecv& rc, const De
 cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
                                  const DevOut& out, cudaStream_t st);
 
+// Extruded convex footprints kept on the device (scenes built from footprints).
+struct FootprintSet {
+    int B;
+    const float2* xy;      // footprint vertices, CCW per building
+    const int* fp_off;     // [B + 1] offsets into xy
+    const int* bands;      // [B] wall bands
+    const int* vert_off;   // [B + 1] mesh vertex offsets
+    const int* tri_off;    // [B + 1] mesh triangle offsets
+    long long n_verts, n_tris;
+};
+cudaError_t extrude_footprints(const FootprintSet& fs, const float* d_heights, float* d_verts,
+                               int* d_tris, int* d_tri_b, cudaStream_t st);
+// d(shadow-minutes of a ground grid)/d(heights); d_S (nullable) receives S itself
+cudaError_t launch_height_grad(const DevScene& sc, const FootprintSet& fs, const float* d_heights,
+                               const DevRecv& rc, const DevSun& sun, float step_minutes,
+                               const float* weights, float* dS_dh, double* d_S, cudaStream_t st);
+
+// inverse accrual map of a ground grid (h_blocks: host copy of the block constants)
+cudaError_t launch_iam(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                       const BlockConst* h_blocks, int L, const DevOut& out, cudaStream_t st);
+
 // LBVH build (device), returns node / triangle arrays owned by the caller
 struct LbvhBuild {
     float4* nodes;   // [2 * n_nodes]

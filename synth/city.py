@@ -49,18 +49,28 @@ class Mesh:
         return np.ascontiguousarray(self.verts[self.tris].reshape(-1, 9), dtype=np.float32)
 
 
-def extrude(city: City, heights: np.ndarray | None = None) -> Mesh:
-    """Closed prisms from convex CCW footprints; roof/bottom fans; walls in bands."""
+def band_counts(city: City, heights=None) -> np.ndarray:
+    """Wall bands per building: ceil(h / band_height), at least 1 (1 if no banding)."""
     hs = np.asarray(city.heights if heights is None else heights, dtype=np.float32)
+    if city.band_height <= 0:
+        return np.ones(len(hs), np.int32)
+    return np.asarray([max(1, int(math.ceil(float(h) / city.band_height))) for h in hs], np.int32)
+
+
+def extrude(city: City, heights: np.ndarray | None = None, bands=None) -> Mesh:
+    """Closed prisms from convex CCW footprints; roof/bottom fans; walls in bands.
+    `bands` fixes the band count per building (default: from the heights)."""
+    hs = np.asarray(city.heights if heights is None else heights, dtype=np.float32)
+    nbs = band_counts(city, hs) if bands is None else np.asarray(bands, np.int32)
     verts, tris, tb, vb, vroof = [], [], [], [], []
     base = 0
     for b, fp in enumerate(city.footprints):
         fp = np.asarray(fp, dtype=np.float32)
         v = fp.shape[0]
-        h = float(hs[b])
-        nb = 1 if city.band_height <= 0 else max(1, int(math.ceil(h / city.band_height)))
-        zs = np.float32(h) * (np.arange(nb + 1, dtype=np.float32) / np.float32(nb))
-        zs[-1] = np.float32(h)
+        h = hs[b]
+        nb = int(nbs[b])
+        zs = h * (np.arange(nb + 1, dtype=np.float32) / np.float32(nb))
+        zs[-1] = h
         # rings k = 0..nb, each v vertices
         for k in range(nb + 1):
             for i in range(v):
@@ -187,7 +197,7 @@ def city_ring_around_park(seed: int, park=(0.0, 0.0, 500.0, 300.0), band: float 
         dy = max(py0 - y1, 0.0, y0 - py1)
         if not inside_park and max(dx, dy) <= band:
             keep.append(k)
-    lots = lots[np.asarray(keep)]
+    lots = lots[np.asarray(keep, dtype=np.int64)]
     return _district_from_lots(rng, lots, n_buildings, h_median, h_sigma, h_cap, band_height)
 
 

@@ -66,10 +66,13 @@ def season(n_days: int = 92, ground_n: int = 4096) -> Workload:
     return Workload("season", city, C.extrude(city), g, None, None, sun)
 
 
-def park() -> Workload:
-    city = C.city_ring_around_park(C.SEED_BASE + 5)
-    g = C.GroundGrid(x0=0.0, y0=0.0, dx=0.5, nx=1000, ny=600)
-    sun = sun_table(LAT, [79], 9.0, 17.0, 1.0)
+def park(width: float = 500.0, depth: float = 300.0, dx: float = 0.5, n_buildings: int = 200,
+         band: float = 300.0, step: float = 1.0, seed_off: int = 5) -> Workload:
+    """A width x depth park sampled at dx, ringed by c2-style buildings (median 60 m)."""
+    city = C.city_ring_around_park(C.SEED_BASE + seed_off, park=(0.0, 0.0, width, depth),
+                                   band=band, n_buildings=n_buildings)
+    g = C.GroundGrid(x0=0.0, y0=0.0, dx=dx, nx=int(round(width / dx)), ny=int(round(depth / dx)))
+    sun = sun_table(LAT, [79], 9.0, 17.0, step)
     return Workload("park", city, C.extrude(city), g, None, None, sun)
 
 

@@ -1,0 +1,118 @@
+"""Pins of the oracle's inverse accrual map (Sec. 5), an approximation by design.
+
+What geometry fixes exactly: with one step per block the map draws no lines, and every
+cell with a source (the 100 cm rule aside) is shadowed -- the exact result; reversing the
+steps of a block swaps the forward and backward maps; and on a fine grid with one-minute
+steps the map's shadow area stays within the paper's error bar (mean < 1 % of the area).
+"""
+import numpy as np
+
+import oracle
+from synth import city as C
+from synth import configs
+from synth.sun import sun_table
+
+
+def _grid(w):
+    g = w.ground
+    return (g.x0, g.y0, g.dx, g.nx, g.ny)
+
+
+def inside_any_footprint(city, pos):
+    inside = np.zeros(pos.shape[0], bool)
+    for fp in city.footprints:
+        f = fp.astype(np.float32).astype(np.float64)
+        ok = np.ones(pos.shape[0], bool)
+        for i in range(f.shape[0]):
+            a, b = f[i], f[(i + 1) % f.shape[0]]
+            ok &= (b[0] - a[0]) * (pos[:, 1] - a[1]) - (b[1] - a[1]) * (pos[:, 0] - a[0]) >= 0
+        inside |= ok
+    return inside
+
+
+def _hit_distances(t9, o, d):
+    """All ray/triangle hit distances t > 0, by a separate numpy brute force."""
+    out = []
+    for v0, v1, v2 in t9:
+        e1, e2 = v1 - v0, v2 - v0
+        p = np.cross(d, e2)
+        det = e1 @ p
+        if det == 0:
+            continue
+        s = o - v0
+        u = (s @ p) / det
+        q = np.cross(s, e1)
+        v = (d @ q) / det
+        if u < 0 or v < 0 or u + v > 1:
+            continue
+        t = (e2 @ q) / det
+        if t > 0:
+            out.append(t)
+    return out
+
+
+def test_one_step_blocks_reduce_to_the_exact_shadow():
+    """With one step per block no line is drawn: a cell is marked exactly when its own ray
+    has a source.  The only departures allowed are the paper's 100 cm rule: cells whose
+    every intersection lies within 1 m (inside a footprint next to a wall, or a ray that
+    clips a building's corner) lose their shadow."""
+    w = configs.district_small()
+    exact = oracle.shadow_bits(w.mesh.tri9(), w.mesh.tri_building, w.ground.positions(), None,
+                               w.sun.dirs)
+    near = oracle.near_boundary(w.mesh.tri9(), w.mesh.tri_building, w.ground.positions(), None,
+                                w.sun.dirs, w.sun.day_start, exact)
+    iam = oracle.iam_bits(w.mesh.tri9(), w.mesh.tri_building, _grid(w), w.sun.dirs,
+                          w.sun.day_start, block_len=1, levels=1)
+    assert not ((iam == 1) & (exact == 0) & (near == 0)).any()
+    missed = np.argwhere((iam == 0) & (exact == 1) & (near == 0))
+    assert missed.shape[0] < 0.01 * iam.size
+    outside = ~inside_any_footprint(w.city, w.ground.positions().astype(np.float64))
+    t9 = w.mesh.tri9().astype(np.float64).reshape(-1, 3, 3)
+    pos = w.ground.positions().astype(np.float64)
+    for r, j in missed[outside[missed[:, 0]]]:
+        ts = _hit_distances(t9, pos[r], w.sun.dirs[j].astype(np.float64))
+        assert ts and max(ts) <= 1.0 + 1e-9, (r, j, ts)
+    assert iam.sum() > 0
+
+
+def test_reversed_steps_mirror_the_bits():
+    """Forward and backward maps swap when the steps of each block run backwards."""
+    city = C.city_boxes(3, nx=2, ny=2)
+    mesh = C.extrude(city)
+    st = sun_table(40.7, [172], 10.0, 11.0, 4.0)            # 16 steps, one block
+    grid = (-20.0, -20.0, 1.0, 150, 150)
+    a = oracle.iam_bits(mesh.tri9(), mesh.tri_building, grid, st.dirs, st.day_start, levels=2)
+    b = oracle.iam_bits(mesh.tri9(), mesh.tri_building, grid, st.dirs[::-1].copy(),
+                        st.day_start, levels=2)
+    assert np.array_equal(a, b[:, ::-1])
+    assert a.sum() > 0
+
+
+def test_single_box_area_error_within_the_paper_bar():
+    fp = C.box_footprint(0.0, 0.0, 30.0, 20.0)
+    city = C.City([fp], np.array([45.0], np.float32))
+    mesh = C.extrude(city)
+    st = sun_table(40.7, [172], 9.0, 15.0, 1.0)
+    g = C.GroundGrid(-150.0, -60.0, 0.5, 600, 240)
+    exact = oracle.shadow_bits(mesh.tri9(), mesh.tri_building, g.positions(), None, st.dirs)
+    iam = oracle.iam_bits(mesh.tri9(), mesh.tri_building, (g.x0, g.y0, g.dx, g.nx, g.ny),
+                          st.dirs, st.day_start, levels=3)
+    j0, K = oracle.block_partition(st.day_start)
+    errs = []
+    for a, k in zip(j0, K):
+        e = exact[:, a:a + k].sum() / k
+        i = iam[:, a:a + k].sum() / k
+        errs.append(abs(i - e) / g.R)
+    assert np.mean(errs) < 0.01 and max(errs) < 0.026, errs
+
+
+def test_more_levels_find_more_shadow_behind_the_first_source():
+    """Two boxes in a row along the sun: level 2 adds the far box's shadow lines."""
+    fps = [C.box_footprint(0.0, 0.0, 10.0, 10.0), C.box_footprint(40.0, 0.0, 50.0, 10.0)]
+    city = C.City(fps, np.array([20.0, 60.0], np.float32))
+    mesh = C.extrude(city)
+    st = sun_table(40.7, [172], 15.0, 16.0, 2.0)            # afternoon: sun in the west
+    grid = (-120.0, -40.0, 1.0, 200, 100)
+    one = oracle.iam_bits(mesh.tri9(), mesh.tri_building, grid, st.dirs, st.day_start, levels=1)
+    two = oracle.iam_bits(mesh.tri9(), mesh.tri_building, grid, st.dirs, st.day_start, levels=2)
+    assert np.all(two >= one) and two.sum() > one.sum()
