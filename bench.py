@@ -155,7 +155,8 @@ def run_gpu(args):
     w = make_workload(args.workload)
     st = w.sun
     # resident inputs
-    scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B)
+    # the synthetic buildings are closed, outward-wound prisms
+    scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
     sun = B.Sun(st.dirs, st.day_start, args.block_len)
     g = w.ground
     grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
@@ -318,7 +319,7 @@ def end_to_end(B, w, args, dev):
     d2h = 3 * R * 4
 
     def once():
-        scene = B.Scene(verts, tris, tb, w.city.B)
+        scene = B.Scene(verts, tris, tb, w.city.B, closed=True)
         sun = B.Sun(st.dirs, st.day_start, args.block_len)
         grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
         gg, gm, gc = B.sa_accumulate(scene, grid, sun, st.step_minutes, "accrual_sam")

@@ -84,6 +84,18 @@ const char* sa_last_error(void);
 /* Library version, (major << 16) | minor. */
 int32_t sa_version(void);
 
+/* Process-wide tuning options (set between calls; not thread-safe against running calls).
+ *   SA_OPT_SWEEP_TRAVERSAL, SA_OPT_ACCRUAL_TRAVERSAL: BVH traversal of the ray-traced
+ *   methods -- 1 warp-coherent (the 32 lanes of a warp walk the node list together), 2 one
+ *   traversal per lane, 0 the default (per lane for the sweep, warp-coherent for the
+ *   accrual, the faster of the two on the district workload).  Results do not depend on
+ *   the option.
+ * sa_get_option returns the current value, or -1 for an unknown key. */
+#define SA_OPT_SWEEP_TRAVERSAL 1
+#define SA_OPT_ACCRUAL_TRAVERSAL 2
+sa_status sa_set_option(int32_t key, int32_t value);
+int32_t sa_get_option(int32_t key);
+
 /* ---------------------------------------------------------------------------- scene
  * Build a scene from an indexed triangle mesh (Sec. 8.2: the city mesh): vertices
  * float [nv][3] and triangles int32 [nt][3] (0-based vertex indices), optional int32
@@ -120,6 +132,14 @@ sa_status sa_scene_set_heights(sa_scene* scene, const float* heights, int32_t de
 
 /* Release a scene (NULL is ignored). Synchronises the device first. */
 void sa_scene_destroy(sa_scene* scene);
+
+/* Declare (closed = 1) that every building of the scene is a closed solid whose triangles
+ * are wound counter-clockwise seen from outside.  The projection of a closed solid is
+ * covered by its faces that face the sun, so the raster methods then skip the others
+ * (about half the work) with the same result; the ray-traced methods are unaffected.
+ * Scenes from sa_scene_from_footprints are closed from the start.  Declaring an open
+ * or inward-wound mesh closed gives wrong raster results. */
+sa_status sa_scene_declare_closed(sa_scene* scene, int32_t closed);
 
 /* Triangle and BVH node counts, number of buildings, minimum vertex z. */
 sa_status sa_scene_info(const sa_scene* scene, int64_t* n_tris, int64_t* n_nodes,

@@ -67,13 +67,18 @@ def lib():
             L.sa_shadow_masks.argtypes = [P, P, P, i32, i32, P, P]
             L.sa_accumulate_grid_noalloc.argtypes = [P, P, P, f32, i32, P, P, P, P]
             L.sa_work_counters.argtypes = [P, P, P, i32, P, P]
+            L.sa_scene_declare_closed.argtypes = [P, i32]
+            L.sa_set_option.argtypes = [i32, i32]
+            L.sa_get_option.argtypes = [i32]
+            L.sa_get_option.restype = i32
             L.sa_scene_from_footprints.argtypes = [P, P, i32, P, f32, i32, P, PP]
             L.sa_scene_set_heights.argtypes = [P, P, i32, P]
             L.sa_height_grad.argtypes = [P, P, P, f32, P, P, P, P]
             for name in ("sa_scene_from_mesh", "sa_scene_info", "sa_sun_create", "sa_sun_info",
                          "sa_receivers_grid", "sa_receivers_points", "sa_accumulate",
                          "sa_shadow_masks", "sa_accumulate_grid_noalloc", "sa_work_counters",
-                         "sa_scene_from_footprints", "sa_scene_set_heights", "sa_height_grad"):
+                         "sa_scene_from_footprints", "sa_scene_set_heights", "sa_height_grad",
+                         "sa_scene_declare_closed", "sa_set_option"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
     return _lib
@@ -114,7 +119,8 @@ def _ptr(x):
 class Scene:
     """sa_scene: device copy of the mesh plus its linear BVH."""
 
-    def __init__(self, verts, tris, tri_building=None, n_buildings=None, stream=None):
+    def __init__(self, verts, tris, tri_building=None, n_buildings=None, stream=None,
+                 closed: bool = False):
         v, t = _host_f32(verts).reshape(-1, 3), _host_i32(tris).reshape(-1, 3)
         b = None if tri_building is None else _host_i32(tri_building).reshape(-1)
         nb = int(n_buildings if n_buildings is not None else (int(b.max()) + 1 if b is not None and b.size else 1))
@@ -123,6 +129,8 @@ class Scene:
                                         ct.c_void_p(_stream(stream)), ct.byref(h)))
         self.handle = h
         self.n_buildings = nb
+        if closed:
+            _check(lib().sa_scene_declare_closed(h, 1))
 
     @classmethod
     def from_footprints(cls, footprints, heights, band_height: float = 0.0, stream=None):
@@ -266,6 +274,18 @@ def sa_work_counters(scene: Scene, recv: Receivers, sun: Sun, method, stream=Non
     _check(lib().sa_work_counters(scene.handle, recv.handle, sun.handle, m, _ptr(c),
                                   ct.c_void_p(_stream(stream))))
     return [int(x) for x in c.cpu().tolist()]
+
+
+SA_OPT_SWEEP_TRAVERSAL, SA_OPT_ACCRUAL_TRAVERSAL = 1, 2
+TRAVERSAL = {"auto": 0, "packet": 1, "lane": 2}
+
+
+def sa_set_option(key: int, value: int):
+    _check(lib().sa_set_option(int(key), int(value)))
+
+
+def sa_get_option(key: int) -> int:
+    return int(lib().sa_get_option(int(key)))
 
 
 def sa_height_grad(scene: Scene, grid: Receivers, sun: Sun, step_minutes: float, weights=None,

@@ -130,6 +130,7 @@ sa::DevScene dev_scene(const sa_scene* s) {
     d.tris = s->bvh.tris;
     d.n_nodes = s->bvh.n_nodes;
     d.T = (int)s->T;
+    d.closed = s->closed;
     return d;
 }
 
@@ -331,6 +332,7 @@ sa_status sa_scene_from_footprints(const float* xy, const int32_t* poly_off, int
     sc->n_buildings = n_buildings;
     sc->min_z = 0.f;
     sc->has_footprints = 1;
+    sc->closed = 1;
     cudaStream_t st = as_stream(stream);
     // one device block: xy (float2) | fp_off | bands | vert_off | tri_off
     const size_t b_xy = sizeof(float) * 2 * (size_t)std::max(nv, 1);
@@ -386,6 +388,30 @@ sa_status sa_scene_set_heights(sa_scene* scene, const float* heights, int32_t de
         : cudaSuccess;
     if (e == cudaSuccess) e = rebuild_from_footprints(scene, st);
     if (e != cudaSuccess) return cuda_fail(e, who);
+    return SA_OK;
+}
+
+sa_status sa_set_option(int32_t key, int32_t value) {
+    switch (key) {
+        case SA_OPT_SWEEP_TRAVERSAL:
+        case SA_OPT_ACCRUAL_TRAVERSAL:
+            if (value < 0 || value > 2) return fail(SA_ERR_INVALID_ARG, "sa_set_option: traversal mode %d", value);
+            sa::set_trace_mode(key == SA_OPT_SWEEP_TRAVERSAL ? 0 : 1, value);
+            return SA_OK;
+        default:
+            return fail(SA_ERR_INVALID_ARG, "sa_set_option: unknown key %d", key);
+    }
+}
+
+int32_t sa_get_option(int32_t key) {
+    if (key == SA_OPT_SWEEP_TRAVERSAL) return sa::get_trace_mode(0);
+    if (key == SA_OPT_ACCRUAL_TRAVERSAL) return sa::get_trace_mode(1);
+    return -1;
+}
+
+sa_status sa_scene_declare_closed(sa_scene* scene, int32_t closed) {
+    if (!scene) return fail(SA_ERR_INVALID_ARG, "sa_scene_declare_closed: NULL scene");
+    scene->closed = closed ? 1 : 0;
     return SA_OK;
 }
 

@@ -10,6 +10,7 @@ struct sa_scene {
     long long T;
     int n_buildings;
     float min_z;
+    int closed = 0;                    // buildings declared closed, outward-oriented solids
     // scenes built from footprints keep them (height changes, height gradient)
     int has_footprints = 0;
     sa::FootprintSet fs{};

@@ -59,6 +59,7 @@ struct DevScene {
     const float4* tris;
     int n_nodes;
     int T;
+    int closed;     // every building is a closed, outward-oriented solid
 };
 
 // ------------------------------------------------------------------- reduction state
@@ -187,6 +188,9 @@ cudaError_t launch_sweep_trace(const DevScene& sc, const DevRecv& rc, const DevS
                                const DevOut& out, cudaStream_t st);
 cudaError_t launch_accrual_trace(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
                                  const DevOut& out, cudaStream_t st);
+// traversal mode of the sweep (which = 0) and accrual (which = 1) kernels
+void set_trace_mode(int which, int mode);
+int get_trace_mode(int which);
 // ground raster; `sun` may be the per-step partition (K = 1 blocks) for SA_SWEEP_RASTER
 cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
                                  const DevOut& out, cudaStream_t st);

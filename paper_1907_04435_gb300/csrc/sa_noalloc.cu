@@ -74,6 +74,7 @@ extern "C" sa_status sa_accumulate_grid_noalloc(const sa_scene* scene, const sa_
     dsc.tris = scene->bvh.tris;
     dsc.n_nodes = scene->bvh.n_nodes;
     dsc.T = (int)scene->T;
+    dsc.closed = scene->closed;
     sa::DevRecv drc;
     drc.is_grid = 1;
     drc.x0 = grid->x0; drc.y0 = grid->y0; drc.dx = grid->dx; drc.nx = grid->nx; drc.ny = grid->ny;

@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kTile = 32;               // cells per tile side
 constexpr int kRasterThreads = 256;     // 8 warps x 4 rows each
-constexpr int kTriBatch = 16;           // triangles staged per batch
+constexpr int kTriBatch = 8;            // triangles staged per batch
 constexpr int kMaxItems = kTriBatch * kMaxBlock;
 
 struct TileGeom {
@@ -68,7 +68,22 @@ __device__ __forceinline__ bool swept_tiles(const float4& a, const float4& b, co
     return true;
 }
 
-__global__ void k_bin_count(DevScene sc, const BlockConst* __restrict__ blocks, int b0,
+// For a closed scene only triangles facing the sun at some step of the block cast the
+// shadow's coverage (the projection of a closed solid is covered by its sun-facing faces).
+__device__ __forceinline__ bool faces_sun(const float4& a, const float4& b, const float4& c,
+                                          const StepConst* steps, const BlockConst& bc) {
+    const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+    const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+    const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+    for (int k = 0; k < bc.K; ++k) {
+        const StepConst& s = steps[bc.j0 + k];
+        if (nx * s.dx + ny * s.dy + nz * s.dz > 0.f) return true;
+    }
+    return false;
+}
+
+__global__ void k_bin_count(DevScene sc, const StepConst* __restrict__ steps,
+                            const BlockConst* __restrict__ blocks, int b0,
                             TileGeom g, unsigned* __restrict__ counts) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int bl = blockIdx.y;
@@ -76,6 +91,7 @@ __global__ void k_bin_count(DevScene sc, const BlockConst* __restrict__ blocks, 
     const float4 a = __ldg(&sc.tris[3 * t]), b = __ldg(&sc.tris[3 * t + 1]),
                  c = __ldg(&sc.tris[3 * t + 2]);
     if (!tri_above_ground(a, b, c)) return;
+    if (sc.closed && !faces_sun(a, b, c, steps, blocks[b0 + bl])) return;
     int tx0, tx1, ty0, ty1;
     if (!swept_tiles(a, b, c, blocks[b0 + bl], g, &tx0, &tx1, &ty0, &ty1)) return;
     unsigned* row = counts + (size_t)bl * g.tiles_x * g.tiles_y;
@@ -83,7 +99,8 @@ __global__ void k_bin_count(DevScene sc, const BlockConst* __restrict__ blocks, 
         for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&row[ty * g.tiles_x + tx], 1u);
 }
 
-__global__ void k_bin_fill(DevScene sc, const BlockConst* __restrict__ blocks, int b0,
+__global__ void k_bin_fill(DevScene sc, const StepConst* __restrict__ steps,
+                           const BlockConst* __restrict__ blocks, int b0,
                            TileGeom g, const unsigned* __restrict__ offsets,
                            unsigned* __restrict__ cursor, int* __restrict__ bins) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -92,6 +109,7 @@ __global__ void k_bin_fill(DevScene sc, const BlockConst* __restrict__ blocks, i
     const float4 a = __ldg(&sc.tris[3 * t]), b = __ldg(&sc.tris[3 * t + 1]),
                  c = __ldg(&sc.tris[3 * t + 2]);
     if (!tri_above_ground(a, b, c)) return;
+    if (sc.closed && !faces_sun(a, b, c, steps, blocks[b0 + bl])) return;
     int tx0, tx1, ty0, ty1;
     if (!swept_tiles(a, b, c, blocks[b0 + bl], g, &tx0, &tx1, &ty0, &ty1)) return;
     const size_t row = (size_t)bl * g.tiles_x * g.tiles_y;
@@ -102,11 +120,11 @@ __global__ void k_bin_fill(DevScene sc, const BlockConst* __restrict__ blocks, i
         }
 }
 
-// One projected (triangle, step): sign-folded canonical edge functions, inside iff all >= 0,
-// and the clipped cell range [c0, c1] x [r0, r1] of its bounding box (r0 > r1: empty).
-struct Item {
+// One projected (triangle, step): sign-folded canonical edge functions (inside iff all
+// three are >= 0) and, packed, its clipped cell range and step:
+//   c0 | c1 << 5 | r0 << 10 | r1 << 15 | k << 20
+struct ItemCoef {
     float A[3], B[3], C[3];
-    int range;   // c0 | c1 << 8 | r0 << 16 | r1 << 24
 };
 
 __device__ __forceinline__ void canonical_edge(float px, float py, float qx, float qy, float fold,
@@ -120,41 +138,32 @@ __device__ __forceinline__ void canonical_edge(float px, float py, float qx, flo
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
-__device__ void setup_item(const float4& a, const float4& b, const float4& c, const StepConst& s,
-                           float tox, float toy, float dx, Item* it) {
-    // project along d onto z = 0, then to tile-local coordinates
+// Projects one triangle along step s onto z = 0 in tile-local coordinates.  Returns the
+// packed range, or -1 if the projection is degenerate, misses the tile, or (cull) faces
+// away from the sun: the projected signed area has the sign of n . d because d_z > 0.
+__device__ int setup_item(const float4& a, const float4& b, const float4& c, const StepConst& s,
+                          float tox, float toy, float dx, int k, bool cull, ItemCoef* it) {
     const float p0x = fmaf(-a.z, s.ux, a.x) - tox, p0y = fmaf(-a.z, s.uy, a.y) - toy;
     const float p1x = fmaf(-b.z, s.ux, b.x) - tox, p1y = fmaf(-b.z, s.uy, b.y) - toy;
     const float p2x = fmaf(-c.z, s.ux, c.x) - tox, p2y = fmaf(-c.z, s.uy, c.y) - toy;
     const float area = __fsub_rn(__fmul_rn(p1x - p0x, p2y - p0y), __fmul_rn(p1y - p0y, p2x - p0x));
-    int range = 0x00ff00ff;   // r0 = 255 > r1 = 0: empty
-    if (area != 0.f) {
-        const float fold = area > 0.f ? 1.f : -1.f;
-        canonical_edge(p0x, p0y, p1x, p1y, fold, &it->A[0], &it->B[0], &it->C[0]);
-        canonical_edge(p1x, p1y, p2x, p2y, fold, &it->A[1], &it->B[1], &it->C[1]);
-        canonical_edge(p2x, p2y, p0x, p0y, fold, &it->A[2], &it->B[2], &it->C[2]);
-        const float inv = 1.f / dx;
-        const float xmin = fminf(p0x, fminf(p1x, p2x)), xmax = fmaxf(p0x, fmaxf(p1x, p2x));
-        const float ymin = fminf(p0y, fminf(p1y, p2y)), ymax = fmaxf(p0y, fmaxf(p1y, p2y));
-        // cell k has its centre near (k + 0.5) dx; one cell of margin on each side
-        const float fc0 = floorf(xmin * inv - 0.5f) - 1.f, fc1 = ceilf(xmax * inv - 0.5f) + 1.f;
-        const float fr0 = floorf(ymin * inv - 0.5f) - 1.f, fr1 = ceilf(ymax * inv - 0.5f) + 1.f;
-        if (fc1 >= 0.f && fr1 >= 0.f && fc0 <= (float)(kTile - 1) && fr0 <= (float)(kTile - 1)) {
-            const int c0 = clampi((int)fmaxf(fc0, -1.f), 0, kTile - 1);
-            const int c1 = clampi((int)fminf(fc1, (float)kTile), 0, kTile - 1);
-            const int r0 = clampi((int)fmaxf(fr0, -1.f), 0, kTile - 1);
-            const int r1 = clampi((int)fminf(fr1, (float)kTile), 0, kTile - 1);
-            range = c0 | (c1 << 8) | (r0 << 16) | (r1 << 24);
-        }
-    }
-    it->range = range;
-}
-
-__device__ __forceinline__ bool covered(const Item& it, float x, float y) {
-    const float e0 = fmaf(it.A[0], x, fmaf(it.B[0], y, it.C[0]));
-    const float e1 = fmaf(it.A[1], x, fmaf(it.B[1], y, it.C[1]));
-    const float e2 = fmaf(it.A[2], x, fmaf(it.B[2], y, it.C[2]));
-    return e0 >= 0.f && e1 >= 0.f && e2 >= 0.f;
+    if (area == 0.f || (cull && area < 0.f)) return -1;
+    const float inv = 1.f / dx;
+    const float xmin = fminf(p0x, fminf(p1x, p2x)), xmax = fmaxf(p0x, fmaxf(p1x, p2x));
+    const float ymin = fminf(p0y, fminf(p1y, p2y)), ymax = fmaxf(p0y, fmaxf(p1y, p2y));
+    // cell k has its centre near (k + 0.5) dx; one cell of margin on each side
+    const float fc0 = floorf(xmin * inv - 0.5f) - 1.f, fc1 = ceilf(xmax * inv - 0.5f) + 1.f;
+    const float fr0 = floorf(ymin * inv - 0.5f) - 1.f, fr1 = ceilf(ymax * inv - 0.5f) + 1.f;
+    if (fc1 < 0.f || fr1 < 0.f || fc0 > (float)(kTile - 1) || fr0 > (float)(kTile - 1)) return -1;
+    const float fold = area > 0.f ? 1.f : -1.f;
+    canonical_edge(p0x, p0y, p1x, p1y, fold, &it->A[0], &it->B[0], &it->C[0]);
+    canonical_edge(p1x, p1y, p2x, p2y, fold, &it->A[1], &it->B[1], &it->C[1]);
+    canonical_edge(p2x, p2y, p0x, p0y, fold, &it->A[2], &it->B[2], &it->C[2]);
+    const int c0 = clampi((int)fmaxf(fc0, -1.f), 0, kTile - 1);
+    const int c1 = clampi((int)fminf(fc1, (float)kTile), 0, kTile - 1);
+    const int r0 = clampi((int)fmaxf(fr0, -1.f), 0, kTile - 1);
+    const int r1 = clampi((int)fminf(fr1, (float)kTile), 0, kTile - 1);
+    return c0 | (c1 << 5) | (r0 << 10) | (r1 << 15) | (k << 20);
 }
 
 struct RasterArgs {
@@ -169,31 +178,48 @@ struct RasterArgs {
     int* best;                       // continuous state (== out.continuous or scratch)
     int load_state;                  // 0: start from zero, 1: from out.gross / best / run
     int final_chunk;
+    int cull;                        // closed scene: only faces toward the sun
     long long R;
 };
 
+constexpr int kWarpsRaster = kRasterThreads / 32;   // 8 bands of 4 rows
+
+// One CTA per 32 x 32-cell tile.  Per block: the binned triangles are staged in batches;
+// every (triangle, step) of a batch is projected once and appended to the lists of the
+// 4-row bands its box overlaps; each warp then covers its own band's items, its lanes
+// spread over the item's cells (8, 16 or 32 columns by up to 4 rows per pass), and ORs
+// the step bit into the band's slice of the tile's 64-bit masks in shared memory.  Bands
+// are private to their warp, so the masks need no atomics.
 __global__ void __launch_bounds__(kRasterThreads)
 k_raster(RasterArgs ra) {
     __shared__ float4 s_tri[kTriBatch * 3];
-    __shared__ Item s_item[kMaxItems];
+    __shared__ ItemCoef s_coef[kMaxItems];
+    __shared__ int s_pack[kMaxItems];
+    __shared__ unsigned short s_list[kWarpsRaster][kMaxItems];
+    __shared__ int s_cnt[kWarpsRaster];
+    __shared__ unsigned long long s_mask[kTile * kTile];
+    __shared__ float s_xl[kTile], s_yl[kTile];
     const TileGeom& g = ra.g;
     const int tile = blockIdx.x;
     const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row0 = warp * 4;
-    // tile origin and this thread's cell centres in tile-local coordinates; the centres
-    // are rounded exactly as the receivers' world coordinates, then shifted
+    // tile origin and cell centres in tile-local coordinates; the centres are rounded
+    // exactly as the receivers' world coordinates, then shifted
     const float tox = __fadd_rn(g.x0, __fmul_rn((float)(tx * kTile), g.dx));
     const float toy = __fadd_rn(g.y0, __fmul_rn((float)(ty * kTile), g.dx));
+    if (threadIdx.x < kTile) {
+        s_xl[threadIdx.x] = __fadd_rn(g.x0, __fmul_rn(__fadd_rn((float)(tx * kTile + threadIdx.x), 0.5f), g.dx)) - tox;
+    } else if (threadIdx.x < 2 * kTile) {
+        const int q = threadIdx.x - kTile;
+        s_yl[q] = __fadd_rn(g.y0, __fmul_rn(__fadd_rn((float)(ty * kTile + q), 0.5f), g.dx)) - toy;
+    }
     const int ix = tx * kTile + lane;
-    const float xl = __fadd_rn(g.x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), g.dx)) - tox;
-    float yl[4];
     long long outi[4];
     bool act[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int iy = ty * kTile + row0 + q;
-        yl[q] = __fadd_rn(g.y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), g.dx)) - toy;
         act[q] = ix < g.nx && iy < g.ny;
         outi[q] = (long long)iy * g.nx + ix;
     }
@@ -206,12 +232,13 @@ k_raster(RasterArgs ra) {
             st[q].best = ra.best[outi[q]];
             st[q].run = ra.out.run[outi[q]];
         }
+        s_mask[(row0 + q) * kTile + lane] = 0ull;
     }
     const int n_tiles = g.tiles_x * g.tiles_y;
+    const bool cull = ra.cull != 0;
     for (int bl = 0; bl < ra.nbc; ++bl) {
         const BlockConst* bcp = &ra.sun.blocks[ra.b0 + bl];
         const int j0 = bcp->j0, K = bcp->K;
-        uint64_t m[4] = {0, 0, 0, 0};
         const unsigned off = ra.offsets[(size_t)bl * n_tiles + tile];
         const unsigned cnt = ra.counts[(size_t)bl * n_tiles + tile];
         for (unsigned base = 0; base < cnt; base += kTriBatch) {
@@ -221,37 +248,55 @@ k_raster(RasterArgs ra) {
                 const int t = ra.bins[off + base + threadIdx.x / 3];
                 s_tri[threadIdx.x] = __ldg(&ra.sc.tris[3 * t + threadIdx.x % 3]);
             }
+            if (threadIdx.x < kWarpsRaster) s_cnt[threadIdx.x] = 0;
             __syncthreads();
             const int items = nt * K;
             for (int it = threadIdx.x; it < items; it += kRasterThreads) {
                 const int t = it / K, k = it - t * K;
-                const StepConst s = ra.sun.steps[j0 + k];
-                setup_item(s_tri[3 * t], s_tri[3 * t + 1], s_tri[3 * t + 2], s, tox, toy, g.dx,
-                           &s_item[it]);
+                const int pk = setup_item(s_tri[3 * t], s_tri[3 * t + 1], s_tri[3 * t + 2],
+                                          ra.sun.steps[j0 + k], tox, toy, g.dx, k, cull, &s_coef[it]);
+                if (pk >= 0) {
+                    s_pack[it] = pk;
+                    const int w0 = ((pk >> 10) & 31) >> 2, w1 = ((pk >> 15) & 31) >> 2;
+                    for (int w = w0; w <= w1; ++w) s_list[w][atomicAdd(&s_cnt[w], 1)] = (unsigned short)it;
+                }
             }
             __syncthreads();
-            for (int it = 0; it < items; ++it) {
-                const int range = s_item[it].range;
-                const int c0 = range & 0xff, c1 = (range >> 8) & 0xff;
-                const int r0 = (range >> 16) & 0xff, r1 = (range >> 24) & 0xff;
-                const int ra0 = max(r0, row0), ra1 = min(r1, row0 + 3);
-                if (ra0 > ra1) continue;                       // warp-uniform
-                if (lane < c0 || lane > c1) continue;
-                const Item& item = s_item[it];
-                const int k = it % K;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int row = row0 + q;
-                    if (row >= ra0 && row <= ra1 && covered(item, xl, yl[q])) m[q] |= 1ull << k;
+            const int n = s_cnt[warp];
+            for (int q = 0; q < n; ++q) {
+                const int it = s_list[warp][q];
+                const int pk = s_pack[it];
+                const int c0 = pk & 31, c1 = (pk >> 5) & 31;
+                const int ra0 = max((pk >> 10) & 31, row0), ra1 = min((pk >> 15) & 31, row0 + 3);
+                const unsigned long long bit = 1ull << (pk >> 20);
+                const int width = c1 - c0 + 1;
+                const int sh = width <= 8 ? 3 : (width <= 16 ? 4 : 5);
+                const int col = c0 + (lane & ((1 << sh) - 1));
+                const int rpp = 32 >> sh;
+                if (col > c1) continue;
+                const ItemCoef& ic = s_coef[it];
+                const float x = s_xl[col];
+                const float e0x = fmaf(ic.A[0], x, ic.C[0]), e1x = fmaf(ic.A[1], x, ic.C[1]),
+                            e2x = fmaf(ic.A[2], x, ic.C[2]);
+                for (int r = ra0 + (lane >> sh); r <= ra1; r += rpp) {
+                    const float y = s_yl[r];
+                    if (fmaf(ic.B[0], y, e0x) >= 0.f && fmaf(ic.B[1], y, e1x) >= 0.f &&
+                        fmaf(ic.B[2], y, e2x) >= 0.f)
+                        s_mask[r * kTile + col] |= bit;
                 }
             }
         }
+        __syncwarp();
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            stitch(st[q], m[q], K, bcp->new_day);
+            const int cell = (row0 + q) * kTile + lane;
+            const unsigned long long m = s_mask[cell];
+            s_mask[cell] = 0ull;
+            stitch(st[q], m, K, bcp->new_day);
             if (ra.out.masks && act[q])
-                ra.out.masks[(size_t)bcp->mask_block * ra.R + outi[q]] |= m[q] << bcp->mask_bit;
+                ra.out.masks[(size_t)bcp->mask_block * ra.R + outi[q]] |= m << bcp->mask_bit;
         }
+        __syncwarp();
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -305,7 +350,7 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
         unsigned total = 0;
         if (sc.T > 0) {
             dim3 grid((sc.T + tpb - 1) / tpb, nbc);
-            k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.blocks, b0, g, counts);
+            k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, counts);
             e = cudaMemcpyAsync(offsets, counts, sizeof(unsigned) * ncc, cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) break;
             e = exclusive_scan_u32(offsets, (long long)ncc, d_total, st);
@@ -320,7 +365,7 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
                 e = cudaMallocAsync(&bins, sizeof(int) * bins_cap, st);
                 if (e != cudaSuccess) { bins = nullptr; break; }
             }
-            if (total > 0) k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.blocks, b0, g, offsets, cursor, bins);
+            if (total > 0) k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, offsets, cursor, bins);
         } else {
             e = cudaMemsetAsync(offsets, 0, sizeof(unsigned) * ncc, st);
             if (e != cudaSuccess) break;
@@ -332,6 +377,7 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
         ra.load_state = (b0 > 0) || out.accumulate_into;
         ra.final_chunk = (b0 + nbc >= sun.n_blocks);
         ra.R = R;
+        ra.cull = sc.closed;
         if (b0 == 0 && out.accumulate_into) {
             // run lengths never cross calls (calls cover whole days)
             e = cudaMemsetAsync(out.run, 0, sizeof(int) * (size_t)R, st);
@@ -413,7 +459,7 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
         unsigned total = 0;
         dim3 grid((sc.T + tpb - 1) / tpb, nbc);
         if (sc.T > 0) {
-            k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.blocks, b0, g, counts);
+            k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, counts);
             e = cudaMemcpyAsync(offsets, counts, sizeof(unsigned) * ncc, cudaMemcpyDeviceToDevice, st);
             if (e == cudaSuccess) e = exclusive_scan_u32_with(offsets, (long long)ncc, partial, d_total, st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
@@ -428,7 +474,7 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
             nbc = (nbc + 1) / 2;          // retry this chunk with fewer blocks
             continue;
         }
-        if (total > 0) k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.blocks, b0, g, offsets, cursor, bins);
+        if (total > 0) k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, offsets, cursor, bins);
         RasterArgs ra;
         ra.sc = sc; ra.sun = sun; ra.g = g; ra.b0 = b0; ra.nbc = nbc;
         ra.offsets = offsets; ra.counts = counts; ra.bins = bins;
@@ -436,6 +482,7 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
         ra.load_state = (b0 > 0) || out.accumulate_into;
         ra.final_chunk = (b0 + nbc >= sun.n_blocks);
         ra.R = R;
+        ra.cull = sc.closed;
         k_raster<<<n_tiles, kRasterThreads, 0, st>>>(ra);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -288,6 +288,133 @@ k_accrual(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
     if (COUNT && warp_live) flush_counts(out, n_box, n_tri);
 }
 
+// ------------------------------------------------------------ per-lane traversal
+// Watertight test with the major axis chosen at run time (component selects instead of
+// the template), so lanes of a warp can test different steps at once.
+__device__ __forceinline__ float pick(const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+__device__ __forceinline__ float pick3(const float3& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+__device__ __forceinline__ bool hit_tri_rt(const float3& o, const float4& a, const float4& b,
+                                           const float4& c, const StepConst& s, float tmin) {
+    const int kz = s.kz, kx = kz == 2 ? 0 : kz + 1, ky = kz == 0 ? 2 : kz - 1;
+    const float oz = pick3(o, kz), ox = pick3(o, kx), oy = pick3(o, ky);
+    const float az = pick(a, kz) - oz, bz = pick(b, kz) - oz, cz = pick(c, kz) - oz;
+    const float ax = fmaf(-s.Sx, az, pick(a, kx) - ox), ay = fmaf(-s.Sy, az, pick(a, ky) - oy);
+    const float bx = fmaf(-s.Sx, bz, pick(b, kx) - ox), by = fmaf(-s.Sy, bz, pick(b, ky) - oy);
+    const float cx = fmaf(-s.Sx, cz, pick(c, kx) - ox), cy = fmaf(-s.Sy, cz, pick(c, ky) - oy);
+    const float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
+    const float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
+    const float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
+    const float det = U + V + W;
+    if (det == 0.f) return false;
+    const float T = U * (s.Sz * az) + V * (s.Sz * bz) + W * (s.Sz * cz);
+    return det > 0.f ? (T > tmin * det) : (T < tmin * det);
+}
+
+// Ray-traced accrual with one independent traversal per lane ("while-while": each lane
+// descends internal nodes until it reaches a leaf its fan overlaps, then the lanes process
+// their leaves together).  Block and step constants are copied per warp into shared
+// memory, so warps of a CTA never wait for one another.
+template <bool COUNT>
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
+k_accrual_lane(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
+    __shared__ BlockConst s_bc[kWarpsPerCta];
+    __shared__ StepConst s_st[kWarpsPerCta][kMaxBlock];
+    unsigned long long n_box = 0, n_tri = 0;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long warp_id = (long long)blockIdx.x * kWarpsPerCta + wib;
+    if (warp_id >= warp_count(rc)) return;
+    const Receiver r = load_receiver(rc, warp_id, lane);
+    RunState st = load_state(out, r);
+    BlockConst& bc = s_bc[wib];
+    StepConst* ss = s_st[wib];
+    for (int b = 0; b < sun.n_blocks; ++b) {
+        __syncwarp();
+        for (int w = lane; w < (int)(sizeof(BlockConst) / 4); w += 32)
+            reinterpret_cast<int*>(&bc)[w] = reinterpret_cast<const int*>(&sun.blocks[b])[w];
+        __syncwarp();
+        const int K = bc.K;
+        for (int w = lane; w < K * (int)(sizeof(StepConst) / 4); w += 32)
+            reinterpret_cast<int*>(ss)[w] = reinterpret_cast<const int*>(&sun.steps[bc.j0])[w];
+        __syncwarp();
+        const uint64_t full = (K >= 64) ? ~0ull : ((1ull << K) - 1ull);
+        const bool wedge = bc.wedge_ok != 0.f;
+        uint64_t m = 0;
+        int i = r.active ? 0 : sc.n_nodes;
+        while (i < sc.n_nodes && m != full) {
+            int tri = -1;
+            float4 lo, hi;
+            while (i < sc.n_nodes) {
+                lo = __ldg(&sc.nodes[2 * i]);
+                hi = __ldg(&sc.nodes[2 * i + 1]);
+                const int esc = __float_as_int(lo.w);
+                const bool in = wedge ? fan_box(r.o, bc, lo, hi) : slope_box(r.o, bc, lo, hi);
+                if (COUNT) ++n_box;
+                if (!in) { i = esc; continue; }
+                tri = __float_as_int(hi.w);
+                if (tri >= 0) { i = esc; break; }
+                i = i + 1;
+            }
+            if (tri < 0) break;
+            const float4 ta = __ldg(&sc.tris[3 * tri]);
+            const float4 tb = __ldg(&sc.tris[3 * tri + 1]);
+            const float4 tc = __ldg(&sc.tris[3 * tri + 2]);
+            int ka, kb;
+            candidate_steps(r.o, bc, bc.psi, ta, tb, tc, &ka, &kb);
+            for (int k = ka; k <= kb; ++k) {
+                if ((m >> k) & 1ull) continue;
+                if (COUNT) ++n_tri;
+                if (hit_tri_rt(r.o, ta, tb, tc, ss[k], r.tmin)) m |= 1ull << k;
+            }
+        }
+        stitch(st, m, K, bc.new_day);
+        if (out.masks && r.active) out.masks[(long long)bc.mask_block * rc.R + r.out] |= m << bc.mask_bit;
+    }
+    store_state(out, r, st);
+    if (COUNT) flush_counts(out, n_box, n_tri);
+}
+
+// Per-step sweep with one independent traversal per lane.
+template <bool COUNT>
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
+k_sweep_lane(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
+    unsigned long long n_box = 0, n_tri = 0;
+    const int lane = threadIdx.x & 31;
+    const long long warp_id = (long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+    if (warp_id >= warp_count(rc)) return;
+    const Receiver r = load_receiver(rc, warp_id, lane);
+    RunState st = load_state(out, r);
+    for (int b = 0; b < sun.n_blocks; ++b) {
+        const int j0 = sun.blocks[b].j0, K = sun.blocks[b].K;
+        uint64_t m = 0;
+        for (int k = 0; k < K; ++k) {
+            const StepConst s = sun.steps[j0 + k];
+            bool hit = false;
+            int i = r.active ? 0 : sc.n_nodes;
+            while (i < sc.n_nodes && !hit) {
+                const float4 lo = __ldg(&sc.nodes[2 * i]);
+                const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
+                const int esc = __float_as_int(lo.w);
+                const int tri = __float_as_int(hi.w);
+                if (COUNT) ++n_box;
+                if (!hit_box(r.o, s.ix, s.iy, s.iz, lo, hi)) { i = esc; continue; }
+                if (tri < 0) { i = i + 1; continue; }
+                if (COUNT) ++n_tri;
+                hit = hit_tri_rt(r.o, __ldg(&sc.tris[3 * tri]), __ldg(&sc.tris[3 * tri + 1]),
+                                 __ldg(&sc.tris[3 * tri + 2]), s, r.tmin);
+                i = esc;
+            }
+            if (hit) m |= 1ull << k;
+        }
+        stitch(st, m, K, sun.blocks[b].new_day);
+        if (out.masks && r.active)
+            out.masks[(long long)sun.blocks[b].mask_block * rc.R + r.out] |= m << sun.blocks[b].mask_bit;
+    }
+    store_state(out, r, st);
+    if (COUNT) flush_counts(out, n_box, n_tri);
+}
+
 long long host_warps(const DevRecv& rc) {
     if (rc.is_grid) return (long long)((rc.nx + 7) / 8) * ((rc.ny + 3) / 4);
     return (rc.R + 31) / 32;
@@ -295,13 +422,30 @@ long long host_warps(const DevRecv& rc) {
 
 }  // namespace
 
+// Traversal mode: 1 = warp-coherent (packet), 2 = per lane, 0 = the measured default:
+// per lane for the per-step sweep (single rays: lanes rarely wait on each other), packet
+// for the accrual (its leaf work is a loop over steps that lanes share best in lockstep).
+int g_trace_mode[2] = {0, 0};   // [0] sweep, [1] accrual
+
+static bool use_lane(int which, const DevRecv& rc) {
+    const int mode = g_trace_mode[which];
+    (void)rc;
+    return mode == 2 || (mode == 0 && which == 0);
+}
+
 cudaError_t launch_sweep_trace(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
                                const DevOut& out, cudaStream_t st) {
     const long long warps = host_warps(rc);
     if (warps == 0) return cudaSuccess;
-    const long long ctas = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
-    if (out.stats) k_sweep<true><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, st>>>(sc, rc, sun, out);
-    else k_sweep<false><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, st>>>(sc, rc, sun, out);
+    const unsigned ctas = (unsigned)((warps + kWarpsPerCta - 1) / kWarpsPerCta);
+    const int T = 32 * kWarpsPerCta;
+    if (use_lane(0, rc)) {
+        if (out.stats) k_sweep_lane<true><<<ctas, T, 0, st>>>(sc, rc, sun, out);
+        else k_sweep_lane<false><<<ctas, T, 0, st>>>(sc, rc, sun, out);
+    } else {
+        if (out.stats) k_sweep<true><<<ctas, T, 0, st>>>(sc, rc, sun, out);
+        else k_sweep<false><<<ctas, T, 0, st>>>(sc, rc, sun, out);
+    }
     return cudaGetLastError();
 }
 
@@ -309,10 +453,19 @@ cudaError_t launch_accrual_trace(const DevScene& sc, const DevRecv& rc, const De
                                  const DevOut& out, cudaStream_t st) {
     const long long warps = host_warps(rc);
     if (warps == 0) return cudaSuccess;
-    const long long ctas = (warps + kWarpsPerCta - 1) / kWarpsPerCta;
-    if (out.stats) k_accrual<true><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, st>>>(sc, rc, sun, out);
-    else k_accrual<false><<<(unsigned)ctas, 32 * kWarpsPerCta, 0, st>>>(sc, rc, sun, out);
+    const unsigned ctas = (unsigned)((warps + kWarpsPerCta - 1) / kWarpsPerCta);
+    const int T = 32 * kWarpsPerCta;
+    if (use_lane(1, rc)) {
+        if (out.stats) k_accrual_lane<true><<<ctas, T, 0, st>>>(sc, rc, sun, out);
+        else k_accrual_lane<false><<<ctas, T, 0, st>>>(sc, rc, sun, out);
+    } else {
+        if (out.stats) k_accrual<true><<<ctas, T, 0, st>>>(sc, rc, sun, out);
+        else k_accrual<false><<<ctas, T, 0, st>>>(sc, rc, sun, out);
+    }
     return cudaGetLastError();
 }
+
+void set_trace_mode(int which, int mode) { g_trace_mode[which] = mode; }
+int get_trace_mode(int which) { return g_trace_mode[which]; }
 
 }  // namespace sa

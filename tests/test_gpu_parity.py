@@ -181,3 +181,43 @@ def test_raster_methods_reject_point_receivers(cuda_lib):
     with pytest.raises(B.SAError) as e:
         B.sa_accumulate(sc, rc, sun, 1.0, "sweep_raster")
     assert e.value.status == -8
+
+
+@pytest.mark.parametrize("mode", ["packet", "lane"])
+@pytest.mark.parametrize("method", ["sweep_trace", "accrual_trace"])
+def test_traversal_modes_give_the_same_parity(cuda_lib, mode, method):
+    """Both BVH traversal modes, on ground grids and facade points."""
+    B = cuda_lib
+    w = workload("district_small")
+    key = B.SA_OPT_SWEEP_TRAVERSAL if method == "sweep_trace" else B.SA_OPT_ACCRUAL_TRAVERSAL
+    B.sa_set_option(key, B.TRAVERSAL[mode])
+    try:
+        sc = _scene(B, w)
+        sun = B.Sun(w.sun.dirs, w.sun.day_start)
+        for part, rc in (("ground", _ground(B, w)),
+                         ("facade", B.Receivers.points(w.facade_pos, w.facade_nrm))):
+            bits, near = cached_oracle(f"district_small/{part}", w, part)
+            masks = B.sa_shadow_masks(sc, rc, sun, method)
+            gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start))
+            assert_bits_parity(gb, bits, near, f"{method}/{mode}/{part}")
+    finally:
+        B.sa_set_option(key, 0)
+
+
+@pytest.mark.parametrize("block_len", [0, 9])
+def test_closed_scene_rasters_only_sun_facing_faces(cuda_lib, block_len):
+    """A scene declared closed skips faces turned away from the sun; parity and Theorem 1
+    still hold."""
+    B = cuda_lib
+    w = workload("district_small")
+    bits, near = cached_oracle("district_small/ground", w, "ground")
+    sc = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+    rc = _ground(B, w)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start, block_len)
+    a = B.sa_shadow_masks(sc, rc, sun, "accrual_sam")
+    b = B.sa_shadow_masks(sc, rc, sun, "sweep_raster")
+    assert torch.equal(a, b)
+    gb = B.unpack_masks(a, B.block_sizes(w.sun.day_start, block_len))
+    assert_bits_parity(gb, bits, near, f"closed/K{block_len}")
+    g, _, c = _run(B, sc, rc, sun, "accrual_sam")
+    assert_counts_parity(g, c, bits, near, w.sun.day_start, "closed")
