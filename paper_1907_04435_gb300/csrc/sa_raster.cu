@@ -30,8 +30,7 @@ namespace {
 
 constexpr int kTile = 32;               // cells per tile side
 constexpr int kRasterThreads = 256;     // 8 warps x 4 rows each
-constexpr int kTriBatch = 8;            // triangles staged per batch
-constexpr int kMaxItems = kTriBatch * kMaxBlock;
+constexpr int kTriBatch = 32;           // triangles staged per batch
 
 struct TileGeom {
     float x0, y0, dx;
@@ -120,52 +119,6 @@ __global__ void k_bin_fill(DevScene sc, const StepConst* __restrict__ steps,
         }
 }
 
-// One projected (triangle, step): sign-folded canonical edge functions (inside iff all
-// three are >= 0) and, packed, its clipped cell range and step:
-//   c0 | c1 << 5 | r0 << 10 | r1 << 15 | k << 20
-struct ItemCoef {
-    float A[3], B[3], C[3];
-};
-
-__device__ __forceinline__ void canonical_edge(float px, float py, float qx, float qy, float fold,
-                                               float* A, float* B, float* C) {
-    float ax = px, ay = py, bx = qx, by = qy, s = fold;
-    if (!(px < qx || (px == qx && py < qy))) { ax = qx; ay = qy; bx = px; by = py; s = -fold; }
-    const float a = ay - by, b = bx - ax;
-    const float c = -fmaf(a, ax, b * ay);
-    *A = s * a; *B = s * b; *C = s * c;    // exact sign flips
-}
-
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-
-// Projects one triangle along step s onto z = 0 in tile-local coordinates.  Returns the
-// packed range, or -1 if the projection is degenerate, misses the tile, or (cull) faces
-// away from the sun: the projected signed area has the sign of n . d because d_z > 0.
-__device__ int setup_item(const float4& a, const float4& b, const float4& c, const StepConst& s,
-                          float tox, float toy, float dx, int k, bool cull, ItemCoef* it) {
-    const float p0x = fmaf(-a.z, s.ux, a.x) - tox, p0y = fmaf(-a.z, s.uy, a.y) - toy;
-    const float p1x = fmaf(-b.z, s.ux, b.x) - tox, p1y = fmaf(-b.z, s.uy, b.y) - toy;
-    const float p2x = fmaf(-c.z, s.ux, c.x) - tox, p2y = fmaf(-c.z, s.uy, c.y) - toy;
-    const float area = __fsub_rn(__fmul_rn(p1x - p0x, p2y - p0y), __fmul_rn(p1y - p0y, p2x - p0x));
-    if (area == 0.f || (cull && area < 0.f)) return -1;
-    const float inv = 1.f / dx;
-    const float xmin = fminf(p0x, fminf(p1x, p2x)), xmax = fmaxf(p0x, fmaxf(p1x, p2x));
-    const float ymin = fminf(p0y, fminf(p1y, p2y)), ymax = fmaxf(p0y, fmaxf(p1y, p2y));
-    // cell k has its centre near (k + 0.5) dx; one cell of margin on each side
-    const float fc0 = floorf(xmin * inv - 0.5f) - 1.f, fc1 = ceilf(xmax * inv - 0.5f) + 1.f;
-    const float fr0 = floorf(ymin * inv - 0.5f) - 1.f, fr1 = ceilf(ymax * inv - 0.5f) + 1.f;
-    if (fc1 < 0.f || fr1 < 0.f || fc0 > (float)(kTile - 1) || fr0 > (float)(kTile - 1)) return -1;
-    const float fold = area > 0.f ? 1.f : -1.f;
-    canonical_edge(p0x, p0y, p1x, p1y, fold, &it->A[0], &it->B[0], &it->C[0]);
-    canonical_edge(p1x, p1y, p2x, p2y, fold, &it->A[1], &it->B[1], &it->C[1]);
-    canonical_edge(p2x, p2y, p0x, p0y, fold, &it->A[2], &it->B[2], &it->C[2]);
-    const int c0 = clampi((int)fmaxf(fc0, -1.f), 0, kTile - 1);
-    const int c1 = clampi((int)fminf(fc1, (float)kTile), 0, kTile - 1);
-    const int r0 = clampi((int)fmaxf(fr0, -1.f), 0, kTile - 1);
-    const int r1 = clampi((int)fminf(fr1, (float)kTile), 0, kTile - 1);
-    return c0 | (c1 << 5) | (r0 << 10) | (r1 << 15) | (k << 20);
-}
-
 struct RasterArgs {
     DevScene sc;
     DevSun sun;
@@ -182,21 +135,40 @@ struct RasterArgs {
     long long R;
 };
 
-constexpr int kWarpsRaster = kRasterThreads / 32;   // 8 bands of 4 rows
+constexpr int kWarpsRaster = kRasterThreads / 32;
+constexpr int kSub = 8;                        // steps per work unit
 
-// One CTA per 32 x 32-cell tile.  Per block: the binned triangles are staged in batches;
-// every (triangle, step) of a batch is projected once and appended to the lists of the
-// 4-row bands its box overlaps; each warp then covers its own band's items, its lanes
-// spread over the item's cells (8, 16 or 32 columns by up to 4 rows per pass), and ORs
-// the step bit into the band's slice of the tile's 64-bit masks in shared memory.  Bands
-// are private to their warp, so the masks need no atomics.
+// Edge function of a triangle edge (3D endpoints v -> v') projected along step k, at a
+// ground point p (all xy tile-local).  With c = p - v.xy and e = v' - v,
+//   E_k(p) = cross(q' - q, p - q),  q = v.xy - v.z u_k,  u_k = d_xy / d_z,
+// expands to  E_k(p) = P + Qx u_k.x + Qy u_k.y  with
+//   P = e.x c.y - e.y c.x,  Qx = -v.z e.y - e.z c.y,  Qy = v.z e.x + e.z c.x,
+// so a cell sets (P, Qx, Qy) up once and tests a run of steps with two FMAs per edge.
+// The endpoints are taken in a canonical order (the other order only flips the sign), so
+// an edge shared by two triangles gives the same value in both up to an exact negation:
+// a cell on it is covered by at least one (watertight).
+struct EdgeRef {
+    float vx, vy, vz, ex, ey, ez, s;
+};
+
+__device__ __forceinline__ EdgeRef edge_ref(const float4& a, const float4& b) {
+    const bool keep = a.x < b.x || (a.x == b.x && (a.y < b.y || (a.y == b.y && a.z < b.z)));
+    const float4& v = keep ? a : b;
+    const float4& w = keep ? b : a;
+    return EdgeRef{v.x, v.y, v.z, w.x - v.x, w.y - v.y, w.z - v.z, keep ? 1.f : -1.f};
+}
+
+// One CTA per 32 x 32-cell tile.  Per block, the binned triangles are staged in batches
+// (xy shifted to the tile); each warp takes work units (triangle, run of <= 8 steps),
+// bounds the run's swept projection, spreads its lanes over the covered cells (8, 16 or
+// 32 columns per pass), and per cell tests the run's steps with the expanded edge
+// functions; the step bits are ORed into the tile's 64-bit masks in shared memory.
 __global__ void __launch_bounds__(kRasterThreads)
 k_raster(RasterArgs ra) {
-    __shared__ float4 s_tri[kTriBatch * 3];
-    __shared__ ItemCoef s_coef[kMaxItems];
-    __shared__ int s_pack[kMaxItems];
-    __shared__ unsigned short s_list[kWarpsRaster][kMaxItems];
-    __shared__ int s_cnt[kWarpsRaster];
+    __shared__ float4 s_tri[kTriBatch * 3];                  // xy tile-local
+    __shared__ unsigned long long s_front[kTriBatch];        // steps with n . d > 0
+    __shared__ unsigned long long s_back[kTriBatch];         // steps with n . d < 0
+    __shared__ float2 s_u[kMaxBlock];                        // ground slope per step
     __shared__ unsigned long long s_mask[kTile * kTile];
     __shared__ float s_xl[kTile], s_yl[kTile];
     const TileGeom& g = ra.g;
@@ -217,76 +189,126 @@ k_raster(RasterArgs ra) {
     const int ix = tx * kTile + lane;
     long long outi[4];
     bool act[4];
+    RunState st[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int iy = ty * kTile + row0 + q;
         act[q] = ix < g.nx && iy < g.ny;
         outi[q] = (long long)iy * g.nx + ix;
-    }
-    RunState st[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
         st[q] = RunState{0, 0, 0};
         if (act[q] && ra.load_state) {
             st[q].gross = ra.out.gross[outi[q]];
             st[q].best = ra.best[outi[q]];
             st[q].run = ra.out.run[outi[q]];
         }
-        s_mask[(row0 + q) * kTile + lane] = 0ull;
     }
+    for (int c = threadIdx.x; c < kTile * kTile; c += kRasterThreads) s_mask[c] = 0ull;
     const int n_tiles = g.tiles_x * g.tiles_y;
     const bool cull = ra.cull != 0;
+    const float inv_dx = 1.f / g.dx;
     for (int bl = 0; bl < ra.nbc; ++bl) {
         const BlockConst* bcp = &ra.sun.blocks[ra.b0 + bl];
         const int j0 = bcp->j0, K = bcp->K;
+        const int nsub = (K + kSub - 1) / kSub;
         const unsigned off = ra.offsets[(size_t)bl * n_tiles + tile];
         const unsigned cnt = ra.counts[(size_t)bl * n_tiles + tile];
+        __syncthreads();
+        if (threadIdx.x < K) {
+            const StepConst& s = ra.sun.steps[j0 + threadIdx.x];
+            s_u[threadIdx.x] = make_float2(s.ux, s.uy);
+        }
         for (unsigned base = 0; base < cnt; base += kTriBatch) {
             const int nt = (int)min((unsigned)kTriBatch, cnt - base);
             __syncthreads();
             if (threadIdx.x < nt * 3) {
                 const int t = ra.bins[off + base + threadIdx.x / 3];
-                s_tri[threadIdx.x] = __ldg(&ra.sc.tris[3 * t + threadIdx.x % 3]);
+                float4 v = __ldg(&ra.sc.tris[3 * t + threadIdx.x % 3]);
+                v.x -= tox;
+                v.y -= toy;
+                s_tri[threadIdx.x] = v;
             }
-            if (threadIdx.x < kWarpsRaster) s_cnt[threadIdx.x] = 0;
             __syncthreads();
-            const int items = nt * K;
-            for (int it = threadIdx.x; it < items; it += kRasterThreads) {
-                const int t = it / K, k = it - t * K;
-                const int pk = setup_item(s_tri[3 * t], s_tri[3 * t + 1], s_tri[3 * t + 2],
-                                          ra.sun.steps[j0 + k], tox, toy, g.dx, k, cull, &s_coef[it]);
-                if (pk >= 0) {
-                    s_pack[it] = pk;
-                    const int w0 = ((pk >> 10) & 31) >> 2, w1 = ((pk >> 15) & 31) >> 2;
-                    for (int w = w0; w <= w1; ++w) s_list[w][atomicAdd(&s_cnt[w], 1)] = (unsigned short)it;
+            if (threadIdx.x < nt) {
+                const float4 a = s_tri[3 * threadIdx.x], b = s_tri[3 * threadIdx.x + 1], c = s_tri[3 * threadIdx.x + 2];
+                const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+                const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+                const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+                unsigned long long fr = 0, bk = 0;
+                for (int k = 0; k < K; ++k) {
+                    const StepConst& s = ra.sun.steps[j0 + k];
+                    const float nd = nx * s.dx + ny * s.dy + nz * s.dz;
+                    if (nd > 0.f) fr |= 1ull << k;
+                    if (nd < 0.f && !cull) bk |= 1ull << k;
                 }
+                s_front[threadIdx.x] = fr;
+                s_back[threadIdx.x] = bk;
             }
             __syncthreads();
-            const int n = s_cnt[warp];
-            for (int q = 0; q < n; ++q) {
-                const int it = s_list[warp][q];
-                const int pk = s_pack[it];
-                const int c0 = pk & 31, c1 = (pk >> 5) & 31;
-                const int ra0 = max((pk >> 10) & 31, row0), ra1 = min((pk >> 15) & 31, row0 + 3);
-                const unsigned long long bit = 1ull << (pk >> 20);
+            const int units = nt * nsub;
+            for (int un = warp; un < units; un += kWarpsRaster) {
+                const int t = un / nsub, k0 = (un - t * nsub) * kSub;
+                const int kn = min(kSub, K - k0);
+                const unsigned long long run_bits = ((kn >= 64) ? ~0ull : ((1ull << kn) - 1ull)) << k0;
+                const unsigned long long fr = s_front[t] & run_bits, bk = s_back[t] & run_bits;
+                if ((fr | bk) == 0ull) continue;
+                const float4 a = s_tri[3 * t], b = s_tri[3 * t + 1], c = s_tri[3 * t + 2];
+                // swept bounding box of the run's projections (one cell of margin)
+                float uxlo = 3.4e38f, uxhi = -3.4e38f, uylo = 3.4e38f, uyhi = -3.4e38f;
+                for (int k = k0; k < k0 + kn; ++k) {
+                    const float2 u = s_u[k];
+                    uxlo = fminf(uxlo, u.x); uxhi = fmaxf(uxhi, u.x);
+                    uylo = fminf(uylo, u.y); uyhi = fmaxf(uyhi, u.y);
+                }
+                const float az = fmaxf(a.z, 0.f), bz = fmaxf(b.z, 0.f), cz = fmaxf(c.z, 0.f);
+                const float xmin = fminf(a.x - az * uxhi, fminf(b.x - bz * uxhi, c.x - cz * uxhi));
+                const float xmax = fmaxf(a.x - az * uxlo, fmaxf(b.x - bz * uxlo, c.x - cz * uxlo));
+                const float ymin = fminf(a.y - az * uyhi, fminf(b.y - bz * uyhi, c.y - cz * uyhi));
+                const float ymax = fmaxf(a.y - az * uylo, fmaxf(b.y - bz * uylo, c.y - cz * uylo));
+                // cells whose centres (k + 0.5) dx fall in the box, with 0.01 cell of slack
+                const float fc0 = ceilf(xmin * inv_dx - 0.51f), fc1 = floorf(xmax * inv_dx - 0.49f);
+                const float fr0 = ceilf(ymin * inv_dx - 0.51f), fr1 = floorf(ymax * inv_dx - 0.49f);
+                if (fc1 < 0.f || fr1 < 0.f || fc0 > (float)(kTile - 1) || fr0 > (float)(kTile - 1) ||
+                    fc0 > fc1 || fr0 > fr1) continue;
+                const int c0 = (int)fmaxf(fc0, 0.f), c1 = (int)fminf(fc1, (float)(kTile - 1));
+                const int r0 = (int)fmaxf(fr0, 0.f), r1 = (int)fminf(fr1, (float)(kTile - 1));
+                const EdgeRef E0 = edge_ref(a, b), E1 = edge_ref(b, c), E2 = edge_ref(c, a);
+                // lanes walk the box's cells in row-major order, 32 at a time; the row of
+                // cell index i is floor((i + 0.5) / width), exact in FP32 for <= 1024 cells
                 const int width = c1 - c0 + 1;
-                const int sh = width <= 8 ? 3 : (width <= 16 ? 4 : 5);
-                const int col = c0 + (lane & ((1 << sh) - 1));
-                const int rpp = 32 >> sh;
-                if (col > c1) continue;
-                const ItemCoef& ic = s_coef[it];
-                const float x = s_xl[col];
-                const float e0x = fmaf(ic.A[0], x, ic.C[0]), e1x = fmaf(ic.A[1], x, ic.C[1]),
-                            e2x = fmaf(ic.A[2], x, ic.C[2]);
-                for (int r = ra0 + (lane >> sh); r <= ra1; r += rpp) {
+                const int ncell = width * (r1 - r0 + 1);
+                const float inv_w = 1.f / (float)width;
+                for (int idx = lane; idx < ncell; idx += 32) {
+                    const int rr = (int)(((float)idx + 0.5f) * inv_w);
+                    const int r = r0 + rr, col = c0 + (idx - rr * width);
+                    const float x = s_xl[col];
                     const float y = s_yl[r];
-                    if (fmaf(ic.B[0], y, e0x) >= 0.f && fmaf(ic.B[1], y, e1x) >= 0.f &&
-                        fmaf(ic.B[2], y, e2x) >= 0.f)
-                        s_mask[r * kTile + col] |= bit;
+                    float P[3], QX[3], QY[3], SG[3];
+                    const EdgeRef* ee[3] = {&E0, &E1, &E2};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const EdgeRef& e = *ee[q];
+                        const float cx = x - e.vx, cy = y - e.vy;
+                        P[q] = __fsub_rn(__fmul_rn(e.ex, cy), __fmul_rn(e.ey, cx));
+                        QX[q] = -fmaf(e.vz, e.ey, e.ez * cy);
+                        QY[q] = fmaf(e.vz, e.ex, e.ez * cx);
+                        SG[q] = e.s;
+                    }
+                    unsigned long long hit = 0;
+                    for (int k = k0; k < k0 + kn; ++k) {
+                        const float2 u = s_u[k];
+                        const float f0 = SG[0] * fmaf(QY[0], u.y, fmaf(QX[0], u.x, P[0]));
+                        const float f1 = SG[1] * fmaf(QY[1], u.y, fmaf(QX[1], u.x, P[1]));
+                        const float f2 = SG[2] * fmaf(QY[2], u.y, fmaf(QX[2], u.x, P[2]));
+                        const bool inf = f0 >= 0.f && f1 >= 0.f && f2 >= 0.f;
+                        const bool inb = f0 <= 0.f && f1 <= 0.f && f2 <= 0.f;
+                        const unsigned long long bit = 1ull << k;
+                        if ((inf && (fr & bit)) || (inb && (bk & bit))) hit |= bit;
+                    }
+                    if (hit) atomicOr(&s_mask[r * kTile + col], hit);
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int cell = (row0 + q) * kTile + lane;
@@ -296,7 +318,6 @@ k_raster(RasterArgs ra) {
             if (ra.out.masks && act[q])
                 ra.out.masks[(size_t)bcp->mask_block * ra.R + outi[q]] |= m << bcp->mask_bit;
         }
-        __syncwarp();
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
