@@ -73,6 +73,12 @@ sa::BlockConst make_block(const float* dirs, const std::vector<sa::StepConst>& s
     b.j0 = j0; b.K = K; b.new_day = new_day; b.monotone = 0;
     b.mask_block = 0; b.mask_bit = 0;
     b.uxlo = b.uylo = 3.4e38f; b.uxhi = b.uyhi = -3.4e38f;
+    for (int q = 0; q < 3; ++q) { b.dlo[q] = 3.4e38f; b.dhi[q] = -3.4e38f; }
+    for (int k = 0; k < K; ++k)
+        for (int q = 0; q < 3; ++q) {
+            b.dlo[q] = std::min(b.dlo[q], dirs[3 * (j0 + k) + q]);
+            b.dhi[q] = std::max(b.dhi[q], dirs[3 * (j0 + k) + q]);
+        }
     for (int k = 0; k < K; ++k) {
         b.uxlo = std::min(b.uxlo, steps[j0 + k].ux); b.uxhi = std::max(b.uxhi, steps[j0 + k].ux);
         b.uylo = std::min(b.uylo, steps[j0 + k].uy); b.uyhi = std::max(b.uyhi, steps[j0 + k].uy);

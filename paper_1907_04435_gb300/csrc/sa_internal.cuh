@@ -46,8 +46,30 @@ struct BlockConst {
     float g2x, g2y, g2z, psi_eps;
     float e1x, e1y, e1z, pad_f0;
     float e2x, e2y, e2z, pad_f1;
+    float dlo[3], dhi[3];           // component-wise box of the block's directions
     float psi[kMaxBlock];
 };
+
+// Can some ray of the block (directions inside [dlo, dhi]) from o meet the plane of the
+// triangle (a, b, c) at t > 0?  If o lies strictly on one side and every direction in the
+// box points away from the plane, no ray of the block can hit the triangle.
+__device__ __forceinline__ bool plane_reachable(const float3& o, const float4& a, const float4& b,
+                                                const float4& c, const BlockConst& bc) {
+    const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+    const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+    const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+    const float s0 = nx * (o.x - a.x) + ny * (o.y - a.y) + nz * (o.z - a.z);
+    const float lo = fminf(nx * bc.dlo[0], nx * bc.dhi[0]) + fminf(ny * bc.dlo[1], ny * bc.dhi[1]) +
+                     fminf(nz * bc.dlo[2], nz * bc.dhi[2]);
+    const float hi = fmaxf(nx * bc.dlo[0], nx * bc.dhi[0]) + fmaxf(ny * bc.dlo[1], ny * bc.dhi[1]) +
+                     fmaxf(nz * bc.dlo[2], nz * bc.dhi[2]);
+    // relative slack for rounding of s0 and of the bounds
+    const float tol = 1e-5f * (fabsf(nx) + fabsf(ny) + fabsf(nz)) *
+                      (1.f + fabsf(o.x - a.x) + fabsf(o.y - a.y) + fabsf(o.z - a.z));
+    if (s0 > tol && lo > tol) return false;
+    if (s0 < -tol && hi < -tol) return false;
+    return true;
+}
 
 // ---------------------------------------------------------------------------- scene
 // BVH nodes in depth-first order, two float4 each:

@@ -219,75 +219,6 @@ __device__ __forceinline__ void candidate_steps(const float3& o, const BlockCons
     *kb = l - 1;
 }
 
-template <bool COUNT>
-__global__ void __launch_bounds__(32 * kWarpsPerCta)
-k_accrual(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
-    __shared__ BlockConst s_bc;
-    unsigned long long n_box = 0, n_tri = 0;
-    const int lane = threadIdx.x & 31;
-    const long long warp_id = (long long)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
-    const bool warp_live = warp_id < warp_count(rc);
-    Receiver r;
-    if (warp_live) r = load_receiver(rc, warp_id, lane);
-    else r.active = false;
-    RunState st = load_state(out, r);
-    for (int b = 0; b < sun.n_blocks; ++b) {
-        __syncthreads();
-        for (int w = threadIdx.x; w < (int)(sizeof(BlockConst) / 4); w += blockDim.x)
-            reinterpret_cast<int*>(&s_bc)[w] = reinterpret_cast<const int*>(&sun.blocks[b])[w];
-        __syncthreads();
-        if (!warp_live) continue;
-        const BlockConst& bc = s_bc;
-        const int K = bc.K;
-        const uint64_t full = (K >= 64) ? ~0ull : ((1ull << K) - 1ull);
-        uint64_t m = 0;
-        const bool wedge = bc.wedge_ok != 0.f;
-        int i = 0;
-        unsigned live = __ballot_sync(kFull, r.active);
-        while (live != 0u && i < sc.n_nodes) {
-            const float4 lo = __ldg(&sc.nodes[2 * i]);
-            const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
-            const int esc = __float_as_int(lo.w);
-            const int tri = __float_as_int(hi.w);
-            const bool want = r.active && m != full;
-            const bool in = want && (wedge ? fan_box(r.o, bc, lo, hi) : slope_box(r.o, bc, lo, hi));
-            if (COUNT && want) ++n_box;
-            if (tri >= 0) {
-                int ka = K, kb = -1;
-                float4 ta, tb, tc;
-                if (in) {
-                    ta = __ldg(&sc.tris[3 * tri]);
-                    tb = __ldg(&sc.tris[3 * tri + 1]);
-                    tc = __ldg(&sc.tris[3 * tri + 2]);
-                    candidate_steps(r.o, bc, bc.psi, ta, tb, tc, &ka, &kb);
-                }
-                const int wa = __reduce_min_sync(kFull, ka);
-                const int wb = __reduce_max_sync(kFull, kb);
-                for (int k = wa; k <= wb; ++k) {
-                    const StepConst s = sun.steps[bc.j0 + k];
-                    const bool test = in && k >= ka && k <= kb && !((m >> k) & 1ull);
-                    if (test) {
-                        if (COUNT) ++n_tri;
-                        bool h;
-                        if (s.kz == 2) h = hit_tri<2>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
-                        else if (s.kz == 0) h = hit_tri<0>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
-                        else h = hit_tri<1>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
-                        if (h) m |= 1ull << k;
-                    }
-                }
-                i = esc;
-                live = __ballot_sync(kFull, r.active && m != full);
-            } else {
-                i = __any_sync(kFull, in) ? i + 1 : esc;
-            }
-        }
-        stitch(st, m, K, bc.new_day);
-        if (out.masks && r.active) out.masks[(long long)bc.mask_block * rc.R + r.out] |= m << bc.mask_bit;
-    }
-    if (warp_live) store_state(out, r, st);
-    if (COUNT && warp_live) flush_counts(out, n_box, n_tri);
-}
-
 // ------------------------------------------------------------ per-lane traversal
 // Watertight test with the major axis chosen at run time (component selects instead of
 // the template), so lanes of a warp can test different steps at once.
@@ -310,6 +241,93 @@ __device__ __forceinline__ bool hit_tri_rt(const float3& o, const float4& a, con
     if (det == 0.f) return false;
     const float T = U * (s.Sz * az) + V * (s.Sz * bz) + W * (s.Sz * cz);
     return det > 0.f ? (T > tmin * det) : (T < tmin * det);
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(32 * kWarpsPerCta)
+k_accrual(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
+    // block and step constants are copied per warp, so warps never wait for one another
+    __shared__ BlockConst s_bc[kWarpsPerCta];
+    __shared__ StepConst s_st[kWarpsPerCta][kMaxBlock];
+    unsigned long long n_box = 0, n_tri = 0;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long warp_id = (long long)blockIdx.x * kWarpsPerCta + wib;
+    if (warp_id >= warp_count(rc)) return;
+    const Receiver r = load_receiver(rc, warp_id, lane);
+    RunState st = load_state(out, r);
+    BlockConst& bc = s_bc[wib];
+    StepConst* ss = s_st[wib];
+    // occluder cache: the last triangle that shadowed this receiver is tried first in the
+    // next block (shadows move slowly, so it often covers many of the block's steps)
+    int ctri = -1;
+    for (int b = 0; b < sun.n_blocks; ++b) {
+        __syncwarp();
+        for (int w = lane; w < (int)(sizeof(BlockConst) / 4); w += 32)
+            reinterpret_cast<int*>(&bc)[w] = reinterpret_cast<const int*>(&sun.blocks[b])[w];
+        __syncwarp();
+        const int K = bc.K;
+        for (int w = lane; w < K * (int)(sizeof(StepConst) / 4); w += 32)
+            reinterpret_cast<int*>(ss)[w] = reinterpret_cast<const int*>(&sun.steps[bc.j0])[w];
+        __syncwarp();
+        const uint64_t full = (K >= 64) ? ~0ull : ((1ull << K) - 1ull);
+        uint64_t m = 0;
+        const bool wedge = bc.wedge_ok != 0.f;
+        if (r.active && ctri >= 0) {
+            const float4 ta = __ldg(&sc.tris[3 * ctri]);
+            const float4 tb = __ldg(&sc.tris[3 * ctri + 1]);
+            const float4 tc = __ldg(&sc.tris[3 * ctri + 2]);
+            int ka, kb;
+            candidate_steps(r.o, bc, bc.psi, ta, tb, tc, &ka, &kb);
+            for (int k = ka; k <= kb; ++k) {
+                if (COUNT) ++n_tri;
+                if (hit_tri_rt(r.o, ta, tb, tc, ss[k], r.tmin)) m |= 1ull << k;
+            }
+        }
+        int i = 0;
+        unsigned live = __ballot_sync(kFull, r.active && m != full);
+        while (live != 0u && i < sc.n_nodes) {
+            const float4 lo = __ldg(&sc.nodes[2 * i]);
+            const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
+            const int esc = __float_as_int(lo.w);
+            const int tri = __float_as_int(hi.w);
+            const bool want = r.active && m != full;
+            const bool in = want && (wedge ? fan_box(r.o, bc, lo, hi) : slope_box(r.o, bc, lo, hi));
+            if (COUNT && want) ++n_box;
+            if (tri >= 0) {
+                int ka = K, kb = -1;
+                float4 ta, tb, tc;
+                if (in) {
+                    ta = __ldg(&sc.tris[3 * tri]);
+                    tb = __ldg(&sc.tris[3 * tri + 1]);
+                    tc = __ldg(&sc.tris[3 * tri + 2]);
+                    if (plane_reachable(r.o, ta, tb, tc, bc))
+                        candidate_steps(r.o, bc, bc.psi, ta, tb, tc, &ka, &kb);
+                }
+                const int wa = __reduce_min_sync(kFull, ka);
+                const int wb = __reduce_max_sync(kFull, kb);
+                for (int k = wa; k <= wb; ++k) {
+                    const bool test = in && k >= ka && k <= kb && !((m >> k) & 1ull);
+                    if (test) {
+                        const StepConst& s = ss[k];
+                        if (COUNT) ++n_tri;
+                        bool h;
+                        if (s.kz == 2) h = hit_tri<2>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
+                        else if (s.kz == 0) h = hit_tri<0>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
+                        else h = hit_tri<1>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
+                        if (h) { m |= 1ull << k; ctri = tri; }
+                    }
+                }
+                i = esc;
+                live = __ballot_sync(kFull, r.active && m != full);
+            } else {
+                i = __any_sync(kFull, in) ? i + 1 : esc;
+            }
+        }
+        stitch(st, m, K, bc.new_day);
+        if (out.masks && r.active) out.masks[(long long)bc.mask_block * rc.R + r.out] |= m << bc.mask_bit;
+    }
+    store_state(out, r, st);
+    if (COUNT) flush_counts(out, n_box, n_tri);
 }
 
 // Ray-traced accrual with one independent traversal per lane ("while-while": each lane
@@ -360,8 +378,8 @@ k_accrual_lane(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
             const float4 ta = __ldg(&sc.tris[3 * tri]);
             const float4 tb = __ldg(&sc.tris[3 * tri + 1]);
             const float4 tc = __ldg(&sc.tris[3 * tri + 2]);
-            int ka, kb;
-            candidate_steps(r.o, bc, bc.psi, ta, tb, tc, &ka, &kb);
+            int ka = 0, kb = -1;
+            if (plane_reachable(r.o, ta, tb, tc, bc)) candidate_steps(r.o, bc, bc.psi, ta, tb, tc, &ka, &kb);
             for (int k = ka; k <= kb; ++k) {
                 if ((m >> k) & 1ull) continue;
                 if (COUNT) ++n_tri;
