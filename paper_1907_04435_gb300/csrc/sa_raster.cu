@@ -163,8 +163,10 @@ __device__ __forceinline__ EdgeRef edge_ref(const float4& a, const float4& b) {
 // bounds the run's swept projection, spreads its lanes over the covered cells (8, 16 or
 // 32 columns per pass), and per cell tests the run's steps with the expanded edge
 // functions; the step bits are ORed into the tile's 64-bit masks in shared memory.
+template <bool COUNT>
 __global__ void __launch_bounds__(kRasterThreads)
 k_raster(RasterArgs ra) {
+    unsigned long long n_cell = 0, n_test = 0;
     __shared__ float4 s_tri[kTriBatch * 3];                  // xy tile-local
     __shared__ unsigned long long s_front[kTriBatch];        // steps with n . d > 0
     __shared__ unsigned long long s_back[kTriBatch];         // steps with n . d < 0
@@ -278,6 +280,7 @@ k_raster(RasterArgs ra) {
                 const int ncell = width * (r1 - r0 + 1);
                 const float inv_w = 1.f / (float)width;
                 for (int idx = lane; idx < ncell; idx += 32) {
+                    if (COUNT) { ++n_cell; n_test += kn; }
                     const int rr = (int)(((float)idx + 0.5f) * inv_w);
                     const int r = r0 + rr, col = c0 + (idx - rr * width);
                     const float x = s_xl[col];
@@ -326,6 +329,16 @@ k_raster(RasterArgs ra) {
         ra.best[outi[q]] = st[q].best;
         ra.out.run[outi[q]] = st[q].run;
         if (ra.final_chunk && ra.out.minutes) ra.out.minutes[outi[q]] = (float)st[q].gross * ra.out.step_minutes;
+    }
+    if (COUNT) {
+        for (int o = 16; o > 0; o >>= 1) {
+            n_cell += __shfl_down_sync(0xffffffffu, n_cell, o);
+            n_test += __shfl_down_sync(0xffffffffu, n_test, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&ra.out.stats[2], n_cell);
+            atomicAdd(&ra.out.stats[3], n_test);
+        }
     }
 }
 
@@ -408,7 +421,8 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
                 if (e != cudaSuccess) break;
             }
         }
-        k_raster<<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        if (out.stats) k_raster<true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        else k_raster<false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
         e = cudaGetLastError();
     }
     if (counts) cudaFreeAsync(counts, st);
@@ -504,7 +518,8 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
         ra.final_chunk = (b0 + nbc >= sun.n_blocks);
         ra.R = R;
         ra.cull = sc.closed;
-        k_raster<<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        if (out.stats) k_raster<true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        else k_raster<false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         b0 += nbc;
