@@ -145,6 +145,7 @@ sa::DevRecv dev_recv(const sa_receivers* r) {
     d.is_grid = r->is_grid;
     d.x0 = r->x0; d.y0 = r->y0; d.dx = r->dx; d.nx = r->nx; d.ny = r->ny;
     d.orig = r->d_orig;
+    d.nrm = r->d_nrm;
     d.perm = r->d_perm;
     d.R = r->R;
     return d;
@@ -557,7 +558,8 @@ sa_status sa_receivers_points(const float* pos, const float* normal, int64_t n,
     if (e == cudaSuccess && normal) e = upload(hn.data(), hn.size(), 0, &dn, st);
     if (e == cudaSuccess && n > 0) e = cudaMalloc(&r->d_orig, sizeof(float4) * (size_t)n);
     if (e == cudaSuccess && n > 0) e = cudaMalloc(&r->d_perm, sizeof(int) * (size_t)n);
-    if (e == cudaSuccess) e = sa::sort_points(dp, dn, n, r->d_orig, r->d_perm, st);
+    if (e == cudaSuccess && n > 0 && normal) e = cudaMalloc(&r->d_nrm, sizeof(float4) * (size_t)n);
+    if (e == cudaSuccess) e = sa::sort_points(dp, dn, n, r->d_orig, r->d_nrm, r->d_perm, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (dp) cudaFree(dp);
     if (dn) cudaFree(dn);
@@ -574,6 +576,7 @@ void sa_receivers_destroy(sa_receivers* recv) {
     cudaDeviceSynchronize();
     if (recv->d_orig) cudaFree(recv->d_orig);
     if (recv->d_perm) cudaFree(recv->d_perm);
+    if (recv->d_nrm) cudaFree(recv->d_nrm);
     delete recv;
 }
 

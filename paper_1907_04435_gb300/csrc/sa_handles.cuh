@@ -34,6 +34,7 @@ struct sa_receivers {
     int nx, ny;
     long long R;
     float4* d_orig = nullptr;
+    float4* d_nrm = nullptr;           // facade normals (sorted), null for ground points
     int* d_perm = nullptr;
 };
 

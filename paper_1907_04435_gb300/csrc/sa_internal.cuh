@@ -183,6 +183,7 @@ struct DevRecv {
     int nx, ny;
     // points, in Morton order: origin (already offset) and t_min; perm = input index
     const float4* orig;
+    const float4* nrm;      // facade normals in the same order, or null
     const int* perm;
     long long R;
 };
@@ -249,7 +250,7 @@ cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, lo
 
 // Morton order of point receivers: fills perm (sorted -> input index) and sorted origins
 cudaError_t sort_points(const float* d_pos, const float* d_nrm, long long n, float4* d_orig,
-                        int* d_perm, cudaStream_t st);
+                        float4* d_nrm_sorted, int* d_perm, cudaStream_t st);
 
 // radix sort of (key, value) pairs by key (stable, 32-bit keys), in place via scratch
 cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, long long n, cudaStream_t st);

@@ -313,9 +313,13 @@ __global__ void k_points_prep(const float* __restrict__ pos, const float* __rest
     }
 }
 
-__global__ void k_points_morton(const float4* __restrict__ o, long long n,
-                                const unsigned* __restrict__ box, unsigned* __restrict__ keys,
-                                unsigned* __restrict__ vals) {
+// Sort key of a point receiver: 30-bit Morton code of its origin; facade points are first
+// grouped by the azimuth of their normal (16 sectors in the top 4 bits, Morton in the
+// remaining 28), so a warp holds walls that face the same way and turn toward or away
+// from the sun together.
+__global__ void k_points_morton(const float4* __restrict__ o, const float* __restrict__ nrm,
+                                long long n, const unsigned* __restrict__ box,
+                                unsigned* __restrict__ keys, unsigned* __restrict__ vals) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float lo[3], inv[3];
@@ -325,23 +329,33 @@ __global__ void k_points_morton(const float4* __restrict__ o, long long n,
         inv[k] = ext > 0.f ? 1.f / ext : 0.f;
     }
     float4 p = o[i];
-    keys[i] = morton3((p.x - lo[0]) * inv[0], (p.y - lo[1]) * inv[1], (p.z - lo[2]) * inv[2]);
+    unsigned key = morton3((p.x - lo[0]) * inv[0], (p.y - lo[1]) * inv[1], (p.z - lo[2]) * inv[2]);
+    if (nrm) {
+        const float az = atan2f(nrm[3 * i + 1], nrm[3 * i]);          // (-pi, pi]
+        unsigned sector = (unsigned)((az + 3.14159265f) * (16.f / 6.2831853f));
+        sector = sector > 15u ? 15u : sector;
+        key = (sector << 28) | (key >> 2);
+    }
+    keys[i] = key;
     vals[i] = (unsigned)i;
 }
 
-__global__ void k_points_gather(const float4* __restrict__ o, const unsigned* __restrict__ order,
-                                long long n, float4* __restrict__ out, int* __restrict__ perm) {
+__global__ void k_points_gather(const float4* __restrict__ o, const float* __restrict__ nrm,
+                                const unsigned* __restrict__ order, long long n,
+                                float4* __restrict__ out, float4* __restrict__ nout,
+                                int* __restrict__ perm) {
     long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     unsigned i = order[k];
     out[k] = o[i];
     perm[k] = (int)i;
+    if (nout) nout[k] = make_float4(nrm[3ll * i], nrm[3ll * i + 1], nrm[3ll * i + 2], 0.f);
 }
 
 }  // namespace
 
 cudaError_t sort_points(const float* d_pos, const float* d_nrm, long long n, float4* d_orig,
-                        int* d_perm, cudaStream_t st) {
+                        float4* d_nrm_sorted, int* d_perm, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     float4* tmp = nullptr;
     unsigned *box = nullptr, *keys = nullptr, *vals = nullptr;
@@ -353,10 +367,11 @@ cudaError_t sort_points(const float* d_pos, const float* d_nrm, long long n, flo
         unsigned init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
         e = cudaMemcpyAsync(box, init, sizeof(init), cudaMemcpyHostToDevice, st);
         k_points_prep<<<nblk(n), kThreads, 0, st>>>(d_pos, d_nrm, n, tmp, box);
-        k_points_morton<<<nblk(n), kThreads, 0, st>>>(tmp, n, box, keys, vals);
+        k_points_morton<<<nblk(n), kThreads, 0, st>>>(tmp, d_nrm, n, box, keys, vals);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, n, st);
-        k_points_gather<<<nblk(n), kThreads, 0, st>>>(tmp, vals, n, d_orig, d_perm);
+        k_points_gather<<<nblk(n), kThreads, 0, st>>>(tmp, d_nrm, vals, n, d_orig,
+                                                       d_nrm ? d_nrm_sorted : nullptr, d_perm);
         if (e == cudaSuccess) e = cudaGetLastError();
         cudaError_t e2 = cudaStreamSynchronize(st);
         if (e == cudaSuccess) e = e2;

@@ -78,7 +78,7 @@ extern "C" sa_status sa_accumulate_grid_noalloc(const sa_scene* scene, const sa_
     sa::DevRecv drc;
     drc.is_grid = 1;
     drc.x0 = grid->x0; drc.y0 = grid->y0; drc.dx = grid->dx; drc.nx = grid->nx; drc.ny = grid->ny;
-    drc.orig = nullptr; drc.perm = nullptr; drc.R = grid->R;
+    drc.orig = nullptr; drc.nrm = nullptr; drc.perm = nullptr; drc.R = grid->R;
     sa::DevSun dsun;
     dsun.steps = sun->d_steps;
     dsun.blocks = sun->d_blocks;

@@ -26,6 +26,7 @@ constexpr int kWarpsPerCta = 4;
 struct Receiver {
     float3 o;
     float tmin;
+    float3 n;        // facade normal (zero for ground receivers)
     long long out;   // output index
     bool active;
 };
@@ -44,6 +45,7 @@ __device__ __forceinline__ Receiver load_receiver(const DevRecv& rc, long long w
         r.o.y = __fadd_rn(rc.y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), rc.dx));
         r.o.z = 0.f;
         r.tmin = kGroundTmin;
+        r.n = make_float3(0.f, 0.f, 0.f);
         r.out = iy * rc.nx + ix;
     } else {
         const long long s = warp_id * 32 + lane;
@@ -51,6 +53,8 @@ __device__ __forceinline__ Receiver load_receiver(const DevRecv& rc, long long w
         const float4 p = r.active ? rc.orig[s] : make_float4(0.f, 0.f, 0.f, 0.f);
         r.o = make_float3(p.x, p.y, p.z);
         r.tmin = p.w;
+        const float4 nn = (r.active && rc.nrm) ? rc.nrm[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+        r.n = make_float3(nn.x, nn.y, nn.z);
         r.out = r.active ? rc.perm[s] : 0;
     }
     return r;
@@ -153,12 +157,18 @@ k_sweep(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
 
 // ------------------------------------------------------------------- accrual trace
 // Conservative test of a box against the block's ray fan from origin o (see BlockConst).
+// front: the receiver's normal nf has nf . d > 0 for every direction of the block, so all
+// rays stay in front of the receiver's wall plane and boxes wholly behind it are skipped.
 __device__ __forceinline__ bool fan_box(const float3& o, const BlockConst& bc, const float4& lo,
-                                        const float4& hi) {
+                                        const float4& hi, bool front = false,
+                                        const float3& nf = float3{0.f, 0.f, 0.f}) {
     if (hi.z < o.z) return false;                       // every ray climbs
     const float cx = 0.5f * (lo.x + hi.x) - o.x, cy = 0.5f * (lo.y + hi.y) - o.y,
                 cz = 0.5f * (lo.z + hi.z) - o.z;
     const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y), hz = 0.5f * (hi.z - lo.z);
+    if (front && nf.x * cx + nf.y * cy + nf.z * cz + fabsf(nf.x) * hx + fabsf(nf.y) * hy +
+                     fabsf(nf.z) * hz < -1e-4f)
+        return false;
     const float R = sqrtf(cx * cx + cy * cy + cz * cz) + sqrtf(hx * hx + hy * hy + hz * hz);
     const float slack = 1e-5f * R + 1e-4f;
     // in-plane half-spaces
@@ -243,6 +253,62 @@ __device__ __forceinline__ bool hit_tri_rt(const float3& o, const float4& a, con
     return det > 0.f ? (T > tmin * det) : (T < tmin * det);
 }
 
+
+// Plücker form of the exact ray/triangle test for one origin and many steps.  For the
+// line through o along d, the side of edge v -> v' is  d . ((v - o) x (v' - o)):  the
+// moment m_e = (v - o) x (v' - o) depends only on the origin and the edge, so a triangle
+// is set up once per receiver and each step costs three dot products.  Edges are taken in
+// a canonical vertex order (the other order negates m exactly), so a line through an edge
+// shared by two triangles sees exactly negated values and is inside at least one
+// (watertight, zero counts as inside).  The hit distance t = ((a - o) . n) / (d . n) must
+// exceed t_min.
+struct PluckerTri {
+    float m[3][3];
+    float nx, ny, nz, aon;
+};
+
+__device__ __forceinline__ void plucker_edge(const float3& o, const float4& a, const float4& b,
+                                             float* m) {
+    const bool keep = a.x < b.x || (a.x == b.x && (a.y < b.y || (a.y == b.y && a.z < b.z)));
+    const float4& v = keep ? a : b;
+    const float4& w = keep ? b : a;
+    const float px = v.x - o.x, py = v.y - o.y, pz = v.z - o.z;
+    const float qx = w.x - o.x, qy = w.y - o.y, qz = w.z - o.z;
+    const float mx = __fsub_rn(__fmul_rn(py, qz), __fmul_rn(pz, qy));
+    const float my = __fsub_rn(__fmul_rn(pz, qx), __fmul_rn(px, qz));
+    const float mz = __fsub_rn(__fmul_rn(px, qy), __fmul_rn(py, qx));
+    const float sg = keep ? 1.f : -1.f;
+    m[0] = sg * mx; m[1] = sg * my; m[2] = sg * mz;
+}
+
+__device__ __forceinline__ PluckerTri plucker_setup(const float3& o, const float4& a,
+                                                    const float4& b, const float4& c) {
+    PluckerTri p;
+    plucker_edge(o, a, b, p.m[0]);
+    plucker_edge(o, b, c, p.m[1]);
+    plucker_edge(o, c, a, p.m[2]);
+    const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+    const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+    p.nx = uy * vz - uz * vy;
+    p.ny = uz * vx - ux * vz;
+    p.nz = ux * vy - uy * vx;
+    p.aon = p.nx * (a.x - o.x) + p.ny * (a.y - o.y) + p.nz * (a.z - o.z);
+    return p;
+}
+
+__device__ __forceinline__ bool plucker_hit(const PluckerTri& p, float dx, float dy, float dz,
+                                            float tmin) {
+    // d . m computed in a fixed order, so a negated m gives an exactly negated value
+    const float s0 = fmaf(dz, p.m[0][2], fmaf(dy, p.m[0][1], dx * p.m[0][0]));
+    const float s1 = fmaf(dz, p.m[1][2], fmaf(dy, p.m[1][1], dx * p.m[1][0]));
+    const float s2 = fmaf(dz, p.m[2][2], fmaf(dy, p.m[2][1], dx * p.m[2][0]));
+    const bool inside = (s0 >= 0.f && s1 >= 0.f && s2 >= 0.f) || (s0 <= 0.f && s1 <= 0.f && s2 <= 0.f);
+    if (!inside) return false;
+    const float nd = fmaf(dz, p.nz, fmaf(dy, p.ny, dx * p.nx));
+    if (nd == 0.f) return false;
+    return nd > 0.f ? (p.aon > tmin * nd) : (p.aon < tmin * nd);
+}
+
 template <bool COUNT>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_accrual(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
@@ -272,15 +338,21 @@ k_accrual(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
         const uint64_t full = (K >= 64) ? ~0ull : ((1ull << K) - 1ull);
         uint64_t m = 0;
         const bool wedge = bc.wedge_ok != 0.f;
+        // lower bound of n . d over the block's direction box
+        const float nd_lo = fminf(r.n.x * bc.dlo[0], r.n.x * bc.dhi[0]) +
+                            fminf(r.n.y * bc.dlo[1], r.n.y * bc.dhi[1]) +
+                            fminf(r.n.z * bc.dlo[2], r.n.z * bc.dhi[2]);
+        const bool front = nd_lo > 1e-6f;
         if (r.active && ctri >= 0) {
             const float4 ta = __ldg(&sc.tris[3 * ctri]);
             const float4 tb = __ldg(&sc.tris[3 * ctri + 1]);
             const float4 tc = __ldg(&sc.tris[3 * ctri + 2]);
             int ka, kb;
             candidate_steps(r.o, bc, bc.psi, ta, tb, tc, &ka, &kb);
+            const PluckerTri pt = plucker_setup(r.o, ta, tb, tc);
             for (int k = ka; k <= kb; ++k) {
                 if (COUNT) ++n_tri;
-                if (hit_tri_rt(r.o, ta, tb, tc, ss[k], r.tmin)) m |= 1ull << k;
+                if (plucker_hit(pt, ss[k].dx, ss[k].dy, ss[k].dz, r.tmin)) m |= 1ull << k;
             }
         }
         int i = 0;
@@ -291,7 +363,7 @@ k_accrual(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
             const int esc = __float_as_int(lo.w);
             const int tri = __float_as_int(hi.w);
             const bool want = r.active && m != full;
-            const bool in = want && (wedge ? fan_box(r.o, bc, lo, hi) : slope_box(r.o, bc, lo, hi));
+            const bool in = want && (wedge ? fan_box(r.o, bc, lo, hi, front, r.n) : slope_box(r.o, bc, lo, hi));
             if (COUNT && want) ++n_box;
             if (tri >= 0) {
                 int ka = K, kb = -1;
@@ -305,16 +377,18 @@ k_accrual(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
                 }
                 const int wa = __reduce_min_sync(kFull, ka);
                 const int wb = __reduce_max_sync(kFull, kb);
-                for (int k = wa; k <= wb; ++k) {
-                    const bool test = in && k >= ka && k <= kb && !((m >> k) & 1ull);
-                    if (test) {
-                        const StepConst& s = ss[k];
-                        if (COUNT) ++n_tri;
-                        bool h;
-                        if (s.kz == 2) h = hit_tri<2>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
-                        else if (s.kz == 0) h = hit_tri<0>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
-                        else h = hit_tri<1>(r.o, ta, tb, tc, s.Sx, s.Sy, s.Sz, r.tmin);
-                        if (h) { m |= 1ull << k; ctri = tri; }
+                if (wa <= wb) {
+                    PluckerTri pt;
+                    if (ka <= kb) pt = plucker_setup(r.o, ta, tb, tc);
+                    for (int k = wa; k <= wb; ++k) {
+                        const bool test = k >= ka && k <= kb && !((m >> k) & 1ull);
+                        if (test) {
+                            if (COUNT) ++n_tri;
+                            if (plucker_hit(pt, ss[k].dx, ss[k].dy, ss[k].dz, r.tmin)) {
+                                m |= 1ull << k;
+                                ctri = tri;
+                            }
+                        }
                     }
                 }
                 i = esc;
