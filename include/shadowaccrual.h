@@ -90,9 +90,12 @@ int32_t sa_version(void);
  *   traversal per lane, 0 the default (per lane for the sweep, warp-coherent for the
  *   accrual, the faster of the two on the district workload).  Results do not depend on
  *   the option.
+ *   SA_OPT_RASTER_RUN: steps the ground raster tests per cell set-up (1..64, default 8):
+ *   longer runs amortise the set-up, shorter runs bound the swept box more tightly.
  * sa_get_option returns the current value, or -1 for an unknown key. */
 #define SA_OPT_SWEEP_TRAVERSAL 1
 #define SA_OPT_ACCRUAL_TRAVERSAL 2
+#define SA_OPT_RASTER_RUN 3
 sa_status sa_set_option(int32_t key, int32_t value);
 int32_t sa_get_option(int32_t key);
 
@@ -215,6 +218,52 @@ sa_status sa_shadow_masks(const sa_scene* scene, const sa_receivers* recv, const
 sa_status sa_height_grad(const sa_scene* scene, const sa_receivers* grid, const sa_sun* sun,
                          float step_minutes, const float* weights, float* dS_dh, double* S_out,
                          void* stream);
+
+/* ---------------------------------------------------------------- batched scenarios
+ * Impact of development variants (Sec. 7.1: the impact of a new or replaced building is
+ * the difference of the two states' accumulations), many variants x sun intervals in one
+ * persistent, CUDA-graph-captured launch over a ground grid.
+ * A variant adds tower triangles and removes base buildings (by building id of the base
+ * scene); its receivers are a rectangle of the base grid.  All arrays are host memory,
+ * copied at creation:
+ *   tower_tris  float [n_tower_tris][9], z >= 0      tower_off   int32 [V + 1]
+ *   removed_ids int32 [n_removed]                    removed_off int32 [V + 1]
+ *   regions     int32 [V][4]: first cell ix0, iy0 and size nx, ny of the region */
+typedef struct {
+    int32_t n_variants;
+    const float* tower_tris;
+    const int32_t* tower_off;
+    const int32_t* removed_ids;
+    const int32_t* removed_off;
+    const int32_t* regions;
+} sa_variants;
+typedef struct sa_batch sa_batch;
+
+/* Create a batch: the base scene's triangles are binned once per block of every interval,
+ * and with with_impact = 1 the base counts of the whole grid are computed per interval.
+ * The scene, grid and suns must outlive the batch.  Synchronises `stream`.
+ * Errors: SA_ERR_INVALID_ARG (offsets, regions outside the grid, bad towers),
+ * SA_ERR_UNSUPPORTED (point receivers, geometry below z = 0), SA_ERR_OOM, SA_ERR_CUDA. */
+sa_status sa_batch_create(const sa_scene* base, const sa_receivers* grid, const sa_variants* v,
+                          const sa_sun* const* intervals, int32_t n_intervals,
+                          int32_t with_impact, void* stream, sa_batch** out);
+void sa_batch_destroy(sa_batch* b);
+/* Outputs hold n_intervals x (sum of region cells); interval-major, then variant, then the
+ * region's cells row by row.  sa_batch_output_offset gives the first index of (interval,
+ * variant), or -1.  sa_batch_work_items is the number of (interval, variant, tile) items. */
+int64_t sa_batch_output_count(const sa_batch* b);
+int64_t sa_batch_output_offset(const sa_batch* b, int32_t interval, int32_t variant);
+int32_t sa_batch_work_items(const sa_batch* b);
+/* Run every item: counts int32 (gross shadowed steps per receiver, dev) and, if the batch
+ * has base counts and impact is non-NULL, impact int32 = variant minus base (dev).  The
+ * work runs as a CUDA graph (instantiated on the first call with these output pointers)
+ * holding one persistent launch that drains a work queue. */
+sa_status sa_batch_run(sa_batch* b, int32_t* counts, int32_t* impact, void* stream);
+/* Autotuner: times 1 or 2 persistent CTAs per SM x raster runs of 4, 8 or 16 steps on an
+ * eighth of the work items and keeps the fastest; reports the choice. */
+sa_status sa_batch_tune(sa_batch* b, int32_t* best_ctas, int32_t* best_run, void* stream);
+/* Work counters of one batch run (counters [2] cell set-ups, [3] cell-step tests). */
+sa_status sa_batch_work_counters(sa_batch* b, uint64_t* counters, void* stream);
 
 /* Work counters of one accumulation (diagnostics for roofline accounting): runs `method`
  * with counting enabled and writes counters uint64 [4] dev: [0] ray/fan-versus-box tests

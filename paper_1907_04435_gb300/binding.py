@@ -69,6 +69,18 @@ def lib():
             L.sa_work_counters.argtypes = [P, P, P, i32, P, P]
             L.sa_scene_declare_closed.argtypes = [P, i32]
             L.sa_set_option.argtypes = [i32, i32]
+            L.sa_batch_create.argtypes = [P, P, P, P, i32, i32, P, PP]
+            L.sa_batch_destroy.argtypes = [P]
+            L.sa_batch_destroy.restype = None
+            L.sa_batch_output_count.argtypes = [P]
+            L.sa_batch_output_count.restype = i64
+            L.sa_batch_output_offset.argtypes = [P, i32, i32]
+            L.sa_batch_output_offset.restype = i64
+            L.sa_batch_work_items.argtypes = [P]
+            L.sa_batch_work_items.restype = i32
+            L.sa_batch_run.argtypes = [P, P, P, P]
+            L.sa_batch_tune.argtypes = [P, P, P, P]
+            L.sa_batch_work_counters.argtypes = [P, P, P]
             L.sa_get_option.argtypes = [i32]
             L.sa_get_option.restype = i32
             L.sa_scene_from_footprints.argtypes = [P, P, i32, P, f32, i32, P, PP]
@@ -78,7 +90,8 @@ def lib():
                          "sa_receivers_grid", "sa_receivers_points", "sa_accumulate",
                          "sa_shadow_masks", "sa_accumulate_grid_noalloc", "sa_work_counters",
                          "sa_scene_from_footprints", "sa_scene_set_heights", "sa_height_grad",
-                         "sa_scene_declare_closed", "sa_set_option"):
+                         "sa_scene_declare_closed", "sa_set_option", "sa_batch_create",
+                         "sa_batch_run", "sa_batch_tune", "sa_batch_work_counters"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
     return _lib
@@ -276,7 +289,7 @@ def sa_work_counters(scene: Scene, recv: Receivers, sun: Sun, method, stream=Non
     return [int(x) for x in c.cpu().tolist()]
 
 
-SA_OPT_SWEEP_TRAVERSAL, SA_OPT_ACCRUAL_TRAVERSAL = 1, 2
+SA_OPT_SWEEP_TRAVERSAL, SA_OPT_ACCRUAL_TRAVERSAL, SA_OPT_RASTER_RUN = 1, 2, 3
 TRAVERSAL = {"auto": 0, "packet": 1, "lane": 2}
 
 
@@ -298,6 +311,69 @@ def sa_height_grad(scene: Scene, grid: Receivers, sun: Sun, step_minutes: float,
     _check(lib().sa_height_grad(scene.handle, grid.handle, sun.handle, float(step_minutes), _ptr(w),
                                 _ptr(g), _ptr(S), ct.c_void_p(_stream(stream))))
     return g, S[0]
+
+
+class _Variants(ct.Structure):
+    _fields_ = [("n_variants", ct.c_int32), ("tower_tris", ct.c_void_p), ("tower_off", ct.c_void_p),
+                ("removed_ids", ct.c_void_p), ("removed_off", ct.c_void_p), ("regions", ct.c_void_p)]
+
+
+class Batch:
+    """sa_batch: base scene + variants (towers, removed buildings, regions) x intervals."""
+
+    def __init__(self, scene: Scene, grid: Receivers, tower_tris, removed, regions, suns,
+                 with_impact: bool = True, stream=None):
+        V = len(tower_tris)
+        tow = np.ascontiguousarray(np.concatenate([np.asarray(t, np.float32).reshape(-1, 9)
+                                                   for t in tower_tris]) if V else
+                                   np.zeros((0, 9), np.float32), dtype=np.float32)
+        toff = np.zeros(V + 1, np.int32)
+        toff[1:] = np.cumsum([np.asarray(t).reshape(-1, 9).shape[0] for t in tower_tris])
+        rem = np.ascontiguousarray(np.concatenate([np.asarray(r, np.int32) for r in removed])
+                                   if V else np.zeros(0, np.int32), dtype=np.int32)
+        roff = np.zeros(V + 1, np.int32)
+        roff[1:] = np.cumsum([len(r) for r in removed])
+        reg = np.ascontiguousarray(regions, dtype=np.int32).reshape(-1, 4)
+        self._keep = (tow, toff, rem, roff, reg, scene, grid, list(suns))
+        desc = _Variants(V, tow.ctypes.data, toff.ctypes.data, rem.ctypes.data, roff.ctypes.data,
+                         reg.ctypes.data)
+        arr = (ct.c_void_p * max(1, len(suns)))(*[s.handle.value for s in suns])
+        h = ct.c_void_p()
+        _check(lib().sa_batch_create(scene.handle, grid.handle, ct.byref(desc), arr, len(suns),
+                                     1 if with_impact else 0, ct.c_void_p(_stream(stream)),
+                                     ct.byref(h)))
+        self.handle = h
+        self.V, self.I = V, len(suns)
+        self.n_out = int(lib().sa_batch_output_count(h))
+        self.n_items = int(lib().sa_batch_work_items(h))
+
+    def offset(self, interval: int, variant: int) -> int:
+        return int(lib().sa_batch_output_offset(self.handle, interval, variant))
+
+    def run(self, counts=None, impact=None, want_impact=True, stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if counts is None:
+            counts = torch.empty(max(1, self.n_out), dtype=torch.int32, device=dev)
+        if impact is None and want_impact:
+            impact = torch.empty(max(1, self.n_out), dtype=torch.int32, device=dev)
+        _check(lib().sa_batch_run(self.handle, _ptr(counts), _ptr(impact), ct.c_void_p(_stream(stream))))
+        return counts, impact
+
+    def tune(self, stream=None):
+        c, r = ct.c_int32(), ct.c_int32()
+        _check(lib().sa_batch_tune(self.handle, ct.byref(c), ct.byref(r), ct.c_void_p(_stream(stream))))
+        return c.value, r.value
+
+    def work_counters(self, stream=None):
+        c = torch.zeros(4, dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device()))
+        _check(lib().sa_batch_work_counters(self.handle, _ptr(c), ct.c_void_p(_stream(stream))))
+        return [int(x) for x in c.cpu().tolist()]
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.sa_batch_destroy(h)
+            self.handle = None
 
 
 def sa_shadow_masks(scene: Scene, recv: Receivers, sun: Sun, method, iam_levels: int = 0,

@@ -405,6 +405,10 @@ sa_status sa_set_option(int32_t key, int32_t value) {
             if (value < 0 || value > 2) return fail(SA_ERR_INVALID_ARG, "sa_set_option: traversal mode %d", value);
             sa::set_trace_mode(key == SA_OPT_SWEEP_TRAVERSAL ? 0 : 1, value);
             return SA_OK;
+        case SA_OPT_RASTER_RUN:
+            if (value < 1 || value > 64) return fail(SA_ERR_INVALID_ARG, "sa_set_option: raster run %d", value);
+            sa::set_raster_run(value);
+            return SA_OK;
         default:
             return fail(SA_ERR_INVALID_ARG, "sa_set_option: unknown key %d", key);
     }
@@ -413,6 +417,7 @@ sa_status sa_set_option(int32_t key, int32_t value) {
 int32_t sa_get_option(int32_t key) {
     if (key == SA_OPT_SWEEP_TRAVERSAL) return sa::get_trace_mode(0);
     if (key == SA_OPT_ACCRUAL_TRAVERSAL) return sa::get_trace_mode(1);
+    if (key == SA_OPT_RASTER_RUN) return sa::get_raster_run();
     return -1;
 }
 

@@ -235,6 +235,47 @@ cudaError_t launch_height_grad(const DevScene& sc, const FootprintSet& fs, const
                                const DevRecv& rc, const DevSun& sun, float step_minutes,
                                const float* weights, float* dS_dh, double* d_S, cudaStream_t st);
 
+// batched scenarios (device-side descriptors; see sa_raster.cu)
+struct BatchInterval {
+    const StepConst* steps;
+    const BlockConst* blocks;
+    int n_blocks;
+    const unsigned* offsets;      // [n_blocks][tiles] base bins
+    const unsigned* counts;
+    const int* bins;
+    const int* base_counts;       // [R] gross of the base city (nullable)
+    long long out_base;           // offset of this interval's outputs
+};
+struct BatchVariant {
+    int tower_off, n_tower;       // triangles in the tower list
+    int rem_off, n_rem;           // ids in the removed list
+    int ix0, iy0, nx, ny;         // region in cells of the base grid
+    long long out_off;            // offset within an interval's outputs
+};
+// Base bins of every block of one interval over all tiles (device, caller frees with
+// cudaFree): offsets / counts [n_blocks][tiles], bins [total].
+cudaError_t build_bins(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                       unsigned** offsets, unsigned** counts, int** bins, cudaStream_t st);
+struct BatchLaunch {
+    DevScene base;
+    DevRecv grid;
+    const BatchInterval* intervals;
+    const BatchVariant* variants;
+    const int4* items;
+    int n_items;
+    unsigned* counter;
+    const int* removed;
+    const float4* tower_tris;
+    int* counts_out;
+    int* impact_out;
+    unsigned long long* stats;
+    int ctas;                     // persistent CTAs
+    int run;                      // raster steps per work unit
+};
+void set_raster_run(int run);
+int get_raster_run();
+cudaError_t launch_batch(const BatchLaunch& bl, cudaStream_t st);
+
 // inverse accrual map of a ground grid (h_blocks: host copy of the block constants)
 cudaError_t launch_iam(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
                        const BlockConst* h_blocks, int L, const DevOut& out, cudaStream_t st);

@@ -132,11 +132,30 @@ struct RasterArgs {
     int load_state;                  // 0: start from zero, 1: from out.gross / best / run
     int final_chunk;
     int cull;                        // closed scene: only faces toward the sun
+    int run;                         // steps per work unit
     long long R;
 };
 
 constexpr int kWarpsRaster = kRasterThreads / 32;
-constexpr int kSub = 8;                        // steps per work unit
+
+struct BatchArgs {
+    TileGeom g;
+    const float4* base_tris;
+    const BatchInterval* intervals;
+    const BatchVariant* variants;
+    const int4* items;                // (interval, variant, tile, 0)
+    int n_items;
+    unsigned* counter;                // work queue head, zeroed before the launch
+    const int* removed;               // removed base building ids of all variants
+    const float4* tower_tris;         // tower triangles of all variants (3 float4 each)
+    int* counts_out;
+    int* impact_out;                  // nullable
+    int cull;
+    int run;                          // steps per work unit
+    unsigned long long* stats;        // nullable
+};
+// steps per work unit (run length); a process-wide option, 8 by default
+int g_raster_run = 8;
 
 // Edge function of a triangle edge (3D endpoints v -> v') projected along step k, at a
 // ground point p (all xy tile-local).  With c = p - v.xy and e = v' - v,
@@ -158,36 +177,173 @@ __device__ __forceinline__ EdgeRef edge_ref(const float4& a, const float4& b) {
     return EdgeRef{v.x, v.y, v.z, w.x - v.x, w.y - v.y, w.z - v.z, keep ? 1.f : -1.f};
 }
 
-// One CTA per 32 x 32-cell tile.  Per block, the binned triangles are staged in batches
-// (xy shifted to the tile); each warp takes work units (triangle, run of <= 8 steps),
-// bounds the run's swept projection, spreads its lanes over the covered cells (8, 16 or
-// 32 columns per pass), and per cell tests the run's steps with the expanded edge
-// functions; the step bits are ORed into the tile's 64-bit masks in shared memory.
+// Shared memory of one tile: staged triangles (xy tile-local), their sun-facing step
+// masks, the block's ground slopes, the tile's 64-bit step masks and its cell centres.
+struct TileSmem {
+    float4 tri[kTriBatch * 3];
+    unsigned long long front[kTriBatch];     // steps with n . d > 0
+    unsigned long long back[kTriBatch];      // steps with n . d < 0 (open scenes only)
+    int valid[kTriBatch];
+    float2 u[kMaxBlock];
+    unsigned long long mask[kTile * kTile];
+    float xl[kTile], yl[kTile];
+};
+
+// Tile origin and cell centres in tile-local coordinates; the centres are rounded exactly
+// as the receivers' world coordinates, then shifted.
+__device__ __forceinline__ void tile_setup(TileSmem& sm, const TileGeom& g, int tx, int ty,
+                                           float* tox, float* toy) {
+    *tox = __fadd_rn(g.x0, __fmul_rn((float)(tx * kTile), g.dx));
+    *toy = __fadd_rn(g.y0, __fmul_rn((float)(ty * kTile), g.dx));
+    if (threadIdx.x < kTile) {
+        sm.xl[threadIdx.x] = __fadd_rn(g.x0, __fmul_rn(__fadd_rn((float)(tx * kTile + threadIdx.x), 0.5f), g.dx)) - *tox;
+    } else if (threadIdx.x < 2 * kTile) {
+        const int q = threadIdx.x - kTile;
+        sm.yl[q] = __fadd_rn(g.y0, __fmul_rn(__fadd_rn((float)(ty * kTile + q), 0.5f), g.dx)) - *toy;
+    }
+    for (int c = threadIdx.x; c < kTile * kTile; c += kRasterThreads) sm.mask[c] = 0ull;
+}
+
+// One block of steps of one tile: the n triangles given by fetch(i, vertex, &v) (false =
+// skip the triangle) are staged in batches; each warp takes work units (triangle, run of
+// <= 8 steps), bounds the run's swept projection, spreads its lanes over the covered cells
+// (row-major, 32 at a time) and per cell tests the run's steps with the expanded edge
+// functions; step bits are ORed into sm.mask.  Leaves sm.mask complete for the block.
+template <bool COUNT, class Fetch>
+__device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const StepConst* steps,
+                             int j0, int K, bool cull, float tox, float toy, float inv_dx,
+                             int kSub, unsigned long long& n_cell, unsigned long long& n_test) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nsub = (K + kSub - 1) / kSub;
+    __syncthreads();
+    if (threadIdx.x < K) {
+        const StepConst& s = steps[j0 + threadIdx.x];
+        sm.u[threadIdx.x] = make_float2(s.ux, s.uy);
+    }
+    for (int base = 0; base < n; base += kTriBatch) {
+        const int nt = min(kTriBatch, n - base);
+        __syncthreads();
+        if (threadIdx.x < nt * 3) {
+            float4 v;
+            const bool ok = fetch(base + threadIdx.x / 3, threadIdx.x % 3, &v);
+            v.x -= tox;
+            v.y -= toy;
+            sm.tri[threadIdx.x] = v;
+            if (threadIdx.x % 3 == 0) sm.valid[threadIdx.x / 3] = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (threadIdx.x < nt) {
+            unsigned long long fr = 0, bk = 0;
+            if (sm.valid[threadIdx.x]) {
+                const float4 a = sm.tri[3 * threadIdx.x], b = sm.tri[3 * threadIdx.x + 1], c = sm.tri[3 * threadIdx.x + 2];
+                const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+                const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+                const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+                for (int k = 0; k < K; ++k) {
+                    const StepConst& s = steps[j0 + k];
+                    const float nd = nx * s.dx + ny * s.dy + nz * s.dz;
+                    if (nd > 0.f) fr |= 1ull << k;
+                    if (nd < 0.f && !cull) bk |= 1ull << k;
+                }
+            }
+            sm.front[threadIdx.x] = fr;
+            sm.back[threadIdx.x] = bk;
+        }
+        __syncthreads();
+        const int units = nt * nsub;
+        for (int un = warp; un < units; un += kWarpsRaster) {
+            const int t = un / nsub, k0 = (un - t * nsub) * kSub;
+            const int kn = min(kSub, K - k0);
+            const unsigned long long run_bits = ((kn >= 64) ? ~0ull : ((1ull << kn) - 1ull)) << k0;
+            const unsigned long long fr = sm.front[t] & run_bits, bk = sm.back[t] & run_bits;
+            if ((fr | bk) == 0ull) continue;
+            const float4 a = sm.tri[3 * t], b = sm.tri[3 * t + 1], c = sm.tri[3 * t + 2];
+            // swept bounding box of the run's projections
+            float uxlo = 3.4e38f, uxhi = -3.4e38f, uylo = 3.4e38f, uyhi = -3.4e38f;
+            for (int k = k0; k < k0 + kn; ++k) {
+                const float2 u = sm.u[k];
+                uxlo = fminf(uxlo, u.x); uxhi = fmaxf(uxhi, u.x);
+                uylo = fminf(uylo, u.y); uyhi = fmaxf(uyhi, u.y);
+            }
+            const float az = fmaxf(a.z, 0.f), bz = fmaxf(b.z, 0.f), cz = fmaxf(c.z, 0.f);
+            const float xmin = fminf(a.x - az * uxhi, fminf(b.x - bz * uxhi, c.x - cz * uxhi));
+            const float xmax = fmaxf(a.x - az * uxlo, fmaxf(b.x - bz * uxlo, c.x - cz * uxlo));
+            const float ymin = fminf(a.y - az * uyhi, fminf(b.y - bz * uyhi, c.y - cz * uyhi));
+            const float ymax = fmaxf(a.y - az * uylo, fmaxf(b.y - bz * uylo, c.y - cz * uylo));
+            // cells whose centres (k + 0.5) dx fall in the box, with 0.01 cell of slack
+            const float fc0 = ceilf(xmin * inv_dx - 0.51f), fc1 = floorf(xmax * inv_dx - 0.49f);
+            const float fr0 = ceilf(ymin * inv_dx - 0.51f), fr1 = floorf(ymax * inv_dx - 0.49f);
+            if (fc1 < 0.f || fr1 < 0.f || fc0 > (float)(kTile - 1) || fr0 > (float)(kTile - 1) ||
+                fc0 > fc1 || fr0 > fr1) continue;
+            const int c0 = (int)fmaxf(fc0, 0.f), c1 = (int)fminf(fc1, (float)(kTile - 1));
+            const int r0 = (int)fmaxf(fr0, 0.f), r1 = (int)fminf(fr1, (float)(kTile - 1));
+            const EdgeRef E0 = edge_ref(a, b), E1 = edge_ref(b, c), E2 = edge_ref(c, a);
+            // lanes walk the box's cells in row-major order, 32 at a time; the row of
+            // cell index i is floor((i + 0.5) / width), exact in FP32 for <= 1024 cells
+            const int width = c1 - c0 + 1;
+            const int ncell = width * (r1 - r0 + 1);
+            const float inv_w = 1.f / (float)width;
+            for (int idx = lane; idx < ncell; idx += 32) {
+                if (COUNT) { ++n_cell; n_test += kn; }
+                const int rr = (int)(((float)idx + 0.5f) * inv_w);
+                const int r = r0 + rr, col = c0 + (idx - rr * width);
+                const float x = sm.xl[col];
+                const float y = sm.yl[r];
+                float P[3], QX[3], QY[3], SG[3];
+                const EdgeRef* ee[3] = {&E0, &E1, &E2};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const EdgeRef& e = *ee[q];
+                    const float cx = x - e.vx, cy = y - e.vy;
+                    P[q] = __fsub_rn(__fmul_rn(e.ex, cy), __fmul_rn(e.ey, cx));
+                    QX[q] = -fmaf(e.vz, e.ey, e.ez * cy);
+                    QY[q] = fmaf(e.vz, e.ex, e.ez * cx);
+                    SG[q] = e.s;
+                }
+                unsigned long long hit = 0;
+                for (int k = k0; k < k0 + kn; ++k) {
+                    const float2 u = sm.u[k];
+                    const float f0 = SG[0] * fmaf(QY[0], u.y, fmaf(QX[0], u.x, P[0]));
+                    const float f1 = SG[1] * fmaf(QY[1], u.y, fmaf(QX[1], u.x, P[1]));
+                    const float f2 = SG[2] * fmaf(QY[2], u.y, fmaf(QX[2], u.x, P[2]));
+                    const bool inf = f0 >= 0.f && f1 >= 0.f && f2 >= 0.f;
+                    const bool inb = f0 <= 0.f && f1 <= 0.f && f2 <= 0.f;
+                    const unsigned long long bit = 1ull << k;
+                    if ((inf && (fr & bit)) || (inb && (bk & bit))) hit |= bit;
+                }
+                if (hit) atomicOr(&sm.mask[r * kTile + col], hit);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void flush_raster_counts(unsigned long long* stats, unsigned long long n_cell,
+                                                    unsigned long long n_test) {
+    for (int o = 16; o > 0; o >>= 1) {
+        n_cell += __shfl_down_sync(0xffffffffu, n_cell, o);
+        n_test += __shfl_down_sync(0xffffffffu, n_test, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&stats[2], n_cell);
+        atomicAdd(&stats[3], n_test);
+    }
+}
+
+// One CTA per 32 x 32-cell tile, every block of the chunk in order; the gross /
+// continuous state of the thread's four cells stays in registers between blocks.
 template <bool COUNT>
 __global__ void __launch_bounds__(kRasterThreads)
 k_raster(RasterArgs ra) {
+    __shared__ TileSmem sm;
     unsigned long long n_cell = 0, n_test = 0;
-    __shared__ float4 s_tri[kTriBatch * 3];                  // xy tile-local
-    __shared__ unsigned long long s_front[kTriBatch];        // steps with n . d > 0
-    __shared__ unsigned long long s_back[kTriBatch];         // steps with n . d < 0
-    __shared__ float2 s_u[kMaxBlock];                        // ground slope per step
-    __shared__ unsigned long long s_mask[kTile * kTile];
-    __shared__ float s_xl[kTile], s_yl[kTile];
     const TileGeom& g = ra.g;
     const int tile = blockIdx.x;
     const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row0 = warp * 4;
-    // tile origin and cell centres in tile-local coordinates; the centres are rounded
-    // exactly as the receivers' world coordinates, then shifted
-    const float tox = __fadd_rn(g.x0, __fmul_rn((float)(tx * kTile), g.dx));
-    const float toy = __fadd_rn(g.y0, __fmul_rn((float)(ty * kTile), g.dx));
-    if (threadIdx.x < kTile) {
-        s_xl[threadIdx.x] = __fadd_rn(g.x0, __fmul_rn(__fadd_rn((float)(tx * kTile + threadIdx.x), 0.5f), g.dx)) - tox;
-    } else if (threadIdx.x < 2 * kTile) {
-        const int q = threadIdx.x - kTile;
-        s_yl[q] = __fadd_rn(g.y0, __fmul_rn(__fadd_rn((float)(ty * kTile + q), 0.5f), g.dx)) - toy;
-    }
+    float tox, toy;
+    tile_setup(sm, g, tx, ty, &tox, &toy);
     const int ix = tx * kTile + lane;
     long long outi[4];
     bool act[4];
@@ -204,120 +360,27 @@ k_raster(RasterArgs ra) {
             st[q].run = ra.out.run[outi[q]];
         }
     }
-    for (int c = threadIdx.x; c < kTile * kTile; c += kRasterThreads) s_mask[c] = 0ull;
     const int n_tiles = g.tiles_x * g.tiles_y;
     const bool cull = ra.cull != 0;
     const float inv_dx = 1.f / g.dx;
     for (int bl = 0; bl < ra.nbc; ++bl) {
         const BlockConst* bcp = &ra.sun.blocks[ra.b0 + bl];
-        const int j0 = bcp->j0, K = bcp->K;
-        const int nsub = (K + kSub - 1) / kSub;
         const unsigned off = ra.offsets[(size_t)bl * n_tiles + tile];
         const unsigned cnt = ra.counts[(size_t)bl * n_tiles + tile];
-        __syncthreads();
-        if (threadIdx.x < K) {
-            const StepConst& s = ra.sun.steps[j0 + threadIdx.x];
-            s_u[threadIdx.x] = make_float2(s.ux, s.uy);
-        }
-        for (unsigned base = 0; base < cnt; base += kTriBatch) {
-            const int nt = (int)min((unsigned)kTriBatch, cnt - base);
-            __syncthreads();
-            if (threadIdx.x < nt * 3) {
-                const int t = ra.bins[off + base + threadIdx.x / 3];
-                float4 v = __ldg(&ra.sc.tris[3 * t + threadIdx.x % 3]);
-                v.x -= tox;
-                v.y -= toy;
-                s_tri[threadIdx.x] = v;
-            }
-            __syncthreads();
-            if (threadIdx.x < nt) {
-                const float4 a = s_tri[3 * threadIdx.x], b = s_tri[3 * threadIdx.x + 1], c = s_tri[3 * threadIdx.x + 2];
-                const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
-                const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
-                const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
-                unsigned long long fr = 0, bk = 0;
-                for (int k = 0; k < K; ++k) {
-                    const StepConst& s = ra.sun.steps[j0 + k];
-                    const float nd = nx * s.dx + ny * s.dy + nz * s.dz;
-                    if (nd > 0.f) fr |= 1ull << k;
-                    if (nd < 0.f && !cull) bk |= 1ull << k;
-                }
-                s_front[threadIdx.x] = fr;
-                s_back[threadIdx.x] = bk;
-            }
-            __syncthreads();
-            const int units = nt * nsub;
-            for (int un = warp; un < units; un += kWarpsRaster) {
-                const int t = un / nsub, k0 = (un - t * nsub) * kSub;
-                const int kn = min(kSub, K - k0);
-                const unsigned long long run_bits = ((kn >= 64) ? ~0ull : ((1ull << kn) - 1ull)) << k0;
-                const unsigned long long fr = s_front[t] & run_bits, bk = s_back[t] & run_bits;
-                if ((fr | bk) == 0ull) continue;
-                const float4 a = s_tri[3 * t], b = s_tri[3 * t + 1], c = s_tri[3 * t + 2];
-                // swept bounding box of the run's projections (one cell of margin)
-                float uxlo = 3.4e38f, uxhi = -3.4e38f, uylo = 3.4e38f, uyhi = -3.4e38f;
-                for (int k = k0; k < k0 + kn; ++k) {
-                    const float2 u = s_u[k];
-                    uxlo = fminf(uxlo, u.x); uxhi = fmaxf(uxhi, u.x);
-                    uylo = fminf(uylo, u.y); uyhi = fmaxf(uyhi, u.y);
-                }
-                const float az = fmaxf(a.z, 0.f), bz = fmaxf(b.z, 0.f), cz = fmaxf(c.z, 0.f);
-                const float xmin = fminf(a.x - az * uxhi, fminf(b.x - bz * uxhi, c.x - cz * uxhi));
-                const float xmax = fmaxf(a.x - az * uxlo, fmaxf(b.x - bz * uxlo, c.x - cz * uxlo));
-                const float ymin = fminf(a.y - az * uyhi, fminf(b.y - bz * uyhi, c.y - cz * uyhi));
-                const float ymax = fmaxf(a.y - az * uylo, fmaxf(b.y - bz * uylo, c.y - cz * uylo));
-                // cells whose centres (k + 0.5) dx fall in the box, with 0.01 cell of slack
-                const float fc0 = ceilf(xmin * inv_dx - 0.51f), fc1 = floorf(xmax * inv_dx - 0.49f);
-                const float fr0 = ceilf(ymin * inv_dx - 0.51f), fr1 = floorf(ymax * inv_dx - 0.49f);
-                if (fc1 < 0.f || fr1 < 0.f || fc0 > (float)(kTile - 1) || fr0 > (float)(kTile - 1) ||
-                    fc0 > fc1 || fr0 > fr1) continue;
-                const int c0 = (int)fmaxf(fc0, 0.f), c1 = (int)fminf(fc1, (float)(kTile - 1));
-                const int r0 = (int)fmaxf(fr0, 0.f), r1 = (int)fminf(fr1, (float)(kTile - 1));
-                const EdgeRef E0 = edge_ref(a, b), E1 = edge_ref(b, c), E2 = edge_ref(c, a);
-                // lanes walk the box's cells in row-major order, 32 at a time; the row of
-                // cell index i is floor((i + 0.5) / width), exact in FP32 for <= 1024 cells
-                const int width = c1 - c0 + 1;
-                const int ncell = width * (r1 - r0 + 1);
-                const float inv_w = 1.f / (float)width;
-                for (int idx = lane; idx < ncell; idx += 32) {
-                    if (COUNT) { ++n_cell; n_test += kn; }
-                    const int rr = (int)(((float)idx + 0.5f) * inv_w);
-                    const int r = r0 + rr, col = c0 + (idx - rr * width);
-                    const float x = s_xl[col];
-                    const float y = s_yl[r];
-                    float P[3], QX[3], QY[3], SG[3];
-                    const EdgeRef* ee[3] = {&E0, &E1, &E2};
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const EdgeRef& e = *ee[q];
-                        const float cx = x - e.vx, cy = y - e.vy;
-                        P[q] = __fsub_rn(__fmul_rn(e.ex, cy), __fmul_rn(e.ey, cx));
-                        QX[q] = -fmaf(e.vz, e.ey, e.ez * cy);
-                        QY[q] = fmaf(e.vz, e.ex, e.ez * cx);
-                        SG[q] = e.s;
-                    }
-                    unsigned long long hit = 0;
-                    for (int k = k0; k < k0 + kn; ++k) {
-                        const float2 u = s_u[k];
-                        const float f0 = SG[0] * fmaf(QY[0], u.y, fmaf(QX[0], u.x, P[0]));
-                        const float f1 = SG[1] * fmaf(QY[1], u.y, fmaf(QX[1], u.x, P[1]));
-                        const float f2 = SG[2] * fmaf(QY[2], u.y, fmaf(QX[2], u.x, P[2]));
-                        const bool inf = f0 >= 0.f && f1 >= 0.f && f2 >= 0.f;
-                        const bool inb = f0 <= 0.f && f1 <= 0.f && f2 <= 0.f;
-                        const unsigned long long bit = 1ull << k;
-                        if ((inf && (fr & bit)) || (inb && (bk & bit))) hit |= bit;
-                    }
-                    if (hit) atomicOr(&s_mask[r * kTile + col], hit);
-                }
-            }
-        }
-        __syncthreads();
+        const int* bins = ra.bins + off;
+        const float4* tris = ra.sc.tris;
+        auto fetch = [bins, tris](int i, int v, float4* out) {
+            *out = __ldg(&tris[3 * bins[i] + v]);
+            return true;
+        };
+        raster_block<COUNT>(sm, fetch, (int)cnt, ra.sun.steps, bcp->j0, bcp->K, cull, tox, toy,
+                            inv_dx, ra.run, n_cell, n_test);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int cell = (row0 + q) * kTile + lane;
-            const unsigned long long m = s_mask[cell];
-            s_mask[cell] = 0ull;
-            stitch(st[q], m, K, bcp->new_day);
+            const unsigned long long m = sm.mask[cell];
+            sm.mask[cell] = 0ull;
+            stitch(st[q], m, bcp->K, bcp->new_day);
             if (ra.out.masks && act[q])
                 ra.out.masks[(size_t)bcp->mask_block * ra.R + outi[q]] |= m << bcp->mask_bit;
         }
@@ -330,16 +393,88 @@ k_raster(RasterArgs ra) {
         ra.out.run[outi[q]] = st[q].run;
         if (ra.final_chunk && ra.out.minutes) ra.out.minutes[outi[q]] = (float)st[q].gross * ra.out.step_minutes;
     }
-    if (COUNT) {
-        for (int o = 16; o > 0; o >>= 1) {
-            n_cell += __shfl_down_sync(0xffffffffu, n_cell, o);
-            n_test += __shfl_down_sync(0xffffffffu, n_test, o);
+    if (COUNT) flush_raster_counts(ra.out.stats, n_cell, n_test);
+}
+
+// --------------------------------------------------------------- batched scenarios
+// A persistent launch over work items (interval, variant, tile of the variant's region).
+// Each item rasters every block of its interval for one tile: the base city's binned
+// triangles minus the variant's removed buildings, plus the variant's tower triangles.
+// It writes the counts of the tile's cells inside the region and, where the base counts
+// are given, the impact (variant minus base).
+template <bool COUNT>
+__global__ void __launch_bounds__(kRasterThreads)
+k_batch(BatchArgs ba) {
+    __shared__ TileSmem sm;
+    __shared__ int s_item;
+    unsigned long long n_cell = 0, n_test = 0;
+    const TileGeom& g = ba.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int row0 = warp * 4;
+    const float inv_dx = 1.f / g.dx;
+    const int n_tiles = g.tiles_x * g.tiles_y;
+    while (true) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(ba.counter, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= ba.n_items) break;
+        const int4 it = ba.items[item];                  // interval, variant, tile
+        const BatchInterval& iv = ba.intervals[it.x];
+        const BatchVariant& var = ba.variants[it.y];
+        const int tile = it.z;
+        const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
+        float tox, toy;
+        tile_setup(sm, g, tx, ty, &tox, &toy);
+        RunState st[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st[q] = RunState{0, 0, 0};
+        const int* rem = ba.removed + var.rem_off;
+        const int n_rem = var.n_rem;
+        const float4* towers = ba.tower_tris + 3ll * var.tower_off;
+        const int n_tow = var.n_tower;
+        for (int bl = 0; bl < iv.n_blocks; ++bl) {
+            const BlockConst& bc = iv.blocks[bl];
+            const unsigned off = iv.offsets[(size_t)bl * n_tiles + tile];
+            const int cnt = (int)iv.counts[(size_t)bl * n_tiles + tile];
+            const int* bins = iv.bins + off;
+            const float4* tris = ba.base_tris;
+            auto fetch = [=](int i, int v, float4* out) {
+                if (i >= cnt) {
+                    *out = __ldg(&towers[3 * (i - cnt) + v]);
+                    return true;
+                }
+                const float4 x = __ldg(&tris[3 * bins[i] + v]);
+                *out = x;
+                if (v != 0) return true;
+                const int bid = __float_as_int(__ldg(&tris[3 * bins[i]]).w);
+                for (int q = 0; q < n_rem; ++q)
+                    if (rem[q] == bid) return false;
+                return true;
+            };
+            raster_block<COUNT>(sm, fetch, cnt + n_tow, iv.steps, bc.j0, bc.K, ba.cull != 0, tox,
+                                toy, inv_dx, ba.run, n_cell, n_test);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int cell = (row0 + q) * kTile + lane;
+                const unsigned long long m = sm.mask[cell];
+                sm.mask[cell] = 0ull;
+                stitch(st[q], m, bc.K, bc.new_day);
+            }
         }
-        if (lane == 0) {
-            atomicAdd(&ra.out.stats[2], n_cell);
-            atomicAdd(&ra.out.stats[3], n_test);
+        const int ix = tx * kTile + lane;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int iy = ty * kTile + row0 + q;
+            const int lx = ix - var.ix0, ly = iy - var.iy0;
+            if (ix >= g.nx || iy >= g.ny || lx < 0 || ly < 0 || lx >= var.nx || ly >= var.ny) continue;
+            const long long o = iv.out_base + var.out_off + (long long)ly * var.nx + lx;
+            ba.counts_out[o] = st[q].gross;
+            if (ba.impact_out && iv.base_counts)
+                ba.impact_out[o] = st[q].gross - iv.base_counts[(long long)iy * g.nx + ix];
         }
     }
+    if (COUNT) flush_raster_counts(ba.stats, n_cell, n_test);
 }
 
 }  // namespace
@@ -412,6 +547,7 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
         ra.final_chunk = (b0 + nbc >= sun.n_blocks);
         ra.R = R;
         ra.cull = sc.closed;
+        ra.run = g_raster_run;
         if (b0 == 0 && out.accumulate_into) {
             // run lengths never cross calls (calls cover whole days)
             e = cudaMemsetAsync(out.run, 0, sizeof(int) * (size_t)R, st);
@@ -518,6 +654,7 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
         ra.final_chunk = (b0 + nbc >= sun.n_blocks);
         ra.R = R;
         ra.cull = sc.closed;
+        ra.run = g_raster_run;
         if (out.stats) k_raster<true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
         else k_raster<false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
         e = cudaGetLastError();
@@ -525,6 +662,82 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
         b0 += nbc;
     }
     return cudaSuccess;
+}
+
+void set_raster_run(int run) { g_raster_run = run; }
+int get_raster_run() { return g_raster_run; }
+
+cudaError_t build_bins(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                       unsigned** offsets, unsigned** counts, int** bins, cudaStream_t st) {
+    *offsets = nullptr; *counts = nullptr; *bins = nullptr;
+    TileGeom g;
+    g.x0 = rc.x0; g.y0 = rc.y0; g.dx = rc.dx; g.nx = rc.nx; g.ny = rc.ny;
+    g.tiles_x = (rc.nx + kTile - 1) / kTile;
+    g.tiles_y = (rc.ny + kTile - 1) / kTile;
+    const size_t nc = (size_t)sun.n_blocks * g.tiles_x * g.tiles_y;
+    if (nc == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(counts, sizeof(unsigned) * nc);
+    if (e == cudaSuccess) e = cudaMalloc(offsets, sizeof(unsigned) * nc);
+    unsigned* cursor = nullptr;
+    unsigned* d_total = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync(&cursor, sizeof(unsigned) * nc, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_total, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(*counts, 0, sizeof(unsigned) * nc, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(unsigned) * nc, st);
+    unsigned total = 0;
+    const int tpb = 128;
+    dim3 grid((sc.T + tpb - 1) / tpb > 0 ? (sc.T + tpb - 1) / tpb : 1, sun.n_blocks);
+    if (e == cudaSuccess && sc.T > 0) {
+        k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, 0, g, *counts);
+        e = cudaMemcpyAsync(*offsets, *counts, sizeof(unsigned) * nc, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = exclusive_scan_u32(*offsets, (long long)nc, d_total, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    } else if (e == cudaSuccess) {
+        e = cudaMemsetAsync(*offsets, 0, sizeof(unsigned) * nc, st);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(bins, sizeof(int) * ((size_t)total + 1));
+    if (e == cudaSuccess && total > 0)
+        k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, 0, g, *offsets, cursor, *bins);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (cursor) cudaFreeAsync(cursor, st);
+    if (d_total) cudaFreeAsync(d_total, st);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        if (*counts) cudaFree(*counts);
+        if (*offsets) cudaFree(*offsets);
+        if (*bins) cudaFree(*bins);
+        *counts = nullptr; *offsets = nullptr; *bins = nullptr;
+    }
+    return e;
+}
+
+cudaError_t launch_batch(const BatchLaunch& bl, cudaStream_t st) {
+    BatchArgs ba;
+    ba.g.x0 = bl.grid.x0; ba.g.y0 = bl.grid.y0; ba.g.dx = bl.grid.dx;
+    ba.g.nx = bl.grid.nx; ba.g.ny = bl.grid.ny;
+    ba.g.tiles_x = (bl.grid.nx + kTile - 1) / kTile;
+    ba.g.tiles_y = (bl.grid.ny + kTile - 1) / kTile;
+    ba.base_tris = bl.base.tris;
+    ba.intervals = bl.intervals;
+    ba.variants = bl.variants;
+    ba.items = bl.items;
+    ba.n_items = bl.n_items;
+    ba.counter = bl.counter;
+    ba.removed = bl.removed;
+    ba.tower_tris = bl.tower_tris;
+    ba.counts_out = bl.counts_out;
+    ba.impact_out = bl.impact_out;
+    ba.cull = bl.base.closed;
+    ba.run = bl.run;
+    ba.stats = bl.stats;
+    cudaError_t e = cudaMemsetAsync(bl.counter, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    if (bl.n_items == 0) return cudaSuccess;
+    if (bl.stats) k_batch<true><<<bl.ctas, kRasterThreads, 0, st>>>(ba);
+    else k_batch<false><<<bl.ctas, kRasterThreads, 0, st>>>(ba);
+    return cudaGetLastError();
 }
 
 }  // namespace sa

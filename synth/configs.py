@@ -90,3 +90,76 @@ def district_small(seed_off: int = 6, n_buildings: int = 120, extent: float = 52
 
 BY_NAME = {"boxes16": boxes16, "district": district, "season": season, "park": park,
            "district_small": district_small}
+
+
+# ------------------------------------------------------------------ batched scenarios
+@dataclass
+class Scenarios:
+    """Development variants of a base city: each adds towers and removes the base
+    buildings whose footprints they overlap; each has a square receiver region (cells of
+    the base ground grid) around its towers; the same sun intervals apply to all."""
+    base: Workload
+    tower_tris: list          # per variant: float32 [n, 9] tower triangles (12 per tower)
+    removed: list             # per variant: int32 base building ids removed
+    regions: np.ndarray       # int32 [V, 4]: ix0, iy0, nx, ny (clipped to the grid)
+    intervals: list           # SunTable per interval
+
+    @property
+    def V(self) -> int:
+        return len(self.tower_tris)
+
+    def variant_mesh(self, v: int):
+        """Triangle soup [T, 9] and building ids of variant v (towers get ids B, B+1, ...)."""
+        m = self.base.mesh
+        keep = ~np.isin(m.tri_building, self.removed[v])
+        t9 = m.tri9()[keep]
+        tb = m.tri_building[keep]
+        tw = self.tower_tris[v]
+        tbw = self.base.city.B + np.arange(tw.shape[0], dtype=np.int32) // 12
+        return (np.concatenate([t9, tw]).astype(np.float32),
+                np.concatenate([tb, tbw]).astype(np.int32))
+
+
+def scenarios(n_variants: int = 64, days: int = 31, step: float = 1.0, base=None,
+              region_sides=(256, 512, 1024, 2048), centres=(79, 172, 266, 355),
+              t0: float = 9.0, t1: float = 17.0, seed_off: int = 4) -> Scenarios:
+    """The batched-scenario workload: base district + n_variants x U{1..5} towers (square
+    30-60 m, heights U(150, 450)) x 4 seasonal intervals (`days` days around the solstices
+    and equinoxes) x receiver regions with side log-uniform in `region_sides`."""
+    rng = np.random.default_rng(C.SEED_BASE + seed_off)
+    w = base if base is not None else district(n_facade=0)
+    g = w.ground
+    ext = g.nx * g.dx
+    fps = w.city.footprints
+    boxes = np.array([[f[:, 0].min(), f[:, 1].min(), f[:, 0].max(), f[:, 1].max()] for f in fps])
+    towers, removed, regions = [], [], []
+    for v in range(n_variants):
+        nt = int(rng.integers(1, 6))
+        fp_list, hs, rem = [], [], set()
+        cx0, cy0 = rng.uniform(0.2 * ext, 0.8 * ext, 2)
+        for _ in range(nt):
+            side = rng.uniform(30.0, 60.0)
+            cx, cy = cx0 + rng.uniform(-150, 150), cy0 + rng.uniform(-150, 150)
+            x0, y0 = g.x0 + cx - side / 2, g.y0 + cy - side / 2
+            x1, y1 = x0 + side, y0 + side
+            # no overlap with earlier towers of this variant
+            if any(not (x1 < f[0, 0] - 2 or x0 > f[1, 0] + 2 or y1 < f[0, 1] - 2 or y0 > f[2, 1] + 2)
+                   for f in fp_list):
+                continue
+            fp_list.append(C.box_footprint(x0, y0, x1, y1))
+            hs.append(rng.uniform(150.0, 450.0))
+            hit = ~((boxes[:, 2] < x0 - 1) | (boxes[:, 0] > x1 + 1) | (boxes[:, 3] < y0 - 1) |
+                    (boxes[:, 1] > y1 + 1))
+            rem |= set(np.nonzero(hit)[0].tolist())
+        tw = C.extrude(C.City(fp_list, np.asarray(hs, np.float32))).tri9()
+        towers.append(tw)
+        removed.append(np.asarray(sorted(rem), np.int32))
+        side = int(region_sides[int(rng.integers(0, len(region_sides)))])
+        mx = np.mean([f[:, 0].mean() for f in fp_list]) - g.x0
+        my = np.mean([f[:, 1].mean() for f in fp_list]) - g.y0
+        ix0 = int(np.clip(round(mx / g.dx) - side // 2, 0, max(g.nx - side, 0)))
+        iy0 = int(np.clip(round(my / g.dx) - side // 2, 0, max(g.ny - side, 0)))
+        regions.append((ix0, iy0, min(side, g.nx), min(side, g.ny)))
+    intervals = [sun_table(LAT, [((c - 1 + k) % 365) + 1 for k in range(-(days // 2), days - days // 2)],
+                           t0, t1, step) for c in centres]
+    return Scenarios(w, towers, removed, np.asarray(regions, np.int32), intervals)
