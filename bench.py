@@ -243,6 +243,9 @@ def run_gpu(args):
     # ---- end to end through the C ABI from host buffers
     e2e = end_to_end(B, w, args, dev)
 
+    # ---- batched scenarios (development variants x seasonal intervals)
+    batch = None if args.skip_batch else bench_batch(B, w, args)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -260,6 +263,7 @@ def run_gpu(args):
             "roofline_kernels": roof_all,
             "e2e": e2e,
             "gpu_launches": count_launches(scene, sun, grid, fac),
+            "batch": batch,
             "clocks": clk,
         }
         if world == 1 and not args.skip_cpu:
@@ -314,6 +318,57 @@ def roofline(B, scene, grid, fac, sun, st, ms_g, ms_f):
     head["peak_source"] = (f"152 SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz "
                            f"(sm_max_mhz, {src})")
     return head, out
+
+
+def bench_batch(B, w, args):
+    """Development variants of the district (towers added, overlapped buildings removed)
+    x 4 seasonal intervals, each variant on its own receiver region: one graph-captured
+    persistent launch (sa_batch_run) against per-scenario scene builds and accumulations."""
+    import torch
+    from synth import configs
+    sc = configs.scenarios(n_variants=args.batch_variants, days=args.batch_days, base=w)
+    st0 = sc.intervals
+    scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+    g = w.ground
+    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+    suns = [B.Sun(it.dirs, it.day_start) for it in st0]
+    units = int(sum((sc.regions[:, 2] * sc.regions[:, 3]).sum() * it.S for it in st0))
+    t0 = time.perf_counter()
+    bt = B.Batch(scene, grid, sc.tower_tris, sc.removed, sc.regions, suns, with_impact=True)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    ctas, run = bt.tune()
+    counts, impact = bt.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    e0.record()
+    for _ in range(reps):
+        bt.run(counts, impact)
+    e1.record()
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / reps
+    # per-scenario launches: build each variant's scene, accumulate each interval on its region
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for v in range(sc.V):
+        t9, tb = sc.variant_mesh(v)
+        verts = t9.reshape(-1, 3)
+        tris = np.arange(verts.shape[0], dtype=np.int32).reshape(-1, 3)
+        vs = B.Scene(verts, tris, tb, int(tb.max()) + 1, closed=True)
+        ix0, iy0, nx, ny = (int(x) for x in sc.regions[v])
+        rg = B.Receivers.ground_grid(g.x0 + ix0 * g.dx, g.y0 + iy0 * g.dx, g.dx, nx, ny)
+        for s in suns:
+            B.sa_accumulate(vs, rg, s, 1.0, "accrual_sam", want_minutes=False, want_continuous=False)
+    torch.cuda.synchronize()
+    per_ms = (time.perf_counter() - t0) * 1e3
+    return {"workload": f"{sc.V} variants x {len(st0)} intervals of {args.batch_days} days "
+                        f"(09-17 h @ 1 min) on district regions of 256..2048 cells a side",
+            "receiver_steps": units, "items": bt.n_items, "items_rastered": bt.n_affected,
+            "tuned": {"ctas": ctas, "run": run},
+            "batched_ms": batch_ms, "batched_value": units / (batch_ms * 1e-3),
+            "per_scenario_ms": per_ms, "per_scenario_value": units / (per_ms * 1e-3),
+            "speedup": per_ms / batch_ms, "batch_setup_s": setup_s, "unit": UNIT}
 
 
 def end_to_end(B, w, args, dev):
@@ -394,6 +449,9 @@ def main():
     ap.add_argument("--only-step", action="store_true",
                     help="time the headline method only (for profiler runs); prints one JSON line")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--batch-variants", type=int, default=64)
+    ap.add_argument("--batch-days", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":

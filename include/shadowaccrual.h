@@ -239,8 +239,11 @@ typedef struct {
 } sa_variants;
 typedef struct sa_batch sa_batch;
 
-/* Create a batch: the base scene's triangles are binned once per block of every interval,
- * and with with_impact = 1 the base counts of the whole grid are computed per interval.
+/* Create a batch: the base scene's triangles are binned once per block of every interval
+ * and the base counts of the whole grid are computed per interval.  A work item (interval,
+ * variant, tile) is rastered only if the shadow of a removed building or of a tower, swept
+ * over the interval's sun directions, can reach the tile; the others take the base counts
+ * (their impact is zero).  with_impact is kept for compatibility and may be 0 or 1.
  * The scene, grid and suns must outlive the batch.  Synchronises `stream`.
  * Errors: SA_ERR_INVALID_ARG (offsets, regions outside the grid, bad towers),
  * SA_ERR_UNSUPPORTED (point receivers, geometry below z = 0), SA_ERR_OOM, SA_ERR_CUDA. */
@@ -254,6 +257,7 @@ void sa_batch_destroy(sa_batch* b);
 int64_t sa_batch_output_count(const sa_batch* b);
 int64_t sa_batch_output_offset(const sa_batch* b, int32_t interval, int32_t variant);
 int32_t sa_batch_work_items(const sa_batch* b);
+int32_t sa_batch_affected_items(const sa_batch* b);
 /* Run every item: counts int32 (gross shadowed steps per receiver, dev) and, if the batch
  * has base counts and impact is non-NULL, impact int32 = variant minus base (dev).  The
  * work runs as a CUDA graph (instantiated on the first call with these output pointers)

@@ -78,6 +78,8 @@ def lib():
             L.sa_batch_output_offset.restype = i64
             L.sa_batch_work_items.argtypes = [P]
             L.sa_batch_work_items.restype = i32
+            L.sa_batch_affected_items.argtypes = [P]
+            L.sa_batch_affected_items.restype = i32
             L.sa_batch_run.argtypes = [P, P, P, P]
             L.sa_batch_tune.argtypes = [P, P, P, P]
             L.sa_batch_work_counters.argtypes = [P, P, P]
@@ -346,6 +348,7 @@ class Batch:
         self.V, self.I = V, len(suns)
         self.n_out = int(lib().sa_batch_output_count(h))
         self.n_items = int(lib().sa_batch_work_items(h))
+        self.n_affected = int(lib().sa_batch_affected_items(h))
 
     def offset(self, interval: int, variant: int) -> int:
         return int(lib().sa_batch_output_offset(self.handle, interval, variant))

@@ -28,6 +28,7 @@ struct sa_batch {
     sa::BatchVariant* d_var = nullptr;
     int4* d_items = nullptr;
     int n_items = 0;
+    int n_affected = 0;
     unsigned* d_counter = nullptr;
     int* d_removed = nullptr;
     float4* d_towers = nullptr;
@@ -42,6 +43,12 @@ struct sa_batch {
 };
 
 namespace {
+
+inline int __float_as_int_host(float f) {
+    int i;
+    memcpy(&i, &f, sizeof(i));
+    return i;
+}
 
 sa::BatchLaunch launch_of(const sa_batch* b, int* counts, int* impact, int n_items, int ctas,
                           int run, unsigned long long* stats) {
@@ -186,7 +193,7 @@ sa_status sa_batch_create(const sa_scene* base, const sa_receivers* grid, const 
         if (bins) b->owned.push_back(bins);
         bi.offsets = off; bi.counts = cnt; bi.bins = bins;
         bi.base_counts = nullptr;
-        if (e == cudaSuccess && with_impact && grid->R > 0) {
+        if (e == cudaSuccess && grid->R > 0) {
             int *bc = nullptr, *run = nullptr;
             e = cudaMalloc(&bc, sizeof(int) * (size_t)grid->R);
             if (e == cudaSuccess) b->owned.push_back(bc);
@@ -204,18 +211,84 @@ sa_status sa_batch_create(const sa_scene* base, const sa_receivers* grid, const 
         b->h_iv.push_back(bi);
     }
     if (e == cudaSuccess) e = dev_copy(b, b->h_iv.data(), b->h_iv.size(), &b->d_iv);
-    // work items: every tile of every variant's region, for every interval
+    // Boxes of what each variant changes: its removed base buildings and its towers.
+    std::vector<std::vector<float>> changed(V);     // per variant: lo.xyz hi.xyz ...
+    if (e == cudaSuccess && V > 0) {
+        std::vector<float4> bt((size_t)base->T * 3);
+        if (base->T > 0)
+            e = cudaMemcpy(bt.data(), base->bvh.tris, sizeof(float4) * bt.size(), cudaMemcpyDeviceToHost);
+        std::vector<float> bbox((size_t)std::max(base->n_buildings, 1) * 6);
+        for (size_t q = 0; q < bbox.size(); q += 6) {
+            bbox[q] = bbox[q + 1] = bbox[q + 2] = 3.4e38f;
+            bbox[q + 3] = bbox[q + 4] = bbox[q + 5] = -3.4e38f;
+        }
+        for (long long t = 0; t < base->T; ++t) {
+            const int bid = __float_as_int_host(bt[3 * t].w);
+            if (bid < 0 || bid >= base->n_buildings) continue;
+            float* bb = &bbox[6 * (size_t)bid];
+            for (int q = 0; q < 3; ++q) {
+                const float4& p = bt[3 * t + q];
+                bb[0] = std::min(bb[0], p.x); bb[1] = std::min(bb[1], p.y); bb[2] = std::min(bb[2], p.z);
+                bb[3] = std::max(bb[3], p.x); bb[4] = std::max(bb[4], p.y); bb[5] = std::max(bb[5], p.z);
+            }
+        }
+        for (int k = 0; k < V; ++k) {
+            for (int q = v->removed_off[k]; q < v->removed_off[k + 1]; ++q) {
+                const int bid = v->removed_ids[q];
+                if (bid < 0 || bid >= base->n_buildings) continue;
+                changed[k].insert(changed[k].end(), &bbox[6 * (size_t)bid], &bbox[6 * (size_t)bid] + 6);
+            }
+            for (int t = v->tower_off[k]; t < v->tower_off[k + 1]; ++t) {
+                float b6[6] = {3.4e38f, 3.4e38f, 3.4e38f, -3.4e38f, -3.4e38f, -3.4e38f};
+                for (int q = 0; q < 3; ++q)
+                    for (int c = 0; c < 3; ++c) {
+                        const float x = v->tower_tris[9 * (size_t)t + 3 * q + c];
+                        b6[c] = std::min(b6[c], x);
+                        b6[3 + c] = std::max(b6[3 + c], x);
+                    }
+                changed[k].insert(changed[k].end(), b6, b6 + 6);
+            }
+        }
+    }
+    // Work items: every tile of every variant's region, for every interval.  A tile is
+    // marked affected if the shadow of a changed box, swept over the interval's slope
+    // range, can reach it (one cell of margin); other tiles keep the base counts.
     std::vector<int4> items;
-    for (int i = 0; i < n_intervals; ++i)
+    std::vector<unsigned char> hit((size_t)tiles_x * tiles_y);
+    for (int i = 0; i < n_intervals; ++i) {
+        float uxlo = 3.4e38f, uxhi = -3.4e38f, uylo = 3.4e38f, uyhi = -3.4e38f;
+        for (const sa::StepConst& sc : intervals[i]->h_steps) {
+            uxlo = std::min(uxlo, sc.ux); uxhi = std::max(uxhi, sc.ux);
+            uylo = std::min(uylo, sc.uy); uyhi = std::max(uyhi, sc.uy);
+        }
         for (int k = 0; k < V; ++k) {
             const sa::BatchVariant& var = hv[k];
             if (var.nx == 0 || var.ny == 0) continue;
+            std::fill(hit.begin(), hit.end(), 0);
+            const std::vector<float>& ch = changed[k];
+            for (size_t q = 0; q < ch.size(); q += 6) {
+                const float zh = std::max(ch[q + 5], 0.f);
+                const double x0 = ch[q] - zh * std::max(uxhi, 0.f), x1 = ch[q + 3] - zh * std::min(uxlo, 0.f);
+                const double y0 = ch[q + 1] - zh * std::max(uyhi, 0.f), y1 = ch[q + 4] - zh * std::min(uylo, 0.f);
+                const double cell = grid->dx;
+                const int tx0 = (int)std::max(0.0, std::floor((x0 - grid->x0 - cell) / (32.0 * cell)));
+                const int tx1 = (int)std::min((double)tiles_x - 1, std::floor((x1 - grid->x0 + cell) / (32.0 * cell)));
+                const int ty0 = (int)std::max(0.0, std::floor((y0 - grid->y0 - cell) / (32.0 * cell)));
+                const int ty1 = (int)std::min((double)tiles_y - 1, std::floor((y1 - grid->y0 + cell) / (32.0 * cell)));
+                for (int ty = ty0; ty <= ty1; ++ty)
+                    for (int tx = tx0; tx <= tx1; ++tx) hit[(size_t)ty * tiles_x + tx] = 1;
+            }
             const int tx0 = var.ix0 / 32, tx1 = (var.ix0 + var.nx - 1) / 32;
             const int ty0 = var.iy0 / 32, ty1 = (var.iy0 + var.ny - 1) / 32;
             for (int ty = ty0; ty <= std::min(ty1, tiles_y - 1); ++ty)
                 for (int tx = tx0; tx <= std::min(tx1, tiles_x - 1); ++tx)
-                    items.push_back(make_int4(i, k, ty * tiles_x + tx, 0));
+                    items.push_back(make_int4(i, k, ty * tiles_x + tx, hit[(size_t)ty * tiles_x + tx]));
         }
+    }
+    // affected items first, so the persistent CTAs take the heavy work early
+    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
+    b->n_affected = 0;
+    for (const int4& it : items) b->n_affected += it.w;
     b->n_items = (int)items.size();
     if (e == cudaSuccess) e = dev_copy(b, items.data(), items.size(), &b->d_items);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
@@ -238,6 +311,7 @@ int64_t sa_batch_output_offset(const sa_batch* b, int32_t interval, int32_t vari
 }
 
 int32_t sa_batch_work_items(const sa_batch* b) { return b ? b->n_items : -1; }
+int32_t sa_batch_affected_items(const sa_batch* b) { return b ? b->n_affected : -1; }
 
 sa_status sa_batch_run(sa_batch* b, int32_t* counts, int32_t* impact, void* stream) {
     if (!b) return sa::report_error(SA_ERR_INVALID_ARG, "sa_batch_run: NULL batch");

@@ -283,10 +283,14 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
             const int width = c1 - c0 + 1;
             const int ncell = width * (r1 - r0 + 1);
             const float inv_w = 1.f / (float)width;
+            const unsigned long long can = fr | bk;       // steps this unit could set
             for (int idx = lane; idx < ncell; idx += 32) {
-                if (COUNT) { ++n_cell; n_test += kn; }
                 const int rr = (int)(((float)idx + 0.5f) * inv_w);
                 const int r = r0 + rr, col = c0 + (idx - rr * width);
+                // a cell already shadowed at every step the unit could set has nothing to
+                // gain (a stale read only skips less)
+                if ((sm.mask[r * kTile + col] & can) == can) continue;
+                if (COUNT) { ++n_cell; n_test += kn; }
                 const float x = sm.xl[col];
                 const float y = sm.yl[r];
                 float P[3], QX[3], QY[3], SG[3];
@@ -419,11 +423,24 @@ k_batch(BatchArgs ba) {
         __syncthreads();
         const int item = s_item;
         if (item >= ba.n_items) break;
-        const int4 it = ba.items[item];                  // interval, variant, tile
+        const int4 it = ba.items[item];                  // interval, variant, tile, affected
         const BatchInterval& iv = ba.intervals[it.x];
         const BatchVariant& var = ba.variants[it.y];
         const int tile = it.z;
         const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
+        if (!it.w) {
+            // neither a removed building's nor a tower's shadow can reach this tile during
+            // the interval: the variant's counts are the base counts
+            for (int c = threadIdx.x; c < kTile * kTile; c += kRasterThreads) {
+                const int ix = tx * kTile + (c & (kTile - 1)), iy = ty * kTile + c / kTile;
+                const int lx = ix - var.ix0, ly = iy - var.iy0;
+                if (ix >= g.nx || iy >= g.ny || lx < 0 || ly < 0 || lx >= var.nx || ly >= var.ny) continue;
+                const long long o = iv.out_base + var.out_off + (long long)ly * var.nx + lx;
+                ba.counts_out[o] = iv.base_counts[(long long)iy * g.nx + ix];
+                if (ba.impact_out) ba.impact_out[o] = 0;
+            }
+            continue;
+        }
         float tox, toy;
         tile_setup(sm, g, tx, ty, &tox, &toy);
         RunState st[4];
