@@ -1,0 +1,174 @@
+"""Full-size workloads in the benchmark's launch configuration (closed scene, blocks of 60
+steps, ground accrual raster and facade ray-traced accrual), checked against the FP64
+oracle on sampled receivers it can compute one by one."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import city as C
+from synth import configs
+
+from parity import assert_bits_parity, assert_counts_parity
+
+pytestmark = pytest.mark.gpu
+
+
+def _closed_scene(B, w):
+    return B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+
+
+def _grid(B, g):
+    return B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+
+
+def test_district_full_size_sampled(cuda_lib):
+    """2,000 buildings, 2048^2 ground cells + 1M facade samples, 481 steps."""
+    B = cuda_lib
+    w = configs.district()
+    scene = _closed_scene(B, w)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    rng = np.random.default_rng(11)
+    t9, tb = w.mesh.tri9(), w.mesh.tri_building
+    # ground: the accrual raster over the whole grid
+    g, _, c = B.sa_accumulate(scene, _grid(B, w.ground), sun, 1.0, "accrual_sam")
+    g, c = g.cpu().numpy(), c.cpu().numpy()
+    sel = rng.choice(w.ground.R, 1200, replace=False)
+    pos = w.ground.positions()[sel]
+    bits = oracle.shadow_bits(t9, tb, pos, None, w.sun.dirs)
+    near = oracle.near_boundary(t9, tb, pos, None, w.sun.dirs, w.sun.day_start, bits)
+    assert_counts_parity(g[sel], c[sel], bits, near, w.sun.day_start, "district ground")
+    # facades: the ray-traced accrual over all 1M points
+    fac = B.Receivers.points(w.facade_pos, w.facade_nrm)
+    fg, _, fc = B.sa_accumulate(scene, fac, sun, 1.0, "accrual_trace")
+    fg, fc = fg.cpu().numpy(), fc.cpu().numpy()
+    fsel = rng.choice(w.facade_pos.shape[0], 400, replace=False)
+    fb = oracle.shadow_bits(t9, tb, w.facade_pos[fsel], w.facade_nrm[fsel], w.sun.dirs)
+    fn = oracle.near_boundary(t9, tb, w.facade_pos[fsel], w.facade_nrm[fsel], w.sun.dirs,
+                              w.sun.day_start, fb)
+    assert_counts_parity(fg[fsel], fc[fsel], fb, fn, w.sun.day_start, "district facades")
+    # the per-step sweep agrees on the same sample
+    sg, _, _ = B.sa_accumulate(scene, fac, sun, 1.0, "sweep_trace")
+    assert_counts_parity(sg.cpu().numpy()[fsel], None, fb, fn, w.sun.day_start, "sweep facades")
+
+
+def test_season_full_size_sampled(cuda_lib):
+    """50,000 buildings (1.53M triangles), central 4096^2 cells, 92 days x 481 steps.
+    Over 44,252 steps nearly every receiver has steps within 1e-4 rad of a boundary, so
+    the grid counts are held to |difference| <= the receiver's near-boundary steps, and
+    the sampled cells, traced as points, to per-step bit parity away from boundaries."""
+    B = cuda_lib
+    w = configs.season()
+    assert w.mesh.T > 1_400_000 and w.sun.S == 92 * 481
+    scene = _closed_scene(B, w)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    g, m, c = B.sa_accumulate(scene, _grid(B, w.ground), sun, 1.0, "accrual_sam")
+    g, m = g.cpu().numpy(), m.cpu().numpy()
+    rng = np.random.default_rng(12)
+    sel = rng.choice(w.ground.R, 12, replace=False)
+    pos = w.ground.positions()[sel]
+    # Only buildings within the longest possible shadow can shadow a sample: a ray from the
+    # ground rising at >= the table's lowest elevation is above the tallest roof beyond
+    # h_max / tan(el_min) horizontally.  Keep buildings whose footprint box is within that.
+    el_min = float(np.arcsin(w.sun.dirs[:, 2].min()))
+    reach = float(w.city.heights.max()) / np.tan(el_min) + 10.0
+    boxes = np.array([[f[:, 0].min(), f[:, 1].min(), f[:, 0].max(), f[:, 1].max()]
+                      for f in w.city.footprints])
+    dx = np.maximum(0, np.maximum(boxes[:, 0][None] - pos[:, 0:1], pos[:, 0:1] - boxes[:, 2][None]))
+    dy = np.maximum(0, np.maximum(boxes[:, 1][None] - pos[:, 1:2], pos[:, 1:2] - boxes[:, 3][None]))
+    near_b = (np.hypot(dx, dy) <= reach).any(axis=0)
+    keep = near_b[w.mesh.tri_building]
+    t9, tb = w.mesh.tri9()[keep], w.mesh.tri_building[keep]
+    assert 0 < keep.sum() < w.mesh.T
+    bits = oracle.shadow_bits(t9, tb, pos, None, w.sun.dirs)
+    near = oracle.near_boundary(t9, tb, pos, None, w.sun.dirs, w.sun.day_start, bits)
+    og, _ = oracle.reduce(bits, w.sun.day_start)
+    assert np.all(np.abs(g[sel].astype(np.int64) - og) <= near.sum(axis=1)), (g[sel], og)
+    assert np.allclose(m[sel], g[sel].astype(np.float32))
+    masks = B.sa_shadow_masks(scene, B.Receivers.points(pos), sun, "accrual_trace")
+    gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start))
+    assert_bits_parity(gb, bits, near, "season points")
+
+
+def test_park_adjoint_full_size(cuda_lib):
+    """600k receivers (500 x 300 m at 0.5 m), 200 buildings, equinox 09-17 h @ 1 min.
+    The gradient is computed over the whole park; finite differences of the FP64 oracle
+    are taken on a 60 x 50-cell patch (weights 1 there, 0 elsewhere on both sides) for
+    the five buildings with the largest gradient there, receivers whose step statuses
+    change under the +-0.01 m perturbations left out (the objective jumps there)."""
+    B = cuda_lib
+    w = configs.park()
+    g = w.ground
+    assert g.R == 600_000 and w.city.B == 200 and w.sun.S == 481
+    scene = B.Scene.from_footprints(w.city.footprints, w.city.heights, w.city.band_height)
+    grid = _grid(B, g)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    full, S_full = B.sa_height_grad(scene, grid, sun, w.sun.step_minutes)
+    assert float(S_full) > 0 and torch.isfinite(full).all()
+    # patch near the park's south-west corner, where the ring's shadows fall in the morning
+    ix0, iy0, nx, ny = 20, 20, 60, 50
+    idx = ((iy0 + np.arange(ny))[:, None] * g.nx + (ix0 + np.arange(nx))[None, :]).ravel()
+    pos = g.positions()[idx]
+    bands = C.band_counts(w.city)
+
+    def mesh(hs):
+        return C.extrude(w.city, heights=hs, bands=bands)
+
+    wpatch = np.zeros(g.R, np.float32)
+    wpatch[idx] = 1.0
+    gpatch, _ = B.sa_height_grad(scene, grid, sun, w.sun.step_minutes, weights=wpatch)
+    gpatch = gpatch.cpu().numpy().astype(np.float64)
+    top = np.argsort(-np.abs(gpatch))[:5]
+    assert np.abs(gpatch[top[0]]) > 0
+    pert, jump = [], np.zeros(idx.size, bool)
+    for b in top:
+        hp, hm = w.city.heights.copy(), w.city.heights.copy()
+        hp[b] += np.float32(0.01)
+        hm[b] -= np.float32(0.01)
+        pert.append((b, hp, hm))
+        mp, mm = mesh(hp), mesh(hm)
+        jump |= (oracle.shadow_bits(mp.tri9(), mp.tri_building, pos, None, w.sun.dirs) !=
+                 oracle.shadow_bits(mm.tri9(), mm.tri_building, pos, None, w.sun.dirs)).any(axis=1)
+    keep = ~jump
+    wsub = np.zeros(g.R, np.float32)
+    wsub[idx[keep]] = 1.0
+    gsub, _ = B.sa_height_grad(scene, grid, sun, w.sun.step_minutes, weights=wsub)
+    gsub = gsub.cpu().numpy().astype(np.float64)
+    for b, hp, hm in pert:
+        mp, mm = mesh(hp), mesh(hm)
+        sp = oracle.shadow_integral(mp.tri9(), mp.tri_building, pos[keep], w.sun.dirs,
+                                    w.sun.day_start, w.sun.step_minutes)
+        sm = oracle.shadow_integral(mm.tri9(), mm.tri_building, pos[keep], w.sun.dirs,
+                                    w.sun.day_start, w.sun.step_minutes)
+        fd = (sp - sm) / (float(hp[b]) - float(hm[b]))
+        assert abs(gsub[b] - fd) <= 1e-3 * abs(fd) + 1e-6, (b, gsub[b], fd)
+
+
+def test_batched_scenarios_full_size_sampled(cuda_lib):
+    """64 variants x 1-5 towers x 4 seasonal intervals of 31 days on regions of 256..2048
+    cells: sampled receivers of three variants against the oracle on the variant mesh."""
+    B = cuda_lib
+    sc = configs.scenarios()
+    w = sc.base
+    scene = _closed_scene(B, w)
+    grid = _grid(B, w.ground)
+    suns = [B.Sun(it.dirs, it.day_start) for it in sc.intervals]
+    bt = B.Batch(scene, grid, sc.tower_tris, sc.removed, sc.regions, suns, with_impact=True)
+    counts, impact = bt.run()
+    counts, impact = counts.cpu().numpy(), impact.cpu().numpy()
+    g = w.ground
+    pos = g.positions()
+    rng = np.random.default_rng(13)
+    for v in (0, 1, 2):
+        t9, tb = sc.variant_mesh(v)
+        ix0, iy0, nx, ny = (int(x) for x in sc.regions[v])
+        loc = rng.choice(nx * ny, 6, replace=False)
+        gl = (iy0 + loc // nx) * g.nx + (ix0 + loc % nx)
+        for i in (0, 3):
+            it = sc.intervals[i]
+            bits = oracle.shadow_bits(t9, tb, pos[gl], None, it.dirs)
+            near = oracle.near_boundary(t9, tb, pos[gl], None, it.dirs, it.day_start, bits)
+            og, _ = oracle.reduce(bits, it.day_start)
+            o = bt.offset(i, v)
+            got = counts[o + loc].astype(np.int64)
+            assert np.all(np.abs(got - og) <= near.sum(axis=1)), (v, i, got, og)
