@@ -76,12 +76,17 @@ def test_season_full_size_sampled(cuda_lib):
                       for f in w.city.footprints])
     dx = np.maximum(0, np.maximum(boxes[:, 0][None] - pos[:, 0:1], pos[:, 0:1] - boxes[:, 2][None]))
     dy = np.maximum(0, np.maximum(boxes[:, 1][None] - pos[:, 1:2], pos[:, 1:2] - boxes[:, 3][None]))
-    near_b = (np.hypot(dx, dy) <= reach).any(axis=0)
-    keep = near_b[w.mesh.tri_building]
-    t9, tb = w.mesh.tri9()[keep], w.mesh.tri_building[keep]
-    assert 0 < keep.sum() < w.mesh.T
-    bits = oracle.shadow_bits(t9, tb, pos, None, w.sun.dirs)
-    near = oracle.near_boundary(t9, tb, pos, None, w.sun.dirs, w.sun.day_start, bits)
+    within = np.hypot(dx, dy) <= reach                  # [sample, building]
+    tri9_all = w.mesh.tri9()
+    bits = np.zeros((pos.shape[0], w.sun.S), np.uint8)
+    near = np.zeros_like(bits)
+    for k in range(pos.shape[0]):
+        keep = within[k][w.mesh.tri_building]
+        assert 0 < keep.sum() < w.mesh.T
+        t9, tb = tri9_all[keep], w.mesh.tri_building[keep]
+        bits[k:k + 1] = oracle.shadow_bits(t9, tb, pos[k:k + 1], None, w.sun.dirs)
+        near[k:k + 1] = oracle.near_boundary(t9, tb, pos[k:k + 1], None, w.sun.dirs,
+                                             w.sun.day_start, bits[k:k + 1])
     og, _ = oracle.reduce(bits, w.sun.day_start)
     assert np.all(np.abs(g[sel].astype(np.int64) - og) <= near.sum(axis=1)), (g[sel], og)
     assert np.allclose(m[sel], g[sel].astype(np.float32))
