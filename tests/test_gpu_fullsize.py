@@ -83,7 +83,8 @@ def test_season_full_size_sampled(cuda_lib):
     for k in range(pos.shape[0]):
         keep = within[k][w.mesh.tri_building]
         assert 0 < keep.sum() < w.mesh.T
-        t9, tb = tri9_all[keep], w.mesh.tri_building[keep]
+        t9 = tri9_all[keep]
+        tb = np.unique(w.mesh.tri_building[keep], return_inverse=True)[1].astype(np.int32)
         bits[k:k + 1] = oracle.shadow_bits(t9, tb, pos[k:k + 1], None, w.sun.dirs)
         near[k:k + 1] = oracle.near_boundary(t9, tb, pos[k:k + 1], None, w.sun.dirs,
                                              w.sun.day_start, bits[k:k + 1])
