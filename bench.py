@@ -86,6 +86,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------------ multi-rank
+def slowest_rank_ms(ms: float, dist=None, device=None) -> float:
+    """Max of the per-rank step times over all ranks (the job is as slow as its slowest
+    replica); ms itself when not distributed."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank processes its own copy of the workload."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------------ workload
 def make_workload(name: str):
     from synth import configs
@@ -217,11 +234,9 @@ def run_gpu(args):
     clk = clocks.stop()
     torch.cuda.synchronize()
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = slowest_rank_ms(ms, dist, dev)
         dist.barrier()
-    value = world * units / (ms * 1e-3)
+    value = weak_scaling_value(units, world, ms)
 
     # ---- per-step baselines and the other exact method on the same workload
     methods = {"accrual_sam": {"ms": ms, "ground_ms": ms_g, "facade_ms": ms_f,
