@@ -118,16 +118,29 @@ __global__ void k_lt_bin(DevScene sc, const StepConst* __restrict__ steps,
         }
 }
 
+// Receivers are Morton-ordered, so neighbouring lanes usually share a tile: lanes with the
+// same tile are grouped (match_any) and their leader makes one atomic for the group.
 __global__ void k_lr_bin(const float4* __restrict__ orig, long long R,
                          const RunLight* __restrict__ runs, int n_runs, bool fill,
                          unsigned* __restrict__ counts, const unsigned* __restrict__ offsets,
                          unsigned* __restrict__ cursor, int* __restrict__ bins) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
-    if (s >= R || r >= n_runs) return;
-    const int cell = recv_tile(orig[s], runs[r]);
-    if (fill) bins[offsets[cell] + atomicAdd(&cursor[cell], 1u)] = (int)s;
-    else atomicAdd(&counts[cell], 1u);
+    const int lane = threadIdx.x & 31;
+    const bool valid = s < R && r < n_runs;
+    const int cell = valid ? recv_tile(orig[s], runs[r]) : -1 - lane;   // unique when invalid
+    const unsigned peers = __match_any_sync(0xffffffffu, cell);
+    const int leader = __ffs(peers) - 1;
+    const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+    unsigned base = 0;
+    if (valid && lane == leader) {
+        if (fill) base = atomicAdd(&cursor[cell], (unsigned)__popc(peers));
+        else atomicAdd(&counts[cell], (unsigned)__popc(peers));
+    }
+    if (fill) {
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (valid) bins[offsets[cell] + base + rank] = (int)s;
+    }
 }
 
 // Plücker test, as in the ray-traced accrual (sa_trace.cu): moments of the canonically
