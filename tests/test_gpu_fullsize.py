@@ -1,6 +1,6 @@
 """Full-size workloads in the benchmark's launch configuration (closed scene, blocks of 60
-steps, ground accrual raster and facade ray-traced accrual), checked against the FP64
-oracle on sampled receivers it can compute one by one."""
+steps, the accrual maps for ground and facades), checked against the FP64 oracle on
+sampled receivers it can compute one by one."""
 import numpy as np
 import pytest
 import torch
@@ -38,10 +38,13 @@ def test_district_full_size_sampled(cuda_lib):
     bits = oracle.shadow_bits(t9, tb, pos, None, w.sun.dirs)
     near = oracle.near_boundary(t9, tb, pos, None, w.sun.dirs, w.sun.day_start, bits)
     assert_counts_parity(g[sel], c[sel], bits, near, w.sun.day_start, "district ground")
-    # facades: the ray-traced accrual over all 1M points
+    # facades: the light-space accrual map over all 1M points
     fac = B.Receivers.points(w.facade_pos, w.facade_nrm)
-    fg, _, fc = B.sa_accumulate(scene, fac, sun, 1.0, "accrual_trace")
+    fg, _, fc = B.sa_accumulate(scene, fac, sun, 1.0, "accrual_sam")
     fg, fc = fg.cpu().numpy(), fc.cpu().numpy()
+    # the ray-traced accrual is exact too and must agree everywhere, bit for bit
+    tg, _, tc = B.sa_accumulate(scene, fac, sun, 1.0, "accrual_trace")
+    assert np.array_equal(tg.cpu().numpy(), fg) and np.array_equal(tc.cpu().numpy(), fc)
     fsel = rng.choice(w.facade_pos.shape[0], 400, replace=False)
     fb = oracle.shadow_bits(t9, tb, w.facade_pos[fsel], w.facade_nrm[fsel], w.sun.dirs)
     fn = oracle.near_boundary(t9, tb, w.facade_pos[fsel], w.facade_nrm[fsel], w.sun.dirs,
