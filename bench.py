@@ -202,10 +202,16 @@ def run_gpu(args):
         if ev is not None:
             ev[2].record(stream)
 
-    def timed(method_ground, method_fac, steps, warmup):
+    def timed(method_ground, method_fac, steps, warmup, kernel_times=None):
+        """Mean ms per step (whole step, ground call, facade call).  With kernel_times (a
+        dict) the library also times each launch of its main kernels on the stream it
+        launches on, and the per-class (total ms, launches) of the timed steps land there."""
         for _ in range(warmup):
             step(method_ground, method_fac)
         torch.cuda.synchronize()
+        if kernel_times is not None:
+            B.sa_kernel_times()
+            B.sa_set_option(B.SA_OPT_KERNEL_TIMING, 1)
         tot, tg, tf = 0.0, 0.0, 0.0
         for _ in range(steps):
             flush.fill_(1.0)                     # evict L2 between timed iterations
@@ -215,6 +221,9 @@ def run_gpu(args):
             tg += ev[0].elapsed_time(ev[1])
             tf += ev[1].elapsed_time(ev[2])
             tot += ev[0].elapsed_time(ev[2])
+        if kernel_times is not None:
+            B.sa_set_option(B.SA_OPT_KERNEL_TIMING, 0)
+            kernel_times.update(B.sa_kernel_times())
         return tot / steps, tg / steps, tf / steps
 
     if args.only_step:
@@ -230,7 +239,8 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".", f"clocks_rank{rank}.csv"))
-    ms, ms_g, ms_f = timed("accrual_sam", "accrual_sam", args.steps, args.warmup)
+    ktimes = {}
+    ms, ms_g, ms_f = timed("accrual_sam", "accrual_sam", args.steps, args.warmup, ktimes)
     clk = clocks.stop()
     torch.cuda.synchronize()
     if world > 1:
@@ -253,7 +263,7 @@ def run_gpu(args):
             v["speedup_vs_sweep_trace"] = v["value"] / sweep
 
     # ---- roofline of the dominant kernel (instrumented work counters)
-    roof, roof_all = roofline(B, scene, grid, fac, sun, st, ms_g, ms_f)
+    roof, roof_all = roofline(B, scene, grid, fac, sun, ktimes, args.steps)
 
     # ---- end to end through the C ABI from host buffers
     e2e = end_to_end(B, w, args, dev)
@@ -307,34 +317,39 @@ OPS_PAIR, OPS_PTEST = 55, 15
 OPS_BOX, OPS_TRI = 12, 25
 
 
-def roofline(B, scene, grid, fac, sun, st, ms_g, ms_f):
-    """ALU rooflines of the two kernels of a step: achieved = counted algorithmic FP32 ops
-    / the kernel's CUDA-event time in the timed region; peak = 152 SMs x 128 FP32 lanes x
-    the maximum SM clock (one op per lane per clock)."""
+def roofline(B, scene, grid, fac, sun, ktimes, steps):
+    """ALU rooflines of the two hot kernels of a step: achieved = counted algorithmic FP32
+    ops per launch / the kernel's mean launch duration, both from the timed region (CUDA
+    events the library records around each launch, on its launching stream); peak = 152
+    SMs x 128 FP32 lanes x the maximum SM clock (one op per lane per clock)."""
     peaks, src = load_peaks()
     clk = peaks.get("sm_max_mhz", 2070.0) * 1e6
     peak_ops = 152 * 128 * clk
     out = {}
+
+    def entry(name, desc, ops_step, cls, work):
+        t_ms, n = ktimes.get(cls, (0.0, 0))
+        per_step = n / steps
+        launch_ms = t_ms / n
+        ops_launch = ops_step / per_step
+        ach = ops_launch / (launch_ms * 1e-3)
+        out[name] = {"bound": "alu", "kernel": desc, "achieved": ach / 1e12,
+                     "peak": peak_ops / 1e12, "unit": "Tops/s", "frac": ach / peak_ops,
+                     "traffic": None, "launches_per_step": per_step,
+                     "mean_launch_ms": launch_ms, "kernel_ms_per_step": t_ms / steps,
+                     "ops_per_launch": ops_launch, "work": work}
+
     c = B.sa_work_counters(scene, grid, sun, "accrual_sam")
-    ops_g = c[2] * OPS_CELL + c[3] * OPS_TEST
-    out["k_raster"] = {"bound": "alu", "kernel": "k_raster (ground accrual raster; the call also "
-                                                  "runs its binning kernels)",
-                       "achieved": ops_g / (ms_g * 1e-3) / 1e12, "peak": peak_ops / 1e12,
-                       "unit": "Tops/s", "frac": ops_g / (ms_g * 1e-3) / peak_ops,
-                       "traffic": None,
-                       "work": {"cell_setups": c[2], "cell_step_tests": c[3],
-                                "ops_per_setup": OPS_CELL, "ops_per_test": OPS_TEST}}
+    entry("k_raster", "k_raster (ground accrual raster)", c[2] * OPS_CELL + c[3] * OPS_TEST,
+          "raster", {"cell_setups": c[2], "cell_step_tests": c[3],
+                     "ops_per_setup": OPS_CELL, "ops_per_test": OPS_TEST})
     if fac is not None:
         c = B.sa_work_counters(scene, fac, sun, "accrual_sam")
-        ops_f = c[0] * OPS_PAIR + c[1] * OPS_PTEST
-        out["k_sam_tile"] = {"bound": "alu", "kernel": "k_sam_tile (facade light-space accrual map; "
-                                                       "the call also runs its binning kernels)",
-                             "achieved": ops_f / (ms_f * 1e-3) / 1e12, "peak": peak_ops / 1e12,
-                             "unit": "Tops/s", "frac": ops_f / (ms_f * 1e-3) / peak_ops,
-                             "traffic": None,
-                             "work": {"pair_setups": c[0], "step_tests": c[1],
-                                      "ops_per_setup": OPS_PAIR, "ops_per_test": OPS_PTEST}}
-    dom = max(out, key=lambda k: ms_f if k == "k_sam_tile" else ms_g)
+        entry("k_sam_tile", "k_sam_tile (facade light-space accrual map)",
+              c[0] * OPS_PAIR + c[1] * OPS_PTEST, "sam_points",
+              {"pair_setups": c[0], "step_tests": c[1],
+               "ops_per_setup": OPS_PAIR, "ops_per_test": OPS_PTEST})
+    dom = max(out, key=lambda k: out[k]["kernel_ms_per_step"])
     head = dict(out[dom])
     head["peak_source"] = (f"152 SMs x 128 FP32 lanes x {clk / 1e6:.0f} MHz "
                            f"(sm_max_mhz, {src})")

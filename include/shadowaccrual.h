@@ -93,12 +93,31 @@ int32_t sa_version(void);
  *   the option.
  *   SA_OPT_RASTER_RUN: steps the ground raster tests per cell set-up (1..64, default 8):
  *   longer runs amortise the set-up, shorter runs bound the swept box more tightly.
+ *   SA_OPT_KERNEL_TIMING: 1 records a CUDA event pair on the launching stream around every
+ *   launch of the main kernels (below), 0 (default) records nothing.  Launches inside a
+ *   stream capture, and those of sa_accumulate_grid_noalloc, are never timed.
  * sa_get_option returns the current value, or -1 for an unknown key. */
 #define SA_OPT_SWEEP_TRAVERSAL 1
 #define SA_OPT_ACCRUAL_TRAVERSAL 2
 #define SA_OPT_RASTER_RUN 3
+#define SA_OPT_KERNEL_TIMING 4
 sa_status sa_set_option(int32_t key, int32_t value);
 int32_t sa_get_option(int32_t key);
+
+/* Kernel classes timed under SA_OPT_KERNEL_TIMING. */
+#define SA_KERNEL_RASTER 0       /* ground accrual raster (Sec. 4) and per-step raster */
+#define SA_KERNEL_SAM_POINTS 1   /* light-space accrual map of point receivers (Sec. 4) */
+#define SA_KERNEL_ACCRUAL 2      /* ray-traced accrual */
+#define SA_KERNEL_SWEEP 3        /* per-step ray sweep (Sec. 8.1 baseline) */
+#define SA_KERNEL_IAM 4          /* inverse accrual map line drawing (Sec. 5) */
+#define SA_KERNEL_CLASSES 5
+
+/* Collect the timed launches recorded since the last collection: waits for their events,
+ * ADDS each launch's duration in milliseconds to ms[class] and 1 to launches[class]
+ * (arrays of n entries, host memory, either may be NULL; classes >= n are dropped), and
+ * empties the record.  Errors: SA_ERR_INVALID_ARG (n < 0), SA_ERR_CUDA (an event failed;
+ * the others are still added). */
+sa_status sa_kernel_times(double* ms, int64_t* launches, int32_t n);
 
 /* ---------------------------------------------------------------------------- scene
  * Build a scene from an indexed triangle mesh (Sec. 8.2: the city mesh): vertices

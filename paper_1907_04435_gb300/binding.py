@@ -88,12 +88,14 @@ def lib():
             L.sa_scene_from_footprints.argtypes = [P, P, i32, P, f32, i32, P, PP]
             L.sa_scene_set_heights.argtypes = [P, P, i32, P]
             L.sa_height_grad.argtypes = [P, P, P, f32, P, P, P, P]
+            L.sa_kernel_times.argtypes = [P, P, i32]
             for name in ("sa_scene_from_mesh", "sa_scene_info", "sa_sun_create", "sa_sun_info",
                          "sa_receivers_grid", "sa_receivers_points", "sa_accumulate",
                          "sa_shadow_masks", "sa_accumulate_grid_noalloc", "sa_work_counters",
                          "sa_scene_from_footprints", "sa_scene_set_heights", "sa_height_grad",
                          "sa_scene_declare_closed", "sa_set_option", "sa_batch_create",
-                         "sa_batch_run", "sa_batch_tune", "sa_batch_work_counters"):
+                         "sa_batch_run", "sa_batch_tune", "sa_batch_work_counters",
+                         "sa_kernel_times"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
     return _lib
@@ -292,7 +294,9 @@ def sa_work_counters(scene: Scene, recv: Receivers, sun: Sun, method, stream=Non
 
 
 SA_OPT_SWEEP_TRAVERSAL, SA_OPT_ACCRUAL_TRAVERSAL, SA_OPT_RASTER_RUN = 1, 2, 3
+SA_OPT_KERNEL_TIMING = 4
 TRAVERSAL = {"auto": 0, "packet": 1, "lane": 2}
+KERNEL_CLASSES = ("raster", "sam_points", "accrual", "sweep", "iam")
 
 
 def sa_set_option(key: int, value: int):
@@ -301,6 +305,16 @@ def sa_set_option(key: int, value: int):
 
 def sa_get_option(key: int) -> int:
     return int(lib().sa_get_option(int(key)))
+
+
+def sa_kernel_times():
+    """Launches timed since the last collection (SA_OPT_KERNEL_TIMING on): a dict from
+    kernel class to (total milliseconds, launches)."""
+    n = len(KERNEL_CLASSES)
+    ms = (ct.c_double * n)()
+    cnt = (ct.c_int64 * n)()
+    _check(lib().sa_kernel_times(ms, cnt, n))
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
 
 def sa_height_grad(scene: Scene, grid: Receivers, sun: Sun, step_minutes: float, weights=None,

@@ -429,6 +429,10 @@ sa_status sa_set_option(int32_t key, int32_t value) {
             if (value < 1 || value > 64) return fail(SA_ERR_INVALID_ARG, "sa_set_option: raster run %d", value);
             sa::set_raster_run(value);
             return SA_OK;
+        case SA_OPT_KERNEL_TIMING:
+            if (value < 0 || value > 1) return fail(SA_ERR_INVALID_ARG, "sa_set_option: kernel timing %d", value);
+            sa::set_kernel_timing(value);
+            return SA_OK;
         default:
             return fail(SA_ERR_INVALID_ARG, "sa_set_option: unknown key %d", key);
     }
@@ -438,7 +442,18 @@ int32_t sa_get_option(int32_t key) {
     if (key == SA_OPT_SWEEP_TRAVERSAL) return sa::get_trace_mode(0);
     if (key == SA_OPT_ACCRUAL_TRAVERSAL) return sa::get_trace_mode(1);
     if (key == SA_OPT_RASTER_RUN) return sa::get_raster_run();
+    if (key == SA_OPT_KERNEL_TIMING) return sa::get_kernel_timing();
     return -1;
+}
+
+sa_status sa_kernel_times(double* ms, int64_t* launches, int32_t n) {
+    if (n < 0) return fail(SA_ERR_INVALID_ARG, "sa_kernel_times: n = %d", n);
+    std::vector<long long> cnt((size_t)n, 0);
+    cudaError_t e = sa::collect_kernel_times(ms, cnt.data(), n);
+    if (launches)
+        for (int i = 0; i < n; ++i) launches[i] += (int64_t)cnt[i];
+    if (e != cudaSuccess) return cuda_fail(e, "sa_kernel_times");
+    return SA_OK;
 }
 
 sa_status sa_scene_declare_closed(sa_scene* scene, int32_t closed) {

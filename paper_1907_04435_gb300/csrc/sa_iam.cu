@@ -226,7 +226,10 @@ cudaError_t launch_iam(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
     const unsigned ctas = (unsigned)((warps + kWarps - 1) / kWarps);
     for (int b = 0; b < sun.n_blocks && e == cudaSuccess; ++b) {
         const BlockConst& bc = h_blocks[b];
-        k_iam_draw<<<ctas, 32 * kWarps, 0, st>>>(sc, g, sun.steps, bc.j0, bc.K, L, masks);
+        {
+            KernelTimer kt(KT_IAM, st);
+            k_iam_draw<<<ctas, 32 * kWarps, 0, st>>>(sc, g, sun.steps, bc.j0, bc.K, L, masks);
+        }
         k_iam_fold<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(R, bc.K, bc.new_day, bc.mask_block,
                                                                masks, out, b == 0,
                                                                b == sun.n_blocks - 1);

@@ -320,3 +320,25 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
                                     size_t bytes, int* capacity_error);
 
 }  // namespace sa
+
+namespace sa {
+
+// Per-kernel device timing: while enabled, a CUDA event pair is recorded on the launching
+// stream around each launch of the library's main kernels (not inside stream capture).
+enum KernelClass { KT_RASTER = 0, KT_SAM_POINTS = 1, KT_ACCRUAL = 2, KT_SWEEP = 3, KT_IAM = 4 };
+void set_kernel_timing(int on);
+int get_kernel_timing();
+struct KernelTimer {
+    int id;
+    cudaStream_t st;
+    void* begin;     // cudaEvent_t, or null when timing is off
+    KernelTimer(int id, cudaStream_t st);
+    ~KernelTimer();  // records the end event and queues the pair
+    KernelTimer(const KernelTimer&) = delete;
+    KernelTimer& operator=(const KernelTimer&) = delete;
+};
+// waits for the queued pairs, adds their durations and counts into ms[id] and n[id]
+// (n_classes entries), and empties the queue
+cudaError_t collect_kernel_times(double* ms, long long* n, int n_classes);
+
+}  // namespace sa

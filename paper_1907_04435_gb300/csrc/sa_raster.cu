@@ -574,8 +574,11 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
                 if (e != cudaSuccess) break;
             }
         }
-        if (out.stats) k_raster<true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
-        else k_raster<false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        {
+            KernelTimer kt(KT_RASTER, st);
+            if (out.stats) k_raster<true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+            else k_raster<false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        }
         e = cudaGetLastError();
     }
     if (counts) cudaFreeAsync(counts, st);

@@ -438,6 +438,7 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
             ta.r_off = roff; ta.r_cnt = rcn; ta.r_bins = rbins;
             ta.orig = rc.orig; ta.masks = masks; ta.stats = out.stats;
             if (tiles > 0) {
+                KernelTimer kt(KT_SAM_POINTS, st);
                 if (out.stats) k_sam_tile<true><<<tiles, kTileThreads, 0, st>>>(ta);
                 else k_sam_tile<false><<<tiles, kTileThreads, 0, st>>>(ta);
             }

@@ -531,6 +531,7 @@ cudaError_t launch_sweep_trace(const DevScene& sc, const DevRecv& rc, const DevS
     if (warps == 0) return cudaSuccess;
     const unsigned ctas = (unsigned)((warps + kWarpsPerCta - 1) / kWarpsPerCta);
     const int T = 32 * kWarpsPerCta;
+    KernelTimer kt(KT_SWEEP, st);
     if (use_lane(0, rc)) {
         if (out.stats) k_sweep_lane<true><<<ctas, T, 0, st>>>(sc, rc, sun, out);
         else k_sweep_lane<false><<<ctas, T, 0, st>>>(sc, rc, sun, out);
@@ -547,6 +548,7 @@ cudaError_t launch_accrual_trace(const DevScene& sc, const DevRecv& rc, const De
     if (warps == 0) return cudaSuccess;
     const unsigned ctas = (unsigned)((warps + kWarpsPerCta - 1) / kWarpsPerCta);
     const int T = 32 * kWarpsPerCta;
+    KernelTimer kt(KT_ACCRUAL, st);
     if (use_lane(1, rc)) {
         if (out.stats) k_accrual_lane<true><<<ctas, T, 0, st>>>(sc, rc, sun, out);
         else k_accrual_lane<false><<<ctas, T, 0, st>>>(sc, rc, sun, out);

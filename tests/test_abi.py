@@ -85,3 +85,19 @@ def test_block_partition_mirror():
     assert block_sizes([0, 5, 5, 70], 64) == [5, 33, 32]
     assert block_sizes([0, 3], 1) == [1, 1, 1]
     assert max(block_sizes([0, 1000], 64)) <= 64
+
+
+def test_options_and_kernel_timing_record_need_no_device(L):
+    from paper_1907_04435_gb300 import binding as B
+    for key, good, bad in ((B.SA_OPT_RASTER_RUN, 8, 65), (B.SA_OPT_KERNEL_TIMING, 1, 2),
+                           (B.SA_OPT_ACCRUAL_TRAVERSAL, 0, 3)):
+        old = B.sa_get_option(key)
+        B.sa_set_option(key, good)
+        assert B.sa_get_option(key) == good
+        assert L.sa_set_option(key, bad) == -1
+        B.sa_set_option(key, old)
+    assert B.sa_get_option(99) == -1
+    assert L.sa_kernel_times(None, None, -1) == -1
+    # nothing launched: the record is empty
+    t = B.sa_kernel_times()
+    assert set(t) == set(B.KERNEL_CLASSES) and all(v == (0.0, 0) for v in t.values())
