@@ -127,9 +127,11 @@ def cpu_oracle_sample(w, seconds_hint: float = 15.0, seed: int = 0):
     import oracle
     rng = np.random.default_rng(seed)
     t9, tb = w.mesh.tri9(), w.mesh.tri_building
-    # calibrate on a tiny sample, then size the sample to ~seconds_hint of work
+    # calibrate on a small sample (after a warm-up call that loads the library and starts
+    # its threads), then size the sample to ~seconds_hint of work
     pos_all = w.ground.positions() if w.ground is not None else None
-    n_g = 64
+    oracle.shadow_bits(t9, tb, pos_all[:16], None, w.sun.dirs)
+    n_g = 512
     sel = rng.choice(pos_all.shape[0], n_g, replace=False)
     t0 = time.perf_counter()
     oracle.shadow_bits(t9, tb, pos_all[sel], None, w.sun.dirs)
@@ -476,7 +478,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="district")

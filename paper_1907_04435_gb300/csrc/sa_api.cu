@@ -426,7 +426,7 @@ sa_status sa_set_option(int32_t key, int32_t value) {
             sa::set_trace_mode(key == SA_OPT_SWEEP_TRAVERSAL ? 0 : 1, value);
             return SA_OK;
         case SA_OPT_RASTER_RUN:
-            if (value < 1 || value > 64) return fail(SA_ERR_INVALID_ARG, "sa_set_option: raster run %d", value);
+            if (value < 1 || value > 32) return fail(SA_ERR_INVALID_ARG, "sa_set_option: raster run %d", value);
             sa::set_raster_run(value);
             return SA_OK;
         case SA_OPT_KERNEL_TIMING:

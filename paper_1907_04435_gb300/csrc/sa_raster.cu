@@ -167,24 +167,33 @@ int g_raster_run = 8;
 // an edge shared by two triangles gives the same value in both up to an exact negation:
 // a cell on it is covered by at least one (watertight).
 struct EdgeRef {
-    float vx, vy, vz, ex, ey, ez, s;
+    float vx, vy, vz, ex, ey, ez;   // canonical start point, and the edge vector times the
+                                    // sign of the triangle's own orientation of the edge
 };
 
+// The sign is folded into the edge vector: P, Qx and Qy are then the canonical values
+// times +-1, and since rounding to nearest is symmetric under negation every step's edge
+// value is the canonical one times +-1 exactly (zeros may change sign, which no
+// comparison below sees).
 __device__ __forceinline__ EdgeRef edge_ref(const float4& a, const float4& b) {
     const bool keep = a.x < b.x || (a.x == b.x && (a.y < b.y || (a.y == b.y && a.z < b.z)));
     const float4& v = keep ? a : b;
     const float4& w = keep ? b : a;
-    return EdgeRef{v.x, v.y, v.z, w.x - v.x, w.y - v.y, w.z - v.z, keep ? 1.f : -1.f};
+    const float s = keep ? 1.f : -1.f;
+    return EdgeRef{v.x, v.y, v.z, s * (w.x - v.x), s * (w.y - v.y), s * (w.z - v.z)};
 }
 
 // Shared memory of one tile: staged triangles (xy tile-local), their sun-facing step
-// masks, the block's ground slopes, the tile's 64-bit step masks and its cell centres.
+// masks, the block's directions, ground slopes and per-run slope boxes, the tile's 64-bit
+// step masks and its cell centres.
 struct TileSmem {
     float4 tri[kTriBatch * 3];
     unsigned long long front[kTriBatch];     // steps with n . d > 0
     unsigned long long back[kTriBatch];      // steps with n . d < 0 (open scenes only)
     int valid[kTriBatch];
     float2 u[kMaxBlock];
+    float4 d[kMaxBlock];                     // step directions
+    float4 ubox[kMaxBlock];                  // per run: (min u.x, max u.x, min u.y, max u.y)
     unsigned long long mask[kTile * kTile];
     float xl[kTile], yl[kTile];
 };
@@ -204,21 +213,62 @@ __device__ __forceinline__ void tile_setup(TileSmem& sm, const TileGeom& g, int 
     for (int c = threadIdx.x; c < kTile * kTile; c += kRasterThreads) sm.mask[c] = 0ull;
 }
 
+// The steps of one run (kn <= 32 steps from k0) that cover cell (x, y): bit k of the
+// result is step k0 + k.  CULL: closed scene, only front faces count.
+template <bool CULL>
+__device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeRef& E0,
+                                               const EdgeRef& E1, const EdgeRef& E2, float x,
+                                               float y, int k0, int kn, unsigned fr, unsigned bk) {
+    float P[3], QX[3], QY[3];
+    const EdgeRef* ee[3] = {&E0, &E1, &E2};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const EdgeRef& e = *ee[q];
+        const float cx = x - e.vx, cy = y - e.vy;
+        P[q] = __fsub_rn(__fmul_rn(e.ex, cy), __fmul_rn(e.ey, cx));
+        QX[q] = -fmaf(e.vz, e.ey, e.ez * cy);
+        QY[q] = fmaf(e.vz, e.ex, e.ez * cx);
+    }
+    unsigned hf = 0, hb = 0;
+#pragma unroll 8
+    for (int k = 0; k < kn; ++k) {
+        const float2 u = sm.u[k0 + k];
+        const float f0 = fmaf(QY[0], u.y, fmaf(QX[0], u.x, P[0]));
+        const float f1 = fmaf(QY[1], u.y, fmaf(QX[1], u.x, P[1]));
+        const float f2 = fmaf(QY[2], u.y, fmaf(QX[2], u.x, P[2]));
+        if (fminf(f0, fminf(f1, f2)) >= 0.f) hf |= 1u << k;
+        if (!CULL && fmaxf(f0, fmaxf(f1, f2)) <= 0.f) hb |= 1u << k;
+    }
+    return CULL ? (hf & fr) : ((hf & fr) | (hb & bk));
+}
+
 // One block of steps of one tile: the n triangles given by fetch(i, vertex, &v) (false =
 // skip the triangle) are staged in batches; each warp takes work units (triangle, run of
-// <= 8 steps), bounds the run's swept projection, spreads its lanes over the covered cells
-// (row-major, 32 at a time) and per cell tests the run's steps with the expanded edge
-// functions; step bits are ORed into sm.mask.  Leaves sm.mask complete for the block.
-template <bool COUNT, class Fetch>
+// <= 32 steps), bounds the run's swept projection, spreads its lanes over the covered
+// cells (row-major, 32 at a time) and per cell tests the run's steps with the expanded
+// edge functions; step bits are ORed into sm.mask.  Leaves sm.mask complete for the block.
+template <bool COUNT, bool CULL, class Fetch>
 __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const StepConst* steps,
-                             int j0, int K, bool cull, float tox, float toy, float inv_dx,
-                             int kSub, unsigned long long& n_cell, unsigned long long& n_test) {
+                             int j0, int K, float tox, float toy, float inv_dx, int kSub,
+                             unsigned long long& n_cell, unsigned long long& n_test) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nsub = (K + kSub - 1) / kSub;
     __syncthreads();
     if (threadIdx.x < K) {
         const StepConst& s = steps[j0 + threadIdx.x];
         sm.u[threadIdx.x] = make_float2(s.ux, s.uy);
+        sm.d[threadIdx.x] = make_float4(s.dx, s.dy, s.dz, 0.f);
+    }
+    __syncthreads();
+    if (threadIdx.x < nsub) {
+        const int k0 = threadIdx.x * kSub, k1 = min(k0 + kSub, K);
+        float4 b = make_float4(3.4e38f, -3.4e38f, 3.4e38f, -3.4e38f);
+        for (int k = k0; k < k1; ++k) {
+            const float2 u = sm.u[k];
+            b.x = fminf(b.x, u.x); b.y = fmaxf(b.y, u.x);
+            b.z = fminf(b.z, u.y); b.w = fmaxf(b.w, u.y);
+        }
+        sm.ubox[threadIdx.x] = b;
     }
     for (int base = 0; base < n; base += kTriBatch) {
         const int nt = min(kTriBatch, n - base);
@@ -232,39 +282,47 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
             if (threadIdx.x % 3 == 0) sm.valid[threadIdx.x / 3] = ok ? 1 : 0;
         }
         __syncthreads();
-        if (threadIdx.x < nt) {
+        // sun-facing steps of each staged triangle: a warp per triangle, a lane per step
+        for (int t = warp; t < nt; t += kWarpsRaster) {
             unsigned long long fr = 0, bk = 0;
-            if (sm.valid[threadIdx.x]) {
-                const float4 a = sm.tri[3 * threadIdx.x], b = sm.tri[3 * threadIdx.x + 1], c = sm.tri[3 * threadIdx.x + 2];
+            if (sm.valid[t]) {
+                const float4 a = sm.tri[3 * t], b = sm.tri[3 * t + 1], c = sm.tri[3 * t + 2];
                 const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
                 const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
                 const float nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
-                for (int k = 0; k < K; ++k) {
-                    const StepConst& s = steps[j0 + k];
-                    const float nd = nx * s.dx + ny * s.dy + nz * s.dz;
-                    if (nd > 0.f) fr |= 1ull << k;
-                    if (nd < 0.f && !cull) bk |= 1ull << k;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = lane + 32 * h;
+                    float nd = 0.f;
+                    if (k < K) {
+                        const float4 d = sm.d[k];
+                        nd = nx * d.x + ny * d.y + nz * d.z;
+                    }
+                    const unsigned f = __ballot_sync(0xffffffffu, nd > 0.f);
+                    const unsigned g = __ballot_sync(0xffffffffu, nd < 0.f);
+                    fr |= (unsigned long long)f << (32 * h);
+                    bk |= (unsigned long long)g << (32 * h);
                 }
+                if (CULL) bk = 0ull;
             }
-            sm.front[threadIdx.x] = fr;
-            sm.back[threadIdx.x] = bk;
+            if (lane == 0) {
+                sm.front[t] = fr;
+                sm.back[t] = bk;
+            }
         }
         __syncthreads();
         const int units = nt * nsub;
         for (int un = warp; un < units; un += kWarpsRaster) {
-            const int t = un / nsub, k0 = (un - t * nsub) * kSub;
+            const int t = un / nsub, sub = un - t * nsub, k0 = sub * kSub;
             const int kn = min(kSub, K - k0);
-            const unsigned long long run_bits = ((kn >= 64) ? ~0ull : ((1ull << kn) - 1ull)) << k0;
-            const unsigned long long fr = sm.front[t] & run_bits, bk = sm.back[t] & run_bits;
-            if ((fr | bk) == 0ull) continue;
+            const unsigned run_bits = (kn >= 32) ? 0xffffffffu : ((1u << kn) - 1u);
+            const unsigned fr = (unsigned)(sm.front[t] >> k0) & run_bits;
+            const unsigned bk = CULL ? 0u : ((unsigned)(sm.back[t] >> k0) & run_bits);
+            if ((fr | bk) == 0u) continue;
             const float4 a = sm.tri[3 * t], b = sm.tri[3 * t + 1], c = sm.tri[3 * t + 2];
             // swept bounding box of the run's projections
-            float uxlo = 3.4e38f, uxhi = -3.4e38f, uylo = 3.4e38f, uyhi = -3.4e38f;
-            for (int k = k0; k < k0 + kn; ++k) {
-                const float2 u = sm.u[k];
-                uxlo = fminf(uxlo, u.x); uxhi = fmaxf(uxhi, u.x);
-                uylo = fminf(uylo, u.y); uyhi = fmaxf(uyhi, u.y);
-            }
+            const float4 ub = sm.ubox[sub];
+            const float uxlo = ub.x, uxhi = ub.y, uylo = ub.z, uyhi = ub.w;
             const float az = fmaxf(a.z, 0.f), bz = fmaxf(b.z, 0.f), cz = fmaxf(c.z, 0.f);
             const float xmin = fminf(a.x - az * uxhi, fminf(b.x - bz * uxhi, c.x - cz * uxhi));
             const float xmax = fmaxf(a.x - az * uxlo, fmaxf(b.x - bz * uxlo, c.x - cz * uxlo));
@@ -283,7 +341,7 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
             const int width = c1 - c0 + 1;
             const int ncell = width * (r1 - r0 + 1);
             const float inv_w = 1.f / (float)width;
-            const unsigned long long can = fr | bk;       // steps this unit could set
+            const unsigned long long can = (unsigned long long)(fr | bk) << k0;
             for (int idx = lane; idx < ncell; idx += 32) {
                 const int rr = (int)(((float)idx + 0.5f) * inv_w);
                 const int r = r0 + rr, col = c0 + (idx - rr * width);
@@ -291,31 +349,8 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
                 // gain (a stale read only skips less)
                 if ((sm.mask[r * kTile + col] & can) == can) continue;
                 if (COUNT) { ++n_cell; n_test += kn; }
-                const float x = sm.xl[col];
-                const float y = sm.yl[r];
-                float P[3], QX[3], QY[3], SG[3];
-                const EdgeRef* ee[3] = {&E0, &E1, &E2};
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const EdgeRef& e = *ee[q];
-                    const float cx = x - e.vx, cy = y - e.vy;
-                    P[q] = __fsub_rn(__fmul_rn(e.ex, cy), __fmul_rn(e.ey, cx));
-                    QX[q] = -fmaf(e.vz, e.ey, e.ez * cy);
-                    QY[q] = fmaf(e.vz, e.ex, e.ez * cx);
-                    SG[q] = e.s;
-                }
-                unsigned long long hit = 0;
-                for (int k = k0; k < k0 + kn; ++k) {
-                    const float2 u = sm.u[k];
-                    const float f0 = SG[0] * fmaf(QY[0], u.y, fmaf(QX[0], u.x, P[0]));
-                    const float f1 = SG[1] * fmaf(QY[1], u.y, fmaf(QX[1], u.x, P[1]));
-                    const float f2 = SG[2] * fmaf(QY[2], u.y, fmaf(QX[2], u.x, P[2]));
-                    const bool inf = f0 >= 0.f && f1 >= 0.f && f2 >= 0.f;
-                    const bool inb = f0 <= 0.f && f1 <= 0.f && f2 <= 0.f;
-                    const unsigned long long bit = 1ull << k;
-                    if ((inf && (fr & bit)) || (inb && (bk & bit))) hit |= bit;
-                }
-                if (hit) atomicOr(&sm.mask[r * kTile + col], hit);
+                const unsigned hit = cell_steps<CULL>(sm, E0, E1, E2, sm.xl[col], sm.yl[r], k0, kn, fr, bk);
+                if (hit) atomicOr(&sm.mask[r * kTile + col], (unsigned long long)hit << k0);
             }
         }
     }
@@ -336,8 +371,8 @@ __device__ __forceinline__ void flush_raster_counts(unsigned long long* stats, u
 
 // One CTA per 32 x 32-cell tile, every block of the chunk in order; the gross /
 // continuous state of the thread's four cells stays in registers between blocks.
-template <bool COUNT>
-__global__ void __launch_bounds__(kRasterThreads)
+template <bool COUNT, bool CULL>
+__global__ void __launch_bounds__(kRasterThreads, 3)
 k_raster(RasterArgs ra) {
     __shared__ TileSmem sm;
     unsigned long long n_cell = 0, n_test = 0;
@@ -365,7 +400,6 @@ k_raster(RasterArgs ra) {
         }
     }
     const int n_tiles = g.tiles_x * g.tiles_y;
-    const bool cull = ra.cull != 0;
     const float inv_dx = 1.f / g.dx;
     for (int bl = 0; bl < ra.nbc; ++bl) {
         const BlockConst* bcp = &ra.sun.blocks[ra.b0 + bl];
@@ -377,8 +411,8 @@ k_raster(RasterArgs ra) {
             *out = __ldg(&tris[3 * bins[i] + v]);
             return true;
         };
-        raster_block<COUNT>(sm, fetch, (int)cnt, ra.sun.steps, bcp->j0, bcp->K, cull, tox, toy,
-                            inv_dx, ra.run, n_cell, n_test);
+        raster_block<COUNT, CULL>(sm, fetch, (int)cnt, ra.sun.steps, bcp->j0, bcp->K, tox, toy,
+                                  inv_dx, ra.run, n_cell, n_test);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int cell = (row0 + q) * kTile + lane;
@@ -406,7 +440,7 @@ k_raster(RasterArgs ra) {
 // triangles minus the variant's removed buildings, plus the variant's tower triangles.
 // It writes the counts of the tile's cells inside the region and, where the base counts
 // are given, the impact (variant minus base).
-template <bool COUNT>
+template <bool COUNT, bool CULL>
 __global__ void __launch_bounds__(kRasterThreads)
 k_batch(BatchArgs ba) {
     __shared__ TileSmem sm;
@@ -469,8 +503,8 @@ k_batch(BatchArgs ba) {
                     if (rem[q] == bid) return false;
                 return true;
             };
-            raster_block<COUNT>(sm, fetch, cnt + n_tow, iv.steps, bc.j0, bc.K, ba.cull != 0, tox,
-                                toy, inv_dx, ba.run, n_cell, n_test);
+            raster_block<COUNT, CULL>(sm, fetch, cnt + n_tow, iv.steps, bc.j0, bc.K, tox, toy,
+                                      inv_dx, ba.run, n_cell, n_test);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int cell = (row0 + q) * kTile + lane;
@@ -492,6 +526,16 @@ k_batch(BatchArgs ba) {
         }
     }
     if (COUNT) flush_raster_counts(ba.stats, n_cell, n_test);
+}
+
+void launch_k_raster(const RasterArgs& ra, int n_tiles, bool stats, cudaStream_t st) {
+    if (ra.cull) {
+        if (stats) k_raster<true, true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        else k_raster<false, true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+    } else {
+        if (stats) k_raster<true, false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        else k_raster<false, false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+    }
 }
 
 }  // namespace
@@ -576,8 +620,7 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
         }
         {
             KernelTimer kt(KT_RASTER, st);
-            if (out.stats) k_raster<true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
-            else k_raster<false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+            launch_k_raster(ra, n_tiles, out.stats != nullptr, st);
         }
         e = cudaGetLastError();
     }
@@ -675,8 +718,7 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
         ra.R = R;
         ra.cull = sc.closed;
         ra.run = g_raster_run;
-        if (out.stats) k_raster<true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
-        else k_raster<false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        launch_k_raster(ra, n_tiles, out.stats != nullptr, st);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         b0 += nbc;
@@ -755,8 +797,13 @@ cudaError_t launch_batch(const BatchLaunch& bl, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(bl.counter, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     if (bl.n_items == 0) return cudaSuccess;
-    if (bl.stats) k_batch<true><<<bl.ctas, kRasterThreads, 0, st>>>(ba);
-    else k_batch<false><<<bl.ctas, kRasterThreads, 0, st>>>(ba);
+    if (ba.cull) {
+        if (bl.stats) k_batch<true, true><<<bl.ctas, kRasterThreads, 0, st>>>(ba);
+        else k_batch<false, true><<<bl.ctas, kRasterThreads, 0, st>>>(ba);
+    } else {
+        if (bl.stats) k_batch<true, false><<<bl.ctas, kRasterThreads, 0, st>>>(ba);
+        else k_batch<false, false><<<bl.ctas, kRasterThreads, 0, st>>>(ba);
+    }
     return cudaGetLastError();
 }
 

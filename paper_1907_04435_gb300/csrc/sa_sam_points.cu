@@ -185,84 +185,166 @@ struct TileArgs {
     unsigned long long* stats;
 };
 
-// One CTA per light-space tile: the tile's triangles are staged in shared memory with
-// their widened light boxes and sun-facing step bits; each thread takes receivers of the
-// tile and tests them against the staged triangles for the run's steps.
+// One CTA per light-space tile.  The tile's triangles are staged in shared memory with
+// their light boxes, top heights and sun-facing step bits.  Each warp then takes 32 of the
+// tile's receivers at a time, one per lane, and runs over the staged triangles in step:
+//   - a cheap per-pair cull (the triangle is not wholly below the receiver, and the
+//     receiver's light-space point lies inside the triangle's box widened by the drift a
+//     ray of the run can make before it rises to the triangle's top);
+//   - the pairs that survive (a few in a hundred) are appended to a per-warp queue;
+//   - whenever the queue holds 32 pairs, every lane takes one and runs the exact test, so
+//     the expensive set-up is never paid by idle lanes.
+// Results are OR-ed into per-receiver masks in shared memory, then into the block masks.
+constexpr int kQueue = 64;
+
+template <bool COUNT>
+__device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int lane,
+                                            const float4* s_tri, const unsigned* s_front,
+                                            const float4* s_o, unsigned* s_m, const float (*s_d)[4],
+                                            int kn, unsigned long long& n_pair,
+                                            unsigned long long& n_test) {
+    if (lane >= n) return;
+    const unsigned e = q[lane];
+    const int who = (int)(e >> 8), t = (int)(e & 0xffu);
+    const float4 p = s_o[who];
+    const float3 o = make_float3(p.x, p.y, p.z);
+    const float4 a = s_tri[3 * t], b = s_tri[3 * t + 1], c = s_tri[3 * t + 2];
+    const unsigned want = s_front[t];
+    if (COUNT) ++n_pair;
+    PTri pt;
+    p_edge(o, a, b, pt.m[0]);
+    p_edge(o, b, c, pt.m[1]);
+    p_edge(o, c, a, pt.m[2]);
+    const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
+    const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
+    pt.nx = uy * vz - uz * vy;
+    pt.ny = uz * vx - ux * vz;
+    pt.nz = ux * vy - uy * vx;
+    pt.aon = pt.nx * (a.x - o.x) + pt.ny * (a.y - o.y) + pt.nz * (a.z - o.z);
+    unsigned m = 0;
+    for (int k = 0; k < kn; ++k) {
+        if (!((want >> k) & 1u)) continue;
+        if (COUNT) ++n_test;
+        if (p_hit(pt, s_d[k][0], s_d[k][1], s_d[k][2], p.w)) m |= 1u << k;
+    }
+    if (m) atomicOr(&s_m[who], m);
+}
+
 template <bool COUNT>
 __global__ void __launch_bounds__(kTileThreads)
 k_sam_tile(TileArgs ta) {
+    constexpr int kWarps = kTileThreads / 32;
     __shared__ float4 s_tri[kTriChunk * 3];
     __shared__ float4 s_box[kTriChunk];            // light box (amin, amax, bmin, bmax)
     __shared__ float s_ztop[kTriChunk];            // highest vertex z
     __shared__ unsigned s_front[kTriChunk];
     __shared__ float s_d[kRunMax][4];
+    __shared__ float4 s_o[kTileThreads];           // receiver origins (and t_min) of the pass
+    __shared__ unsigned s_m[kTileThreads];         // their step bits
+    __shared__ unsigned short s_q[kWarps][kQueue]; // pair queues: receiver slot << 8 | triangle
+    __shared__ unsigned char s_list[kWarps][kTriChunk];  // triangles near the warp's receivers
     unsigned long long n_pair = 0, n_test = 0;
     const int tile = blockIdx.x;
     const unsigned tcnt = ta.t_cnt[tile], rcnt = ta.r_cnt[tile];
     if (tcnt == 0 || rcnt == 0) return;
     const RunLight& rl = ta.runs[ta.tile_run[tile]];
     const int kn = rl.kn;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < kn) {
         const StepConst& s = ta.steps[rl.j0 + rl.k0 + threadIdx.x];
         s_d[threadIdx.x][0] = s.dx; s_d[threadIdx.x][1] = s.dy; s_d[threadIdx.x][2] = s.dz;
     }
     const bool cull = ta.sc.closed != 0;
+    const float inv_dz = 1.f / rl.min_dz;
+    const float drift = inv_dz * rl.max_sin * 1.0001f;
+    unsigned short* q = s_q[warp];
     for (unsigned base = 0; base < tcnt; base += kTriChunk) {
         const int nt = (int)min((unsigned)kTriChunk, tcnt - base);
         __syncthreads();
-        for (int q = threadIdx.x; q < nt; q += kTileThreads) {
-            const int t = ta.t_bins[ta.t_off[tile] + base + q];
+        for (int i = threadIdx.x; i < nt; i += kTileThreads) {
+            const int t = ta.t_bins[ta.t_off[tile] + base + i];
             const float4 a = __ldg(&ta.sc.tris[3 * t]), b = __ldg(&ta.sc.tris[3 * t + 1]),
                          c = __ldg(&ta.sc.tris[3 * t + 2]);
-            s_tri[3 * q] = a; s_tri[3 * q + 1] = b; s_tri[3 * q + 2] = c;
+            s_tri[3 * i] = a; s_tri[3 * i + 1] = b; s_tri[3 * i + 2] = c;
             float pa[3], pb[3];
             light_ab(rl, a.x, a.y, a.z, &pa[0], &pb[0]);
             light_ab(rl, b.x, b.y, b.z, &pa[1], &pb[1]);
             light_ab(rl, c.x, c.y, c.z, &pa[2], &pb[2]);
-            s_box[q] = make_float4(fminf(pa[0], fminf(pa[1], pa[2])), fmaxf(pa[0], fmaxf(pa[1], pa[2])),
+            s_box[i] = make_float4(fminf(pa[0], fminf(pa[1], pa[2])), fmaxf(pa[0], fmaxf(pa[1], pa[2])),
                                    fminf(pb[0], fminf(pb[1], pb[2])), fmaxf(pb[0], fmaxf(pb[1], pb[2])));
-            s_ztop[q] = fmaxf(a.z, fmaxf(b.z, c.z));
-            s_front[q] = run_front(a, b, c, ta.steps, rl, cull);
+            s_ztop[i] = fmaxf(a.z, fmaxf(b.z, c.z));
+            s_front[i] = run_front(a, b, c, ta.steps, rl, cull);
         }
         __syncthreads();
-        for (unsigned i = threadIdx.x; i < rcnt; i += kTileThreads) {
-            const int s = ta.r_bins[ta.r_off[tile] + i];
-            const float4 p = ta.orig[s];
-            const float3 o = make_float3(p.x, p.y, p.z);
-            float la, lb;
-            light_ab(rl, o.x, o.y, o.z, &la, &lb);
-            unsigned m = 0;
-            const unsigned full = (1u << kn) - 1u;
-            const float inv_dz = 1.f / rl.min_dz;
-            for (int q = 0; q < nt && m != full; ++q) {
-                // a ray climbs at least min_dz per metre: it can only reach this triangle
-                // within t <= (z_top - o.z) / min_dz, drifting at most t * max_sin sideways
-                const float rise = s_ztop[q] - o.z;
-                if (rise < -0.01f) continue;
-                const float mg = fmaxf(rise, 0.f) * inv_dz * rl.max_sin * 1.0001f + 0.05f;
-                const float4 bx = s_box[q];
-                if (la < bx.x - mg || la > bx.y + mg || lb < bx.z - mg || lb > bx.w + mg) continue;
-                const unsigned want = s_front[q] & ~m;
-                if (!want) continue;
-                if (COUNT) ++n_pair;
-                const float4 a = s_tri[3 * q], b = s_tri[3 * q + 1], c = s_tri[3 * q + 2];
-                PTri pt;
-                p_edge(o, a, b, pt.m[0]);
-                p_edge(o, b, c, pt.m[1]);
-                p_edge(o, c, a, pt.m[2]);
-                const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
-                const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
-                pt.nx = uy * vz - uz * vy;
-                pt.ny = uz * vx - ux * vz;
-                pt.nz = ux * vy - uy * vx;
-                pt.aon = pt.nx * (a.x - o.x) + pt.ny * (a.y - o.y) + pt.nz * (a.z - o.z);
-                for (int k = 0; k < kn; ++k) {
-                    if (!((want >> k) & 1u)) continue;
-                    if (COUNT) ++n_test;
-                    if (p_hit(pt, s_d[k][0], s_d[k][1], s_d[k][2], p.w)) m |= 1u << k;
+        // every warp runs the same number of passes, so the loop below stays warp-uniform
+        for (unsigned r0 = (unsigned)warp * 32u; r0 < rcnt; r0 += kTileThreads) {
+            const unsigned i = r0 + lane;
+            const bool live = i < rcnt;
+            const int s = live ? ta.r_bins[ta.r_off[tile] + i] : -1;
+            const float4 p = live ? ta.orig[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+            s_o[threadIdx.x] = p;
+            s_m[threadIdx.x] = 0u;
+            float la = 0.f, lb = 0.f;
+            light_ab(rl, p.x, p.y, p.z, &la, &lb);
+            // the warp's receivers' light-space box and lowest height: triangles no ray of
+            // any of them can reach are dropped for the whole warp at once
+            float wa0 = live ? la : 3.4e38f, wa1 = live ? la : -3.4e38f;
+            float wb0 = live ? lb : 3.4e38f, wb1 = live ? lb : -3.4e38f;
+            float wz = live ? p.z : 3.4e38f;
+            for (int off = 16; off > 0; off >>= 1) {
+                wa0 = fminf(wa0, __shfl_xor_sync(0xffffffffu, wa0, off));
+                wa1 = fmaxf(wa1, __shfl_xor_sync(0xffffffffu, wa1, off));
+                wb0 = fminf(wb0, __shfl_xor_sync(0xffffffffu, wb0, off));
+                wb1 = fmaxf(wb1, __shfl_xor_sync(0xffffffffu, wb1, off));
+                wz = fminf(wz, __shfl_xor_sync(0xffffffffu, wz, off));
+            }
+            int nl = 0;
+            for (int t0 = 0; t0 < nt; t0 += 32) {
+                const int t = t0 + lane;
+                bool near = false;
+                if (t < nt && s_front[t]) {
+                    const float rise = s_ztop[t] - wz;
+                    if (rise >= -0.01f) {
+                        const float mg = fmaf(fmaxf(rise, 0.f), drift, 0.05f);
+                        const float4 bx = s_box[t];
+                        near = !(wa1 < bx.x - mg || wa0 > bx.y + mg || wb1 < bx.z - mg || wb0 > bx.w + mg);
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, near);
+                if (near) s_list[warp][nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)t;
+                nl += __popc(bal);
+            }
+            int n = 0;
+            __syncwarp();
+            for (int j = 0; j < nl; ++j) {
+                const int t = s_list[warp][j];
+                bool pass = false;
+                if (live) {
+                    const float rise = s_ztop[t] - p.z;
+                    if (rise >= -0.01f) {
+                        const float mg = fmaf(fmaxf(rise, 0.f), drift, 0.05f);
+                        const float4 bx = s_box[t];
+                        pass = !(la < bx.x - mg || la > bx.y + mg || lb < bx.z - mg || lb > bx.w + mg);
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, pass);
+                if (pass) q[n + __popc(bal & ((1u << lane) - 1u))] =
+                    (unsigned short)(((unsigned)threadIdx.x << 8) | (unsigned)t);
+                n += __popc(bal);
+                if (n >= 32) {
+                    __syncwarp();
+                    drain_pairs<COUNT>(q + (n - 32), 32, lane, s_tri, s_front, s_o, s_m, s_d, kn,
+                                       n_pair, n_test);
+                    n -= 32;
+                    __syncwarp();
                 }
             }
-            if (m) atomicOr(&ta.masks[s], (unsigned long long)m << rl.k0);
+            __syncwarp();
+            drain_pairs<COUNT>(q, n, lane, s_tri, s_front, s_o, s_m, s_d, kn, n_pair, n_test);
+            __syncwarp();
+            const unsigned m = s_m[threadIdx.x];
+            if (live && m) atomicOr(&ta.masks[s], (unsigned long long)m << rl.k0);
+            __syncwarp();
         }
     }
     if (COUNT) {
@@ -270,7 +352,7 @@ k_sam_tile(TileArgs ta) {
             n_pair += __shfl_down_sync(0xffffffffu, n_pair, off);
             n_test += __shfl_down_sync(0xffffffffu, n_test, off);
         }
-        if ((threadIdx.x & 31) == 0) {
+        if (lane == 0) {
             atomicAdd(&ta.stats[0], n_pair);
             atomicAdd(&ta.stats[1], n_test);
         }
