@@ -302,10 +302,22 @@ def run_gpu(args):
 
 def count_launches(scene, sun, grid, fac):
     """Kernels of one timed step.  Ground raster, per chunk of <= 64 blocks: bin count,
-    3 scan kernels, bin fill, raster.  Facade map, per block: triangle and receiver bin
-    counts, 2 x 3 scan kernels, the two fills, the tile kernel and the fold."""
+    3 scan kernels, bin fill, raster.  Facade map, per chunk of blocks (<= 64, and bins of
+    <= 1 GiB at 4 bytes per receiver and run plus 8 per receiver and block): triangle and
+    receiver bin counts, 2 x 3 scan kernels, the two fills, the tile kernel and the fold."""
     chunks = (sun.n_blocks + 63) // 64
-    return chunks * 6 + (sun.n_blocks * 12 if fac else 0)
+    n = chunks * 6
+    if fac:
+        run = min(16, max(1, B_option_run()))
+        per_block = fac.R * (4 * ((64 + run - 1) // run) + 8)
+        fchunk = max(1, min(64, (1 << 30) // max(1, per_block)))
+        n += 12 * ((sun.n_blocks + fchunk - 1) // fchunk)
+    return n
+
+
+def B_option_run():
+    from paper_1907_04435_gb300 import binding as B
+    return B.sa_get_option(B.SA_OPT_RASTER_RUN)
 
 
 # Algorithmic FP32 operations per unit of work (the method's own work, counted by the

@@ -91,9 +91,10 @@ int32_t sa_version(void);
  *   traversal per lane, 0 the default (per lane for the sweep, warp-coherent for the
  *   accrual, the faster of the two on the district workload).  Results do not depend on
  *   the option.
- *   SA_OPT_RASTER_RUN: steps the accrual maps test per set-up (1..32, default 8; the map
- *   of point receivers takes at most 8): longer runs amortise the set-up, shorter runs
- *   bound the swept box more tightly.  Results do not depend on the option.
+ *   SA_OPT_RASTER_RUN: steps the accrual maps test per set-up (1..32, default 12, the
+ *   fastest on the district workload; the map of point receivers takes at most 16):
+ *   longer runs amortise the set-up, shorter runs bound the swept box more tightly.
+ *   Results do not depend on the option.
  *   SA_OPT_KERNEL_TIMING: 1 records a CUDA event pair on the launching stream around every
  *   launch of the main kernels (below), 0 (default) records nothing.  Launches inside a
  *   stream capture, and those of sa_accumulate_grid_noalloc, are never timed.

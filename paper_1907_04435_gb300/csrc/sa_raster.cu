@@ -154,8 +154,8 @@ struct BatchArgs {
     int run;                          // steps per work unit
     unsigned long long* stats;        // nullable
 };
-// steps per work unit (run length); a process-wide option, 8 by default
-int g_raster_run = 8;
+// steps per work unit (run length); a process-wide option, 12 by default
+int g_raster_run = 12;
 
 // Edge function of a triangle edge (3D endpoints v -> v') projected along step k, at a
 // ground point p (all xy tile-local).  With c = p - v.xy and e = v' - v,

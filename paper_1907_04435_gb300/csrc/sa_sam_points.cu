@@ -1,7 +1,7 @@
 // sa_sam_points.cu -- shadow accrual map for point receivers (facades), in light space.
 //
 // Sec. 4 renders the scene once per interval into a map on a plane orthogonal to the sun
-// direction and tests every receiver against its n slices.  Here each run of <= 8
+// direction and tests every receiver against its n slices.  Here each run of <= 16
 // consecutive steps of a block gets such a light-space map.  Coordinates are taken in a
 // basis (e1, e2) orthogonal to the run's middle direction d_m, around a reference point.
 // The map is a grid of light-space tiles:
@@ -28,7 +28,7 @@ namespace sa {
 
 namespace {
 
-constexpr int kRunMax = 8;
+constexpr int kRunMax = 16;
 constexpr int kTileThreads = 128;
 constexpr int kTriChunk = 128;
 
@@ -41,7 +41,7 @@ struct RunLight {
     int tile_base;               // first global tile index of this run
     int k0, kn;                  // steps of the run within the block
     int j0;                      // first step of the block
-    int pad;
+    int blk;                     // block within the chunk (row of the chunk's masks)
     float min_dz, max_sin;       // lowest sin(elevation), largest sin(angle to d_m) of the run
     float pad2[2];
 };
@@ -181,7 +181,8 @@ struct TileArgs {
     const unsigned* t_off; const unsigned* t_cnt; const int* t_bins;
     const unsigned* r_off; const unsigned* r_cnt; const int* r_bins;
     const float4* orig;
-    unsigned long long* masks;     // [R] block masks (sorted order)
+    unsigned long long* masks;     // [blocks of the chunk][R] block masks (sorted order)
+    long long R;
     unsigned long long* stats;
 };
 
@@ -343,7 +344,7 @@ k_sam_tile(TileArgs ta) {
             drain_pairs<COUNT>(q, n, lane, s_tri, s_front, s_o, s_m, s_d, kn, n_pair, n_test);
             __syncwarp();
             const unsigned m = s_m[threadIdx.x];
-            if (live && m) atomicOr(&ta.masks[s], (unsigned long long)m << rl.k0);
+            if (live && m) atomicOr(&ta.masks[(long long)rl.blk * ta.R + s], (unsigned long long)m << rl.k0);
             __syncwarp();
         }
     }
@@ -359,8 +360,10 @@ k_sam_tile(TileArgs ta) {
     }
 }
 
-__global__ void k_points_fold(long long R, const int* __restrict__ perm, int K, int new_day,
-                              int mask_block, unsigned long long* __restrict__ masks, DevOut out,
+// Stitch the chunk's blocks, in order, into each receiver's gross / continuous state.
+__global__ void k_points_fold(long long R, const int* __restrict__ perm,
+                              const BlockConst* __restrict__ blocks, int nbc,
+                              unsigned long long* __restrict__ masks, DevOut out,
                               int* __restrict__ run, int* __restrict__ best, int first, int last) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= R) return;
@@ -371,13 +374,15 @@ __global__ void k_points_fold(long long R, const int* __restrict__ perm, int K, 
         st.best = best[r];
         st.run = first ? 0 : run[r];
     }
-    const unsigned long long m = masks[s];
-    masks[s] = 0ull;
-    stitch(st, m, K, new_day);
+    for (int b = 0; b < nbc; ++b) {
+        const BlockConst& bc = blocks[b];
+        const unsigned long long m = masks[(long long)b * R + s];
+        stitch(st, m, bc.K, bc.new_day);
+        if (out.masks) out.masks[(long long)bc.mask_block * R + r] |= m;
+    }
     out.gross[r] = st.gross;
     best[r] = st.best;
     run[r] = st.run;
-    if (out.masks) out.masks[(long long)mask_block * R + r] |= m;
     if (last && out.minutes) out.minutes[r] = (float)st.gross * out.step_minutes;
 }
 
@@ -394,14 +399,19 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
                               const std::vector<StepConst>& h_steps, const DevOut& out,
                               cudaStream_t st) {
     const long long R = rc.R;
-    if (R == 0) return cudaSuccess;
+    if (R == 0 || h_blocks.empty()) return cudaSuccess;
     const int run_len = std::max(1, std::min(kRunMax, get_raster_run()));
     const float tile = 32.f;
+    // blocks per chunk: the receiver bins hold every receiver once per run (4 bytes), the
+    // masks 8 bytes per receiver and block; keep both within ~1 GiB and <= 64 blocks
+    const int runs_per_block = (kMaxBlock + run_len - 1) / run_len;
+    const long long per_block = (long long)R * (4ll * runs_per_block + 8ll);
+    const int chunk = (int)std::max(1ll, std::min(64ll, (1ll << 30) / std::max(1ll, per_block)));
+    const int nbc_max = std::min(chunk, (int)h_blocks.size());
     cudaError_t e = cudaSuccess;
     unsigned long long* masks = nullptr;
     int *run = nullptr, *best = nullptr;
-    e = cudaMallocAsync(&masks, sizeof(unsigned long long) * (size_t)R, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(masks, 0, sizeof(unsigned long long) * (size_t)R, st);
+    e = cudaMallocAsync(&masks, sizeof(unsigned long long) * (size_t)R * nbc_max, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&run, sizeof(int) * (size_t)R, st);
     if (e == cudaSuccess && !out.continuous) e = cudaMallocAsync(&best, sizeof(int) * (size_t)R, st);
     if (e == cudaSuccess && out.accumulate_into && !out.continuous)
@@ -412,63 +422,70 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
     const double zmax = scene_box[5], zmin_r = recv_box[2];
     std::vector<RunLight> hr;
     std::vector<int> tile_run;
-    for (int bidx = 0; bidx < (int)h_blocks.size() && e == cudaSuccess; ++bidx) {
-        const BlockConst& bc = h_blocks[bidx];
+    const int n_blocks = (int)h_blocks.size();
+    // a chunk also ends once its runs hold kMaxTiles light-space tiles
+    constexpr long long kMaxTiles = 1ll << 24;
+    for (int b0 = 0, nbc = 0; b0 < n_blocks && e == cudaSuccess; b0 += nbc) {
         hr.clear();
         tile_run.clear();
         int tiles = 0;
-        for (int k0 = 0; k0 < bc.K; k0 += run_len) {
-            RunLight rl;
-            memset(&rl, 0, sizeof(rl));
-            rl.k0 = k0;
-            rl.kn = std::min(run_len, bc.K - k0);
-            rl.j0 = bc.j0;
-            const int jm = bc.j0 + k0 + rl.kn / 2;
-            double dm[3] = {h_steps[jm].dx, h_steps[jm].dy, h_steps[jm].dz};
-            normalize3(dm);
-            double e1[3] = {dm[1], -dm[0], 0.0};          // horizontal, orthogonal to dm
-            if (e1[0] * e1[0] + e1[1] * e1[1] < 1e-12) { e1[0] = 1.0; e1[1] = 0.0; }
-            normalize3(e1);
-            double e2[3] = {dm[1] * e1[2] - dm[2] * e1[1], dm[2] * e1[0] - dm[0] * e1[2],
-                            dm[0] * e1[1] - dm[1] * e1[0]};
-            normalize3(e2);
-            double max_sin = 0.0, min_dz = 1.0;
-            for (int k = 0; k < rl.kn; ++k) {
-                const StepConst& s = h_steps[bc.j0 + k0 + k];
-                double d[3] = {s.dx, s.dy, s.dz};
-                normalize3(d);
-                const double cs = d[0] * dm[0] + d[1] * dm[1] + d[2] * dm[2];
-                max_sin = std::max(max_sin, sqrt(std::max(0.0, 1.0 - cs * cs)));
-                min_dz = std::min(min_dz, d[2]);
+        for (nbc = 0; nbc < chunk && b0 + nbc < n_blocks && (nbc == 0 || tiles < kMaxTiles); ++nbc) {
+            const int bl = nbc;
+            const BlockConst& bc = h_blocks[b0 + bl];
+            for (int k0 = 0; k0 < bc.K; k0 += run_len) {
+                RunLight rl;
+                memset(&rl, 0, sizeof(rl));
+                rl.k0 = k0;
+                rl.kn = std::min(run_len, bc.K - k0);
+                rl.j0 = bc.j0;
+                rl.blk = bl;
+                const int jm = bc.j0 + k0 + rl.kn / 2;
+                double dm[3] = {h_steps[jm].dx, h_steps[jm].dy, h_steps[jm].dz};
+                normalize3(dm);
+                double e1[3] = {dm[1], -dm[0], 0.0};          // horizontal, orthogonal to dm
+                if (e1[0] * e1[0] + e1[1] * e1[1] < 1e-12) { e1[0] = 1.0; e1[1] = 0.0; }
+                normalize3(e1);
+                double e2[3] = {dm[1] * e1[2] - dm[2] * e1[1], dm[2] * e1[0] - dm[0] * e1[2],
+                                dm[0] * e1[1] - dm[1] * e1[0]};
+                normalize3(e2);
+                double max_sin = 0.0, min_dz = 1.0;
+                for (int k = 0; k < rl.kn; ++k) {
+                    const StepConst& s = h_steps[bc.j0 + k0 + k];
+                    double d[3] = {s.dx, s.dy, s.dz};
+                    normalize3(d);
+                    const double cs = d[0] * dm[0] + d[1] * dm[1] + d[2] * dm[2];
+                    max_sin = std::max(max_sin, sqrt(std::max(0.0, 1.0 - cs * cs)));
+                    min_dz = std::min(min_dz, d[2]);
+                }
+                // a ray of the run rises at sin(elevation) >= min_dz: beyond t_max it is
+                // above every triangle, and its sideways drift in light space is <= t * max_sin
+                const double t_max = std::max(0.0, zmax - zmin_r) / std::max(min_dz, 1e-3) + 1.0;
+                rl.margin = (float)(t_max * max_sin * 1.0001 + 0.05);
+                rl.min_dz = (float)std::max(min_dz, 1e-3) * 0.9999f;
+                rl.max_sin = (float)max_sin;
+                for (int q = 0; q < 3; ++q) { rl.e1[q] = (float)e1[q]; rl.e2[q] = (float)e2[q]; rl.c[q] = (float)c[q]; }
+                // tile grid over the light-space box of the receivers
+                double amin = 1e30, amax = -1e30, bmin = 1e30, bmax = -1e30;
+                for (int corner = 0; corner < 8; ++corner) {
+                    const double x = (corner & 1 ? recv_box[3] : recv_box[0]) - c[0];
+                    const double y = (corner & 2 ? recv_box[4] : recv_box[1]) - c[1];
+                    const double z = (corner & 4 ? recv_box[5] : recv_box[2]) - c[2];
+                    const double a = e1[0] * x + e1[1] * y + e1[2] * z, b = e2[0] * x + e2[1] * y + e2[2] * z;
+                    amin = std::min(amin, a); amax = std::max(amax, a);
+                    bmin = std::min(bmin, b); bmax = std::max(bmax, b);
+                }
+                double ts = tile;
+                while ((amax - amin) / ts * (bmax - bmin) / ts > 4.0e6) ts *= 2.0;
+                rl.tile = (float)ts;
+                rl.a0 = (float)(amin - 1.0);
+                rl.b0 = (float)(bmin - 1.0);
+                rl.nta = std::max(1, (int)std::ceil((amax - amin + 2.0) / ts));
+                rl.ntb = std::max(1, (int)std::ceil((bmax - bmin + 2.0) / ts));
+                rl.tile_base = tiles;
+                tiles += rl.nta * rl.ntb;
+                for (int q = 0; q < rl.nta * rl.ntb; ++q) tile_run.push_back((int)hr.size());
+                hr.push_back(rl);
             }
-            // a ray of the run rises at sin(elevation) >= min_dz: beyond t_max it is above
-            // every triangle, and its sideways drift in light space is <= t * max_sin
-            const double t_max = std::max(0.0, zmax - zmin_r) / std::max(min_dz, 1e-3) + 1.0;
-            rl.margin = (float)(t_max * max_sin * 1.0001 + 0.05);
-            rl.min_dz = (float)std::max(min_dz, 1e-3) * 0.9999f;
-            rl.max_sin = (float)max_sin;
-            for (int q = 0; q < 3; ++q) { rl.e1[q] = (float)e1[q]; rl.e2[q] = (float)e2[q]; rl.c[q] = (float)c[q]; }
-            // tile grid over the light-space box of the receivers
-            double amin = 1e30, amax = -1e30, bmin = 1e30, bmax = -1e30;
-            for (int corner = 0; corner < 8; ++corner) {
-                const double x = (corner & 1 ? recv_box[3] : recv_box[0]) - c[0];
-                const double y = (corner & 2 ? recv_box[4] : recv_box[1]) - c[1];
-                const double z = (corner & 4 ? recv_box[5] : recv_box[2]) - c[2];
-                const double a = e1[0] * x + e1[1] * y + e1[2] * z, b = e2[0] * x + e2[1] * y + e2[2] * z;
-                amin = std::min(amin, a); amax = std::max(amax, a);
-                bmin = std::min(bmin, b); bmax = std::max(bmax, b);
-            }
-            double ts = tile;
-            while ((amax - amin) / ts * (bmax - bmin) / ts > 4.0e6) ts *= 2.0;
-            rl.tile = (float)ts;
-            rl.a0 = (float)(amin - 1.0);
-            rl.b0 = (float)(bmin - 1.0);
-            rl.nta = std::max(1, (int)std::ceil((amax - amin + 2.0) / ts));
-            rl.ntb = std::max(1, (int)std::ceil((bmax - bmin + 2.0) / ts));
-            rl.tile_base = tiles;
-            tiles += rl.nta * rl.ntb;
-            for (int q = 0; q < rl.nta * rl.ntb; ++q) tile_run.push_back((int)hr.size());
-            hr.push_back(rl);
         }
         const int n_runs = (int)hr.size();
         RunLight* d_runs = nullptr;
@@ -478,6 +495,7 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
         int *tbins = nullptr, *rbins = nullptr;
         const size_t nt = (size_t)tiles;
 #define TRYB(x) do { if (e == cudaSuccess) e = (x); } while (0)
+        TRYB(cudaMemsetAsync(masks, 0, sizeof(unsigned long long) * (size_t)R * nbc, st));
         TRYB(cudaMallocAsync(&d_runs, sizeof(RunLight) * hr.size(), st));
         TRYB(cudaMallocAsync(&d_tile_run, sizeof(int) * nt, st));
         TRYB(cudaMallocAsync(&tc, sizeof(unsigned) * nt, st));
@@ -518,15 +536,15 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
             ta.tile_run = d_tile_run;
             ta.t_off = toff; ta.t_cnt = tc; ta.t_bins = tbins;
             ta.r_off = roff; ta.r_cnt = rcn; ta.r_bins = rbins;
-            ta.orig = rc.orig; ta.masks = masks; ta.stats = out.stats;
+            ta.orig = rc.orig; ta.masks = masks; ta.R = R; ta.stats = out.stats;
             if (tiles > 0) {
                 KernelTimer kt(KT_SAM_POINTS, st);
                 if (out.stats) k_sam_tile<true><<<tiles, kTileThreads, 0, st>>>(ta);
                 else k_sam_tile<false><<<tiles, kTileThreads, 0, st>>>(ta);
             }
             k_points_fold<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(
-                R, rc.perm, bc.K, bc.new_day, bc.mask_block, masks, out, run, bestp, bidx == 0,
-                bidx == (int)h_blocks.size() - 1);
+                R, rc.perm, sun.blocks + b0, nbc, masks, out, run, bestp, b0 == 0,
+                b0 + nbc == n_blocks);
             e = cudaGetLastError();
         }
         for (void* p : {(void*)d_runs, (void*)d_tile_run, (void*)tc, (void*)toff, (void*)tcur,
