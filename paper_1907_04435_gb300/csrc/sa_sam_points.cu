@@ -198,6 +198,34 @@ struct TileArgs {
 // Results are OR-ed into per-receiver masks in shared memory, then into the block masks.
 constexpr int kQueue = 64;
 
+// Lines of a triangle's light-space projection, as unit inward normals and offsets: a point
+// x is inside iff n . x + c >= 0 for all three.  A ray of the run that meets the triangle
+// leaves the receiver's light-space point within the drift bound of the projection, so a
+// receiver more than that bound outside one line cannot be shadowed by the triangle.  A
+// projection too thin to orient passes every point (the light box still applies).
+__device__ __forceinline__ void light_edges(const float* pa, const float* pb, float4& e0,
+                                            float4& e1, float4& e2) {
+    float4* e[3] = {&e0, &e1, &e2};
+    const float ax = pa[1] - pa[0], ay = pb[1] - pb[0];
+    const float bx = pa[2] - pa[0], by = pb[2] - pb[0];
+    const float area2 = ax * by - ay * bx;
+    const float l0 = sqrtf(ax * ax + ay * ay), l1 = sqrtf(bx * bx + by * by);
+    const bool thin = !(fabsf(area2) > 1e-4f * l0 * l1);
+    const float sg = area2 > 0.f ? 1.f : -1.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = i == 2 ? 0 : i + 1;
+        const float ex = pa[j] - pa[i], ey = pb[j] - pb[i];
+        const float len = sqrtf(ex * ex + ey * ey);
+        if (thin || !(len > 1e-6f)) {
+            *e[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const float nx = -sg * ey / len, ny = sg * ex / len;
+        *e[i] = make_float4(nx, ny, -(nx * pa[i] + ny * pb[i]), 0.f);
+    }
+}
+
 template <bool COUNT>
 __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int lane,
                                             const float4* s_tri, const unsigned* s_front,
@@ -237,6 +265,7 @@ k_sam_tile(TileArgs ta) {
     constexpr int kWarps = kTileThreads / 32;
     __shared__ float4 s_tri[kTriChunk * 3];
     __shared__ float4 s_box[kTriChunk];            // light box (amin, amax, bmin, bmax)
+    __shared__ float4 s_edge[3][kTriChunk];        // light-space edge lines (nx, ny, c)
     __shared__ float s_ztop[kTriChunk];            // highest vertex z
     __shared__ unsigned s_front[kTriChunk];
     __shared__ float s_d[kRunMax][4];
@@ -273,6 +302,7 @@ k_sam_tile(TileArgs ta) {
             light_ab(rl, c.x, c.y, c.z, &pa[2], &pb[2]);
             s_box[i] = make_float4(fminf(pa[0], fminf(pa[1], pa[2])), fmaxf(pa[0], fmaxf(pa[1], pa[2])),
                                    fminf(pb[0], fminf(pb[1], pb[2])), fmaxf(pb[0], fmaxf(pb[1], pb[2])));
+            light_edges(pa, pb, s_edge[0][i], s_edge[1][i], s_edge[2][i]);
             s_ztop[i] = fmaxf(a.z, fmaxf(b.z, c.z));
             s_front[i] = run_front(a, b, c, ta.steps, rl, cull);
         }
@@ -309,6 +339,11 @@ k_sam_tile(TileArgs ta) {
                         const float mg = fmaf(fmaxf(rise, 0.f), drift, 0.05f);
                         const float4 bx = s_box[t];
                         near = !(wa1 < bx.x - mg || wa0 > bx.y + mg || wb1 < bx.z - mg || wb0 > bx.w + mg);
+#pragma unroll
+                        for (int q3 = 0; q3 < 3; ++q3) {
+                            const float4 e = s_edge[q3][t];
+                            near = near && fmaxf(e.x * wa0, e.x * wa1) + fmaxf(e.y * wb0, e.y * wb1) + e.z >= -mg;
+                        }
                     }
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, near);
@@ -326,6 +361,13 @@ k_sam_tile(TileArgs ta) {
                         const float mg = fmaf(fmaxf(rise, 0.f), drift, 0.05f);
                         const float4 bx = s_box[t];
                         pass = !(la < bx.x - mg || la > bx.y + mg || lb < bx.z - mg || lb > bx.w + mg);
+                        if (pass) {
+#pragma unroll
+                            for (int q3 = 0; q3 < 3; ++q3) {
+                                const float4 e = s_edge[q3][t];
+                                pass = pass && fmaf(e.x, la, fmaf(e.y, lb, e.z)) >= -mg;
+                            }
+                        }
                     }
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, pass);
