@@ -308,7 +308,7 @@ def count_launches(scene, sun, grid, fac):
     chunks = (sun.n_blocks + 63) // 64
     n = chunks * 6
     if fac:
-        run = min(16, max(1, B_option_run()))
+        run = min(16, max(1, B_option_run()))   # steps per light-space map
         per_block = fac.R * (4 * ((64 + run - 1) // run) + 8)
         fchunk = max(1, min(64, (1 << 30) // max(1, per_block)))
         n += 12 * ((sun.n_blocks + fchunk - 1) // fchunk)
@@ -317,7 +317,7 @@ def count_launches(scene, sun, grid, fac):
 
 def B_option_run():
     from paper_1907_04435_gb300 import binding as B
-    return B.sa_get_option(B.SA_OPT_RASTER_RUN)
+    return B.sa_get_option(B.SA_OPT_POINT_RUN)
 
 
 # Algorithmic FP32 operations per unit of work (the method's own work, counted by the

@@ -295,6 +295,7 @@ def sa_work_counters(scene: Scene, recv: Receivers, sun: Sun, method, stream=Non
 
 SA_OPT_SWEEP_TRAVERSAL, SA_OPT_ACCRUAL_TRAVERSAL, SA_OPT_RASTER_RUN = 1, 2, 3
 SA_OPT_KERNEL_TIMING = 4
+SA_OPT_POINT_RUN = 5
 TRAVERSAL = {"auto": 0, "packet": 1, "lane": 2}
 KERNEL_CLASSES = ("raster", "sam_points", "accrual", "sweep", "iam")
 

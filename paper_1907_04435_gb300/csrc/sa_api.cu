@@ -429,6 +429,10 @@ sa_status sa_set_option(int32_t key, int32_t value) {
             if (value < 1 || value > 32) return fail(SA_ERR_INVALID_ARG, "sa_set_option: raster run %d", value);
             sa::set_raster_run(value);
             return SA_OK;
+        case SA_OPT_POINT_RUN:
+            if (value < 1 || value > 16) return fail(SA_ERR_INVALID_ARG, "sa_set_option: point run %d", value);
+            sa::set_point_run(value);
+            return SA_OK;
         case SA_OPT_KERNEL_TIMING:
             if (value < 0 || value > 1) return fail(SA_ERR_INVALID_ARG, "sa_set_option: kernel timing %d", value);
             sa::set_kernel_timing(value);
@@ -443,6 +447,7 @@ int32_t sa_get_option(int32_t key) {
     if (key == SA_OPT_ACCRUAL_TRAVERSAL) return sa::get_trace_mode(1);
     if (key == SA_OPT_RASTER_RUN) return sa::get_raster_run();
     if (key == SA_OPT_KERNEL_TIMING) return sa::get_kernel_timing();
+    if (key == SA_OPT_POINT_RUN) return sa::get_point_run();
     return -1;
 }
 

@@ -276,6 +276,9 @@ struct BatchLaunch {
 };
 void set_raster_run(int run);
 int get_raster_run();
+// steps per light-space map of point receivers (1..16)
+void set_point_run(int run);
+int get_point_run();
 cudaError_t launch_batch(const BatchLaunch& bl, cudaStream_t st);
 
 // shadow accrual map of point receivers in light space (scene_box, recv_box: lo.xyz hi.xyz)

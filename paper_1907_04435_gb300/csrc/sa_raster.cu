@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kTile = 32;               // cells per tile side
 constexpr int kRasterThreads = 256;     // 8 warps x 4 rows each
-constexpr int kTriBatch = 32;           // triangles staged per batch
+constexpr int kTriBatch = 64;           // triangles staged per batch
 
 struct TileGeom {
     float x0, y0, dx;
@@ -154,8 +154,8 @@ struct BatchArgs {
     int run;                          // steps per work unit
     unsigned long long* stats;        // nullable
 };
-// steps per work unit (run length); a process-wide option, 12 by default
-int g_raster_run = 12;
+// steps per work unit (run length); a process-wide option, 24 by default
+int g_raster_run = 24;
 
 // Edge function of a triangle edge (3D endpoints v -> v') projected along step k, at a
 // ground point p (all xy tile-local).  With c = p - v.xy and e = v' - v,
@@ -336,15 +336,73 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
             const int c0 = (int)fmaxf(fc0, 0.f), c1 = (int)fminf(fc1, (float)(kTile - 1));
             const int r0 = (int)fmaxf(fr0, 0.f), r1 = (int)fminf(fr1, (float)(kTile - 1));
             const EdgeRef E0 = edge_ref(a, b), E1 = edge_ref(b, c), E2 = edge_ref(c, a);
-            // lanes walk the box's cells in row-major order, 32 at a time; the row of
-            // cell index i is floor((i + 0.5) / width), exact in FP32 for <= 1024 cells
-            const int width = c1 - c0 + 1;
-            const int ncell = width * (r1 - r0 + 1);
-            const float inv_w = 1.f / (float)width;
+            // Row spans.  Each step's projection lies inside the projection for the run's
+            // middle slope u_m widened by (sx, sy) = z_max |u_hi - u_lo| / 2 (a vertex at
+            // height z moves by z (u_m - u_k)).  Lane j takes row r0 + j: the x-range of the
+            // middle projection over the band [y - sy, y + sy], widened by sx, bounds the
+            // row's covered cells (0.05 cell and 2 mm of slack absorb rounding).
             const unsigned long long can = (unsigned long long)(fr | bk) << k0;
-            for (int idx = lane; idx < ncell; idx += 32) {
-                const int rr = (int)(((float)idx + 0.5f) * inv_w);
-                const int r = r0 + rr, col = c0 + (idx - rr * width);
+            const float umx = 0.5f * (uxlo + uxhi), umy = 0.5f * (uylo + uyhi);
+            const float zm = fmaxf(az, fmaxf(bz, cz));
+            const float slack = 0.05f + 2e-3f * inv_dx;                 // in cells
+            const float sx = zm * (uxhi - uxlo) * 0.5f, sy = zm * (uyhi - uylo) * 0.5f;
+            const float px[3] = {a.x - az * umx, b.x - bz * umx, c.x - cz * umx};
+            const float py[3] = {a.y - az * umy, b.y - bz * umy, c.y - cz * umy};
+            int cs = 0, w = 0;
+            if (r0 + lane <= r1) {
+                const float y = sm.yl[r0 + lane];
+                const float band = sy + slack / inv_dx;
+                const float ya = y - band, yb = y + band;
+                float lo = 3.4e38f, hi = -3.4e38f;
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    if (py[v] >= ya && py[v] <= yb) { lo = fminf(lo, px[v]); hi = fmaxf(hi, px[v]); }
+                    const int q = v == 2 ? 0 : v + 1;
+                    const float dy = py[q] - py[v];
+                    if (dy != 0.f) {
+                        const float slope = (px[q] - px[v]) / dy;
+                        const float e0 = fminf(py[v], py[q]), e1 = fmaxf(py[v], py[q]);
+                        if (ya >= e0 && ya <= e1) {
+                            const float x = fmaf(ya - py[v], slope, px[v]);
+                            lo = fminf(lo, x); hi = fmaxf(hi, x);
+                        }
+                        if (yb >= e0 && yb <= e1) {
+                            const float x = fmaf(yb - py[v], slope, px[v]);
+                            lo = fminf(lo, x); hi = fmaxf(hi, x);
+                        }
+                    }
+                }
+                if (lo <= hi) {
+                    const float f0 = fmaxf(ceilf((lo - sx) * inv_dx - 0.5f - slack), (float)c0);
+                    const float f1 = fminf(floorf((hi + sx) * inv_dx - 0.5f + slack), (float)c1);
+                    if (f0 <= f1) {
+                        cs = (int)f0;
+                        w = (int)f1 - cs + 1;
+                    }
+                }
+            }
+            // lanes walk the spans' cells, 32 at a time; a binary search over the rows'
+            // inclusive prefix sums finds each cell's row
+            int incl = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            const int excl = incl - w;
+            for (int base = 0; base < total; base += 32) {
+                const int idx = base + lane;
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+                    if (v <= idx) j += step;
+                }
+                const int ex = __shfl_sync(0xffffffffu, excl, j & 31);
+                const int cj = __shfl_sync(0xffffffffu, cs, j & 31);
+                if (idx >= total) continue;
+                const int r = r0 + j, col = cj + (idx - ex);
                 // a cell already shadowed at every step the unit could set has nothing to
                 // gain (a stale read only skips less)
                 if ((sm.mask[r * kTile + col] & can) == can) continue;
@@ -372,9 +430,10 @@ __device__ __forceinline__ void flush_raster_counts(unsigned long long* stats, u
 // One CTA per 32 x 32-cell tile, every block of the chunk in order; the gross /
 // continuous state of the thread's four cells stays in registers between blocks.
 template <bool COUNT, bool CULL>
-__global__ void __launch_bounds__(kRasterThreads, 3)
+__global__ void __launch_bounds__(kRasterThreads, 4)
 k_raster(RasterArgs ra) {
     __shared__ TileSmem sm;
+    __shared__ RunState s_st[kTile * kTile];       // gross / run / best of the tile's cells
     unsigned long long n_cell = 0, n_test = 0;
     const TileGeom& g = ra.g;
     const int tile = blockIdx.x;
@@ -384,20 +443,18 @@ k_raster(RasterArgs ra) {
     float tox, toy;
     tile_setup(sm, g, tx, ty, &tox, &toy);
     const int ix = tx * kTile + lane;
-    long long outi[4];
-    bool act[4];
-    RunState st[4];
+    // each thread owns the cells (row0 + q, lane), q < 4, and alone touches their state
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int iy = ty * kTile + row0 + q;
-        act[q] = ix < g.nx && iy < g.ny;
-        outi[q] = (long long)iy * g.nx + ix;
-        st[q] = RunState{0, 0, 0};
-        if (act[q] && ra.load_state) {
-            st[q].gross = ra.out.gross[outi[q]];
-            st[q].best = ra.best[outi[q]];
-            st[q].run = ra.out.run[outi[q]];
+        const long long o = (long long)iy * g.nx + ix;
+        RunState st{0, 0, 0};
+        if (ix < g.nx && iy < g.ny && ra.load_state) {
+            st.gross = ra.out.gross[o];
+            st.best = ra.best[o];
+            st.run = ra.out.run[o];
         }
+        s_st[(row0 + q) * kTile + lane] = st;
     }
     const int n_tiles = g.tiles_x * g.tiles_y;
     const float inv_dx = 1.f / g.dx;
@@ -413,23 +470,30 @@ k_raster(RasterArgs ra) {
         };
         raster_block<COUNT, CULL>(sm, fetch, (int)cnt, ra.sun.steps, bcp->j0, bcp->K, tox, toy,
                                   inv_dx, ra.run, n_cell, n_test);
+        const int K = bcp->K, new_day = bcp->new_day;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int cell = (row0 + q) * kTile + lane;
             const unsigned long long m = sm.mask[cell];
             sm.mask[cell] = 0ull;
-            stitch(st[q], m, bcp->K, bcp->new_day);
-            if (ra.out.masks && act[q])
-                ra.out.masks[(size_t)bcp->mask_block * ra.R + outi[q]] |= m << bcp->mask_bit;
+            RunState st = s_st[cell];
+            stitch(st, m, K, new_day);
+            s_st[cell] = st;
+            const int iy = ty * kTile + row0 + q;
+            if (ra.out.masks && ix < g.nx && iy < g.ny)
+                ra.out.masks[(size_t)bcp->mask_block * ra.R + (long long)iy * g.nx + ix] |= m << bcp->mask_bit;
         }
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        if (!act[q]) continue;
-        ra.out.gross[outi[q]] = st[q].gross;
-        ra.best[outi[q]] = st[q].best;
-        ra.out.run[outi[q]] = st[q].run;
-        if (ra.final_chunk && ra.out.minutes) ra.out.minutes[outi[q]] = (float)st[q].gross * ra.out.step_minutes;
+        const int iy = ty * kTile + row0 + q;
+        if (ix >= g.nx || iy >= g.ny) continue;
+        const long long o = (long long)iy * g.nx + ix;
+        const RunState st = s_st[(row0 + q) * kTile + lane];
+        ra.out.gross[o] = st.gross;
+        ra.best[o] = st.best;
+        ra.out.run[o] = st.run;
+        if (ra.final_chunk && ra.out.minutes) ra.out.minutes[o] = (float)st.gross * ra.out.step_minutes;
     }
     if (COUNT) flush_raster_counts(ra.out.stats, n_cell, n_test);
 }

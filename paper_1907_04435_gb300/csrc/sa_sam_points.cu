@@ -433,7 +433,12 @@ void normalize3(double* v) {
     v[0] /= n; v[1] /= n; v[2] /= n;
 }
 
+int g_point_run = 16;
+
 }  // namespace
+
+void set_point_run(int run) { g_point_run = run; }
+int get_point_run() { return g_point_run; }
 
 cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const DevRecv& rc,
                               const float* recv_box, const DevSun& sun,
@@ -442,7 +447,7 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
                               cudaStream_t st) {
     const long long R = rc.R;
     if (R == 0 || h_blocks.empty()) return cudaSuccess;
-    const int run_len = std::max(1, std::min(kRunMax, get_raster_run()));
+    const int run_len = std::max(1, std::min(kRunMax, get_point_run()));
     const float tile = 32.f;
     // blocks per chunk: the receiver bins hold every receiver once per run (4 bytes), the
     // masks 8 bytes per receiver and block; keep both within ~1 GiB and <= 64 blocks

@@ -254,23 +254,23 @@ def test_facade_sam_multi_day_and_progressive(cuda_lib):
 
 @pytest.mark.parametrize("closed", [True, False])
 def test_accrual_maps_do_not_depend_on_the_run_length(cuda_lib, closed):
-    """Steps per set-up (1..32) only regroup the same per-step coverage tests (Theorem 1),
-    so both accrual maps give identical counts for every run length."""
+    """Steps per set-up (ground 1..32, points 1..16) only regroup the same per-step tests
+    (Theorem 1), so both accrual maps give identical counts for every run length."""
     B = cuda_lib
     w = workload("district_small")
     scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=closed)
     sun = B.Sun(w.sun.dirs, w.sun.day_start)
     grid = _ground(B, w)
     fac = B.Receivers.points(w.facade_pos, w.facade_nrm)
-    key = B.SA_OPT_RASTER_RUN
-    old = B.sa_get_option(key)
-    try:
-        B.sa_set_option(key, 8)
-        ref = [_run(B, scene, r, sun, "accrual_sam") for r in (grid, fac)]
-        for run in (1, 3, 13, 32):
-            B.sa_set_option(key, run)
-            for r, want in zip((grid, fac), ref):
+    for r, key, runs in ((grid, B.SA_OPT_RASTER_RUN, (1, 3, 13, 24, 32)),
+                         (fac, B.SA_OPT_POINT_RUN, (1, 3, 13, 16))):
+        old = B.sa_get_option(key)
+        try:
+            B.sa_set_option(key, 8)
+            want = _run(B, scene, r, sun, "accrual_sam")
+            for run in runs:
+                B.sa_set_option(key, run)
                 got = _run(B, scene, r, sun, "accrual_sam")
                 assert np.array_equal(got[0], want[0]) and np.array_equal(got[2], want[2]), run
-    finally:
-        B.sa_set_option(key, old)
+        finally:
+            B.sa_set_option(key, old)
