@@ -164,7 +164,7 @@ sa_status sa_batch_create(const sa_scene* base, const sa_receivers* grid, const 
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    b->ctas = 2 * b->sms;
+    b->ctas = 4 * b->sms;
     b->run = sa::get_raster_run();
     if (e == cudaSuccess) e = dev_copy(b, hv.data(), hv.size(), &b->d_var);
     if (e == cudaSuccess) e = dev_copy(b, towers.data(), towers.size(), &b->d_towers);
@@ -340,8 +340,8 @@ sa_status sa_batch_run(sa_batch* b, int32_t* counts, int32_t* impact, void* stre
     return SA_OK;
 }
 
-// Launch shape: 1 or 2 persistent CTAs per SM and 4, 8 or 16 steps per raster run, each
-// timed on the first eighth of the work queue; the fastest is kept for sa_batch_run.
+// Launch shape: 2, 3 or 4 persistent CTAs per SM and 8, 16 or 24 steps per raster run,
+// each timed on the first eighth of the work queue; the fastest is kept for sa_batch_run.
 sa_status sa_batch_tune(sa_batch* b, int32_t* best_ctas, int32_t* best_run, void* stream) {
     if (!b) return sa::report_error(SA_ERR_INVALID_ARG, "sa_batch_tune: NULL batch");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -353,8 +353,8 @@ sa_status sa_batch_tune(sa_batch* b, int32_t* best_ctas, int32_t* best_run, void
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = 3.4e38f;
     int bc = b->ctas, br = b->run;
-    const int runs[3] = {4, 8, 16};
-    for (int c = 1; c <= 2 && e == cudaSuccess; ++c)
+    const int runs[3] = {8, 16, 24};
+    for (int c = 2; c <= 4 && e == cudaSuccess; ++c)
         for (int r : runs) {
             const sa::BatchLaunch bl = launch_of(b, scratch, nullptr, n, c * b->sms, r, nullptr);
             e = sa::launch_batch(bl, st);                                   // warm-up

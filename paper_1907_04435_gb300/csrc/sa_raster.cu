@@ -505,9 +505,10 @@ k_raster(RasterArgs ra) {
 // It writes the counts of the tile's cells inside the region and, where the base counts
 // are given, the impact (variant minus base).
 template <bool COUNT, bool CULL>
-__global__ void __launch_bounds__(kRasterThreads)
+__global__ void __launch_bounds__(kRasterThreads, 4)
 k_batch(BatchArgs ba) {
     __shared__ TileSmem sm;
+    __shared__ RunState s_st[kTile * kTile];       // gross / run / best of the tile's cells
     __shared__ int s_item;
     unsigned long long n_cell = 0, n_test = 0;
     const TileGeom& g = ba.g;
@@ -541,9 +542,8 @@ k_batch(BatchArgs ba) {
         }
         float tox, toy;
         tile_setup(sm, g, tx, ty, &tox, &toy);
-        RunState st[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) st[q] = RunState{0, 0, 0};
+        for (int q = 0; q < 4; ++q) s_st[(row0 + q) * kTile + lane] = RunState{0, 0, 0};
         const int* rem = ba.removed + var.rem_off;
         const int n_rem = var.n_rem;
         const float4* towers = ba.tower_tris + 3ll * var.tower_off;
@@ -574,7 +574,9 @@ k_batch(BatchArgs ba) {
                 const int cell = (row0 + q) * kTile + lane;
                 const unsigned long long m = sm.mask[cell];
                 sm.mask[cell] = 0ull;
-                stitch(st[q], m, bc.K, bc.new_day);
+                RunState st = s_st[cell];
+                stitch(st, m, bc.K, bc.new_day);
+                s_st[cell] = st;
             }
         }
         const int ix = tx * kTile + lane;
@@ -584,9 +586,10 @@ k_batch(BatchArgs ba) {
             const int lx = ix - var.ix0, ly = iy - var.iy0;
             if (ix >= g.nx || iy >= g.ny || lx < 0 || ly < 0 || lx >= var.nx || ly >= var.ny) continue;
             const long long o = iv.out_base + var.out_off + (long long)ly * var.nx + lx;
-            ba.counts_out[o] = st[q].gross;
+            const int gross = s_st[(row0 + q) * kTile + lane].gross;
+            ba.counts_out[o] = gross;
             if (ba.impact_out && iv.base_counts)
-                ba.impact_out[o] = st[q].gross - iv.base_counts[(long long)iy * g.nx + ix];
+                ba.impact_out[o] = gross - iv.base_counts[(long long)iy * g.nx + ix];
         }
     }
     if (COUNT) flush_raster_counts(ba.stats, n_cell, n_test);

@@ -85,7 +85,7 @@ def test_batch_tuning_keeps_results_and_reruns_are_stable(cuda_lib):
     a, ia = bt.run()
     a, ia = a.clone(), ia.clone()
     ctas, run = bt.tune()
-    assert ctas > 0 and run in (4, 8, 16)
+    assert ctas > 0 and run in (8, 16, 24)
     b, ib = bt.run()
     c, ic = bt.run()
     torch.cuda.synchronize()
