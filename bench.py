@@ -265,7 +265,7 @@ def run_gpu(args):
             v["speedup_vs_sweep_trace"] = v["value"] / sweep
 
     # ---- roofline of the dominant kernel (instrumented work counters)
-    roof, roof_all = roofline(B, scene, grid, fac, sun, ktimes, args.steps)
+    roof, roof_all = roofline(B, scene, grid, fac, sun, ktimes, args.steps, args.workload)
 
     # ---- end to end through the C ABI from host buffers
     e2e = end_to_end(B, w, args, dev)
@@ -330,8 +330,32 @@ OPS_CELL, OPS_TEST = 15, 9
 OPS_PAIR, OPS_PTEST = 55, 15
 OPS_BOX, OPS_TRI = 12, 25
 
+# DRAM bytes (read + write) of one launch of each hot kernel on the `district` workload,
+# from one ncu capture of `dram__bytes_read.sum,dram__bytes_write.sum` (the launch list's
+# profile summary gives the command).  A figure is reported only while the kernel's
+# sources hash to the value they had when it was captured; otherwise traffic is null.
+TRAFFIC = {
+    "k_raster": {"bytes": 6979072 + 8615424, "workload": "district",
+                 "sources": ("sa_raster.cu", "sa_internal.cuh"), "sha256_16": "a4a3d5655091528f"},
+    "k_sam_tile": {"bytes": 239854848 + 31076352, "workload": "district",
+                   "sources": ("sa_sam_points.cu", "sa_internal.cuh", "sa_handles.cuh"),
+                   "sha256_16": "795983851bb7e717"},
+}
 
-def roofline(B, scene, grid, fac, sun, ktimes, steps):
+
+def kernel_traffic(name: str, workload: str):
+    import hashlib
+    t = TRAFFIC.get(name)
+    if t is None or t["workload"] != workload:
+        return None
+    m = hashlib.sha256()
+    for f in t["sources"]:
+        with open(os.path.join(ROOT, "paper_1907_04435_gb300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
+    return t["bytes"] if m.hexdigest()[:16] == t["sha256_16"] else None
+
+
+def roofline(B, scene, grid, fac, sun, ktimes, steps, workload):
     """ALU rooflines of the two hot kernels of a step: achieved = counted algorithmic FP32
     ops per launch / the kernel's mean launch duration, both from the timed region (CUDA
     events the library records around each launch, on its launching stream); peak = 152
@@ -349,7 +373,8 @@ def roofline(B, scene, grid, fac, sun, ktimes, steps):
         ach = ops_launch / (launch_ms * 1e-3)
         out[name] = {"bound": "alu", "kernel": desc, "achieved": ach / 1e12,
                      "peak": peak_ops / 1e12, "unit": "Tops/s", "frac": ach / peak_ops,
-                     "traffic": None, "launches_per_step": per_step,
+                     "traffic": kernel_traffic(name, workload), "traffic_unit": "bytes per launch",
+                     "launches_per_step": per_step,
                      "mean_launch_ms": launch_ms, "kernel_ms_per_step": t_ms / steps,
                      "ops_per_launch": ops_launch, "work": work}
 
