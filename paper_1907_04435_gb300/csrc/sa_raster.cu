@@ -134,6 +134,7 @@ struct RasterArgs {
     int cull;                        // closed scene: only faces toward the sun
     int run;                         // steps per work unit
     long long R;
+    const int* order;                // tile of each CTA (null: CTA i takes tile i)
 };
 
 constexpr int kWarpsRaster = kRasterThreads / 32;
@@ -196,6 +197,7 @@ struct TileSmem {
     float4 ubox[kMaxBlock];                  // per run: (min u.x, max u.x, min u.y, max u.y)
     unsigned long long mask[kTile * kTile];
     float xl[kTile], yl[kTile];
+    int next_unit;                           // next work unit of the batch to hand out
 };
 
 // Tile origin and cell centres in tile-local coordinates; the centres are rounded exactly
@@ -242,6 +244,113 @@ __device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeRef
     return CULL ? (hf & fr) : ((hf & fr) | (hb & bk));
 }
 
+// One work unit: triangle t of the staged batch and run `sub` of the block.  The warp
+// bounds the run's swept projection, enumerates the covered cells row by row and tests
+// the run's steps per cell; step bits are ORed into sm.mask.
+template <bool COUNT, bool CULL>
+__device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int kSub, int K,
+                                            float inv_dx, unsigned long long& n_cell,
+                                            unsigned long long& n_test) {
+    const int lane = threadIdx.x & 31;
+    const int t = un / nsub, sub = un - t * nsub, k0 = sub * kSub;
+    const int kn = min(kSub, K - k0);
+    const unsigned run_bits = (kn >= 32) ? 0xffffffffu : ((1u << kn) - 1u);
+    const unsigned fr = (unsigned)(sm.front[t] >> k0) & run_bits;
+    const unsigned bk = CULL ? 0u : ((unsigned)(sm.back[t] >> k0) & run_bits);
+    if ((fr | bk) == 0u) return;
+    const float4 a = sm.tri[3 * t], b = sm.tri[3 * t + 1], c = sm.tri[3 * t + 2];
+    // swept bounding box of the run's projections
+    const float4 ub = sm.ubox[sub];
+    const float uxlo = ub.x, uxhi = ub.y, uylo = ub.z, uyhi = ub.w;
+    const float az = fmaxf(a.z, 0.f), bz = fmaxf(b.z, 0.f), cz = fmaxf(c.z, 0.f);
+    const float xmin = fminf(a.x - az * uxhi, fminf(b.x - bz * uxhi, c.x - cz * uxhi));
+    const float xmax = fmaxf(a.x - az * uxlo, fmaxf(b.x - bz * uxlo, c.x - cz * uxlo));
+    const float ymin = fminf(a.y - az * uyhi, fminf(b.y - bz * uyhi, c.y - cz * uyhi));
+    const float ymax = fmaxf(a.y - az * uylo, fmaxf(b.y - bz * uylo, c.y - cz * uylo));
+    // cells whose centres (k + 0.5) dx fall in the box, with 0.01 cell of slack
+    const float fc0 = ceilf(xmin * inv_dx - 0.51f), fc1 = floorf(xmax * inv_dx - 0.49f);
+    const float fr0 = ceilf(ymin * inv_dx - 0.51f), fr1 = floorf(ymax * inv_dx - 0.49f);
+    if (fc1 < 0.f || fr1 < 0.f || fc0 > (float)(kTile - 1) || fr0 > (float)(kTile - 1) ||
+        fc0 > fc1 || fr0 > fr1) return;
+    const int c0 = (int)fmaxf(fc0, 0.f), c1 = (int)fminf(fc1, (float)(kTile - 1));
+    const int r0 = (int)fmaxf(fr0, 0.f), r1 = (int)fminf(fr1, (float)(kTile - 1));
+    const EdgeRef E0 = edge_ref(a, b), E1 = edge_ref(b, c), E2 = edge_ref(c, a);
+    // Row spans.  Each step's projection lies inside the projection for the run's
+    // middle slope u_m widened by (sx, sy) = z_max |u_hi - u_lo| / 2 (a vertex at
+    // height z moves by z (u_m - u_k)).  Lane j takes row r0 + j: the x-range of the
+    // middle projection over the band [y - sy, y + sy], widened by sx, bounds the
+    // row's covered cells (0.05 cell and 2 mm of slack absorb rounding).
+    const unsigned long long can = (unsigned long long)(fr | bk) << k0;
+    const float umx = 0.5f * (uxlo + uxhi), umy = 0.5f * (uylo + uyhi);
+    const float zm = fmaxf(az, fmaxf(bz, cz));
+    const float slack = 0.05f + 2e-3f * inv_dx;                 // in cells
+    const float sx = zm * (uxhi - uxlo) * 0.5f, sy = zm * (uyhi - uylo) * 0.5f;
+    const float px[3] = {a.x - az * umx, b.x - bz * umx, c.x - cz * umx};
+    const float py[3] = {a.y - az * umy, b.y - bz * umy, c.y - cz * umy};
+    int cs = 0, w = 0;
+    if (r0 + lane <= r1) {
+        const float y = sm.yl[r0 + lane];
+        const float band = sy + slack / inv_dx;
+        const float ya = y - band, yb = y + band;
+        float lo = 3.4e38f, hi = -3.4e38f;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            if (py[v] >= ya && py[v] <= yb) { lo = fminf(lo, px[v]); hi = fmaxf(hi, px[v]); }
+            const int q = v == 2 ? 0 : v + 1;
+            const float dy = py[q] - py[v];
+            if (dy != 0.f) {
+                const float slope = (px[q] - px[v]) / dy;
+                const float e0 = fminf(py[v], py[q]), e1 = fmaxf(py[v], py[q]);
+                if (ya >= e0 && ya <= e1) {
+                    const float x = fmaf(ya - py[v], slope, px[v]);
+                    lo = fminf(lo, x); hi = fmaxf(hi, x);
+                }
+                if (yb >= e0 && yb <= e1) {
+                    const float x = fmaf(yb - py[v], slope, px[v]);
+                    lo = fminf(lo, x); hi = fmaxf(hi, x);
+                }
+            }
+        }
+        if (lo <= hi) {
+            const float f0 = fmaxf(ceilf((lo - sx) * inv_dx - 0.5f - slack), (float)c0);
+            const float f1 = fminf(floorf((hi + sx) * inv_dx - 0.5f + slack), (float)c1);
+            if (f0 <= f1) {
+                cs = (int)f0;
+                w = (int)f1 - cs + 1;
+            }
+        }
+    }
+    // lanes walk the spans' cells, 32 at a time; a binary search over the rows'
+    // inclusive prefix sums finds each cell's row
+    int incl = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - w;
+    for (int base = 0; base < total; base += 32) {
+        const int idx = base + lane;
+        int j = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+            if (v <= idx) j += step;
+        }
+        const int ex = __shfl_sync(0xffffffffu, excl, j & 31);
+        const int cj = __shfl_sync(0xffffffffu, cs, j & 31);
+        if (idx >= total) continue;
+        const int r = r0 + j, col = cj + (idx - ex);
+        // a cell already shadowed at every step the unit could set has nothing to
+        // gain (a stale read only skips less)
+        if ((sm.mask[r * kTile + col] & can) == can) continue;
+        if (COUNT) { ++n_cell; n_test += kn; }
+        const unsigned hit = cell_steps<CULL>(sm, E0, E1, E2, sm.xl[col], sm.yl[r], k0, kn, fr, bk);
+        if (hit) atomicOr(&sm.mask[r * kTile + col], (unsigned long long)hit << k0);
+    }
+}
+
 // One block of steps of one tile: the n triangles given by fetch(i, vertex, &v) (false =
 // skip the triangle) are staged in batches; each warp takes work units (triangle, run of
 // <= 32 steps), bounds the run's swept projection, spreads its lanes over the covered
@@ -282,6 +391,7 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
             if (threadIdx.x % 3 == 0) sm.valid[threadIdx.x / 3] = ok ? 1 : 0;
         }
         __syncthreads();
+        if (threadIdx.x == 0) sm.next_unit = kWarpsRaster;
         // sun-facing steps of each staged triangle: a warp per triangle, a lane per step
         for (int t = warp; t < nt; t += kWarpsRaster) {
             unsigned long long fr = 0, bk = 0;
@@ -312,104 +422,14 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
         }
         __syncthreads();
         const int units = nt * nsub;
-        for (int un = warp; un < units; un += kWarpsRaster) {
-            const int t = un / nsub, sub = un - t * nsub, k0 = sub * kSub;
-            const int kn = min(kSub, K - k0);
-            const unsigned run_bits = (kn >= 32) ? 0xffffffffu : ((1u << kn) - 1u);
-            const unsigned fr = (unsigned)(sm.front[t] >> k0) & run_bits;
-            const unsigned bk = CULL ? 0u : ((unsigned)(sm.back[t] >> k0) & run_bits);
-            if ((fr | bk) == 0u) continue;
-            const float4 a = sm.tri[3 * t], b = sm.tri[3 * t + 1], c = sm.tri[3 * t + 2];
-            // swept bounding box of the run's projections
-            const float4 ub = sm.ubox[sub];
-            const float uxlo = ub.x, uxhi = ub.y, uylo = ub.z, uyhi = ub.w;
-            const float az = fmaxf(a.z, 0.f), bz = fmaxf(b.z, 0.f), cz = fmaxf(c.z, 0.f);
-            const float xmin = fminf(a.x - az * uxhi, fminf(b.x - bz * uxhi, c.x - cz * uxhi));
-            const float xmax = fmaxf(a.x - az * uxlo, fmaxf(b.x - bz * uxlo, c.x - cz * uxlo));
-            const float ymin = fminf(a.y - az * uyhi, fminf(b.y - bz * uyhi, c.y - cz * uyhi));
-            const float ymax = fmaxf(a.y - az * uylo, fmaxf(b.y - bz * uylo, c.y - cz * uylo));
-            // cells whose centres (k + 0.5) dx fall in the box, with 0.01 cell of slack
-            const float fc0 = ceilf(xmin * inv_dx - 0.51f), fc1 = floorf(xmax * inv_dx - 0.49f);
-            const float fr0 = ceilf(ymin * inv_dx - 0.51f), fr1 = floorf(ymax * inv_dx - 0.49f);
-            if (fc1 < 0.f || fr1 < 0.f || fc0 > (float)(kTile - 1) || fr0 > (float)(kTile - 1) ||
-                fc0 > fc1 || fr0 > fr1) continue;
-            const int c0 = (int)fmaxf(fc0, 0.f), c1 = (int)fminf(fc1, (float)(kTile - 1));
-            const int r0 = (int)fmaxf(fr0, 0.f), r1 = (int)fminf(fr1, (float)(kTile - 1));
-            const EdgeRef E0 = edge_ref(a, b), E1 = edge_ref(b, c), E2 = edge_ref(c, a);
-            // Row spans.  Each step's projection lies inside the projection for the run's
-            // middle slope u_m widened by (sx, sy) = z_max |u_hi - u_lo| / 2 (a vertex at
-            // height z moves by z (u_m - u_k)).  Lane j takes row r0 + j: the x-range of the
-            // middle projection over the band [y - sy, y + sy], widened by sx, bounds the
-            // row's covered cells (0.05 cell and 2 mm of slack absorb rounding).
-            const unsigned long long can = (unsigned long long)(fr | bk) << k0;
-            const float umx = 0.5f * (uxlo + uxhi), umy = 0.5f * (uylo + uyhi);
-            const float zm = fmaxf(az, fmaxf(bz, cz));
-            const float slack = 0.05f + 2e-3f * inv_dx;                 // in cells
-            const float sx = zm * (uxhi - uxlo) * 0.5f, sy = zm * (uyhi - uylo) * 0.5f;
-            const float px[3] = {a.x - az * umx, b.x - bz * umx, c.x - cz * umx};
-            const float py[3] = {a.y - az * umy, b.y - bz * umy, c.y - cz * umy};
-            int cs = 0, w = 0;
-            if (r0 + lane <= r1) {
-                const float y = sm.yl[r0 + lane];
-                const float band = sy + slack / inv_dx;
-                const float ya = y - band, yb = y + band;
-                float lo = 3.4e38f, hi = -3.4e38f;
-#pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    if (py[v] >= ya && py[v] <= yb) { lo = fminf(lo, px[v]); hi = fmaxf(hi, px[v]); }
-                    const int q = v == 2 ? 0 : v + 1;
-                    const float dy = py[q] - py[v];
-                    if (dy != 0.f) {
-                        const float slope = (px[q] - px[v]) / dy;
-                        const float e0 = fminf(py[v], py[q]), e1 = fmaxf(py[v], py[q]);
-                        if (ya >= e0 && ya <= e1) {
-                            const float x = fmaf(ya - py[v], slope, px[v]);
-                            lo = fminf(lo, x); hi = fmaxf(hi, x);
-                        }
-                        if (yb >= e0 && yb <= e1) {
-                            const float x = fmaf(yb - py[v], slope, px[v]);
-                            lo = fminf(lo, x); hi = fmaxf(hi, x);
-                        }
-                    }
-                }
-                if (lo <= hi) {
-                    const float f0 = fmaxf(ceilf((lo - sx) * inv_dx - 0.5f - slack), (float)c0);
-                    const float f1 = fminf(floorf((hi + sx) * inv_dx - 0.5f + slack), (float)c1);
-                    if (f0 <= f1) {
-                        cs = (int)f0;
-                        w = (int)f1 - cs + 1;
-                    }
-                }
-            }
-            // lanes walk the spans' cells, 32 at a time; a binary search over the rows'
-            // inclusive prefix sums finds each cell's row
-            int incl = w;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += v;
-            }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            const int excl = incl - w;
-            for (int base = 0; base < total; base += 32) {
-                const int idx = base + lane;
-                int j = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
-                    if (v <= idx) j += step;
-                }
-                const int ex = __shfl_sync(0xffffffffu, excl, j & 31);
-                const int cj = __shfl_sync(0xffffffffu, cs, j & 31);
-                if (idx >= total) continue;
-                const int r = r0 + j, col = cj + (idx - ex);
-                // a cell already shadowed at every step the unit could set has nothing to
-                // gain (a stale read only skips less)
-                if ((sm.mask[r * kTile + col] & can) == can) continue;
-                if (COUNT) { ++n_cell; n_test += kn; }
-                const unsigned hit = cell_steps<CULL>(sm, E0, E1, E2, sm.xl[col], sm.yl[r], k0, kn, fr, bk);
-                if (hit) atomicOr(&sm.mask[r * kTile + col], (unsigned long long)hit << k0);
-            }
+        // warps take units from a shared counter, so an expensive unit does not hold the
+        // warps that would otherwise wait for its warp at the next barrier
+        int un = warp;
+        while (un < units) {
+            raster_unit<COUNT, CULL>(sm, un, nsub, kSub, K, inv_dx, n_cell, n_test);
+            int nx = 0;
+            if (lane == 0) nx = atomicAdd(&sm.next_unit, 1);
+            un = __shfl_sync(0xffffffffu, nx, 0);
         }
     }
     __syncthreads();
@@ -436,7 +456,7 @@ k_raster(RasterArgs ra) {
     __shared__ RunState s_st[kTile * kTile];       // gross / run / best of the tile's cells
     unsigned long long n_cell = 0, n_test = 0;
     const TileGeom& g = ra.g;
-    const int tile = blockIdx.x;
+    const int tile = ra.order ? ra.order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row0 = warp * 4;
@@ -595,6 +615,37 @@ k_batch(BatchArgs ba) {
     if (COUNT) flush_raster_counts(ba.stats, n_cell, n_test);
 }
 
+// Launch order of the tiles: descending by the triangles binned to them over the chunk's
+// blocks, bucketed at half powers of two.  The CTAs that start last are then the cheap
+// ones, which shortens the launch's tail; the order does not change any result.
+__global__ void k_tile_order(const unsigned* __restrict__ counts, int nbc, int n_tiles,
+                             int* __restrict__ order) {
+    constexpr int kBuckets = 64;
+    __shared__ unsigned hist[kBuckets];
+    auto bucket = [&](int t) {
+        unsigned c = 0;
+        for (int b = 0; b < nbc; ++b) c += counts[(size_t)b * n_tiles + t];
+        if (c <= 1u) return kBuckets - 1;
+        const int l = 31 - __clz(c);
+        const int key = 2 * l + (int)((c >> (l - 1)) & 1u);     // 2 .. 63
+        return kBuckets - 1 - key;
+    };
+    if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&hist[bucket(t)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int k = 0; k < kBuckets; ++k) {
+            const unsigned h = hist[k];
+            hist[k] = run;
+            run += h;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&hist[bucket(t)], 1u)] = t;
+}
+
 void launch_k_raster(const RasterArgs& ra, int n_tiles, bool stats, cudaStream_t st) {
     if (ra.cull) {
         if (stats) k_raster<true, true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
@@ -629,13 +680,14 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
     const int chunk = 64;
     const int max_chunk_blocks = sun.n_blocks < chunk ? sun.n_blocks : chunk;
     unsigned *counts = nullptr, *offsets = nullptr, *cursor = nullptr, *d_total = nullptr;
-    int* bins = nullptr;
+    int *bins = nullptr, *order = nullptr;
     size_t bins_cap = 0;
     const size_t nc = (size_t)max_chunk_blocks * n_tiles;
     e = cudaMallocAsync(&counts, sizeof(unsigned) * nc, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&offsets, sizeof(unsigned) * nc, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&cursor, sizeof(unsigned) * nc, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&d_total, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&order, sizeof(int) * (size_t)n_tiles, st);
     const int tpb = 128;
     for (int b0 = 0; b0 < sun.n_blocks && e == cudaSuccess; b0 += chunk) {
         const int nbc = (sun.n_blocks - b0) < chunk ? (sun.n_blocks - b0) : chunk;
@@ -648,6 +700,7 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
         if (sc.T > 0) {
             dim3 grid((sc.T + tpb - 1) / tpb, nbc);
             k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, counts);
+            k_tile_order<<<1, 1024, 0, st>>>(counts, nbc, n_tiles, order);
             e = cudaMemcpyAsync(offsets, counts, sizeof(unsigned) * ncc, cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) break;
             e = exclusive_scan_u32(offsets, (long long)ncc, d_total, st);
@@ -676,6 +729,7 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
         ra.R = R;
         ra.cull = sc.closed;
         ra.run = g_raster_run;
+        ra.order = sc.T > 0 ? order : nullptr;
         if (b0 == 0 && out.accumulate_into) {
             // run lengths never cross calls (calls cover whole days)
             e = cudaMemsetAsync(out.run, 0, sizeof(int) * (size_t)R, st);
@@ -696,6 +750,7 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
     if (cursor) cudaFreeAsync(cursor, st);
     if (d_total) cudaFreeAsync(d_total, st);
     if (bins) cudaFreeAsync(bins, st);
+    if (order) cudaFreeAsync(order, st);
     if (best_scratch) cudaFreeAsync(best_scratch, st);
     return e;
 }
@@ -785,6 +840,7 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
         ra.R = R;
         ra.cull = sc.closed;
         ra.run = g_raster_run;
+        ra.order = nullptr;
         launch_k_raster(ra, n_tiles, out.stats != nullptr, st);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
