@@ -302,16 +302,17 @@ def run_gpu(args):
 
 def count_launches(scene, sun, grid, fac):
     """Kernels of one timed step.  Ground raster, per chunk of <= 64 blocks: bin count,
-    3 scan kernels, bin fill, raster.  Facade map, per chunk of blocks (<= 64, and bins of
+    tile order, 3 scan kernels, bin fill, raster.  Facade map, per chunk of blocks (<= 64, and bins of
     <= 1 GiB at 4 bytes per receiver and run plus 8 per receiver and block): triangle and
-    receiver bin counts, 2 x 3 scan kernels, the two fills, the tile kernel and the fold."""
+    receiver bin counts, 2 x 3 scan kernels, 3 kernels ordering the tiles by work, the two
+    fills, the tile kernel and the fold."""
     chunks = (sun.n_blocks + 63) // 64
-    n = chunks * 6
+    n = chunks * 7
     if fac:
         run = min(16, max(1, B_option_run()))   # steps per light-space map
         per_block = fac.R * (4 * ((64 + run - 1) // run) + 8)
         fchunk = max(1, min(64, (1 << 30) // max(1, per_block)))
-        n += 12 * ((sun.n_blocks + fchunk - 1) // fchunk)
+        n += 15 * ((sun.n_blocks + fchunk - 1) // fchunk)
     return n
 
 

@@ -162,14 +162,19 @@ __device__ __forceinline__ void p_edge(const float3& o, const float4& a, const f
     m[2] = sg * __fsub_rn(__fmul_rn(px, qy), __fmul_rn(py, qx));
 }
 
-__device__ __forceinline__ bool p_hit(const PTri& p, float dx, float dy, float dz, float tmin) {
+// Does the ray from the set-up origin along d meet the triangle beyond t_min?  The three
+// Plücker signs must agree (the line passes through the triangle) and the plane must be
+// hit at t = aon / (n . d) > t_min.  Evaluated without early exits, so the steps of a run
+// form independent chains.
+__device__ __forceinline__ bool p_hit_all(const PTri& p, float dx, float dy, float dz, float tmin) {
     const float s0 = fmaf(dz, p.m[0][2], fmaf(dy, p.m[0][1], dx * p.m[0][0]));
     const float s1 = fmaf(dz, p.m[1][2], fmaf(dy, p.m[1][1], dx * p.m[1][0]));
     const float s2 = fmaf(dz, p.m[2][2], fmaf(dy, p.m[2][1], dx * p.m[2][0]));
-    if (!((s0 >= 0.f && s1 >= 0.f && s2 >= 0.f) || (s0 <= 0.f && s1 <= 0.f && s2 <= 0.f))) return false;
     const float nd = fmaf(dz, p.nz, fmaf(dy, p.ny, dx * p.nx));
-    if (nd == 0.f) return false;
-    return nd > 0.f ? (p.aon > tmin * nd) : (p.aon < tmin * nd);
+    const bool inside = fminf(s0, fminf(s1, s2)) >= 0.f || fmaxf(s0, fmaxf(s1, s2)) <= 0.f;
+    const float lim = tmin * nd;
+    const bool ahead = (nd > 0.f && p.aon > lim) || (nd < 0.f && p.aon < lim);
+    return inside && ahead;
 }
 
 struct TileArgs {
@@ -178,6 +183,7 @@ struct TileArgs {
     const RunLight* runs;
     int n_runs;
     const int* tile_run;           // run of each global tile
+    const int* order;              // tile of each CTA, most work first, empty tiles left out
     const unsigned* t_off; const unsigned* t_cnt; const int* t_bins;
     const unsigned* r_off; const unsigned* r_cnt; const int* r_bins;
     const float4* orig;
@@ -250,12 +256,14 @@ __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int 
     pt.ny = uz * vx - ux * vz;
     pt.nz = ux * vy - uy * vx;
     pt.aon = pt.nx * (a.x - o.x) + pt.ny * (a.y - o.y) + pt.nz * (a.z - o.z);
+    // every step of the run is tested without branches (independent chains the scheduler
+    // can interleave); steps the triangle turns away from are masked off afterwards
     unsigned m = 0;
-    for (int k = 0; k < kn; ++k) {
-        if (!((want >> k) & 1u)) continue;
-        if (COUNT) ++n_test;
-        if (p_hit(pt, s_d[k][0], s_d[k][1], s_d[k][2], p.w)) m |= 1u << k;
-    }
+#pragma unroll 4
+    for (int k = 0; k < kn; ++k)
+        if (p_hit_all(pt, s_d[k][0], s_d[k][1], s_d[k][2], p.w)) m |= 1u << k;
+    m &= want;
+    if (COUNT) n_test += (unsigned)__popc(want);
     if (m) atomicOr(&s_m[who], m);
 }
 
@@ -274,7 +282,7 @@ k_sam_tile(TileArgs ta) {
     __shared__ unsigned short s_q[kWarps][kQueue]; // pair queues: receiver slot << 8 | triangle
     __shared__ unsigned char s_list[kWarps][kTriChunk];  // triangles near the warp's receivers
     unsigned long long n_pair = 0, n_test = 0;
-    const int tile = blockIdx.x;
+    const int tile = ta.order[blockIdx.x];
     const unsigned tcnt = ta.t_cnt[tile], rcnt = ta.r_cnt[tile];
     if (tcnt == 0 || rcnt == 0) return;
     const RunLight& rl = ta.runs[ta.tile_run[tile]];
@@ -400,6 +408,59 @@ k_sam_tile(TileArgs ta) {
             atomicAdd(&ta.stats[1], n_test);
         }
     }
+}
+
+// Launch order of the light-space tiles: descending by (triangles x receivers), bucketed at
+// half powers of two; tiles with no pair go last and are not launched.  The order changes
+// no result, only which CTAs start last (the cheap ones, which shortens the tail).
+constexpr int kOrderBuckets = 64;
+
+__device__ __forceinline__ int pair_bucket(unsigned tcount, unsigned rcount) {
+    const unsigned long long c = (unsigned long long)tcount * rcount;
+    if (c == 0ull) return kOrderBuckets - 1;
+    if (c == 1ull) return kOrderBuckets - 2;
+    const int l = 63 - __clzll(c);
+    const int key = min(kOrderBuckets - 2, 2 * l + (int)((c >> (l - 1)) & 1ull));
+    return kOrderBuckets - 2 - key;
+}
+
+__global__ void k_order_hist(const unsigned* __restrict__ tc, const unsigned* __restrict__ rc,
+                             long long n, unsigned* __restrict__ hist) {
+    __shared__ unsigned h[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) h[threadIdx.x] = 0u;
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&h[pair_bucket(tc[i], rc[i])], 1u);
+    __syncthreads();
+    if (threadIdx.x < kOrderBuckets && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// exclusive scan of the histogram into the bucket cursors; n_work = tiles with a pair
+__global__ void k_order_scan(unsigned* __restrict__ hist, unsigned* __restrict__ n_work) {
+    if (threadIdx.x != 0) return;
+    unsigned run = 0;
+    for (int k = 0; k < kOrderBuckets; ++k) {
+        const unsigned h = hist[k];
+        hist[k] = run;
+        run += h;
+        if (k == kOrderBuckets - 2) *n_work = run;
+    }
+}
+
+__global__ void k_order_fill(const unsigned* __restrict__ tc, const unsigned* __restrict__ rc,
+                             long long n, unsigned* __restrict__ cursor, int* __restrict__ order) {
+    __shared__ unsigned h[kOrderBuckets], base[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) h[threadIdx.x] = 0u;
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = i < n ? pair_bucket(tc[i], rc[i]) : -1;
+    unsigned rank = 0;
+    if (b >= 0) rank = atomicAdd(&h[b], 1u);
+    __syncthreads();
+    if (threadIdx.x < kOrderBuckets && h[threadIdx.x])
+        base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], h[threadIdx.x]);
+    __syncthreads();
+    if (b >= 0) order[base[b] + rank] = (int)i;
 }
 
 // Stitch the chunk's blocks, in order, into each receiver's gross / continuous state.
@@ -538,8 +599,8 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
         RunLight* d_runs = nullptr;
         int* d_tile_run = nullptr;
         unsigned *tc = nullptr, *toff = nullptr, *tcur = nullptr, *rcn = nullptr, *roff = nullptr,
-                 *rcur = nullptr, *d_total = nullptr;
-        int *tbins = nullptr, *rbins = nullptr;
+                 *rcur = nullptr, *d_total = nullptr, *hist = nullptr;
+        int *tbins = nullptr, *rbins = nullptr, *order = nullptr;
         const size_t nt = (size_t)tiles;
 #define TRYB(x) do { if (e == cudaSuccess) e = (x); } while (0)
         TRYB(cudaMemsetAsync(masks, 0, sizeof(unsigned long long) * (size_t)R * nbc, st));
@@ -551,7 +612,9 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
         TRYB(cudaMallocAsync(&rcn, sizeof(unsigned) * nt, st));
         TRYB(cudaMallocAsync(&roff, sizeof(unsigned) * nt, st));
         TRYB(cudaMallocAsync(&rcur, sizeof(unsigned) * nt, st));
-        TRYB(cudaMallocAsync(&d_total, sizeof(unsigned), st));
+        TRYB(cudaMallocAsync(&d_total, 2 * sizeof(unsigned), st));   // bin total, tiles with work
+        TRYB(cudaMallocAsync(&hist, sizeof(unsigned) * kOrderBuckets, st));
+        TRYB(cudaMallocAsync(&order, sizeof(int) * nt, st));
         TRYB(cudaMallocAsync(&rbins, sizeof(int) * (size_t)R * n_runs, st));
         TRYB(cudaMemcpyAsync(d_runs, hr.data(), sizeof(RunLight) * hr.size(), cudaMemcpyHostToDevice, st));
         TRYB(cudaMemcpyAsync(d_tile_run, tile_run.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
@@ -559,20 +622,26 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
         TRYB(cudaMemsetAsync(tcur, 0, sizeof(unsigned) * nt, st));
         TRYB(cudaMemsetAsync(rcn, 0, sizeof(unsigned) * nt, st));
         TRYB(cudaMemsetAsync(rcur, 0, sizeof(unsigned) * nt, st));
+        TRYB(cudaMemsetAsync(hist, 0, sizeof(unsigned) * kOrderBuckets, st));
         const dim3 gt((unsigned)std::max(1, (sc.T + 127) / 128), n_runs);
         const dim3 gr((unsigned)((R + 255) / 256), n_runs);
-        unsigned total = 0;
+        unsigned totals[2] = {0u, 0u};
+        const unsigned go = (unsigned)((nt + 255) / 256);
         if (e == cudaSuccess) {
             if (sc.T > 0) k_lt_bin<<<gt, 128, 0, st>>>(sc, sun.steps, d_runs, n_runs, false, tc, nullptr, nullptr, nullptr);
             k_lr_bin<<<gr, 256, 0, st>>>(rc.orig, R, d_runs, n_runs, false, rcn, nullptr, nullptr, nullptr);
+            k_order_hist<<<go, 256, 0, st>>>(tc, rcn, (long long)nt, hist);
+            k_order_scan<<<1, 32, 0, st>>>(hist, d_total + 1);
+            k_order_fill<<<go, 256, 0, st>>>(tc, rcn, (long long)nt, hist, order);
             e = cudaGetLastError();
         }
         TRYB(cudaMemcpyAsync(toff, tc, sizeof(unsigned) * nt, cudaMemcpyDeviceToDevice, st));
         TRYB(cudaMemcpyAsync(roff, rcn, sizeof(unsigned) * nt, cudaMemcpyDeviceToDevice, st));
         TRYB(exclusive_scan_u32(roff, (long long)nt, nullptr, st));
         TRYB(exclusive_scan_u32(toff, (long long)nt, d_total, st));
-        TRYB(cudaMemcpyAsync(&total, d_total, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        TRYB(cudaMemcpyAsync(totals, d_total, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         TRYB(cudaStreamSynchronize(st));
+        const unsigned total = totals[0], work_tiles = totals[1];
         TRYB(cudaMallocAsync(&tbins, sizeof(int) * ((size_t)total + 1), st));
         if (e == cudaSuccess) {
             if (sc.T > 0 && total > 0)
@@ -581,13 +650,14 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
             TileArgs ta;
             ta.sc = sc; ta.steps = sun.steps; ta.runs = d_runs; ta.n_runs = n_runs;
             ta.tile_run = d_tile_run;
+            ta.order = order;
             ta.t_off = toff; ta.t_cnt = tc; ta.t_bins = tbins;
             ta.r_off = roff; ta.r_cnt = rcn; ta.r_bins = rbins;
             ta.orig = rc.orig; ta.masks = masks; ta.R = R; ta.stats = out.stats;
-            if (tiles > 0) {
+            if (work_tiles > 0) {
                 KernelTimer kt(KT_SAM_POINTS, st);
-                if (out.stats) k_sam_tile<true><<<tiles, kTileThreads, 0, st>>>(ta);
-                else k_sam_tile<false><<<tiles, kTileThreads, 0, st>>>(ta);
+                if (out.stats) k_sam_tile<true><<<work_tiles, kTileThreads, 0, st>>>(ta);
+                else k_sam_tile<false><<<work_tiles, kTileThreads, 0, st>>>(ta);
             }
             k_points_fold<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(
                 R, rc.perm, sun.blocks + b0, nbc, masks, out, run, bestp, b0 == 0,
@@ -595,7 +665,8 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
             e = cudaGetLastError();
         }
         for (void* p : {(void*)d_runs, (void*)d_tile_run, (void*)tc, (void*)toff, (void*)tcur,
-                        (void*)rcn, (void*)roff, (void*)rcur, (void*)d_total, (void*)tbins, (void*)rbins})
+                        (void*)rcn, (void*)roff, (void*)rcur, (void*)d_total, (void*)tbins, (void*)rbins,
+                        (void*)hist, (void*)order})
             if (p) cudaFreeAsync(p, st);
 #undef TRYB
     }

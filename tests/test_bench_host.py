@@ -41,6 +41,6 @@ def test_launch_count_covers_both_maps(monkeypatch):
             self.R = R
 
     monkeypatch.setattr(bench, "B_option_run", lambda: 16)
-    assert bench.count_launches(None, _Sun(), None, None) == 6
-    assert bench.count_launches(None, _Sun(), None, _Fac(1_000_000)) == 6 + 12
-    assert bench.count_launches(None, _Sun(), None, _Fac(40_000_000)) == 6 + 12 * 9
+    assert bench.count_launches(None, _Sun(), None, None) == 7
+    assert bench.count_launches(None, _Sun(), None, _Fac(1_000_000)) == 7 + 15
+    assert bench.count_launches(None, _Sun(), None, _Fac(40_000_000)) == 7 + 15 * 9
