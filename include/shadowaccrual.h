@@ -195,9 +195,12 @@ sa_status sa_receivers_grid(float x0, float y0, float dx, int32_t nx, int32_t ny
 
 /* Point receivers: pos float [n][3]; normal float [n][3] outward unit normals (facade
  * receivers) or NULL (ground receivers at their own z, using the ground rule).  Host or
- * device memory per device_ptrs; copied and sorted internally along a Morton curve so
- * a warp holds neighbouring points.  Outputs always come back in input order.
- * Errors: SA_ERR_INVALID_ARG, SA_ERR_DEGENERATE (non-finite), SA_ERR_OOM, SA_ERR_CUDA. */
+ * device memory per device_ptrs (host memory is copied with cudaMemcpyAsync, so pinned
+ * buffers transfer fastest); sorted internally along a Morton curve so a warp holds
+ * neighbouring points.  The values are checked on the device while they are sorted; the
+ * call synchronises `stream` once.  Outputs always come back in input order.
+ * Errors: SA_ERR_INVALID_ARG, SA_ERR_DEGENERATE (non-finite position or normal; the
+ * message names the first such point), SA_ERR_OOM, SA_ERR_CUDA. */
 sa_status sa_receivers_points(const float* pos, const float* normal, int64_t n,
                               int32_t device_ptrs, void* stream, sa_receivers** out);
 void sa_receivers_destroy(sa_receivers* recv);

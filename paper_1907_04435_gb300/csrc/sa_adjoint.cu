@@ -288,28 +288,28 @@ cudaError_t launch_height_grad(const DevScene& sc, const FootprintSet& fs, const
     int* gross = nullptr;
     const int B = fs.B;
 #define TRY(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
-    TRY(cudaMallocAsync(&dsdh, sizeof(double) * (B > 0 ? B : 1), st));
-    TRY(cudaMallocAsync(&S, sizeof(double), st));
+    TRY(sa::scratch_alloc(&dsdh, sizeof(double) * (B > 0 ? B : 1), st));
+    TRY(sa::scratch_alloc(&S, sizeof(double), st));
     TRY(cudaMemsetAsync(dsdh, 0, sizeof(double) * (B > 0 ? B : 1), st));
     TRY(cudaMemsetAsync(S, 0, sizeof(double), st));
     if (R > 0 && sun.n_blocks > 0) {
-        TRY(cudaMallocAsync(&masks, sizeof(unsigned long long) * (size_t)R * sun.n_blocks, st));
+        TRY(sa::scratch_alloc(&masks, sizeof(unsigned long long) * (size_t)R * sun.n_blocks, st));
         TRY(cudaMemsetAsync(masks, 0, sizeof(unsigned long long) * (size_t)R * sun.n_blocks, st));
-        TRY(cudaMallocAsync(&gross, sizeof(int) * (size_t)R, st));
+        TRY(sa::scratch_alloc(&gross, sizeof(int) * (size_t)R, st));
         {
             DevOut out;
             memset(&out, 0, sizeof(out));
             out.gross = gross;
             out.masks = reinterpret_cast<uint64_t*>(masks);
             int* run = nullptr;
-            TRY(cudaMallocAsync(&run, sizeof(int) * (size_t)R, st));
+            TRY(sa::scratch_alloc(&run, sizeof(int) * (size_t)R, st));
             out.run = run;
             e = launch_raster_ground(sc, rc, sun, out, st);
             cudaFreeAsync(run, st);
             if (e != cudaSuccess) goto done;
         }
-        TRY(cudaMallocAsync(&counts, sizeof(unsigned) * (size_t)R, st));
-        TRY(cudaMallocAsync(&d_total, sizeof(unsigned), st));
+        TRY(sa::scratch_alloc(&counts, sizeof(unsigned) * (size_t)R, st));
+        TRY(sa::scratch_alloc(&d_total, sizeof(unsigned), st));
         const double dt = step_minutes;
         const unsigned grid = (unsigned)((R + 255) / 256);
         k_flip_count<<<grid, 256, 0, st>>>(masks, R, sun.blocks, sun.n_blocks, weights, dt, counts, S);
@@ -319,7 +319,7 @@ cudaError_t launch_height_grad(const DevScene& sc, const FootprintSet& fs, const
         TRY(cudaMemcpyAsync(&total, d_total, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
         if (total > 0) {
-            TRY(cudaMallocAsync(&flips, sizeof(int4) * (size_t)total, st));
+            TRY(sa::scratch_alloc(&flips, sizeof(int4) * (size_t)total, st));
             k_flip_fill<<<grid, 256, 0, st>>>(masks, R, sun.blocks, sun.n_blocks, counts, flips);
             SolveArgs sa;
             sa.sc = sc; sa.fs = fs; sa.heights = d_heights; sa.steps = sun.steps;

@@ -582,43 +582,42 @@ sa_status sa_receivers_points(const float* pos, const float* normal, int64_t n,
     *out = nullptr;
     if (n < 0 || n > (1ll << 31) - 1) return fail(SA_ERR_INVALID_ARG, "sa_receivers_points: bad count");
     if (n > 0 && !pos) return fail(SA_ERR_INVALID_ARG, "sa_receivers_points: NULL positions");
-    std::vector<float> hp, hn;
-    sa_status s = host_copy(pos, (size_t)n * 3, device_ptrs, &hp);
-    if (s != SA_OK) return s;
-    if (normal) {
-        s = host_copy(normal, (size_t)n * 3, device_ptrs, &hn);
-        if (s != SA_OK) return s;
-    }
-    for (size_t i = 0; i < hp.size(); ++i)
-        if (!isfinite(hp[i])) return fail(SA_ERR_DEGENERATE, "sa_receivers_points: non-finite position %zu", i / 3);
-    for (size_t i = 0; i < hn.size(); ++i)
-        if (!isfinite(hn[i])) return fail(SA_ERR_DEGENERATE, "sa_receivers_points: non-finite normal %zu", i / 3);
     sa_receivers* r = new (std::nothrow) sa_receivers();
     if (!r) return fail(SA_ERR_OOM, "sa_receivers_points: host allocation");
     r->is_grid = 0;
     r->R = n;
-    for (int q = 0; q < 3; ++q) { r->box[q] = INFINITY; r->box[3 + q] = -INFINITY; }
-    for (int64_t i = 0; i < n; ++i)
-        for (int q = 0; q < 3; ++q) {
-            const float x = hp[3 * (size_t)i + q] + (normal ? 1e-2f * hn[3 * (size_t)i + q] : 0.f);
-            r->box[q] = std::min(r->box[q], x);
-            r->box[3 + q] = std::max(r->box[3 + q], x);
-        }
-    if (n == 0) for (int q = 0; q < 6; ++q) r->box[q] = 0.f;
     cudaStream_t st = as_stream(stream);
-    float *dp = nullptr, *dn = nullptr;
-    cudaError_t e = upload(hp.data(), hp.size(), 0, &dp, st);
-    if (e == cudaSuccess && normal) e = upload(hn.data(), hn.size(), 0, &dn, st);
+    // host inputs are copied to stream-ordered staging; device inputs are read in place.
+    // Validation (finite values) and the bounds run on the device, in the sort's pass.
+    const float *dp = pos, *dn = normal;
+    float *sp = nullptr, *sn = nullptr;
+    cudaError_t e = cudaSuccess;
+    const size_t bytes = sizeof(float) * 3 * (size_t)n;
+    if (n > 0 && !device_ptrs) {
+        e = sa::scratch_alloc(&sp, bytes, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sp, pos, bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && normal) e = sa::scratch_alloc(&sn, bytes, st);
+        if (e == cudaSuccess && normal) e = cudaMemcpyAsync(sn, normal, bytes, cudaMemcpyHostToDevice, st);
+        dp = sp;
+        dn = normal ? sn : nullptr;
+    }
     if (e == cudaSuccess && n > 0) e = cudaMalloc(&r->d_orig, sizeof(float4) * (size_t)n);
     if (e == cudaSuccess && n > 0) e = cudaMalloc(&r->d_perm, sizeof(int) * (size_t)n);
     if (e == cudaSuccess && n > 0 && normal) e = cudaMalloc(&r->d_nrm, sizeof(float4) * (size_t)n);
-    if (e == cudaSuccess) e = sa::sort_points(dp, dn, n, r->d_orig, r->d_nrm, r->d_perm, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (dp) cudaFree(dp);
-    if (dn) cudaFree(dn);
+    long long bad[2] = {-1, -1};
+    if (e == cudaSuccess)
+        e = sa::sort_points(dp, dn, n, r->d_orig, r->d_nrm, r->d_perm, st, bad, r->box);
+    if (sp) cudaFreeAsync(sp, st);
+    if (sn) cudaFreeAsync(sn, st);
     if (e != cudaSuccess) {
         sa_receivers_destroy(r);
         return cuda_fail(e, "sa_receivers_points");
+    }
+    if (bad[0] >= 0 || bad[1] >= 0) {
+        sa_receivers_destroy(r);
+        return bad[0] >= 0
+            ? fail(SA_ERR_DEGENERATE, "sa_receivers_points: non-finite position %lld", bad[0])
+            : fail(SA_ERR_DEGENERATE, "sa_receivers_points: non-finite normal %lld", bad[1]);
     }
     *out = r;
     return SA_OK;
@@ -674,12 +673,12 @@ static sa_status run_method(const sa_scene* scene, const sa_receivers* recv, con
     }
     int* run = nullptr;
     if (method == SA_IAM) {
-        e = cudaMallocAsync(&run, sizeof(int) * (size_t)R, st);
+        e = sa::scratch_alloc(&run, sizeof(int) * (size_t)R, st);
         if (e != cudaSuccess) return cuda_fail(e, who);
         out.run = run;
         e = sa::launch_iam(dsc, drc, dsun, sun->h_blocks.data(), iam_levels ? iam_levels : 3, out, st);
     } else if (raster) {
-        e = cudaMallocAsync(&run, sizeof(int) * (size_t)R, st);
+        e = sa::scratch_alloc(&run, sizeof(int) * (size_t)R, st);
         if (e != cudaSuccess) return cuda_fail(e, who);
         out.run = run;
         e = sa::launch_raster_ground(dsc, drc, dsun, out, st);
@@ -723,7 +722,7 @@ sa_status sa_shadow_masks(const sa_scene* scene, const sa_receivers* recv, const
     cudaStream_t st = as_stream(stream);
     int* gross = nullptr;
     if (recv->R > 0) {
-        cudaError_t e = cudaMallocAsync(&gross, sizeof(int) * (size_t)recv->R, st);
+        cudaError_t e = sa::scratch_alloc(&gross, sizeof(int) * (size_t)recv->R, st);
         if (e != cudaSuccess) return cuda_fail(e, "sa_shadow_masks");
     }
     if (recv->R > 0 && sun) {
@@ -769,7 +768,7 @@ sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, cons
     if (e != cudaSuccess) return cuda_fail(e, "sa_work_counters");
     int* gross = nullptr;
     if (recv->R > 0) {
-        e = cudaMallocAsync(&gross, sizeof(int) * (size_t)recv->R, st);
+        e = sa::scratch_alloc(&gross, sizeof(int) * (size_t)recv->R, st);
         if (e != cudaSuccess) return cuda_fail(e, "sa_work_counters");
     }
     sa::DevOut out;

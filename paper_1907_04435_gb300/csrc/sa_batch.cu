@@ -197,7 +197,7 @@ sa_status sa_batch_create(const sa_scene* base, const sa_receivers* grid, const 
             int *bc = nullptr, *run = nullptr;
             e = cudaMalloc(&bc, sizeof(int) * (size_t)grid->R);
             if (e == cudaSuccess) b->owned.push_back(bc);
-            if (e == cudaSuccess) e = cudaMallocAsync(&run, sizeof(int) * (size_t)grid->R, st);
+            if (e == cudaSuccess) e = sa::scratch_alloc(&run, sizeof(int) * (size_t)grid->R, st);
             if (e == cudaSuccess) {
                 sa::DevOut o;
                 memset(&o, 0, sizeof(o));
@@ -347,7 +347,7 @@ sa_status sa_batch_tune(sa_batch* b, int32_t* best_ctas, int32_t* best_run, void
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int n = std::max(1, b->n_items / 8);
     int* scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(&scratch, sizeof(int) * (size_t)std::max<long long>(1, b->I * b->cells_per_interval), st);
+    cudaError_t e = sa::scratch_alloc(&scratch, sizeof(int) * (size_t)std::max<long long>(1, b->I * b->cells_per_interval), st);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -386,7 +386,7 @@ sa_status sa_batch_work_counters(sa_batch* b, uint64_t* counters, void* stream) 
     int* scratch = nullptr;
     cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(uint64_t) * 4, st);
     if (e == cudaSuccess)
-        e = cudaMallocAsync(&scratch, sizeof(int) * (size_t)std::max<long long>(1, b->I * b->cells_per_interval), st);
+        e = sa::scratch_alloc(&scratch, sizeof(int) * (size_t)std::max<long long>(1, b->I * b->cells_per_interval), st);
     if (e == cudaSuccess)
         e = sa::launch_batch(launch_of(b, scratch, nullptr, b->n_items, b->ctas, b->run,
                                        reinterpret_cast<unsigned long long*>(counters)), st);

@@ -218,7 +218,7 @@ cudaError_t launch_iam(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
     if (R == 0) return cudaSuccess;
     if (L < 1 || L > kMaxLevels) return cudaErrorInvalidValue;
     unsigned long long* masks = nullptr;
-    cudaError_t e = cudaMallocAsync(&masks, sizeof(unsigned long long) * (size_t)R, st);
+    cudaError_t e = sa::scratch_alloc(&masks, sizeof(unsigned long long) * (size_t)R, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(masks, 0, sizeof(unsigned long long) * (size_t)R, st);
     Grid g{rc.x0, rc.y0, rc.dx, rc.nx, rc.ny};

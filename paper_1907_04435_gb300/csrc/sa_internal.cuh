@@ -14,6 +14,15 @@
 
 namespace sa {
 
+// Stream-ordered scratch from the library's own memory pool (one per device, created on
+// first use).  The pool keeps up to 4 GiB reserved across synchronisations, so calls that
+// repeat do not map and unmap their scratch every time; free with cudaFreeAsync.
+cudaError_t scratch_alloc_bytes(void** p, size_t bytes, cudaStream_t st);
+template <class T>
+inline cudaError_t scratch_alloc(T** p, size_t bytes, cudaStream_t st) {
+    return scratch_alloc_bytes(reinterpret_cast<void**>(p), bytes, st);
+}
+
 constexpr float kGroundTmin = 1e-3f;     // ground receivers: hits closer than 1 mm ignored
 constexpr float kFacadeOffset = 1e-2f;   // facade receivers start 1 cm along their normal
 constexpr int kMaxBlock = 64;            // steps per accrual block (one uint64 mask)
@@ -302,8 +311,11 @@ cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, lo
                        const int* d_tri_building, LbvhBuild* out, cudaStream_t st);
 
 // Morton order of point receivers: fills perm (sorted -> input index) and sorted origins
+// (synchronises st).  bad_out[0] / [1]: first point with a non-finite position / normal
+// (-1: none); box_out: bounds (lo xyz, hi xyz) of the offset origins.
 cudaError_t sort_points(const float* d_pos, const float* d_nrm, long long n, float4* d_orig,
-                        float4* d_nrm_sorted, int* d_perm, cudaStream_t st);
+                        float4* d_nrm_sorted, int* d_perm, cudaStream_t st, long long* bad_out,
+                        float* box_out);
 
 // radix sort of (key, value) pairs by key (stable, 32-bit keys), in place via scratch
 cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, long long n, cudaStream_t st);

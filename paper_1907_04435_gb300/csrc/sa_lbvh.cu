@@ -8,6 +8,8 @@
 // the subtree size, and traversal needs no stack.
 #include <float.h>
 
+#include <string.h>
+
 #include "sa_internal.cuh"
 
 namespace sa {
@@ -228,14 +230,14 @@ cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, lo
 #define TRY(x) do { e = (x); if (e != cudaSuccess) goto fail; } while (0)
     TRY(cudaMalloc(&out->nodes, sizeof(float4) * 2 * (size_t)n_nodes));
     TRY(cudaMalloc(&out->tris, sizeof(float4) * 3 * (size_t)n));
-    TRY(cudaMallocAsync(&raw, sizeof(float4) * 3 * (size_t)n, st));
-    TRY(cudaMallocAsync(&cbox, sizeof(unsigned) * 6, st));
-    TRY(cudaMallocAsync(&keys, sizeof(unsigned) * (size_t)n, st));
-    TRY(cudaMallocAsync(&vals, sizeof(unsigned) * (size_t)n, st));
-    TRY(cudaMallocAsync(&blo, sizeof(float4) * (size_t)n_nodes, st));
-    TRY(cudaMallocAsync(&bhi, sizeof(float4) * (size_t)n_nodes, st));
-    TRY(cudaMallocAsync(&flags, sizeof(unsigned) * (size_t)n, st));
-    TRY(cudaMallocAsync(&ibuf, sizeof(int) * 6 * (size_t)n_nodes, st));
+    TRY(sa::scratch_alloc(&raw, sizeof(float4) * 3 * (size_t)n, st));
+    TRY(sa::scratch_alloc(&cbox, sizeof(unsigned) * 6, st));
+    TRY(sa::scratch_alloc(&keys, sizeof(unsigned) * (size_t)n, st));
+    TRY(sa::scratch_alloc(&vals, sizeof(unsigned) * (size_t)n, st));
+    TRY(sa::scratch_alloc(&blo, sizeof(float4) * (size_t)n_nodes, st));
+    TRY(sa::scratch_alloc(&bhi, sizeof(float4) * (size_t)n_nodes, st));
+    TRY(sa::scratch_alloc(&flags, sizeof(unsigned) * (size_t)n, st));
+    TRY(sa::scratch_alloc(&ibuf, sizeof(int) * 6 * (size_t)n_nodes, st));
     {
         int* left = ibuf;
         int* right = ibuf + n_nodes;
@@ -287,7 +289,7 @@ namespace {
 
 __global__ void k_points_prep(const float* __restrict__ pos, const float* __restrict__ nrm,
                               long long n, float4* __restrict__ orig_unsorted,
-                              unsigned* __restrict__ box) {
+                              unsigned* __restrict__ box, int* __restrict__ bad) {
     __shared__ unsigned s_lo[3], s_hi[3];
     if (threadIdx.x < 3) { s_lo[threadIdx.x] = 0xffffffffu; s_hi[threadIdx.x] = 0u; }
     __syncthreads();
@@ -296,7 +298,10 @@ __global__ void k_points_prep(const float* __restrict__ pos, const float* __rest
         float o[3];
         float tmin = kGroundTmin;
         for (int k = 0; k < 3; ++k) o[k] = pos[3 * i + k];
+        if (!(isfinite(o[0]) && isfinite(o[1]) && isfinite(o[2]))) atomicMin(&bad[0], (int)i);
         if (nrm) {
+            const float n0 = nrm[3 * i], n1 = nrm[3 * i + 1], n2 = nrm[3 * i + 2];
+            if (!(isfinite(n0) && isfinite(n1) && isfinite(n2))) atomicMin(&bad[1], (int)i);
             for (int k = 0; k < 3; ++k) o[k] = fmaf(kFacadeOffset, nrm[3 * i + k], o[k]);
             tmin = 0.f;
         }
@@ -354,25 +359,39 @@ __global__ void k_points_gather(const float4* __restrict__ o, const float* __res
 
 }  // namespace
 
+namespace {
+float o2f_host(unsigned u) {
+    const unsigned v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float f;
+    memcpy(&f, &v, sizeof(f));
+    return f;
+}
+}  // namespace
+
 cudaError_t sort_points(const float* d_pos, const float* d_nrm, long long n, float4* d_orig,
-                        float4* d_nrm_sorted, int* d_perm, cudaStream_t st) {
+                        float4* d_nrm_sorted, int* d_perm, cudaStream_t st, long long* bad_out,
+                        float* box_out) {
+    bad_out[0] = bad_out[1] = -1;
+    for (int k = 0; k < 6; ++k) box_out[k] = 0.f;
     if (n == 0) return cudaSuccess;
     float4* tmp = nullptr;
     unsigned *box = nullptr, *keys = nullptr, *vals = nullptr;
-    cudaError_t e = cudaMallocAsync(&tmp, sizeof(float4) * (size_t)n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&box, sizeof(unsigned) * 6, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&keys, sizeof(unsigned) * (size_t)n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&vals, sizeof(unsigned) * (size_t)n, st);
+    cudaError_t e = sa::scratch_alloc(&tmp, sizeof(float4) * (size_t)n, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&box, sizeof(unsigned) * 8, st);   // box, bad[2]
+    if (e == cudaSuccess) e = sa::scratch_alloc(&keys, sizeof(unsigned) * (size_t)n, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&vals, sizeof(unsigned) * (size_t)n, st);
+    unsigned h[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0x7fffffffu, 0x7fffffffu};
     if (e == cudaSuccess) {
-        unsigned init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
-        e = cudaMemcpyAsync(box, init, sizeof(init), cudaMemcpyHostToDevice, st);
-        k_points_prep<<<nblk(n), kThreads, 0, st>>>(d_pos, d_nrm, n, tmp, box);
+        e = cudaMemcpyAsync(box, h, sizeof(h), cudaMemcpyHostToDevice, st);
+        k_points_prep<<<nblk(n), kThreads, 0, st>>>(d_pos, d_nrm, n, tmp, box,
+                                                     reinterpret_cast<int*>(box + 6));
         k_points_morton<<<nblk(n), kThreads, 0, st>>>(tmp, d_nrm, n, box, keys, vals);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, n, st);
         k_points_gather<<<nblk(n), kThreads, 0, st>>>(tmp, d_nrm, vals, n, d_orig,
                                                        d_nrm ? d_nrm_sorted : nullptr, d_perm);
         if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, box, sizeof(h), cudaMemcpyDeviceToHost, st);
         cudaError_t e2 = cudaStreamSynchronize(st);
         if (e == cudaSuccess) e = e2;
     }
@@ -380,6 +399,11 @@ cudaError_t sort_points(const float* d_pos, const float* d_nrm, long long n, flo
     if (box) cudaFreeAsync(box, st);
     if (keys) cudaFreeAsync(keys, st);
     if (vals) cudaFreeAsync(vals, st);
+    if (e == cudaSuccess) {
+        for (int k = 0; k < 6; ++k) box_out[k] = o2f_host(h[k]);
+        if (h[6] != 0x7fffffffu) bad_out[0] = (long long)h[6];
+        if (h[7] != 0x7fffffffu) bad_out[1] = (long long)h[7];
+    }
     return e;
 }
 

@@ -1,0 +1,55 @@
+// sa_pool.cu -- the library's stream-ordered scratch pool.
+//
+// Scratch (bins, masks, sort buffers) is allocated and freed on the caller's stream within
+// each call.  The default pool would return that memory to the device at every
+// synchronisation, so a repeated call would map it again each time; this pool keeps up to
+// kKeep bytes reserved instead.
+#include <mutex>
+#include <vector>
+
+#include "sa_internal.cuh"
+
+namespace sa {
+
+namespace {
+constexpr unsigned long long kKeep = 4ull << 30;
+std::mutex g_pool_mu;
+std::vector<cudaMemPool_t> g_pools;   // by device ordinal; null until first use
+
+cudaError_t pool_of_current_device(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        unsigned long long keep = kKeep;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pools[dev] = pool;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t scratch_alloc_bytes(void** p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = pool_of_current_device(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+}  // namespace sa

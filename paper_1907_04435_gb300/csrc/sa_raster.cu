@@ -673,7 +673,7 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
     int* best = out.continuous;
     int* best_scratch = nullptr;
     if (!best) {
-        e = cudaMallocAsync(&best_scratch, sizeof(int) * (size_t)R, st);
+        e = sa::scratch_alloc(&best_scratch, sizeof(int) * (size_t)R, st);
         if (e != cudaSuccess) return e;
         best = best_scratch;
     }
@@ -683,11 +683,11 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
     int *bins = nullptr, *order = nullptr;
     size_t bins_cap = 0;
     const size_t nc = (size_t)max_chunk_blocks * n_tiles;
-    e = cudaMallocAsync(&counts, sizeof(unsigned) * nc, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&offsets, sizeof(unsigned) * nc, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&cursor, sizeof(unsigned) * nc, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_total, sizeof(unsigned), st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&order, sizeof(int) * (size_t)n_tiles, st);
+    e = sa::scratch_alloc(&counts, sizeof(unsigned) * nc, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&offsets, sizeof(unsigned) * nc, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&cursor, sizeof(unsigned) * nc, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&d_total, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&order, sizeof(int) * (size_t)n_tiles, st);
     const int tpb = 128;
     for (int b0 = 0; b0 < sun.n_blocks && e == cudaSuccess; b0 += chunk) {
         const int nbc = (sun.n_blocks - b0) < chunk ? (sun.n_blocks - b0) : chunk;
@@ -712,7 +712,7 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
             if (total > bins_cap) {
                 if (bins) cudaFreeAsync(bins, st);
                 bins_cap = (size_t)total + total / 4 + 1024;
-                e = cudaMallocAsync(&bins, sizeof(int) * bins_cap, st);
+                e = sa::scratch_alloc(&bins, sizeof(int) * bins_cap, st);
                 if (e != cudaSuccess) { bins = nullptr; break; }
             }
             if (total > 0) k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, offsets, cursor, bins);
@@ -865,8 +865,8 @@ cudaError_t build_bins(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
     if (e == cudaSuccess) e = cudaMalloc(offsets, sizeof(unsigned) * nc);
     unsigned* cursor = nullptr;
     unsigned* d_total = nullptr;
-    if (e == cudaSuccess) e = cudaMallocAsync(&cursor, sizeof(unsigned) * nc, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_total, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&cursor, sizeof(unsigned) * nc, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&d_total, sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(*counts, 0, sizeof(unsigned) * nc, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(unsigned) * nc, st);
     unsigned total = 0;

@@ -519,9 +519,9 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
     cudaError_t e = cudaSuccess;
     unsigned long long* masks = nullptr;
     int *run = nullptr, *best = nullptr;
-    e = cudaMallocAsync(&masks, sizeof(unsigned long long) * (size_t)R * nbc_max, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&run, sizeof(int) * (size_t)R, st);
-    if (e == cudaSuccess && !out.continuous) e = cudaMallocAsync(&best, sizeof(int) * (size_t)R, st);
+    e = sa::scratch_alloc(&masks, sizeof(unsigned long long) * (size_t)R * nbc_max, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&run, sizeof(int) * (size_t)R, st);
+    if (e == cudaSuccess && !out.continuous) e = sa::scratch_alloc(&best, sizeof(int) * (size_t)R, st);
     if (e == cudaSuccess && out.accumulate_into && !out.continuous)
         e = cudaMemsetAsync(best, 0, sizeof(int) * (size_t)R, st);
     int* bestp = out.continuous ? out.continuous : best;
@@ -604,18 +604,18 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
         const size_t nt = (size_t)tiles;
 #define TRYB(x) do { if (e == cudaSuccess) e = (x); } while (0)
         TRYB(cudaMemsetAsync(masks, 0, sizeof(unsigned long long) * (size_t)R * nbc, st));
-        TRYB(cudaMallocAsync(&d_runs, sizeof(RunLight) * hr.size(), st));
-        TRYB(cudaMallocAsync(&d_tile_run, sizeof(int) * nt, st));
-        TRYB(cudaMallocAsync(&tc, sizeof(unsigned) * nt, st));
-        TRYB(cudaMallocAsync(&toff, sizeof(unsigned) * nt, st));
-        TRYB(cudaMallocAsync(&tcur, sizeof(unsigned) * nt, st));
-        TRYB(cudaMallocAsync(&rcn, sizeof(unsigned) * nt, st));
-        TRYB(cudaMallocAsync(&roff, sizeof(unsigned) * nt, st));
-        TRYB(cudaMallocAsync(&rcur, sizeof(unsigned) * nt, st));
-        TRYB(cudaMallocAsync(&d_total, 2 * sizeof(unsigned), st));   // bin total, tiles with work
-        TRYB(cudaMallocAsync(&hist, sizeof(unsigned) * kOrderBuckets, st));
-        TRYB(cudaMallocAsync(&order, sizeof(int) * nt, st));
-        TRYB(cudaMallocAsync(&rbins, sizeof(int) * (size_t)R * n_runs, st));
+        TRYB(sa::scratch_alloc(&d_runs, sizeof(RunLight) * hr.size(), st));
+        TRYB(sa::scratch_alloc(&d_tile_run, sizeof(int) * nt, st));
+        TRYB(sa::scratch_alloc(&tc, sizeof(unsigned) * nt, st));
+        TRYB(sa::scratch_alloc(&toff, sizeof(unsigned) * nt, st));
+        TRYB(sa::scratch_alloc(&tcur, sizeof(unsigned) * nt, st));
+        TRYB(sa::scratch_alloc(&rcn, sizeof(unsigned) * nt, st));
+        TRYB(sa::scratch_alloc(&roff, sizeof(unsigned) * nt, st));
+        TRYB(sa::scratch_alloc(&rcur, sizeof(unsigned) * nt, st));
+        TRYB(sa::scratch_alloc(&d_total, 2 * sizeof(unsigned), st));   // bin total, tiles with work
+        TRYB(sa::scratch_alloc(&hist, sizeof(unsigned) * kOrderBuckets, st));
+        TRYB(sa::scratch_alloc(&order, sizeof(int) * nt, st));
+        TRYB(sa::scratch_alloc(&rbins, sizeof(int) * (size_t)R * n_runs, st));
         TRYB(cudaMemcpyAsync(d_runs, hr.data(), sizeof(RunLight) * hr.size(), cudaMemcpyHostToDevice, st));
         TRYB(cudaMemcpyAsync(d_tile_run, tile_run.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, st));
         TRYB(cudaMemsetAsync(tc, 0, sizeof(unsigned) * nt, st));
@@ -642,7 +642,7 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
         TRYB(cudaMemcpyAsync(totals, d_total, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         TRYB(cudaStreamSynchronize(st));
         const unsigned total = totals[0], work_tiles = totals[1];
-        TRYB(cudaMallocAsync(&tbins, sizeof(int) * ((size_t)total + 1), st));
+        TRYB(sa::scratch_alloc(&tbins, sizeof(int) * ((size_t)total + 1), st));
         if (e == cudaSuccess) {
             if (sc.T > 0 && total > 0)
                 k_lt_bin<<<gt, 128, 0, st>>>(sc, sun.steps, d_runs, n_runs, true, nullptr, toff, tcur, tbins);

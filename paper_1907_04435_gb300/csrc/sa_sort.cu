@@ -169,7 +169,7 @@ cudaError_t exclusive_scan_u32(unsigned* data, long long n, unsigned* d_total, c
     }
     const int np = (int)((n + kScanTile - 1) / kScanTile);
     unsigned* partial = nullptr;
-    cudaError_t e = cudaMallocAsync(&partial, sizeof(unsigned) * np, st);
+    cudaError_t e = sa::scratch_alloc(&partial, sizeof(unsigned) * np, st);
     if (e != cudaSuccess) return e;
     k_scan_reduce<<<np, kScanThreads, 0, st>>>(data, n, partial);
     k_scan_partials<<<1, kScanThreads, 0, st>>>(partial, np, d_total);
@@ -198,9 +198,9 @@ cudaError_t radix_sort_pairs(unsigned* keys, unsigned* vals, long long n, cudaSt
     if (n <= 1) return cudaSuccess;
     const int n_tiles = (int)((n + kSortTile - 1) / kSortTile);
     unsigned *k2 = nullptr, *v2 = nullptr, *hist = nullptr;
-    cudaError_t e = cudaMallocAsync(&k2, sizeof(unsigned) * n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&v2, sizeof(unsigned) * n, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&hist, sizeof(unsigned) * kRadix * (size_t)n_tiles, st);
+    cudaError_t e = sa::scratch_alloc(&k2, sizeof(unsigned) * n, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&v2, sizeof(unsigned) * n, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&hist, sizeof(unsigned) * kRadix * (size_t)n_tiles, st);
     if (e != cudaSuccess) {
         if (k2) cudaFreeAsync(k2, st);
         if (v2) cudaFreeAsync(v2, st);

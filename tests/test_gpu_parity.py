@@ -274,3 +274,21 @@ def test_accrual_maps_do_not_depend_on_the_run_length(cuda_lib, closed):
                 assert np.array_equal(got[0], want[0]) and np.array_equal(got[2], want[2]), run
         finally:
             B.sa_set_option(key, old)
+
+
+def test_non_finite_points_are_rejected_and_the_context_stays_usable(cuda_lib):
+    B = cuda_lib
+    pos = np.random.default_rng(0).uniform(0, 50, (1000, 3)).astype(np.float32)
+    nrm = np.tile(np.array([[1.0, 0.0, 0.0]], np.float32), (1000, 1))
+    bad = pos.copy()
+    bad[617, 1] = np.nan
+    with pytest.raises(B.SAError) as ex:
+        B.Receivers.points(bad, nrm)
+    assert ex.value.status == -5 and "position 617" in str(ex.value)
+    badn = nrm.copy()
+    badn[42, 2] = np.inf
+    with pytest.raises(B.SAError) as ex:
+        B.Receivers.points(torch.from_numpy(pos).cuda(), torch.from_numpy(badn).cuda())
+    assert ex.value.status == -5 and "normal 42" in str(ex.value)
+    ok = B.Receivers.points(pos, nrm)
+    assert ok.R == 1000
