@@ -185,6 +185,85 @@ __device__ __forceinline__ bool hit_box(const float3& o, float ix, float iy, flo
     return tn <= tf * 1.0000005f;
 }
 
+// Plücker form of the exact ray/triangle test for one origin and many steps.  For the
+// line through o along d, the side of edge v -> v' is  d . ((v - o) x (v' - o)):  the
+// moment m_e = (v - o) x (v' - o) depends only on the origin and the edge, so a triangle
+// is set up once per receiver and each step costs three dot products.  The cross product
+// is formed from correctly rounded products and differences, so the reversed edge gives
+// exactly the negated moment (up to the sign of zero): a line through an edge shared by
+// two triangles sees exactly negated values and is inside at least one (watertight; zero
+// counts as inside on both sides).  The hit distance t = ((a - o) . n) / (d . n) must
+// exceed t_min.  Every quantity is formed with explicit roundings, so all kernels that use
+// these helpers take identical decisions.
+struct PluckerTri {
+    float m[3][3];
+    float nx, ny, nz, aon;
+};
+
+__device__ __forceinline__ void plucker_edge(const float3& o, const float4& v, const float4& w,
+                                             float* m) {
+    const float px = __fsub_rn(v.x, o.x), py = __fsub_rn(v.y, o.y), pz = __fsub_rn(v.z, o.z);
+    const float qx = __fsub_rn(w.x, o.x), qy = __fsub_rn(w.y, o.y), qz = __fsub_rn(w.z, o.z);
+    m[0] = __fsub_rn(__fmul_rn(py, qz), __fmul_rn(pz, qy));
+    m[1] = __fsub_rn(__fmul_rn(pz, qx), __fmul_rn(px, qz));
+    m[2] = __fsub_rn(__fmul_rn(px, qy), __fmul_rn(py, qx));
+}
+
+// the triangle's (unnormalised) normal (b - a) x (c - a); independent of the origin
+__device__ __forceinline__ float3 plucker_normal(const float4& a, const float4& b, const float4& c) {
+    const float ux = __fsub_rn(b.x, a.x), uy = __fsub_rn(b.y, a.y), uz = __fsub_rn(b.z, a.z);
+    const float vx = __fsub_rn(c.x, a.x), vy = __fsub_rn(c.y, a.y), vz = __fsub_rn(c.z, a.z);
+    return make_float3(__fsub_rn(__fmul_rn(uy, vz), __fmul_rn(uz, vy)),
+                       __fsub_rn(__fmul_rn(uz, vx), __fmul_rn(ux, vz)),
+                       __fsub_rn(__fmul_rn(ux, vy), __fmul_rn(uy, vx)));
+}
+
+// set-up with the normal given (from plucker_normal of the same triangle)
+__device__ __forceinline__ PluckerTri plucker_setup_n(const float3& o, const float4& a,
+                                                      const float4& b, const float4& c,
+                                                      const float3& n) {
+    PluckerTri p;
+    plucker_edge(o, a, b, p.m[0]);
+    plucker_edge(o, b, c, p.m[1]);
+    plucker_edge(o, c, a, p.m[2]);
+    p.nx = n.x; p.ny = n.y; p.nz = n.z;
+    p.aon = fmaf(n.z, __fsub_rn(a.z, o.z), fmaf(n.y, __fsub_rn(a.y, o.y), __fmul_rn(n.x, __fsub_rn(a.x, o.x))));
+    return p;
+}
+
+__device__ __forceinline__ PluckerTri plucker_setup(const float3& o, const float4& a,
+                                                    const float4& b, const float4& c) {
+    return plucker_setup_n(o, a, b, c, plucker_normal(a, b, c));
+}
+
+// d . m and d . n in a fixed order, so a negated m gives an exactly negated value
+__device__ __forceinline__ bool plucker_hit(const PluckerTri& p, float dx, float dy, float dz,
+                                            float tmin) {
+    const float s0 = fmaf(dz, p.m[0][2], fmaf(dy, p.m[0][1], __fmul_rn(dx, p.m[0][0])));
+    const float s1 = fmaf(dz, p.m[1][2], fmaf(dy, p.m[1][1], __fmul_rn(dx, p.m[1][0])));
+    const float s2 = fmaf(dz, p.m[2][2], fmaf(dy, p.m[2][1], __fmul_rn(dx, p.m[2][0])));
+    const bool inside = (s0 >= 0.f && s1 >= 0.f && s2 >= 0.f) || (s0 <= 0.f && s1 <= 0.f && s2 <= 0.f);
+    if (!inside) return false;
+    const float nd = fmaf(dz, p.nz, fmaf(dy, p.ny, __fmul_rn(dx, p.nx)));
+    if (nd == 0.f) return false;
+    const float lim = __fmul_rn(tmin, nd);
+    return nd > 0.f ? (p.aon > lim) : (p.aon < lim);
+}
+
+// the same decision as plucker_hit, evaluated without early exits, so the steps of a run
+// form independent chains
+__device__ __forceinline__ bool plucker_hit_all(const PluckerTri& p, float dx, float dy, float dz,
+                                                float tmin) {
+    const float s0 = fmaf(dz, p.m[0][2], fmaf(dy, p.m[0][1], __fmul_rn(dx, p.m[0][0])));
+    const float s1 = fmaf(dz, p.m[1][2], fmaf(dy, p.m[1][1], __fmul_rn(dx, p.m[1][0])));
+    const float s2 = fmaf(dz, p.m[2][2], fmaf(dy, p.m[2][1], __fmul_rn(dx, p.m[2][0])));
+    const float nd = fmaf(dz, p.nz, fmaf(dy, p.ny, __fmul_rn(dx, p.nx)));
+    const bool inside = fminf(s0, fminf(s1, s2)) >= 0.f || fmaxf(s0, fmaxf(s1, s2)) <= 0.f;
+    const float lim = __fmul_rn(tmin, nd);
+    const bool ahead = (nd > 0.f && p.aon > lim) || (nd < 0.f && p.aon < lim);
+    return inside && ahead;
+}
+
 // --------------------------------------------------------------- host-side launchers
 // Receivers as the kernels see them.
 struct DevRecv {

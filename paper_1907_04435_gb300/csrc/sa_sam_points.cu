@@ -143,40 +143,6 @@ __global__ void k_lr_bin(const float4* __restrict__ orig, long long R,
     }
 }
 
-// Plücker test, as in the ray-traced accrual (sa_trace.cu): moments of the canonically
-// ordered edges seen from the origin, then per step three dot products and t > t_min.
-struct PTri {
-    float m[3][3];
-    float nx, ny, nz, aon;
-};
-
-__device__ __forceinline__ void p_edge(const float3& o, const float4& a, const float4& b, float* m) {
-    const bool keep = a.x < b.x || (a.x == b.x && (a.y < b.y || (a.y == b.y && a.z < b.z)));
-    const float4& v = keep ? a : b;
-    const float4& w = keep ? b : a;
-    const float px = v.x - o.x, py = v.y - o.y, pz = v.z - o.z;
-    const float qx = w.x - o.x, qy = w.y - o.y, qz = w.z - o.z;
-    const float sg = keep ? 1.f : -1.f;
-    m[0] = sg * __fsub_rn(__fmul_rn(py, qz), __fmul_rn(pz, qy));
-    m[1] = sg * __fsub_rn(__fmul_rn(pz, qx), __fmul_rn(px, qz));
-    m[2] = sg * __fsub_rn(__fmul_rn(px, qy), __fmul_rn(py, qx));
-}
-
-// Does the ray from the set-up origin along d meet the triangle beyond t_min?  The three
-// Plücker signs must agree (the line passes through the triangle) and the plane must be
-// hit at t = aon / (n . d) > t_min.  Evaluated without early exits, so the steps of a run
-// form independent chains.
-__device__ __forceinline__ bool p_hit_all(const PTri& p, float dx, float dy, float dz, float tmin) {
-    const float s0 = fmaf(dz, p.m[0][2], fmaf(dy, p.m[0][1], dx * p.m[0][0]));
-    const float s1 = fmaf(dz, p.m[1][2], fmaf(dy, p.m[1][1], dx * p.m[1][0]));
-    const float s2 = fmaf(dz, p.m[2][2], fmaf(dy, p.m[2][1], dx * p.m[2][0]));
-    const float nd = fmaf(dz, p.nz, fmaf(dy, p.ny, dx * p.nx));
-    const bool inside = fminf(s0, fminf(s1, s2)) >= 0.f || fmaxf(s0, fmaxf(s1, s2)) <= 0.f;
-    const float lim = tmin * nd;
-    const bool ahead = (nd > 0.f && p.aon > lim) || (nd < 0.f && p.aon < lim);
-    return inside && ahead;
-}
-
 struct TileArgs {
     DevScene sc;
     const StepConst* steps;
@@ -234,8 +200,9 @@ __device__ __forceinline__ void light_edges(const float* pa, const float* pb, fl
 
 template <bool COUNT>
 __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int lane,
-                                            const float4* s_tri, const unsigned* s_front,
-                                            const float4* s_o, unsigned* s_m, const float (*s_d)[4],
+                                            const float4* s_tri, const float4* s_n,
+                                            const unsigned* s_front, const float4* s_o,
+                                            unsigned* s_m, const float (*s_d)[4],
                                             int kn, unsigned long long& n_pair,
                                             unsigned long long& n_test) {
     if (lane >= n) return;
@@ -246,22 +213,14 @@ __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int 
     const float4 a = s_tri[3 * t], b = s_tri[3 * t + 1], c = s_tri[3 * t + 2];
     const unsigned want = s_front[t];
     if (COUNT) ++n_pair;
-    PTri pt;
-    p_edge(o, a, b, pt.m[0]);
-    p_edge(o, b, c, pt.m[1]);
-    p_edge(o, c, a, pt.m[2]);
-    const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
-    const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
-    pt.nx = uy * vz - uz * vy;
-    pt.ny = uz * vx - ux * vz;
-    pt.nz = ux * vy - uy * vx;
-    pt.aon = pt.nx * (a.x - o.x) + pt.ny * (a.y - o.y) + pt.nz * (a.z - o.z);
+    const float4 nv = s_n[t];
+    const PluckerTri pt = plucker_setup_n(o, a, b, c, make_float3(nv.x, nv.y, nv.z));
     // every step of the run is tested without branches (independent chains the scheduler
     // can interleave); steps the triangle turns away from are masked off afterwards
     unsigned m = 0;
 #pragma unroll 4
     for (int k = 0; k < kn; ++k)
-        if (p_hit_all(pt, s_d[k][0], s_d[k][1], s_d[k][2], p.w)) m |= 1u << k;
+        if (plucker_hit_all(pt, s_d[k][0], s_d[k][1], s_d[k][2], p.w)) m |= 1u << k;
     m &= want;
     if (COUNT) n_test += (unsigned)__popc(want);
     if (m) atomicOr(&s_m[who], m);
@@ -272,6 +231,7 @@ __global__ void __launch_bounds__(kTileThreads)
 k_sam_tile(TileArgs ta) {
     constexpr int kWarps = kTileThreads / 32;
     __shared__ float4 s_tri[kTriChunk * 3];
+    __shared__ float4 s_n[kTriChunk];              // triangle normals (origin-independent set-up)
     __shared__ float4 s_box[kTriChunk];            // light box (amin, amax, bmin, bmax)
     __shared__ float4 s_edge[3][kTriChunk];        // light-space edge lines (nx, ny, c)
     __shared__ float s_ztop[kTriChunk];            // highest vertex z
@@ -304,6 +264,8 @@ k_sam_tile(TileArgs ta) {
             const float4 a = __ldg(&ta.sc.tris[3 * t]), b = __ldg(&ta.sc.tris[3 * t + 1]),
                          c = __ldg(&ta.sc.tris[3 * t + 2]);
             s_tri[3 * i] = a; s_tri[3 * i + 1] = b; s_tri[3 * i + 2] = c;
+            const float3 nrm = plucker_normal(a, b, c);
+            s_n[i] = make_float4(nrm.x, nrm.y, nrm.z, 0.f);
             float pa[3], pb[3];
             light_ab(rl, a.x, a.y, a.z, &pa[0], &pb[0]);
             light_ab(rl, b.x, b.y, b.z, &pa[1], &pb[1]);
@@ -384,14 +346,14 @@ k_sam_tile(TileArgs ta) {
                 n += __popc(bal);
                 if (n >= 32) {
                     __syncwarp();
-                    drain_pairs<COUNT>(q + (n - 32), 32, lane, s_tri, s_front, s_o, s_m, s_d, kn,
-                                       n_pair, n_test);
+                    drain_pairs<COUNT>(q + (n - 32), 32, lane, s_tri, s_n, s_front, s_o, s_m, s_d,
+                                       kn, n_pair, n_test);
                     n -= 32;
                     __syncwarp();
                 }
             }
             __syncwarp();
-            drain_pairs<COUNT>(q, n, lane, s_tri, s_front, s_o, s_m, s_d, kn, n_pair, n_test);
+            drain_pairs<COUNT>(q, n, lane, s_tri, s_n, s_front, s_o, s_m, s_d, kn, n_pair, n_test);
             __syncwarp();
             const unsigned m = s_m[threadIdx.x];
             if (live && m) atomicOr(&ta.masks[(long long)rl.blk * ta.R + s], (unsigned long long)m << rl.k0);

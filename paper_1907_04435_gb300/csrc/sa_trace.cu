@@ -254,61 +254,6 @@ __device__ __forceinline__ bool hit_tri_rt(const float3& o, const float4& a, con
 }
 
 
-// Plücker form of the exact ray/triangle test for one origin and many steps.  For the
-// line through o along d, the side of edge v -> v' is  d . ((v - o) x (v' - o)):  the
-// moment m_e = (v - o) x (v' - o) depends only on the origin and the edge, so a triangle
-// is set up once per receiver and each step costs three dot products.  Edges are taken in
-// a canonical vertex order (the other order negates m exactly), so a line through an edge
-// shared by two triangles sees exactly negated values and is inside at least one
-// (watertight, zero counts as inside).  The hit distance t = ((a - o) . n) / (d . n) must
-// exceed t_min.
-struct PluckerTri {
-    float m[3][3];
-    float nx, ny, nz, aon;
-};
-
-__device__ __forceinline__ void plucker_edge(const float3& o, const float4& a, const float4& b,
-                                             float* m) {
-    const bool keep = a.x < b.x || (a.x == b.x && (a.y < b.y || (a.y == b.y && a.z < b.z)));
-    const float4& v = keep ? a : b;
-    const float4& w = keep ? b : a;
-    const float px = v.x - o.x, py = v.y - o.y, pz = v.z - o.z;
-    const float qx = w.x - o.x, qy = w.y - o.y, qz = w.z - o.z;
-    const float mx = __fsub_rn(__fmul_rn(py, qz), __fmul_rn(pz, qy));
-    const float my = __fsub_rn(__fmul_rn(pz, qx), __fmul_rn(px, qz));
-    const float mz = __fsub_rn(__fmul_rn(px, qy), __fmul_rn(py, qx));
-    const float sg = keep ? 1.f : -1.f;
-    m[0] = sg * mx; m[1] = sg * my; m[2] = sg * mz;
-}
-
-__device__ __forceinline__ PluckerTri plucker_setup(const float3& o, const float4& a,
-                                                    const float4& b, const float4& c) {
-    PluckerTri p;
-    plucker_edge(o, a, b, p.m[0]);
-    plucker_edge(o, b, c, p.m[1]);
-    plucker_edge(o, c, a, p.m[2]);
-    const float ux = b.x - a.x, uy = b.y - a.y, uz = b.z - a.z;
-    const float vx = c.x - a.x, vy = c.y - a.y, vz = c.z - a.z;
-    p.nx = uy * vz - uz * vy;
-    p.ny = uz * vx - ux * vz;
-    p.nz = ux * vy - uy * vx;
-    p.aon = p.nx * (a.x - o.x) + p.ny * (a.y - o.y) + p.nz * (a.z - o.z);
-    return p;
-}
-
-__device__ __forceinline__ bool plucker_hit(const PluckerTri& p, float dx, float dy, float dz,
-                                            float tmin) {
-    // d . m computed in a fixed order, so a negated m gives an exactly negated value
-    const float s0 = fmaf(dz, p.m[0][2], fmaf(dy, p.m[0][1], dx * p.m[0][0]));
-    const float s1 = fmaf(dz, p.m[1][2], fmaf(dy, p.m[1][1], dx * p.m[1][0]));
-    const float s2 = fmaf(dz, p.m[2][2], fmaf(dy, p.m[2][1], dx * p.m[2][0]));
-    const bool inside = (s0 >= 0.f && s1 >= 0.f && s2 >= 0.f) || (s0 <= 0.f && s1 <= 0.f && s2 <= 0.f);
-    if (!inside) return false;
-    const float nd = fmaf(dz, p.nz, fmaf(dy, p.ny, dx * p.nx));
-    if (nd == 0.f) return false;
-    return nd > 0.f ? (p.aon > tmin * nd) : (p.aon < tmin * nd);
-}
-
 template <bool COUNT>
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_accrual(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
