@@ -309,7 +309,7 @@ def count_launches(scene, sun, grid, fac):
     chunks = (sun.n_blocks + 63) // 64
     n = chunks * 7
     if fac:
-        run = min(16, max(1, B_option_run()))   # steps per light-space map
+        run = min(32, max(1, B_option_run()))   # steps per light-space map
         per_block = fac.R * (4 * ((64 + run - 1) // run) + 8)
         fchunk = max(1, min(64, (1 << 30) // max(1, per_block)))
         n += 15 * ((sun.n_blocks + fchunk - 1) // fchunk)

@@ -91,11 +91,12 @@ int32_t sa_version(void);
  *   traversal per lane, 0 the default (per lane for the sweep, warp-coherent for the
  *   accrual, the faster of the two on the district workload).  Results do not depend on
  *   the option.
- *   SA_OPT_RASTER_RUN: steps the ground accrual raster tests per cell set-up (1..32,
- *   default 24), and SA_OPT_POINT_RUN: steps per light-space map of point receivers
- *   (1..16, default 16); the defaults are the fastest on the district workload.  Longer
- *   runs amortise the set-up, shorter runs bound the swept region more tightly.  Results
- *   do not depend on either option.
+ *   SA_OPT_RASTER_RUN: at most this many steps the ground accrual raster tests per cell
+ *   set-up (1..32, default 24), and SA_OPT_POINT_RUN: at most this many steps per
+ *   light-space map of point receivers (1..32, default 20); each block is split into
+ *   runs of balanced lengths within the bound.  The defaults are the fastest on the
+ *   district workload.  Longer runs amortise the set-up, shorter runs bound the swept
+ *   region more tightly.  Results do not depend on either option.
  *   SA_OPT_KERNEL_TIMING: 1 records a CUDA event pair on the launching stream around every
  *   launch of the main kernels (below), 0 (default) records nothing.  Launches inside a
  *   stream capture, and those of sa_accumulate_grid_noalloc, are never timed.

@@ -430,7 +430,7 @@ sa_status sa_set_option(int32_t key, int32_t value) {
             sa::set_raster_run(value);
             return SA_OK;
         case SA_OPT_POINT_RUN:
-            if (value < 1 || value > 16) return fail(SA_ERR_INVALID_ARG, "sa_set_option: point run %d", value);
+            if (value < 1 || value > 32) return fail(SA_ERR_INVALID_ARG, "sa_set_option: point run %d", value);
             sa::set_point_run(value);
             return SA_OK;
         case SA_OPT_KERNEL_TIMING:

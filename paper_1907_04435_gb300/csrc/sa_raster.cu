@@ -248,12 +248,12 @@ __device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeRef
 // bounds the run's swept projection, enumerates the covered cells row by row and tests
 // the run's steps per cell; step bits are ORed into sm.mask.
 template <bool COUNT, bool CULL>
-__device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int kSub, int K,
+__device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int K,
                                             float inv_dx, unsigned long long& n_cell,
                                             unsigned long long& n_test) {
     const int lane = threadIdx.x & 31;
-    const int t = un / nsub, sub = un - t * nsub, k0 = sub * kSub;
-    const int kn = min(kSub, K - k0);
+    const int t = un / nsub, sub = un - t * nsub;
+    const int k0 = sub * K / nsub, kn = (sub + 1) * K / nsub - k0;     // balanced runs
     const unsigned run_bits = (kn >= 32) ? 0xffffffffu : ((1u << kn) - 1u);
     const unsigned fr = (unsigned)(sm.front[t] >> k0) & run_bits;
     const unsigned bk = CULL ? 0u : ((unsigned)(sm.back[t] >> k0) & run_bits);
@@ -370,7 +370,7 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
     }
     __syncthreads();
     if (threadIdx.x < nsub) {
-        const int k0 = threadIdx.x * kSub, k1 = min(k0 + kSub, K);
+        const int k0 = threadIdx.x * K / nsub, k1 = (threadIdx.x + 1) * K / nsub;
         float4 b = make_float4(3.4e38f, -3.4e38f, 3.4e38f, -3.4e38f);
         for (int k = k0; k < k1; ++k) {
             const float2 u = sm.u[k];
@@ -426,7 +426,7 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
         // warps that would otherwise wait for its warp at the next barrier
         int un = warp;
         while (un < units) {
-            raster_unit<COUNT, CULL>(sm, un, nsub, kSub, K, inv_dx, n_cell, n_test);
+            raster_unit<COUNT, CULL>(sm, un, nsub, K, inv_dx, n_cell, n_test);
             int nx = 0;
             if (lane == 0) nx = atomicAdd(&sm.next_unit, 1);
             un = __shfl_sync(0xffffffffu, nx, 0);

@@ -28,7 +28,7 @@ namespace sa {
 
 namespace {
 
-constexpr int kRunMax = 16;
+constexpr int kRunMax = 32;
 constexpr int kTileThreads = 128;
 constexpr int kTriChunk = 128;
 
@@ -456,7 +456,7 @@ void normalize3(double* v) {
     v[0] /= n; v[1] /= n; v[2] /= n;
 }
 
-int g_point_run = 16;
+int g_point_run = 20;
 
 }  // namespace
 
@@ -502,11 +502,14 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
         for (nbc = 0; nbc < chunk && b0 + nbc < n_blocks && (nbc == 0 || tiles < kMaxTiles); ++nbc) {
             const int bl = nbc;
             const BlockConst& bc = h_blocks[b0 + bl];
-            for (int k0 = 0; k0 < bc.K; k0 += run_len) {
+            // the block's steps in nr runs of balanced lengths (<= run_len)
+            const int nr = (bc.K + run_len - 1) / run_len;
+            for (int ri = 0; ri < nr; ++ri) {
+                const int k0 = ri * bc.K / nr;
                 RunLight rl;
                 memset(&rl, 0, sizeof(rl));
                 rl.k0 = k0;
-                rl.kn = std::min(run_len, bc.K - k0);
+                rl.kn = (ri + 1) * bc.K / nr - k0;
                 rl.j0 = bc.j0;
                 rl.blk = bl;
                 const int jm = bc.j0 + k0 + rl.kn / 2;

@@ -90,7 +90,7 @@ def test_block_partition_mirror():
 def test_options_and_kernel_timing_record_need_no_device(L):
     from paper_1907_04435_gb300 import binding as B
     for key, good, bad in ((B.SA_OPT_RASTER_RUN, 8, 33), (B.SA_OPT_KERNEL_TIMING, 1, 2),
-                           (B.SA_OPT_ACCRUAL_TRAVERSAL, 0, 3), (B.SA_OPT_POINT_RUN, 4, 17)):
+                           (B.SA_OPT_ACCRUAL_TRAVERSAL, 0, 3), (B.SA_OPT_POINT_RUN, 4, 33)):
         old = B.sa_get_option(key)
         B.sa_set_option(key, good)
         assert B.sa_get_option(key) == good

@@ -254,7 +254,7 @@ def test_facade_sam_multi_day_and_progressive(cuda_lib):
 
 @pytest.mark.parametrize("closed", [True, False])
 def test_accrual_maps_do_not_depend_on_the_run_length(cuda_lib, closed):
-    """Steps per set-up (ground 1..32, points 1..16) only regroup the same per-step tests
+    """Steps per set-up (ground 1..32, points 1..32) only regroup the same per-step tests
     (Theorem 1), so both accrual maps give identical counts for every run length."""
     B = cuda_lib
     w = workload("district_small")
@@ -263,7 +263,7 @@ def test_accrual_maps_do_not_depend_on_the_run_length(cuda_lib, closed):
     grid = _ground(B, w)
     fac = B.Receivers.points(w.facade_pos, w.facade_nrm)
     for r, key, runs in ((grid, B.SA_OPT_RASTER_RUN, (1, 3, 13, 24, 32)),
-                         (fac, B.SA_OPT_POINT_RUN, (1, 3, 13, 16))):
+                         (fac, B.SA_OPT_POINT_RUN, (1, 3, 13, 20, 32))):
         old = B.sa_get_option(key)
         try:
             B.sa_set_option(key, 8)
