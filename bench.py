@@ -229,11 +229,11 @@ def run_gpu(args):
         return tot / steps, tg / steps, tf / steps
 
     if args.only_step:
-        # profiling mode: W warm-up steps and K timed steps of the headline method only
-        ms, ms_g, ms_f = timed("accrual_sam", "accrual_sam", args.steps, args.warmup)
+        # profiling mode: W warm-up steps and K timed steps of one method only
+        ms, ms_g, ms_f = timed(args.method, args.method, args.steps, args.warmup)
         if rank == 0:
-            print(json.dumps({"only_step": True, "workload": args.workload, "ms_per_step": ms,
-                              "ground_ms": ms_g, "facade_ms": ms_f}))
+            print(json.dumps({"only_step": True, "workload": args.workload, "method": args.method,
+                              "ms_per_step": ms, "ground_ms": ms_g, "facade_ms": ms_f}))
         return
 
     # ---- headline: shadow accrual (ground accrual raster + facade ray-traced accrual)
@@ -273,6 +273,9 @@ def run_gpu(args):
     # ---- batched scenarios (development variants x seasonal intervals)
     batch = None if args.skip_batch else bench_batch(B, w, args)
 
+    # ---- the other workloads (small sweep case, season, height gradient)
+    other = None if (args.skip_configs or world > 1) else bench_configs(B)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -291,6 +294,7 @@ def run_gpu(args):
             "e2e": e2e,
             "gpu_launches": count_launches(scene, sun, grid, fac),
             "batch": batch,
+            "other_workloads": other,
             "clocks": clk,
         }
         if world == 1 and not args.skip_cpu:
@@ -447,6 +451,74 @@ def bench_batch(B, w, args):
             "speedup": per_ms / batch_ms, "batch_setup_s": setup_s, "unit": UNIT}
 
 
+def _event_ms(fn, reps: int) -> float:
+    """Median CUDA-event time of fn() over reps runs (after one warm-up)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def bench_configs(B):
+    """The other workloads of the method, each in its own terms: the small sweep case
+    (16 boxes, 64^2 cells, 241 steps), the season (50,000 buildings, 4096^2 cells, 92 days)
+    and the height gradient over the park (600k cells, 200 buildings, one day)."""
+    import torch
+    from synth import configs
+    out = {}
+    # 16 boxes: accrual map against both per-step sweeps (launch-bound at this size)
+    w = configs.boxes16()
+    g = w.ground
+    scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+    units = g.R * w.sun.S
+    c1 = {"workload": f"16 boxes, {g.nx}x{g.ny} ground @ {g.dx} m, {w.sun.S} steps",
+          "receiver_steps": units}
+    for m in ("accrual_sam", "accrual_trace", "sweep_raster", "sweep_trace"):
+        ms = _event_ms(lambda: B.sa_accumulate(scene, grid, sun, w.sun.step_minutes, m), 5)
+        c1[m] = {"ms": ms, "value": units / (ms * 1e-3)}
+    out["boxes16"] = c1
+    # season: ground accrual raster over 92 days
+    w = configs.season()
+    g = w.ground
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+    units = g.R * w.sun.S
+    ms = _event_ms(lambda: B.sa_accumulate(scene, grid, sun, w.sun.step_minutes, "accrual_sam"), 2)
+    out["season"] = {"workload": f"{w.city.B} buildings, {w.mesh.T} triangles, {g.nx}x{g.ny} "
+                                 f"ground @ {g.dx} m, {w.sun.D} days x 481 steps ({w.sun.S})",
+                     "receiver_steps": units, "accrual_sam_ms": ms,
+                     "value": units / (ms * 1e-3), "scene_build_s": build_s, "unit": UNIT}
+    del scene, grid
+    # park: forward accrual and the height gradient (forward masks + FP64 flip refinement)
+    w = configs.park()
+    g = w.ground
+    scene = B.Scene.from_footprints(w.city.footprints, w.city.heights, w.city.band_height)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+    fwd = _event_ms(lambda: B.sa_accumulate(scene, grid, sun, w.sun.step_minutes, "accrual_sam"), 5)
+    grad = _event_ms(lambda: B.sa_height_grad(scene, grid, sun, w.sun.step_minutes), 5)
+    out["park_adjoint"] = {"workload": f"{g.nx}x{g.ny} park cells @ {g.dx} m, {w.city.B} buildings, "
+                                       f"{w.sun.S} steps",
+                           "forward_ms": fwd, "gradient_ms": grad,
+                           "gradient_over_forward": grad / fwd}
+    return out
+
+
 def end_to_end(B, w, args, dev):
     """Same metric through the C ABI from host buffers: scene + BVH build, sun table,
     receiver sort, accumulation, and the results copied back to pinned host memory."""
@@ -476,7 +548,7 @@ def end_to_end(B, w, args, dev):
 
     once()
     times = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(5):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         once()
@@ -523,9 +595,14 @@ def main():
     ap.add_argument("--block-len", dest="block_len", type=int, default=0)
     ap.add_argument("--skip-baselines", action="store_true")
     ap.add_argument("--only-step", action="store_true",
-                    help="time the headline method only (for profiler runs); prints one JSON line")
+                    help="time one method only (for profiler runs); prints one JSON line")
+    ap.add_argument("--method", default="accrual_sam",
+                    choices=["accrual_sam", "accrual_trace", "sweep_trace"],
+                    help="the method --only-step times (ground and facades)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-configs", action="store_true",
+                    help="skip the small-sweep, season and height-gradient workloads")
     ap.add_argument("--batch-variants", type=int, default=64)
     ap.add_argument("--batch-days", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -14,7 +14,9 @@
 //                               intervals without a flip add dt * chi to S directly.
 //   k_flip_solve                per flip, in FP64: find the buildings that shadow the
 //                               receiver at the shadowed end (FP32 BVH traversal), locate
-//                               each one's flip a*_b by bisection on an exact prism test,
+//                               each one's flip a*_b by bisection on an exact prism test
+//                               (in a projective parameter of the same arc, which needs no
+//                               trigonometry per step, then converted to the slerp one),
 //                               take the first (lit -> shadow) or last (shadow -> lit), and
 //                               if the flip is the shadow of a roof edge e of building b
 //                               crossing the receiver, differentiate the grazing condition
@@ -32,7 +34,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxCand = 8;
-constexpr int kBisect = 60;
+constexpr int kBisect = 40;   // halvings of [0, 1]: the flip to 1e-12 of a step
+constexpr int kLinEdges = 8;  // footprints up to this many edges take the linear form
 
 // Visits every interval (j, j+1) inside a day of receiver r: f(j, chi0, chi1).
 template <class F>
@@ -146,11 +149,96 @@ __device__ Entry prism(const float2* xy, int a, int v, double h, double px, doub
     return Entry{zlo <= zhi, zlo, zhi, elo};
 }
 
-__device__ __forceinline__ bool prism_at(const FootprintSet& fs, const float* heights, int b,
-                                         double px, double py, const Arc& arc, double al) {
-    const Vec3 d = arc_dir(arc, al);
-    return prism(fs.xy, fs.fp_off[b], fs.fp_off[b + 1] - fs.fp_off[b], (double)heights[b], px, py,
-                 d.x / d.z, d.y / d.z).inside;
+// The same decision as prism(...).inside, without divisions: each bound z = -A / B of the
+// entry interval is kept as a fraction with a positive denominator and compared by cross
+// multiplication.
+__device__ bool prism_inside(const float2* xy, int a, int v, double h, double px, double py,
+                             double ux, double uy) {
+    double nlo = 0.0, dlo = 1.0;     // lower bound nlo / dlo
+    double nhi = h, dhi = 1.0;       // upper bound nhi / dhi
+    for (int i = 0; i < v; ++i) {
+        const float2 p0 = xy[a + i], p1 = xy[a + (i + 1 == v ? 0 : i + 1)];
+        const double cx = (double)p1.x - (double)p0.x, cy = (double)p1.y - (double)p0.y;
+        const double A = cx * (py - (double)p0.y) - cy * (px - (double)p0.x);
+        const double Bc = cx * uy - cy * ux;
+        if (Bc > 0.0) {
+            if (-A * dlo > nlo * Bc) { nlo = -A; dlo = Bc; }
+        } else if (Bc < 0.0) {
+            if (A * dhi < nhi * -Bc) { nhi = A; dhi = -Bc; }
+        } else if (A < 0.0) {
+            return false;
+        }
+    }
+    return nlo * dhi <= nhi * dlo;
+}
+
+// Status of building b along the arc in the projective parameter be: the direction
+// a + be (b - a) (not normalised: the slopes u = d_xy / d_z do not depend on its length)
+// runs over the same great-circle arc as slerp, monotonically, so a flip found in be is
+// the same physical flip; its slerp parameter follows from the angle to a.
+__device__ __forceinline__ bool prism_along(const FootprintSet& fs, const float* heights, int b,
+                                            double px, double py, const Arc& arc, double be) {
+    const double dx = fma(be, arc.b.x - arc.a.x, arc.a.x);
+    const double dy = fma(be, arc.b.y - arc.a.y, arc.a.y);
+    const double dz = fma(be, arc.b.z - arc.a.z, arc.a.z);
+    const double iz = 1.0 / dz;
+    return prism_inside(fs.xy, fs.fp_off[b], fs.fp_off[b + 1] - fs.fp_off[b], (double)heights[b],
+                        px, py, dx * iz, dy * iz);
+}
+
+// Along the arc d(be) = a + be (b - a) every edge constraint of the prism is linear in be
+// once multiplied by d_z(be) > 0: the bound z = -A / B_c becomes (-A d_z) / (B_c d_z) with
+// B_c d_z = c x d_xy = E0 + be E1.  Set up once per (flip, building), each bisection step
+// then costs a few FP64 multiply-adds per edge and no division.
+struct PrismLin {
+    int v;
+    double h, az, ez;
+    double A[kLinEdges], E0[kLinEdges], E1[kLinEdges];
+};
+
+__device__ void prism_lin_setup(PrismLin& P, const float2* xy, int a, int v, double h, double px,
+                                double py, const Arc& arc) {
+    P.v = v;
+    P.h = h;
+    P.az = arc.a.z;
+    P.ez = arc.b.z - arc.a.z;
+    const double ex = arc.b.x - arc.a.x, ey = arc.b.y - arc.a.y;
+    for (int i = 0; i < v; ++i) {
+        const float2 p0 = xy[a + i], p1 = xy[a + (i + 1 == v ? 0 : i + 1)];
+        const double cx = (double)p1.x - (double)p0.x, cy = (double)p1.y - (double)p0.y;
+        P.A[i] = cx * (py - (double)p0.y) - cy * (px - (double)p0.x);
+        P.E0[i] = cx * arc.a.y - cy * arc.a.x;
+        P.E1[i] = cx * ey - cy * ex;
+    }
+}
+
+__device__ bool prism_lin_inside(const PrismLin& P, double be) {
+    const double dz = fma(be, P.ez, P.az);
+    double nlo = 0.0, dlo = 1.0, nhi = P.h, dhi = 1.0;
+    for (int i = 0; i < P.v; ++i) {
+        const double den = fma(be, P.E1[i], P.E0[i]);
+        const double num = -P.A[i] * dz;
+        if (den > 0.0) {
+            if (num * dlo > nlo * den) { nlo = num; dlo = den; }
+        } else if (den < 0.0) {
+            if (-num * dhi < nhi * -den) { nhi = -num; dhi = -den; }
+        } else if (P.A[i] < 0.0) {
+            return false;
+        }
+    }
+    return nlo * dhi <= nhi * dlo;
+}
+
+// slerp parameter of the projective parameter be (see prism_along)
+__device__ __forceinline__ double slerp_param(const Arc& arc, double be) {
+    if (arc.theta < 1e-12) return be;
+    const double dx = fma(be, arc.b.x - arc.a.x, arc.a.x);
+    const double dy = fma(be, arc.b.y - arc.a.y, arc.a.y);
+    const double dz = fma(be, arc.b.z - arc.a.z, arc.a.z);
+    const double cx = arc.a.y * dz - arc.a.z * dy, cy = arc.a.z * dx - arc.a.x * dz,
+                 cz = arc.a.x * dy - arc.a.y * dx;
+    const double ang = atan2(sqrt(cx * cx + cy * cy + cz * cz), arc.a.x * dx + arc.a.y * dy + arc.a.z * dz);
+    return fmin(1.0, fmax(0.0, ang / arc.theta));
 }
 
 // Buildings hit by the FP32 ray from o toward step s (all hits, not only the first).
@@ -227,15 +315,25 @@ __global__ void k_flip_solve(SolveArgs a) {
     int bbest = -1;
     for (int q = 0; q < n; ++q) {
         const int b = ids[q];
-        if (!prism_at(a.fs, a.heights, b, px, py, arc, al_sh)) continue;
-        if (prism_at(a.fs, a.heights, b, px, py, arc, al_lit)) continue;
-        double lo = 0.0, hi = 1.0;   // invariant: status(lo) == status at a = 0
+        if (!prism_along(a.fs, a.heights, b, px, py, arc, al_sh)) continue;
+        if (prism_along(a.fs, a.heights, b, px, py, arc, al_lit)) continue;
+        double lo = 0.0, hi = 1.0;   // invariant: status(lo) == status at the arc's start
         const bool s0 = c0 != 0;
-        for (int it = 0; it < kBisect; ++it) {
-            const double mid = 0.5 * (lo + hi);
-            if (prism_at(a.fs, a.heights, b, px, py, arc, mid) == s0) lo = mid; else hi = mid;
+        const int fa = a.fs.fp_off[b], v = a.fs.fp_off[b + 1] - fa;
+        if (v <= kLinEdges) {
+            PrismLin P;
+            prism_lin_setup(P, a.fs.xy, fa, v, (double)a.heights[b], px, py, arc);
+            for (int it = 0; it < kBisect; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (prism_lin_inside(P, mid) == s0) lo = mid; else hi = mid;
+            }
+        } else {
+            for (int it = 0; it < kBisect; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (prism_along(a.fs, a.heights, b, px, py, arc, mid) == s0) lo = mid; else hi = mid;
+            }
         }
-        const double as = 0.5 * (lo + hi);
+        const double as = slerp_param(arc, 0.5 * (lo + hi));
         if (c0 ? (as > best) : (as < best)) { best = as; bbest = b; }
     }
     if (bbest < 0) {
