@@ -14,9 +14,12 @@
 //                               intervals without a flip add dt * chi to S directly.
 //   k_flip_solve                per flip, in FP64: find the buildings that shadow the
 //                               receiver at the shadowed end (FP32 BVH traversal), locate
-//                               each one's flip a*_b by bisection on an exact prism test
-//                               (in a projective parameter of the same arc, which needs no
-//                               trigonometry per step, then converted to the slerp one),
+//                               each one's flip a*_b on the exact prism test, in a
+//                               projective parameter of the same arc in which every prism
+//                               constraint is linear: an FP32 bisection brackets the flip,
+//                               the pair of constraints that close the entry interval there
+//                               gives it in closed form, and FP64 statuses on both sides
+//                               confirm it (otherwise an FP64 bisection finds it); then
 //                               take the first (lit -> shadow) or last (shadow -> lit), and
 //                               if the flip is the shadow of a roof edge e of building b
 //                               crossing the receiver, differentiate the grazing condition
@@ -36,6 +39,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxCand = 8;
 constexpr int kBisect = 40;   // halvings of [0, 1]: the flip to 1e-12 of a step
 constexpr int kLinEdges = 8;  // footprints up to this many edges take the linear form
+constexpr int kBisectF = 22;  // FP32 halvings that bracket a flip before its closed form
+constexpr double kSide = 1e-10;   // FP64 status checks this far on both sides of a root
 
 // Visits every interval (j, j+1) inside a day of receiver r: f(j, chi0, chi1).
 template <class F>
@@ -229,6 +234,71 @@ __device__ bool prism_lin_inside(const PrismLin& P, double be) {
     return nlo * dhi <= nhi * dlo;
 }
 
+// The same test with FP32 coefficients: used only to bracket the flip coarsely (the
+// bracket is confirmed in FP64 below).
+struct PrismLinF {
+    int v;
+    float h, az, ez;
+    float A[kLinEdges], E0[kLinEdges], E1[kLinEdges];
+};
+
+__device__ void prism_lin_to_f(const PrismLin& P, PrismLinF& F) {
+    F.v = P.v; F.h = (float)P.h; F.az = (float)P.az; F.ez = (float)P.ez;
+    for (int i = 0; i < P.v; ++i) { F.A[i] = (float)P.A[i]; F.E0[i] = (float)P.E0[i]; F.E1[i] = (float)P.E1[i]; }
+}
+
+__device__ bool prism_lin_inside_f(const PrismLinF& P, float be) {
+    const float dz = fmaf(be, P.ez, P.az);
+    float nlo = 0.f, dlo = 1.f, nhi = P.h, dhi = 1.f;
+    for (int i = 0; i < P.v; ++i) {
+        const float den = fmaf(be, P.E1[i], P.E0[i]);
+        const float num = -P.A[i] * dz;
+        if (den > 0.f) {
+            if (num * dlo > nlo * den) { nlo = num; dlo = den; }
+        } else if (den < 0.f) {
+            if (-num * dhi < nhi * -den) { nhi = -num; dhi = -den; }
+        } else if (P.A[i] < 0.f) {
+            return false;
+        }
+    }
+    return nlo * dhi <= nhi * dlo;
+}
+
+// The constraints that bound the entry interval at be: il the lower bound (-1: the ground),
+// iu the upper bound (-1: the roof height h).
+__device__ void prism_lin_active(const PrismLin& P, double be, int* il, int* iu) {
+    const double dz = fma(be, P.ez, P.az);
+    double nlo = 0.0, dlo = 1.0, nhi = P.h, dhi = 1.0;
+    *il = -1;
+    *iu = -1;
+    for (int i = 0; i < P.v; ++i) {
+        const double den = fma(be, P.E1[i], P.E0[i]);
+        const double num = -P.A[i] * dz;
+        if (den > 0.0 && num * dlo > nlo * den) { nlo = num; dlo = den; *il = i; }
+        if (den < 0.0 && -num * dhi < nhi * -den) { nhi = -num; dhi = -den; *iu = i; }
+    }
+}
+
+// The flip where the interval closes between lower bound il and upper bound iu, in closed
+// form: both bounds are ratios of functions linear in be, so their equality is linear.
+//   edge il against the roof:  -A_i d_z(be) = h (E0_i + be E1_i)
+//   edge il against edge iu:    A_i (E0_j + be E1_j) = A_j (E0_i + be E1_i)
+__device__ bool pair_root(const PrismLin& P, int il, int iu, double* be) {
+    if (il < 0) return false;
+    const double Ai = P.A[il];
+    if (iu < 0) {
+        const double den = fma(Ai, P.ez, P.h * P.E1[il]);
+        if (den == 0.0) return false;
+        *be = -fma(Ai, P.az, P.h * P.E0[il]) / den;
+        return true;
+    }
+    const double Aj = P.A[iu];
+    const double den = Ai * P.E1[iu] - Aj * P.E1[il];
+    if (den == 0.0) return false;
+    *be = (Aj * P.E0[il] - Ai * P.E0[iu]) / den;
+    return true;
+}
+
 // slerp parameter of the projective parameter be (see prism_along)
 __device__ __forceinline__ double slerp_param(const Arc& arc, double be) {
     if (arc.theta < 1e-12) return be;
@@ -315,25 +385,48 @@ __global__ void k_flip_solve(SolveArgs a) {
     int bbest = -1;
     for (int q = 0; q < n; ++q) {
         const int b = ids[q];
-        if (!prism_along(a.fs, a.heights, b, px, py, arc, al_sh)) continue;
-        if (prism_along(a.fs, a.heights, b, px, py, arc, al_lit)) continue;
-        double lo = 0.0, hi = 1.0;   // invariant: status(lo) == status at the arc's start
         const bool s0 = c0 != 0;
         const int fa = a.fs.fp_off[b], v = a.fs.fp_off[b + 1] - fa;
+        double be_star = -1.0;
         if (v <= kLinEdges) {
             PrismLin P;
             prism_lin_setup(P, a.fs.xy, fa, v, (double)a.heights[b], px, py, arc);
-            for (int it = 0; it < kBisect; ++it) {
-                const double mid = 0.5 * (lo + hi);
-                if (prism_lin_inside(P, mid) == s0) lo = mid; else hi = mid;
+            if (!prism_lin_inside(P, al_sh) || prism_lin_inside(P, al_lit)) continue;
+            // bracket in FP32, then the closed form of the pair of constraints that close
+            // the interval, confirmed by FP64 statuses on both sides of it
+            PrismLinF F;
+            prism_lin_to_f(P, F);
+            float flo = 0.f, fhi = 1.f;
+            for (int it = 0; it < kBisectF; ++it) {
+                const float mid = 0.5f * (flo + fhi);
+                if (prism_lin_inside_f(F, mid) == s0) flo = mid; else fhi = mid;
+            }
+            int il, iu;
+            prism_lin_active(P, s0 ? (double)flo : (double)fhi, &il, &iu);
+            double r;
+            if (pair_root(P, il, iu, &r) && r > kSide && r < 1.0 - kSide &&
+                fabs(r - 0.5 * ((double)flo + (double)fhi)) < 1e-4 &&
+                prism_lin_inside(P, r - kSide) == s0 && prism_lin_inside(P, r + kSide) != s0) {
+                be_star = r;
+            } else {
+                double lo = 0.0, hi = 1.0;   // invariant: status(lo) == status at the start
+                for (int it = 0; it < kBisect; ++it) {
+                    const double mid = 0.5 * (lo + hi);
+                    if (prism_lin_inside(P, mid) == s0) lo = mid; else hi = mid;
+                }
+                be_star = 0.5 * (lo + hi);
             }
         } else {
+            if (!prism_along(a.fs, a.heights, b, px, py, arc, al_sh)) continue;
+            if (prism_along(a.fs, a.heights, b, px, py, arc, al_lit)) continue;
+            double lo = 0.0, hi = 1.0;
             for (int it = 0; it < kBisect; ++it) {
                 const double mid = 0.5 * (lo + hi);
                 if (prism_along(a.fs, a.heights, b, px, py, arc, mid) == s0) lo = mid; else hi = mid;
             }
+            be_star = 0.5 * (lo + hi);
         }
-        const double as = slerp_param(arc, 0.5 * (lo + hi));
+        const double as = slerp_param(arc, be_star);
         if (c0 ? (as > best) : (as < best)) { best = as; bbest = b; }
     }
     if (bbest < 0) {
