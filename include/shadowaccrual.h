@@ -93,7 +93,7 @@ int32_t sa_version(void);
  *   the option.
  *   SA_OPT_RASTER_RUN: at most this many steps the ground accrual raster tests per cell
  *   set-up (1..32, default 24), and SA_OPT_POINT_RUN: at most this many steps per
- *   light-space map of point receivers (1..32, default 20); each block is split into
+ *   light-space map of point receivers (1..32, default 27); each block is split into
  *   runs of balanced lengths within the bound.  The defaults are the fastest on the
  *   district workload.  Longer runs amortise the set-up, shorter runs bound the swept
  *   region more tightly.  Results do not depend on either option.

@@ -23,6 +23,29 @@ inline cudaError_t scratch_alloc(T** p, size_t bytes, cudaStream_t st) {
     return scratch_alloc_bytes(reinterpret_cast<void**>(p), bytes, st);
 }
 
+// Two FP32 values in one 64-bit register.  The packed multiply-add and multiply of sm_100
+// and later (fma.rn.f32x2, mul.rn.f32x2) round each half exactly as the scalar instruction
+// does, so code may pair two independent steps per instruction without changing a result.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 constexpr float kGroundTmin = 1e-3f;     // ground receivers: hits closer than 1 mm ignored
 constexpr float kFacadeOffset = 1e-2f;   // facade receivers start 1 cm along their normal
 constexpr int kMaxBlock = 64;            // steps per accrual block (one uint64 mask)

@@ -193,6 +193,9 @@ struct TileSmem {
     unsigned long long back[kTriBatch];      // steps with n . d < 0 (open scenes only)
     int valid[kTriBatch];
     float2 u[kMaxBlock];
+    // slopes of steps (k, k + 1) packed for the paired step tests: [0][i] starts at step
+    // 2i, [1][i] at step 2i + 1 (the last pair of a block repeats its last step)
+    unsigned long long upx[2][kMaxBlock / 2], upy[2][kMaxBlock / 2];
     float4 d[kMaxBlock];                     // step directions
     float4 ubox[kMaxBlock];                  // per run: (min u.x, max u.x, min u.y, max u.y)
     unsigned long long mask[kTile * kTile];
@@ -231,16 +234,30 @@ __device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeRef
         QX[q] = -fmaf(e.vz, e.ey, e.ez * cy);
         QY[q] = fmaf(e.vz, e.ex, e.ez * cx);
     }
-    unsigned hf = 0, hb = 0;
-#pragma unroll 8
-    for (int k = 0; k < kn; ++k) {
-        const float2 u = sm.u[k0 + k];
-        const float f0 = fmaf(QY[0], u.y, fmaf(QX[0], u.x, P[0]));
-        const float f1 = fmaf(QY[1], u.y, fmaf(QX[1], u.x, P[1]));
-        const float f2 = fmaf(QY[2], u.y, fmaf(QX[2], u.x, P[2]));
-        if (fminf(f0, fminf(f1, f2)) >= 0.f) hf |= 1u << k;
-        if (!CULL && fmaxf(f0, fmaxf(f1, f2)) <= 0.f) hb |= 1u << k;
+    // steps in pairs: E = P + Qx u_x + Qy u_y for two steps per packed instruction
+    unsigned long long P2[3], QX2[3], QY2[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        P2[q] = f2_pack(P[q], P[q]);
+        QX2[q] = f2_pack(QX[q], QX[q]);
+        QY2[q] = f2_pack(QY[q], QY[q]);
     }
+    const unsigned long long* upx = sm.upx[k0 & 1] + (k0 >> 1);
+    const unsigned long long* upy = sm.upy[k0 & 1] + (k0 >> 1);
+    unsigned hf = 0, hb = 0;
+#pragma unroll 4
+    for (int k = 0; k < kn; k += 2) {
+        const unsigned long long ux = upx[k >> 1], uy = upy[k >> 1];
+        float f[3][2];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) f2_unpack(f2_fma(QY2[q], uy, f2_fma(QX2[q], ux, P2[q])), f[q][0], f[q][1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (fminf(f[0][h], fminf(f[1][h], f[2][h])) >= 0.f) hf |= 1u << (k + h);
+            if (!CULL && fmaxf(f[0][h], fmaxf(f[1][h], f[2][h])) <= 0.f) hb |= 1u << (k + h);
+        }
+    }
+    // an odd run's last pair repeats a step beyond it; the masks below drop that bit
     return CULL ? (hf & fr) : ((hf & fr) | (hb & bk));
 }
 
@@ -369,6 +386,11 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
         sm.d[threadIdx.x] = make_float4(s.dx, s.dy, s.dz, 0.f);
     }
     __syncthreads();
+    if (threadIdx.x < K) {
+        const int k = threadIdx.x, k1 = min(k + 1, K - 1);
+        sm.upx[k & 1][k >> 1] = f2_pack(sm.u[k].x, sm.u[k1].x);
+        sm.upy[k & 1][k >> 1] = f2_pack(sm.u[k].y, sm.u[k1].y);
+    }
     if (threadIdx.x < nsub) {
         const int k0 = threadIdx.x * K / nsub, k1 = (threadIdx.x + 1) * K / nsub;
         float4 b = make_float4(3.4e38f, -3.4e38f, 3.4e38f, -3.4e38f);

@@ -202,7 +202,7 @@ template <bool COUNT>
 __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int lane,
                                             const float4* s_tri, const float4* s_n,
                                             const unsigned* s_front, const float4* s_o,
-                                            unsigned* s_m, const float (*s_d)[4],
+                                            unsigned* s_m, const unsigned long long (*s_d2)[3],
                                             int kn, unsigned long long& n_pair,
                                             unsigned long long& n_test) {
     if (lane >= n) return;
@@ -215,12 +215,33 @@ __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int 
     if (COUNT) ++n_pair;
     const float4 nv = s_n[t];
     const PluckerTri pt = plucker_setup_n(o, a, b, c, make_float3(nv.x, nv.y, nv.z));
-    // every step of the run is tested without branches (independent chains the scheduler
-    // can interleave); steps the triangle turns away from are masked off afterwards
+    // every step of the run is tested without branches, two steps per packed instruction
+    // (the same roundings as plucker_hit_all); steps the triangle turns away from, and the
+    // repeated step of an odd run's last pair, are masked off afterwards
+    unsigned long long M[3][3], N[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M[e][c] = f2_pack(pt.m[e][c], pt.m[e][c]);
+    N[0] = f2_pack(pt.nx, pt.nx); N[1] = f2_pack(pt.ny, pt.ny); N[2] = f2_pack(pt.nz, pt.nz);
     unsigned m = 0;
-#pragma unroll 4
-    for (int k = 0; k < kn; ++k)
-        if (plucker_hit_all(pt, s_d[k][0], s_d[k][1], s_d[k][2], p.w)) m |= 1u << k;
+#pragma unroll 2
+    for (int k = 0; k < kn; k += 2) {
+        const unsigned long long dx = s_d2[k >> 1][0], dy = s_d2[k >> 1][1], dz = s_d2[k >> 1][2];
+        float sv[3][2], nd[2];
+#pragma unroll
+        for (int e = 0; e < 3; ++e)
+            f2_unpack(f2_fma(dz, M[e][2], f2_fma(dy, M[e][1], f2_mul(dx, M[e][0]))), sv[e][0], sv[e][1]);
+        f2_unpack(f2_fma(dz, N[2], f2_fma(dy, N[1], f2_mul(dx, N[0]))), nd[0], nd[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const bool inside = fminf(sv[0][h], fminf(sv[1][h], sv[2][h])) >= 0.f ||
+                                fmaxf(sv[0][h], fmaxf(sv[1][h], sv[2][h])) <= 0.f;
+            const float lim = __fmul_rn(p.w, nd[h]);
+            const bool ahead = (nd[h] > 0.f && pt.aon > lim) || (nd[h] < 0.f && pt.aon < lim);
+            if (inside && ahead) m |= 1u << (k + h);
+        }
+    }
     m &= want;
     if (COUNT) n_test += (unsigned)__popc(want);
     if (m) atomicOr(&s_m[who], m);
@@ -236,7 +257,7 @@ k_sam_tile(TileArgs ta) {
     __shared__ float4 s_edge[3][kTriChunk];        // light-space edge lines (nx, ny, c)
     __shared__ float s_ztop[kTriChunk];            // highest vertex z
     __shared__ unsigned s_front[kTriChunk];
-    __shared__ float s_d[kRunMax][4];
+    __shared__ unsigned long long s_d2[kRunMax / 2][3];   // directions of steps (k, k + 1), k even
     __shared__ float4 s_o[kTileThreads];           // receiver origins (and t_min) of the pass
     __shared__ unsigned s_m[kTileThreads];         // their step bits
     __shared__ unsigned short s_q[kWarps][kQueue]; // pair queues: receiver slot << 8 | triangle
@@ -248,9 +269,13 @@ k_sam_tile(TileArgs ta) {
     const RunLight& rl = ta.runs[ta.tile_run[tile]];
     const int kn = rl.kn;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < kn) {
-        const StepConst& s = ta.steps[rl.j0 + rl.k0 + threadIdx.x];
-        s_d[threadIdx.x][0] = s.dx; s_d[threadIdx.x][1] = s.dy; s_d[threadIdx.x][2] = s.dz;
+    if (2 * threadIdx.x < kn) {
+        const int k = 2 * threadIdx.x, k1 = min(k + 1, kn - 1);
+        const StepConst& s = ta.steps[rl.j0 + rl.k0 + k];
+        const StepConst& t = ta.steps[rl.j0 + rl.k0 + k1];
+        s_d2[threadIdx.x][0] = f2_pack(s.dx, t.dx);
+        s_d2[threadIdx.x][1] = f2_pack(s.dy, t.dy);
+        s_d2[threadIdx.x][2] = f2_pack(s.dz, t.dz);
     }
     const bool cull = ta.sc.closed != 0;
     const float inv_dz = 1.f / rl.min_dz;
@@ -346,14 +371,14 @@ k_sam_tile(TileArgs ta) {
                 n += __popc(bal);
                 if (n >= 32) {
                     __syncwarp();
-                    drain_pairs<COUNT>(q + (n - 32), 32, lane, s_tri, s_n, s_front, s_o, s_m, s_d,
+                    drain_pairs<COUNT>(q + (n - 32), 32, lane, s_tri, s_n, s_front, s_o, s_m, s_d2,
                                        kn, n_pair, n_test);
                     n -= 32;
                     __syncwarp();
                 }
             }
             __syncwarp();
-            drain_pairs<COUNT>(q, n, lane, s_tri, s_n, s_front, s_o, s_m, s_d, kn, n_pair, n_test);
+            drain_pairs<COUNT>(q, n, lane, s_tri, s_n, s_front, s_o, s_m, s_d2, kn, n_pair, n_test);
             __syncwarp();
             const unsigned m = s_m[threadIdx.x];
             if (live && m) atomicOr(&ta.masks[(long long)rl.blk * ta.R + s], (unsigned long long)m << rl.k0);
@@ -456,7 +481,7 @@ void normalize3(double* v) {
     v[0] /= n; v[1] /= n; v[2] /= n;
 }
 
-int g_point_run = 20;
+int g_point_run = 27;
 
 }  // namespace
 
