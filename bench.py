@@ -263,6 +263,16 @@ def run_gpu(args):
         sweep = methods["sweep_trace"]["value"]
         for v in methods.values():
             v["speedup_vs_sweep_trace"] = v["value"] / sweep
+        # the inverse accrual map (approximate, ground receivers only: Sec. 5) beside the
+        # exact methods' ground calls
+        gsteps = grid.R * st.S
+        iam_ms = _event_ms(lambda: B.sa_accumulate(scene, grid, sun, st.step_minutes, "iam",
+                                                   gross=out_g[0], minutes=out_g[1],
+                                                   continuous=out_g[2]), 3)
+        methods["iam_ground_only"] = {
+            "ground_ms": iam_ms, "ground_value": gsteps / (iam_ms * 1e-3),
+            "note": "approximate (3 source levels, 1 m acne rule); accuracy in the IAM tests",
+            "speedup_vs_sweep_trace_ground": methods["sweep_trace"]["ground_ms"] / iam_ms}
 
     # ---- roofline of the dominant kernel (instrumented work counters)
     roof, roof_all = roofline(B, scene, grid, fac, sun, ktimes, args.steps, args.workload)

@@ -198,51 +198,71 @@ sa_status sa_scene_from_mesh(const float* verts, int64_t nv, const int32_t* tris
     if ((nv > 0 && !verts) || (nt > 0 && !tris))
         return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: NULL buffer");
     if (n_buildings < 0) return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: n_buildings < 0");
+    // validation reads host memory in place (device inputs are copied to the host first)
     std::vector<float> hv;
     std::vector<int32_t> ht, hb;
-    sa_status s = host_copy(verts, (size_t)nv * 3, device_ptrs, &hv);
-    if (s != SA_OK) return s;
-    s = host_copy(tris, (size_t)nt * 3, device_ptrs, &ht);
-    if (s != SA_OK) return s;
-    if (tri_building) {
-        s = host_copy(tri_building, (size_t)nt, device_ptrs, &hb);
+    const float* pv = verts;
+    const int32_t *pt = tris, *pb = tri_building;
+    if (device_ptrs) {
+        sa_status s = host_copy(verts, (size_t)nv * 3, 1, &hv);
+        if (s == SA_OK) s = host_copy(tris, (size_t)nt * 3, 1, &ht);
+        if (s == SA_OK && tri_building) s = host_copy(tri_building, (size_t)nt, 1, &hb);
         if (s != SA_OK) return s;
+        pv = hv.data();
+        pt = ht.data();
+        pb = tri_building ? hb.data() : nullptr;
     }
-    float min_z = INFINITY;
-    for (size_t i = 0; i < hv.size(); ++i)
-        if (!isfinite(hv[i])) return fail(SA_ERR_DEGENERATE, "sa_scene_from_mesh: non-finite vertex %zu", i / 3);
-    for (size_t t = 0; t < ht.size(); ++t) {
-        if (ht[t] < 0 || ht[t] >= nv)
-            return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: triangle %zu indexes vertex %d", t / 3, ht[t]);
-        min_z = std::min(min_z, hv[3 * (size_t)ht[t] + 2]);
+    for (int64_t i = 0; i < 3 * nv; ++i)
+        if (!isfinite(pv[i])) return fail(SA_ERR_DEGENERATE, "sa_scene_from_mesh: non-finite vertex %lld", (long long)(i / 3));
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const int32_t nb_max = std::max(n_buildings, 1);
+    for (int64_t t = 0; t < nt; ++t) {
+        for (int q = 0; q < 3; ++q) {
+            const int32_t ix = pt[3 * t + q];
+            if (ix < 0 || ix >= nv)
+                return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: triangle %lld indexes vertex %d", (long long)t, ix);
+            const float* v = pv + 3 * (size_t)ix;
+            for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], v[k]); hi[k] = std::max(hi[k], v[k]); }
+        }
+        if (pb && (pb[t] < 0 || pb[t] >= nb_max))
+            return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: building id %d of triangle %lld", pb[t], (long long)t);
     }
-    for (size_t t = 0; t < hb.size(); ++t)
-        if (hb[t] < 0 || hb[t] >= std::max(n_buildings, 1))
-            return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: building id %d of triangle %zu", hb[t], t);
     cudaStream_t st = as_stream(stream);
     sa_scene* sc = new (std::nothrow) sa_scene();
     if (!sc) return fail(SA_ERR_OOM, "sa_scene_from_mesh: host allocation");
     sc->T = nt;
     sc->n_buildings = n_buildings;
-    sc->min_z = nt > 0 ? min_z : 0.f;
-    for (int q = 0; q < 3; ++q) { sc->box[q] = INFINITY; sc->box[3 + q] = -INFINITY; }
-    for (size_t t = 0; t < ht.size(); ++t)
-        for (int q = 0; q < 3; ++q) {
-            const float x = hv[3 * (size_t)ht[t] + q];
-            sc->box[q] = std::min(sc->box[q], x);
-            sc->box[3 + q] = std::max(sc->box[3 + q], x);
+    sc->min_z = nt > 0 ? lo[2] : 0.f;
+    for (int q = 0; q < 3; ++q) { sc->box[q] = nt > 0 ? lo[q] : 0.f; sc->box[3 + q] = nt > 0 ? hi[q] : 0.f; }
+    // inputs to the device: device buffers are used in place, host buffers go through
+    // stream-ordered staging (pinned host memory copies asynchronously)
+    const float* dv = verts;
+    const int *dt = tris, *db = tri_building;
+    float* sv = nullptr;
+    int *stt = nullptr, *sb = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!device_ptrs) {
+        if (nv > 0) {
+            e = sa::scratch_alloc(&sv, sizeof(float) * 3 * (size_t)nv, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(sv, verts, sizeof(float) * 3 * (size_t)nv, cudaMemcpyHostToDevice, st);
         }
-    if (nt == 0) for (int q = 0; q < 6; ++q) sc->box[q] = 0.f;
-    float* dv = nullptr;
-    int *dt = nullptr, *db = nullptr;
-    cudaError_t e = upload(hv.data(), hv.size(), 0, &dv, st);
-    if (e == cudaSuccess) e = upload(ht.data(), ht.size(), 0, &dt, st);
-    if (e == cudaSuccess && tri_building) e = upload(hb.data(), hb.size(), 0, &db, st);
+        if (e == cudaSuccess && nt > 0) {
+            e = sa::scratch_alloc(&stt, sizeof(int) * 3 * (size_t)nt, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(stt, tris, sizeof(int) * 3 * (size_t)nt, cudaMemcpyHostToDevice, st);
+        }
+        if (e == cudaSuccess && nt > 0 && tri_building) {
+            e = sa::scratch_alloc(&sb, sizeof(int) * (size_t)nt, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(sb, tri_building, sizeof(int) * (size_t)nt, cudaMemcpyHostToDevice, st);
+        }
+        dv = sv;
+        dt = stt;
+        db = tri_building ? sb : nullptr;
+    }
     if (e == cudaSuccess) e = sa::build_lbvh(dv, nv, dt, nt, db, &sc->bvh, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (dv) cudaFree(dv);
-    if (dt) cudaFree(dt);
-    if (db) cudaFree(db);
+    if (sv) cudaFreeAsync(sv, st);
+    if (stt) cudaFreeAsync(stt, st);
+    if (sb) cudaFreeAsync(sb, st);
     if (e != cudaSuccess) {
         delete sc;
         return cuda_fail(e, "sa_scene_from_mesh");
