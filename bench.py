@@ -396,7 +396,8 @@ def roofline(B, scene, grid, fac, sun, ktimes, steps, workload):
     c = B.sa_work_counters(scene, grid, sun, "accrual_sam")
     entry("k_raster", "k_raster (ground accrual raster)", c[2] * OPS_CELL + c[3] * OPS_TEST,
           "raster", {"cell_setups": c[2], "cell_step_tests": c[3],
-                     "ops_per_setup": OPS_CELL, "ops_per_test": OPS_TEST})
+                     "ops_per_setup": OPS_CELL, "ops_per_test": OPS_TEST,
+                     "work_units": c[0], "cells_enumerated": c[1]})
     if fac is not None:
         c = B.sa_work_counters(scene, fac, sun, "accrual_sam")
         entry("k_sam_tile", "k_sam_tile (facade light-space accrual map)",

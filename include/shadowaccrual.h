@@ -298,9 +298,13 @@ sa_status sa_batch_tune(sa_batch* b, int32_t* best_ctas, int32_t* best_run, void
 sa_status sa_batch_work_counters(sa_batch* b, uint64_t* counters, void* stream);
 
 /* Work counters of one accumulation (diagnostics for roofline accounting): runs `method`
- * with counting enabled and writes counters uint64 [4] dev: [0] ray/fan-versus-box tests
- * and [1] ray-versus-triangle tests performed per receiver lane (trace methods),
- * [2] projected (triangle, step) set-ups and [3] cell coverage tests (raster methods).
+ * with counting enabled and writes counters uint64 [4] dev.
+ *   trace methods: [0] ray/fan-versus-box tests, [1] ray-versus-triangle tests per
+ *   receiver lane.
+ *   raster methods (ground grids): [0] work units (triangle, run of steps) that reached
+ *   the tile's cells, [1] cells their row spans enumerated, [2] cell set-ups (cells not
+ *   already shadowed at every step of the unit), [3] cell-step coverage tests.
+ *   light-space map of point receivers: [0] receiver-triangle set-ups, [1] step tests.
  * The outputs of the accumulation itself are discarded. */
 sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
                            sa_method method, uint64_t* counters, void* stream);

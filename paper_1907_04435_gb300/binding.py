@@ -284,8 +284,10 @@ def sa_accumulate_grid_noalloc(scene: Scene, grid: Receivers, sun: Sun, step_min
 
 
 def sa_work_counters(scene: Scene, recv: Receivers, sun: Sun, method, stream=None):
-    """Work counters of one accumulation: (box tests, triangle tests, raster set-ups,
-    raster cell tests), as Python ints."""
+    """Work counters of one accumulation, as four Python ints: box and triangle tests of
+    the trace methods; work units, enumerated cells, cell set-ups and cell-step tests of
+    the raster ones; pair set-ups and step tests of the light-space map of points (see
+    sa_work_counters in the C header)."""
     m = METHODS[method] if isinstance(method, str) else int(method)
     c = torch.zeros(4, dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device()))
     _check(lib().sa_work_counters(scene.handle, recv.handle, sun.handle, m, _ptr(c),

@@ -46,6 +46,19 @@ __device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsig
     return d;
 }
 
+// three-input minimum and maximum (one instruction on sm_100 and later; no NaN reaches
+// them here)
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 constexpr float kGroundTmin = 1e-3f;     // ground receivers: hits closer than 1 mm ignored
 constexpr float kFacadeOffset = 1e-2f;   // facade receivers start 1 cm along their normal
 constexpr int kMaxBlock = 64;            // steps per accrual block (one uint64 mask)

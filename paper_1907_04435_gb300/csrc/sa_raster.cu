@@ -244,17 +244,19 @@ __device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeRef
     }
     const unsigned long long* upx = sm.upx[k0 & 1] + (k0 >> 1);
     const unsigned long long* upy = sm.upy[k0 & 1] + (k0 >> 1);
+    // fully unrolled over the longest run, so every step's bit is a constant
     unsigned hf = 0, hb = 0;
-#pragma unroll 4
-    for (int k = 0; k < kn; k += 2) {
+#pragma unroll
+    for (int k = 0; k < 32; k += 2) {
+        if (k >= kn) break;
         const unsigned long long ux = upx[k >> 1], uy = upy[k >> 1];
         float f[3][2];
 #pragma unroll
         for (int q = 0; q < 3; ++q) f2_unpack(f2_fma(QY2[q], uy, f2_fma(QX2[q], ux, P2[q])), f[q][0], f[q][1]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            if (fminf(f[0][h], fminf(f[1][h], f[2][h])) >= 0.f) hf |= 1u << (k + h);
-            if (!CULL && fmaxf(f[0][h], fmaxf(f[1][h], f[2][h])) <= 0.f) hb |= 1u << (k + h);
+            if (min3f(f[0][h], f[1][h], f[2][h]) >= 0.f) hf |= 1u << (k + h);
+            if (!CULL && max3f(f[0][h], f[1][h], f[2][h]) <= 0.f) hb |= 1u << (k + h);
         }
     }
     // an odd run's last pair repeats a step beyond it; the masks below drop that bit
@@ -267,7 +269,9 @@ __device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeRef
 template <bool COUNT, bool CULL>
 __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int K,
                                             float inv_dx, unsigned long long& n_cell,
-                                            unsigned long long& n_test) {
+                                            unsigned long long& n_test,
+                                            unsigned long long& n_unit,
+                                            unsigned long long& n_span) {
     const int lane = threadIdx.x & 31;
     const int t = un / nsub, sub = un - t * nsub;
     const int k0 = sub * K / nsub, kn = (sub + 1) * K / nsub - k0;     // balanced runs
@@ -346,6 +350,7 @@ __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int 
         if (lane >= o) incl += v;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (COUNT && lane == 0) { ++n_unit; n_span += (unsigned long long)total; }
     const int excl = incl - w;
     for (int base = 0; base < total; base += 32) {
         const int idx = base + lane;
@@ -376,7 +381,8 @@ __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int 
 template <bool COUNT, bool CULL, class Fetch>
 __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const StepConst* steps,
                              int j0, int K, float tox, float toy, float inv_dx, int kSub,
-                             unsigned long long& n_cell, unsigned long long& n_test) {
+                             unsigned long long& n_cell, unsigned long long& n_test,
+                             unsigned long long& n_unit, unsigned long long& n_span) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nsub = (K + kSub - 1) / kSub;
     __syncthreads();
@@ -448,7 +454,7 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
         // warps that would otherwise wait for its warp at the next barrier
         int un = warp;
         while (un < units) {
-            raster_unit<COUNT, CULL>(sm, un, nsub, K, inv_dx, n_cell, n_test);
+            raster_unit<COUNT, CULL>(sm, un, nsub, K, inv_dx, n_cell, n_test, n_unit, n_span);
             int nx = 0;
             if (lane == 0) nx = atomicAdd(&sm.next_unit, 1);
             un = __shfl_sync(0xffffffffu, nx, 0);
@@ -458,12 +464,18 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
 }
 
 __device__ __forceinline__ void flush_raster_counts(unsigned long long* stats, unsigned long long n_cell,
-                                                    unsigned long long n_test) {
+                                                    unsigned long long n_test,
+                                                    unsigned long long n_unit,
+                                                    unsigned long long n_span) {
     for (int o = 16; o > 0; o >>= 1) {
         n_cell += __shfl_down_sync(0xffffffffu, n_cell, o);
         n_test += __shfl_down_sync(0xffffffffu, n_test, o);
+        n_unit += __shfl_down_sync(0xffffffffu, n_unit, o);
+        n_span += __shfl_down_sync(0xffffffffu, n_span, o);
     }
     if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&stats[0], n_unit);
+        atomicAdd(&stats[1], n_span);
         atomicAdd(&stats[2], n_cell);
         atomicAdd(&stats[3], n_test);
     }
@@ -476,7 +488,7 @@ __global__ void __launch_bounds__(kRasterThreads, 4)
 k_raster(RasterArgs ra) {
     __shared__ TileSmem sm;
     __shared__ RunState s_st[kTile * kTile];       // gross / run / best of the tile's cells
-    unsigned long long n_cell = 0, n_test = 0;
+    unsigned long long n_cell = 0, n_test = 0, n_unit = 0, n_span = 0;
     const TileGeom& g = ra.g;
     const int tile = ra.order ? ra.order[blockIdx.x] : (int)blockIdx.x;
     const int tx = tile % g.tiles_x, ty = tile / g.tiles_x;
@@ -511,7 +523,7 @@ k_raster(RasterArgs ra) {
             return true;
         };
         raster_block<COUNT, CULL>(sm, fetch, (int)cnt, ra.sun.steps, bcp->j0, bcp->K, tox, toy,
-                                  inv_dx, ra.run, n_cell, n_test);
+                                  inv_dx, ra.run, n_cell, n_test, n_unit, n_span);
         const int K = bcp->K, new_day = bcp->new_day;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -537,7 +549,7 @@ k_raster(RasterArgs ra) {
         ra.out.run[o] = st.run;
         if (ra.final_chunk && ra.out.minutes) ra.out.minutes[o] = (float)st.gross * ra.out.step_minutes;
     }
-    if (COUNT) flush_raster_counts(ra.out.stats, n_cell, n_test);
+    if (COUNT) flush_raster_counts(ra.out.stats, n_cell, n_test, n_unit, n_span);
 }
 
 // --------------------------------------------------------------- batched scenarios
@@ -552,7 +564,7 @@ k_batch(BatchArgs ba) {
     __shared__ TileSmem sm;
     __shared__ RunState s_st[kTile * kTile];       // gross / run / best of the tile's cells
     __shared__ int s_item;
-    unsigned long long n_cell = 0, n_test = 0;
+    unsigned long long n_cell = 0, n_test = 0, n_unit = 0, n_span = 0;
     const TileGeom& g = ba.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row0 = warp * 4;
@@ -610,7 +622,7 @@ k_batch(BatchArgs ba) {
                 return true;
             };
             raster_block<COUNT, CULL>(sm, fetch, cnt + n_tow, iv.steps, bc.j0, bc.K, tox, toy,
-                                      inv_dx, ba.run, n_cell, n_test);
+                                      inv_dx, ba.run, n_cell, n_test, n_unit, n_span);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int cell = (row0 + q) * kTile + lane;
@@ -634,7 +646,7 @@ k_batch(BatchArgs ba) {
                 ba.impact_out[o] = gross - iv.base_counts[(long long)iy * g.nx + ix];
         }
     }
-    if (COUNT) flush_raster_counts(ba.stats, n_cell, n_test);
+    if (COUNT) flush_raster_counts(ba.stats, n_cell, n_test, n_unit, n_span);
 }
 
 // Launch order of the tiles: descending by the triangles binned to them over the chunk's

@@ -225,8 +225,9 @@ __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int 
         for (int c = 0; c < 3; ++c) M[e][c] = f2_pack(pt.m[e][c], pt.m[e][c]);
     N[0] = f2_pack(pt.nx, pt.nx); N[1] = f2_pack(pt.ny, pt.ny); N[2] = f2_pack(pt.nz, pt.nz);
     unsigned m = 0;
-#pragma unroll 2
-    for (int k = 0; k < kn; k += 2) {
+#pragma unroll
+    for (int k = 0; k < kRunMax; k += 2) {
+        if (k >= kn) break;
         const unsigned long long dx = s_d2[k >> 1][0], dy = s_d2[k >> 1][1], dz = s_d2[k >> 1][2];
         float sv[3][2], nd[2];
 #pragma unroll
@@ -235,8 +236,8 @@ __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int 
         f2_unpack(f2_fma(dz, N[2], f2_fma(dy, N[1], f2_mul(dx, N[0]))), nd[0], nd[1]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const bool inside = fminf(sv[0][h], fminf(sv[1][h], sv[2][h])) >= 0.f ||
-                                fmaxf(sv[0][h], fmaxf(sv[1][h], sv[2][h])) <= 0.f;
+            const bool inside = min3f(sv[0][h], sv[1][h], sv[2][h]) >= 0.f ||
+                                max3f(sv[0][h], sv[1][h], sv[2][h]) <= 0.f;
             const float lim = __fmul_rn(p.w, nd[h]);
             const bool ahead = (nd[h] > 0.f && pt.aon > lim) || (nd[h] < 0.f && pt.aon < lim);
             if (inside && ahead) m |= 1u << (k + h);
