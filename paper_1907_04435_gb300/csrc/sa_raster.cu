@@ -201,6 +201,8 @@ struct TileSmem {
     unsigned long long mask[kTile * kTile];
     float xl[kTile], yl[kTile];
     int next_unit;                           // next work unit of the batch to hand out
+    float inv_nsub;                          // 1 / runs of the block
+    unsigned char run_k0[kMaxBlock + 1];     // first step of each run, and K
 };
 
 // Tile origin and cell centres in tile-local coordinates; the centres are rounded exactly
@@ -273,8 +275,10 @@ __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int 
                                             unsigned long long& n_unit,
                                             unsigned long long& n_span) {
     const int lane = threadIdx.x & 31;
-    const int t = un / nsub, sub = un - t * nsub;
-    const int k0 = sub * K / nsub, kn = (sub + 1) * K / nsub - k0;     // balanced runs
+    // un = t nsub + sub; (un + 1/2) / nsub is at least 1 / (2 nsub) from an integer, far
+    // beyond the float quotient's rounding for un < 2^12
+    const int t = (int)(((float)un + 0.5f) * sm.inv_nsub), sub = un - t * nsub;
+    const int k0 = sm.run_k0[sub], kn = sm.run_k0[sub + 1] - k0;       // balanced runs
     const unsigned run_bits = (kn >= 32) ? 0xffffffffu : ((1u << kn) - 1u);
     const unsigned fr = (unsigned)(sm.front[t] >> k0) & run_bits;
     const unsigned bk = CULL ? 0u : ((unsigned)(sm.back[t] >> k0) & run_bits);
@@ -397,6 +401,8 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
         sm.upx[k & 1][k >> 1] = f2_pack(sm.u[k].x, sm.u[k1].x);
         sm.upy[k & 1][k >> 1] = f2_pack(sm.u[k].y, sm.u[k1].y);
     }
+    if (threadIdx.x <= nsub) sm.run_k0[threadIdx.x] = (unsigned char)(threadIdx.x * K / nsub);
+    if (threadIdx.x == 0) sm.inv_nsub = 1.f / (float)nsub;
     if (threadIdx.x < nsub) {
         const int k0 = threadIdx.x * K / nsub, k1 = (threadIdx.x + 1) * K / nsub;
         float4 b = make_float4(3.4e38f, -3.4e38f, 3.4e38f, -3.4e38f);
@@ -452,11 +458,12 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
         const int units = nt * nsub;
         // warps take units from a shared counter, so an expensive unit does not hold the
         // warps that would otherwise wait for its warp at the next barrier
+        // (the next unit is claimed before this one is worked, hiding the atomic's latency)
         int un = warp;
         while (un < units) {
-            raster_unit<COUNT, CULL>(sm, un, nsub, K, inv_dx, n_cell, n_test, n_unit, n_span);
             int nx = 0;
             if (lane == 0) nx = atomicAdd(&sm.next_unit, 1);
+            raster_unit<COUNT, CULL>(sm, un, nsub, K, inv_dx, n_cell, n_test, n_unit, n_span);
             un = __shfl_sync(0xffffffffu, nx, 0);
         }
     }
