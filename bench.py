@@ -54,7 +54,7 @@ class ClockSampler:
             self.f = open(path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}",
                                           f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
-                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -350,11 +350,11 @@ OPS_BOX, OPS_TRI = 12, 25
 # profile summary gives the command).  A figure is reported only while the kernel's
 # sources hash to the value they had when it was captured; otherwise traffic is null.
 TRAFFIC = {
-    "k_raster": {"bytes": 6988800 + 9983488, "workload": "district",
-                 "sources": ("sa_raster.cu", "sa_internal.cuh"), "sha256_16": "33a6f88e12d26f26"},
-    "k_sam_tile": {"bytes": 171865344 + 25958400, "workload": "district",
+    "k_raster": {"bytes": 6988800 + 6751488, "workload": "district",
+                 "sources": ("sa_raster.cu", "sa_internal.cuh"), "sha256_16": "1dd157a2394eae06"},
+    "k_sam_tile": {"bytes": 173326592 + 26281472, "workload": "district",
                    "sources": ("sa_sam_points.cu", "sa_internal.cuh", "sa_handles.cuh"),
-                   "sha256_16": "7e71bd8d9ceb6168"},
+                   "sha256_16": "30647a678fb8ed74"},
 }
 
 
@@ -599,7 +599,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="district")

@@ -249,7 +249,7 @@ __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int 
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, 9)   // 9 CTAs per SM: 55 registers, no spills
 k_sam_tile(TileArgs ta) {
     constexpr int kWarps = kTileThreads / 32;
     __shared__ float4 s_tri[kTriChunk * 3];
