@@ -292,3 +292,40 @@ def test_non_finite_points_are_rejected_and_the_context_stays_usable(cuda_lib):
     assert ex.value.status == -5 and "normal 42" in str(ex.value)
     ok = B.Receivers.points(pos, nrm)
     assert ok.R == 1000
+
+
+def test_scene_from_device_buffers_equals_scene_from_host_buffers(cuda_lib):
+    """sa_scene_from_mesh with device_ptrs = 1 reads the caller's device buffers in place and
+    builds the same scene (same counts for every method) as from host buffers; bad device
+    input is rejected with the same errors."""
+    import ctypes as ct
+    B = cuda_lib
+    L = B.lib()
+    w = workload("district_small")
+    host = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+    dv = torch.from_numpy(np.ascontiguousarray(w.mesh.verts, np.float32)).cuda()
+    dt = torch.from_numpy(np.ascontiguousarray(w.mesh.tris, np.int32)).cuda()
+    db = torch.from_numpy(np.ascontiguousarray(w.mesh.tri_building, np.int32)).cuda()
+    stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    h = ct.c_void_p()
+    assert L.sa_scene_from_mesh(ct.c_void_p(dv.data_ptr()), dv.shape[0], ct.c_void_p(dt.data_ptr()),
+                                dt.shape[0], ct.c_void_p(db.data_ptr()), w.city.B, 1, stream,
+                                ct.byref(h)) == 0
+    dev = B.Scene.__new__(B.Scene)
+    dev.handle, dev.n_buildings = h, w.city.B
+    B.lib().sa_scene_declare_closed(h, 1)
+    assert dev.info() == host.info()
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    grid = _ground(B, w)
+    fac = B.Receivers.points(w.facade_pos, w.facade_nrm)
+    for r, methods in ((grid, EXACT), (fac, POINT_METHODS)):
+        for m in methods:
+            a = _run(B, host, r, sun, m)
+            b = _run(B, dev, r, sun, m)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2]), m
+    bad = dt.clone()
+    bad[5, 1] = dv.shape[0]
+    h2 = ct.c_void_p()
+    assert L.sa_scene_from_mesh(ct.c_void_p(dv.data_ptr()), dv.shape[0], ct.c_void_p(bad.data_ptr()),
+                                bad.shape[0], None, 1, 1, stream, ct.byref(h2)) == -1
+    assert b"triangle 5" in L.sa_last_error()
