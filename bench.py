@@ -122,6 +122,15 @@ def make_workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def workload_config(args, w) -> dict:
+    """The workload part of the JSON line's config, the same for both arms."""
+    g = w.ground
+    nf = 0 if w.facade_pos is None else int(w.facade_pos.shape[0])
+    return {"workload": f"{args.workload}: {w.city.B} buildings, {w.mesh.T} triangles, "
+                        f"{g.nx}x{g.ny} ground @ {g.dx} m + {nf} facade samples, {w.sun.S} sun steps",
+            "receivers": int(w.R), "sun_steps": int(w.sun.S), "block_len": args.block_len or 60}
+
+
 def cpu_oracle_sample(w, seconds_hint: float = 15.0, seed: int = 0):
     """Time the FP64 oracle on a bounded receiver sample of the workload (all steps)."""
     import oracle
@@ -291,13 +300,10 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {w.city.B} buildings, {w.mesh.T} triangles, "
-                                   f"{g.nx}x{g.ny} ground @ {g.dx} m + "
-                                   f"{0 if fac is None else fac.R} facade samples, {st.S} sun steps",
-                       "receivers": R, "sun_steps": st.S, "block_len": args.block_len or 60,
-                       "method": "accrual_sam: ground accrual raster + facade light-space accrual map",
-                       "l2": "flushed (256 MB write) before every timed iteration",
-                       "parallelism": f"replicas x{world}"},
+            "config": dict(workload_config(args, w),
+                           method="accrual_sam: ground accrual raster + facade light-space accrual map",
+                           l2="flushed (256 MB write) before every timed iteration",
+                           parallelism=f"replicas x{world}"),
             "methods": methods,
             "roofline": roof,
             "roofline_kernels": roof_all,
@@ -577,11 +583,14 @@ def run_reference(args):
         return
     w = make_workload(args.workload)
     import oracle
+    # each step is a seeded receiver sample sized so that the whole run takes about
+    # 150 s of oracle work, at most cpu_seconds / 2 per step
+    per_step = max(0.5, min(args.cpu_seconds / 2, 150.0 / (args.steps + 0.5 * args.warmup)))
     vals = []
     for _ in range(args.warmup):
-        cpu_oracle_sample(w, args.cpu_seconds / 4)
+        cpu_oracle_sample(w, per_step / 2)
     for k in range(args.steps):
-        vals.append(cpu_oracle_sample(w, args.cpu_seconds / 2, seed=k))
+        vals.append(cpu_oracle_sample(w, per_step, seed=k))
     value = statistics.median([v["value"] for v in vals])
     s = vals[0]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
@@ -589,7 +598,8 @@ def run_reference(args):
             "ms_per_step": statistics.median([v["seconds"] for v in vals]) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "sample": s["sample"]},
+            "config": dict(workload_config(args, w), method="FP64 oracle on a seeded receiver sample",
+                           sample=s["sample"]),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.default_threads(),
                              "kind": "oracle", "sample": s["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
