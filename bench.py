@@ -537,22 +537,30 @@ def bench_configs(B):
 
 
 def end_to_end(B, w, args, dev):
-    """Same metric through the C ABI from host buffers: scene + BVH build, sun table,
-    receiver sort, accumulation, and the results copied back to pinned host memory."""
+    """Same metric through the C ABI from pinned host buffers: every step copies the mesh,
+    the sun table and the facade points to the device, builds the scene and its BVH, the
+    sun table and the sorted receivers, accumulates, and copies the results back to pinned
+    host memory."""
     import torch
+
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
     st = w.sun
     g = w.ground
-    verts, tris, tb = w.mesh.verts, w.mesh.tris, w.mesh.tri_building
-    fpos, fnrm = w.facade_pos, w.facade_nrm
+    verts, tris, tb = pinned(w.mesh.verts), pinned(w.mesh.tris), pinned(w.mesh.tri_building)
+    dirs, day_start = pinned(st.dirs), pinned(st.day_start)
+    fpos = None if w.facade_pos is None else pinned(w.facade_pos)
+    fnrm = None if w.facade_nrm is None else pinned(w.facade_nrm)
     R = g.R + (0 if fpos is None else fpos.shape[0])
     host_out = torch.empty(3 * R, dtype=torch.int32).pin_memory()
-    h2d = verts.nbytes + tris.nbytes + tb.nbytes + st.dirs.nbytes + st.day_start.nbytes + \
-        (0 if fpos is None else fpos.nbytes + fnrm.nbytes)
+    nbytes = lambda t: 0 if t is None else t.numel() * t.element_size()
+    h2d = sum(nbytes(t) for t in (verts, tris, tb, dirs, day_start, fpos, fnrm))
     d2h = 3 * R * 4
 
     def once():
         scene = B.Scene(verts, tris, tb, w.city.B, closed=True)
-        sun = B.Sun(st.dirs, st.day_start, args.block_len)
+        sun = B.Sun(dirs, day_start, args.block_len)
         grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
         gg, gm, gc = B.sa_accumulate(scene, grid, sun, st.step_minutes, "accrual_sam")
         parts = [gg, gm.view(torch.int32), gc]
