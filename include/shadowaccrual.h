@@ -62,8 +62,9 @@ typedef enum {
  *                     (the moving-shadow observation of Sec. 3.2 applied to rays).
  *   SA_ACCRUAL_SAM    shadow accrual map (Sec. 4): one pass over the geometry serves all
  *                     the steps of a block (ground grids: the receiver-space accrual
- *                     raster) or of a run of <= 8 steps (points: a light-space map
- *                     orthogonal to the run's middle direction, tested exactly per step).
+ *                     raster) or of a run of <= 32 steps (points: a light-space map
+ *                     orthogonal to the run's middle direction, tested exactly per step;
+ *                     SA_OPT_POINT_RUN sets the bound).
  *   SA_IAM            inverse accrual map (Sec. 5): L source levels traced from both
  *                     ends of each block, shadow lines drawn into per-step bit vectors.
  *                     Ground grids only; approximate by design. */

@@ -1,7 +1,7 @@
 // sa_sam_points.cu -- shadow accrual map for point receivers (facades), in light space.
 //
 // Sec. 4 renders the scene once per interval into a map on a plane orthogonal to the sun
-// direction and tests every receiver against its n slices.  Here each run of <= 16
+// direction and tests every receiver against its n slices.  Here each run of <= 32
 // consecutive steps of a block gets such a light-space map.  Coordinates are taken in a
 // basis (e1, e2) orthogonal to the run's middle direction d_m, around a reference point.
 // The map is a grid of light-space tiles:
