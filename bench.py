@@ -360,7 +360,7 @@ TRAFFIC = {
                  "sources": ("sa_raster.cu", "sa_internal.cuh"), "sha256_16": "1dd157a2394eae06"},
     "k_sam_tile": {"bytes": 173326592 + 26281472, "workload": "district",
                    "sources": ("sa_sam_points.cu", "sa_internal.cuh", "sa_handles.cuh"),
-                   "sha256_16": "30647a678fb8ed74"},
+                   "sha256_16": "b34def48448306d0"},
 }
 
 
