@@ -310,6 +310,23 @@ sa_status sa_batch_work_counters(sa_batch* b, uint64_t* counters, void* stream);
 sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
                            sa_method method, uint64_t* counters, void* stream);
 
+/* ---------------------------------------------------------------- analysis measures
+ * Shadow area over a polygonal region (Sec. 7.2, "Analysis measures"): the sum, over the
+ * cells of a ground grid whose centre lies inside the polygon (even-odd rule), of
+ * shadow(p) x area(p), with shadow(p) = steps[p] / total_steps the fraction of the
+ * interval's steps the cell is in shadow, and area(p) = dx^2.  Gross counts give the gross
+ * area, continuous counts the continuous one.  The paper's shadow score over intervals
+ * t with weights w_t in [-1, 1] is sum_t w_t x (the area of interval t).
+ *   grid: from sa_receivers_grid.  steps: int32 [nx * ny] device, in output order (as
+ *   sa_accumulate writes it).  poly_xy: float [n][2] host, n >= 3, a simple polygon of
+ *   either orientation.  total_steps > 0 (the interval's steps, e.g. S of its sun table).
+ *   *area (host) receives the area in square metres, summed in FP64.
+ * Cell centres are rounded as the receivers' (FP32) and tested in FP64.  Synchronises
+ * `stream`.  Errors: SA_ERR_INVALID_ARG (NULL, not a grid, n < 3, total_steps <= 0),
+ * SA_ERR_DEGENERATE (non-finite vertex), SA_ERR_CUDA. */
+sa_status sa_shadow_area(const sa_receivers* grid, const int32_t* steps, int32_t total_steps,
+                         const float* poly_xy, int32_t n, void* stream, double* area);
+
 /* ------------------------------------------------------------ allocation-free variant
  * The paper has no counterpart to this call; it exists for callers that cannot allocate
  * device memory while they run -- for example a host application that reserved the

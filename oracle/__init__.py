@@ -176,3 +176,43 @@ def accumulate(tri9, tri_building, pos, nrm, dirs, day_start, step_minutes,
     bits = shadow_bits(tri9, tri_building, pos, nrm, dirs, nthreads)
     g, c = reduce(bits, day_start)
     return g, (g.astype(np.float64) * step_minutes).astype(np.float32), c, bits
+
+
+# ------------------------------------------------------------------ analysis measures
+def point_in_polygon(x, y, poly):
+    """Even-odd rule for points (x, y) (FP64 arrays) against a polygon [n, 2]: a point is
+    inside when a ray from it toward +x crosses an odd number of edges."""
+    poly = np.asarray(poly, dtype=np.float64).reshape(-1, 2)
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    inside = np.zeros(np.broadcast(x, y).shape, dtype=bool)
+    n = poly.shape[0]
+    for i in range(n):
+        ax, ay = poly[i]
+        bx, by = poly[(i + 1) % n]
+        crosses = (ay > y) != (by > y)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = (y - ay) / (by - ay)
+            xc = ax + t * (bx - ax)
+        inside ^= crosses & (x < xc)
+    return inside
+
+
+def shadow_area(grid, steps, total_steps, poly):
+    """Shadow area over a polygonal region (Sec. 7.2): the sum over the grid cells whose
+    centre lies in the polygon of (steps / total_steps) x dx^2.  grid = (x0, y0, dx, nx, ny);
+    the centres are the receivers' FP32 centres."""
+    x0, y0, dx, nx, ny = grid
+    ix = np.arange(nx, dtype=np.float32)
+    iy = np.arange(ny, dtype=np.float32)
+    cx = np.float32(x0) + (ix + np.float32(0.5)) * np.float32(dx)
+    cy = np.float32(y0) + (iy + np.float32(0.5)) * np.float32(dx)
+    X, Y = np.meshgrid(cx.astype(np.float64), cy.astype(np.float64))
+    inside = point_in_polygon(X, Y, poly).ravel()
+    frac = np.asarray(steps, dtype=np.float64).ravel() / float(total_steps)
+    return float(frac[inside].sum()) * float(np.float32(dx)) ** 2
+
+
+def shadow_score(areas, weights):
+    """Shadow score (Sec. 7.2): the sum over intervals of weight x shadow area."""
+    return float(np.dot(np.asarray(weights, np.float64), np.asarray(areas, np.float64)))

@@ -89,13 +89,14 @@ def lib():
             L.sa_scene_set_heights.argtypes = [P, P, i32, P]
             L.sa_height_grad.argtypes = [P, P, P, f32, P, P, P, P]
             L.sa_kernel_times.argtypes = [P, P, i32]
+            L.sa_shadow_area.argtypes = [P, P, i32, P, i32, P, P]
             for name in ("sa_scene_from_mesh", "sa_scene_info", "sa_sun_create", "sa_sun_info",
                          "sa_receivers_grid", "sa_receivers_points", "sa_accumulate",
                          "sa_shadow_masks", "sa_accumulate_grid_noalloc", "sa_work_counters",
                          "sa_scene_from_footprints", "sa_scene_set_heights", "sa_height_grad",
                          "sa_scene_declare_closed", "sa_set_option", "sa_batch_create",
                          "sa_batch_run", "sa_batch_tune", "sa_batch_work_counters",
-                         "sa_kernel_times"):
+                         "sa_kernel_times", "sa_shadow_area"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
     return _lib
@@ -432,3 +433,28 @@ def block_sizes(day_start, block_len: int = 0):
         base, rem = divmod(n, nb)
         out += [base + (1 if q < rem else 0) for q in range(nb)]
     return out
+
+
+def sa_shadow_area(grid: Receivers, steps, total_steps: int, polygon, stream=None) -> float:
+    """Shadow area (m^2) over a polygon [n, 2] of a ground grid, from per-cell step counts
+    (an int32 CUDA tensor in output order) out of total_steps (Sec. 7.2)."""
+    if grid.grid is None:
+        raise SAError(-1, "sa_shadow_area: receivers must be a ground grid")
+    st = steps.detach().to(torch.int32).contiguous()
+    poly = _host_f32(polygon).reshape(-1, 2)
+    out = ct.c_double()
+    _check(lib().sa_shadow_area(grid.handle, _ptr(st), int(total_steps), _ptr(poly), poly.shape[0],
+                                ct.c_void_p(_stream(stream)), ct.byref(out)))
+    return float(out.value)
+
+
+def shadow_score(areas, weights) -> float:
+    """Shadow score over intervals (Sec. 7.2): sum of weight x shadow area, weights in
+    [-1, 1] (Table 3 gives one such weighting by month)."""
+    a = np.asarray(areas, dtype=np.float64).reshape(-1)
+    w = np.asarray(weights, dtype=np.float64).reshape(-1)
+    if a.shape != w.shape:
+        raise ValueError("one weight per interval")
+    if np.any(np.abs(w) > 1.0):
+        raise ValueError("weights must lie in [-1, 1]")
+    return float(np.dot(w, a))

@@ -1,0 +1,111 @@
+"""Pins of the oracle's analysis measures (Sec. 7.2): shadow area over a polygonal region
+and the shadow score, checked against index-range sums, an independent inside test,
+additivity, orientation independence and the month weights of Table 3."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GRID = (8.25, 6.75, 2.5, 200, 150)          # x0, y0, dx, nx, ny (the small district's grid)
+
+
+def _steps(seed=0, hi=100):
+    x0, y0, dx, nx, ny = GRID
+    return np.random.default_rng(seed).integers(0, hi, nx * ny)
+
+
+def _rect(ix0, ix1, iy0, iy1):
+    """Polygon along cell boundaries enclosing cells [ix0, ix1) x [iy0, iy1)."""
+    x0, y0, dx, _, _ = GRID
+    xa, xb = x0 + ix0 * dx, x0 + ix1 * dx
+    ya, yb = y0 + iy0 * dx, y0 + iy1 * dx
+    return np.array([[xa, ya], [xb, ya], [xb, yb], [xa, yb]], np.float64)
+
+
+def test_rectangle_on_cell_boundaries_sums_its_cells():
+    x0, y0, dx, nx, ny = GRID
+    s = _steps()
+    got = oracle.shadow_area(GRID, s, 100, _rect(20, 77, 13, 91))
+    want = s.reshape(ny, nx)[13:91, 20:77].sum() / 100 * dx * dx
+    assert got == pytest.approx(want, rel=1e-12)
+
+
+def test_whole_grid_and_empty_region():
+    x0, y0, dx, nx, ny = GRID
+    s = _steps(1)
+    assert oracle.shadow_area(GRID, s, 100, _rect(0, nx, 0, ny)) == pytest.approx(s.sum() / 100 * dx * dx, rel=1e-12)
+    # a sliver between two columns of centres holds no centre
+    xa = x0 + 10.6 * dx
+    sliver = np.array([[xa, y0], [xa + 0.2 * dx, y0], [xa + 0.2 * dx, y0 + ny * dx], [xa, y0 + ny * dx]])
+    assert oracle.shadow_area(GRID, s, 100, sliver) == 0.0
+    # fully shadowed cells: the area is the cells' area
+    full = np.full(nx * ny, 100)
+    assert oracle.shadow_area(GRID, full, 100, _rect(5, 45, 7, 17)) == pytest.approx(40 * 10 * dx * dx, rel=1e-12)
+
+
+def test_orientation_and_starting_vertex_do_not_matter():
+    s = _steps(2)
+    poly = np.array([[60.0, 40.0], [420.0, 90.0], [300.0, 330.0], [150.0, 250.0], [90.0, 300.0]])
+    a = oracle.shadow_area(GRID, s, 100, poly)
+    assert oracle.shadow_area(GRID, s, 100, poly[::-1]) == a
+    assert oracle.shadow_area(GRID, s, 100, np.roll(poly, 2, axis=0)) == a
+    assert a > 0
+
+
+def test_triangle_inside_test_matches_barycentric_signs():
+    x0, y0, dx, nx, ny = GRID
+    tri = np.array([[37.3, 22.9], [401.7, 120.4], [155.2, 341.8]])
+    ix, iy = np.meshgrid(np.arange(nx, dtype=np.float32), np.arange(ny, dtype=np.float32))
+    cx = (np.float32(x0) + (ix + np.float32(0.5)) * np.float32(dx)).astype(np.float64)
+    cy = (np.float32(y0) + (iy + np.float32(0.5)) * np.float32(dx)).astype(np.float64)
+
+    def side(a, b):
+        return (b[0] - a[0]) * (cy - a[1]) - (b[1] - a[1]) * (cx - a[0])
+
+    s0, s1, s2 = side(tri[0], tri[1]), side(tri[1], tri[2]), side(tri[2], tri[0])
+    bary = ((s0 > 0) & (s1 > 0) & (s2 > 0)) | ((s0 < 0) & (s1 < 0) & (s2 < 0))
+    clear = np.minimum(np.minimum(np.abs(s0), np.abs(s1)), np.abs(s2)) > 1e-6
+    pip = oracle.point_in_polygon(cx, cy, tri)
+    assert np.array_equal(pip[clear], bary[clear])
+    assert bary.sum() > 1000
+
+
+def test_non_convex_region_is_the_sum_of_its_parts():
+    s = _steps(3)
+    # an L made of cells [10, 60) x [10, 30) and [10, 30) x [30, 80)
+    x0, y0, dx, _, _ = GRID
+    X = lambda i: x0 + i * dx
+    Y = lambda j: y0 + j * dx
+    ell = np.array([[X(10), Y(10)], [X(60), Y(10)], [X(60), Y(30)], [X(30), Y(30)],
+                    [X(30), Y(80)], [X(10), Y(80)]])
+    a = oracle.shadow_area(GRID, s, 100, ell)
+    b = oracle.shadow_area(GRID, s, 100, _rect(10, 60, 10, 30)) + oracle.shadow_area(GRID, s, 100, _rect(10, 30, 30, 80))
+    assert a == pytest.approx(b, rel=1e-12)
+
+
+def _table3():
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "table3_month_weights.txt"))
+            if l.strip() and not l.startswith("#")]
+    return [r[0] for r in rows], np.array([float(r[1]) for r in rows])
+
+
+def test_shadow_score_with_the_month_weights_of_table3():
+    months, w = _table3()
+    assert months == ["Jan", "Feb", "Mar", "Apr", "May", "Jun", "Jul", "Aug", "Sep", "Oct", "Nov", "Dec"]
+    assert np.all(np.abs(w) <= 1)
+    # the weights balance: the same shadow every month scores zero
+    assert oracle.shadow_score(np.full(12, 1234.5), w) == pytest.approx(0.0, abs=1e-9)
+    # shadow only from May to September scores the sum of those weights
+    summer = np.array([0, 0, 0, 0, 1, 1, 1, 1, 1, 0, 0, 0], np.float64) * 100.0
+    assert oracle.shadow_score(summer, w) == pytest.approx(400.0)
+    # the binding's host formula agrees, and refuses weights outside [-1, 1]
+    from paper_1907_04435_gb300 import binding as B
+    areas = np.random.default_rng(4).uniform(0, 1e4, 12)
+    assert B.shadow_score(areas, w) == pytest.approx(oracle.shadow_score(areas, w), rel=1e-15)
+    with pytest.raises(ValueError):
+        B.shadow_score(areas, w * 1.5)
+    with pytest.raises(ValueError):
+        B.shadow_score(areas[:11], w)
