@@ -49,6 +49,8 @@ def lib():
             L.sao_shadow_integral.argtypes = [P, P, i64, P, i64, P, P, i32, f64, P, i32, P, P, ci]
             L.sao_iam.argtypes = [P, P, i64, f32, f32, f32, i32, i32, P, P, P, i32, i32, f64,
                                   i32, i32, P, ci]
+            L.sao_building_steps.argtypes = [P, P, i64, P, P, i64, P, P, i32, f64, i32, P, P, P,
+                                             P, ci]
             _lib = L
     return _lib
 
@@ -216,3 +218,26 @@ def shadow_area(grid, steps, total_steps, poly):
 def shadow_score(areas, weights):
     """Shadow score (Sec. 7.2): the sum over intervals of weight x shadow area."""
     return float(np.dot(np.asarray(weights, np.float64), np.asarray(areas, np.float64)))
+
+
+def building_steps(tri9, tri_building, pos, nrm, dirs, day_start, n_buildings, eps=1e-4,
+                   nthreads: int | None = None):
+    """Building contribution counts (Sec. 7.2) over the given receivers and all steps:
+    (casting [B], nearest [B], unstable [B], unstable_any) as int64 -- pairs whose ray meets
+    each building, pairs whose nearest hit is on it, pairs where meeting it flips under a
+    +-eps rotation along the sun arc, and pairs where any building flips."""
+    t9 = _f32(tri9).reshape(-1, 9)
+    tb = _i32(tri_building).reshape(-1)
+    p = _f32(pos).reshape(-1, 3)
+    n = None if nrm is None else _f32(nrm).reshape(-1, 3)
+    d = _f32(dirs).reshape(-1, 3)
+    ds = _i32(day_start).reshape(-1)
+    out = [np.zeros(int(n_buildings), np.int64) for _ in range(3)]
+    anyc = np.zeros(1, np.int64)
+    rc = lib().sao_building_steps(_ptr(t9), _ptr(tb), t9.shape[0], _ptr(p), _ptr(n), p.shape[0],
+                                  _ptr(d), _ptr(ds), ds.shape[0] - 1, float(eps), int(n_buildings),
+                                  _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _ptr(anyc),
+                                  nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"sao_building_steps failed ({rc})")
+    return out[0], out[1], out[2], int(anyc[0])

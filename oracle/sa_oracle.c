@@ -527,3 +527,95 @@ int sao_shadow_integral(const float* tri9, const int32_t* tri_building, int64_t 
     scene_free(&sc);
     return 0;
 }
+
+/* ---------------------------------------------------------------- building contribution
+ * Sec. 7.2 ("Building contribution"): the shadow that results from each building.  For a
+ * receiver and step, building g casts the shadow when the ray meets one of g's triangles
+ * beyond t_min; the nearest caster is the building of the nearest such hit.  Summed over
+ * the given receivers and all steps:
+ *   casting[g]    pairs (receiver, step) whose ray meets building g
+ *   nearest[g]    pairs whose nearest hit lies on building g
+ *   unstable[g]   pairs where rotating d_j by +-eps along the sun arc changes whether the
+ *                 ray meets g (the parity bar's near-boundary rule, per building)
+ *   *unstable_any pairs where that happens for some building
+ * Buildings are the tri_building groups; n_buildings must exceed every id. */
+static int building_hit(const oscene* s, int32_t g, const double* o, const double* d,
+                        double tmin, double* t_best) {
+    if (!ray_box(o, d, s->gbox + 6 * g)) return 0;
+    int hit = 0;
+    for (int64_t i = s->goff[g]; i < s->goff[g + 1]; ++i) {
+        double t;
+        if (ray_tri(o, d, &s->tri[s->gtri[i]], tmin, &t)) {
+            if (!hit || t < *t_best) *t_best = t;
+            hit = 1;
+        }
+    }
+    return hit;
+}
+
+int sao_building_steps(const float* tri9, const int32_t* tri_building, int64_t T,
+                       const float* pos, const float* nrm, int64_t R,
+                       const float* dirs, const int32_t* day_start, int32_t D, double eps,
+                       int32_t n_buildings, int64_t* casting, int64_t* nearest,
+                       int64_t* unstable, int64_t* unstable_any, int nthreads) {
+    if (T < 0 || R < 0 || D < 0 || n_buildings < 1) return -1;
+    int32_t S = D > 0 ? day_start[D] : 0;
+    oscene sc;
+    if (scene_init(&sc, tri9, tri_building, T) != 0) { scene_free(&sc); return -3; }
+    if (sc.G > n_buildings) { scene_free(&sc); return -1; }
+    set_threads(nthreads);
+    double* rot = (double*)malloc(sizeof(double) * 6 * (size_t)(S > 0 ? S : 1));
+    uint8_t* has = (uint8_t*)malloc((size_t)(S > 0 ? S : 1));
+    for (int32_t k = 0; k < D; ++k)
+        for (int32_t j = day_start[k]; j < day_start[k + 1]; ++j) {
+            double t[3], d[3];
+            has[j] = (uint8_t)arc_tangent(dirs, j, day_start[k], day_start[k + 1], t);
+            for (int c = 0; c < 3; ++c) d[c] = dirs[3 * j + c];
+            double dn = sqrt(dot3(d, d));
+            for (int c = 0; c < 3; ++c) {
+                rot[6 * j + c] = cos(eps) * d[c] / dn + sin(eps) * (has[j] ? t[c] : 0.0);
+                rot[6 * j + 3 + c] = cos(eps) * d[c] / dn - sin(eps) * (has[j] ? t[c] : 0.0);
+            }
+        }
+    for (int32_t g = 0; g < n_buildings; ++g) casting[g] = nearest[g] = unstable[g] = 0;
+    int64_t any_total = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : any_total)
+    for (int64_t r = 0; r < R; ++r) {
+        double o[3], tmin;
+        receiver_origin(pos, nrm, r, o, &tmin);
+        for (int32_t j = 0; j < S; ++j) {
+            double d[3] = {(double)dirs[3 * j], (double)dirs[3 * j + 1], (double)dirs[3 * j + 2]};
+            int32_t best_g = -1;
+            double best_t = INFINITY;
+            int any_flip = 0;
+            for (int32_t g = 0; g < sc.G; ++g) {
+                double t = INFINITY;
+                const int h = building_hit(&sc, g, o, d, tmin, &t);
+                if (h) {
+#pragma omp atomic
+                    casting[g]++;
+                    if (t < best_t) { best_t = t; best_g = g; }
+                }
+                if (has[j]) {
+                    double tp, tm;
+                    const int flip = building_hit(&sc, g, o, rot + 6 * j, tmin, &tp) != h ||
+                                     building_hit(&sc, g, o, rot + 6 * j + 3, tmin, &tm) != h;
+                    if (flip) {
+#pragma omp atomic
+                        unstable[g]++;
+                        any_flip = 1;
+                    }
+                }
+            }
+            if (best_g >= 0) {
+#pragma omp atomic
+                nearest[best_g]++;
+            }
+            any_total += any_flip;
+        }
+    }
+    *unstable_any = any_total;
+    free(rot); free(has);
+    scene_free(&sc);
+    return 0;
+}

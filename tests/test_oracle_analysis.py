@@ -109,3 +109,62 @@ def test_shadow_score_with_the_month_weights_of_table3():
         B.shadow_score(areas, w * 1.5)
     with pytest.raises(ValueError):
         B.shadow_score(areas[:11], w)
+
+
+# ------------------------------------------------------------- building contribution
+def _boxes_case(n_cells=300, seed=5):
+    from synth import configs
+    w = configs.boxes16()
+    rng = np.random.default_rng(seed)
+    pos = w.ground.positions()[rng.choice(w.ground.R, n_cells, replace=False)]
+    return w, pos
+
+
+def test_building_counts_agree_with_the_plain_shadow_bits():
+    w, pos = _boxes_case()
+    t9, tb = w.mesh.tri9(), w.mesh.tri_building
+    casting, nearest, unstable, unstable_any = oracle.building_steps(
+        t9, tb, pos, None, w.sun.dirs, w.sun.day_start, w.city.B)
+    bits = oracle.shadow_bits(t9, tb, pos, None, w.sun.dirs)
+    # every shadowed pair has exactly one nearest caster, and no lit pair has any
+    assert nearest.sum() == bits.sum() > 0
+    assert casting.sum() >= nearest.sum()
+    assert np.all(nearest <= casting)
+    # each building's casting count is its own shadow alone (the scene of its triangles)
+    for b in range(w.city.B):
+        keep = tb == b
+        own = oracle.shadow_bits(t9[keep], np.zeros(int(keep.sum()), np.int32), pos, None, w.sun.dirs)
+        assert casting[b] == own.sum(), b
+    # the per-building near-boundary counts bound each other as sets do
+    assert unstable_any <= unstable.sum()
+    near = oracle.near_boundary(t9, tb, pos, None, w.sun.dirs, w.sun.day_start, bits)
+    assert near.sum() <= unstable_any
+
+
+def test_single_building_counts_are_its_shadow_and_near_boundary():
+    w, pos = _boxes_case(200, seed=6)
+    t9, tb = w.mesh.tri9(), w.mesh.tri_building
+    keep = tb == 5
+    t9b, tbb = t9[keep], np.zeros(int(keep.sum()), np.int32)
+    casting, nearest, unstable, unstable_any = oracle.building_steps(
+        t9b, tbb, pos, None, w.sun.dirs, w.sun.day_start, 1)
+    bits = oracle.shadow_bits(t9b, tbb, pos, None, w.sun.dirs)
+    near = oracle.near_boundary(t9b, tbb, pos, None, w.sun.dirs, w.sun.day_start, bits)
+    assert casting[0] == nearest[0] == bits.sum()
+    assert unstable[0] == unstable_any == near.sum()
+
+
+def test_the_nearer_of_two_buildings_in_line_is_the_nearest_caster():
+    """Two boxes one behind the other toward a low sun in the east: a receiver west of
+    both is shadowed by both, and the nearer (western) box holds every nearest hit."""
+    from synth import city as C
+    city = C.City([C.box_footprint(10, -5, 20, 5), C.box_footprint(40, -5, 50, 5)],
+                  np.array([30.0, 60.0], np.float32))
+    mesh = C.extrude(city)
+    el = np.radians(20.0)
+    dirs = np.array([[np.cos(el), 0.0, np.sin(el)]], np.float32)      # toward the east
+    pos = np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.0], [-1.0, -0.5, 0.0]], np.float32)
+    casting, nearest, _, _ = oracle.building_steps(mesh.tri9(), mesh.tri_building, pos, None,
+                                                   dirs, np.array([0, 1], np.int32), 2)
+    assert list(casting) == [3, 3]
+    assert list(nearest) == [3, 0]
