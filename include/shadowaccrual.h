@@ -327,6 +327,36 @@ sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, cons
 sa_status sa_shadow_area(const sa_receivers* grid, const int32_t* steps, int32_t total_steps,
                          const float* poly_xy, int32_t n, void* stream, double* area);
 
+/* Building contribution to the shadow of a region (Sec. 7.2, the contribution of each
+ * building to the analysis measures): for every cell of a ground grid whose centre lies
+ * inside the polygon (as in sa_shadow_area) and every step of `sun` at which the cell is in
+ * shadow, the ray from the cell centre toward the sun is followed through the whole scene
+ * and each building it meets beyond t_min = 1e-3 is credited dx^2 / S (S = the sun table's
+ * steps).
+ *   casting[b]: the area building b shadows on its own, over the interval (a cell-step
+ *     shadowed by several buildings is credited to each of them, so the sum over buildings
+ *     is at least the region's gross shadow area).
+ *   nearest[b]: the area for which b holds the nearest hit along the ray; these partition
+ *     the region's shadow: their sum plus stats[1] x dx^2 / S is its gross shadow area
+ *     (sa_shadow_area of the gross counts with total_steps = S).
+ *   scene: any (mesh or footprints); building ids are the ones the scene was built with.
+ *   grid: from sa_receivers_grid.  poly_xy: float [n][2] host, n >= 3.
+ *   casting, nearest: double [n_buildings] host.  stats: int64 [2] host, nullable:
+ *     [0] cell-steps whose ray met more than 32 distinct buildings (those past the 32nd
+ *         are not credited in casting; nearest is exact);
+ *     [1] cell-steps the raster marks shadowed whose ray met no triangle beyond t_min in
+ *         FP32 (rays that graze a shadow edge), credited to no building.
+ * The shadowed steps come from the ground accrual raster (as SA_ACCRUAL_SAM computes
+ * them); the call keeps its per-step masks, 8 bytes per cell and block of steps, and
+ * rejects with SA_ERR_INVALID_ARG a grid and sun table whose masks exceed 4 GiB (split the
+ * interval).  Synchronises `stream`.  Errors: SA_ERR_INVALID_ARG (NULL, not a grid,
+ * n < 3), SA_ERR_DEGENERATE (non-finite vertex), SA_ERR_UNSUPPORTED (geometry below
+ * z = 0, as for the raster methods), SA_ERR_OOM, SA_ERR_CUDA. */
+sa_status sa_building_contribution(const sa_scene* scene, const sa_receivers* grid,
+                                   const sa_sun* sun, const float* poly_xy, int32_t n,
+                                   void* stream, double* casting, double* nearest,
+                                   int64_t* stats);
+
 /* ------------------------------------------------------------ allocation-free variant
  * The paper has no counterpart to this call; it exists for callers that cannot allocate
  * device memory while they run -- for example a host application that reserved the

@@ -90,13 +90,14 @@ def lib():
             L.sa_height_grad.argtypes = [P, P, P, f32, P, P, P, P]
             L.sa_kernel_times.argtypes = [P, P, i32]
             L.sa_shadow_area.argtypes = [P, P, i32, P, i32, P, P]
+            L.sa_building_contribution.argtypes = [P, P, P, P, i32, P, P, P, P]
             for name in ("sa_scene_from_mesh", "sa_scene_info", "sa_sun_create", "sa_sun_info",
                          "sa_receivers_grid", "sa_receivers_points", "sa_accumulate",
                          "sa_shadow_masks", "sa_accumulate_grid_noalloc", "sa_work_counters",
                          "sa_scene_from_footprints", "sa_scene_set_heights", "sa_height_grad",
                          "sa_scene_declare_closed", "sa_set_option", "sa_batch_create",
                          "sa_batch_run", "sa_batch_tune", "sa_batch_work_counters",
-                         "sa_kernel_times", "sa_shadow_area"):
+                         "sa_kernel_times", "sa_shadow_area", "sa_building_contribution"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
     return _lib
@@ -446,6 +447,27 @@ def sa_shadow_area(grid: Receivers, steps, total_steps: int, polygon, stream=Non
     _check(lib().sa_shadow_area(grid.handle, _ptr(st), int(total_steps), _ptr(poly), poly.shape[0],
                                 ct.c_void_p(_stream(stream)), ct.byref(out)))
     return float(out.value)
+
+
+def sa_building_contribution(scene: Scene, grid: Receivers, sun: Sun, polygon, stream=None):
+    """Per-building shadow over a polygon of a ground grid (Sec. 7.2), in m^2 over the sun
+    table's interval: (casting, nearest, stats).  casting[b] is the area building b
+    shadows on its own; nearest[b] the area where b is the nearest caster.  stats[0]
+    counts cell-steps that met more than 32 buildings (casting is short for those),
+    stats[1] shadowed cell-steps whose ray grazed past every triangle; sum(nearest) plus
+    stats[1] x dx^2 / S is the region's gross shadow area."""
+    if grid.grid is None:
+        raise SAError(-1, "sa_building_contribution: receivers must be a ground grid")
+    poly = _host_f32(polygon).reshape(-1, 2)
+    nb = max(int(scene.n_buildings), 1)
+    casting = np.zeros(nb, np.float64)
+    nearest = np.zeros(nb, np.float64)
+    stats = np.zeros(2, np.int64)
+    _check(lib().sa_building_contribution(scene.handle, grid.handle, sun.handle, _ptr(poly), poly.shape[0],
+                                          ct.c_void_p(_stream(stream)), casting.ctypes.data,
+                                          nearest.ctypes.data, stats.ctypes.data))
+    n = int(scene.n_buildings)
+    return casting[:n], nearest[:n], (int(stats[0]), int(stats[1]))
 
 
 def shadow_score(areas, weights) -> float:

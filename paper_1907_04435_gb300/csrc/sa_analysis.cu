@@ -12,6 +12,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -60,7 +62,142 @@ __global__ void k_shadow_area(const int* __restrict__ steps, float x0, float y0,
     }
 }
 
+// Building contribution (Sec. 7.2): for every cell of the region and every step the
+// accrual raster marks as shadowed, one ray toward the sun collects the buildings it meets
+// beyond t_min (all of them, through the whole BVH) and the building of the nearest hit.
+// Each of them is credited dx^2 / total_steps: "casting" sums the shadow each building casts
+// on the region, overlaps counted once per building; "nearest" splits the region's shadow
+// area among the nearest casters, so it sums to the shadow area itself, less the cell-steps
+// the raster marks shadowed whose FP32 ray grazes past every triangle (shadow edges),
+// which are counted apart.
+constexpr int kMaxCasters = 32;
+constexpr int kContribThreads = 128;
+
+__global__ void k_building_contribution(DevScene sc, const StepConst* __restrict__ steps,
+                                        const BlockConst* __restrict__ blocks, int n_blocks,
+                                        const unsigned long long* __restrict__ masks,
+                                        float x0, float y0, float dx, int nx, long long R,
+                                        const double2* __restrict__ poly, int n, double w,
+                                        double* __restrict__ casting, double* __restrict__ nearest,
+                                        unsigned long long* __restrict__ stats) {
+    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= R * n_blocks) return;
+    const long long c = item % R;
+    const int bl = (int)(item / R);
+    const BlockConst& bc = blocks[bl];
+    unsigned long long m = masks[(long long)bc.mask_block * R + c] >> bc.mask_bit;
+    if (bc.K < 64) m &= (1ull << bc.K) - 1ull;
+    if (m == 0ull) return;
+    const int ix = (int)(c % nx), iy = (int)(c / nx);
+    float3 o;
+    o.x = __fadd_rn(x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), dx));
+    o.y = __fadd_rn(y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), dx));
+    o.z = 0.f;
+    if (!inside_polygon(poly, n, (double)o.x, (double)o.y)) return;
+    int ids[kMaxCasters];
+    while (m) {
+        const int k = __ffsll((long long)m) - 1;
+        m &= m - 1ull;
+        const StepConst& s = steps[bc.j0 + k];
+        int nh = 0, best = -1;
+        float best_t = 3.4e38f;
+        bool lost = false;
+        for (int i = 0; i < sc.n_nodes;) {
+            const float4 lo = __ldg(&sc.nodes[2 * i]);
+            const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
+            const int esc = __float_as_int(lo.w);
+            const int tri = __float_as_int(hi.w);
+            const bool in = hit_box(o, s.ix, s.iy, s.iz, lo, hi);
+            if (tri >= 0) {
+                if (in) {
+                    const float4 a = __ldg(&sc.tris[3 * tri]);
+                    const float4 b = __ldg(&sc.tris[3 * tri + 1]);
+                    const float4 cc = __ldg(&sc.tris[3 * tri + 2]);
+                    const float t = hit_dist_any(s.kz, o, a, b, cc, s, kGroundTmin);
+                    if (t >= 0.f) {
+                        const int bid = __float_as_int(a.w);
+                        if (t < best_t) { best_t = t; best = bid; }
+                        bool seen = false;
+                        for (int q = 0; q < nh; ++q) seen |= (ids[q] == bid);
+                        if (!seen) {
+                            if (nh < kMaxCasters) ids[nh++] = bid;
+                            else lost = true;
+                        }
+                    }
+                }
+                i = esc;
+            } else {
+                i = in ? i + 1 : esc;
+            }
+        }
+        for (int q = 0; q < nh; ++q) atomicAdd(&casting[ids[q]], w);
+        if (best >= 0) atomicAdd(&nearest[best], w);
+        else atomicAdd(&stats[1], 1ull);     // marked shadowed by the raster, ray met nothing
+        if (lost) atomicAdd(&stats[0], 1ull);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                                         int n_buildings, const float* poly_xy, int n,
+                                         double* casting_out, double* nearest_out,
+                                         unsigned long long* stats_out, cudaStream_t st) {
+    const long long R = (long long)rc.nx * rc.ny;
+    const int B = n_buildings > 0 ? n_buildings : 1;
+    cudaError_t e = cudaSuccess;
+    unsigned long long *masks = nullptr, *ovf = nullptr;
+    int *gross = nullptr, *run = nullptr;
+    double2* dp = nullptr;
+    double* acc = nullptr;
+    std::vector<double2> hp((size_t)n);
+    for (int i = 0; i < n; ++i) hp[(size_t)i] = make_double2((double)poly_xy[2 * i], (double)poly_xy[2 * i + 1]);
+    std::vector<double> h_acc(2 * (size_t)B, 0.0);
+    unsigned long long h_stats[2] = {0ull, 0ull};
+#define TRY(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
+    TRY(sa::scratch_alloc(&acc, sizeof(double) * 2 * (size_t)B, st));
+    TRY(sa::scratch_alloc(&ovf, 2 * sizeof(unsigned long long), st));
+    TRY(sa::scratch_alloc(&dp, sizeof(double2) * (size_t)n, st));
+    TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 2 * (size_t)B, st));
+    TRY(cudaMemsetAsync(ovf, 0, 2 * sizeof(unsigned long long), st));
+    TRY(cudaMemcpyAsync(dp, hp.data(), sizeof(double2) * (size_t)n, cudaMemcpyHostToDevice, st));
+    if (R > 0 && sun.n_blocks > 0 && sc.T > 0) {
+        // the accrual raster's per-block step masks mark the shadowed steps
+        TRY(sa::scratch_alloc(&masks, sizeof(unsigned long long) * (size_t)R * sun.n_blocks, st));
+        TRY(cudaMemsetAsync(masks, 0, sizeof(unsigned long long) * (size_t)R * sun.n_blocks, st));
+        TRY(sa::scratch_alloc(&gross, sizeof(int) * (size_t)R, st));
+        TRY(sa::scratch_alloc(&run, sizeof(int) * (size_t)R, st));
+        {
+            DevOut out;
+            memset(&out, 0, sizeof(out));
+            out.gross = gross;
+            out.run = run;
+            out.masks = reinterpret_cast<uint64_t*>(masks);
+            TRY(launch_raster_ground(sc, rc, sun, out, st));
+        }
+        const long long items = R * sun.n_blocks;
+        const double w = (double)rc.dx * (double)rc.dx / (double)sun.S;
+        k_building_contribution<<<(unsigned)((items + kContribThreads - 1) / kContribThreads),
+                                  kContribThreads, 0, st>>>(
+            sc, sun.steps, sun.blocks, sun.n_blocks, masks, rc.x0, rc.y0, rc.dx, rc.nx, R, dp, n, w,
+            acc, acc + B, ovf);
+        TRY(cudaGetLastError());
+    }
+    TRY(cudaMemcpyAsync(h_acc.data(), acc, sizeof(double) * 2 * (size_t)B, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(h_stats, ovf, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    for (int b = 0; b < n_buildings; ++b) {
+        casting_out[b] = h_acc[(size_t)b];
+        nearest_out[b] = h_acc[(size_t)B + b];
+    }
+    stats_out[0] = h_stats[0];
+    stats_out[1] = h_stats[1];
+done:
+    for (void* p : {(void*)masks, (void*)ovf, (void*)gross, (void*)run, (void*)dp, (void*)acc})
+        if (p) cudaFreeAsync(p, st);
+    return e;
+#undef TRY
+}
 
 }  // namespace sa
 

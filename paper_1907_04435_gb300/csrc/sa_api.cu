@@ -779,6 +779,40 @@ sa_status sa_height_grad(const sa_scene* scene, const sa_receivers* grid, const 
     return SA_OK;
 }
 
+sa_status sa_building_contribution(const sa_scene* scene, const sa_receivers* grid,
+                                   const sa_sun* sun, const float* poly_xy, int32_t n,
+                                   void* stream, double* casting, double* nearest,
+                                   int64_t* stats) {
+    const char* who = "sa_building_contribution";
+    if (!scene || !grid || !sun || !poly_xy) return fail(SA_ERR_INVALID_ARG, "%s: NULL argument", who);
+    if (scene->n_buildings > 0 && (!casting || !nearest))
+        return fail(SA_ERR_INVALID_ARG, "%s: NULL output", who);
+    if (!grid->is_grid) return fail(SA_ERR_INVALID_ARG, "%s: receivers must be a ground grid", who);
+    if (n < 3) return fail(SA_ERR_INVALID_ARG, "%s: a polygon needs 3 vertices", who);
+    for (int i = 0; i < 2 * n; ++i)
+        if (!isfinite(poly_xy[i])) return fail(SA_ERR_DEGENERATE, "%s: non-finite polygon vertex", who);
+    if (scene->T > 0 && scene->min_z < 0.f)
+        return fail(SA_ERR_UNSUPPORTED, "%s: scene geometry below z = 0", who);
+    const double mask_bytes = 8.0 * (double)grid->R * (double)sun->h_blocks.size();
+    if (mask_bytes > 4.0 * 1024.0 * 1024.0 * 1024.0)
+        return fail(SA_ERR_INVALID_ARG, "%s: step masks of %.0f bytes exceed 4 GiB; split the interval", who,
+                    mask_bytes);
+    sa::DevSun dsun;
+    dsun.steps = sun->d_steps;
+    dsun.blocks = sun->d_blocks;
+    dsun.S = sun->S;
+    dsun.n_blocks = (int)sun->h_blocks.size();
+    unsigned long long h[2] = {0ull, 0ull};
+    cudaError_t e = sa::launch_building_contribution(dev_scene(scene), dev_recv(grid), dsun, scene->n_buildings,
+                                                     poly_xy, n, casting, nearest, h, as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    if (stats) {
+        stats[0] = (int64_t)h[0];
+        stats[1] = (int64_t)h[1];
+    }
+    return SA_OK;
+}
+
 sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
                            sa_method method, uint64_t* counters, void* stream) {
     if (!counters) return fail(SA_ERR_INVALID_ARG, "sa_work_counters: NULL counters");

@@ -178,10 +178,12 @@ template <> __device__ __forceinline__ float comp3<2>(const float3& v) { return 
 // differences (no contraction), so the value computed for an edge shared by two
 // triangles is the exact negation in the other and a ray through the edge hits at
 // least one of them.  Zero edge values count as inside (inclusive, like the oracle).
+// woop_td: false when the ray's line misses the triangle or lies in its plane; otherwise
+// T and det, the hit distance being T / det in units of |d|.
 template <int KZ>
-__device__ __forceinline__ bool hit_tri(const float3& o, const float4& a, const float4& b,
+__device__ __forceinline__ bool woop_td(const float3& o, const float4& a, const float4& b,
                                         const float4& c, float Sx, float Sy, float Sz,
-                                        float tmin) {
+                                        float& T, float& det) {
     constexpr int KX = (KZ + 1) % 3, KY = (KZ + 2) % 3;
     const float az = comp<KZ>(a) - comp3<KZ>(o);
     const float bz = comp<KZ>(b) - comp3<KZ>(o);
@@ -196,10 +198,31 @@ __device__ __forceinline__ bool hit_tri(const float3& o, const float4& a, const 
     const float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
     const float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
     if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
-    const float det = U + V + W;
+    det = U + V + W;
     if (det == 0.f) return false;
-    const float T = U * (Sz * az) + V * (Sz * bz) + W * (Sz * cz);
+    T = U * (Sz * az) + V * (Sz * bz) + W * (Sz * cz);
+    return true;
+}
+
+// the watertight test: does the ray meet the triangle beyond tmin?
+template <int KZ>
+__device__ __forceinline__ bool hit_tri(const float3& o, const float4& a, const float4& b,
+                                        const float4& c, float Sx, float Sy, float Sz,
+                                        float tmin) {
+    float T, det;
+    if (!woop_td<KZ>(o, a, b, c, Sx, Sy, Sz, T, det)) return false;
     return det > 0.f ? (T > tmin * det) : (T < tmin * det);
+}
+
+// the same decision, returning the hit distance T / det (in units of |d|), or -1
+template <int KZ>
+__device__ __forceinline__ float hit_tri_dist(const float3& o, const float4& a, const float4& b,
+                                              const float4& c, float Sx, float Sy, float Sz,
+                                              float tmin) {
+    float T, det;
+    if (!woop_td<KZ>(o, a, b, c, Sx, Sy, Sz, T, det)) return -1.f;
+    const bool ahead = det > 0.f ? (T > tmin * det) : (T < tmin * det);
+    return ahead ? T / det : -1.f;
 }
 
 __device__ __forceinline__ bool hit_tri_any(int kz, const float3& o, const float4& a,
@@ -208,6 +231,14 @@ __device__ __forceinline__ bool hit_tri_any(int kz, const float3& o, const float
     if (kz == 2) return hit_tri<2>(o, a, b, c, s.Sx, s.Sy, s.Sz, tmin);
     if (kz == 0) return hit_tri<0>(o, a, b, c, s.Sx, s.Sy, s.Sz, tmin);
     return hit_tri<1>(o, a, b, c, s.Sx, s.Sy, s.Sz, tmin);
+}
+
+__device__ __forceinline__ float hit_dist_any(int kz, const float3& o, const float4& a,
+                                              const float4& b, const float4& c,
+                                              const StepConst& s, float tmin) {
+    if (kz == 2) return hit_tri_dist<2>(o, a, b, c, s.Sx, s.Sy, s.Sz, tmin);
+    if (kz == 0) return hit_tri_dist<0>(o, a, b, c, s.Sx, s.Sy, s.Sz, tmin);
+    return hit_tri_dist<1>(o, a, b, c, s.Sx, s.Sy, s.Sz, tmin);
 }
 
 // Slab test of the ray o + t d, t in [0, inf), against a (padded) box.
@@ -360,6 +391,14 @@ cudaError_t extrude_footprints(const FootprintSet& fs, const float* d_heights, f
 cudaError_t launch_height_grad(const DevScene& sc, const FootprintSet& fs, const float* d_heights,
                                const DevRecv& rc, const DevSun& sun, float step_minutes,
                                const float* weights, float* dS_dh, double* d_S, cudaStream_t st);
+
+// building contribution over a polygonal region (sa_analysis.cu); casting_out and
+// nearest_out are host arrays of n_buildings, stats_out two host counters (cell-steps past
+// 32 buildings, shadowed cell-steps whose ray met no building)
+cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
+                                         int n_buildings, const float* poly_xy, int n,
+                                         double* casting_out, double* nearest_out,
+                                         unsigned long long* stats_out, cudaStream_t st);
 
 // batched scenarios (device-side descriptors; see sa_raster.cu)
 struct BatchInterval {

@@ -1,5 +1,8 @@
-"""The shadow area over a polygonal region (Sec. 7.2) on the device against the FP64 oracle,
-from the accrual raster's own counts, and the shadow score built from it."""
+"""The analysis measures of Sec. 7.2 on the device against the FP64 oracle: the shadow area
+over a polygonal region from the accrual raster's own counts, the shadow score built from
+it, and each building's contribution to the region's shadow."""
+from types import SimpleNamespace
+
 import numpy as np
 import pytest
 import torch
@@ -70,3 +73,99 @@ def test_shadow_area_rejects_bad_arguments(cuda_lib):
     with pytest.raises(B.SAError):
         B.sa_shadow_area(pts, steps, 10, [[0, 0], [4, 0], [4, 4]])
     assert B.sa_shadow_area(grid, steps, 10, [[0, 0], [4, 0], [4, 4]]) == 0.0
+
+
+# ------------------------------------------------------------- building contribution
+def _region_centres(g, poly):
+    """Cell centres of the grid inside the polygon, rounded as the receivers' (FP32)."""
+    ix, iy = np.meshgrid(np.arange(g.nx, dtype=np.float32), np.arange(g.ny, dtype=np.float32))
+    cx = (np.float32(g.x0) + (ix + np.float32(0.5)) * np.float32(g.dx)).ravel()
+    cy = (np.float32(g.y0) + (iy + np.float32(0.5)) * np.float32(g.dx)).ravel()
+    keep = oracle.point_in_polygon(cx.astype(np.float64), cy.astype(np.float64), poly.astype(np.float64))
+    return np.stack([cx[keep], cy[keep], np.zeros(int(keep.sum()), np.float32)], 1)
+
+
+@pytest.mark.parametrize("name", ["convex", "non_convex"])
+def test_building_contribution_matches_the_oracle(cuda_lib, name):
+    """Per-building counts on the device against the FP64 oracle's: each building's casting
+    count within its own near-boundary pairs, the nearest-caster counts within the pairs
+    near the shadow boundary of any building, and the nearest counts plus the unattributed
+    cell-steps equal to the region's gross shadow area from the raster's own counts."""
+    B = cuda_lib
+    w = workload("district_small")
+    g = w.ground
+    scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+    poly = np.array(POLYGONS[name], np.float32)
+    casting, nearest, (over, unattributed) = B.sa_building_contribution(scene, grid, sun, poly)
+    unit = g.dx * g.dx / w.sun.S
+    cnt_c = casting / unit
+    cnt_n = nearest / unit
+    assert np.allclose(cnt_c, np.round(cnt_c), atol=1e-6) and np.allclose(cnt_n, np.round(cnt_n), atol=1e-6)
+    cnt_c, cnt_n = np.round(cnt_c).astype(np.int64), np.round(cnt_n).astype(np.int64)
+    assert over == 0
+    # internal consistency: the nearest casters partition the raster's shadowed cell-steps
+    gross, _, _ = B.sa_accumulate(scene, grid, sun, w.sun.step_minutes, "accrual_sam")
+    area = B.sa_shadow_area(grid, gross, w.sun.S, poly)
+    assert (cnt_n.sum() + unattributed) * unit == pytest.approx(area, rel=1e-12)
+    # against the oracle on the region's cell centres
+    pos = _region_centres(g, poly)
+    c_o, n_o, u_o, u_any = oracle.building_steps(w.mesh.tri9(), w.mesh.tri_building, pos, None,
+                                                 w.sun.dirs, w.sun.day_start, w.city.B)
+    assert c_o.sum() > 10000
+    dc = np.abs(cnt_c - c_o)
+    assert np.all(dc <= u_o), (np.nonzero(dc > u_o)[0], dc[dc > u_o], u_o[dc > u_o])
+    dn = np.abs(cnt_n - n_o)
+    assert dn.sum() <= 2 * u_any, (dn.sum(), u_any)
+    assert unattributed <= u_any
+    assert np.all(cnt_n <= cnt_c)
+
+
+def test_building_contribution_of_two_boxes_in_line(cuda_lib):
+    """Two boxes one behind the other toward a low morning sun: every cell shadowed by the
+    farther box alone is credited to it, and where both boxes shadow a cell the nearer box
+    is the nearest caster; the device agrees with the oracle pair by pair."""
+    B = cuda_lib
+    from synth import city as C
+    city = C.City([C.box_footprint(40, 45, 50, 55), C.box_footprint(70, 45, 80, 55)],
+                  np.array([30.0, 60.0], np.float32))
+    mesh = C.extrude(city)
+    el = np.radians(np.linspace(15.0, 25.0, 8))
+    az = np.radians(np.linspace(-8.0, 8.0, 8))
+    dirs = np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], 1).astype(np.float32)
+    day_start = np.array([0, 8], np.int32)
+    scene = B.Scene(mesh.verts, mesh.tris, mesh.tri_building, 2, closed=True)
+    sun = B.Sun(dirs, day_start)
+    x0, y0, dx, nx, ny = 0.0, 0.0, 1.0, 100, 100
+    grid = B.Receivers.ground_grid(x0, y0, dx, nx, ny)
+    poly = np.array([[0.0, 20.0], [40.0, 20.0], [40.0, 80.0], [0.0, 80.0]], np.float32)
+    casting, nearest, (over, unattributed) = B.sa_building_contribution(scene, grid, sun, poly)
+    pos = _region_centres(SimpleNamespace(x0=x0, y0=y0, dx=dx, nx=nx, ny=ny), poly)
+    c_o, n_o, u_o, u_any = oracle.building_steps(mesh.tri9(), mesh.tri_building, pos, None, dirs,
+                                                 day_start, 2)
+    unit = dx * dx / 8
+    cnt_c, cnt_n = np.round(casting / unit).astype(np.int64), np.round(nearest / unit).astype(np.int64)
+    assert np.all(np.abs(cnt_c - c_o) <= u_o)
+    assert np.abs(cnt_n - n_o).sum() <= 2 * u_any
+    assert c_o[1] > n_o[1] > 0 and n_o[0] == c_o[0] > 0     # the tall far box reaches past the near one
+    assert over == 0
+
+
+def test_building_contribution_rejects_bad_arguments(cuda_lib):
+    B = cuda_lib
+    w = workload("district_small")
+    g = w.ground
+    scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+    with pytest.raises(B.SAError):
+        B.sa_building_contribution(scene, grid, sun, [[0, 0], [1, 1]])
+    with pytest.raises(B.SAError):
+        B.sa_building_contribution(scene, grid, sun, [[0, 0], [np.nan, 0], [4, 4]])
+    pts = B.Receivers.points(np.zeros((4, 3), np.float32))
+    with pytest.raises(B.SAError):
+        B.sa_building_contribution(scene, pts, sun, [[0, 0], [4, 0], [4, 4]])
+    # a region holding no cell centre credits nothing
+    c, n, st = B.sa_building_contribution(scene, grid, sun, [[0, 0], [1, 0], [1, 1]])
+    assert not c.any() and not n.any() and st == (0, 0)
