@@ -241,3 +241,33 @@ def building_steps(tri9, tri_building, pos, nrm, dirs, day_start, n_buildings, e
     if rc != 0:
         raise RuntimeError(f"sao_building_steps failed ({rc})")
     return out[0], out[1], out[2], int(anyc[0])
+
+
+# ------------------------------------------------------------- endpoint-interpolated sun
+def sun_interpolate(dirs, day_start, block_len: int = 0):
+    """The paper's short-interval sun (Sec. 3.2, Sec. 4): inside each block of
+    `block_partition`, only the first and last directions d_1, d_n are kept and the steps
+    between are rebuilt from them, the sun moving at a constant angular rate along the great
+    circle through d_1 and d_n: step i (i' = i - 1 = 0 .. n-1) is d_1 rotated toward d_n by
+    i' theta / (n - 1), theta the angle between them.  (This is what the tangent law of
+    Sec. 4 draws on a shadow plane orthogonal to d_1; the denominator n - 1 makes the last
+    step land on d_n.)  Blocks of one or two steps, and the first and last step of every
+    block, are unchanged.  Returns float32 [S, 3] (FP64 arithmetic, rounded once)."""
+    d = np.asarray(dirs, np.float32).reshape(-1, 3).astype(np.float64)
+    out = d.copy()
+    j0, K = block_partition(day_start, block_len)
+    for a, n in zip(j0.tolist(), K.tolist()):
+        if n <= 2:
+            continue
+        d1 = d[a] / np.linalg.norm(d[a])
+        dn = d[a + n - 1] / np.linalg.norm(d[a + n - 1])
+        theta = float(np.arctan2(np.linalg.norm(np.cross(d1, dn)), np.dot(d1, dn)))
+        tau = np.arange(1, n - 1, dtype=np.float64) / (n - 1)
+        if theta < 1e-12:
+            mid = np.repeat(d1[None, :], n - 2, axis=0)
+        else:
+            s = np.sin(theta)
+            mid = (np.sin((1.0 - tau) * theta) / s)[:, None] * d1[None, :] + \
+                  (np.sin(tau * theta) / s)[:, None] * dn[None, :]
+        out[a + 1:a + n - 1] = mid
+    return out.astype(np.float32)
