@@ -185,6 +185,22 @@ sa_status sa_scene_info(const sa_scene* scene, int64_t* n_tris, int64_t* n_nodes
 sa_status sa_sun_create(const float* dirs, int32_t S, const int32_t* day_start, int32_t D,
                         int32_t block_len, void* stream, sa_sun** out);
 void sa_sun_destroy(sa_sun* sun);
+/* The paper's short-interval sun (Sec. 3.2, and Sec. 4, where the accrual map draws every
+ * step from the first and last direction of its interval): writes a table in which every
+ * block (as sa_sun_create cuts it with the same block_len) keeps its first and last
+ * directions d_1, d_n and the steps between move at a constant angular rate along the
+ * great circle through them: step i (i' = i - 1 = 0 .. n-1) is d_1 rotated toward d_n by
+ * i' theta / (n - 1), theta = angle(d_1, d_n).  This is what the paper's tangent law
+ * draws on a shadow plane orthogonal to d_1, read with n - 1 in the denominator so that
+ * the last step lands on d_n.  Pass the result to sa_sun_create with the same block_len
+ * to run any method in the paper's mode; comparing with the exact table measures the
+ * error of the linear-motion assumption.
+ *   dirs, day_start: as for sa_sun_create (host, validated the same way).
+ *   dirs_out: float [S][3] host; may be dirs itself.  Blocks of 1 or 2 steps are copied.
+ * FP64 arithmetic, rounded once to FP32.  Errors: as sa_sun_create's checks. */
+sa_status sa_sun_interpolate(const float* dirs, int32_t S, const int32_t* day_start, int32_t D,
+                             int32_t block_len, float* dirs_out);
+
 /* Number of steps, days and blocks. */
 sa_status sa_sun_info(const sa_sun* sun, int32_t* S, int32_t* D, int32_t* n_blocks);
 

@@ -91,13 +91,15 @@ def lib():
             L.sa_kernel_times.argtypes = [P, P, i32]
             L.sa_shadow_area.argtypes = [P, P, i32, P, i32, P, P]
             L.sa_building_contribution.argtypes = [P, P, P, P, i32, P, P, P, P]
+            L.sa_sun_interpolate.argtypes = [P, i32, P, i32, i32, P]
             for name in ("sa_scene_from_mesh", "sa_scene_info", "sa_sun_create", "sa_sun_info",
                          "sa_receivers_grid", "sa_receivers_points", "sa_accumulate",
                          "sa_shadow_masks", "sa_accumulate_grid_noalloc", "sa_work_counters",
                          "sa_scene_from_footprints", "sa_scene_set_heights", "sa_height_grad",
                          "sa_scene_declare_closed", "sa_set_option", "sa_batch_create",
                          "sa_batch_run", "sa_batch_tune", "sa_batch_work_counters",
-                         "sa_kernel_times", "sa_shadow_area", "sa_building_contribution"):
+                         "sa_kernel_times", "sa_shadow_area", "sa_building_contribution",
+                         "sa_sun_interpolate"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
     return _lib
@@ -209,6 +211,18 @@ class Sun:
         if h and _lib is not None:
             _lib.sa_sun_destroy(h)
             self.handle = None
+
+
+def sun_interpolate(dirs, day_start, block_len: int = 0) -> np.ndarray:
+    """The paper's short-interval sun (Sec. 3.2, Sec. 4): float32 [S, 3] in which each
+    block keeps its first and last directions and the steps between follow the great
+    circle through them at a constant angular rate.  Build a `Sun` from it with the same
+    block_len to run a method in the paper's mode."""
+    d = _host_f32(dirs).reshape(-1, 3)
+    ds = _host_i32(day_start).reshape(-1)
+    out = np.empty_like(d)
+    _check(lib().sa_sun_interpolate(_ptr(d), d.shape[0], _ptr(ds), ds.shape[0] - 1, int(block_len), _ptr(out)))
+    return out
 
 
 class Receivers:

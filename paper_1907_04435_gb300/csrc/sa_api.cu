@@ -498,36 +498,42 @@ sa_status sa_scene_info(const sa_scene* scene, int64_t* n_tris, int64_t* n_nodes
 }
 
 // -------------------------------------------------------------------------------- sun
-sa_status sa_sun_create(const float* dirs, int32_t S, const int32_t* day_start, int32_t D,
-                        int32_t block_len, void* stream, sa_sun** out) {
-    if (!out) return fail(SA_ERR_INVALID_ARG, "sa_sun_create: out is NULL");
-    *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// Checks of a sun table shared by sa_sun_create and sa_sun_interpolate; *block_len 0
+// becomes 60.
+sa_status check_sun_table(const float* dirs, int32_t S, const int32_t* day_start, int32_t D,
+                          int32_t* block_len, const char* who) {
     if (S < 0 || D < 0 || (S > 0 && !dirs) || !day_start)
-        return fail(SA_ERR_INVALID_ARG, "sa_sun_create: bad sizes or NULL pointers");
-    if (block_len == 0) block_len = 60;
-    if (block_len < 1 || block_len > sa::kMaxBlock)
-        return fail(SA_ERR_INVALID_ARG, "sa_sun_create: block_len %d outside 1..64", block_len);
+        return fail(SA_ERR_INVALID_ARG, "%s: bad sizes or NULL pointers", who);
+    if (*block_len == 0) *block_len = 60;
+    if (*block_len < 1 || *block_len > sa::kMaxBlock)
+        return fail(SA_ERR_INVALID_ARG, "%s: block_len %d outside 1..64", who, *block_len);
     if (day_start[0] != 0 || day_start[D] != S)
-        return fail(SA_ERR_INVALID_ARG, "sa_sun_create: day_start must run from 0 to S");
+        return fail(SA_ERR_INVALID_ARG, "%s: day_start must run from 0 to S", who);
     for (int k = 0; k < D; ++k)
         if (day_start[k + 1] < day_start[k])
-            return fail(SA_ERR_INVALID_ARG, "sa_sun_create: day_start decreases at day %d", k);
+            return fail(SA_ERR_INVALID_ARG, "%s: day_start decreases at day %d", who, k);
     for (int j = 0; j < S; ++j) {
         const float* d = dirs + 3 * j;
         if (!isfinite(d[0]) || !isfinite(d[1]) || !isfinite(d[2]))
-            return fail(SA_ERR_INVALID_ARG, "sa_sun_create: non-finite direction at step %d", j);
+            return fail(SA_ERR_INVALID_ARG, "%s: non-finite direction at step %d", who, j);
         const double n = sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
         if (fabs(n - 1.0) > 1e-5)
-            return fail(SA_ERR_INVALID_ARG, "sa_sun_create: |d| = %.8f at step %d", n, j);
+            return fail(SA_ERR_INVALID_ARG, "%s: |d| = %.8f at step %d", who, n, j);
         if (!(d[2] > 0.f))
-            return fail(SA_ERR_SUN_BELOW_HORIZON, "sa_sun_create: d_z <= 0 at step %d", j);
+            return fail(SA_ERR_SUN_BELOW_HORIZON, "%s: d_z <= 0 at step %d", who, j);
     }
-    sa_sun* sun = new (std::nothrow) sa_sun();
-    if (!sun) return fail(SA_ERR_OOM, "sa_sun_create: host allocation");
-    sun->S = S;
-    sun->D = D;
-    sun->h_steps.resize(S);
-    for (int j = 0; j < S; ++j) make_step(dirs + 3 * j, &sun->h_steps[j]);
+    return SA_OK;
+}
+
+// Calls fn(first step, steps, block of the day) for every block: each day of n steps is
+// cut into ceil(n / block_len) consecutive blocks whose sizes differ by at most one, the
+// longer ones first.
+template <class Fn>
+void for_each_block(const int32_t* day_start, int32_t D, int32_t block_len, Fn fn) {
     for (int k = 0; k < D; ++k) {
         const int a = day_start[k], n = day_start[k + 1] - a;
         if (n == 0) continue;
@@ -536,17 +542,38 @@ sa_status sa_sun_create(const float* dirs, int32_t S, const int32_t* day_start, 
         int j = a;
         for (int q = 0; q < nb; ++q) {
             const int K = base + (q < rem ? 1 : 0);
-            const int mb = (int)sun->h_blocks.size();
-            sun->h_blocks.push_back(make_block(dirs, sun->h_steps, j, K, q == 0, true));
-            sun->h_blocks.back().mask_block = mb;
-            for (int i = 0; i < K; ++i) {
-                sun->h_step_blocks.push_back(make_block(dirs, sun->h_steps, j + i, 1, q == 0 && i == 0, false));
-                sun->h_step_blocks.back().mask_block = mb;
-                sun->h_step_blocks.back().mask_bit = i;
-            }
+            fn(j, K, q);
             j += K;
         }
     }
+}
+
+}  // namespace
+
+extern "C" {
+
+sa_status sa_sun_create(const float* dirs, int32_t S, const int32_t* day_start, int32_t D,
+                        int32_t block_len, void* stream, sa_sun** out) {
+    if (!out) return fail(SA_ERR_INVALID_ARG, "sa_sun_create: out is NULL");
+    *out = nullptr;
+    const sa_status chk = check_sun_table(dirs, S, day_start, D, &block_len, "sa_sun_create");
+    if (chk != SA_OK) return chk;
+    sa_sun* sun = new (std::nothrow) sa_sun();
+    if (!sun) return fail(SA_ERR_OOM, "sa_sun_create: host allocation");
+    sun->S = S;
+    sun->D = D;
+    sun->h_steps.resize(S);
+    for (int j = 0; j < S; ++j) make_step(dirs + 3 * j, &sun->h_steps[j]);
+    for_each_block(day_start, D, block_len, [&](int j, int K, int q) {
+        const int mb = (int)sun->h_blocks.size();
+        sun->h_blocks.push_back(make_block(dirs, sun->h_steps, j, K, q == 0, true));
+        sun->h_blocks.back().mask_block = mb;
+        for (int i = 0; i < K; ++i) {
+            sun->h_step_blocks.push_back(make_block(dirs, sun->h_steps, j + i, 1, q == 0 && i == 0, false));
+            sun->h_step_blocks.back().mask_block = mb;
+            sun->h_step_blocks.back().mask_bit = i;
+        }
+    });
     cudaStream_t st = as_stream(stream);
     cudaError_t e = upload(sun->h_steps.data(), sun->h_steps.size(), 0, &sun->d_steps, st);
     if (e == cudaSuccess) e = upload(sun->h_blocks.data(), sun->h_blocks.size(), 0, &sun->d_blocks, st);
@@ -558,6 +585,41 @@ sa_status sa_sun_create(const float* dirs, int32_t S, const int32_t* day_start, 
         return cuda_fail(e, "sa_sun_create");
     }
     *out = sun;
+    return SA_OK;
+}
+
+sa_status sa_sun_interpolate(const float* dirs, int32_t S, const int32_t* day_start, int32_t D,
+                             int32_t block_len, float* dirs_out) {
+    const sa_status chk = check_sun_table(dirs, S, day_start, D, &block_len, "sa_sun_interpolate");
+    if (chk != SA_OK) return chk;
+    if (S > 0 && !dirs_out) return fail(SA_ERR_INVALID_ARG, "sa_sun_interpolate: dirs_out is NULL");
+    // a copy, so that dirs_out may alias dirs
+    std::vector<double> d((size_t)S * 3);
+    for (size_t i = 0; i < d.size(); ++i) d[i] = (double)dirs[i];
+    for (size_t i = 0; i < d.size(); ++i) dirs_out[i] = (float)d[i];
+    for_each_block(day_start, D, block_len, [&](int a, int n, int) {
+        if (n <= 2) return;
+        double d1[3], dn[3];
+        const double l1 = sqrt(d[3 * a] * d[3 * a] + d[3 * a + 1] * d[3 * a + 1] + d[3 * a + 2] * d[3 * a + 2]);
+        const size_t e = 3 * (size_t)(a + n - 1);
+        const double ln = sqrt(d[e] * d[e] + d[e + 1] * d[e + 1] + d[e + 2] * d[e + 2]);
+        for (int c = 0; c < 3; ++c) {
+            d1[c] = d[3 * (size_t)a + c] / l1;
+            dn[c] = d[e + c] / ln;
+        }
+        const double cx = d1[1] * dn[2] - d1[2] * dn[1], cy = d1[2] * dn[0] - d1[0] * dn[2],
+                     cz = d1[0] * dn[1] - d1[1] * dn[0];
+        const double theta = atan2(sqrt(cx * cx + cy * cy + cz * cz), d1[0] * dn[0] + d1[1] * dn[1] + d1[2] * dn[2]);
+        for (int i = 1; i < n - 1; ++i) {
+            double w1 = 1.0, wn = 0.0;
+            if (theta >= 1e-12) {
+                const double tau = (double)i / (double)(n - 1);
+                w1 = sin((1.0 - tau) * theta) / sin(theta);
+                wn = sin(tau * theta) / sin(theta);
+            }
+            for (int c = 0; c < 3; ++c) dirs_out[3 * (size_t)(a + i) + c] = (float)(w1 * d1[c] + wn * dn[c]);
+        }
+    });
     return SA_OK;
 }
 

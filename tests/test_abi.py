@@ -101,3 +101,27 @@ def test_options_and_kernel_timing_record_need_no_device(L):
     # nothing launched: the record is empty
     t = B.sa_kernel_times()
     assert set(t) == set(B.KERNEL_CLASSES) and all(v == (0.0, 0) for v in t.values())
+
+
+def test_interpolated_sun_matches_the_oracle_on_the_host():
+    """sa_sun_interpolate is host code: its table equals the oracle's FP64 interpolation to
+    FP32 rounding, keeps every block's ends bit for bit, and validates like sa_sun_create."""
+    import oracle
+    from paper_1907_04435_gb300 import binding as B
+    from synth.sun import sun_table
+    st = sun_table(40.7, [79, 172, 355], 9.0, 17.0, 1.0)
+    for bl in (0, 17, 60, 64):
+        got = B.sun_interpolate(st.dirs, st.day_start, bl)
+        want = oracle.sun_interpolate(st.dirs, st.day_start, bl)
+        assert np.abs(got.astype(np.float64) - want).max() <= 1.2e-7, bl
+        j0, K = oracle.block_partition(st.day_start, bl)
+        assert np.array_equal(got[j0], st.dirs[j0]) and np.array_equal(got[j0 + K - 1], st.dirs[j0 + K - 1])
+    # in place
+    d = st.dirs.copy()
+    L = B.lib()
+    assert L.sa_sun_interpolate(d.ctypes.data, d.shape[0], st.day_start.ctypes.data, st.D, 60, d.ctypes.data) == 0
+    assert np.array_equal(d, B.sun_interpolate(st.dirs, st.day_start, 60))
+    with pytest.raises(B.SAError):
+        B.sun_interpolate(st.dirs * 2.0, st.day_start, 60)
+    with pytest.raises(B.SAError):
+        B.sun_interpolate(st.dirs, st.day_start, 65)
