@@ -271,3 +271,52 @@ def sun_interpolate(dirs, day_start, block_len: int = 0):
                   (np.sin(tau * theta) / s)[:, None] * dn[None, :]
         out[a + 1:a + n - 1] = mid
     return out.astype(np.float32)
+
+
+# ------------------------------------------------------------- direction bins and graph
+def direction_bins(dirs, bin_deg: float = 5.0):
+    """Sec. 6 direction bins: the hemisphere cut into quads bounded by bin_deg in both
+    angles -- elevation bands [k b, (k+1) b) above the horizon and azimuth sectors
+    [m b, (m+1) b), azimuth measured from +y toward +x.  (elev_bin, az_bin) int64 [S]."""
+    d = np.asarray(dirs, np.float32).reshape(-1, 3).astype(np.float64)
+    n = np.linalg.norm(d, axis=1)
+    el = np.degrees(np.arcsin(np.clip(d[:, 2] / n, -1.0, 1.0)))
+    az = np.degrees(np.arctan2(d[:, 0], d[:, 1]))
+    return np.floor(el / bin_deg).astype(np.int64), np.floor(az / bin_deg).astype(np.int64)
+
+
+def direction_graph(dirs, day_start, block_len: int = 0, bin_deg: float = 5.0):
+    """Sec. 6 direction graph over the blocks of `block_partition`: a block (an interval of
+    the day) is the pair (bin of its first direction, bin of its last direction); blocks
+    with the same pair and the same number of steps are one edge, numbered in order of
+    first appearance.  Returns (edge [n_blocks], rep [E] = the first block of each edge,
+    weight [E] = how many blocks the edge stands for)."""
+    j0, K = block_partition(day_start, block_len)
+    eb, ab = direction_bins(dirs, bin_deg)
+    ids, rep, weight = {}, [], []
+    edge = np.zeros(len(j0), np.int64)
+    for b, (a, k) in enumerate(zip(j0.tolist(), K.tolist())):
+        key = (eb[a], ab[a], eb[a + k - 1], ab[a + k - 1], k)
+        if key not in ids:
+            ids[key] = len(rep)
+            rep.append(b)
+            weight.append(0)
+        edge[b] = ids[key]
+        weight[ids[key]] += 1
+    return edge, np.asarray(rep, np.int64), np.asarray(weight, np.int64)
+
+
+def graph_bits(bits, dirs, day_start, block_len: int = 0, bin_deg: float = 5.0):
+    """Per-step bits as the direction graph sees them: every block takes the bits its
+    edge's map holds, i.e. those of the edge's first block (Sec. 6: one map per edge,
+    reused for every interval on that edge).  Gross and continuous counts of the graph
+    are `reduce` of this array: Eq. 1 sums the edge maps with their weights, and the
+    continuous count stitches each day's path of edges in time order."""
+    bits = np.asarray(bits)
+    j0, K = block_partition(day_start, block_len)
+    edge, rep, _ = direction_graph(dirs, day_start, block_len, bin_deg)
+    out = np.empty_like(bits)
+    for b, (a, k) in enumerate(zip(j0.tolist(), K.tolist())):
+        r0 = int(j0[rep[edge[b]]])
+        out[:, a:a + k] = bits[:, r0:r0 + k]
+    return out
