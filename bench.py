@@ -520,6 +520,19 @@ def bench_configs(B):
                                  f"ground @ {g.dx} m, {w.sun.D} days x 481 steps ({w.sun.S})",
                      "receiver_steps": units, "accrual_sam_ms": ms,
                      "value": units / (ms * 1e-3), "scene_build_s": build_s, "unit": UNIT}
+    # the same season through the direction graph (5 degree bins, approximate): its time,
+    # the maps it computes against the exact path's blocks, and its error
+    ge, _, ce = B.sa_accumulate(scene, grid, sun, w.sun.step_minutes, "accrual_sam")
+    gg, _, cg, n_edges = B.sa_accumulate_graph(scene, grid, sun, w.sun.step_minutes, "accrual_sam", 5.0)
+    ge, gg = ge.double(), gg.double()
+    gms = _event_ms(lambda: B.sa_accumulate_graph(scene, grid, sun, w.sun.step_minutes, "accrual_sam", 5.0), 2)
+    out["season"]["direction_graph"] = {
+        "bin_deg": 5.0, "maps": n_edges, "blocks": sun.n_blocks, "ms": gms,
+        "speedup_over_exact": ms / gms,
+        "gross_error_pct": float(100.0 * (gg - ge).abs().sum() / ge.sum()),
+        "gross_area_change_pct": float(100.0 * (gg.sum() - ge.sum()) / ge.sum()),
+        "continuous_mean_abs_steps": float((cg - ce).double().abs().mean())}
+    del ge, gg, ce, cg
     del scene, grid
     # park: forward accrual and the height gradient (forward masks + FP64 flip refinement)
     w = configs.park()

@@ -326,6 +326,44 @@ sa_status sa_batch_work_counters(sa_batch* b, uint64_t* counters, void* stream);
 sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
                            sa_method method, uint64_t* counters, void* stream);
 
+/* --------------------------------------------------- long periods: the direction graph
+ * Sec. 6: over many days the sun retraces nearly the same arcs.  Directions fall into bins,
+ * quads of the hemisphere bounded by bin_deg in elevation (bands [k b, (k+1) b) above the
+ * horizon) and in azimuth (sectors [m b, (m+1) b), azimuth from +y toward +x).  A block of
+ * the sun table (as sa_sun_create cuts it) becomes the pair (bin of its first direction,
+ * bin of its last direction); blocks with the same pair and the same number of steps are
+ * one edge of the direction graph, numbered in order of first appearance, and its weight
+ * is the number of blocks it stands for.  The paper uses 5 degree bins.  An edge's map is
+ * computed from one of its blocks, which the paper leaves open: here the middle one in
+ * time order (member (m - 1) / 2 of its m blocks), so that the map's sun lies inside the
+ * spread of the suns it stands for.
+ *
+ * sa_direction_graph (host only): the graph of a sun table.  *n_blocks and *n_edges
+ * (required) receive the counts; edge_of_block int32 [n_blocks], map_block int32
+ * [n_edges] and weight int32 [n_edges] (host, each nullable: call once with NULLs to size
+ * them) receive each block's edge, the block each edge's map is computed from, and each
+ * edge's weight.
+ * Errors: as sa_sun_create's checks, SA_ERR_INVALID_ARG (bin_deg outside (0, 90]). */
+sa_status sa_direction_graph(const float* dirs, int32_t S, const int32_t* day_start, int32_t D,
+                             int32_t block_len, float bin_deg, int32_t* n_blocks, int32_t* n_edges,
+                             int32_t* edge_of_block, int32_t* map_block, int32_t* weight);
+
+/* Accumulation through the direction graph (Sec. 6, approximate): one shadow map per edge,
+ * computed by `method` over the edge's map block, stands for every block of the edge.
+ * gross = sum over edges of the edge's count times its weight (Eq. 1); the continuous
+ * count stitches each day's path of edges in time order from each edge's leading,
+ * longest and trailing runs, and takes the longest over the days.  Outputs and methods as
+ * sa_accumulate (SA_ACCUMULATE_INTO is not offered); *n_edges (host, nullable) receives
+ * the number of maps computed, against sa_sun_info's n_blocks for the exact result.  With
+ * a bin_deg small enough that no two blocks share an edge the result is sa_accumulate's.
+ * Scratch: 4 bytes per receiver and edge, plus the step masks of at most 4 GiB of edges
+ * at a time.  Synchronises `stream` once per chunk of edges.  Errors: as sa_accumulate,
+ * SA_ERR_INVALID_ARG (bin_deg outside (0, 90]). */
+sa_status sa_accumulate_graph(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
+                              sa_method method, int32_t iam_levels, float bin_deg, float step_minutes,
+                              int32_t* gross_steps, float* gross_minutes, int32_t* continuous_steps,
+                              int32_t* n_edges, void* stream);
+
 /* ---------------------------------------------------------------- analysis measures
  * Shadow area over a polygonal region (Sec. 7.2, "Analysis measures"): the sum, over the
  * cells of a ground grid whose centre lies inside the polygon (even-odd rule), of

@@ -289,8 +289,11 @@ def direction_graph(dirs, day_start, block_len: int = 0, bin_deg: float = 5.0):
     """Sec. 6 direction graph over the blocks of `block_partition`: a block (an interval of
     the day) is the pair (bin of its first direction, bin of its last direction); blocks
     with the same pair and the same number of steps are one edge, numbered in order of
-    first appearance.  Returns (edge [n_blocks], rep [E] = the first block of each edge,
-    weight [E] = how many blocks the edge stands for)."""
+    first appearance.  The edge's map is computed once, from one of its blocks: the middle
+    one in time order (element (m - 1) // 2 of its m blocks), so that the sun of the map
+    lies inside the spread of the intervals it stands for.  Returns (edge [n_blocks],
+    rep [E] = the block each edge's map is computed from, weight [E] = how many blocks the
+    edge stands for)."""
     j0, K = block_partition(day_start, block_len)
     eb, ab = direction_bins(dirs, bin_deg)
     ids, rep, weight = {}, [], []
@@ -303,12 +306,15 @@ def direction_graph(dirs, day_start, block_len: int = 0, bin_deg: float = 5.0):
             weight.append(0)
         edge[b] = ids[key]
         weight[ids[key]] += 1
+    for e in range(len(rep)):
+        members = np.nonzero(edge == e)[0]
+        rep[e] = int(members[(len(members) - 1) // 2])
     return edge, np.asarray(rep, np.int64), np.asarray(weight, np.int64)
 
 
 def graph_bits(bits, dirs, day_start, block_len: int = 0, bin_deg: float = 5.0):
     """Per-step bits as the direction graph sees them: every block takes the bits its
-    edge's map holds, i.e. those of the edge's first block (Sec. 6: one map per edge,
+    edge's map holds, i.e. those of the edge's chosen block (Sec. 6: one map per edge,
     reused for every interval on that edge).  Gross and continuous counts of the graph
     are `reduce` of this array: Eq. 1 sums the edge maps with their weights, and the
     continuous count stitches each day's path of edges in time order."""

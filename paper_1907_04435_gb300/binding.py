@@ -92,6 +92,8 @@ def lib():
             L.sa_shadow_area.argtypes = [P, P, i32, P, i32, P, P]
             L.sa_building_contribution.argtypes = [P, P, P, P, i32, P, P, P, P]
             L.sa_sun_interpolate.argtypes = [P, i32, P, i32, i32, P]
+            L.sa_direction_graph.argtypes = [P, i32, P, i32, i32, f32, P, P, P, P, P]
+            L.sa_accumulate_graph.argtypes = [P, P, P, i32, i32, f32, f32, P, P, P, P, P]
             for name in ("sa_scene_from_mesh", "sa_scene_info", "sa_sun_create", "sa_sun_info",
                          "sa_receivers_grid", "sa_receivers_points", "sa_accumulate",
                          "sa_shadow_masks", "sa_accumulate_grid_noalloc", "sa_work_counters",
@@ -99,7 +101,7 @@ def lib():
                          "sa_scene_declare_closed", "sa_set_option", "sa_batch_create",
                          "sa_batch_run", "sa_batch_tune", "sa_batch_work_counters",
                          "sa_kernel_times", "sa_shadow_area", "sa_building_contribution",
-                         "sa_sun_interpolate"):
+                         "sa_sun_interpolate", "sa_direction_graph", "sa_accumulate_graph"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
     return _lib
@@ -284,6 +286,40 @@ def sa_accumulate(scene: Scene, recv: Receivers, sun: Sun, step_minutes: float, 
                                _ptr(gross), _ptr(minutes), _ptr(continuous),
                                ct.c_void_p(_stream(stream))))
     return gross, minutes, continuous
+
+
+def direction_graph(dirs, day_start, block_len: int = 0, bin_deg: float = 5.0):
+    """The direction graph of a sun table (Sec. 6): (edge of each block, the block each
+    edge's map is computed from -- its middle block --, weight of each edge) as int32
+    arrays.  Host only."""
+    d = _host_f32(dirs).reshape(-1, 3)
+    ds = _host_i32(day_start).reshape(-1)
+    nb, ne = ct.c_int32(), ct.c_int32()
+    args = (_ptr(d), d.shape[0], _ptr(ds), ds.shape[0] - 1, int(block_len), float(bin_deg))
+    _check(lib().sa_direction_graph(*args, ct.byref(nb), ct.byref(ne), None, None, None))
+    edge = np.zeros(nb.value, np.int32)
+    first = np.zeros(ne.value, np.int32)
+    weight = np.zeros(ne.value, np.int32)
+    _check(lib().sa_direction_graph(*args, ct.byref(nb), ct.byref(ne), _ptr(edge), _ptr(first), _ptr(weight)))
+    return edge, first, weight
+
+
+def sa_accumulate_graph(scene: Scene, recv: Receivers, sun: Sun, step_minutes: float, method,
+                        bin_deg: float = 5.0, iam_levels: int = 0, stream=None):
+    """Accumulation through the direction graph (Sec. 6, approximate): one map per edge,
+    reused for every block of the edge.  Returns (gross_steps int32, gross_minutes float32,
+    continuous int32, number of maps computed)."""
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    R = recv.R
+    gross = torch.zeros(R, dtype=torch.int32, device=dev)
+    minutes = torch.zeros(R, dtype=torch.float32, device=dev)
+    continuous = torch.zeros(R, dtype=torch.int32, device=dev)
+    ne = ct.c_int32()
+    _check(lib().sa_accumulate_graph(scene.handle, recv.handle, sun.handle, m, int(iam_levels), float(bin_deg),
+                                     float(step_minutes), _ptr(gross), _ptr(minutes), _ptr(continuous),
+                                     ct.byref(ne), ct.c_void_p(_stream(stream))))
+    return gross, minutes, continuous, ne.value
 
 
 def sa_accumulate_grid_noalloc(scene: Scene, grid: Receivers, sun: Sun, step_minutes: float,

@@ -623,6 +623,28 @@ sa_status sa_sun_interpolate(const float* dirs, int32_t S, const int32_t* day_st
     return SA_OK;
 }
 
+sa_status sa_direction_graph(const float* dirs, int32_t S, const int32_t* day_start, int32_t D,
+                             int32_t block_len, float bin_deg, int32_t* n_blocks, int32_t* n_edges,
+                             int32_t* edge_of_block, int32_t* map_block, int32_t* weight) {
+    const char* who = "sa_direction_graph";
+    if (!n_blocks || !n_edges) return fail(SA_ERR_INVALID_ARG, "%s: NULL count", who);
+    if (!(bin_deg > 0.f && bin_deg <= 90.f)) return fail(SA_ERR_INVALID_ARG, "%s: bin_deg outside (0, 90]", who);
+    const sa_status chk = check_sun_table(dirs, S, day_start, D, &block_len, who);
+    if (chk != SA_OK) return chk;
+    std::vector<int> j0, K, edge, rep, wt;
+    for_each_block(day_start, D, block_len, [&](int j, int k, int) {
+        j0.push_back(j);
+        K.push_back(k);
+    });
+    sa::direction_graph(dirs, (int)j0.size(), j0.data(), K.data(), (double)bin_deg, edge, rep, wt);
+    *n_blocks = (int32_t)j0.size();
+    *n_edges = (int32_t)rep.size();
+    for (size_t b = 0; edge_of_block && b < edge.size(); ++b) edge_of_block[b] = edge[b];
+    for (size_t e = 0; map_block && e < rep.size(); ++e) map_block[e] = rep[e];
+    for (size_t e = 0; weight && e < wt.size(); ++e) weight[e] = wt[e];
+    return SA_OK;
+}
+
 void sa_sun_destroy(sa_sun* sun) {
     if (!sun) return;
     cudaDeviceSynchronize();
@@ -819,6 +841,116 @@ sa_status sa_shadow_masks(const sa_scene* scene, const sa_receivers* recv, const
     sa_status s = run_method(scene, recv, sun, method, iam_levels, out, st, "sa_shadow_masks");
     if (gross) cudaFreeAsync(gross, st);
     return s;
+}
+
+sa_status sa_accumulate_graph(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
+                              sa_method method, int32_t iam_levels, float bin_deg, float step_minutes,
+                              int32_t* gross_steps, float* gross_minutes, int32_t* continuous_steps,
+                              int32_t* n_edges, void* stream) {
+    const char* who = "sa_accumulate_graph";
+    if (!scene || !recv || !sun) return fail(SA_ERR_INVALID_ARG, "%s: NULL handle", who);
+    if (!(bin_deg > 0.f && bin_deg <= 90.f)) return fail(SA_ERR_INVALID_ARG, "%s: bin_deg outside (0, 90]", who);
+    if (!isfinite(step_minutes) || step_minutes < 0.f) return fail(SA_ERR_INVALID_ARG, "%s: step_minutes", who);
+    if (recv->R > 0 && !gross_steps) return fail(SA_ERR_INVALID_ARG, "%s: gross_steps is NULL", who);
+    cudaStream_t st = as_stream(stream);
+    // the graph over the sun table's own blocks
+    const int nb = (int)sun->h_blocks.size();
+    std::vector<float> dirs((size_t)sun->S * 3);
+    for (int j = 0; j < sun->S; ++j) {
+        dirs[3 * (size_t)j] = sun->h_steps[j].dx;
+        dirs[3 * (size_t)j + 1] = sun->h_steps[j].dy;
+        dirs[3 * (size_t)j + 2] = sun->h_steps[j].dz;
+    }
+    std::vector<int> j0(nb), K(nb), path, rep, wt, day_block;
+    for (int b = 0; b < nb; ++b) {
+        j0[b] = sun->h_blocks[b].j0;
+        K[b] = sun->h_blocks[b].K;
+        if (sun->h_blocks[b].new_day) day_block.push_back(b);
+    }
+    day_block.push_back(nb);
+    sa::direction_graph(dirs.data(), nb, j0.data(), K.data(), (double)bin_deg, path, rep, wt);
+    const int E = (int)rep.size();
+    if (n_edges) *n_edges = E;
+    const long long R = recv->R;
+    if (R == 0) return SA_OK;
+    cudaError_t e = cudaSuccess;
+    if (nb == 0) {
+        e = cudaMemsetAsync(gross_steps, 0, sizeof(int) * (size_t)R, st);
+        if (e == cudaSuccess && continuous_steps) e = cudaMemsetAsync(continuous_steps, 0, sizeof(int) * (size_t)R, st);
+        if (e == cudaSuccess && gross_minutes) e = cudaMemsetAsync(gross_minutes, 0, sizeof(float) * (size_t)R, st);
+        return e == cudaSuccess ? SA_OK : cuda_fail(e, who);
+    }
+    std::vector<int> edge_K((size_t)E);
+    for (int q = 0; q < E; ++q) edge_K[(size_t)q] = K[(size_t)rep[(size_t)q]];
+    const int D = (int)day_block.size() - 1;
+    unsigned* summary = nullptr;
+    unsigned long long* masks = nullptr;
+    int *d_path = nullptr, *d_day = nullptr, *d_K = nullptr, *scratch = nullptr;
+    // one chunk of edges' masks at a time, at most 4 GiB
+    const long long per_edge = 8ll * R;
+    const int chunk = (int)std::max(1ll, std::min((long long)E, (4ll << 30) / per_edge));
+    sa_status status = SA_OK;
+#define TRY(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
+    TRY(sa::scratch_alloc(&summary, sizeof(unsigned) * (size_t)E * (size_t)R, st));
+    TRY(sa::scratch_alloc(&masks, sizeof(unsigned long long) * (size_t)chunk * (size_t)R, st));
+    TRY(sa::scratch_alloc(&scratch, sizeof(int) * (size_t)R, st));
+    TRY(sa::scratch_alloc(&d_path, sizeof(int) * (size_t)nb, st));
+    TRY(sa::scratch_alloc(&d_day, sizeof(int) * (size_t)(D + 1), st));
+    TRY(sa::scratch_alloc(&d_K, sizeof(int) * (size_t)E, st));
+    TRY(cudaMemcpyAsync(d_path, path.data(), sizeof(int) * (size_t)nb, cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(d_day, day_block.data(), sizeof(int) * (size_t)(D + 1), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(d_K, edge_K.data(), sizeof(int) * (size_t)E, cudaMemcpyHostToDevice, st));
+    for (int e0 = 0; e0 < E; e0 += chunk) {
+        const int e1 = std::min(E, e0 + chunk);
+        // a sun table holding the chunk's map blocks, one per edge, each its own day; it
+        // borrows the steps of `sun`
+        sa_sun gs;
+        gs.S = sun->S;
+        gs.D = e1 - e0;
+        gs.h_steps = sun->h_steps;
+        for (int q = e0; q < e1; ++q) {
+            sa::BlockConst bc = sun->h_blocks[(size_t)rep[(size_t)q]];
+            bc.mask_block = q - e0;
+            bc.mask_bit = 0;
+            bc.new_day = 1;
+            gs.h_blocks.push_back(bc);
+            for (int i = 0; i < bc.K; ++i) {
+                sa::BlockConst sb = sun->h_step_blocks[(size_t)bc.j0 + i];
+                sb.mask_block = q - e0;
+                sb.mask_bit = i;
+                sb.new_day = i == 0;
+                gs.h_step_blocks.push_back(sb);
+            }
+        }
+        gs.d_steps = sun->d_steps;
+        e = upload(gs.h_blocks.data(), gs.h_blocks.size(), 0, &gs.d_blocks, st);
+        if (e == cudaSuccess) e = upload(gs.h_step_blocks.data(), gs.h_step_blocks.size(), 0, &gs.d_step_blocks, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(masks, 0, sizeof(unsigned long long) * (size_t)(e1 - e0) * (size_t)R, st);
+        if (e == cudaSuccess) {
+            sa::DevOut out;
+            memset(&out, 0, sizeof(out));
+            out.gross = scratch;
+            out.masks = reinterpret_cast<uint64_t*>(masks);
+            out.write_final = 1;
+            status = run_method(scene, recv, &gs, method, iam_levels, out, st, who);
+        }
+        if (e == cudaSuccess && status == SA_OK)
+            e = sa::launch_edge_summary(masks, R, e1 - e0, d_K + e0, summary + (size_t)e0 * (size_t)R, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (gs.d_blocks) cudaFree(gs.d_blocks);
+        if (gs.d_step_blocks) cudaFree(gs.d_step_blocks);
+        gs.d_steps = nullptr;
+        if (e != cudaSuccess || status != SA_OK) goto done;
+    }
+    TRY(sa::launch_graph_reduce(summary, R, d_path, d_day, D, d_K, step_minutes, gross_steps, gross_minutes,
+                                continuous_steps, st));
+done:
+    for (void* p : {(void*)summary, (void*)masks, (void*)scratch, (void*)d_path, (void*)d_day, (void*)d_K})
+        if (p) cudaFreeAsync(p, st);
+#undef TRY
+    if (status != SA_OK) return status;
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return SA_OK;
 }
 
 sa_status sa_height_grad(const sa_scene* scene, const sa_receivers* grid, const sa_sun* sun,

@@ -400,6 +400,19 @@ cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, 
                                          double* casting_out, double* nearest_out,
                                          unsigned long long* stats_out, cudaStream_t st);
 
+// direction graph (sa_graph.cu): edge of each block (blocks given by first step j0 and
+// length K over dirs [S][3]), the block each edge's map is computed from (its middle
+// block), and each edge's weight
+void direction_graph(const float* dirs, int n_blocks, const int* j0, const int* K, double bin_deg,
+                     std::vector<int>& edge, std::vector<int>& rep, std::vector<int>& weight);
+// per (edge, receiver) run summary of masks [n_edges][R] into summary [n_edges][R]
+cudaError_t launch_edge_summary(const unsigned long long* masks, long long R, int n_edges,
+                                const int* d_edge_K, unsigned* summary, cudaStream_t st);
+// gross / minutes / continuous per receiver from the summaries along each day's path
+cudaError_t launch_graph_reduce(const unsigned* summary, long long R, const int* d_path,
+                                const int* d_day_block, int D, const int* d_edge_K, float step_minutes,
+                                int* gross, float* minutes, int* continuous, cudaStream_t st);
+
 // batched scenarios (device-side descriptors; see sa_raster.cu)
 struct BatchInterval {
     const StepConst* steps;

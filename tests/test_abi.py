@@ -125,3 +125,22 @@ def test_interpolated_sun_matches_the_oracle_on_the_host():
         B.sun_interpolate(st.dirs * 2.0, st.day_start, 60)
     with pytest.raises(B.SAError):
         B.sun_interpolate(st.dirs, st.day_start, 65)
+
+
+def test_direction_graph_matches_the_oracle_on_the_host():
+    """sa_direction_graph is host code: the same edges, map blocks and weights as the
+    oracle's graph, bit for bit, on a season of one-minute steps and on the Fig. 7 case."""
+    import oracle
+    from paper_1907_04435_gb300 import binding as B
+    from synth.sun import sun_table
+    st = sun_table(40.7, list(range(172, 264)), 9.0, 17.0, 1.0)
+    for bl, bd in ((60, 5.0), (30, 2.5), (64, 10.0), (60, 1e-6)):
+        e, f, w = B.direction_graph(st.dirs, st.day_start, bl, bd)
+        oe, of, ow = oracle.direction_graph(st.dirs, st.day_start, bl, bd)
+        assert np.array_equal(e, oe) and np.array_equal(f, of) and np.array_equal(w, ow), (bl, bd)
+    e, f, w = B.direction_graph(st.dirs, st.day_start, 60, 5.0)
+    assert len(f) < len(e) / 4 and w.sum() == len(e)
+    with pytest.raises(B.SAError):
+        B.direction_graph(st.dirs, st.day_start, 60, 0.0)
+    with pytest.raises(B.SAError):
+        B.direction_graph(st.dirs, st.day_start, 60, 91.0)

@@ -1,6 +1,6 @@
 """Pins of the oracle's direction bins and direction graph (Sec. 6): the worked example of
 Fig. 7, the bins' angular bound, exactness when every interval is its own edge, repeated
-days, and the weighted gross sum of Eq. 1."""
+days (and the middle block as each edge's map), and the weighted gross sum of Eq. 1."""
 import os
 
 import numpy as np
@@ -86,6 +86,8 @@ def test_repeated_days_share_every_edge():
     edge, rep, weight = oracle.direction_graph(dirs, ds, 60, 5.0)
     nb = len(oracle.block_partition(one.day_start, 60)[0])
     assert len(rep) == nb and np.all(weight == d)
+    # each edge's map is computed from its middle block: the second of four days
+    assert np.array_equal(rep, np.arange(nb) + nb)
     bits1 = _box_bits(one.dirs)
     g1, c1 = oracle.reduce(bits1, one.day_start)
     gd, cd = oracle.reduce(oracle.graph_bits(_box_bits(dirs), dirs, ds, 60, 5.0), ds)
