@@ -627,6 +627,42 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_only_graph(args):
+    """Profiling mode for the direction graph: the season's city and sun (92 days) over a
+    smaller central ground grid (--graph-n cells a side), accumulated through the graph with
+    5 degree bins after W warm-up runs, K timed runs; prints one JSON line."""
+    import torch
+
+    from paper_1907_04435_gb300 import binding as B
+    from synth import configs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = configs.season(ground_n=args.graph_n)
+    g = w.ground
+    scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+    run = lambda: B.sa_accumulate_graph(scene, grid, sun, w.sun.step_minutes, "accrual_sam", 5.0)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    ts, maps = [], 0
+    B.sa_kernel_times()
+    B.sa_set_option(B.SA_OPT_KERNEL_TIMING, 1)
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        maps = run()[3]
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    B.sa_set_option(B.SA_OPT_KERNEL_TIMING, 0)
+    kt = {k: {"ms_per_run": v[0] / args.steps, "launches_per_run": v[1] / args.steps}
+          for k, v in B.sa_kernel_times().items() if v[1]}
+    print(json.dumps({"only_graph": True, "workload": f"season city, {g.nx}x{g.ny} ground @ {g.dx} m, "
+                      f"{w.sun.D} days ({w.sun.S} steps)", "maps": maps, "blocks": sun.n_blocks,
+                      "ms": statistics.median(ts), "kernel_times": kt}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -641,6 +677,10 @@ def main():
     ap.add_argument("--method", default="accrual_sam",
                     choices=["accrual_sam", "accrual_trace", "sweep_trace"],
                     help="the method --only-step times (ground and facades)")
+    ap.add_argument("--only-graph", action="store_true",
+                    help="time the direction graph over the season's sun only (for profiler runs)")
+    ap.add_argument("--graph-n", dest="graph_n", type=int, default=1024,
+                    help="ground cells a side for --only-graph")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-configs", action="store_true",
@@ -651,6 +691,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_graph:
+        run_only_graph(args)
     else:
         run_gpu(args)
 

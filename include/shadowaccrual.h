@@ -116,7 +116,9 @@ int32_t sa_get_option(int32_t key);
 #define SA_KERNEL_ACCRUAL 2      /* ray-traced accrual */
 #define SA_KERNEL_SWEEP 3        /* per-step ray sweep (Sec. 8.1 baseline) */
 #define SA_KERNEL_IAM 4          /* inverse accrual map line drawing (Sec. 5) */
-#define SA_KERNEL_CLASSES 5
+#define SA_KERNEL_GRAPH 5        /* direction graph: edge run summaries and day-path reduce (Sec. 6) */
+#define SA_KERNEL_RASTER_BIN 6   /* triangle binning of the ground raster (count and fill passes) */
+#define SA_KERNEL_CLASSES 7
 
 /* Collect the timed launches recorded since the last collection: waits for their events,
  * ADDS each launch's duration in milliseconds to ms[class] and 1 to launches[class]

@@ -351,7 +351,7 @@ SA_OPT_SWEEP_TRAVERSAL, SA_OPT_ACCRUAL_TRAVERSAL, SA_OPT_RASTER_RUN = 1, 2, 3
 SA_OPT_KERNEL_TIMING = 4
 SA_OPT_POINT_RUN = 5
 TRAVERSAL = {"auto": 0, "packet": 1, "lane": 2}
-KERNEL_CLASSES = ("raster", "sam_points", "accrual", "sweep", "iam")
+KERNEL_CLASSES = ("raster", "sam_points", "accrual", "sweep", "iam", "graph", "raster_bin")
 
 
 def sa_set_option(key: int, value: int):

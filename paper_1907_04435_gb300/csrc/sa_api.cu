@@ -861,16 +861,19 @@ sa_status sa_accumulate_graph(const sa_scene* scene, const sa_receivers* recv, c
         dirs[3 * (size_t)j + 1] = sun->h_steps[j].dy;
         dirs[3 * (size_t)j + 2] = sun->h_steps[j].dz;
     }
-    std::vector<int> j0(nb), K(nb), path, rep, wt, day_block;
+    std::vector<int> j0(nb), K(nb), path, rep, wt;
     for (int b = 0; b < nb; ++b) {
         j0[b] = sun->h_blocks[b].j0;
         K[b] = sun->h_blocks[b].K;
-        if (sun->h_blocks[b].new_day) day_block.push_back(b);
     }
-    day_block.push_back(nb);
     sa::direction_graph(dirs.data(), nb, j0.data(), K.data(), (double)bin_deg, path, rep, wt);
     const int E = (int)rep.size();
     if (n_edges) *n_edges = E;
+    if (E >= (1 << 20)) return fail(SA_ERR_INVALID_ARG, "%s: %d edges (at most 2^20 - 1)", who, E);
+    // every block in time order: its edge, its steps and whether it starts a day
+    std::vector<int> walk((size_t)nb);
+    for (int b = 0; b < nb; ++b)
+        walk[(size_t)b] = path[(size_t)b] | (K[(size_t)b] << 20) | ((sun->h_blocks[b].new_day ? 1 : 0) << 27);
     const long long R = recv->R;
     if (R == 0) return SA_OK;
     cudaError_t e = cudaSuccess;
@@ -882,23 +885,24 @@ sa_status sa_accumulate_graph(const sa_scene* scene, const sa_receivers* recv, c
     }
     std::vector<int> edge_K((size_t)E);
     for (int q = 0; q < E; ++q) edge_K[(size_t)q] = K[(size_t)rep[(size_t)q]];
-    const int D = (int)day_block.size() - 1;
     unsigned* summary = nullptr;
     unsigned long long* masks = nullptr;
-    int *d_path = nullptr, *d_day = nullptr, *d_K = nullptr, *scratch = nullptr;
-    // one chunk of edges' masks at a time, at most 4 GiB
+    int *d_walk = nullptr, *d_K = nullptr, *scratch = nullptr;
+    // one chunk of edges' masks at a time, at most 4 GiB (the scratch pool keeps 4 GiB
+    // across synchronisations; larger chunks are mapped again on every call), in multiples
+    // of the raster's own 64-block chunks where it holds that many
     const long long per_edge = 8ll * R;
-    const int chunk = (int)std::max(1ll, std::min((long long)E, (4ll << 30) / per_edge));
+    long long fit = std::max(1ll, (4ll << 30) / per_edge);
+    if (fit >= 64) fit -= fit % 64;
+    const int chunk = (int)std::min((long long)E, fit);
     sa_status status = SA_OK;
 #define TRY(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
     TRY(sa::scratch_alloc(&summary, sizeof(unsigned) * (size_t)E * (size_t)R, st));
     TRY(sa::scratch_alloc(&masks, sizeof(unsigned long long) * (size_t)chunk * (size_t)R, st));
     TRY(sa::scratch_alloc(&scratch, sizeof(int) * (size_t)R, st));
-    TRY(sa::scratch_alloc(&d_path, sizeof(int) * (size_t)nb, st));
-    TRY(sa::scratch_alloc(&d_day, sizeof(int) * (size_t)(D + 1), st));
+    TRY(sa::scratch_alloc(&d_walk, sizeof(int) * (size_t)nb, st));
     TRY(sa::scratch_alloc(&d_K, sizeof(int) * (size_t)E, st));
-    TRY(cudaMemcpyAsync(d_path, path.data(), sizeof(int) * (size_t)nb, cudaMemcpyHostToDevice, st));
-    TRY(cudaMemcpyAsync(d_day, day_block.data(), sizeof(int) * (size_t)(D + 1), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(d_walk, walk.data(), sizeof(int) * (size_t)nb, cudaMemcpyHostToDevice, st));
     TRY(cudaMemcpyAsync(d_K, edge_K.data(), sizeof(int) * (size_t)E, cudaMemcpyHostToDevice, st));
     for (int e0 = 0; e0 < E; e0 += chunk) {
         const int e1 = std::min(E, e0 + chunk);
@@ -942,10 +946,10 @@ sa_status sa_accumulate_graph(const sa_scene* scene, const sa_receivers* recv, c
         gs.d_steps = nullptr;
         if (e != cudaSuccess || status != SA_OK) goto done;
     }
-    TRY(sa::launch_graph_reduce(summary, R, d_path, d_day, D, d_K, step_minutes, gross_steps, gross_minutes,
+    TRY(sa::launch_graph_reduce(summary, R, d_walk, nb, step_minutes, gross_steps, gross_minutes,
                                 continuous_steps, st));
 done:
-    for (void* p : {(void*)summary, (void*)masks, (void*)scratch, (void*)d_path, (void*)d_day, (void*)d_K})
+    for (void* p : {(void*)summary, (void*)masks, (void*)scratch, (void*)d_walk, (void*)d_K})
         if (p) cudaFreeAsync(p, st);
 #undef TRY
     if (status != SA_OK) return status;

@@ -17,8 +17,10 @@
 //                     popcount (Eq. 1: each edge's count times its weight), and the longest
 //                     continuous run, stitched along each day's path of edges in time order
 //                     from the prefix / longest / suffix runs (Sec. 6, continuous shadows).
+//                     The days' paths are one walk of packed codes staged in shared memory.
 #include <math.h>
 
+#include <algorithm>
 #include <map>
 #include <tuple>
 #include <vector>
@@ -30,66 +32,106 @@ namespace sa {
 namespace {
 
 constexpr int kGraphThreads = 256;
+constexpr int kGather = 8;        // summaries a thread loads ahead in the walk
+constexpr int kWalkTile = 2048;   // walk codes staged in shared memory at a time
 
+// Longest run of ones in x, which is not all ones.  With A_k the bits i at which a run of
+// at least k ones starts (A_1 = x, A_{a+b} = A_a & (A_b >> a)), the longest run is the
+// largest n with A_n != 0; it is found bit by bit from 32 down, since it is below 64.
 __device__ __forceinline__ unsigned longest_run(unsigned long long x) {
+    const unsigned long long a1 = x, a2 = a1 & (a1 >> 1), a4 = a2 & (a2 >> 2), a8 = a4 & (a4 >> 4),
+                             a16 = a8 & (a8 >> 8), a32 = a16 & (a16 >> 16);
+    unsigned long long cur = ~0ull;   // A_0
     unsigned n = 0;
-    while (x) {        // each pass shortens every run of ones by one
-        x &= x >> 1;
-        ++n;
-    }
+    unsigned long long c;
+    c = cur & (a32 >> n); if (c) { cur = c; n += 32; }
+    c = cur & (a16 >> n); if (c) { cur = c; n += 16; }
+    c = cur & (a8 >> n);  if (c) { cur = c; n += 8; }
+    c = cur & (a4 >> n);  if (c) { cur = c; n += 4; }
+    c = cur & (a2 >> n);  if (c) { cur = c; n += 2; }
+    c = cur & (a1 >> n);  if (c) { n += 1; }
     return n;
 }
 
+// grid: x over receivers, y over edges (strided)
 __global__ void k_edge_summary(const unsigned long long* __restrict__ masks, long long R, int n_edges,
                                const int* __restrict__ edge_K, unsigned* __restrict__ summary) {
-    const long long items = R * n_edges;
-    for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < items;
-         it += (long long)gridDim.x * blockDim.x) {
-        const int e = (int)(it / R);
+    for (int e = blockIdx.y; e < n_edges; e += gridDim.y) {
         const int K = __ldg(&edge_K[e]);
         const unsigned long long low = K >= 64 ? ~0ull : ((1ull << K) - 1ull);
-        const unsigned long long m = masks[it] & low;
-        const unsigned pop = (unsigned)__popcll(m);
-        unsigned pre, suf, best;
-        if (pop == (unsigned)K) {
-            pre = suf = best = (unsigned)K;
-        } else {
-            pre = (unsigned)(__ffsll((long long)~m) - 1);            // ones below the first zero
-            suf = (unsigned)__clzll((long long)~(m << (64 - K)));   // ones above the last zero
-            best = longest_run(m);
+        const unsigned long long* __restrict__ me = masks + (long long)e * R;
+        unsigned* __restrict__ se = summary + (long long)e * R;
+        for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < R;
+             r += (long long)gridDim.x * blockDim.x) {
+            const unsigned long long m = me[r] & low;
+            if (m == 0ull) {            // lit at every step: the most common case
+                se[r] = 0u;
+                continue;
+            }
+            const unsigned pop = (unsigned)__popcll(m);
+            unsigned pre, suf, best;
+            if (pop == (unsigned)K) {
+                pre = suf = best = (unsigned)K;
+            } else {
+                pre = (unsigned)(__ffsll((long long)~m) - 1);            // ones below the first zero
+                suf = (unsigned)__clzll((long long)~(m << (64 - K)));   // ones above the last zero
+                best = longest_run(m);
+            }
+            se[r] = pop | (pre << 8) | (suf << 16) | (best << 24);
         }
-        summary[it] = pop | (pre << 8) | (suf << 16) | (best << 24);
     }
 }
 
-__global__ void k_graph_reduce(const unsigned* __restrict__ summary, long long R,
-                               const int* __restrict__ path, const int* __restrict__ day_block,
-                               int D, const int* __restrict__ edge_K, float step_minutes,
-                               int* __restrict__ gross, float* __restrict__ minutes,
-                               int* __restrict__ continuous) {
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < R;
-         r += (long long)gridDim.x * blockDim.x) {
-        int g = 0, best_all = 0;
-        for (int d = 0; d < D; ++d) {
-            int run = 0, best = 0;
-            const int b1 = __ldg(&day_block[d + 1]);
-            for (int b = __ldg(&day_block[d]); b < b1; ++b) {
-                const int e = __ldg(&path[b]);
-                const unsigned s = summary[(long long)e * R + r];
-                const int pop = (int)(s & 255u);
-                if (pop == __ldg(&edge_K[e])) {
-                    run += pop;
-                } else {
-                    best = max(best, max(run + (int)((s >> 8) & 255u), (int)(s >> 24)));
-                    run = (int)((s >> 16) & 255u);
+// The walk: every block of every day in time order, packed as edge | K << 20 | new_day << 27.
+// Each CTA stages kWalkTile codes of it in shared memory; each thread walks them for its
+// receiver, loading kGather summaries ahead of their use.
+__global__ void __launch_bounds__(kGraphThreads) k_graph_reduce(
+    const unsigned* __restrict__ summary, long long R, const int* __restrict__ walk, int n_walk,
+    float step_minutes, int* __restrict__ gross, float* __restrict__ minutes, int* __restrict__ continuous) {
+    __shared__ int s_walk[kWalkTile];
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < R; base += (long long)gridDim.x * blockDim.x) {
+        const long long r = base + threadIdx.x;
+        const bool valid = r < R;
+        int g = 0, best_all = 0, run = 0, best = 0;
+        for (int p0 = 0; p0 < n_walk; p0 += kWalkTile) {
+            const int n = min(kWalkTile, n_walk - p0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) s_walk[i] = __ldg(&walk[p0 + i]);
+            __syncthreads();
+            if (!valid) continue;
+            for (int i = 0; i < n; i += kGather) {
+                unsigned sm[kGather];
+                int code[kGather];
+#pragma unroll
+                for (int q = 0; q < kGather; ++q) {
+                    code[q] = i + q < n ? s_walk[i + q] : -1;
+                    sm[q] = code[q] >= 0 ? summary[(long long)(code[q] & 0xFFFFF) * R + r] : 0u;
                 }
-                g += pop;
+#pragma unroll
+                for (int q = 0; q < kGather; ++q) {
+                    if (code[q] < 0) break;
+                    if (code[q] & (1 << 27)) {          // a new day: close the previous one
+                        best_all = max(best_all, max(best, run));
+                        run = best = 0;
+                    }
+                    const int K = (code[q] >> 20) & 127;
+                    const int pop = (int)(sm[q] & 255u);
+                    if (pop == K) {
+                        run += pop;
+                    } else {
+                        best = max(best, max(run + (int)((sm[q] >> 8) & 255u), (int)(sm[q] >> 24)));
+                        run = (int)((sm[q] >> 16) & 255u);
+                    }
+                    g += pop;
+                }
             }
-            best_all = max(best_all, max(best, run));
         }
-        gross[r] = g;
-        if (minutes) minutes[r] = (float)g * step_minutes;
-        if (continuous) continuous[r] = best_all;
+        if (valid) {
+            best_all = max(best_all, max(best, run));
+            gross[r] = g;
+            if (minutes) minutes[r] = (float)g * step_minutes;
+            if (continuous) continuous[r] = best_all;
+        }
     }
 }
 
@@ -140,16 +182,20 @@ void direction_graph(const float* dirs, int n_blocks, const int* j0, const int* 
 cudaError_t launch_edge_summary(const unsigned long long* masks, long long R, int n_edges,
                                 const int* d_edge_K, unsigned* summary, cudaStream_t st) {
     if (R <= 0 || n_edges <= 0) return cudaSuccess;
-    k_edge_summary<<<grid_for(R * n_edges), kGraphThreads, 0, st>>>(masks, R, n_edges, d_edge_K, summary);
+    const long long bx = (R + kGraphThreads - 1) / kGraphThreads;
+    dim3 grid((unsigned)std::min(bx, 152ll * 8), (unsigned)std::min(n_edges, 65535));
+    KernelTimer kt(KT_GRAPH, st);
+    k_edge_summary<<<grid, kGraphThreads, 0, st>>>(masks, R, n_edges, d_edge_K, summary);
     return cudaGetLastError();
 }
 
-cudaError_t launch_graph_reduce(const unsigned* summary, long long R, const int* d_path,
-                                const int* d_day_block, int D, const int* d_edge_K, float step_minutes,
-                                int* gross, float* minutes, int* continuous, cudaStream_t st) {
+cudaError_t launch_graph_reduce(const unsigned* summary, long long R, const int* d_walk, int n_walk,
+                                float step_minutes, int* gross, float* minutes, int* continuous,
+                                cudaStream_t st) {
     if (R <= 0) return cudaSuccess;
-    k_graph_reduce<<<grid_for(R), kGraphThreads, 0, st>>>(summary, R, d_path, d_day_block, D, d_edge_K,
-                                                          step_minutes, gross, minutes, continuous);
+    KernelTimer kt(KT_GRAPH, st);
+    k_graph_reduce<<<grid_for(R), kGraphThreads, 0, st>>>(summary, R, d_walk, n_walk, step_minutes, gross,
+                                                          minutes, continuous);
     return cudaGetLastError();
 }
 

@@ -408,10 +408,11 @@ void direction_graph(const float* dirs, int n_blocks, const int* j0, const int* 
 // per (edge, receiver) run summary of masks [n_edges][R] into summary [n_edges][R]
 cudaError_t launch_edge_summary(const unsigned long long* masks, long long R, int n_edges,
                                 const int* d_edge_K, unsigned* summary, cudaStream_t st);
-// gross / minutes / continuous per receiver from the summaries along each day's path
-cudaError_t launch_graph_reduce(const unsigned* summary, long long R, const int* d_path,
-                                const int* d_day_block, int D, const int* d_edge_K, float step_minutes,
-                                int* gross, float* minutes, int* continuous, cudaStream_t st);
+// gross / minutes / continuous per receiver from the summaries along each day's path; the
+// walk holds every block in time order as edge | K << 20 | (first block of a day) << 27
+cudaError_t launch_graph_reduce(const unsigned* summary, long long R, const int* d_walk, int n_walk,
+                                float step_minutes, int* gross, float* minutes, int* continuous,
+                                cudaStream_t st);
 
 // batched scenarios (device-side descriptors; see sa_raster.cu)
 struct BatchInterval {
@@ -507,7 +508,8 @@ namespace sa {
 
 // Per-kernel device timing: while enabled, a CUDA event pair is recorded on the launching
 // stream around each launch of the library's main kernels (not inside stream capture).
-enum KernelClass { KT_RASTER = 0, KT_SAM_POINTS = 1, KT_ACCRUAL = 2, KT_SWEEP = 3, KT_IAM = 4 };
+enum KernelClass { KT_RASTER = 0, KT_SAM_POINTS = 1, KT_ACCRUAL = 2, KT_SWEEP = 3, KT_IAM = 4,
+                   KT_GRAPH = 5, KT_RASTER_BIN = 6 };
 void set_kernel_timing(int on);
 int get_kernel_timing();
 struct KernelTimer {

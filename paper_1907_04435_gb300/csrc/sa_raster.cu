@@ -90,9 +90,11 @@ __global__ void k_bin_count(DevScene sc, const StepConst* __restrict__ steps,
     const float4 a = __ldg(&sc.tris[3 * t]), b = __ldg(&sc.tris[3 * t + 1]),
                  c = __ldg(&sc.tris[3 * t + 2]);
     if (!tri_above_ground(a, b, c)) return;
-    if (sc.closed && !faces_sun(a, b, c, steps, blocks[b0 + bl])) return;
+    // the tile range first: it culls the triangles whose shadow misses the grid before the
+    // per-step facing test (both are conservative, so the order leaves the bins unchanged)
     int tx0, tx1, ty0, ty1;
     if (!swept_tiles(a, b, c, blocks[b0 + bl], g, &tx0, &tx1, &ty0, &ty1)) return;
+    if (sc.closed && !faces_sun(a, b, c, steps, blocks[b0 + bl])) return;
     unsigned* row = counts + (size_t)bl * g.tiles_x * g.tiles_y;
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&row[ty * g.tiles_x + tx], 1u);
@@ -108,9 +110,9 @@ __global__ void k_bin_fill(DevScene sc, const StepConst* __restrict__ steps,
     const float4 a = __ldg(&sc.tris[3 * t]), b = __ldg(&sc.tris[3 * t + 1]),
                  c = __ldg(&sc.tris[3 * t + 2]);
     if (!tri_above_ground(a, b, c)) return;
-    if (sc.closed && !faces_sun(a, b, c, steps, blocks[b0 + bl])) return;
     int tx0, tx1, ty0, ty1;
     if (!swept_tiles(a, b, c, blocks[b0 + bl], g, &tx0, &tx1, &ty0, &ty1)) return;
+    if (sc.closed && !faces_sun(a, b, c, steps, blocks[b0 + bl])) return;
     const size_t row = (size_t)bl * g.tiles_x * g.tiles_y;
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
@@ -740,7 +742,10 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
         unsigned total = 0;
         if (sc.T > 0) {
             dim3 grid((sc.T + tpb - 1) / tpb, nbc);
-            k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, counts);
+            {
+                KernelTimer kt(KT_RASTER_BIN, st);
+                k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, counts);
+            }
             k_tile_order<<<1, 1024, 0, st>>>(counts, nbc, n_tiles, order);
             e = cudaMemcpyAsync(offsets, counts, sizeof(unsigned) * ncc, cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) break;
@@ -756,7 +761,10 @@ cudaError_t launch_raster_ground(const DevScene& sc, const DevRecv& rc, const De
                 e = sa::scratch_alloc(&bins, sizeof(int) * bins_cap, st);
                 if (e != cudaSuccess) { bins = nullptr; break; }
             }
-            if (total > 0) k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, offsets, cursor, bins);
+            if (total > 0) {
+                KernelTimer kt(KT_RASTER_BIN, st);
+                k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, offsets, cursor, bins);
+            }
         } else {
             e = cudaMemsetAsync(offsets, 0, sizeof(unsigned) * ncc, st);
             if (e != cudaSuccess) break;
