@@ -295,6 +295,22 @@ def run_gpu(args):
     # ---- the other workloads (small sweep case, season, height gradient)
     other = None if (args.skip_configs or world > 1) else bench_configs(B)
 
+    # ---- analysis measures over the central 1024 x 1024 m of the district (Sec. 7.2)
+    analysis = None
+    if not args.skip_configs and world == 1:
+        gross, _, _ = B.sa_accumulate(scene, grid, sun, st.step_minutes, "accrual_sam")
+        xa, ya = g.x0 + 512 * g.dx, g.y0 + 512 * g.dx
+        xb, yb = xa + 1024 * g.dx, ya + 1024 * g.dx
+        poly = np.array([[xa, ya], [xb, ya], [xb, yb], [xa, yb]], np.float32)
+        area_ms = _event_ms(lambda: B.sa_shadow_area(grid, gross, st.S, poly), 5)
+        contrib_ms = _event_ms(lambda: B.sa_building_contribution(scene, grid, sun, poly), 3)
+        casting, nearest, stats = B.sa_building_contribution(scene, grid, sun, poly)
+        analysis = {"region": "central 1024 x 1024 cells of the ground grid",
+                    "shadow_area_ms": area_ms, "shadow_area_m2": B.sa_shadow_area(grid, gross, st.S, poly),
+                    "building_contribution_ms": contrib_ms,
+                    "buildings_casting": int((casting > 0).sum()),
+                    "nearest_sum_m2": float(nearest.sum()), "unattributed_cell_steps": stats[1]}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -311,6 +327,7 @@ def run_gpu(args):
             "gpu_launches": count_launches(scene, sun, grid, fac),
             "batch": batch,
             "other_workloads": other,
+            "analysis": analysis,
             "clocks": clk,
         }
         if world == 1 and not args.skip_cpu:

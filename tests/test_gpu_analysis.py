@@ -169,3 +169,33 @@ def test_building_contribution_rejects_bad_arguments(cuda_lib):
     # a region holding no cell centre credits nothing
     c, n, st = B.sa_building_contribution(scene, grid, sun, [[0, 0], [1, 0], [1, 1]])
     assert not c.any() and not n.any() and st == (0, 0)
+
+
+def test_building_contribution_without_buildings_and_with_ragged_grids(cuda_lib):
+    """An empty scene credits nothing; a grid whose sides are not multiples of the raster's
+    32-cell tiles gives the same per-building counts as the oracle on its centres."""
+    B = cuda_lib
+    from synth import city as C
+    empty = B.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), None, 0)
+    w = workload("district_small")
+    g = w.ground
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+    c, n, st = B.sa_building_contribution(empty, grid, sun, POLYGONS["convex"])
+    assert c.size == 0 and n.size == 0 and st == (0, 0)
+    city = C.City([C.box_footprint(20, 20, 32, 29), C.box_footprint(45, 12, 51, 40)],
+                  np.array([25.0, 40.0], np.float32))
+    mesh = C.extrude(city)
+    scene = B.Scene(mesh.verts, mesh.tris, mesh.tri_building, 2, closed=True)
+    x0, y0, dx, nx, ny = -3.0, -2.0, 0.7, 101, 77
+    grid = B.Receivers.ground_grid(x0, y0, dx, nx, ny)
+    poly = np.array([[-3.0, -2.0], [60.0, -2.0], [60.0, 45.0], [-3.0, 45.0]], np.float32)
+    casting, nearest, (over, un) = B.sa_building_contribution(scene, grid, sun, poly)
+    pos = _region_centres(SimpleNamespace(x0=x0, y0=y0, dx=dx, nx=nx, ny=ny), poly)
+    c_o, n_o, u_o, u_any = oracle.building_steps(mesh.tri9(), mesh.tri_building, pos, None,
+                                                 w.sun.dirs, w.sun.day_start, 2)
+    unit = dx * dx / w.sun.S
+    cnt_c = np.round(casting / unit).astype(np.int64)
+    cnt_n = np.round(nearest / unit).astype(np.int64)
+    assert np.all(np.abs(cnt_c - c_o) <= u_o) and np.abs(cnt_n - n_o).sum() <= 2 * u_any
+    assert c_o.min() > 0 and over == 0

@@ -109,3 +109,26 @@ def test_graph_rejects_bad_bins(cuda_lib):
     for bd in (0.0, -1.0, 120.0, float("nan")):
         with pytest.raises(B.SAError):
             B.sa_accumulate_graph(scene, grid, sun, w.sun.step_minutes, "accrual_sam", bd)
+
+
+def test_graph_degenerate_inputs(cuda_lib):
+    """No receivers, a sun table with no steps, point receivers with a grid-only method,
+    and one day (every block its own edge): the exact counts."""
+    B = cuda_lib
+    w = _case(n_facade=0)
+    scene, sun, grid = _handles(B, w)
+    empty_grid = B.Receivers.ground_grid(0.0, 0.0, 1.0, 0, 0)
+    g, m, c, ne = B.sa_accumulate_graph(scene, empty_grid, sun, w.sun.step_minutes, "accrual_sam")
+    assert g.numel() == 0 and ne == len(oracle.direction_graph(w.sun.dirs, w.sun.day_start)[1])
+    no_steps = B.Sun(np.zeros((0, 3), np.float32), np.zeros(1, np.int32))
+    g, m, c, ne = B.sa_accumulate_graph(scene, grid, no_steps, w.sun.step_minutes, "accrual_sam")
+    assert ne == 0 and not g.any() and not c.any() and not m.any()
+    pts = B.Receivers.points(np.array([[50.0, 50.0, 0.0]], np.float32))
+    with pytest.raises(B.SAError):
+        B.sa_accumulate_graph(scene, pts, sun, w.sun.step_minutes, "iam")
+    one = configs.district_small(doys=(172,), step=2.0, n_facade=0)
+    sc1, sun1, grid1 = _handles(B, one)
+    ge, _, ce = B.sa_accumulate(sc1, grid1, sun1, one.sun.step_minutes, "accrual_sam")
+    gg, _, cg, ne = B.sa_accumulate_graph(sc1, grid1, sun1, one.sun.step_minutes, "accrual_sam", 5.0)
+    assert ne == sun1.n_blocks
+    assert np.array_equal(gg.cpu().numpy(), ge.cpu().numpy()) and np.array_equal(cg.cpu().numpy(), ce.cpu().numpy())
