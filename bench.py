@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -249,7 +250,8 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".", f"clocks_rank{rank}.csv"))
+    csv_dir = args.clocks_dir or tempfile.gettempdir()
+    clocks = ClockSampler(local, os.path.join(csv_dir, f"clocks_rank{rank}.csv"))
     ktimes = {}
     ms, ms_g, ms_f = timed("accrual_sam", "accrual_sam", args.steps, args.warmup, ktimes)
     clk = clocks.stop()
@@ -722,6 +724,8 @@ def main():
                     help="time the direction graph over the season's sun only (for profiler runs)")
     ap.add_argument("--graph-n", dest="graph_n", type=int, default=1024,
                     help="ground cells a side for --only-graph")
+    ap.add_argument("--clocks-dir", dest="clocks_dir", default=None,
+                    help="folder for the raw nvidia-smi clock samples (default: the temp folder)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-configs", action="store_true",
