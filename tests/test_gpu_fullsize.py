@@ -59,7 +59,8 @@ def test_season_full_size_sampled(cuda_lib):
     """50,000 buildings (1.53M triangles), central 4096^2 cells, 92 days x 481 steps.
     Over 44,252 steps nearly every receiver has steps within 1e-4 rad of a boundary, so
     the grid counts are held to |difference| <= the receiver's near-boundary steps, and
-    the sampled cells, traced as points, to per-step bit parity away from boundaries."""
+    the sampled cells, traced as points, to per-step bit parity away from boundaries; the
+    direction graph over the same season is held to the oracle's graph on the same cells."""
     B = cuda_lib
     w = configs.season()
     assert w.mesh.T > 1_400_000 and w.sun.S == 92 * 481
@@ -97,6 +98,16 @@ def test_season_full_size_sampled(cuda_lib):
     masks = B.sa_shadow_masks(scene, B.Receivers.points(pos), sun, "accrual_trace")
     gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start))
     assert_bits_parity(gb, bits, near, "season points")
+    # the same season through the direction graph (5 degree bins, Sec. 6): the sampled cells
+    # against the oracle's graph of the same bits, within the near-boundary steps its maps use
+    gg, _, gc, n_edges = B.sa_accumulate_graph(scene, _grid(B, w.ground), sun, 1.0, "accrual_sam", 5.0)
+    _, rep, _ = oracle.direction_graph(w.sun.dirs, w.sun.day_start, 0, 5.0)
+    assert n_edges == len(rep) < sun.n_blocks // 4
+    obits = oracle.graph_bits(bits, w.sun.dirs, w.sun.day_start, 0, 5.0)
+    onear = oracle.graph_bits(near, w.sun.dirs, w.sun.day_start, 0, 5.0)
+    ogg, _ = oracle.reduce(obits, w.sun.day_start)
+    gg = gg.cpu().numpy()
+    assert np.all(np.abs(gg[sel].astype(np.int64) - ogg) <= onear.sum(axis=1)), (gg[sel], ogg)
 
 
 def test_park_adjoint_full_size(cuda_lib):
