@@ -192,3 +192,30 @@ def test_batched_scenarios_full_size_sampled(cuda_lib):
             o = bt.offset(i, v)
             got = counts[o + loc].astype(np.int64)
             assert np.all(np.abs(got - og) <= near.sum(axis=1)), (v, i, got, og)
+
+
+def test_building_contribution_full_size_region(cuda_lib):
+    """The district scene (2,000 buildings) over its full 2048^2 grid, with a region of
+    24 x 24 cells small enough for the oracle: every building's casting count within its own
+    near-boundary pairs, the nearest counts within twice the pairs near any boundary."""
+    B = cuda_lib
+    w = configs.district(n_facade=0)
+    g = w.ground
+    scene = _closed_scene(B, w)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    grid = _grid(B, g)
+    ix0, iy0 = 1000, 1012
+    xa, ya = g.x0 + ix0 * g.dx, g.y0 + iy0 * g.dx
+    poly = np.array([[xa, ya], [xa + 24 * g.dx, ya], [xa + 24 * g.dx, ya + 24 * g.dx],
+                     [xa, ya + 24 * g.dx]], np.float32)
+    casting, nearest, (over, un) = B.sa_building_contribution(scene, grid, sun, poly)
+    cells = np.array([(ix0 + i) + (iy0 + j) * g.nx for j in range(24) for i in range(24)])
+    pos = g.positions()[cells]
+    c_o, n_o, u_o, u_any = oracle.building_steps(w.mesh.tri9(), w.mesh.tri_building, pos, None,
+                                                 w.sun.dirs, w.sun.day_start, w.city.B)
+    unit = g.dx * g.dx / w.sun.S
+    cnt_c = np.round(casting / unit).astype(np.int64)
+    cnt_n = np.round(nearest / unit).astype(np.int64)
+    assert c_o.sum() > 1000 and over == 0
+    assert np.all(np.abs(cnt_c - c_o) <= u_o), np.nonzero(np.abs(cnt_c - c_o) > u_o)[0]
+    assert np.abs(cnt_n - n_o).sum() <= 2 * u_any and un <= u_any
