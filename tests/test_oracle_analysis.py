@@ -168,3 +168,84 @@ def test_the_nearer_of_two_buildings_in_line_is_the_nearest_caster():
                                                    dirs, np.array([0, 1], np.int32), 2)
     assert list(casting) == [3, 3]
     assert list(nearest) == [3, 0]
+
+
+def test_a_building_in_parts_is_nearest_by_its_nearest_part():
+    """Building 0 is two boxes with building 1 between them, in line toward a low sun in
+    the east: a receiver west of all three meets building 0 first, so building 0 is the
+    nearest caster although its farther part lies beyond building 1."""
+    from synth import city as C
+    city = C.City([C.box_footprint(10, -5, 20, 5), C.box_footprint(40, -5, 50, 5),
+                   C.box_footprint(70, -5, 80, 5)], np.array([40.0, 40.0, 40.0], np.float32))
+    mesh = C.extrude(city)
+    tb = np.where(mesh.tri_building == 1, 1, 0).astype(np.int32)   # boxes 0 and 2 are one building
+    el = np.radians(15.0)
+    dirs = np.array([[np.cos(el), 0.0, np.sin(el)]], np.float32)
+    pos = np.array([[0.0, 0.0, 0.0], [0.0, 1.5, 0.0], [-2.0, -1.0, 0.0]], np.float32)
+    casting, nearest, _, _ = oracle.building_steps(mesh.tri9(), tb, pos, None, dirs,
+                                                   np.array([0, 1], np.int32), 2)
+    assert list(casting) == [3, 3]
+    assert list(nearest) == [3, 0]
+
+
+def test_per_building_near_boundary_under_a_wide_rotation():
+    """With a rotation wide enough that many pairs flip, one building's near-boundary count
+    equals the plain rule's, which rotates the sun both ways along its arc."""
+    w, pos = _boxes_case(400, seed=8)
+    t9, tb = w.mesh.tri9(), w.mesh.tri_building
+    keep = tb == 3
+    t9b, tbb = t9[keep], np.zeros(int(keep.sum()), np.int32)
+    eps = 0.03
+    _, _, unstable, unstable_any = oracle.building_steps(t9b, tbb, pos, None, w.sun.dirs,
+                                                         w.sun.day_start, 1, eps=eps)
+    bits = oracle.shadow_bits(t9b, tbb, pos, None, w.sun.dirs)
+    near = oracle.near_boundary(t9b, tbb, pos, None, w.sun.dirs, w.sun.day_start, bits, eps=eps)
+    assert near.sum() > 200
+    assert unstable[0] == unstable_any == near.sum()
+
+
+def test_walls_behind_a_receiver_cast_nothing():
+    """Ground receivers 0.3 m outside every wall of a box, and facade receivers on the walls:
+    the casting counts equal the plain shadow bits and the facing closed form, so a wall just
+    behind a receiver, on the far side from the sun, is never counted."""
+    from synth import city as C
+    city = C.City([C.box_footprint(0, 0, 20, 12)], np.array([25.0], np.float32))
+    mesh = C.extrude(city)
+    xs = np.linspace(1.0, 19.0, 10)
+    ys = np.linspace(1.0, 11.0, 6)
+    pts = [(x, -0.3) for x in xs] + [(x, 12.3) for x in xs] + [(-0.3, y) for y in ys] + [(20.3, y) for y in ys]
+    pos = np.array([(x, y, 0.0) for x, y in pts], np.float32)
+    from synth.sun import sun_table
+    st = sun_table(40.7, [172, 355], 7.0, 17.0, 10.0)
+    casting, nearest, _, _ = oracle.building_steps(mesh.tri9(), mesh.tri_building, pos, None,
+                                                   st.dirs, st.day_start, 1)
+    bits = oracle.shadow_bits(mesh.tri9(), mesh.tri_building, pos, None, st.dirs)
+    assert casting[0] == nearest[0] == bits.sum()
+    assert 0 < bits.sum() < bits.size
+    # facade receivers on the walls themselves (origin 1 cm out along the outward normal):
+    # the counts equal the plain facade bits; a lone box shadows a facade point whose wall
+    # faces clearly away from the sun and never one whose wall faces it (at grazing angles
+    # the ray from 1 cm out can pass the wall's edge)
+    fpos = np.array([(x, 0.0, 5.0) for x in xs] + [(x, 12.0, 5.0) for x in xs] +
+                    [(0.0, y, 5.0) for y in ys] + [(20.0, y, 5.0) for y in ys], np.float32)
+    fnrm = np.array([(0, -1, 0)] * 10 + [(0, 1, 0)] * 10 + [(-1, 0, 0)] * 6 + [(1, 0, 0)] * 6, np.float32)
+    casting, nearest, _, _ = oracle.building_steps(mesh.tri9(), mesh.tri_building, fpos, fnrm,
+                                                   st.dirs, st.day_start, 1)
+    fbits = oracle.shadow_bits(mesh.tri9(), mesh.tri_building, fpos, fnrm, st.dirs)
+    assert casting[0] == nearest[0] == fbits.sum() > 0
+    nd = fnrm.astype(np.float64) @ st.dirs.astype(np.float64).T
+    assert np.all(fbits[nd < -0.05] == 1) and np.all(fbits[nd > 0] == 0)
+    # an L-shaped building (two boxes, one id): facade points on its inner walls start
+    # inside the building's bounding box, with their own wall 1 cm behind them
+    city = C.City([C.box_footprint(0, 0, 20, 10), C.box_footprint(0, 10, 10, 30)],
+                  np.array([25.0, 25.0], np.float32))
+    mesh = C.extrude(city)
+    tb = np.zeros_like(mesh.tri_building)
+    lpos = np.array([(10.0, y, 4.0) for y in np.linspace(12.0, 28.0, 9)] +
+                    [(x, 10.0, 4.0) for x in np.linspace(11.0, 19.0, 5)], np.float32)
+    lnrm = np.array([(1, 0, 0)] * 9 + [(0, 1, 0)] * 5, np.float32)
+    casting, nearest, _, _ = oracle.building_steps(mesh.tri9(), tb, lpos, lnrm, st.dirs, st.day_start, 1)
+    lbits = oracle.shadow_bits(mesh.tri9(), tb, lpos, lnrm, st.dirs)
+    assert casting[0] == nearest[0] == lbits.sum()
+    lnd = lnrm.astype(np.float64) @ st.dirs.astype(np.float64).T
+    assert np.any((lnd > 0.05) & (lbits == 0))          # sunlit inner walls exist in the case
