@@ -116,3 +116,31 @@ def test_more_levels_find_more_shadow_behind_the_first_source():
     one = oracle.iam_bits(mesh.tri9(), mesh.tri_building, grid, st.dirs, st.day_start, levels=1)
     two = oracle.iam_bits(mesh.tri9(), mesh.tri_building, grid, st.dirs, st.day_start, levels=2)
     assert np.all(two >= one) and two.sum() > one.sum()
+
+
+def test_the_100_cm_rule_behind_a_thin_low_wall():
+    """A wall 0.4 m thick and 0.6 m tall under a low sun: rays from the cells just behind
+    it meet the wall only within 1 m, so with one-step blocks the map marks none of them
+    (the paper's 100 cm rule), while every cell with a hit beyond 1 m is marked."""
+    city = C.City([C.box_footprint(0.0, 0.0, 0.4, 20.0)], np.array([0.6], np.float32))
+    mesh = C.extrude(city)
+    el = np.radians(25.0)                                  # toward the east, a little south
+    dirs = np.array([[np.cos(el), -0.15, np.sin(el)]], np.float32)
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    grid = (-3.0, 1.0, 0.1, 30, 180)                       # the strip west of the wall
+    g = C.GroundGrid(*grid)
+    iam = oracle.iam_bits(mesh.tri9(), mesh.tri_building, grid, dirs, np.array([0, 1], np.int32),
+                          block_len=1, levels=1)[:, 0]
+    t9 = mesh.tri9().astype(np.float64).reshape(-1, 3, 3)
+    pos = g.positions().astype(np.float64)
+    d = dirs[0].astype(np.float64)
+    far = np.zeros(g.R, bool)
+    near_only = np.zeros(g.R, bool)
+    for r in range(g.R):
+        ts = _hit_distances(t9, pos[r], d)
+        if ts:
+            far[r] = max(ts) > 1.0 + 1e-6
+            near_only[r] = max(ts) < 1.0 - 1e-6
+    assert near_only.sum() > 50 and far.sum() > 50
+    assert not iam[near_only].any()
+    assert iam[far].all()
