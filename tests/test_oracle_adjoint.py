@@ -119,3 +119,21 @@ def test_shadow_integral_counts_whole_steps_without_flips():
     w = np.array([2.0, 5.0])
     assert oracle.shadow_integral(m.tri9(), m.tri_building, pos, st.dirs, st.day_start,
                                   st.step_minutes, weights=w) == 2.0 * per[0]
+
+
+def test_shadow_integral_follows_the_great_circle_between_hourly_steps():
+    """Steps an hour apart (about 15 degrees): between them the sun moves on the great
+    circle at a constant rate, which a straight-line interpolation of the directions would
+    miss by a measurable part of the step at every flip."""
+    fp = C.box_footprint(0.0, 0.0, 30.0, 20.0)
+    h = 40.0
+    city = C.City([fp], np.array([h], np.float32))
+    st = sun_table(40.7, [80], 9.0, 17.0, 60.0)
+    g = C.GroundGrid(-80.0, -80.0, 1.0, 190, 120)
+    pos = g.positions()
+    fp32 = fp.astype(np.float32).astype(np.float64)
+    S_cf, _ = closed_form(fp32, h, pos, st.dirs, st.step_minutes)
+    m = C.extrude(city)
+    S = oracle.shadow_integral(m.tri9(), m.tri_building, pos, st.dirs, st.day_start, st.step_minutes)
+    assert abs(S - S_cf) <= 1e-6 * S_cf, (S, S_cf)
+    assert st.S == 9
