@@ -300,3 +300,24 @@ def test_linear_sun_motion_statistics_match_table_1():
     for m in (5, 10, 30, 60):
         assert means[m] > 0.99999 - 1e-6
     assert means[240] < means[60]
+
+
+def test_near_boundary_does_not_depend_on_the_direction_of_the_arc():
+    """The rule rotates each direction both ways along the sun's arc, so running the day's
+    steps backwards (which reverses the arc's tangent) classifies every pair the same."""
+    fp = C.box_footprint(0.0, 0.0, 20.0, 20.0)
+    city = C.City([fp], np.array([50.0], np.float32))
+    mesh = C.extrude(city)
+    sun = sun_table(40.7, [172], 10.0, 14.0, 30.0)
+    pos = _ground_grid(-80.0, -80.0, 0.37, 300, 300)
+    eps = 2e-3
+    bits = oracle.shadow_bits(mesh.tri9(), mesh.tri_building, pos, None, sun.dirs)
+    near = oracle.near_boundary(mesh.tri9(), mesh.tri_building, pos, None, sun.dirs,
+                                sun.day_start, bits, eps=eps)
+    rev = sun.dirs[::-1].copy()
+    rbits = oracle.shadow_bits(mesh.tri9(), mesh.tri_building, pos, None, rev)
+    rnear = oracle.near_boundary(mesh.tri9(), mesh.tri_building, pos, None, rev,
+                                 sun.day_start, rbits, eps=eps)
+    assert np.array_equal(rbits[:, ::-1], bits)
+    assert np.array_equal(rnear[:, ::-1], near)
+    assert near.sum() > 100
