@@ -144,3 +144,12 @@ def test_direction_graph_matches_the_oracle_on_the_host():
         B.direction_graph(st.dirs, st.day_start, 60, 0.0)
     with pytest.raises(B.SAError):
         B.direction_graph(st.dirs, st.day_start, 60, 91.0)
+
+
+def test_binding_reaches_every_declared_entry_point():
+    """Every call include/*.h declares has its argument types set in the binding and is
+    used by it, so each is reachable from Python."""
+    src = open(os.path.join(ROOT, "paper_1907_04435_gb300", "binding.py")).read()
+    missing = [n for n in sorted(declared_symbols())
+               if f"L.{n}" not in src and f"lib().{n}" not in src and f"_lib.{n}" not in src]
+    assert not missing, missing
