@@ -80,24 +80,33 @@ __global__ void k_building_contribution(DevScene sc, const StepConst* __restrict
                                         const double2* __restrict__ poly, int n, double w,
                                         double* __restrict__ casting, double* __restrict__ nearest,
                                         unsigned long long* __restrict__ stats) {
+    // Every lane of a warp stays to the end (the step loop votes across the warp); lanes
+    // past the items, outside the polygon or never shadowed have no step bits.
     const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (item >= R * n_blocks) return;
-    const long long c = item % R;
-    const int bl = (int)(item / R);
+    const bool valid = item < R * n_blocks;
+    const long long c = valid ? item % R : 0;
+    const int bl = valid ? (int)(item / R) : 0;
     const BlockConst& bc = blocks[bl];
-    unsigned long long m = masks[(long long)bc.mask_block * R + c] >> bc.mask_bit;
-    if (bc.K < 64) m &= (1ull << bc.K) - 1ull;
-    if (m == 0ull) return;
-    const int ix = (int)(c % nx), iy = (int)(c / nx);
-    float3 o;
-    o.x = __fadd_rn(x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), dx));
-    o.y = __fadd_rn(y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), dx));
-    o.z = 0.f;
-    if (!inside_polygon(poly, n, (double)o.x, (double)o.y)) return;
+    unsigned long long m = 0ull;
+    float3 o = make_float3(0.f, 0.f, 0.f);
+    if (valid) {
+        m = masks[(long long)bc.mask_block * R + c] >> bc.mask_bit;
+        if (bc.K < 64) m &= (1ull << bc.K) - 1ull;
+        const int ix = (int)(c % nx), iy = (int)(c / nx);
+        o.x = __fadd_rn(x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), dx));
+        o.y = __fadd_rn(y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), dx));
+        if (m != 0ull && !inside_polygon(poly, n, (double)o.x, (double)o.y)) m = 0ull;
+    }
     int ids[kMaxCasters];
-    while (m) {
-        const int k = __ffsll((long long)m) - 1;
-        m &= m - 1ull;
+    // The warp walks the steps in order, so the lanes tracing at once share a step: one
+    // sun direction from neighbouring cells, a coherent traversal.
+    for (int k = 0; k < 64; ++k) {
+        const bool mine = (m >> k) & 1ull;
+        if (!__any_sync(0xffffffffu, mine)) {
+            if (!__any_sync(0xffffffffu, (m >> k) != 0ull)) break;
+            continue;
+        }
+        if (!mine) continue;
         const StepConst& s = steps[bc.j0 + k];
         int nh = 0, best = -1;
         float best_t = 3.4e38f;
