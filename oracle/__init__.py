@@ -49,6 +49,9 @@ def lib():
             L.sao_shadow_integral.argtypes = [P, P, i64, P, i64, P, P, i32, f64, P, i32, P, P, ci]
             L.sao_iam.argtypes = [P, P, i64, f32, f32, f32, i32, i32, P, P, P, i32, i32, f64,
                                   i32, i32, P, ci]
+            L.sao_iam_bounds.argtypes = [P, P, i64, f32, f32, f32, i32, i32, P, P, P, i32, i32,
+                                         f64, f64, f64, f64, i32, P, P, ci]
+            L.sao_draw_segment.argtypes = [f64, f64, f64, i32, i32, f64, f64, f64, f64, f64, P]
             L.sao_building_steps.argtypes = [P, P, i64, P, P, i64, P, P, i32, f64, i32, P, P, P,
                                              P, ci]
             _lib = L
@@ -136,9 +139,12 @@ IAM_LINE_SUPERCOVER, IAM_LINE_THIN = 0, 1
 
 
 def iam_bits(tri9, tri_building, grid, dirs, day_start, block_len=0, levels=3,
-             tmin_src=1.0, line_mode=IAM_LINE_THIN, nthreads: int | None = None) -> np.ndarray:
+             tmin_src=1.0, line_mode=IAM_LINE_SUPERCOVER, nthreads: int | None = None) -> np.ndarray:
     """uint8 [R, S]: the inverse-accrual-map bits (Sec. 5) of a ground grid (x0, y0, dx,
-    nx, ny), from L = `levels` source levels traced at both ends of every block."""
+    nx, ny), from L = `levels` source levels traced at both ends of every block.  Each
+    piece of a shadow line marks every closed cell it touches (supercover, the reading
+    kept for the n - 1 pieces of Sec. 5); IAM_LINE_THIN marks one cell per sample along
+    the piece instead (the other reading, kept to show that the tests tell them apart)."""
     tri9, tb, dirs = _f32(tri9), _i32(tri_building), _f32(dirs)
     x0, y0, dx, nx, ny = grid
     j0, K = block_partition(day_start, block_len)
@@ -149,6 +155,44 @@ def iam_bits(tri9, tri_building, grid, dirs, day_start, block_len=0, levels=3,
                        float(tmin_src), int(line_mode), S, _ptr(out), nthreads or default_threads())
     if rc != 0:
         raise RuntimeError(f"sao_iam failed: {rc}")
+    return out
+
+
+def iam_bounds(tri9, tri_building, grid, dirs, day_start, block_len=0, levels=3,
+               tmin_src=1.0, eps_cell=1e-3, eps_src=1e-3, eps_t=1e-3,
+               nthreads: int | None = None):
+    """(must, may) uint8 [R, S]: bounds of the supercover inverse accrual map when its
+    sources and shadow-line ends may move by small amounts -- a hit is certain only if the
+    ray passes eps_src (m) inside its triangle, with t beyond tmin_src + eps_t and fewer
+    than L possible hits within eps_t before it; a piece marks a cell for certain only if
+    it reaches eps_cell (m) inside it.  `may` takes every possible source and every cell
+    reached within eps_cell.  With all tolerances 0 both equal `iam_bits`."""
+    tri9, tb, dirs = _f32(tri9), _i32(tri_building), _f32(dirs)
+    x0, y0, dx, nx, ny = grid
+    j0, K = block_partition(day_start, block_len)
+    S = dirs.shape[0]
+    must = np.zeros((int(nx) * int(ny), S), np.uint8)
+    may = np.zeros_like(must)
+    rc = lib().sao_iam_bounds(_ptr(tri9), _ptr(tb), tri9.shape[0], float(x0), float(y0),
+                              float(dx), int(nx), int(ny), _ptr(dirs), _ptr(j0), _ptr(K),
+                              j0.shape[0], int(levels), float(tmin_src), float(eps_cell),
+                              float(eps_src), float(eps_t), S, _ptr(must), _ptr(may),
+                              nthreads or default_threads())
+    if rc != 0:
+        raise RuntimeError(f"sao_iam_bounds failed: {rc}")
+    return must, may
+
+
+def draw_segment(grid, p, q, eps=0.0) -> np.ndarray:
+    """uint8 [ny, nx]: the cells of grid (x0, y0, dx, nx, ny) that the IAM's supercover
+    drawer marks for the segment p -> q (closed cells; grown by eps > 0 or shrunk by
+    |eps| for eps < 0)."""
+    x0, y0, dx, nx, ny = grid
+    out = np.zeros((int(ny), int(nx)), np.uint8)
+    rc = lib().sao_draw_segment(float(x0), float(y0), float(dx), int(nx), int(ny), float(p[0]),
+                                float(p[1]), float(q[0]), float(q[1]), float(eps), _ptr(out))
+    if rc != 0:
+        raise RuntimeError(f"sao_draw_segment failed: {rc}")
     return out
 
 

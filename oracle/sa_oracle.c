@@ -364,16 +364,21 @@ static void draw_thin(const ogrid* g, double px, double py, double qx, double qy
     }
 }
 
-/* every closed cell touched by the segment P -> Q gets bit k */
-static void draw_segment(const ogrid* g, double px, double py, double qx, double qy,
-                         uint8_t* blk, int32_t K, int32_t k) {
+/* every closed cell touched by the segment P -> Q gets bit k.  With eps != 0 each cell is
+ * taken as its square grown by eps on every side (eps > 0) or shrunk by |eps| (eps < 0):
+ * the first touches every cell a copy of the segment moved by up to eps in x and y can
+ * touch, the second only cells every such copy touches (bounds for rounded endpoints). */
+static void draw_segment_eps(const ogrid* g, double px, double py, double qx, double qy,
+                             double eps, uint8_t* blk, int32_t K, int32_t k) {
     const double ymin = fmin(py, qy), ymax = fmax(py, qy);
-    int64_t iy0 = (int64_t)ceil((ymin - g->y0) / g->dx) - 1;
-    int64_t iy1 = (int64_t)floor((ymax - g->y0) / g->dx);
+    int64_t iy0 = (int64_t)ceil((ymin - eps - g->y0) / g->dx) - 1;
+    int64_t iy1 = (int64_t)floor((ymax + eps - g->y0) / g->dx);
     if (iy0 < 0) iy0 = 0;
     if (iy1 > g->ny - 1) iy1 = g->ny - 1;
     for (int64_t iy = iy0; iy <= iy1; ++iy) {
-        const double b0 = g->y0 + (double)iy * g->dx, b1 = b0 + g->dx;
+        const double c0 = g->y0 + (double)iy * g->dx;
+        const double b0 = c0 - eps, b1 = c0 + g->dx + eps;
+        if (b0 > b1) continue;
         double xa, xb;
         if (py == qy) {
             if (py < b0 || py > b1) continue;
@@ -385,12 +390,27 @@ static void draw_segment(const ogrid* g, double px, double py, double qx, double
             double x1 = px + lo * (qx - px), x2 = px + hi * (qx - px);
             xa = fmin(x1, x2); xb = fmax(x1, x2);
         }
-        int64_t ix0 = (int64_t)ceil((xa - g->x0) / g->dx) - 1;
-        int64_t ix1 = (int64_t)floor((xb - g->x0) / g->dx);
+        int64_t ix0 = (int64_t)ceil((xa - eps - g->x0) / g->dx) - 1;
+        int64_t ix1 = (int64_t)floor((xb + eps - g->x0) / g->dx);
         if (ix0 < 0) ix0 = 0;
         if (ix1 > g->nx - 1) ix1 = g->nx - 1;
         for (int64_t ix = ix0; ix <= ix1; ++ix) set_bit_cell(blk, K, iy * g->nx + ix, k);
     }
+}
+
+static void draw_segment(const ogrid* g, double px, double py, double qx, double qy,
+                         uint8_t* blk, int32_t K, int32_t k) {
+    draw_segment_eps(g, px, py, qx, qy, 0.0, blk, K, k);
+}
+
+/* One segment drawn on its own (for the drawer's pins): out[cell] = 1 on every cell of the
+ * nx x ny grid that draw_segment_eps marks. */
+int sao_draw_segment(double x0, double y0, double dx, int32_t nx, int32_t ny, double px,
+                     double py, double qx, double qy, double eps, uint8_t* out) {
+    if (nx < 0 || ny < 0 || !(dx > 0.0) || !out || fabs(eps) * 2.0 >= dx) return -1;
+    ogrid g = {x0, y0, dx, nx, ny};
+    draw_segment_eps(&g, px, py, qx, qy, eps, out, 1, 0);
+    return 0;
 }
 
 int sao_iam(const float* tri9, const int32_t* tri_building, int64_t T,
@@ -450,6 +470,177 @@ int sao_iam(const float* tri9, const int32_t* tri_building, int64_t T,
     free(blk);
     scene_free(&sc);
     return 0;
+}
+
+/* Clearance of the ray o + t d through triangle tr: the perpendicular distance (metres)
+ * from the ray's line to the nearest of the three edge lines, positive when the ray
+ * passes inside the triangle, negative outside; *t_out is the distance along the ray to
+ * the triangle's plane.  Returns 0 for a zero-area triangle, a triangle seen edge-on, or
+ * an edge parallel to the ray (no clearance is defined then). */
+static int ray_tri_clearance(const double* o, const double* d, const otri* tr, double* margin,
+                             double* t_out) {
+    if (tr->degenerate) return 0;
+    double v[3][3], e[3][3];
+    for (int k = 0; k < 3; ++k) {
+        v[0][k] = tr->v0[k];
+        v[1][k] = tr->v0[k] + tr->e1[k];
+        v[2][k] = tr->v0[k] + tr->e2[k];
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) e[i][k] = v[(i + 1) % 3][k] - v[i][k];
+    double sv[3], nv[3], sum = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        double c[3], w[3];
+        cross3(d, e[i], c);
+        for (int k = 0; k < 3; ++k) w[k] = v[i][k] - o[k];
+        sv[i] = dot3(w, c);
+        nv[i] = sqrt(dot3(c, c));
+        if (nv[i] == 0.0) return 0;
+        sum += sv[i];
+    }
+    if (sum == 0.0) return 0;
+    const double sg = sum > 0.0 ? 1.0 : -1.0;
+    double m = INFINITY;
+    for (int i = 0; i < 3; ++i) m = fmin(m, sg * sv[i] / nv[i]);
+    double n[3], w0[3];
+    cross3(tr->e1, tr->e2, n);
+    const double dn = dot3(d, n);
+    if (dn == 0.0) return 0;
+    for (int k = 0; k < 3; ++k) w0[k] = tr->v0[k] - o[k];
+    *margin = m;
+    *t_out = dot3(w0, n) / dn;
+    return 1;
+}
+
+typedef struct { double t, margin; } ocand;
+
+#define IAM_MAX_CANDIDATES 1024
+
+/* Every triangle the ray may hit within the tolerances: clearance >= -eps_src and plane
+ * distance t > tmin - eps_t; sorted by t.  Returns the count, or -1 if there are more
+ * than `cap`. */
+static int candidate_hits(const oscene* s, const double* o, const double* d, double tmin,
+                          double eps_src, double eps_t, ocand* out, int cap) {
+    int n = 0;
+    for (int32_t g = 0; g < s->G; ++g) {
+        /* the padded box pre-test, widened by eps_src so that near misses are kept */
+        double b[6];
+        for (int k = 0; k < 3; ++k) {
+            b[k] = s->gbox[6 * g + k] - eps_src;
+            b[3 + k] = s->gbox[6 * g + 3 + k] + eps_src;
+        }
+        if (!ray_box(o, d, b)) continue;
+        for (int64_t i = s->goff[g]; i < s->goff[g + 1]; ++i) {
+            double m, t;
+            if (!ray_tri_clearance(o, d, &s->tri[s->gtri[i]], &m, &t)) continue;
+            if (m < -eps_src || !(t > tmin - eps_t)) continue;
+            if (n == cap) return -1;
+            int k = n++;
+            while (k > 0 && out[k - 1].t > t) { out[k] = out[k - 1]; --k; }
+            out[k].t = t;
+            out[k].margin = m;
+        }
+    }
+    return n;
+}
+
+/* Bounds of the inverse accrual map (the supercover reading, as sao_iam with line_mode 0)
+ * under small perturbations of its geometry, for comparing an implementation that rounds
+ * differently (e.g. FP32):
+ *   a hit is SURE if the ray passes at least eps_src inside the triangle and t > tmin_src
+ *   + eps_t, POSSIBLE if it passes no more than eps_src outside and t > tmin_src - eps_t;
+ *   a sure hit is a source for certain if fewer than L possible hits lie before t + eps_t;
+ *   a possible hit may be a source if fewer than L sure hits lie before t - eps_t;
+ *   `must` draws the certain sources' lines on cells shrunk by eps_cell, `may` draws the
+ *   possible sources' lines on cells grown by eps_cell (draw_segment_eps).
+ * An implementation whose sources and shadow-line ends stay within these tolerances of
+ * the FP64 ones sets every bit of `must` and no bit outside `may`.  out arrays are [R, S]
+ * like sao_iam's.  Returns -4 if a ray has more than IAM_MAX_CANDIDATES candidates. */
+int sao_iam_bounds(const float* tri9, const int32_t* tri_building, int64_t T,
+                   float x0, float y0, float dx, int32_t nx, int32_t ny,
+                   const float* dirs, const int32_t* block_j0, const int32_t* block_K,
+                   int32_t n_blocks, int32_t L, double tmin_src, double eps_cell, double eps_src,
+                   double eps_t, int32_t S, uint8_t* must, uint8_t* may, int nthreads) {
+    if (T < 0 || nx < 0 || ny < 0 || L < 1 || L > 16 || n_blocks < 0) return -1;
+    if (eps_cell < 0.0 || eps_src < 0.0 || eps_t < 0.0 || 2.0 * eps_cell >= (double)dx) return -1;
+    oscene sc;
+    if (scene_init(&sc, tri9, tri_building, T) != 0) { scene_free(&sc); return -3; }
+    set_threads(nthreads);
+    const int64_t R = (int64_t)nx * ny;
+    ogrid g = {(double)x0, (double)y0, (double)dx, nx, ny};
+    int32_t Kmax = 1;
+    for (int32_t b = 0; b < n_blocks; ++b) if (block_K[b] > Kmax) Kmax = block_K[b];
+    uint8_t* bm = (uint8_t*)malloc((size_t)(R > 0 ? R : 1) * (size_t)Kmax);
+    uint8_t* bp = (uint8_t*)malloc((size_t)(R > 0 ? R : 1) * (size_t)Kmax);
+    if (!bm || !bp) { free(bm); free(bp); scene_free(&sc); return -3; }
+    int overflow = 0;
+    for (int32_t b = 0; b < n_blocks; ++b) {
+        const int32_t j0 = block_j0[b], K = block_K[b];
+        memset(bm, 0, (size_t)R * (size_t)K);
+        memset(bp, 0, (size_t)R * (size_t)K);
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t r = 0; r < R; ++r) {
+            const int64_t ix = r % nx, iy = r / nx;
+            const float cxf = x0 + ((float)ix + 0.5f) * dx;
+            const float cyf = y0 + ((float)iy + 0.5f) * dx;
+            const double o[3] = {(double)cxf, (double)cyf, 0.0};
+            ocand c[IAM_MAX_CANDIDATES];
+            for (int dir = 0; dir < 2; ++dir) {
+                const int32_t js = dir == 0 ? j0 : j0 + K - 1;
+                double d[3] = {dirs[3 * js], dirs[3 * js + 1], dirs[3 * js + 2]};
+                const int n = candidate_hits(&sc, o, d, tmin_src, eps_src, eps_t, c,
+                                             IAM_MAX_CANDIDATES);
+                if (n < 0) {
+#pragma omp atomic write
+                    overflow = 1;
+                    continue;
+                }
+                for (int h = 0; h < n; ++h) {
+                    const int sure = c[h].margin >= eps_src && c[h].t > tmin_src + eps_t;
+                    int before_possible = 0, before_sure = 0;
+                    for (int q = 0; q < n; ++q) {
+                        if (q == h) continue;
+                        if (c[q].t < c[h].t + eps_t) ++before_possible;
+                        if (c[q].t < c[h].t - eps_t && c[q].margin >= eps_src &&
+                            c[q].t > tmin_src + eps_t) ++before_sure;
+                    }
+                    const int certain = sure && before_possible < L;
+                    const int maybe = before_sure < L;
+                    if (!certain && !maybe) continue;
+                    const double s[3] = {o[0] + c[h].t * d[0], o[1] + c[h].t * d[1], o[2] + c[h].t * d[2]};
+                    double qx[64], qy[64];
+                    for (int32_t k = 0; k < K; ++k) {
+                        const double dk[3] = {dirs[3 * (j0 + k)], dirs[3 * (j0 + k) + 1], dirs[3 * (j0 + k) + 2]};
+                        qx[k] = s[0] - s[2] * dk[0] / dk[2];
+                        qy[k] = s[1] - s[2] * dk[1] / dk[2];
+                    }
+                    for (int pass = 0; pass < 2; ++pass) {
+                        if (pass == 0 && !certain) continue;
+                        if (pass == 1 && !maybe) continue;
+                        uint8_t* blk = pass == 0 ? bm : bp;
+                        const double e = pass == 0 ? -eps_cell : eps_cell;
+                        if (dir == 0) {
+                            for (int32_t k = 0; k + 1 < K; ++k)
+                                draw_segment_eps(&g, qx[k], qy[k], qx[k + 1], qy[k + 1], e, blk, K, k);
+                            draw_segment_eps(&g, qx[K - 1], qy[K - 1], qx[K - 1], qy[K - 1], e, blk, K, K - 1);
+                        } else {
+                            for (int32_t k = K - 1; k >= 1; --k)
+                                draw_segment_eps(&g, qx[k], qy[k], qx[k - 1], qy[k - 1], e, blk, K, k);
+                            draw_segment_eps(&g, qx[0], qy[0], qx[0], qy[0], e, blk, K, 0);
+                        }
+                    }
+                }
+            }
+        }
+        for (int64_t r = 0; r < R; ++r)
+            for (int32_t k = 0; k < K; ++k) {
+                must[r * S + j0 + k] = bm[r * K + k];
+                may[r * S + j0 + k] = bp[r * K + k];
+            }
+    }
+    free(bm); free(bp);
+    scene_free(&sc);
+    return overflow ? -4 : 0;
 }
 
 /* ------------------------------------------------------------------------------------

@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import oracle
-from parity import EPS_RAD, assert_counts_parity, workload
+from parity import EPS_RAD, assert_counts_parity, block_sizes, unpack_masks, workload
 from synth import configs
 
 pytestmark = pytest.mark.gpu
@@ -83,8 +83,9 @@ def test_linear_motion_error_against_the_exact_table(cuda_lib, doy):
 
 
 def test_paper_mode_iam_matches_its_restatement(cuda_lib):
-    """The inverse accrual map (Sec. 5) on the interpolated table: the bar of its own
-    parity test (FP32 line ends graze cells at corners: under 0.1 % of the bits differ)."""
+    """The inverse accrual map (Sec. 5) on the interpolated table, held to the bar of its
+    own parity test: every bit the FP64 supercover map sets for certain is set, none
+    outside what it may set within 1 mm of a cell edge, a triangle edge or another source."""
     B = cuda_lib
     w = configs.district_small(dx=1.0, nx=240, ny=180, step=2.0, t0=10.0, t1=15.0)
     g = w.ground
@@ -92,7 +93,10 @@ def test_paper_mode_iam_matches_its_restatement(cuda_lib):
     grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
     masks = B.sa_shadow_masks(scene, grid, sun, "iam", 3)
     torch.cuda.synchronize()
-    gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start, 0))
-    ob = oracle.iam_bits(w.mesh.tri9(), w.mesh.tri_building, (g.x0, g.y0, g.dx, g.nx, g.ny),
-                         odirs, w.sun.day_start, levels=3)
-    assert (gb != ob).mean() < 1e-3
+    gb = unpack_masks(masks, block_sizes(w.sun.day_start, 0))
+    must, may = oracle.iam_bounds(w.mesh.tri9(), w.mesh.tri_building, (g.x0, g.y0, g.dx, g.nx, g.ny),
+                                  odirs, w.sun.day_start, levels=3, eps_cell=1e-3, eps_src=1e-3,
+                                  eps_t=1e-3)
+    assert not ((must == 1) & (gb == 0)).any()
+    assert not ((may == 0) & (gb == 1)).any()
+    assert (may != must).mean() < 1e-3

@@ -144,3 +144,111 @@ def test_the_100_cm_rule_behind_a_thin_low_wall():
     assert near_only.sum() > 50 and far.sum() > 50
     assert not iam[near_only].any()
     assert iam[far].all()
+
+
+# ------------------------------------------------------------- the supercover drawer
+def _cells(a):
+    return set(map(tuple, np.argwhere(a)[:, ::-1].tolist()))       # (ix, iy)
+
+
+def test_supercover_drawer_at_corners_and_edges():
+    """Cells are closed squares: a diagonal through a cell corner touches the four cells
+    around it; a segment along a cell edge touches the rows (or columns) on both sides; a
+    point on a corner touches four cells, inside a cell one."""
+    g = (0.0, 0.0, 1.0, 6, 6)
+    assert _cells(oracle.draw_segment(g, (0.5, 0.5), (1.5, 1.5))) == {(0, 0), (1, 0), (0, 1), (1, 1)}
+    assert _cells(oracle.draw_segment(g, (0.5, 2.0), (2.5, 2.0))) == \
+        {(0, 1), (1, 1), (2, 1), (0, 2), (1, 2), (2, 2)}
+    assert _cells(oracle.draw_segment(g, (3.0, 0.25), (3.0, 1.75))) == {(2, 0), (3, 0), (2, 1), (3, 1)}
+    assert _cells(oracle.draw_segment(g, (2.0, 4.0), (2.0, 4.0))) == {(1, 3), (2, 3), (1, 4), (2, 4)}
+    assert _cells(oracle.draw_segment(g, (2.5, 4.5), (2.5, 4.5))) == {(2, 4)}
+    # a shallow line crosses cells a one-sample-per-cell line steps over
+    assert _cells(oracle.draw_segment(g, (0.1, 0.1), (3.9, 1.3))) == \
+        {(0, 0), (1, 0), (2, 0), (2, 1), (3, 1)}
+    # clipped at the grid: nothing outside, nothing for a segment that misses it
+    assert _cells(oracle.draw_segment(g, (-3.0, -3.0), (0.5, 0.5))) == {(0, 0)}
+    assert not oracle.draw_segment(g, (-3.0, -3.0), (-1.0, 7.0)).any()
+    # shrunk cells lose the corner touches, grown ones gain the near misses
+    assert _cells(oracle.draw_segment(g, (0.5, 0.5), (1.5, 1.5), -1e-6)) == {(0, 0), (1, 1)}
+    assert _cells(oracle.draw_segment(g, (0.5, 1.9999995), (2.5, 1.9999995), 1e-6)) == \
+        {(0, 1), (1, 1), (2, 1), (0, 2), (1, 2), (2, 2)}
+
+
+def _exact_touch(p, q, lo, hi, open_cell):
+    """Does segment p-q meet the square [lo, hi]^2 (closed) or its interior (open)?  Exact
+    rational separating-axis test: the two axes and the segment's normal."""
+    from fractions import Fraction as F
+    px, py, qx, qy = map(F, (p[0], p[1], q[0], q[1]))
+    (ax, ay), (bx, by) = (F(lo[0]), F(lo[1])), (F(hi[0]), F(hi[1]))
+
+    def overlap(a0, a1, b0, b1):            # [a0, a1] against the square's [b0, b1]
+        return (a1 > b0 and a0 < b1) if open_cell else (a1 >= b0 and a0 <= b1)
+    if not overlap(min(px, qx), max(px, qx), ax, bx) or not overlap(min(py, qy), max(py, qy), ay, by):
+        return False
+    nx, ny = qy - py, px - qx
+    if nx == 0 and ny == 0:
+        return True
+    v = nx * px + ny * py
+    side = [nx * x + ny * y - v for x, y in ((ax, ay), (bx, ay), (ax, by), (bx, by))]
+    if open_cell:
+        return min(side) < 0 < max(side)
+    return min(side) <= 0 <= max(side)
+
+
+def test_supercover_drawer_against_exact_intersection():
+    """Random segments with coordinates on a 1/8 m lattice (so that many pass exactly
+    through cell corners and along cell edges) against an exact rational test: every cell
+    whose interior the segment enters is marked, no cell it does not touch is marked, and
+    cells grown by 1e-9 m take every touched cell while shrunk ones take only entered
+    ones."""
+    rng = np.random.default_rng(11)
+    nx = ny = 6
+    g = (0.0, 0.0, 1.0, nx, ny)
+    lattice = np.arange(-8, 8 * 7 + 1) / 8.0
+    for _ in range(400):
+        p = rng.choice(lattice, 2)
+        q = p if rng.random() < 0.1 else rng.choice(lattice, 2)
+        if rng.random() < 0.2:
+            q = np.array([q[0], p[1]])                       # axis-parallel
+        drawn = _cells(oracle.draw_segment(g, p, q))
+        grown = _cells(oracle.draw_segment(g, p, q, 1e-9))
+        shrunk = _cells(oracle.draw_segment(g, p, q, -1e-9))
+        closed = {(i, j) for i in range(nx) for j in range(ny)
+                  if _exact_touch(p, q, (i, j), (i + 1, j + 1), False)}
+        inner = {(i, j) for i in range(nx) for j in range(ny)
+                 if _exact_touch(p, q, (i, j), (i + 1, j + 1), True)}
+        assert inner <= drawn <= closed, (p, q, drawn, closed, inner)
+        assert closed <= grown and shrunk <= inner, (p, q)
+
+
+# ----------------------------------------------------------- bounds of the inverse map
+def _gpu_case():
+    return configs.district_small(dx=1.0, nx=240, ny=180, step=2.0, t0=10.0, t1=15.0)
+
+
+def test_iam_bounds_bracket_the_map():
+    """With zero tolerances both bounds are the map itself; with 1 mm ones the map lies
+    between them and the band they leave is a small fraction of the bits."""
+    w = _gpu_case()
+    g = w.ground
+    args = (w.mesh.tri9(), w.mesh.tri_building, (g.x0, g.y0, g.dx, g.nx, g.ny), w.sun.dirs,
+            w.sun.day_start)
+    sc = oracle.iam_bits(*args, levels=3)
+    m0, M0 = oracle.iam_bounds(*args, levels=3, eps_cell=0.0, eps_src=0.0, eps_t=0.0)
+    assert np.array_equal(m0, sc) and np.array_equal(M0, sc)
+    m, M = oracle.iam_bounds(*args, levels=3, eps_cell=1e-3, eps_src=1e-3, eps_t=1e-3)
+    assert np.all(m <= sc) and np.all(sc <= M)
+    assert 0 < (M != m).mean() < 1e-3
+
+
+def test_thin_lines_fall_outside_the_supercover_bounds():
+    """The GPU test's bar tells the two line readings apart: on its case, the map drawn
+    with thin lines (one cell per sample) leaves unset hundreds of bits the supercover map
+    sets for certain."""
+    w = _gpu_case()
+    g = w.ground
+    args = (w.mesh.tri9(), w.mesh.tri_building, (g.x0, g.y0, g.dx, g.nx, g.ny), w.sun.dirs,
+            w.sun.day_start)
+    thin = oracle.iam_bits(*args, levels=3, line_mode=oracle.IAM_LINE_THIN)
+    m, M = oracle.iam_bounds(*args, levels=3, eps_cell=1e-3, eps_src=1e-3, eps_t=1e-3)
+    assert ((m == 1) & (thin == 0)).sum() > 100
