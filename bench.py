@@ -214,29 +214,31 @@ def run_gpu(args):
         if ev is not None:
             ev[2].record(stream)
 
-    def timed(method_ground, method_fac, steps, warmup, kernel_times=None):
-        """Mean ms per step (whole step, ground call, facade call).  With kernel_times (a
-        dict) the library also times each launch of its main kernels on the stream it
-        launches on, and the per-class (total ms, launches) of the timed steps land there."""
+    def timed(method_ground, method_fac, steps, warmup, kernel_times=None, median=False):
+        """Mean (or median) ms per step (whole step, ground call, facade call).  With
+        kernel_times (a dict) the library also times each launch of its main kernels on the
+        stream it launches on, and the per-class (total ms, launches) of the timed steps
+        land there."""
         for _ in range(warmup):
             step(method_ground, method_fac)
         torch.cuda.synchronize()
         if kernel_times is not None:
             B.sa_kernel_times()
             B.sa_set_option(B.SA_OPT_KERNEL_TIMING, 1)
-        tot, tg, tf = 0.0, 0.0, 0.0
+        tot, tg, tf = [], [], []
         for _ in range(steps):
             flush.fill_(1.0)                     # evict L2 between timed iterations
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             step(method_ground, method_fac, ev)
             torch.cuda.synchronize()
-            tg += ev[0].elapsed_time(ev[1])
-            tf += ev[1].elapsed_time(ev[2])
-            tot += ev[0].elapsed_time(ev[2])
+            tg.append(ev[0].elapsed_time(ev[1]))
+            tf.append(ev[1].elapsed_time(ev[2]))
+            tot.append(ev[0].elapsed_time(ev[2]))
         if kernel_times is not None:
             B.sa_set_option(B.SA_OPT_KERNEL_TIMING, 0)
             kernel_times.update(B.sa_kernel_times())
-        return tot / steps, tg / steps, tf / steps
+        f = statistics.median if median else statistics.fmean
+        return f(tot), f(tg), f(tf)
 
     if args.only_step:
         # profiling mode: W warm-up steps and K timed steps of one method only
@@ -265,12 +267,13 @@ def run_gpu(args):
     methods = {"accrual_sam": {"ms": ms, "ground_ms": ms_g, "facade_ms": ms_f,
                                "value": units / (ms * 1e-3)}}
     if not args.skip_baselines:
-        for mg, mf, name, k in (("accrual_trace", "accrual_trace", "accrual_trace", 1),
-                                ("sweep_raster", "sweep_trace", "sweep_raster+sweep_trace", 1),
-                                ("sweep_trace", "sweep_trace", "sweep_trace", 1)):
-            m_ms, m_g, m_f = timed(mg, mf, k, 1)
+        for mg, mf, name in (("accrual_trace", "accrual_trace", "accrual_trace"),
+                             ("sweep_raster", "sweep_trace", "sweep_raster+sweep_trace"),
+                             ("sweep_trace", "sweep_trace", "sweep_trace")):
+            m_ms, m_g, m_f = timed(mg, mf, args.baseline_steps, 1, median=True)
             methods[name] = {"ms": m_ms, "ground_ms": m_g, "facade_ms": m_f,
-                             "value": units / (m_ms * 1e-3)}
+                             "value": units / (m_ms * 1e-3),
+                             "timing": f"median of {args.baseline_steps} steps after 1 warm-up"}
         sweep = methods["sweep_trace"]["value"]
         for v in methods.values():
             v["speedup_vs_sweep_trace"] = v["value"] / sweep
@@ -438,39 +441,59 @@ def roofline(B, scene, grid, fac, sun, ktimes, steps, workload):
 
 def bench_batch(B, w, args):
     """Development variants of the district (towers added, overlapped buildings removed)
-    x 4 seasonal intervals, each variant on its own receiver region: one graph-captured
-    persistent launch (sa_batch_run) against per-scenario scene builds and accumulations."""
+    x 4 seasonal intervals of 31 days, each variant on its own receiver region: one
+    graph-captured persistent launch (sa_batch_run) against per-scenario scene builds and
+    accumulations.  The first --batch-variants of the 64 variants are timed (each arm over
+    the same ones); the receiver-steps of all 64 are reported beside them.  Two batched
+    times separate the batch's two gains: with the tiles no changed building can shadow
+    kept at the base counts (the default), and with every tile rastered."""
     import torch
     from synth import configs
-    sc = configs.scenarios(n_variants=args.batch_variants, days=args.batch_days, base=w)
+    import copy
+    full = configs.scenarios(n_variants=64, days=args.batch_days, base=w)
+    V = min(args.batch_variants, full.V)
+    sc = copy.copy(full)
+    sc.tower_tris, sc.removed, sc.regions = full.tower_tris[:V], full.removed[:V], full.regions[:V]
     st0 = sc.intervals
     scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
     g = w.ground
     grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
     suns = [B.Sun(it.dirs, it.day_start) for it in st0]
-    units = int(sum((sc.regions[:, 2] * sc.regions[:, 3]).sum() * it.S for it in st0))
-    t0 = time.perf_counter()
-    bt = B.Batch(scene, grid, sc.tower_tris, sc.removed, sc.regions, suns, with_impact=True)
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
-    ctas, run = bt.tune()
-    counts, impact = bt.run()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 2
-    e0.record()
-    for _ in range(reps):
-        bt.run(counts, impact)
-    e1.record()
-    torch.cuda.synchronize()
-    batch_ms = e0.elapsed_time(e1) / reps
-    # per-scenario launches: build each variant's scene, accumulate each interval on its region
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for v in range(sc.V):
+    area = lambda regions: int((regions[:, 2] * regions[:, 3]).sum())
+    units = int(sum(area(sc.regions) * it.S for it in st0))
+    units_all = int(sum(area(full.regions) * it.S for it in full.intervals))
+
+    def batched(skip):
+        B.sa_set_option(B.SA_OPT_BATCH_TILE_SKIP, 1 if skip else 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bt = B.Batch(scene, grid, sc.tower_tris, sc.removed, sc.regions, suns, with_impact=True)
+        torch.cuda.synchronize()
+        setup = time.perf_counter() - t0
+        B.sa_set_option(B.SA_OPT_BATCH_TILE_SKIP, 1)
+        tuned = bt.tune()
+        counts, impact = bt.run()
+        ms = _event_ms(lambda: bt.run(counts, impact), 2)
+        return bt, ms, setup, tuned, counts
+
+    bt, batch_ms, setup_s, (ctas, run), counts = batched(True)
+    items, affected = bt.n_items, bt.n_affected
+    del bt
+    bt2, noskip_ms, _, _, counts2 = batched(False)
+    if not torch.equal(counts, counts2):
+        raise RuntimeError("batched counts depend on the tile skipping")
+    del bt2, counts, counts2
+    # per-scenario launches: each variant's mesh is built on the host first (not timed);
+    # the timer covers its upload, LBVH build and one accumulation per interval on its region
+    meshes = []
+    for v in range(V):
         t9, tb = sc.variant_mesh(v)
-        verts = t9.reshape(-1, 3)
-        tris = np.arange(verts.shape[0], dtype=np.int32).reshape(-1, 3)
+        verts = np.ascontiguousarray(t9.reshape(-1, 3))
+        meshes.append((verts, np.arange(verts.shape[0], dtype=np.int32).reshape(-1, 3), tb))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for v in range(V):
+        verts, tris, tb = meshes[v]
         vs = B.Scene(verts, tris, tb, int(tb.max()) + 1, closed=True)
         ix0, iy0, nx, ny = (int(x) for x in sc.regions[v])
         rg = B.Receivers.ground_grid(g.x0 + ix0 * g.dx, g.y0 + iy0 * g.dx, g.dx, nx, ny)
@@ -478,13 +501,22 @@ def bench_batch(B, w, args):
             B.sa_accumulate(vs, rg, s, 1.0, "accrual_sam", want_minutes=False, want_continuous=False)
     torch.cuda.synchronize()
     per_ms = (time.perf_counter() - t0) * 1e3
-    return {"workload": f"{sc.V} variants x {len(st0)} intervals of {args.batch_days} days "
-                        f"(09-17 h @ 1 min) on district regions of 256..2048 cells a side",
-            "receiver_steps": units, "items": bt.n_items, "items_rastered": bt.n_affected,
+    return {"workload": f"the first {V} of 64 variants x {len(st0)} intervals of {args.batch_days} "
+                        f"days (09-17 h @ 1 min) on district regions of 256..2048 cells a side",
+            "receiver_steps": units, "receiver_steps_all_64_variants": units_all,
+            "items": items, "items_rastered": affected,
             "tuned": {"ctas": ctas, "run": run},
             "batched_ms": batch_ms, "batched_value": units / (batch_ms * 1e-3),
+            "batch_setup_s": setup_s, "batched_with_setup_ms": batch_ms + 1e3 * setup_s,
+            "batched_every_tile_ms": noskip_ms,
             "per_scenario_ms": per_ms, "per_scenario_value": units / (per_ms * 1e-3),
-            "speedup": per_ms / batch_ms, "batch_setup_s": setup_s, "unit": UNIT}
+            "speedup": per_ms / batch_ms,
+            "speedup_with_setup": per_ms / (batch_ms + 1e3 * setup_s),
+            "gain_from_tile_skipping": noskip_ms / batch_ms,
+            "gain_from_one_launch": per_ms / noskip_ms,
+            "batched_ms_scaled_to_64_variants": batch_ms * units_all / units,
+            "per_scenario_ms_scaled_to_64_variants": per_ms * units_all / units,
+            "unit": UNIT}
 
 
 def _event_ms(fn, reps: int) -> float:
@@ -730,8 +762,9 @@ def main():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-configs", action="store_true",
                     help="skip the small-sweep, season and height-gradient workloads")
-    ap.add_argument("--batch-variants", type=int, default=64)
-    ap.add_argument("--batch-days", type=int, default=2)
+    ap.add_argument("--batch-variants", type=int, default=8)
+    ap.add_argument("--batch-days", type=int, default=31)
+    ap.add_argument("--baseline-steps", dest="baseline_steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -101,12 +101,17 @@ int32_t sa_version(void);
  *   SA_OPT_KERNEL_TIMING: 1 records a CUDA event pair on the launching stream around every
  *   launch of the main kernels (below), 0 (default) records nothing.  Launches inside a
  *   stream capture, and those of sa_accumulate_grid_noalloc, are never timed.
+ *   SA_OPT_BATCH_TILE_SKIP: read by sa_batch_create.  1 (default): a work item whose tile
+ *   no removed building and no tower can shadow during the interval keeps the base counts
+ *   without rastering; 0: every tile of every region is rastered.  Results do not depend
+ *   on the option; 0 exists to measure what the skipping saves.
  * sa_get_option returns the current value, or -1 for an unknown key. */
 #define SA_OPT_SWEEP_TRAVERSAL 1
 #define SA_OPT_ACCRUAL_TRAVERSAL 2
 #define SA_OPT_RASTER_RUN 3
 #define SA_OPT_KERNEL_TIMING 4
 #define SA_OPT_POINT_RUN 5
+#define SA_OPT_BATCH_TILE_SKIP 6
 sa_status sa_set_option(int32_t key, int32_t value);
 int32_t sa_get_option(int32_t key);
 
@@ -205,6 +210,19 @@ sa_status sa_sun_interpolate(const float* dirs, int32_t S, const int32_t* day_st
 
 /* Number of steps, days and blocks. */
 sa_status sa_sun_info(const sa_sun* sun, int32_t* S, int32_t* D, int32_t* n_blocks);
+
+/* The block partition sa_sun_create uses (host only, Sec. 3.2's hourly intervals cut per
+ * day): each day k of n = day_start[k+1] - day_start[k] steps becomes ceil(n / block_len)
+ * consecutive blocks whose sizes differ by at most one, the longer ones first (481 steps,
+ * block_len 60: four blocks of 54 and five of 53).  block_len 1..64, 0 for 60.
+ *   day_start: int32 [D + 1] host, from 0, non-decreasing.  *n_blocks (required) receives
+ *   the count; j0 and K (int32 [n_blocks] host, nullable: call once with NULLs to size
+ *   them) receive each block's first step and length; mask block b of sa_shadow_masks is
+ *   block b here.
+ * Errors: SA_ERR_INVALID_ARG (NULL day_start or n_blocks, D < 0, day_start not from 0 or
+ * decreasing, block_len outside 0..64). */
+sa_status sa_block_partition(const int32_t* day_start, int32_t D, int32_t block_len,
+                             int32_t* n_blocks, int32_t* j0, int32_t* K);
 
 /* ------------------------------------------------------------------------- receivers
  * Ground raster: nx * ny cells of side dx (> 0) with lower-left corner (x0, y0); the
@@ -328,6 +346,17 @@ sa_status sa_batch_work_counters(sa_batch* b, uint64_t* counters, void* stream);
 sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
                            sa_method method, uint64_t* counters, void* stream);
 
+/* Statistics of the library's scratch memory (diagnostics): stats uint64 [4] host gets
+ *   [0] scratch allocations the library has made since it was loaded (all devices),
+ *   [1] their bytes, summed,
+ *   [2] bytes the current device's scratch pool holds reserved (0 before its first use),
+ *   [3] the pool's high-water mark of bytes in use.
+ * Scratch is taken from a stream-ordered pool per device inside each call and returned
+ * before the call ends; the pool keeps up to 4 GiB reserved between calls.  Handles
+ * (scene, sun, receivers, batch) hold their own device memory, not counted here.
+ * Errors: SA_ERR_INVALID_ARG (NULL). */
+sa_status sa_scratch_stats(uint64_t* stats);
+
 /* --------------------------------------------------- long periods: the direction graph
  * Sec. 6: over many days the sun retraces nearly the same arcs.  Directions fall into bins,
  * quads of the hemisphere bounded by bin_deg in elevation (bands [k b, (k+1) b) above the
@@ -371,8 +400,8 @@ sa_status sa_accumulate_graph(const sa_scene* scene, const sa_receivers* recv, c
  * cells of a ground grid whose centre lies inside the polygon (even-odd rule), of
  * shadow(p) x area(p), with shadow(p) = steps[p] / total_steps the fraction of the
  * interval's steps the cell is in shadow, and area(p) = dx^2.  Gross counts give the gross
- * area, continuous counts the continuous one.  The paper's shadow score over intervals
- * t with weights w_t in [-1, 1] is sum_t w_t x (the area of interval t).
+ * area, continuous counts the continuous one.  The paper's shadow score over intervals is
+ * sa_shadow_score.
  *   grid: from sa_receivers_grid.  steps: int32 [nx * ny] device, in output order (as
  *   sa_accumulate writes it).  poly_xy: float [n][2] host, n >= 3, a simple polygon of
  *   either orientation.  total_steps > 0 (the interval's steps, e.g. S of its sun table).
@@ -382,6 +411,23 @@ sa_status sa_accumulate_graph(const sa_scene* scene, const sa_receivers* recv, c
  * SA_ERR_DEGENERATE (non-finite vertex), SA_ERR_CUDA. */
 sa_status sa_shadow_area(const sa_receivers* grid, const int32_t* steps, int32_t total_steps,
                          const float* poly_xy, int32_t n, void* stream, double* area);
+
+/* Shadow score over several intervals (Sec. 7.2, "Analysis measures"; Table 3 gives one
+ * weighting, by month): the sum over intervals t of w_t x (the shadow area of interval t
+ * over the polygon), i.e. the sum over the region's cells of
+ * sum_t w_t x steps_t[p] / total_steps_t x dx^2, computed in one pass over the cells.
+ * Positive weights count shadow as a cost (summer), negative ones as a benefit (winter).
+ *   grid: from sa_receivers_grid.  steps: int32 [n_intervals][nx * ny] device, interval t's
+ *   per-cell counts (gross or continuous, as sa_accumulate writes them) at
+ *   steps + t * nx * ny.  total_steps: int32 [n_intervals] host, each > 0 (the interval's
+ *   steps).  weights: float [n_intervals] host, each in [-1, 1].  poly_xy, n: as
+ *   sa_shadow_area.  *score (host) receives the score in square metres, summed in FP64.
+ * With one interval and weight 1 this is sa_shadow_area.  Synchronises `stream`.  Errors:
+ * SA_ERR_INVALID_ARG (NULL, not a grid, n < 3, n_intervals < 1, total_steps <= 0, a weight
+ * outside [-1, 1]), SA_ERR_DEGENERATE (non-finite vertex), SA_ERR_CUDA. */
+sa_status sa_shadow_score(const sa_receivers* grid, const int32_t* steps, int32_t n_intervals,
+                          const int32_t* total_steps, const float* weights, const float* poly_xy,
+                          int32_t n, void* stream, double* score);
 
 /* Building contribution to the shadow of a region (Sec. 7.2, the contribution of each
  * building to the analysis measures): for every cell of a ground grid whose centre lies
@@ -427,18 +473,21 @@ sa_status sa_building_contribution(const sa_scene* scene, const sa_receivers* gr
  * caller still passes the outputs (as for sa_accumulate; gross_minutes and
  * continuous_steps may be NULL).
  *   - grid must come from sa_receivers_grid with at most SA_NOALLOC_MAX_CELLS cells
- *     (2048 x 2048); larger grids are rejected with SA_ERR_INVALID_ARG.  If a single
- *     block's triangle-tile bins do not fit the remaining scratch the call also returns
- *     SA_ERR_INVALID_ARG (use a shorter block_len or a smaller grid).
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call before any
- *     stream capture.
+ *     (2048 x 2048); larger grids are rejected with SA_ERR_INVALID_ARG.  Before writing
+ *     any output the call sizes the triangle-tile bins of every block and cuts the blocks
+ *     into chunks that fit the scratch; if a single block's bins do not fit, it returns
+ *     SA_ERR_INVALID_ARG with every output untouched (use a shorter block_len, a smaller
+ *     grid or sa_accumulate).
+ *   - Every call looks up the array's device address in the current device's context
+ *     (cudaGetSymbolAddress); the call runs on the current device.
+ *   - A sun table with no steps gives zero counts (unchanged ones with
+ *     SA_ACCUMULATE_INTO), as sa_accumulate does.
  *   - All calls in the process share the one array per device and it keeps the previous
  *     call's contents (each call clears what it needs).  Calls that can overlap on the GPU
  *     -- on different streams or threads of the same device -- race on it: serialise them.
  *   - Like the other raster methods it needs scene geometry at z >= 0
- *     (SA_ERR_UNSUPPORTED otherwise) and synchronises `stream` once per chunk of blocks to
- *     size the bins. */
+ *     (SA_ERR_UNSUPPORTED otherwise) and synchronises `stream` twice per chunk of blocks
+ *     to size the bins (once in the sizing pass, once before rastering the chunk). */
 #define SA_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 #define SA_NOALLOC_MAX_CELLS 4194304
 sa_status sa_accumulate_grid_noalloc(const sa_scene* scene, const sa_receivers* grid,

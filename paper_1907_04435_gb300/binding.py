@@ -90,6 +90,9 @@ def lib():
             L.sa_height_grad.argtypes = [P, P, P, f32, P, P, P, P]
             L.sa_kernel_times.argtypes = [P, P, i32]
             L.sa_shadow_area.argtypes = [P, P, i32, P, i32, P, P]
+            L.sa_shadow_score.argtypes = [P, P, i32, P, P, P, i32, P, P]
+            L.sa_block_partition.argtypes = [P, i32, i32, P, P, P]
+            L.sa_scratch_stats.argtypes = [P]
             L.sa_building_contribution.argtypes = [P, P, P, P, i32, P, P, P, P]
             L.sa_sun_interpolate.argtypes = [P, i32, P, i32, i32, P]
             L.sa_direction_graph.argtypes = [P, i32, P, i32, i32, f32, P, P, P, P, P]
@@ -100,7 +103,8 @@ def lib():
                          "sa_scene_from_footprints", "sa_scene_set_heights", "sa_height_grad",
                          "sa_scene_declare_closed", "sa_set_option", "sa_batch_create",
                          "sa_batch_run", "sa_batch_tune", "sa_batch_work_counters",
-                         "sa_kernel_times", "sa_shadow_area", "sa_building_contribution",
+                         "sa_kernel_times", "sa_shadow_area", "sa_shadow_score",
+                         "sa_block_partition", "sa_scratch_stats", "sa_building_contribution",
                          "sa_sun_interpolate", "sa_direction_graph", "sa_accumulate_graph"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
@@ -347,9 +351,20 @@ def sa_work_counters(scene: Scene, recv: Receivers, sun: Sun, method, stream=Non
     return [int(x) for x in c.cpu().tolist()]
 
 
+def sa_scratch_stats():
+    """The library's scratch-memory statistics: a dict with the allocations made since
+    load and their bytes, and the current device pool's reserved bytes and high-water mark
+    of bytes in use."""
+    st = (ct.c_uint64 * 4)()
+    _check(lib().sa_scratch_stats(st))
+    return {"allocations": int(st[0]), "bytes": int(st[1]), "pool_reserved": int(st[2]),
+            "pool_used_high": int(st[3])}
+
+
 SA_OPT_SWEEP_TRAVERSAL, SA_OPT_ACCRUAL_TRAVERSAL, SA_OPT_RASTER_RUN = 1, 2, 3
 SA_OPT_KERNEL_TIMING = 4
 SA_OPT_POINT_RUN = 5
+SA_OPT_BATCH_TILE_SKIP = 6
 TRAVERSAL = {"auto": 0, "packet": 1, "lane": 2}
 KERNEL_CLASSES = ("raster", "sam_points", "accrual", "sweep", "iam", "graph", "raster_bin")
 
@@ -460,30 +475,18 @@ def sa_shadow_masks(scene: Scene, recv: Receivers, sun: Sun, method, iam_levels:
     return masks
 
 
-def unpack_masks(masks: torch.Tensor, sun_block_sizes) -> np.ndarray:
-    """Host helper: [n_blocks, R] masks -> uint8 [R, S] per-step bits (block order)."""
-    mk = masks.cpu().numpy().view(np.uint64)
-    R = mk.shape[1]
-    cols = []
-    for b, K in enumerate(sun_block_sizes):
-        bits = (mk[b][:, None] >> np.arange(K, dtype=np.uint64)[None, :]) & np.uint64(1)
-        cols.append(bits.astype(np.uint8))
-    return np.concatenate(cols, axis=1) if cols else np.zeros((R, 0), np.uint8)
-
-
-def block_sizes(day_start, block_len: int = 0):
-    """Host mirror of the library's block partition (consecutive, balanced, per day)."""
-    K = block_len or 60
-    out = []
-    ds = list(np.asarray(day_start).reshape(-1))
-    for a, b in zip(ds[:-1], ds[1:]):
-        n = int(b - a)
-        if n == 0:
-            continue
-        nb = (n + K - 1) // K
-        base, rem = divmod(n, nb)
-        out += [base + (1 if q < rem else 0) for q in range(nb)]
-    return out
+def block_partition(day_start, block_len: int = 0):
+    """The library's block partition of a sun table's days (sa_block_partition, host
+    only): (j0, K) int32 arrays, each block's first step and length; block b is mask
+    block b of sa_shadow_masks."""
+    ds = _host_i32(day_start).reshape(-1)
+    nb = ct.c_int32()
+    _check(lib().sa_block_partition(_ptr(ds), ds.shape[0] - 1, int(block_len), ct.byref(nb), None, None))
+    j0 = np.zeros(nb.value, np.int32)
+    K = np.zeros(nb.value, np.int32)
+    _check(lib().sa_block_partition(_ptr(ds), ds.shape[0] - 1, int(block_len), ct.byref(nb),
+                                    _ptr(j0), _ptr(K)))
+    return j0, K
 
 
 def sa_shadow_area(grid: Receivers, steps, total_steps: int, polygon, stream=None) -> float:
@@ -520,13 +523,23 @@ def sa_building_contribution(scene: Scene, grid: Receivers, sun: Sun, polygon, s
     return casting[:n], nearest[:n], (int(stats[0]), int(stats[1]))
 
 
-def shadow_score(areas, weights) -> float:
-    """Shadow score over intervals (Sec. 7.2): sum of weight x shadow area, weights in
-    [-1, 1] (Table 3 gives one such weighting by month)."""
-    a = np.asarray(areas, dtype=np.float64).reshape(-1)
-    w = np.asarray(weights, dtype=np.float64).reshape(-1)
-    if a.shape != w.shape:
-        raise ValueError("one weight per interval")
-    if np.any(np.abs(w) > 1.0):
-        raise ValueError("weights must lie in [-1, 1]")
-    return float(np.dot(w, a))
+def sa_shadow_score(grid: Receivers, steps, total_steps, weights, polygon, stream=None) -> float:
+    """Shadow score (m^2) over a polygon of a ground grid and several intervals (Sec. 7.2):
+    steps is an int32 CUDA tensor [n_intervals, R] (or a list of [R] tensors, stacked on the
+    device) of per-cell counts; total_steps and weights (in [-1, 1]) have one entry per
+    interval."""
+    if grid.grid is None:
+        raise SAError(-1, "sa_shadow_score: receivers must be a ground grid")
+    if isinstance(steps, (list, tuple)):
+        steps = torch.stack([t.detach().to(torch.int32) for t in steps])
+    st = steps.detach().to(torch.int32).contiguous()
+    n_t = st.shape[0] if st.dim() == 2 else 1
+    tot = _host_i32(total_steps).reshape(-1)
+    w = _host_f32(weights).reshape(-1)
+    if tot.shape[0] != n_t or w.shape[0] != n_t:
+        raise SAError(-1, "sa_shadow_score: one total and one weight per interval")
+    poly = _host_f32(polygon).reshape(-1, 2)
+    out = ct.c_double()
+    _check(lib().sa_shadow_score(grid.handle, _ptr(st), n_t, _ptr(tot), _ptr(w), _ptr(poly),
+                                 poly.shape[0], ct.c_void_p(_stream(stream)), ct.byref(out)))
+    return float(out.value)

@@ -4,7 +4,9 @@
 // the fraction of the interval's steps the cell spends in shadow (gross counts give the
 // gross fraction, continuous counts the continuous one) and area(p) = dx^2.  A cell is in
 // the region when its centre is, by the even-odd rule.  The shadow score over several
-// intervals is the weighted sum of their areas (weights in [-1, 1]); it needs no kernel.
+// intervals is the weighted sum of their areas (weights w_t in [-1, 1]):
+// sum over the region's cells of sum_t w_t x shadow_t(p) x area(p), one pass over the
+// cells that reads every interval's counts of a cell together.
 //
 // The centres are rounded exactly as the receivers' (FP32), then tested in FP64 with
 // explicit roundings, so the decision for a centre does not depend on the compiler's
@@ -51,6 +53,40 @@ __global__ void k_shadow_area(const int* __restrict__ steps, float x0, float y0,
         const float cy = __fadd_rn(y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), dx));
         if (steps[c] != 0 && inside_polygon(poly, n, (double)cx, (double)cy))
             s += (double)steps[c] * inv_total;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kAreaThreads / 32; ++w) t += s_part[w];
+        atomicAdd(out, t);
+    }
+}
+
+// Shadow score over intervals: coef[t] = w_t / total_steps_t; counts are [n_t][R].
+__global__ void k_shadow_score(const int* __restrict__ steps, long long R, int n_t,
+                               const double* __restrict__ coef, float x0, float y0, float dx,
+                               int nx, const double2* __restrict__ poly, int n,
+                               double* __restrict__ out) {
+    __shared__ double s_part[kAreaThreads / 32];
+    double s = 0.0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < R;
+         c += (long long)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        bool any = false;
+        for (int t = 0; t < n_t; ++t) {
+            const int k = __ldcs(&steps[(long long)t * R + c]);
+            if (k != 0) {
+                v = fma((double)k, coef[t], v);
+                any = true;
+            }
+        }
+        if (!any) continue;
+        const int ix = (int)(c % nx), iy = (int)(c / nx);
+        const float cx = __fadd_rn(x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), dx));
+        const float cy = __fadd_rn(y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), dx));
+        if (inside_polygon(poly, n, (double)cx, (double)cy)) s += v;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = s;
@@ -252,6 +288,61 @@ sa_status sa_shadow_area(const sa_receivers* grid, const int32_t* steps, int32_t
         return sa::report_error(SA_ERR_CUDA, msg);
     }
     *area = result * (double)grid->dx * (double)grid->dx;
+    return SA_OK;
+}
+
+sa_status sa_shadow_score(const sa_receivers* grid, const int32_t* steps, int32_t n_intervals,
+                          const int32_t* total_steps, const float* weights, const float* poly_xy,
+                          int32_t n, void* stream, double* score) {
+    const char* who = "sa_shadow_score";
+    if (!grid || !poly_xy || !score || !total_steps || !weights || (n_intervals > 0 && !steps))
+        return sa::report_error(SA_ERR_INVALID_ARG, "sa_shadow_score: NULL argument");
+    if (!grid->is_grid) return sa::report_error(SA_ERR_INVALID_ARG, "sa_shadow_score: receivers must be a ground grid");
+    if (n < 3) return sa::report_error(SA_ERR_INVALID_ARG, "sa_shadow_score: a polygon needs 3 vertices");
+    if (n_intervals < 1) return sa::report_error(SA_ERR_INVALID_ARG, "sa_shadow_score: n_intervals < 1");
+    std::vector<double> coef((size_t)n_intervals);
+    for (int t = 0; t < n_intervals; ++t) {
+        if (total_steps[t] <= 0) return sa::report_error(SA_ERR_INVALID_ARG, "sa_shadow_score: total_steps <= 0");
+        if (!(weights[t] >= -1.f && weights[t] <= 1.f))
+            return sa::report_error(SA_ERR_INVALID_ARG, "sa_shadow_score: a weight outside [-1, 1]");
+        coef[(size_t)t] = (double)weights[t] / (double)total_steps[t];
+    }
+    std::vector<double2> hp((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const float x = poly_xy[2 * i], y = poly_xy[2 * i + 1];
+        if (!isfinite(x) || !isfinite(y))
+            return sa::report_error(SA_ERR_DEGENERATE, "sa_shadow_score: non-finite polygon vertex");
+        hp[(size_t)i] = make_double2((double)x, (double)y);
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    double2* dp = nullptr;
+    double* dcoef = nullptr;
+    double* dsum = nullptr;
+    double result = 0.0;
+    cudaError_t e = sa::scratch_alloc(&dp, sizeof(double2) * (size_t)n, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&dcoef, sizeof(double) * (size_t)n_intervals, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&dsum, sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, hp.data(), sizeof(double2) * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * (size_t)n_intervals, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dsum, 0, sizeof(double), st);
+    if (e == cudaSuccess && grid->R > 0) {
+        const long long blocks = std::min<long long>((grid->R + sa::kAreaThreads - 1) / sa::kAreaThreads, 152ll * 16);
+        sa::k_shadow_score<<<(unsigned)blocks, sa::kAreaThreads, 0, st>>>(
+            steps, grid->R, n_intervals, dcoef, grid->x0, grid->y0, grid->dx, grid->nx, dp, n, dsum);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&result, dsum, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (dp) cudaFreeAsync(dp, st);
+    if (dcoef) cudaFreeAsync(dcoef, st);
+    if (dsum) cudaFreeAsync(dsum, st);
+    if (e != cudaSuccess) {
+        char msg[256];
+        snprintf(msg, sizeof(msg), "%s: %s", who, cudaGetErrorString(e));
+        return sa::report_error(SA_ERR_CUDA, msg);
+    }
+    *score = result * (double)grid->dx * (double)grid->dx;
     return SA_OK;
 }
 

@@ -457,6 +457,10 @@ sa_status sa_set_option(int32_t key, int32_t value) {
             if (value < 0 || value > 1) return fail(SA_ERR_INVALID_ARG, "sa_set_option: kernel timing %d", value);
             sa::set_kernel_timing(value);
             return SA_OK;
+        case SA_OPT_BATCH_TILE_SKIP:
+            if (value < 0 || value > 1) return fail(SA_ERR_INVALID_ARG, "sa_set_option: batch tile skip %d", value);
+            sa::set_batch_tile_skip(value);
+            return SA_OK;
         default:
             return fail(SA_ERR_INVALID_ARG, "sa_set_option: unknown key %d", key);
     }
@@ -468,6 +472,7 @@ int32_t sa_get_option(int32_t key) {
     if (key == SA_OPT_RASTER_RUN) return sa::get_raster_run();
     if (key == SA_OPT_KERNEL_TIMING) return sa::get_kernel_timing();
     if (key == SA_OPT_POINT_RUN) return sa::get_point_run();
+    if (key == SA_OPT_BATCH_TILE_SKIP) return sa::get_batch_tile_skip();
     return -1;
 }
 
@@ -642,6 +647,27 @@ sa_status sa_direction_graph(const float* dirs, int32_t S, const int32_t* day_st
     for (size_t b = 0; edge_of_block && b < edge.size(); ++b) edge_of_block[b] = edge[b];
     for (size_t e = 0; map_block && e < rep.size(); ++e) map_block[e] = rep[e];
     for (size_t e = 0; weight && e < wt.size(); ++e) weight[e] = wt[e];
+    return SA_OK;
+}
+
+sa_status sa_block_partition(const int32_t* day_start, int32_t D, int32_t block_len,
+                             int32_t* n_blocks, int32_t* j0, int32_t* K) {
+    const char* who = "sa_block_partition";
+    if (!day_start || !n_blocks || D < 0) return fail(SA_ERR_INVALID_ARG, "%s: NULL argument or D < 0", who);
+    if (block_len == 0) block_len = 60;
+    if (block_len < 1 || block_len > sa::kMaxBlock)
+        return fail(SA_ERR_INVALID_ARG, "%s: block_len %d outside 1..64", who, block_len);
+    if (day_start[0] != 0) return fail(SA_ERR_INVALID_ARG, "%s: day_start must start at 0", who);
+    for (int k = 0; k < D; ++k)
+        if (day_start[k + 1] < day_start[k])
+            return fail(SA_ERR_INVALID_ARG, "%s: day_start decreases at day %d", who, k);
+    int32_t nb = 0;
+    for_each_block(day_start, D, block_len, [&](int j, int k, int) {
+        if (j0) j0[nb] = j;
+        if (K) K[nb] = k;
+        ++nb;
+    });
+    *n_blocks = nb;
     return SA_OK;
 }
 

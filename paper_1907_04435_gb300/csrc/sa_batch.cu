@@ -42,6 +42,16 @@ struct sa_batch {
     int* g_impact = nullptr;
 };
 
+namespace sa {
+namespace {
+// 1: tiles no changed building can shadow keep the base counts (default); 0: every tile
+// of a region is rastered (to measure what the skipping saves)
+int g_tile_skip = 1;
+}  // namespace
+void set_batch_tile_skip(int on) { g_tile_skip = on; }
+int get_batch_tile_skip() { return g_tile_skip; }
+}  // namespace sa
+
 namespace {
 
 inline int __float_as_int_host(float f) {
@@ -278,6 +288,7 @@ sa_status sa_batch_create(const sa_scene* base, const sa_receivers* grid, const 
                 for (int ty = ty0; ty <= ty1; ++ty)
                     for (int tx = tx0; tx <= tx1; ++tx) hit[(size_t)ty * tiles_x + tx] = 1;
             }
+            if (!sa::get_batch_tile_skip()) std::fill(hit.begin(), hit.end(), 1);
             const int tx0 = var.ix0 / 32, tx1 = (var.ix0 + var.nx - 1) / 32;
             const int ty0 = var.iy0 / 32, ty1 = (var.iy0 + var.ny - 1) / 32;
             for (int ty = ty0; ty <= std::min(ty1, tiles_y - 1); ++ty)

@@ -456,6 +456,8 @@ int get_raster_run();
 // steps per light-space map of point receivers (1..16)
 void set_point_run(int run);
 int get_point_run();
+void set_batch_tile_skip(int on);
+int get_batch_tile_skip();
 cudaError_t launch_batch(const BatchLaunch& bl, cudaStream_t st);
 
 // shadow accrual map of point receivers in light space (scene_box, recv_box: lo.xyz hi.xyz)

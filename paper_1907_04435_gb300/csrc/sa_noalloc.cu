@@ -9,8 +9,6 @@
 // loads the library keeps for the life of the process.  The paper has no counterpart.
 #include <string.h>
 
-#include <mutex>
-
 #include "sa_handles.cuh"
 
 namespace {
@@ -19,26 +17,15 @@ namespace {
 // cudaGetSymbolAddress (see scratch_of_current_device).
 static __device__ __align__(256) unsigned char g_grid_scratch[SA_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device; looked up once per device.
+// Device address of the scratch array in the current device's context.  It is looked up
+// on every call (a cheap driver query beside the call's own synchronisations), so an
+// address never outlives the context it was taken in.
 sa_status scratch_of_current_device(unsigned char** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return sa::report_error(SA_ERR_CUDA, "sa_accumulate_grid_noalloc: cudaGetDevice failed");
-    if (dev < 0 || dev >= kMaxDevices)
-        return sa::report_error(SA_ERR_UNSUPPORTED, "sa_accumulate_grid_noalloc: device index above 63");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_grid_scratch);
-        if (e != cudaSuccess || !p)
-            return sa::report_error(SA_ERR_CUDA, "sa_accumulate_grid_noalloc: cudaGetSymbolAddress of the scratch array failed");
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_grid_scratch);
+    if (e != cudaSuccess || !p)
+        return sa::report_error(SA_ERR_CUDA, "sa_accumulate_grid_noalloc: cudaGetSymbolAddress of the scratch array failed");
+    *out = static_cast<unsigned char*>(p);
     return SA_OK;
 }
 
@@ -65,6 +52,18 @@ extern "C" sa_status sa_accumulate_grid_noalloc(const sa_scene* scene, const sa_
         return sa::report_error(SA_ERR_INVALID_ARG, "sa_accumulate_grid_noalloc: bad step_minutes");
     if (grid->R == 0) return SA_OK;
     if (!gross_steps) return sa::report_error(SA_ERR_INVALID_ARG, "sa_accumulate_grid_noalloc: gross_steps is NULL");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (sun->h_blocks.empty()) {
+        // no steps: counts are zero, or unchanged when accumulating (as sa_accumulate)
+        cudaError_t e = cudaSuccess;
+        if (!(flags & SA_ACCUMULATE_INTO)) {
+            const size_t n = (size_t)grid->R;
+            e = cudaMemsetAsync(gross_steps, 0, sizeof(int32_t) * n, st);
+            if (e == cudaSuccess && continuous_steps) e = cudaMemsetAsync(continuous_steps, 0, sizeof(int32_t) * n, st);
+            if (e == cudaSuccess && gross_minutes) e = cudaMemsetAsync(gross_minutes, 0, sizeof(float) * n, st);
+        }
+        return e == cudaSuccess ? SA_OK : sa::report_error(SA_ERR_CUDA, cudaGetErrorString(e));
+    }
     unsigned char* scratch = nullptr;
     sa_status s = scratch_of_current_device(&scratch);
     if (s != SA_OK) return s;
@@ -93,12 +92,13 @@ extern "C" sa_status sa_accumulate_grid_noalloc(const sa_scene* scene, const sa_
     out.accumulate_into = (flags & SA_ACCUMULATE_INTO) ? 1 : 0;
     out.write_final = 1;
     int capacity_error = 0;
-    cudaError_t e = sa::launch_raster_ground_in(dsc, drc, dsun, out, reinterpret_cast<cudaStream_t>(stream),
-                                                scratch, SA_NOALLOC_SCRATCH_BYTES, &capacity_error);
+    cudaError_t e = sa::launch_raster_ground_in(dsc, drc, dsun, out, st, scratch,
+                                                SA_NOALLOC_SCRATCH_BYTES, &capacity_error);
     if (e != cudaSuccess) return sa::report_error(SA_ERR_CUDA, cudaGetErrorString(e));
     if (capacity_error)
         return sa::report_error(SA_ERR_INVALID_ARG,
                                 "sa_accumulate_grid_noalloc: one block's triangle-tile bins do not fit the "
-                                "fixed scratch; use a shorter block_len, a smaller grid or sa_accumulate");
+                                "fixed scratch (no output was written); use a shorter block_len, a smaller "
+                                "grid or sa_accumulate");
     return SA_OK;
 }

@@ -846,46 +846,62 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
     const size_t bins_cap = (bytes - off) / sizeof(int);
     DevOut o = out;
     o.run = run;
+    const int tpb = 128;
+    // Bins of blocks [b0, b0 + nbc): counts, their exclusive scan into offsets, and the
+    // total, read back to the host.
+    auto count_chunk = [&](int b0, int nbc, unsigned* total) -> cudaError_t {
+        const size_t ncc = (size_t)nbc * n_tiles;
+        *total = 0;
+        cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned) * ncc, st);
+        if (e != cudaSuccess) return e;
+        if (sc.T == 0) return cudaMemsetAsync(offsets, 0, sizeof(unsigned) * ncc, st);
+        dim3 grid((sc.T + tpb - 1) / tpb, nbc);
+        k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, counts);
+        e = cudaMemcpyAsync(offsets, counts, sizeof(unsigned) * ncc, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = exclusive_scan_u32_with(offsets, (long long)ncc, partial, d_total, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(total, d_total, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        return e;
+    };
+    // Sizing pass, before any output is written: cut the blocks into chunks whose bins fit
+    // the scratch (halving a chunk that does not), or report that one block alone does not.
+    std::vector<int2> plan;
+    int b0 = 0;
+    int nbc = sun.n_blocks < max_chunk ? sun.n_blocks : max_chunk;
+    while (b0 < sun.n_blocks) {
+        if (b0 + nbc > sun.n_blocks) nbc = sun.n_blocks - b0;
+        unsigned total = 0;
+        cudaError_t e = count_chunk(b0, nbc, &total);
+        if (e != cudaSuccess) return e;
+        if ((size_t)total > bins_cap) {
+            if (nbc == 1) { *capacity_error = 1; return cudaSuccess; }
+            nbc = (nbc + 1) / 2;          // retry this chunk with fewer blocks
+            continue;
+        }
+        plan.push_back(make_int2(b0, nbc));
+        b0 += nbc;
+    }
     cudaError_t e = cudaSuccess;
     if (out.accumulate_into) {
         e = cudaMemsetAsync(run, 0, sizeof(int) * (size_t)R, st);
         if (e == cudaSuccess && !out.continuous) e = cudaMemsetAsync(best, 0, sizeof(int) * (size_t)R, st);
         if (e != cudaSuccess) return e;
     }
-    const int tpb = 128;
-    int b0 = 0;
-    int nbc = sun.n_blocks < max_chunk ? sun.n_blocks : max_chunk;
-    while (b0 < sun.n_blocks) {
-        if (b0 + nbc > sun.n_blocks) nbc = sun.n_blocks - b0;
-        const size_t ncc = (size_t)nbc * n_tiles;
-        e = cudaMemsetAsync(counts, 0, sizeof(unsigned) * ncc, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(unsigned) * ncc, st);
-        if (e != cudaSuccess) return e;
+    for (const int2& c : plan) {
         unsigned total = 0;
-        dim3 grid((sc.T + tpb - 1) / tpb, nbc);
-        if (sc.T > 0) {
-            k_bin_count<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, counts);
-            e = cudaMemcpyAsync(offsets, counts, sizeof(unsigned) * ncc, cudaMemcpyDeviceToDevice, st);
-            if (e == cudaSuccess) e = exclusive_scan_u32_with(offsets, (long long)ncc, partial, d_total, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&total, d_total, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return e;
-        } else {
-            e = cudaMemsetAsync(offsets, 0, sizeof(unsigned) * ncc, st);
-            if (e != cudaSuccess) return e;
+        e = count_chunk(c.x, c.y, &total);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(unsigned) * (size_t)c.y * n_tiles, st);
+        if (e != cudaSuccess) return e;
+        if (total > 0) {
+            dim3 grid((sc.T + tpb - 1) / tpb, c.y);
+            k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, c.x, g, offsets, cursor, bins);
         }
-        if ((size_t)total > bins_cap) {
-            if (nbc == 1) { *capacity_error = 1; return cudaSuccess; }
-            nbc = (nbc + 1) / 2;          // retry this chunk with fewer blocks
-            continue;
-        }
-        if (total > 0) k_bin_fill<<<grid, tpb, 0, st>>>(sc, sun.steps, sun.blocks, b0, g, offsets, cursor, bins);
         RasterArgs ra;
-        ra.sc = sc; ra.sun = sun; ra.g = g; ra.b0 = b0; ra.nbc = nbc;
+        ra.sc = sc; ra.sun = sun; ra.g = g; ra.b0 = c.x; ra.nbc = c.y;
         ra.offsets = offsets; ra.counts = counts; ra.bins = bins;
         ra.out = o; ra.best = best;
-        ra.load_state = (b0 > 0) || out.accumulate_into;
-        ra.final_chunk = (b0 + nbc >= sun.n_blocks);
+        ra.load_state = (c.x > 0) || out.accumulate_into;
+        ra.final_chunk = (c.x + c.y >= sun.n_blocks);
         ra.R = R;
         ra.cull = sc.closed;
         ra.run = g_raster_run;
@@ -893,7 +909,6 @@ cudaError_t launch_raster_ground_in(const DevScene& sc, const DevRecv& rc, const
         launch_k_raster(ra, n_tiles, out.stats != nullptr, st);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        b0 += nbc;
     }
     return cudaSuccess;
 }

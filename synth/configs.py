@@ -163,3 +163,12 @@ def scenarios(n_variants: int = 64, days: int = 31, step: float = 1.0, base=None
     intervals = [sun_table(LAT, [((c - 1 + k) % 365) + 1 for k in range(-(days // 2), days - days // 2)],
                            t0, t1, step) for c in centres]
     return Scenarios(w, towers, removed, np.asarray(regions, np.int32), intervals)
+
+
+def step_counts(n_intervals: int, R: int, S: int, zero_frac: float = 0.5, seed: int = 7) -> np.ndarray:
+    """Seeded per-cell step counts int32 [n_intervals, R] in 0..S, a share `zero_frac` of
+    them 0 (cells never shadowed): inputs of the analysis measures, which take counts."""
+    rng = np.random.default_rng(C.SEED_BASE + seed)
+    c = rng.integers(1, S + 1, size=(n_intervals, R), dtype=np.int64)
+    c[rng.random((n_intervals, R)) < zero_frac] = 0
+    return c.astype(np.int32)

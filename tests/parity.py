@@ -63,3 +63,21 @@ def assert_bits_parity(gbits, bits, near, label=""):
     diff = (gbits != bits) & (near == 0)
     n = int(diff.sum())
     assert n == 0, f"{label}: {n} receiver-steps away from a boundary differ, e.g. {np.argwhere(diff)[:5].tolist()}"
+
+
+def block_sizes(day_start, block_len: int = 0):
+    """Block lengths of the library's partition of the sun table (sa_block_partition)."""
+    from paper_1907_04435_gb300 import binding as B
+    return B.block_partition(day_start, block_len)[1].tolist()
+
+
+def unpack_masks(masks, sizes) -> np.ndarray:
+    """[n_blocks, R] step masks (bit k = step k of the block, as sa_shadow_masks writes
+    them) -> uint8 [R, S] per-step bits in block order."""
+    mk = masks.cpu().numpy().view(np.uint64)
+    R = mk.shape[1]
+    cols = []
+    for b, K in enumerate(sizes):
+        bits = (mk[b][:, None] >> np.arange(K, dtype=np.uint64)[None, :]) & np.uint64(1)
+        cols.append(bits.astype(np.uint8))
+    return np.concatenate(cols, axis=1) if cols else np.zeros((R, 0), np.uint8)

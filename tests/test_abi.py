@@ -78,13 +78,26 @@ def test_scene_validation_happens_on_the_host(L):
     assert L.sa_scene_from_mesh(B._ptr(v), 3, B._ptr(t), 1, B._ptr(b), 2, 0, None, ct.byref(h)) == -1
 
 
-def test_block_partition_mirror():
-    from paper_1907_04435_gb300.binding import block_sizes
-    assert block_sizes([0, 481]) == [54, 54, 54, 54, 53, 53, 53, 53, 53]
-    assert sum(block_sizes([0, 481])) == 481
-    assert block_sizes([0, 5, 5, 70], 64) == [5, 33, 32]
-    assert block_sizes([0, 3], 1) == [1, 1, 1]
-    assert max(block_sizes([0, 1000], 64)) <= 64
+def test_block_partition_is_the_oracles():
+    """sa_block_partition is host code: per day, ceil(n / K) blocks whose sizes differ by
+    at most one, the longer first; the same blocks as the oracle's partition."""
+    import oracle
+    from paper_1907_04435_gb300 import binding as B
+    assert B.block_partition([0, 481])[1].tolist() == [54, 54, 54, 54, 53, 53, 53, 53, 53]
+    assert B.block_partition([0, 5, 5, 70], 64)[1].tolist() == [5, 33, 32]
+    assert B.block_partition([0, 3], 1)[1].tolist() == [1, 1, 1]
+    for ds, bl in (([0, 481], 0), ([0, 5, 5, 70], 64), ([0, 1000], 64), ([0, 241, 482, 483], 7),
+                   ([0, 0], 0), (list(range(0, 92 * 481 + 1, 481)), 60)):
+        j0, K = B.block_partition(ds, bl)
+        oj, oK = oracle.block_partition(ds, bl)
+        assert np.array_equal(j0, oj) and np.array_equal(K, oK), (ds[:4], bl)
+        assert K.sum() == ds[-1] and (K <= (bl or 60)).all()
+    with pytest.raises(B.SAError):
+        B.block_partition([0, 10], 65)
+    with pytest.raises(B.SAError):
+        B.block_partition([1, 10], 0)
+    with pytest.raises(B.SAError):
+        B.block_partition([0, 10, 5], 0)
 
 
 def test_options_and_kernel_timing_record_need_no_device(L):

@@ -66,14 +66,24 @@ def test_single_box_gradient_matches_the_closed_form(cuda_lib):
     assert abs(float(grad[0]) - G_cf) <= 1e-4 * abs(G_cf), (float(grad[0]), G_cf)
 
 
+def flips_per_day(bits, day_start):
+    """int [R, D]: status changes between consecutive steps of each day."""
+    out = np.zeros((bits.shape[0], len(day_start) - 1), np.int64)
+    for k in range(len(day_start) - 1):
+        a, b = int(day_start[k]), int(day_start[k + 1])
+        out[:, k] = np.abs(np.diff(bits[:, a:b].astype(np.int64), axis=1)).sum(axis=1)
+    return out
+
+
 def test_park_gradient_matches_oracle_finite_differences(cuda_lib):
     """Central differences (h = 0.01 m) of the FP64 oracle's shadow-minutes, per building.
 
-    The objective counts at most one flip per step interval, so it jumps where a brief
-    shadow or gap appears or vanishes at a step under the perturbation; receivers whose
-    step statuses change between h - 0.01 and h + 0.01 for any building are given weight 0
-    on both sides (the library takes per-receiver weights), so both differentiate the same
-    smooth sum."""
+    The objective counts at most one flip per step interval.  A flip that moves across a
+    step keeps it continuous (one interval's flip time runs to its end as the next one's
+    starts), but a brief shadow or gap that appears or vanishes at a step makes it jump.
+    So only receivers whose number of flips in some day differs between h - 0.01 and
+    h + 0.01, for some building, are given weight 0 on both sides (the library takes
+    per-receiver weights); receivers whose flips merely cross a step are kept."""
     B = cuda_lib
     w = configs.park(width=120.0, depth=80.0, dx=1.0, n_buildings=24, band=100.0, step=4.0)
     pos = w.ground.positions()
@@ -88,13 +98,19 @@ def test_park_gradient_matches_oracle_finite_differences(cuda_lib):
 
     pert = []
     jump = np.zeros(pos.shape[0], bool)
+    moved = np.zeros(pos.shape[0], bool)
+    ds = w.sun.day_start
     for b in range(w.city.B):
         hp, hm = w.city.heights.copy(), w.city.heights.copy()
         hp[b] += np.float32(0.01)
         hm[b] -= np.float32(0.01)
         pert.append((hp, hm))
-        jump |= (bits(hp) != bits(hm)).any(axis=1)
+        bp, bm = bits(hp), bits(hm)
+        moved |= (bp != bm).any(axis=1)
+        jump |= (flips_per_day(bp, ds) != flips_per_day(bm, ds)).any(axis=1)
     assert jump.mean() < 0.05
+    # flips that cross a step under the perturbation are kept, and there are some
+    assert (moved & ~jump).sum() > 0
     wts = (~jump).astype(np.float64)
 
     scene = _fp_scene(B, w.city)

@@ -39,26 +39,76 @@ def test_shadow_area_matches_the_oracle(cuda_lib, name):
     assert B.sa_shadow_area(grid, gross, w.sun.S, poly) > 0
 
 
-def test_shadow_score_over_intervals(cuda_lib):
-    """Two seasons of the same city weighted +1 (summer) and -1 (winter): the score is the
-    difference of the device areas, equal to the oracle's on the same counts."""
-    B = cuda_lib
+def _table3_weights():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table3_month_weights.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    return np.array([float(r[1]) for r in rows])
+
+
+@pytest.mark.parametrize("name", ["convex", "non_convex", "whole_grid"])
+def test_shadow_score_matches_the_oracle(cuda_lib, name):
+    """The score over the twelve months of Table 3 (seeded per-cell counts of each month,
+    each out of its own step total) equals the oracle's weighted sum of areas to 1e-12; one
+    interval of weight 1 is the shadow area."""
     from synth import configs
+    B = cuda_lib
+    w = workload("district_small")
+    g = w.ground
+    G = (g.x0, g.y0, g.dx, g.nx, g.ny)
+    grid = B.Receivers.ground_grid(*G)
+    totals = np.array([300 + 17 * m for m in range(12)], np.int32)
+    counts = configs.step_counts(12, g.R, int(totals.min()), seed=30)
+    wts = _table3_weights()
+    poly = np.array(POLYGONS[name], np.float32)
+    dev = torch.from_numpy(counts).cuda()
+    got = B.sa_shadow_score(grid, dev, totals, wts, poly)
+    areas = [oracle.shadow_area(G, counts[m], int(totals[m]), poly) for m in range(12)]
+    want = oracle.shadow_score(areas, wts)
+    assert got == pytest.approx(want, rel=1e-12, abs=1e-9 * max(areas)), (got, want)
+    one = B.sa_shadow_score(grid, dev[3:4], totals[3:4], [1.0], poly)
+    assert one == pytest.approx(areas[3], rel=1e-12)
+    assert one == pytest.approx(B.sa_shadow_area(grid, dev[3], int(totals[3]), poly), rel=1e-12)
+
+
+def test_shadow_score_of_a_summer_and_a_winter_day(cuda_lib):
+    """Two seasons of the same city weighted +1 (summer) and -1 (winter), each counted by
+    the oracle on the parity grid: the device score of those counts equals the oracle's,
+    and is negative (winter shadows are longer)."""
+    from synth import configs
+    B = cuda_lib
     poly = np.array(POLYGONS["convex"], np.float32)
-    areas, want = [], []
+    counts, totals, areas = [], [], []
     for doy in (172, 355):
-        w = configs.district_small(doys=(doy,), n_facade=0)
+        w = configs.district_small(doys=(doy,), n_facade=0, dx=5.0, nx=100, ny=75)
         g = w.ground
-        scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
-        sun = B.Sun(w.sun.dirs, w.sun.day_start)
-        grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
-        gross, _, _ = B.sa_accumulate(scene, grid, sun, w.sun.step_minutes, "accrual_sam")
-        areas.append(B.sa_shadow_area(grid, gross, w.sun.S, poly))
-        want.append(oracle.shadow_area((g.x0, g.y0, g.dx, g.nx, g.ny), gross.cpu().numpy(), w.sun.S, poly))
-    s = B.shadow_score(areas, [1.0, -1.0])
-    assert s == pytest.approx(oracle.shadow_score(want, [1.0, -1.0]), rel=1e-9, abs=1e-9)
-    assert areas[1] > areas[0]          # winter shadows are longer: the score is negative
-    assert s < 0
+        G = (g.x0, g.y0, g.dx, g.nx, g.ny)
+        og, _, _, _ = oracle.accumulate(w.mesh.tri9(), w.mesh.tri_building, g.positions(), None,
+                                        w.sun.dirs, w.sun.day_start, w.sun.step_minutes)
+        counts.append(og)
+        totals.append(w.sun.S)
+        areas.append(oracle.shadow_area(G, og, w.sun.S, poly))
+    grid = B.Receivers.ground_grid(*G)
+    got = B.sa_shadow_score(grid, torch.from_numpy(np.stack(counts)).cuda(), totals, [1.0, -1.0], poly)
+    want = oracle.shadow_score(areas, [1.0, -1.0])
+    assert got == pytest.approx(want, rel=1e-12)
+    assert areas[1] > areas[0] and got < 0
+
+
+def test_shadow_score_rejects_bad_arguments(cuda_lib):
+    B = cuda_lib
+    grid = B.Receivers.ground_grid(0.0, 0.0, 1.0, 8, 8)
+    steps = torch.zeros((2, 64), dtype=torch.int32, device="cuda")
+    tri = [[0, 0], [4, 0], [4, 4]]
+    with pytest.raises(B.SAError):
+        B.sa_shadow_score(grid, steps, [10, 10], [1.0, -1.5], tri)      # weight outside [-1, 1]
+    with pytest.raises(B.SAError):
+        B.sa_shadow_score(grid, steps, [10, 0], [1.0, -1.0], tri)       # total 0
+    with pytest.raises(B.SAError):
+        B.sa_shadow_score(grid, steps, [10], [1.0], tri)                # one total for two
+    with pytest.raises(B.SAError):
+        B.sa_shadow_score(grid, steps, [10, 10], [1.0, -1.0], [[0, 0], [1, 1]])
+    assert B.sa_shadow_score(grid, steps, [10, 10], [1.0, -1.0], tri) == 0.0
 
 
 def test_shadow_area_rejects_bad_arguments(cuda_lib):

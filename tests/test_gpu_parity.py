@@ -8,7 +8,8 @@ from synth import city as C
 from synth import configs
 from synth.sun import sun_table
 
-from parity import (assert_bits_parity, assert_counts_parity, cached_oracle, workload)
+from parity import (assert_bits_parity, assert_counts_parity, block_sizes, cached_oracle,
+                    unpack_masks, workload)
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +51,7 @@ def test_boxes16_ground_bits(cuda_lib, method):
     sc, rc, sun = _scene(B, w), _ground(B, w), B.Sun(w.sun.dirs, w.sun.day_start)
     masks = B.sa_shadow_masks(sc, rc, sun, method)
     torch.cuda.synchronize()
-    gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start))
+    gb = unpack_masks(masks, block_sizes(w.sun.day_start))
     assert_bits_parity(gb, bits, near, method)
 
 
@@ -66,7 +67,7 @@ def test_district_small_ground(cuda_lib, method, block_len):
     g, _, c = _run(B, sc, rc, sun, method)
     assert_counts_parity(g, c, bits, near, w.sun.day_start, f"{method}/K{block_len}")
     masks = B.sa_shadow_masks(sc, rc, sun, method)
-    gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start, block_len))
+    gb = unpack_masks(masks, block_sizes(w.sun.day_start, block_len))
     assert_bits_parity(gb, bits, near, f"{method}/K{block_len}")
 
 
@@ -81,7 +82,7 @@ def test_district_small_facades(cuda_lib, method):
     g, _, c = _run(B, sc, rc, sun, method)
     assert_counts_parity(g, c, bits, near, w.sun.day_start, method)
     masks = B.sa_shadow_masks(sc, rc, sun, method)
-    gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start))
+    gb = unpack_masks(masks, block_sizes(w.sun.day_start))
     assert_bits_parity(gb, bits, near, method)
 
 
@@ -198,7 +199,7 @@ def test_traversal_modes_give_the_same_parity(cuda_lib, mode, method):
                          ("facade", B.Receivers.points(w.facade_pos, w.facade_nrm))):
             bits, near = cached_oracle(f"district_small/{part}", w, part)
             masks = B.sa_shadow_masks(sc, rc, sun, method)
-            gb = B.unpack_masks(masks, B.block_sizes(w.sun.day_start))
+            gb = unpack_masks(masks, block_sizes(w.sun.day_start))
             assert_bits_parity(gb, bits, near, f"{method}/{mode}/{part}")
     finally:
         B.sa_set_option(key, 0)
@@ -217,7 +218,7 @@ def test_closed_scene_rasters_only_sun_facing_faces(cuda_lib, block_len):
     a = B.sa_shadow_masks(sc, rc, sun, "accrual_sam")
     b = B.sa_shadow_masks(sc, rc, sun, "sweep_raster")
     assert torch.equal(a, b)
-    gb = B.unpack_masks(a, B.block_sizes(w.sun.day_start, block_len))
+    gb = unpack_masks(a, block_sizes(w.sun.day_start, block_len))
     assert_bits_parity(gb, bits, near, f"closed/K{block_len}")
     g, _, c = _run(B, sc, rc, sun, "accrual_sam")
     assert_counts_parity(g, c, bits, near, w.sun.day_start, "closed")
@@ -236,7 +237,7 @@ def test_facade_sam_multi_day_and_progressive(cuda_lib):
     g, _, c = _run(B, sc, rc, sun, "accrual_sam", 8.0)
     assert_counts_parity(g, c, bits, near, ds, "facade sam")
     masks = B.sa_shadow_masks(sc, rc, sun, "accrual_sam")
-    assert_bits_parity(B.unpack_masks(masks, B.block_sizes(ds, 7)), bits, near, "facade sam bits")
+    assert_bits_parity(unpack_masks(masks, block_sizes(ds, 7)), bits, near, "facade sam bits")
     gacc = torch.zeros(rc.R, dtype=torch.int32, device="cuda")
     cacc = torch.zeros(rc.R, dtype=torch.int32, device="cuda")
     for k in range(len(ds) - 1):
@@ -245,10 +246,14 @@ def test_facade_sam_multi_day_and_progressive(cuda_lib):
         B.sa_accumulate(sc, rc, sun_k, 8.0, "accrual_sam", accumulate_into=True, gross=gacc,
                         continuous=cacc, want_minutes=False)
     assert np.array_equal(gacc.cpu().numpy(), g) and np.array_equal(cacc.cpu().numpy(), c)
-    # a closed scene gives the same bits
+    # A closed scene tests only the faces turned toward the sun.  A ray that meets a
+    # closed solid crosses one of them, so the bits agree with the open scene's everywhere
+    # except where a ray grazes a silhouette edge, which FP32 may decide either way on the
+    # two face sets: only steps the oracle classes as near a boundary may differ.
     scc = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
-    assert torch.equal(B.sa_shadow_masks(scc, rc, sun, "accrual_sam"), masks) or True
-    mc = B.unpack_masks(B.sa_shadow_masks(scc, rc, sun, "accrual_sam"), B.block_sizes(ds, 7))
+    mc = unpack_masks(B.sa_shadow_masks(scc, rc, sun, "accrual_sam"), block_sizes(ds, 7))
+    mo = unpack_masks(masks, block_sizes(ds, 7))
+    assert_bits_parity(mc, mo, near, "facade sam closed vs open")
     assert_bits_parity(mc, bits, near, "facade sam closed")
 
 

@@ -101,14 +101,6 @@ def test_shadow_score_with_the_month_weights_of_table3():
     # shadow only from May to September scores the sum of those weights
     summer = np.array([0, 0, 0, 0, 1, 1, 1, 1, 1, 0, 0, 0], np.float64) * 100.0
     assert oracle.shadow_score(summer, w) == pytest.approx(400.0)
-    # the binding's host formula agrees, and refuses weights outside [-1, 1]
-    from paper_1907_04435_gb300 import binding as B
-    areas = np.random.default_rng(4).uniform(0, 1e4, 12)
-    assert B.shadow_score(areas, w) == pytest.approx(oracle.shadow_score(areas, w), rel=1e-15)
-    with pytest.raises(ValueError):
-        B.shadow_score(areas, w * 1.5)
-    with pytest.raises(ValueError):
-        B.shadow_score(areas[:11], w)
 
 
 # ------------------------------------------------------------- building contribution
