@@ -123,7 +123,8 @@ int32_t sa_get_option(int32_t key);
 #define SA_KERNEL_IAM 4          /* inverse accrual map line drawing (Sec. 5) */
 #define SA_KERNEL_GRAPH 5        /* direction graph: edge run summaries and day-path reduce (Sec. 6) */
 #define SA_KERNEL_RASTER_BIN 6   /* triangle binning of the ground raster (count and fill passes) */
-#define SA_KERNEL_CLASSES 7
+#define SA_KERNEL_CONTRIB 7      /* building contribution: fan traversal of the shadowed steps (Sec. 7.2) */
+#define SA_KERNEL_CLASSES 8
 
 /* Collect the timed launches recorded since the last collection: waits for their events,
  * ADDS each launch's duration in milliseconds to ms[class] and 1 to launches[class]
@@ -444,16 +445,20 @@ sa_status sa_shadow_score(const sa_receivers* grid, const int32_t* steps, int32_
  *   scene: any (mesh or footprints); building ids are the ones the scene was built with.
  *   grid: from sa_receivers_grid.  poly_xy: float [n][2] host, n >= 3.
  *   casting, nearest: double [n_buildings] host.  stats: int64 [2] host, nullable:
- *     [0] cell-steps whose ray met more than 32 distinct buildings (those past the 32nd
- *         are not credited in casting; nearest is exact);
+ *     [0] cell-steps whose ray met more than 64 distinct buildings (those past the 64th
+ *         are not credited in casting; nearest is exact); the call then returns
+ *         SA_ERR_UNSUPPORTED, with every output written;
  *     [1] cell-steps the raster marks shadowed whose ray met no triangle beyond t_min in
  *         FP32 (rays that graze a shadow edge), credited to no building.
  * The shadowed steps come from the ground accrual raster (as SA_ACCRUAL_SAM computes
  * them); the call keeps its per-step masks, 8 bytes per cell and block of steps, and
  * rejects with SA_ERR_INVALID_ARG a grid and sun table whose masks exceed 4 GiB (split the
- * interval).  Synchronises `stream`.  Errors: SA_ERR_INVALID_ARG (NULL, not a grid,
- * n < 3), SA_ERR_DEGENERATE (non-finite vertex), SA_ERR_UNSUPPORTED (geometry below
- * z = 0, as for the raster methods), SA_ERR_OOM, SA_ERR_CUDA. */
+ * interval).  The buildings are found by one traversal per cell and run of <= 32 steps,
+ * whose query is the fan of the run's rays (as SA_ACCRUAL_TRACE), testing every triangle
+ * in the fan against the cell's shadowed steps with the exact ray test.  Synchronises
+ * `stream`.  Errors: SA_ERR_INVALID_ARG (NULL, not a grid, n < 3), SA_ERR_DEGENERATE
+ * (non-finite vertex), SA_ERR_UNSUPPORTED (geometry below z = 0, as for the raster
+ * methods; a ray meeting more than 64 buildings, above), SA_ERR_OOM, SA_ERR_CUDA. */
 sa_status sa_building_contribution(const sa_scene* scene, const sa_receivers* grid,
                                    const sa_sun* sun, const float* poly_xy, int32_t n,
                                    void* stream, double* casting, double* nearest,

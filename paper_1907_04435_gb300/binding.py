@@ -366,7 +366,7 @@ SA_OPT_KERNEL_TIMING = 4
 SA_OPT_POINT_RUN = 5
 SA_OPT_BATCH_TILE_SKIP = 6
 TRAVERSAL = {"auto": 0, "packet": 1, "lane": 2}
-KERNEL_CLASSES = ("raster", "sam_points", "accrual", "sweep", "iam", "graph", "raster_bin")
+KERNEL_CLASSES = ("raster", "sam_points", "accrual", "sweep", "iam", "graph", "raster_bin", "contrib")
 
 
 def sa_set_option(key: int, value: int):
@@ -506,7 +506,7 @@ def sa_building_contribution(scene: Scene, grid: Receivers, sun: Sun, polygon, s
     """Per-building shadow over a polygon of a ground grid (Sec. 7.2), in m^2 over the sun
     table's interval: (casting, nearest, stats).  casting[b] is the area building b
     shadows on its own; nearest[b] the area where b is the nearest caster.  stats[0]
-    counts cell-steps that met more than 32 buildings (casting is short for those),
+    counts cell-steps that met more than 64 buildings (the call then raises),
     stats[1] shadowed cell-steps whose ray grazed past every triangle; sum(nearest) plus
     stats[1] x dx^2 / S is the region's gross shadow area."""
     if grid.grid is None:

@@ -98,115 +98,272 @@ __global__ void k_shadow_score(const int* __restrict__ steps, long long R, int n
     }
 }
 
-// Building contribution (Sec. 7.2): for every cell of the region and every step the
-// accrual raster marks as shadowed, one ray toward the sun collects the buildings it meets
-// beyond t_min (all of them, through the whole BVH) and the building of the nearest hit.
-// Each of them is credited dx^2 / total_steps: "casting" sums the shadow each building casts
-// on the region, overlaps counted once per building; "nearest" splits the region's shadow
-// area among the nearest casters, so it sums to the shadow area itself, less the cell-steps
-// the raster marks shadowed whose FP32 ray grazes past every triangle (shadow edges),
-// which are counted apart.
-constexpr int kMaxCasters = 32;
-constexpr int kContribThreads = 128;
+// Building contribution (Sec. 7.2).  For every cell of the region and every step the
+// accrual raster marks as shadowed, the buildings the ray toward the sun meets beyond
+// t_min are found, and each is credited one cell-step: "casting" counts, per building,
+// the cell-steps whose ray meets it (a ray meeting several buildings credits each once);
+// "nearest" counts, per building, the cell-steps whose nearest hit lies on it, so that
+// these partition the region's shadowed cell-steps -- except the ones the raster marks
+// shadowed whose FP32 ray grazes past every triangle (shadow edges), counted apart.
+//
+// One warp takes an 8 x 4 patch of the region's cells and walks, for each run of <= 32
+// consecutive steps of a block, the depth-first node list once with the fan of the run's
+// rays as its query (as the ray-traced accrual does): every triangle in the fan is tested
+// exactly (Plucker form, with its distance) against the lane's shadowed steps it can
+// reach.  Per lane and step the nearest hit (distance, building) is kept in shared
+// memory, and per lane and run a short list of (building, steps met) pairs; a lane whose
+// run meets more buildings than the list holds counts its casting again ray by ray, with
+// a list of kRayList buildings per ray.  Counts are integers, credited by atomics on
+// per-building totals (runs of equal nearest buildings are credited at once).
+constexpr int kContribWarps = 2;
+constexpr int kContribRun = 32;             // steps per fan traversal
+constexpr int kCastList = 16;               // buildings per lane and run in the fan pass
+constexpr int kRayList = 2 * kContribRun;   // buildings per ray in the per-ray recount
 
-__global__ void k_building_contribution(DevScene sc, const StepConst* __restrict__ steps,
-                                        const BlockConst* __restrict__ blocks, int n_blocks,
-                                        const unsigned long long* __restrict__ masks,
-                                        float x0, float y0, float dx, int nx, long long R,
-                                        const double2* __restrict__ poly, int n, double w,
-                                        double* __restrict__ casting, double* __restrict__ nearest,
-                                        unsigned long long* __restrict__ stats) {
-    // Every lane of a warp stays to the end (the step loop votes across the warp); lanes
-    // past the items, outside the polygon or never shadowed have no step bits.
-    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = item < R * n_blocks;
-    const long long c = valid ? item % R : 0;
-    const int bl = valid ? (int)(item / R) : 0;
-    const BlockConst& bc = blocks[bl];
-    unsigned long long m = 0ull;
-    float3 o = make_float3(0.f, 0.f, 0.f);
-    if (valid) {
-        m = masks[(long long)bc.mask_block * R + c] >> bc.mask_bit;
-        if (bc.K < 64) m &= (1ull << bc.K) - 1ull;
-        const int ix = (int)(c % nx), iy = (int)(c / nx);
-        o.x = __fadd_rn(x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), dx));
-        o.y = __fadd_rn(y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), dx));
-        if (m != 0ull && !inside_polygon(poly, n, (double)o.x, (double)o.y)) m = 0ull;
-    }
-    int ids[kMaxCasters];
-    // The warp walks the steps in order, so the lanes tracing at once share a step: one
-    // sun direction from neighbouring cells, a coherent traversal.
-    for (int k = 0; k < 64; ++k) {
-        const bool mine = (m >> k) & 1ull;
-        if (!__any_sync(0xffffffffu, mine)) {
-            if (!__any_sync(0xffffffffu, (m >> k) != 0ull)) break;
-            continue;
-        }
-        if (!mine) continue;
-        const StepConst& s = steps[bc.j0 + k];
-        int nh = 0, best = -1;
-        float best_t = 3.4e38f;
-        bool lost = false;
-        for (int i = 0; i < sc.n_nodes;) {
-            const float4 lo = __ldg(&sc.nodes[2 * i]);
-            const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
+struct ContribArgs {
+    DevScene sc;
+    const StepConst* steps;
+    const BlockConst* runs;           // runs of <= 32 steps; mask_block / mask_bit locate them
+    int n_runs;
+    const unsigned long long* masks;  // the raster's step masks [blocks][R]
+    long long R;
+    float x0, y0, dx;
+    int nx;
+    int bx0, by0, bnx, bny;           // the region's bounding box, in cells
+    const double2* poly;
+    int n;
+    unsigned long long* cast_cnt;     // [B]
+    unsigned long long* near_cnt;     // [B]
+    unsigned long long* stats;        // [2]
+};
+
+struct ContribWarpSmem {
+    float t[kContribRun][32];         // nearest hit distance per step and lane
+    int b[kContribRun][32];           // its building
+    int cb[kCastList][32];            // casting list: building
+    unsigned cm[kCastList][32];       //               steps whose ray meets it
+};
+
+// Plucker test with the hit distance (t = ((a - o) . n) / (d . n)), the same decision as
+// plucker_hit.
+__device__ __forceinline__ bool plucker_hit_t(const PluckerTri& p, const StepConst& s, float tmin,
+                                              float* t) {
+    if (!plucker_hit(p, s.dx, s.dy, s.dz, tmin)) return false;
+    const float nd = fmaf(s.dz, p.nz, fmaf(s.dy, p.ny, __fmul_rn(s.dx, p.nx)));
+    *t = p.aon / nd;
+    return true;
+}
+
+__global__ void __launch_bounds__(32 * kContribWarps)
+k_building_contribution(ContribArgs a) {
+    __shared__ ContribWarpSmem s_w[kContribWarps];
+    __shared__ BlockConst s_bc[kContribWarps];
+    __shared__ StepConst s_st[kContribWarps][kContribRun];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int tiles_x = (a.bnx + 7) >> 3;
+    const long long warp_id = (long long)blockIdx.x * kContribWarps + wib;
+    if (warp_id >= (long long)tiles_x * ((a.bny + 3) >> 2)) return;     // whole warps
+    const int ty = (int)(warp_id / tiles_x), tx = (int)(warp_id - (long long)ty * tiles_x);
+    const int lx = tx * 8 + (lane & 7), ly = ty * 4 + (lane >> 3);
+    const int ix = a.bx0 + lx, iy = a.by0 + ly;
+    float3 o;
+    o.x = __fadd_rn(a.x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), a.dx));
+    o.y = __fadd_rn(a.y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), a.dx));
+    o.z = 0.f;
+    const bool in_region = lx < a.bnx && ly < a.bny && inside_polygon(a.poly, a.n, (double)o.x, (double)o.y);
+    const long long cell = (long long)iy * a.nx + ix;
+    ContribWarpSmem& w = s_w[wib];
+    BlockConst& bc = s_bc[wib];
+    StepConst* ss = s_st[wib];
+    unsigned long long n_graze = 0, n_over = 0;
+    for (int r = 0; r < a.n_runs; ++r) {
+        __syncwarp();
+        for (int q = lane; q < (int)(sizeof(BlockConst) / 4); q += 32)
+            reinterpret_cast<int*>(&bc)[q] = reinterpret_cast<const int*>(&a.runs[r])[q];
+        __syncwarp();
+        const int K = bc.K;
+        for (int q = lane; q < K * (int)(sizeof(StepConst) / 4); q += 32)
+            reinterpret_cast<int*>(ss)[q] = reinterpret_cast<const int*>(&a.steps[bc.j0])[q];
+        const unsigned run_bits = K >= 32 ? 0xffffffffu : ((1u << K) - 1u);
+        unsigned m = 0u;
+        if (in_region) m = (unsigned)(a.masks[(long long)bc.mask_block * a.R + cell] >> bc.mask_bit) & run_bits;
+        __syncwarp();
+        if (!__any_sync(0xffffffffu, m != 0u)) continue;
+        for (int k = 0; k < K; ++k) w.t[k][lane] = 3.4e38f;
+        int n_list = 0;
+        bool ovf = false;
+        unsigned found = 0u;
+        const bool wedge = bc.wedge_ok != 0.f;
+        const bool want = m != 0u;
+        for (int i = 0; i < a.sc.n_nodes;) {
+            const float4 lo = __ldg(&a.sc.nodes[2 * i]);
+            const float4 hi = __ldg(&a.sc.nodes[2 * i + 1]);
             const int esc = __float_as_int(lo.w);
             const int tri = __float_as_int(hi.w);
-            const bool in = hit_box(o, s.ix, s.iy, s.iz, lo, hi);
+            const bool in = want && (wedge ? fan_box(o, bc, lo, hi) : slope_box(o, bc, lo, hi));
             if (tri >= 0) {
+                unsigned cand = 0u;
+                float4 ta, tb, tc;
                 if (in) {
-                    const float4 a = __ldg(&sc.tris[3 * tri]);
-                    const float4 b = __ldg(&sc.tris[3 * tri + 1]);
-                    const float4 cc = __ldg(&sc.tris[3 * tri + 2]);
-                    const float t = hit_dist_any(s.kz, o, a, b, cc, s, kGroundTmin);
-                    if (t >= 0.f) {
-                        const int bid = __float_as_int(a.w);
-                        if (t < best_t) { best_t = t; best = bid; }
-                        bool seen = false;
-                        for (int q = 0; q < nh; ++q) seen |= (ids[q] == bid);
-                        if (!seen) {
-                            if (nh < kMaxCasters) ids[nh++] = bid;
-                            else lost = true;
+                    ta = __ldg(&a.sc.tris[3 * tri]);
+                    tb = __ldg(&a.sc.tris[3 * tri + 1]);
+                    tc = __ldg(&a.sc.tris[3 * tri + 2]);
+                    if (plane_reachable(o, ta, tb, tc, bc)) {
+                        int ka, kb;
+                        candidate_steps(o, bc, bc.psi, ta, tb, tc, &ka, &kb);
+                        if (ka <= kb) {
+                            const unsigned hi_bits = kb >= 31 ? 0xffffffffu : ((2u << kb) - 1u);
+                            cand = m & hi_bits & ~((1u << ka) - 1u);
+                        }
+                    }
+                }
+                const int wa = __reduce_min_sync(0xffffffffu, cand ? __ffs(cand) - 1 : 32);
+                const int wb = __reduce_max_sync(0xffffffffu, cand ? 31 - __clz(cand) : -1);
+                if (wa <= wb) {
+                    unsigned hits = 0u;
+                    PluckerTri pt;
+                    if (cand) pt = plucker_setup(o, ta, tb, tc);
+                    const int bid = cand ? __float_as_int(ta.w) : 0;
+                    for (int k = wa; k <= wb; ++k) {
+                        float t;
+                        if (((cand >> k) & 1u) && plucker_hit_t(pt, ss[k], kGroundTmin, &t)) {
+                            hits |= 1u << k;
+                            if (t < w.t[k][lane]) {
+                                w.t[k][lane] = t;
+                                w.b[k][lane] = bid;
+                            }
+                        }
+                    }
+                    if (hits) {
+                        found |= hits;
+                        int e = 0;
+                        while (e < n_list && w.cb[e][lane] != bid) ++e;
+                        if (e < n_list) {
+                            w.cm[e][lane] |= hits;
+                        } else if (n_list < kCastList) {
+                            w.cb[n_list][lane] = bid;
+                            w.cm[n_list][lane] = hits;
+                            ++n_list;
+                        } else {
+                            ovf = true;
                         }
                     }
                 }
                 i = esc;
             } else {
-                i = in ? i + 1 : esc;
+                i = __any_sync(0xffffffffu, in) ? i + 1 : esc;
             }
         }
-        for (int q = 0; q < nh; ++q) atomicAdd(&casting[ids[q]], w);
-        if (best >= 0) atomicAdd(&nearest[best], w);
-        else atomicAdd(&stats[1], 1ull);     // marked shadowed by the raster, ray met nothing
-        if (lost) atomicAdd(&stats[0], 1ull);
+        // nearest: runs of steps with the same nearest building are credited at once
+        n_graze += (unsigned long long)__popc(m & ~found);
+        unsigned rest = m & found;
+        int cur = -1;
+        unsigned long long cnt = 0;
+        while (rest) {
+            const int k = __ffs(rest) - 1;
+            rest &= rest - 1u;
+            const int bid = w.b[k][lane];
+            if (bid != cur) {
+                if (cnt) atomicAdd(&a.near_cnt[cur], cnt);
+                cur = bid;
+                cnt = 0;
+            }
+            ++cnt;
+        }
+        if (cnt) atomicAdd(&a.near_cnt[cur], cnt);
+        if (!ovf) {
+            for (int e = 0; e < n_list; ++e)
+                atomicAdd(&a.cast_cnt[w.cb[e][lane]], (unsigned long long)__popc(w.cm[e][lane]));
+            continue;
+        }
+        // more buildings than the list holds: casting again, ray by ray (each lane alone;
+        // the nearest arrays, no longer needed, hold the ray's list)
+        int* ids = reinterpret_cast<int*>(&w.t[0][0]);     // kRayList x 32 ints: t, then b
+        unsigned todo = m & found;
+        while (todo) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const StepConst& s = ss[k];
+            int n_ids = 0;
+            bool lost = false;
+            for (int i = 0; i < a.sc.n_nodes;) {
+                const float4 lo = __ldg(&a.sc.nodes[2 * i]);
+                const float4 hi = __ldg(&a.sc.nodes[2 * i + 1]);
+                const int esc = __float_as_int(lo.w);
+                const int tri = __float_as_int(hi.w);
+                const bool in = hit_box(o, s.ix, s.iy, s.iz, lo, hi);
+                if (tri >= 0) {
+                    if (in) {
+                        const float4 ta = __ldg(&a.sc.tris[3 * tri]);
+                        const float4 tb = __ldg(&a.sc.tris[3 * tri + 1]);
+                        const float4 tc = __ldg(&a.sc.tris[3 * tri + 2]);
+                        const PluckerTri pt = plucker_setup(o, ta, tb, tc);
+                        if (plucker_hit(pt, s.dx, s.dy, s.dz, kGroundTmin)) {
+                            const int bid = __float_as_int(ta.w);
+                            int e = 0;
+                            while (e < n_ids && ids[e * 32 + lane] != bid) ++e;
+                            if (e == n_ids) {
+                                if (n_ids < kRayList) ids[(n_ids++) * 32 + lane] = bid;
+                                else lost = true;
+                            }
+                        }
+                    }
+                    i = esc;
+                } else {
+                    i = in ? i + 1 : esc;
+                }
+            }
+            for (int e = 0; e < n_ids; ++e) atomicAdd(&a.cast_cnt[ids[e * 32 + lane]], 1ull);
+            if (lost) ++n_over;
+        }
+    }
+    for (int q = 16; q > 0; q >>= 1) {
+        n_graze += __shfl_down_sync(0xffffffffu, n_graze, q);
+        n_over += __shfl_down_sync(0xffffffffu, n_over, q);
+    }
+    if (lane == 0) {
+        if (n_over) atomicAdd(&a.stats[0], n_over);
+        if (n_graze) atomicAdd(&a.stats[1], n_graze);
     }
 }
 
 }  // namespace
 
 cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
-                                         int n_buildings, const float* poly_xy, int n,
-                                         double* casting_out, double* nearest_out,
-                                         unsigned long long* stats_out, cudaStream_t st) {
+                                         const std::vector<BlockConst>& runs, int n_buildings,
+                                         const float* poly_xy, int n, double* casting_out,
+                                         double* nearest_out, unsigned long long* stats_out,
+                                         cudaStream_t st) {
     const long long R = (long long)rc.nx * rc.ny;
     const int B = n_buildings > 0 ? n_buildings : 1;
+    const size_t n_cnt = 2 * (size_t)B + 2;
     cudaError_t e = cudaSuccess;
-    unsigned long long *masks = nullptr, *ovf = nullptr;
+    unsigned long long *masks = nullptr, *cnt = nullptr;
     int *gross = nullptr, *run = nullptr;
     double2* dp = nullptr;
-    double* acc = nullptr;
+    BlockConst* druns = nullptr;
     std::vector<double2> hp((size_t)n);
-    for (int i = 0; i < n; ++i) hp[(size_t)i] = make_double2((double)poly_xy[2 * i], (double)poly_xy[2 * i + 1]);
-    std::vector<double> h_acc(2 * (size_t)B, 0.0);
-    unsigned long long h_stats[2] = {0ull, 0ull};
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int i = 0; i < n; ++i) {
+        hp[(size_t)i] = make_double2((double)poly_xy[2 * i], (double)poly_xy[2 * i + 1]);
+        xmin = std::min(xmin, hp[(size_t)i].x); xmax = std::max(xmax, hp[(size_t)i].x);
+        ymin = std::min(ymin, hp[(size_t)i].y); ymax = std::max(ymax, hp[(size_t)i].y);
+    }
+    // cells whose centre may lie in the polygon (one cell of margin for rounding)
+    const double dx = rc.dx;
+    const double fx0 = std::max(0.0, std::floor((xmin - rc.x0) / dx - 0.5) - 1.0);
+    const double fx1 = std::min((double)rc.nx - 1.0, std::ceil((xmax - rc.x0) / dx - 0.5) + 1.0);
+    const double fy0 = std::max(0.0, std::floor((ymin - rc.y0) / dx - 0.5) - 1.0);
+    const double fy1 = std::min((double)rc.ny - 1.0, std::ceil((ymax - rc.y0) / dx - 0.5) + 1.0);
+    std::vector<unsigned long long> h_cnt(n_cnt, 0ull);
 #define TRY(x) do { e = (x); if (e != cudaSuccess) goto done; } while (0)
-    TRY(sa::scratch_alloc(&acc, sizeof(double) * 2 * (size_t)B, st));
-    TRY(sa::scratch_alloc(&ovf, 2 * sizeof(unsigned long long), st));
-    TRY(sa::scratch_alloc(&dp, sizeof(double2) * (size_t)n, st));
-    TRY(cudaMemsetAsync(acc, 0, sizeof(double) * 2 * (size_t)B, st));
-    TRY(cudaMemsetAsync(ovf, 0, 2 * sizeof(unsigned long long), st));
-    TRY(cudaMemcpyAsync(dp, hp.data(), sizeof(double2) * (size_t)n, cudaMemcpyHostToDevice, st));
-    if (R > 0 && sun.n_blocks > 0 && sc.T > 0) {
+    TRY(sa::scratch_alloc(&cnt, sizeof(unsigned long long) * n_cnt, st));
+    TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * n_cnt, st));
+    if (R > 0 && sun.n_blocks > 0 && sc.T > 0 && !runs.empty() && fx0 <= fx1 && fy0 <= fy1) {
+        TRY(sa::scratch_alloc(&dp, sizeof(double2) * (size_t)n, st));
+        TRY(cudaMemcpyAsync(dp, hp.data(), sizeof(double2) * (size_t)n, cudaMemcpyHostToDevice, st));
+        TRY(sa::scratch_alloc(&druns, sizeof(BlockConst) * runs.size(), st));
+        TRY(cudaMemcpyAsync(druns, runs.data(), sizeof(BlockConst) * runs.size(), cudaMemcpyHostToDevice, st));
         // the accrual raster's per-block step masks mark the shadowed steps
         TRY(sa::scratch_alloc(&masks, sizeof(unsigned long long) * (size_t)R * sun.n_blocks, st));
         TRY(cudaMemsetAsync(masks, 0, sizeof(unsigned long long) * (size_t)R * sun.n_blocks, st));
@@ -220,25 +377,35 @@ cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, 
             out.masks = reinterpret_cast<uint64_t*>(masks);
             TRY(launch_raster_ground(sc, rc, sun, out, st));
         }
-        const long long items = R * sun.n_blocks;
-        const double w = (double)rc.dx * (double)rc.dx / (double)sun.S;
-        k_building_contribution<<<(unsigned)((items + kContribThreads - 1) / kContribThreads),
-                                  kContribThreads, 0, st>>>(
-            sc, sun.steps, sun.blocks, sun.n_blocks, masks, rc.x0, rc.y0, rc.dx, rc.nx, R, dp, n, w,
-            acc, acc + B, ovf);
+        ContribArgs ca;
+        ca.sc = sc; ca.steps = sun.steps; ca.runs = druns; ca.n_runs = (int)runs.size();
+        ca.masks = masks; ca.R = R;
+        ca.x0 = rc.x0; ca.y0 = rc.y0; ca.dx = rc.dx; ca.nx = rc.nx;
+        ca.bx0 = (int)fx0; ca.by0 = (int)fy0;
+        ca.bnx = (int)fx1 - (int)fx0 + 1; ca.bny = (int)fy1 - (int)fy0 + 1;
+        ca.poly = dp; ca.n = n;
+        ca.cast_cnt = cnt; ca.near_cnt = cnt + B; ca.stats = cnt + 2 * B;
+        const long long warps = (long long)((ca.bnx + 7) / 8) * ((ca.bny + 3) / 4);
+        {
+            KernelTimer kt(KT_CONTRIB, st);
+            k_building_contribution<<<(unsigned)((warps + kContribWarps - 1) / kContribWarps),
+                                      32 * kContribWarps, 0, st>>>(ca);
+        }
         TRY(cudaGetLastError());
     }
-    TRY(cudaMemcpyAsync(h_acc.data(), acc, sizeof(double) * 2 * (size_t)B, cudaMemcpyDeviceToHost, st));
-    TRY(cudaMemcpyAsync(h_stats, ovf, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(h_cnt.data(), cnt, sizeof(unsigned long long) * n_cnt, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
-    for (int b = 0; b < n_buildings; ++b) {
-        casting_out[b] = h_acc[(size_t)b];
-        nearest_out[b] = h_acc[(size_t)B + b];
+    {
+        const double wgt = sun.S > 0 ? (double)rc.dx * (double)rc.dx / (double)sun.S : 0.0;
+        for (int b = 0; b < n_buildings; ++b) {
+            casting_out[b] = (double)h_cnt[(size_t)b] * wgt;
+            nearest_out[b] = (double)h_cnt[(size_t)B + b] * wgt;
+        }
+        stats_out[0] = h_cnt[2 * (size_t)B];
+        stats_out[1] = h_cnt[2 * (size_t)B + 1];
     }
-    stats_out[0] = h_stats[0];
-    stats_out[1] = h_stats[1];
 done:
-    for (void* p : {(void*)masks, (void*)ovf, (void*)gross, (void*)run, (void*)dp, (void*)acc})
+    for (void* p : {(void*)masks, (void*)cnt, (void*)gross, (void*)run, (void*)dp, (void*)druns})
         if (p) cudaFreeAsync(p, st);
     return e;
 #undef TRY

@@ -1026,14 +1026,36 @@ sa_status sa_building_contribution(const sa_scene* scene, const sa_receivers* gr
     dsun.blocks = sun->d_blocks;
     dsun.S = sun->S;
     dsun.n_blocks = (int)sun->h_blocks.size();
+    // runs of <= 32 steps of each block, each with its own fan, pointing into the block's mask
+    std::vector<float> dirs(3 * (size_t)sun->S);
+    for (int j = 0; j < sun->S; ++j) {
+        dirs[3 * (size_t)j] = sun->h_steps[j].dx;
+        dirs[3 * (size_t)j + 1] = sun->h_steps[j].dy;
+        dirs[3 * (size_t)j + 2] = sun->h_steps[j].dz;
+    }
+    std::vector<sa::BlockConst> runs;
+    for (const sa::BlockConst& b : sun->h_blocks) {
+        const int nsub = (b.K + 31) / 32;
+        for (int q = 0; q < nsub; ++q) {
+            const int k0 = q * b.K / nsub, k1 = (q + 1) * b.K / nsub;
+            sa::BlockConst r = make_block(dirs.data(), sun->h_steps, b.j0 + k0, k1 - k0, 0, true);
+            r.mask_block = b.mask_block;
+            r.mask_bit = b.mask_bit + k0;
+            runs.push_back(r);
+        }
+    }
     unsigned long long h[2] = {0ull, 0ull};
-    cudaError_t e = sa::launch_building_contribution(dev_scene(scene), dev_recv(grid), dsun, scene->n_buildings,
-                                                     poly_xy, n, casting, nearest, h, as_stream(stream));
+    cudaError_t e = sa::launch_building_contribution(dev_scene(scene), dev_recv(grid), dsun, runs,
+                                                     scene->n_buildings, poly_xy, n, casting, nearest, h,
+                                                     as_stream(stream));
     if (e != cudaSuccess) return cuda_fail(e, who);
     if (stats) {
         stats[0] = (int64_t)h[0];
         stats[1] = (int64_t)h[1];
     }
+    if (h[0] > 0)
+        return fail(SA_ERR_UNSUPPORTED, "%s: %llu cell-steps met more than 64 buildings along one ray; "
+                    "their casting credit is incomplete", who, h[0]);
     return SA_OK;
 }
 

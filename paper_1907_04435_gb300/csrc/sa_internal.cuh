@@ -118,6 +118,80 @@ __device__ __forceinline__ bool plane_reachable(const float3& o, const float4& a
     return true;
 }
 
+// ------------------------------------------------------------- fan of a block's rays
+// Conservative test of a box against the block's ray fan from origin o (see BlockConst).
+// front: the receiver's normal nf has nf . d > 0 for every direction of the block, so all
+// rays stay in front of the receiver's wall plane and boxes wholly behind it are skipped.
+__device__ __forceinline__ bool fan_box(const float3& o, const BlockConst& bc, const float4& lo,
+                                        const float4& hi, bool front = false,
+                                        const float3& nf = float3{0.f, 0.f, 0.f}) {
+    if (hi.z < o.z) return false;                       // every ray climbs
+    const float cx = 0.5f * (lo.x + hi.x) - o.x, cy = 0.5f * (lo.y + hi.y) - o.y,
+                cz = 0.5f * (lo.z + hi.z) - o.z;
+    const float hx = 0.5f * (hi.x - lo.x), hy = 0.5f * (hi.y - lo.y), hz = 0.5f * (hi.z - lo.z);
+    if (front && nf.x * cx + nf.y * cy + nf.z * cz + fabsf(nf.x) * hx + fabsf(nf.y) * hy +
+                     fabsf(nf.z) * hz < -1e-4f)
+        return false;
+    const float R = sqrtf(cx * cx + cy * cy + cz * cz) + sqrtf(hx * hx + hy * hy + hz * hz);
+    const float slack = 1e-5f * R + 1e-4f;
+    // in-plane half-spaces
+    const float g1 = bc.g1x * cx + bc.g1y * cy + bc.g1z * cz +
+                     fabsf(bc.g1x) * hx + fabsf(bc.g1y) * hy + fabsf(bc.g1z) * hz;
+    const float g2 = bc.g2x * cx + bc.g2y * cy + bc.g2z * cz +
+                     fabsf(bc.g2x) * hx + fabsf(bc.g2y) * hy + fabsf(bc.g2z) * hz;
+    if (g1 < -slack || g2 < -slack) return false;
+    // out of plane: |n . x| <= s_off |x| on the fan
+    const float nc = bc.nx * cx + bc.ny * cy + bc.nz * cz;
+    const float rn = fabsf(bc.nx) * hx + fabsf(bc.ny) * hy + fabsf(bc.nz) * hz;
+    const float lim = bc.s_off * R + slack;
+    return (nc - rn <= lim) && (nc + rn >= -lim);
+}
+
+// Slope-box version (used when the block's wedge is degenerate): a point at height z above
+// o on one of the rays lies at o.xy + (z - o.z) * u with u in the block's slope box.
+__device__ __forceinline__ bool slope_box(const float3& o, const BlockConst& bc, const float4& lo,
+                                          const float4& hi) {
+    const float h1 = hi.z - o.z;
+    if (h1 < 0.f) return false;
+    const float h0 = fmaxf(lo.z - o.z, 0.f);
+    const float xa = fminf(h0 * bc.uxlo, h1 * bc.uxlo), xb = fmaxf(h0 * bc.uxhi, h1 * bc.uxhi);
+    const float ya = fminf(h0 * bc.uylo, h1 * bc.uylo), yb = fmaxf(h0 * bc.uyhi, h1 * bc.uyhi);
+    const float sl = 1e-4f + 1e-6f * (fabsf(o.x) + fabsf(o.y) + h1);
+    return (o.x + xa <= hi.x + sl) && (o.x + xb >= lo.x - sl) && (o.y + ya <= hi.y + sl) &&
+           (o.y + yb >= lo.y - sl);
+}
+
+// Steps of the block whose in-plane angle can meet the triangle: [*ka, *kb] (inclusive).
+__device__ __forceinline__ void candidate_steps(const float3& o, const BlockConst& bc,
+                                                const float* psi, const float4& a,
+                                                const float4& b, const float4& c, int* ka,
+                                                int* kb) {
+    *ka = 0;
+    *kb = bc.K - 1;
+    if (bc.wedge_ok == 0.f || !bc.monotone) return;
+    float ang[3];
+    const float4* v[3] = {&a, &b, &c};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float x = v[q]->x - o.x, y = v[q]->y - o.y, z = v[q]->z - o.z;
+        const float p = bc.e1x * x + bc.e1y * y + bc.e1z * z;
+        const float s = bc.e2x * x + bc.e2y * y + bc.e2z * z;
+        if (p * p + s * s < 1e-12f) return;             // vertex on the fan's axis line
+        ang[q] = atan2f(s, p);
+    }
+    const float amin = fminf(ang[0], fminf(ang[1], ang[2]));
+    const float amax = fmaxf(ang[0], fmaxf(ang[1], ang[2]));
+    if (amax - amin >= 3.1f) return;                    // may surround the origin: all steps
+    const float lo = amin - bc.psi_eps, hi = amax + bc.psi_eps;
+    // first k with psi[k] >= lo, last k with psi[k] <= hi
+    int l = 0, r = bc.K;
+    while (l < r) { int m = (l + r) >> 1; if (psi[m] >= lo) r = m; else l = m + 1; }
+    *ka = l;
+    l = 0; r = bc.K;
+    while (l < r) { int m = (l + r) >> 1; if (psi[m] > hi) r = m; else l = m + 1; }
+    *kb = l - 1;
+}
+
 // ---------------------------------------------------------------------------- scene
 // BVH nodes in depth-first order, two float4 each:
 //   n0 = (lo.x, lo.y, lo.z, escape as int)   escape = index of the next node after the subtree
@@ -396,9 +470,10 @@ cudaError_t launch_height_grad(const DevScene& sc, const FootprintSet& fs, const
 // nearest_out are host arrays of n_buildings, stats_out two host counters (cell-steps past
 // 32 buildings, shadowed cell-steps whose ray met no building)
 cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
-                                         int n_buildings, const float* poly_xy, int n,
-                                         double* casting_out, double* nearest_out,
-                                         unsigned long long* stats_out, cudaStream_t st);
+                                         const std::vector<BlockConst>& runs, int n_buildings,
+                                         const float* poly_xy, int n, double* casting_out,
+                                         double* nearest_out, unsigned long long* stats_out,
+                                         cudaStream_t st);
 
 // direction graph (sa_graph.cu): edge of each block (blocks given by first step j0 and
 // length K over dirs [S][3]), the block each edge's map is computed from (its middle
@@ -511,7 +586,7 @@ namespace sa {
 // Per-kernel device timing: while enabled, a CUDA event pair is recorded on the launching
 // stream around each launch of the library's main kernels (not inside stream capture).
 enum KernelClass { KT_RASTER = 0, KT_SAM_POINTS = 1, KT_ACCRUAL = 2, KT_SWEEP = 3, KT_IAM = 4,
-                   KT_GRAPH = 5, KT_RASTER_BIN = 6 };
+                   KT_GRAPH = 5, KT_RASTER_BIN = 6, KT_CONTRIB = 7 };
 void set_kernel_timing(int on);
 int get_kernel_timing();
 struct KernelTimer {

@@ -103,5 +103,6 @@ cudaError_t collect_kernel_times(double* ms, long long* n, int n_classes) {
 static_assert(sa::KT_RASTER == SA_KERNEL_RASTER && sa::KT_SAM_POINTS == SA_KERNEL_SAM_POINTS &&
                   sa::KT_ACCRUAL == SA_KERNEL_ACCRUAL && sa::KT_SWEEP == SA_KERNEL_SWEEP &&
                   sa::KT_IAM == SA_KERNEL_IAM && sa::KT_GRAPH == SA_KERNEL_GRAPH &&
-                  sa::KT_RASTER_BIN == SA_KERNEL_RASTER_BIN && SA_KERNEL_CLASSES == 7,
+                  sa::KT_RASTER_BIN == SA_KERNEL_RASTER_BIN && sa::KT_CONTRIB == SA_KERNEL_CONTRIB &&
+                  SA_KERNEL_CLASSES == 8,
               "kernel classes of the C ABI and the library agree");
