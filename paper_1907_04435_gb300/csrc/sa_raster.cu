@@ -31,6 +31,10 @@ namespace {
 constexpr int kTile = 32;               // cells per tile side
 constexpr int kRasterThreads = 256;     // 8 warps x 4 rows each
 constexpr int kTriBatch = 64;           // triangles staged per batch
+// resident CTAs per SM the raster kernels are compiled for (registers: 65536 / (256 x this))
+#ifndef SA_RASTER_CTAS
+#define SA_RASTER_CTAS 4
+#endif
 
 struct TileGeom {
     float x0, y0, dx;
@@ -493,7 +497,7 @@ __device__ __forceinline__ void flush_raster_counts(unsigned long long* stats, u
 // One CTA per 32 x 32-cell tile, every block of the chunk in order; the gross /
 // continuous state of the thread's four cells stays in registers between blocks.
 template <bool COUNT, bool CULL>
-__global__ void __launch_bounds__(kRasterThreads, 4)
+__global__ void __launch_bounds__(kRasterThreads, SA_RASTER_CTAS)
 k_raster(RasterArgs ra) {
     __shared__ TileSmem sm;
     __shared__ RunState s_st[kTile * kTile];       // gross / run / best of the tile's cells
@@ -568,7 +572,7 @@ k_raster(RasterArgs ra) {
 // It writes the counts of the tile's cells inside the region and, where the base counts
 // are given, the impact (variant minus base).
 template <bool COUNT, bool CULL>
-__global__ void __launch_bounds__(kRasterThreads, 4)
+__global__ void __launch_bounds__(kRasterThreads, SA_RASTER_CTAS)
 k_batch(BatchArgs ba) {
     __shared__ TileSmem sm;
     __shared__ RunState s_st[kTile * kTile];       // gross / run / best of the tile's cells

@@ -6,8 +6,10 @@
 // basis (e1, e2) orthogonal to the run's middle direction d_m, around a reference point.
 // The map is a grid of light-space tiles:
 //   - every triangle that faces the sun at some step of the run is binned into the tiles
-//     its projection covers, widened by the largest sideways drift of any ray of the run
-//     before it clears the tallest geometry (t_max x sin of the run's half-angle);
+//     its projection covers, widened by the drift of the run's rays up to the triangle's
+//     top: a ray of step k from a receiver leaves the receiver's light-space point by
+//     h x delta_k at height h above it (delta_k = (d_k . e1, d_k . e2) / d_k.z), and the
+//     run's delta_k lie in a box that is long along the sun's motion and thin across it;
 //   - every receiver goes into the single tile holding its own projection.
 // A receiver and a triangle its rays can meet during the run therefore share a tile.
 // One pass over the geometry per run thus serves all of the run's steps.  The test
@@ -29,21 +31,28 @@ namespace sa {
 namespace {
 
 constexpr int kRunMax = 32;
+constexpr float kLightSlack = 0.05f;    // absolute slack (m) of the light-space culls (rounding)
 constexpr int kTileThreads = 128;
 constexpr int kTriChunk = 128;
+// resident CTAs per SM k_sam_tile is compiled for: 9 gives 55 registers and no spills
+#ifndef SA_TILE_CTAS
+#define SA_TILE_CTAS 9
+#endif
 
 struct RunLight {
     float e1[3], e2[3];          // light-space basis (orthogonal to the run's middle direction)
     float c[3];                  // reference point
     float a0, b0, tile;          // tile grid origin and tile side (m)
-    float margin;                // widening of triangle bins (m)
+    float zr;                    // lowest receiver height
     int nta, ntb;                // tiles along e1, e2
     int tile_base;               // first global tile index of this run
     int k0, kn;                  // steps of the run within the block
     int j0;                      // first step of the block
     int blk;                     // block within the chunk (row of the chunk's masks)
-    float min_dz, max_sin;       // lowest sin(elevation), largest sin(angle to d_m) of the run
-    float pad2[2];
+    // light-space drift per metre of height over the run's steps, as the margins it
+    // implies on each side: a ray point at height h above the receiver lies within
+    // [-h da_hi, h da_lo] of it along e1 and [-h db_hi, h db_lo] along e2 (all >= 0)
+    float da_hi, da_lo, db_hi, db_lo;
 };
 
 __device__ __forceinline__ void light_ab(const RunLight& rl, float x, float y, float z, float* a,
@@ -74,10 +83,12 @@ __device__ __forceinline__ bool tri_tiles(const float4& a, const float4& b, cons
     light_ab(rl, a.x, a.y, a.z, &pa[0], &pb[0]);
     light_ab(rl, b.x, b.y, b.z, &pa[1], &pb[1]);
     light_ab(rl, c.x, c.y, c.z, &pa[2], &pb[2]);
-    const float amin = fminf(pa[0], fminf(pa[1], pa[2])) - rl.margin;
-    const float amax = fmaxf(pa[0], fmaxf(pa[1], pa[2])) + rl.margin;
-    const float bmin = fminf(pb[0], fminf(pb[1], pb[2])) - rl.margin;
-    const float bmax = fmaxf(pb[0], fmaxf(pb[1], pb[2])) + rl.margin;
+    // receivers that a ray rising at most H to the triangle's top can reach it from
+    const float H = fmaxf(fmaxf(a.z, fmaxf(b.z, c.z)) - rl.zr, 0.f);
+    const float amin = fminf(pa[0], fminf(pa[1], pa[2])) - fmaf(H, rl.da_hi, kLightSlack);
+    const float amax = fmaxf(pa[0], fmaxf(pa[1], pa[2])) + fmaf(H, rl.da_lo, kLightSlack);
+    const float bmin = fminf(pb[0], fminf(pb[1], pb[2])) - fmaf(H, rl.db_hi, kLightSlack);
+    const float bmax = fmaxf(pb[0], fmaxf(pb[1], pb[2])) + fmaf(H, rl.db_lo, kLightSlack);
     const float inv = 1.f / rl.tile;
     const float fa0 = floorf((amin - rl.a0) * inv), fa1 = floorf((amax - rl.a0) * inv);
     const float fb0 = floorf((bmin - rl.b0) * inv), fb1 = floorf((bmax - rl.b0) * inv);
@@ -171,12 +182,13 @@ struct TileArgs {
 constexpr int kQueue = 64;
 
 // Lines of a triangle's light-space projection, as unit inward normals and offsets: a point
-// x is inside iff n . x + c >= 0 for all three.  A ray of the run that meets the triangle
-// leaves the receiver's light-space point within the drift bound of the projection, so a
-// receiver more than that bound outside one line cannot be shadowed by the triangle.  A
-// projection too thin to orient passes every point (the light box still applies).
-__device__ __forceinline__ void light_edges(const float* pa, const float* pb, float4& e0,
-                                            float4& e1, float4& e2) {
+// x is inside iff n . x + c >= 0 for all three.  A ray of the run that meets the triangle at
+// height h above the receiver passes x = r + h delta, so r can be shadowed by it only if
+// n . r + c >= -h max(0, n . delta) for every line; .w holds max(0, max of n . delta over
+// the run's drift box), so the cull is n . r + c >= -(rise x .w + slack).  A projection
+// too thin to orient passes every point (the light box still applies).
+__device__ __forceinline__ void light_edges(const float* pa, const float* pb, const RunLight& rl,
+                                            float4& e0, float4& e1, float4& e2) {
     float4* e[3] = {&e0, &e1, &e2};
     const float ax = pa[1] - pa[0], ay = pb[1] - pb[0];
     const float bx = pa[2] - pa[0], by = pb[2] - pb[0];
@@ -194,7 +206,9 @@ __device__ __forceinline__ void light_edges(const float* pa, const float* pb, fl
             continue;
         }
         const float nx = -sg * ey / len, ny = sg * ex / len;
-        *e[i] = make_float4(nx, ny, -(nx * pa[i] + ny * pb[i]), 0.f);
+        // largest n . delta over the drift box [-da_lo, da_hi] x [-db_lo, db_hi]
+        const float sup = fmaxf(nx * rl.da_hi, -nx * rl.da_lo) + fmaxf(ny * rl.db_hi, -ny * rl.db_lo);
+        *e[i] = make_float4(nx, ny, -(nx * pa[i] + ny * pb[i]), fmaxf(sup, 0.f) * 1.0001f);
     }
 }
 
@@ -249,7 +263,7 @@ __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int 
 }
 
 template <bool COUNT>
-__global__ void __launch_bounds__(kTileThreads, 9)   // 9 CTAs per SM: 55 registers, no spills
+__global__ void __launch_bounds__(kTileThreads, SA_TILE_CTAS)
 k_sam_tile(TileArgs ta) {
     constexpr int kWarps = kTileThreads / 32;
     __shared__ float4 s_tri[kTriChunk * 3];
@@ -279,8 +293,6 @@ k_sam_tile(TileArgs ta) {
         s_d2[threadIdx.x][2] = f2_pack(s.dz, t.dz);
     }
     const bool cull = ta.sc.closed != 0;
-    const float inv_dz = 1.f / rl.min_dz;
-    const float drift = inv_dz * rl.max_sin * 1.0001f;
     unsigned short* q = s_q[warp];
     for (unsigned base = 0; base < tcnt; base += kTriChunk) {
         const int nt = (int)min((unsigned)kTriChunk, tcnt - base);
@@ -298,7 +310,7 @@ k_sam_tile(TileArgs ta) {
             light_ab(rl, c.x, c.y, c.z, &pa[2], &pb[2]);
             s_box[i] = make_float4(fminf(pa[0], fminf(pa[1], pa[2])), fmaxf(pa[0], fmaxf(pa[1], pa[2])),
                                    fminf(pb[0], fminf(pb[1], pb[2])), fmaxf(pb[0], fmaxf(pb[1], pb[2])));
-            light_edges(pa, pb, s_edge[0][i], s_edge[1][i], s_edge[2][i]);
+            light_edges(pa, pb, rl, s_edge[0][i], s_edge[1][i], s_edge[2][i]);
             s_ztop[i] = fmaxf(a.z, fmaxf(b.z, c.z));
             s_front[i] = run_front(a, b, c, ta.steps, rl, cull);
         }
@@ -332,13 +344,17 @@ k_sam_tile(TileArgs ta) {
                 if (t < nt && s_front[t]) {
                     const float rise = s_ztop[t] - wz;
                     if (rise >= -0.01f) {
-                        const float mg = fmaf(fmaxf(rise, 0.f), drift, 0.05f);
+                        const float h = fmaxf(rise, 0.f);
                         const float4 bx = s_box[t];
-                        near = !(wa1 < bx.x - mg || wa0 > bx.y + mg || wb1 < bx.z - mg || wb0 > bx.w + mg);
+                        near = !(wa1 < bx.x - fmaf(h, rl.da_hi, kLightSlack) ||
+                                 wa0 > bx.y + fmaf(h, rl.da_lo, kLightSlack) ||
+                                 wb1 < bx.z - fmaf(h, rl.db_hi, kLightSlack) ||
+                                 wb0 > bx.w + fmaf(h, rl.db_lo, kLightSlack));
 #pragma unroll
                         for (int q3 = 0; q3 < 3; ++q3) {
                             const float4 e = s_edge[q3][t];
-                            near = near && fmaxf(e.x * wa0, e.x * wa1) + fmaxf(e.y * wb0, e.y * wb1) + e.z >= -mg;
+                            near = near && fmaxf(e.x * wa0, e.x * wa1) + fmaxf(e.y * wb0, e.y * wb1) + e.z >=
+                                               -fmaf(h, e.w, kLightSlack);
                         }
                     }
                 }
@@ -354,14 +370,17 @@ k_sam_tile(TileArgs ta) {
                 if (live) {
                     const float rise = s_ztop[t] - p.z;
                     if (rise >= -0.01f) {
-                        const float mg = fmaf(fmaxf(rise, 0.f), drift, 0.05f);
+                        const float h = fmaxf(rise, 0.f);
                         const float4 bx = s_box[t];
-                        pass = !(la < bx.x - mg || la > bx.y + mg || lb < bx.z - mg || lb > bx.w + mg);
+                        pass = !(la < bx.x - fmaf(h, rl.da_hi, kLightSlack) ||
+                                 la > bx.y + fmaf(h, rl.da_lo, kLightSlack) ||
+                                 lb < bx.z - fmaf(h, rl.db_hi, kLightSlack) ||
+                                 lb > bx.w + fmaf(h, rl.db_lo, kLightSlack));
                         if (pass) {
 #pragma unroll
                             for (int q3 = 0; q3 < 3; ++q3) {
                                 const float4 e = s_edge[q3][t];
-                                pass = pass && fmaf(e.x, la, fmaf(e.y, lb, e.z)) >= -mg;
+                                pass = pass && fmaf(e.x, la, fmaf(e.y, lb, e.z)) >= -fmaf(h, e.w, kLightSlack);
                             }
                         }
                     }
@@ -515,7 +534,7 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
     int* bestp = out.continuous ? out.continuous : best;
     const double c[3] = {0.5 * (recv_box[0] + recv_box[3]), 0.5 * (recv_box[1] + recv_box[4]),
                          0.5 * (recv_box[2] + recv_box[5])};
-    const double zmax = scene_box[5], zmin_r = recv_box[2];
+    const double zmin_r = recv_box[2];
     std::vector<RunLight> hr;
     std::vector<int> tile_run;
     const int n_blocks = (int)h_blocks.size();
@@ -547,21 +566,24 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
                 double e2[3] = {dm[1] * e1[2] - dm[2] * e1[1], dm[2] * e1[0] - dm[0] * e1[2],
                                 dm[0] * e1[1] - dm[1] * e1[0]};
                 normalize3(e2);
-                double max_sin = 0.0, min_dz = 1.0;
+                // drift per metre of height of each step's ray in light space; its box over
+                // the run, padded for rounding, gives the culls' margins
+                double da_lo = 0.0, da_hi = 0.0, db_lo = 0.0, db_hi = 0.0;
                 for (int k = 0; k < rl.kn; ++k) {
                     const StepConst& s = h_steps[bc.j0 + k0 + k];
-                    double d[3] = {s.dx, s.dy, s.dz};
-                    normalize3(d);
-                    const double cs = d[0] * dm[0] + d[1] * dm[1] + d[2] * dm[2];
-                    max_sin = std::max(max_sin, sqrt(std::max(0.0, 1.0 - cs * cs)));
-                    min_dz = std::min(min_dz, d[2]);
+                    const double d[3] = {s.dx, s.dy, s.dz};
+                    const double dz = std::max(d[2], 1e-6);
+                    const double da = (e1[0] * d[0] + e1[1] * d[1] + e1[2] * d[2]) / dz;
+                    const double db = (e2[0] * d[0] + e2[1] * d[1] + e2[2] * d[2]) / dz;
+                    da_lo = std::min(da_lo, da); da_hi = std::max(da_hi, da);
+                    db_lo = std::min(db_lo, db); db_hi = std::max(db_hi, db);
                 }
-                // a ray of the run rises at sin(elevation) >= min_dz: beyond t_max it is
-                // above every triangle, and its sideways drift in light space is <= t * max_sin
-                const double t_max = std::max(0.0, zmax - zmin_r) / std::max(min_dz, 1e-3) + 1.0;
-                rl.margin = (float)(t_max * max_sin * 1.0001 + 0.05);
-                rl.min_dz = (float)std::max(min_dz, 1e-3) * 0.9999f;
-                rl.max_sin = (float)max_sin;
+                const double pad = 1e-6 + 1e-4 * std::max(da_hi - da_lo, db_hi - db_lo);
+                rl.da_hi = (float)(da_hi * 1.0001 + pad);
+                rl.da_lo = (float)(-da_lo * 1.0001 + pad);
+                rl.db_hi = (float)(db_hi * 1.0001 + pad);
+                rl.db_lo = (float)(-db_lo * 1.0001 + pad);
+                rl.zr = (float)zmin_r - 0.01f;
                 for (int q = 0; q < 3; ++q) { rl.e1[q] = (float)e1[q]; rl.e2[q] = (float)e2[q]; rl.c[q] = (float)c[q]; }
                 // tile grid over the light-space box of the receivers
                 double amin = 1e30, amax = -1e30, bmin = 1e30, bmax = -1e30;
