@@ -198,6 +198,9 @@ struct TileSmem {
     unsigned long long front[kTriBatch];     // steps with n . d > 0
     unsigned long long back[kTriBatch];      // steps with n . d < 0 (open scenes only)
     int valid[kTriBatch];
+    // canonical edges (EdgeRef, 6 floats each) of the staged triangles, 20 floats apart so
+    // that a unit reads them as five float4
+    float edges[kTriBatch * 20];
     float2 u[kMaxBlock];
     // slopes of steps (k, k + 1) packed for the paired step tests: [0][i] starts at step
     // 2i, [1][i] at step 2i + 1 (the last pair of a block repeats its last step)
@@ -305,7 +308,11 @@ __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int 
         fc0 > fc1 || fr0 > fr1) return;
     const int c0 = (int)fmaxf(fc0, 0.f), c1 = (int)fminf(fc1, (float)(kTile - 1));
     const int r0 = (int)fmaxf(fr0, 0.f), r1 = (int)fminf(fr1, (float)(kTile - 1));
-    const EdgeRef E0 = edge_ref(a, b), E1 = edge_ref(b, c), E2 = edge_ref(c, a);
+    const float4* ef = reinterpret_cast<const float4*>(&sm.edges[20 * t]);
+    const float4 f0 = ef[0], f1 = ef[1], f2 = ef[2], f3 = ef[3], f4 = ef[4];
+    const EdgeRef E0{f0.x, f0.y, f0.z, f0.w, f1.x, f1.y};
+    const EdgeRef E1{f1.z, f1.w, f2.x, f2.y, f2.z, f2.w};
+    const EdgeRef E2{f3.x, f3.y, f3.z, f3.w, f4.x, f4.y};
     // Row spans.  Each step's projection lies inside the projection for the run's
     // middle slope u_m widened by (sx, sy) = z_max |u_hi - u_lo| / 2 (a vertex at
     // height z moves by z (u_m - u_k)).  Lane j takes row r0 + j: the x-range of the
@@ -330,7 +337,8 @@ __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int 
             const int q = v == 2 ? 0 : v + 1;
             const float dy = py[q] - py[v];
             if (dy != 0.f) {
-                const float slope = (px[q] - px[v]) / dy;
+                // the spans carry slack, so an approximate quotient suffices
+                const float slope = __fdividef(px[q] - px[v], dy);
                 const float e0 = fminf(py[v], py[q]), e1 = fmaxf(py[v], py[q]);
                 if (ya >= e0 && ya <= e1) {
                     const float x = fmaf(ya - py[v], slope, px[v]);
@@ -458,6 +466,13 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
             if (lane == 0) {
                 sm.front[t] = fr;
                 sm.back[t] = bk;
+            }
+            if (lane < 3) {
+                const float4& p = sm.tri[3 * t + lane];
+                const float4& q = sm.tri[3 * t + (lane == 2 ? 0 : lane + 1)];
+                const EdgeRef e = edge_ref(p, q);
+                float* o = &sm.edges[20 * t + 6 * lane];
+                o[0] = e.vx; o[1] = e.vy; o[2] = e.vz; o[3] = e.ex; o[4] = e.ey; o[5] = e.ez;
             }
         }
         __syncthreads();

@@ -34,6 +34,10 @@ constexpr int kRunMax = 32;
 constexpr float kLightSlack = 0.05f;    // absolute slack (m) of the light-space culls (rounding)
 constexpr int kTileThreads = 128;
 constexpr int kTriChunk = 128;
+// side (m) of the light-space tiles
+#ifndef SA_LIGHT_TILE
+#define SA_LIGHT_TILE 32.f
+#endif
 // resident CTAs per SM k_sam_tile is compiled for: 9 gives 55 registers and no spills
 #ifndef SA_TILE_CTAS
 #define SA_TILE_CTAS 9
@@ -516,7 +520,7 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
     const long long R = rc.R;
     if (R == 0 || h_blocks.empty()) return cudaSuccess;
     const int run_len = std::max(1, std::min(kRunMax, get_point_run()));
-    const float tile = 32.f;
+    const float tile = SA_LIGHT_TILE;
     // blocks per chunk: the receiver bins hold every receiver once per run (4 bytes), the
     // masks 8 bytes per receiver and block; keep both within ~1 GiB and <= 64 blocks
     const int runs_per_block = (kMaxBlock + run_len - 1) / run_len;
