@@ -347,6 +347,23 @@ sa_status sa_batch_work_counters(sa_batch* b, uint64_t* counters, void* stream);
 sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
                            sa_method method, uint64_t* counters, void* stream);
 
+/* Bounds-checked build (diagnostics, for where no memory sanitiser can run).  The library built with -DSA_CHECKED (libshadowaccrual_checked.so) range-checks
+ * every index its kernels take from data -- a BVH leaf's triangle, an escape link, a
+ * binned triangle or receiver, a permutation entry, a tile cell, a building id -- before
+ * using it.  The first index out of range is recorded (site, index, bound) and replaced by
+ * one in range (an escape link by the end of the node list), so that no access leaves its
+ * buffer and no loop runs on; the computing calls (sa_accumulate, sa_shadow_masks,
+ * sa_accumulate_graph, sa_height_grad, sa_building_contribution, sa_batch_run,
+ * sa_accumulate_grid_noalloc) then synchronise their stream and return SA_ERR_INTERNAL
+ * naming the site.  In the plain build the checks compile to nothing.
+ *   sa_checked_build: 1 for the checked build, 0 for the plain one.
+ *   sa_check_status: synchronises the device and returns SA_ERR_INTERNAL if a violation
+ *   was recorded since the last report (writing site, index and bound, each nullable, and
+ *   clearing the record), SA_OK otherwise (always SA_OK in the plain build); SA_ERR_CUDA
+ *   if the device reports an error. */
+int32_t sa_checked_build(void);
+sa_status sa_check_status(int32_t* site, int64_t* index, int64_t* bound);
+
 /* Statistics of the library's scratch memory (diagnostics): stats uint64 [4] host gets
  *   [0] scratch allocations the library has made since it was loaded (all devices),
  *   [1] their bytes, summed,

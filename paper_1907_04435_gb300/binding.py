@@ -9,6 +9,7 @@ is built with nvcc; if that fails, importing raises.
 from __future__ import annotations
 
 import ctypes as ct
+import os
 import threading
 
 import numpy as np
@@ -34,8 +35,13 @@ class SAError(RuntimeError):
         self.status = status
 
 
+def checked_requested() -> bool:
+    """SA_CHECKED=1 in the environment selects the bounds-checked build of the library."""
+    return os.environ.get("SA_CHECKED", "0") not in ("", "0")
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked_requested() else _build.LIB
 
 
 def lib():
@@ -43,7 +49,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(checked=checked_requested())
             L = ct.CDLL(path)
             P, i32, i64, f32 = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_float
             PP = ct.POINTER(ct.c_void_p)
@@ -93,6 +99,8 @@ def lib():
             L.sa_shadow_score.argtypes = [P, P, i32, P, P, P, i32, P, P]
             L.sa_block_partition.argtypes = [P, i32, i32, P, P, P]
             L.sa_scratch_stats.argtypes = [P]
+            L.sa_checked_build.restype = i32
+            L.sa_check_status.argtypes = [P, P, P]
             L.sa_building_contribution.argtypes = [P, P, P, P, i32, P, P, P, P]
             L.sa_sun_interpolate.argtypes = [P, i32, P, i32, i32, P]
             L.sa_direction_graph.argtypes = [P, i32, P, i32, i32, f32, P, P, P, P, P]
@@ -104,7 +112,8 @@ def lib():
                          "sa_scene_declare_closed", "sa_set_option", "sa_batch_create",
                          "sa_batch_run", "sa_batch_tune", "sa_batch_work_counters",
                          "sa_kernel_times", "sa_shadow_area", "sa_shadow_score",
-                         "sa_block_partition", "sa_scratch_stats", "sa_building_contribution",
+                         "sa_block_partition", "sa_scratch_stats", "sa_check_status",
+                         "sa_building_contribution",
                          "sa_sun_interpolate", "sa_direction_graph", "sa_accumulate_graph"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
@@ -349,6 +358,24 @@ def sa_work_counters(scene: Scene, recv: Receivers, sun: Sun, method, stream=Non
     _check(lib().sa_work_counters(scene.handle, recv.handle, sun.handle, m, _ptr(c),
                                   ct.c_void_p(_stream(stream))))
     return [int(x) for x in c.cpu().tolist()]
+
+
+def sa_checked_build() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(lib().sa_checked_build())
+
+
+def sa_check_status():
+    """Synchronises the device and returns the first out-of-range index the checked build
+    recorded since the last call, as (site, index, bound), or None if there was none
+    (always None for the plain build)."""
+    site, idx, bound = ct.c_int32(), ct.c_int64(), ct.c_int64()
+    st = lib().sa_check_status(ct.byref(site), ct.byref(idx), ct.byref(bound))
+    if st == 0:
+        return None
+    if st != -7:
+        _check(st)
+    return site.value, idx.value, bound.value
 
 
 def sa_scratch_stats():

@@ -318,8 +318,8 @@ __device__ int hit_buildings(const DevScene& sc, const float3& o, const StepCons
     while (i < sc.n_nodes) {
         const float4 lo = __ldg(&sc.nodes[2 * i]);
         const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
-        const int esc = __float_as_int(lo.w);
-        const int tri = __float_as_int(hi.w);
+        const int esc = SA_ESC(__float_as_int(lo.w), i, sc.n_nodes, sa::CK_ADJ_ESCAPE);
+        const int tri = SA_LEAF(__float_as_int(hi.w), sc.T, sa::CK_ADJ_LEAF);
         const bool in = hit_box(o, s.ix, s.iy, s.iz, lo, hi);
         if (tri >= 0) {
             if (in) {

@@ -135,6 +135,7 @@ struct ContribArgs {
     unsigned long long* cast_cnt;     // [B]
     unsigned long long* near_cnt;     // [B]
     unsigned long long* stats;        // [2]
+    int n_b;                          // buildings (length of the counters)
 };
 
 struct ContribWarpSmem {
@@ -198,8 +199,8 @@ k_building_contribution(ContribArgs a) {
         for (int i = 0; i < a.sc.n_nodes;) {
             const float4 lo = __ldg(&a.sc.nodes[2 * i]);
             const float4 hi = __ldg(&a.sc.nodes[2 * i + 1]);
-            const int esc = __float_as_int(lo.w);
-            const int tri = __float_as_int(hi.w);
+            const int esc = SA_ESC(__float_as_int(lo.w), i, a.sc.n_nodes, sa::CK_CONTRIB_ESCAPE);
+            const int tri = SA_LEAF(__float_as_int(hi.w), a.sc.T, sa::CK_CONTRIB_LEAF);
             const bool in = want && (wedge ? fan_box(o, bc, lo, hi) : slope_box(o, bc, lo, hi));
             if (tri >= 0) {
                 unsigned cand = 0u;
@@ -223,7 +224,7 @@ k_building_contribution(ContribArgs a) {
                     unsigned hits = 0u;
                     PluckerTri pt;
                     if (cand) pt = plucker_setup(o, ta, tb, tc);
-                    const int bid = cand ? __float_as_int(ta.w) : 0;
+                    const int bid = cand ? (int)SA_CHK(__float_as_int(ta.w), a.n_b, sa::CK_CONTRIB_BUILDING) : 0;
                     for (int k = wa; k <= wb; ++k) {
                         float t;
                         if (((cand >> k) & 1u) && plucker_hit_t(pt, ss[k], kGroundTmin, &t)) {
@@ -289,8 +290,8 @@ k_building_contribution(ContribArgs a) {
             for (int i = 0; i < a.sc.n_nodes;) {
                 const float4 lo = __ldg(&a.sc.nodes[2 * i]);
                 const float4 hi = __ldg(&a.sc.nodes[2 * i + 1]);
-                const int esc = __float_as_int(lo.w);
-                const int tri = __float_as_int(hi.w);
+                const int esc = SA_ESC(__float_as_int(lo.w), i, a.sc.n_nodes, sa::CK_CONTRIB_ESCAPE);
+                const int tri = SA_LEAF(__float_as_int(hi.w), a.sc.T, sa::CK_CONTRIB_LEAF);
                 const bool in = hit_box(o, s.ix, s.iy, s.iz, lo, hi);
                 if (tri >= 0) {
                     if (in) {
@@ -299,7 +300,7 @@ k_building_contribution(ContribArgs a) {
                         const float4 tc = __ldg(&a.sc.tris[3 * tri + 2]);
                         const PluckerTri pt = plucker_setup(o, ta, tb, tc);
                         if (plucker_hit(pt, s.dx, s.dy, s.dz, kGroundTmin)) {
-                            const int bid = __float_as_int(ta.w);
+                            const int bid = (int)SA_CHK(__float_as_int(ta.w), a.n_b, sa::CK_CONTRIB_BUILDING);
                             int e = 0;
                             while (e < n_ids && ids[e * 32 + lane] != bid) ++e;
                             if (e == n_ids) {
@@ -384,7 +385,7 @@ cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, 
         ca.bx0 = (int)fx0; ca.by0 = (int)fy0;
         ca.bnx = (int)fx1 - (int)fx0 + 1; ca.bny = (int)fy1 - (int)fy0 + 1;
         ca.poly = dp; ca.n = n;
-        ca.cast_cnt = cnt; ca.near_cnt = cnt + B; ca.stats = cnt + 2 * B;
+        ca.cast_cnt = cnt; ca.near_cnt = cnt + B; ca.stats = cnt + 2 * B; ca.n_b = B;
         const long long warps = (long long)((ca.bnx + 7) / 8) * ((ca.bny + 3) / 4);
         {
             KernelTimer kt(KT_CONTRIB, st);

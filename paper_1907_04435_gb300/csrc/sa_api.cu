@@ -822,7 +822,7 @@ static sa_status run_method(const sa_scene* scene, const sa_receivers* recv, con
     }
     if (run) cudaFreeAsync(run, st);
     if (e != cudaSuccess) return cuda_fail(e, who);
-    return SA_OK;
+    return sa::check_after_call(st, who);
 }
 
 sa_status sa_accumulate(const sa_scene* scene, const sa_receivers* recv, const sa_sun* sun,
@@ -980,7 +980,7 @@ done:
 #undef TRY
     if (status != SA_OK) return status;
     if (e != cudaSuccess) return cuda_fail(e, who);
-    return SA_OK;
+    return sa::check_after_call(st, who);
 }
 
 sa_status sa_height_grad(const sa_scene* scene, const sa_receivers* grid, const sa_sun* sun,
@@ -1000,7 +1000,7 @@ sa_status sa_height_grad(const sa_scene* scene, const sa_receivers* grid, const 
     cudaError_t e = sa::launch_height_grad(dev_scene(scene), scene->fs, scene->d_heights, dev_recv(grid), dsun,
                                            step_minutes, weights, dS_dh, S_out, as_stream(stream));
     if (e != cudaSuccess) return cuda_fail(e, who);
-    return SA_OK;
+    return sa::check_after_call(as_stream(stream), who);
 }
 
 sa_status sa_building_contribution(const sa_scene* scene, const sa_receivers* grid,
@@ -1049,6 +1049,8 @@ sa_status sa_building_contribution(const sa_scene* scene, const sa_receivers* gr
                                                      scene->n_buildings, poly_xy, n, casting, nearest, h,
                                                      as_stream(stream));
     if (e != cudaSuccess) return cuda_fail(e, who);
+    const sa_status chk = sa::check_after_call(as_stream(stream), who);
+    if (chk != SA_OK) return chk;
     if (stats) {
         stats[0] = (int64_t)h[0];
         stats[1] = (int64_t)h[1];

@@ -348,7 +348,7 @@ sa_status sa_batch_run(sa_batch* b, int32_t* counts, int32_t* impact, void* stre
     }
     e = cudaGraphLaunch(b->exec, st);
     if (e != cudaSuccess) return sa::report_error(SA_ERR_CUDA, cudaGetErrorString(e));
-    return SA_OK;
+    return sa::check_after_call(st, "sa_batch_run");
 }
 
 // Launch shape: 2, 3 or 4 persistent CTAs per SM and 8, 16 or 24 steps per raster run,

@@ -43,4 +43,7 @@ struct sa_receivers {
 namespace sa {
 // Records `msg` as the calling thread's last error and returns `s`.
 sa_status report_error(sa_status s, const char* msg);
+// In the bounds-checked build: synchronise `st` and turn a recorded out-of-range index into
+// SA_ERR_INTERNAL (naming `who`, the site, the index and its bound); SA_OK otherwise.
+sa_status check_after_call(cudaStream_t st, const char* who);
 }  // namespace sa

@@ -74,8 +74,8 @@ __device__ int nearest_sources(const DevScene& sc, const float3& o, const StepCo
     while (i < sc.n_nodes && __any_sync(kFull, active)) {
         const float4 lo = __ldg(&sc.nodes[2 * i]);
         const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
-        const int esc = __float_as_int(lo.w);
-        const int tri = __float_as_int(hi.w);
+        const int esc = SA_ESC(__float_as_int(lo.w), i, sc.n_nodes, sa::CK_IAM_ESCAPE);
+        const int tri = SA_LEAF(__float_as_int(hi.w), sc.T, sa::CK_IAM_LEAF);
         const float bound = n < L ? 3.4e38f : best[L - 1];
         const bool in = active && hit_box_before(o, s, lo, hi, bound);
         if (tri >= 0) {

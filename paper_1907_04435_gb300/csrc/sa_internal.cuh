@@ -14,6 +14,71 @@
 
 namespace sa {
 
+// ------------------------------------------------------------- bounds-checked build
+// Built with -DSA_CHECKED, the kernels range-check every index they take from data (a
+// BVH leaf's triangle, an escape link, a binned triangle or receiver, a permutation
+// entry, a tile cell) before using it.  The first index out of range is recorded in a
+// device word of its translation unit -- the site, the index and its bound -- and replaced
+// by an index in range (an escape link by the end of the list), so that no access leaves
+// its buffer and no loop runs on; the public calls then return SA_ERR_INTERNAL.  Without
+// the flag the checks compile to nothing.
+enum CheckSite {
+    CK_NONE = 0, CK_TRACE_LEAF, CK_TRACE_ESCAPE, CK_RASTER_BIN, CK_RASTER_CELL, CK_BIN_SLOT,
+    CK_POINTS_TRI, CK_POINTS_RECV, CK_POINTS_PERM, CK_POINTS_MASK, CK_CONTRIB_LEAF,
+    CK_CONTRIB_ESCAPE, CK_CONTRIB_BUILDING, CK_IAM_LEAF, CK_IAM_ESCAPE, CK_ADJ_LEAF,
+    CK_ADJ_ESCAPE, CK_SITES
+};
+const char* check_site_name(int site);
+// Reader of one translation unit's word: copies [site, index, bound] into w and, if a
+// violation is recorded and reset != 0, clears it.
+typedef cudaError_t (*CheckReader)(unsigned long long* w, int reset);
+int register_check_reader(CheckReader r);
+// The first recorded violation over all translation units (w[0] = 0: none); clears them.
+cudaError_t read_check_words(unsigned long long* w);
+
+}  // namespace sa
+
+#ifdef SA_CHECKED
+namespace {
+__device__ unsigned long long g_sa_check[3];
+__device__ __forceinline__ long long sa_checked_index(long long i, long long n, int site) {
+    if (i >= 0 && i < n) return i;
+    if (atomicCAS(&g_sa_check[0], 0ull, (unsigned long long)site) == 0ull) {
+        g_sa_check[1] = (unsigned long long)i;
+        g_sa_check[2] = (unsigned long long)n;
+    }
+    return 0;
+}
+__device__ __forceinline__ int sa_checked_escape(int esc, int i, int n, int site) {
+    if (esc > i && esc <= n) return esc;
+    if (atomicCAS(&g_sa_check[0], 0ull, (unsigned long long)site) == 0ull) {
+        g_sa_check[1] = (unsigned long long)(long long)esc;
+        g_sa_check[2] = (unsigned long long)(long long)n;
+    }
+    return n;
+}
+cudaError_t sa_read_check_tu(unsigned long long* w, int reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(w, g_sa_check, sizeof(unsigned long long) * 3);
+    if (e == cudaSuccess && reset && w[0]) {
+        const unsigned long long z[3] = {0ull, 0ull, 0ull};
+        e = cudaMemcpyToSymbol(g_sa_check, z, sizeof(z));
+    }
+    return e;
+}
+const int g_sa_check_registered = sa::register_check_reader(&sa_read_check_tu);
+}  // namespace
+// index i checked against [0, n); an escape link checked against (i, n]
+#define SA_CHK(i, n, site) sa_checked_index((long long)(i), (long long)(n), (int)(site))
+#define SA_ESC(esc, i, n, site) sa_checked_escape((esc), (i), (n), (int)(site))
+#else
+#define SA_CHK(i, n, site) (i)
+#define SA_ESC(esc, i, n, site) (esc)
+#endif
+// a node's triangle: -1 for an inner node, else checked against [0, T)
+#define SA_LEAF(tri, T, site) ((tri) < 0 ? (tri) : (int)SA_CHK((tri), (T), (site)))
+
+namespace sa {
+
 // Stream-ordered scratch from the library's own memory pool (one per device, created on
 // first use).  The pool keeps up to 4 GiB reserved across synchronisations, so calls that
 // repeat do not map and unmap their scratch every time; free with cudaFreeAsync.

@@ -100,5 +100,5 @@ extern "C" sa_status sa_accumulate_grid_noalloc(const sa_scene* scene, const sa_
                                 "sa_accumulate_grid_noalloc: one block's triangle-tile bins do not fit the "
                                 "fixed scratch (no output was written); use a shorter block_len, a smaller "
                                 "grid or sa_accumulate");
-    return SA_OK;
+    return sa::check_after_call(st, "sa_accumulate_grid_noalloc");
 }

@@ -384,10 +384,10 @@ __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int 
         const int r = r0 + j, col = cj + (idx - ex);
         // a cell already shadowed at every step the unit could set has nothing to
         // gain (a stale read only skips less)
-        if ((sm.mask[r * kTile + col] & can) == can) continue;
+        if ((sm.mask[SA_CHK(r * kTile + col, kTile * kTile, sa::CK_RASTER_CELL)] & can) == can) continue;
         if (COUNT) { ++n_cell; n_test += kn; }
         const unsigned hit = cell_steps<CULL>(sm, E0, E1, E2, sm.xl[col], sm.yl[r], k0, kn, fr, bk);
-        if (hit) atomicOr(&sm.mask[r * kTile + col], (unsigned long long)hit << k0);
+        if (hit) atomicOr(&sm.mask[SA_CHK(r * kTile + col, kTile * kTile, sa::CK_RASTER_CELL)], (unsigned long long)hit << k0);
     }
 }
 
@@ -546,8 +546,10 @@ k_raster(RasterArgs ra) {
         const unsigned cnt = ra.counts[(size_t)bl * n_tiles + tile];
         const int* bins = ra.bins + off;
         const float4* tris = ra.sc.tris;
-        auto fetch = [bins, tris](int i, int v, float4* out) {
-            *out = __ldg(&tris[3 * bins[i] + v]);
+        const int T = ra.sc.T;
+        auto fetch = [bins, tris, T](int i, int v, float4* out) {
+            *out = __ldg(&tris[3 * SA_CHK(bins[i], T, sa::CK_RASTER_BIN) + v]);
+            (void)T;
             return true;
         };
         raster_block<COUNT, CULL>(sm, fetch, (int)cnt, ra.sun.steps, bcp->j0, bcp->K, tox, toy,

@@ -302,7 +302,7 @@ k_sam_tile(TileArgs ta) {
         const int nt = (int)min((unsigned)kTriChunk, tcnt - base);
         __syncthreads();
         for (int i = threadIdx.x; i < nt; i += kTileThreads) {
-            const int t = ta.t_bins[ta.t_off[tile] + base + i];
+            const int t = (int)SA_CHK(ta.t_bins[ta.t_off[tile] + base + i], ta.sc.T, sa::CK_POINTS_TRI);
             const float4 a = __ldg(&ta.sc.tris[3 * t]), b = __ldg(&ta.sc.tris[3 * t + 1]),
                          c = __ldg(&ta.sc.tris[3 * t + 2]);
             s_tri[3 * i] = a; s_tri[3 * i + 1] = b; s_tri[3 * i + 2] = c;
@@ -323,7 +323,7 @@ k_sam_tile(TileArgs ta) {
         for (unsigned r0 = (unsigned)warp * 32u; r0 < rcnt; r0 += kTileThreads) {
             const unsigned i = r0 + lane;
             const bool live = i < rcnt;
-            const int s = live ? ta.r_bins[ta.r_off[tile] + i] : -1;
+            const int s = live ? (int)SA_CHK(ta.r_bins[ta.r_off[tile] + i], ta.R, sa::CK_POINTS_RECV) : -1;
             const float4 p = live ? ta.orig[s] : make_float4(0.f, 0.f, 0.f, 0.f);
             s_o[threadIdx.x] = p;
             s_m[threadIdx.x] = 0u;
@@ -481,7 +481,7 @@ __global__ void k_points_fold(long long R, const int* __restrict__ perm,
                               int* __restrict__ run, int* __restrict__ best, int first, int last) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= R) return;
-    const long long r = perm[s];
+    const long long r = SA_CHK(perm[s], R, sa::CK_POINTS_PERM);
     RunState st{0, 0, 0};
     if (!first || out.accumulate_into) {
         st.gross = out.gross[r];

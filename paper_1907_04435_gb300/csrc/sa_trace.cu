@@ -94,8 +94,8 @@ __device__ __forceinline__ bool any_hit_packet(const DevScene& sc, const float3&
     while (live != 0u && i < sc.n_nodes) {
         const float4 lo = __ldg(&sc.nodes[2 * i]);
         const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
-        const int esc = __float_as_int(lo.w);
-        const int tri = __float_as_int(hi.w);
+        const int esc = SA_ESC(__float_as_int(lo.w), i, sc.n_nodes, sa::CK_TRACE_ESCAPE);
+        const int tri = SA_LEAF(__float_as_int(hi.w), sc.T, sa::CK_TRACE_LEAF);
         const bool in = want && !hit && hit_box(o, s.ix, s.iy, s.iz, lo, hi);
         if (COUNT && want && !hit) ++n_box;
         if (tri >= 0) {
@@ -232,8 +232,8 @@ k_accrual(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
         while (live != 0u && i < sc.n_nodes) {
             const float4 lo = __ldg(&sc.nodes[2 * i]);
             const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
-            const int esc = __float_as_int(lo.w);
-            const int tri = __float_as_int(hi.w);
+            const int esc = SA_ESC(__float_as_int(lo.w), i, sc.n_nodes, sa::CK_TRACE_ESCAPE);
+            const int tri = SA_LEAF(__float_as_int(hi.w), sc.T, sa::CK_TRACE_LEAF);
             const bool want = r.active && m != full;
             const bool in = want && (wedge ? fan_box(r.o, bc, lo, hi, front, r.n) : slope_box(r.o, bc, lo, hi));
             if (COUNT && want) ++n_box;
@@ -312,11 +312,11 @@ k_accrual_lane(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
             while (i < sc.n_nodes) {
                 lo = __ldg(&sc.nodes[2 * i]);
                 hi = __ldg(&sc.nodes[2 * i + 1]);
-                const int esc = __float_as_int(lo.w);
+                const int esc = SA_ESC(__float_as_int(lo.w), i, sc.n_nodes, sa::CK_TRACE_ESCAPE);
                 const bool in = wedge ? fan_box(r.o, bc, lo, hi) : slope_box(r.o, bc, lo, hi);
                 if (COUNT) ++n_box;
                 if (!in) { i = esc; continue; }
-                tri = __float_as_int(hi.w);
+                tri = SA_LEAF(__float_as_int(hi.w), sc.T, sa::CK_TRACE_LEAF);
                 if (tri >= 0) { i = esc; break; }
                 i = i + 1;
             }
@@ -359,8 +359,8 @@ k_sweep_lane(DevScene sc, DevRecv rc, DevSun sun, DevOut out) {
             while (i < sc.n_nodes && !hit) {
                 const float4 lo = __ldg(&sc.nodes[2 * i]);
                 const float4 hi = __ldg(&sc.nodes[2 * i + 1]);
-                const int esc = __float_as_int(lo.w);
-                const int tri = __float_as_int(hi.w);
+                const int esc = SA_ESC(__float_as_int(lo.w), i, sc.n_nodes, sa::CK_TRACE_ESCAPE);
+                const int tri = SA_LEAF(__float_as_int(hi.w), sc.T, sa::CK_TRACE_LEAF);
                 if (COUNT) ++n_box;
                 if (!hit_box(r.o, s.ix, s.iy, s.iz, lo, hi)) { i = esc; continue; }
                 if (tri < 0) { i = i + 1; continue; }

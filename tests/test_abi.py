@@ -166,3 +166,21 @@ def test_binding_reaches_every_declared_entry_point():
     missing = [n for n in sorted(declared_symbols())
                if f"L.{n}" not in src and f"lib().{n}" not in src and f"_lib.{n}" not in src]
     assert not missing, missing
+
+
+def test_checked_build_exports_the_same_calls_and_says_so():
+    """The bounds-checked variant is built beside the plain library (nvcc cross-compiles
+    here), exports every declared call and reports itself; the plain build reports no
+    check and its status call needs no device."""
+    from paper_1907_04435_gb300 import build as b
+    path = b.build(checked=True)
+    Lc = ct.CDLL(path)
+    for n in sorted(declared_symbols()):
+        assert hasattr(Lc, n), f"missing export {n}"
+    assert Lc.sa_checked_build() == 1
+    from paper_1907_04435_gb300 import binding as B
+    Lp = B.lib()
+    assert Lp.sa_checked_build() == 0
+    site, idx, bound = ct.c_int32(7), ct.c_int64(7), ct.c_int64(7)
+    assert Lp.sa_check_status(ct.byref(site), ct.byref(idx), ct.byref(bound)) == 0
+    assert (site.value, idx.value, bound.value) == (0, 0, 0)
