@@ -9,8 +9,12 @@ ray sweep, per-step raster) are timed on the same workload and reported beside i
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 
-Under torchrun every rank runs its own copy of the workload (independent problems, no
-collective): weak scaling, value = all ranks' receiver-steps / slowest rank's time.
+Under torchrun (`--multi problems`, the default) every rank accumulates a district of its
+own (the same distribution, its own seed): independent problems, no data collective, weak
+scaling, value = all ranks' receiver-steps / the slowest rank's time.  `--multi shard`
+splits one district's receivers instead (bands of grid rows, ranges of facade points; the
+scene and its BVH on every rank) and gathers the results on rank 0: strong scaling, value
+= the district's receiver-steps / the slowest rank's time.
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -105,10 +109,12 @@ def weak_scaling_value(units_per_rank: int, world: int, ms_max: float) -> float:
 
 
 # ------------------------------------------------------------------------ workload
-def make_workload(name: str):
+def make_workload(name: str, rank: int = 0):
+    """The named workload; under `--multi problems` rank r > 0 takes a district of its own
+    (the same distribution, its own seed: an independent problem, not a copy)."""
     from synth import configs
     if name == "district":
-        return configs.district()
+        return configs.district(seed_off=2 + 1000 * rank) if rank else configs.district()
     if name == "district_1k":
         # the district's city with a 1024 x 1024 ground grid over its centre and 250k
         # facade samples: a quarter-size case for detailed profiles
@@ -166,6 +172,57 @@ def cpu_oracle_sample(w, seconds_hint: float = 15.0, seed: int = 0):
             "seconds": el}
 
 
+def cpu_oracle_configs(seconds_each: float = 4.0):
+    """The FP64 oracle on the other workloads, each on a bounded seeded sample: the 16-box
+    sweep case in full, the season (50,000 buildings; its first day), one batched variant
+    (its region, the first day of the summer interval), and the park (all steps)."""
+    import oracle
+    from synth import configs
+    rng = np.random.default_rng(5)
+    out = {}
+
+    cores = oracle.default_threads()
+
+    def timed_sample(t9, tb, pos, dirs, label, full=False, steps_note="all"):
+        # calibrate on two receivers per thread, then size the sample to ~seconds_each
+        n = pos.shape[0] if full else min(pos.shape[0], 2 * cores)
+        t0 = time.perf_counter()
+        oracle.shadow_bits(t9, tb, pos[:n], None, dirs)
+        dt = max(time.perf_counter() - t0, 1e-4)
+        if not full:
+            n = int(max(n, min(pos.shape[0], n * seconds_each / dt)))
+            t0 = time.perf_counter()
+            oracle.shadow_bits(t9, tb, pos[:n], None, dirs)
+            dt = time.perf_counter() - t0
+        return {"value": n * dirs.shape[0] / dt, "unit": UNIT, "cores": cores,
+                "kind": "oracle", "seconds": dt,
+                "sample": f"{n} {label} receivers x {steps_note} {dirs.shape[0]} steps"
+                          + ("" if full else " (seeded uniform sample)")}
+
+    def first_day(sun):
+        return sun.dirs[int(sun.day_start[0]):int(sun.day_start[1])]
+
+    w = configs.boxes16()
+    out["boxes16"] = timed_sample(w.mesh.tri9(), w.mesh.tri_building, w.ground.positions(),
+                                  w.sun.dirs, "ground (every cell)", full=True)
+    w = configs.season()
+    pos = w.ground.positions()[rng.choice(w.ground.R, 2000, replace=False)]
+    out["season"] = timed_sample(w.mesh.tri9(), w.mesh.tri_building, pos, first_day(w.sun), "ground",
+                                 steps_note="the first day's")
+    sc = configs.scenarios(n_variants=1, days=31)
+    t9, tb = sc.variant_mesh(0)
+    ix0, iy0, nx, ny = (int(x) for x in sc.regions[0])
+    gg = sc.base.ground
+    loc = rng.choice(nx * ny, 2000, replace=False)
+    pos = gg.positions()[(iy0 + loc // nx) * gg.nx + (ix0 + loc % nx)]
+    out["batch_variant"] = timed_sample(t9, tb, pos, first_day(sc.intervals[1]), "variant-region ground",
+                                        steps_note="the first day's")
+    w = configs.park()
+    pos = w.ground.positions()[rng.choice(w.ground.R, 20000, replace=False)]
+    out["park"] = timed_sample(w.mesh.tri9(), w.mesh.tri_building, pos, w.sun.dirs, "park")
+    return out
+
+
 # ------------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -181,17 +238,26 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    w = make_workload(args.workload)
+    sharded = world > 1 and args.multi == "shard"
+    w = make_workload(args.workload, rank if (world > 1 and not sharded) else 0)
     st = w.sun
     # resident inputs
     # the synthetic buildings are closed, outward-wound prisms
     scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
     sun = B.Sun(st.dirs, st.day_start, args.block_len)
     g = w.ground
-    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
-    fac = B.Receivers.points(w.facade_pos, w.facade_nrm) if w.facade_pos is not None else None
+    if sharded:
+        from paper_1907_04435_gb300 import shard
+        bx0, by0, bdx, bnx, brows, _ = shard.grid_band((g.x0, g.y0, g.dx, g.nx, g.ny), rank, world)
+        grid = B.Receivers.ground_grid(bx0, by0, bdx, bnx, brows)
+        fa, fb = shard.split(0 if w.facade_pos is None else w.facade_pos.shape[0], rank, world)
+        fac = B.Receivers.points(w.facade_pos[fa:fb], w.facade_nrm[fa:fb]) if fb > fa else None
+    else:
+        grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+        fac = B.Receivers.points(w.facade_pos, w.facade_nrm) if w.facade_pos is not None else None
     R = grid.R + (fac.R if fac else 0)
     units = R * st.S
+    job_units = w.R * st.S if sharded else world * units
     out_g = [torch.zeros(grid.R, dtype=torch.int32, device=dev),
              torch.empty(grid.R, dtype=torch.float32, device=dev),
              torch.zeros(grid.R, dtype=torch.int32, device=dev)]
@@ -261,7 +327,17 @@ def run_gpu(args):
     if world > 1:
         ms = slowest_rank_ms(ms, dist, dev)
         dist.barrier()
-    value = weak_scaling_value(units, world, ms)
+    value = job_units / (ms * 1e-3)
+    gathered = None
+    if sharded:
+        from paper_1907_04435_gb300 import shard
+        parts = [t.cpu().numpy() for t in out_g] + ([t.cpu().numpy() for t in out_f] if fac else
+                                                    [np.zeros(0, np.int32), np.zeros(0, np.float32),
+                                                     np.zeros(0, np.int32)])
+        got = shard.gather_to_root(parts, dist)
+        if rank == 0:
+            gathered = {"ground_receivers": int(got[0].size), "facade_receivers": int(got[3].size),
+                        "gross_sum": int(got[0].sum()) + int(got[3].sum())}
 
     # ---- per-step baselines and the other exact method on the same workload
     methods = {"accrual_sam": {"ms": ms, "ground_ms": ms_g, "facade_ms": ms_f,
@@ -291,8 +367,10 @@ def run_gpu(args):
     # ---- roofline of the dominant kernel (instrumented work counters)
     roof, roof_all = roofline(B, scene, grid, fac, sun, ktimes, args.steps, args.workload)
 
-    # ---- end to end through the C ABI from host buffers
-    e2e = end_to_end(B, w, args, dev)
+    # ---- end to end through the C ABI from host buffers (a rank's own district; the split
+    # mode reports its device-timed value only)
+    e2e = (end_to_end(B, w, args, dev) if not sharded else
+           {"value": None, "unit": UNIT, "note": "not measured when one district is split"})
 
     # ---- batched scenarios (development variants x seasonal intervals)
     batch = None if args.skip_batch else bench_batch(B, w, args)
@@ -319,17 +397,21 @@ def run_gpu(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if sharded else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(args, w),
                            method="accrual_sam: ground accrual raster + facade light-space accrual map",
                            l2="flushed (256 MB write) before every timed iteration",
-                           parallelism=f"replicas x{world}"),
+                           parallelism=(f"receivers split over {world} ranks, gathered on rank 0"
+                                        if sharded else f"independent districts x{world}"
+                                        if world > 1 else "one GPU")),
             "methods": methods,
             "roofline": roof,
             "roofline_kernels": roof_all,
             "e2e": e2e,
             "gpu_launches": count_launches(scene, sun, grid, fac),
+            "gathered": gathered,
             "batch": batch,
             "other_workloads": other,
             "analysis": analysis,
@@ -337,6 +419,8 @@ def run_gpu(args):
         }
         if world == 1 and not args.skip_cpu:
             line["cpu_baseline"] = cpu_oracle_sample(w, args.cpu_seconds)
+            if not args.skip_configs:
+                line["cpu_baseline_other_workloads"] = cpu_oracle_configs()
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -765,6 +849,8 @@ def main():
     ap.add_argument("--batch-variants", type=int, default=8)
     ap.add_argument("--batch-days", type=int, default=31)
     ap.add_argument("--baseline-steps", dest="baseline_steps", type=int, default=5)
+    ap.add_argument("--multi", default="problems", choices=["problems", "shard"],
+                    help="under torchrun: a district per rank (weak) or one district split (strong)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":
