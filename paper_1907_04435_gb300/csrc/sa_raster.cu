@@ -208,6 +208,9 @@ struct TileSmem {
     float4 d[kMaxBlock];                     // step directions
     float4 ubox[kMaxBlock];                  // per run: (min u.x, max u.x, min u.y, max u.y)
     unsigned long long mask[kTile * kTile];
+    // per warp: cells waiting for their step tests, (unit << 10) | cell, drained 32 at a
+    // time so that every lane tests a cell whichever unit it comes from
+    unsigned queue[kRasterThreads / 32][64];
     float xl[kTile], yl[kTile];
     int next_unit;                           // next work unit of the batch to hand out
     float inv_nsub;                          // 1 / runs of the block
@@ -274,12 +277,39 @@ __device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeRef
     return CULL ? (hf & fr) : ((hf & fr) | (hb & bk));
 }
 
+// Step tests of up to 32 queued cells, one per lane: each item names its work unit
+// (triangle of the staged batch and run of the block) and its cell; the unit's run, its
+// facing steps and the triangle's canonical edges are read back from shared memory.
+template <bool COUNT, bool CULL>
+__device__ __forceinline__ void drain_cells(TileSmem& sm, const unsigned* q, int n, int nsub,
+                                            unsigned long long& n_cell,
+                                            unsigned long long& n_test) {
+    const int lane = threadIdx.x & 31;
+    if (lane >= n) return;
+    const unsigned item = q[lane];
+    const int un = (int)(item >> 10), cell = (int)(item & 1023u);
+    const int t = (int)(((float)un + 0.5f) * sm.inv_nsub), sub = un - t * nsub;
+    const int k0 = sm.run_k0[sub], kn = sm.run_k0[sub + 1] - k0;
+    const unsigned run_bits = (kn >= 32) ? 0xffffffffu : ((1u << kn) - 1u);
+    const unsigned fr = (unsigned)(sm.front[t] >> k0) & run_bits;
+    const unsigned bk = CULL ? 0u : ((unsigned)(sm.back[t] >> k0) & run_bits);
+    const float4* ef = reinterpret_cast<const float4*>(&sm.edges[20 * t]);
+    const float4 f0 = ef[0], f1 = ef[1], f2 = ef[2], f3 = ef[3], f4 = ef[4];
+    const EdgeRef E0{f0.x, f0.y, f0.z, f0.w, f1.x, f1.y};
+    const EdgeRef E1{f1.z, f1.w, f2.x, f2.y, f2.z, f2.w};
+    const EdgeRef E2{f3.x, f3.y, f3.z, f3.w, f4.x, f4.y};
+    if (COUNT) { ++n_cell; n_test += kn; }
+    const unsigned hit = cell_steps<CULL>(sm, E0, E1, E2, sm.xl[cell & (kTile - 1)],
+                                          sm.yl[cell >> 5], k0, kn, fr, bk);
+    if (hit) atomicOr(&sm.mask[SA_CHK(cell, kTile * kTile, sa::CK_RASTER_CELL)], (unsigned long long)hit << k0);
+}
+
 // One work unit: triangle t of the staged batch and run `sub` of the block.  The warp
 // bounds the run's swept projection, enumerates the covered cells row by row and tests
 // the run's steps per cell; step bits are ORed into sm.mask.
 template <bool COUNT, bool CULL>
 __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int K,
-                                            float inv_dx, unsigned long long& n_cell,
+                                            float inv_dx, int& qn, unsigned long long& n_cell,
                                             unsigned long long& n_test,
                                             unsigned long long& n_unit,
                                             unsigned long long& n_span) {
@@ -308,11 +338,6 @@ __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int 
         fc0 > fc1 || fr0 > fr1) return;
     const int c0 = (int)fmaxf(fc0, 0.f), c1 = (int)fminf(fc1, (float)(kTile - 1));
     const int r0 = (int)fmaxf(fr0, 0.f), r1 = (int)fminf(fr1, (float)(kTile - 1));
-    const float4* ef = reinterpret_cast<const float4*>(&sm.edges[20 * t]);
-    const float4 f0 = ef[0], f1 = ef[1], f2 = ef[2], f3 = ef[3], f4 = ef[4];
-    const EdgeRef E0{f0.x, f0.y, f0.z, f0.w, f1.x, f1.y};
-    const EdgeRef E1{f1.z, f1.w, f2.x, f2.y, f2.z, f2.w};
-    const EdgeRef E2{f3.x, f3.y, f3.z, f3.w, f4.x, f4.y};
     // Row spans.  Each step's projection lies inside the projection for the run's
     // middle slope u_m widened by (sx, sy) = z_max |u_hi - u_lo| / 2 (a vertex at
     // height z moves by z (u_m - u_k)).  Lane j takes row r0 + j: the x-range of the
@@ -370,6 +395,7 @@ __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int 
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     if (COUNT && lane == 0) { ++n_unit; n_span += (unsigned long long)total; }
     const int excl = incl - w;
+    unsigned* q = sm.queue[threadIdx.x >> 5];
     for (int base = 0; base < total; base += 32) {
         const int idx = base + lane;
         int j = 0;
@@ -380,14 +406,20 @@ __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int 
         }
         const int ex = __shfl_sync(0xffffffffu, excl, j & 31);
         const int cj = __shfl_sync(0xffffffffu, cs, j & 31);
-        if (idx >= total) continue;
-        const int r = r0 + j, col = cj + (idx - ex);
-        // a cell already shadowed at every step the unit could set has nothing to
-        // gain (a stale read only skips less)
-        if ((sm.mask[SA_CHK(r * kTile + col, kTile * kTile, sa::CK_RASTER_CELL)] & can) == can) continue;
-        if (COUNT) { ++n_cell; n_test += kn; }
-        const unsigned hit = cell_steps<CULL>(sm, E0, E1, E2, sm.xl[col], sm.yl[r], k0, kn, fr, bk);
-        if (hit) atomicOr(&sm.mask[SA_CHK(r * kTile + col, kTile * kTile, sa::CK_RASTER_CELL)], (unsigned long long)hit << k0);
+        const int cell = (r0 + j) * kTile + cj + (idx - ex);
+        // a cell already shadowed at every step the unit could set has nothing to gain
+        // (a stale read only skips less); the others join the warp's queue
+        const bool need = idx < total &&
+                          (sm.mask[SA_CHK(cell, kTile * kTile, sa::CK_RASTER_CELL)] & can) != can;
+        const unsigned bal = __ballot_sync(0xffffffffu, need);
+        if (need) q[qn + __popc(bal & ((1u << lane) - 1u))] = ((unsigned)un << 10) | (unsigned)cell;
+        qn += __popc(bal);
+        if (qn >= 32) {
+            __syncwarp();
+            drain_cells<COUNT, CULL>(sm, q + (qn - 32), 32, nsub, n_cell, n_test);
+            qn -= 32;
+            __syncwarp();
+        }
     }
 }
 
@@ -481,12 +513,17 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
         // warps that would otherwise wait for its warp at the next barrier
         // (the next unit is claimed before this one is worked, hiding the atomic's latency)
         int un = warp;
+        int qn = 0;
         while (un < units) {
             int nx = 0;
             if (lane == 0) nx = atomicAdd(&sm.next_unit, 1);
-            raster_unit<COUNT, CULL>(sm, un, nsub, K, inv_dx, n_cell, n_test, n_unit, n_span);
+            raster_unit<COUNT, CULL>(sm, un, nsub, K, inv_dx, qn, n_cell, n_test, n_unit, n_span);
             un = __shfl_sync(0xffffffffu, nx, 0);
         }
+        // the queue's last cells, before the batch's triangles are replaced
+        __syncwarp();
+        drain_cells<COUNT, CULL>(sm, sm.queue[warp], qn, nsub, n_cell, n_test);
+        __syncwarp();
     }
     __syncthreads();
 }
