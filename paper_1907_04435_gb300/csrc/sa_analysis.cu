@@ -106,11 +106,11 @@ __global__ void k_shadow_score(const int* __restrict__ steps, long long R, int n
 // these partition the region's shadowed cell-steps -- except the ones the raster marks
 // shadowed whose FP32 ray grazes past every triangle (shadow edges), counted apart.
 //
-// One warp takes an 8 x 4 patch of the region's cells and walks, for each run of <= 32
-// consecutive steps of a block, the depth-first node list once with the fan of the run's
-// rays as its query (as the ray-traced accrual does): every triangle in the fan is tested
-// exactly (Plucker form, with its distance) against the lane's shadowed steps it can
-// reach.  Per lane and step the nearest hit (distance, building) is kept in shared
+// A first pass lists, per run of <= 32 consecutive steps of a block, the region's cells
+// with a shadowed step in it.  One warp then takes 32 listed cells of one run and walks
+// the depth-first node list once with the fan of the run's rays as its query (as the
+// ray-traced accrual does): every triangle in the fan is tested exactly (Plucker form,
+// with its distance) against the lane's shadowed steps it can reach.  Per lane and step the nearest hit (distance, building) is kept in shared
 // memory, and per lane and run a short list of (building, steps met) pairs; a lane whose
 // run meets more buildings than the list holds counts its casting again ray by ray, with
 // a list of kRayList buildings per ray.  Counts are integers, credited by atomics on
@@ -136,6 +136,11 @@ struct ContribArgs {
     unsigned long long* near_cnt;     // [B]
     unsigned long long* stats;        // [2]
     int n_b;                          // buildings (length of the counters)
+    // compacted work: per run, the cells with a shadowed step in it (global cell index)
+    const int* items;                 // run r's cells at item0[r] .. item0[r] + n_items[r]
+    const unsigned* item0;            // [n_runs]
+    const unsigned* n_items;          // [n_runs]
+    const int* warp_base;             // [n_runs + 1] first warp of each run
 };
 
 struct ContribWarpSmem {
@@ -155,30 +160,63 @@ __device__ __forceinline__ bool plucker_hit_t(const PluckerTri& p, const StepCon
     return true;
 }
 
+// Work list of the fan traversal: per run, the region's cells with at least one shadowed
+// step in it, in patch order (8 x 4 cells per patch, patches row by row), so that the 32
+// cells a traversal warp takes stay close together.  Cells shadowed at no step of a run
+// cost nothing there.  Two passes over the patches: counts per (run, patch), then -- after
+// an exclusive scan of the counts into offsets -- the cells themselves.
+__global__ void k_contrib_items(ContribArgs a, bool fill, unsigned* __restrict__ counts,
+                                const unsigned* __restrict__ offsets, int* __restrict__ items) {
+    const int lane = threadIdx.x & 31;
+    const int tiles_x = (a.bnx + 7) >> 3;
+    const long long n_patches = (long long)tiles_x * ((a.bny + 3) >> 2);
+    const long long warp_id = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp_id >= n_patches) return;                                  // whole warps
+    const int ty = (int)(warp_id / tiles_x), tx = (int)(warp_id - (long long)ty * tiles_x);
+    const int lx = tx * 8 + (lane & 7), ly = ty * 4 + (lane >> 3);
+    const int ix = a.bx0 + lx, iy = a.by0 + ly;
+    const float x = __fadd_rn(a.x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), a.dx));
+    const float y = __fadd_rn(a.y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), a.dx));
+    const bool in_region = lx < a.bnx && ly < a.bny && inside_polygon(a.poly, a.n, (double)x, (double)y);
+    const long long cell = (long long)iy * a.nx + ix;
+    for (int r = 0; r < a.n_runs; ++r) {
+        const BlockConst& bc = a.runs[r];
+        const unsigned run_bits = bc.K >= 32 ? 0xffffffffu : ((1u << bc.K) - 1u);
+        const bool want = in_region &&
+                          ((unsigned)(a.masks[(long long)bc.mask_block * a.R + cell] >> bc.mask_bit) & run_bits) != 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, want);
+        const long long slot = (long long)r * n_patches + warp_id;
+        if (!fill) {
+            if (lane == 0) counts[slot] = (unsigned)__popc(bal);
+        } else if (want) {
+            items[offsets[slot] + __popc(bal & ((1u << lane) - 1u))] = (int)cell;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(32 * kContribWarps)
 k_building_contribution(ContribArgs a) {
     __shared__ ContribWarpSmem s_w[kContribWarps];
     __shared__ BlockConst s_bc[kContribWarps];
     __shared__ StepConst s_st[kContribWarps][kContribRun];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int tiles_x = (a.bnx + 7) >> 3;
-    const long long warp_id = (long long)blockIdx.x * kContribWarps + wib;
-    if (warp_id >= (long long)tiles_x * ((a.bny + 3) >> 2)) return;     // whole warps
-    const int ty = (int)(warp_id / tiles_x), tx = (int)(warp_id - (long long)ty * tiles_x);
-    const int lx = tx * 8 + (lane & 7), ly = ty * 4 + (lane >> 3);
-    const int ix = a.bx0 + lx, iy = a.by0 + ly;
+    const int warp_id = (int)(blockIdx.x * kContribWarps + wib);
+    if (warp_id >= a.warp_base[a.n_runs]) return;                       // whole warps
+    int r = 0;
+    while (a.warp_base[r + 1] <= warp_id) ++r;
+    const unsigned slot = (unsigned)(warp_id - a.warp_base[r]) * 32u + (unsigned)lane;
+    const bool live = slot < a.n_items[r];
+    const long long cell = live ? (long long)SA_CHK(a.items[(long long)a.item0[r] + slot], a.R, sa::CK_CONTRIB_CELL) : 0;
+    const int ix = (int)(cell % a.nx), iy = (int)(cell / a.nx);
     float3 o;
     o.x = __fadd_rn(a.x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), a.dx));
     o.y = __fadd_rn(a.y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), a.dx));
     o.z = 0.f;
-    const bool in_region = lx < a.bnx && ly < a.bny && inside_polygon(a.poly, a.n, (double)o.x, (double)o.y);
-    const long long cell = (long long)iy * a.nx + ix;
     ContribWarpSmem& w = s_w[wib];
     BlockConst& bc = s_bc[wib];
     StepConst* ss = s_st[wib];
     unsigned long long n_graze = 0, n_over = 0;
-    for (int r = 0; r < a.n_runs; ++r) {
-        __syncwarp();
+    {
         for (int q = lane; q < (int)(sizeof(BlockConst) / 4); q += 32)
             reinterpret_cast<int*>(&bc)[q] = reinterpret_cast<const int*>(&a.runs[r])[q];
         __syncwarp();
@@ -187,9 +225,8 @@ k_building_contribution(ContribArgs a) {
             reinterpret_cast<int*>(ss)[q] = reinterpret_cast<const int*>(&a.steps[bc.j0])[q];
         const unsigned run_bits = K >= 32 ? 0xffffffffu : ((1u << K) - 1u);
         unsigned m = 0u;
-        if (in_region) m = (unsigned)(a.masks[(long long)bc.mask_block * a.R + cell] >> bc.mask_bit) & run_bits;
+        if (live) m = (unsigned)(a.masks[(long long)bc.mask_block * a.R + cell] >> bc.mask_bit) & run_bits;
         __syncwarp();
-        if (!__any_sync(0xffffffffu, m != 0u)) continue;
         for (int k = 0; k < K; ++k) w.t[k][lane] = 3.4e38f;
         int n_list = 0;
         bool ovf = false;
@@ -275,12 +312,11 @@ k_building_contribution(ContribArgs a) {
         if (!ovf) {
             for (int e = 0; e < n_list; ++e)
                 atomicAdd(&a.cast_cnt[w.cb[e][lane]], (unsigned long long)__popc(w.cm[e][lane]));
-            continue;
         }
         // more buildings than the list holds: casting again, ray by ray (each lane alone;
         // the nearest arrays, no longer needed, hold the ray's list)
         int* ids = reinterpret_cast<int*>(&w.t[0][0]);     // kRayList x 32 ints: t, then b
-        unsigned todo = m & found;
+        unsigned todo = ovf ? (m & found) : 0u;
         while (todo) {
             const int k = __ffs(todo) - 1;
             todo &= todo - 1u;
@@ -340,7 +376,8 @@ cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, 
     const size_t n_cnt = 2 * (size_t)B + 2;
     cudaError_t e = cudaSuccess;
     unsigned long long *masks = nullptr, *cnt = nullptr;
-    int *gross = nullptr, *run = nullptr;
+    int *gross = nullptr, *run = nullptr, *items = nullptr, *wbase = nullptr;
+    unsigned *pcnt = nullptr, *poff = nullptr, *runinfo = nullptr;
     double2* dp = nullptr;
     BlockConst* druns = nullptr;
     std::vector<double2> hp((size_t)n);
@@ -386,8 +423,42 @@ cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, 
         ca.bnx = (int)fx1 - (int)fx0 + 1; ca.bny = (int)fy1 - (int)fy0 + 1;
         ca.poly = dp; ca.n = n;
         ca.cast_cnt = cnt; ca.near_cnt = cnt + B; ca.stats = cnt + 2 * B; ca.n_b = B;
-        const long long warps = (long long)((ca.bnx + 7) / 8) * ((ca.bny + 3) / 4);
-        {
+        // the work lists: per run, the cells with a shadowed step in it, in patch order
+        const int nr = (int)runs.size();
+        const long long patches = (long long)((ca.bnx + 7) / 8) * ((ca.bny + 3) / 4);
+        const long long nslots = patches * nr;
+        TRY(sa::scratch_alloc(&pcnt, sizeof(unsigned) * (size_t)(nslots + 1), st));
+        TRY(sa::scratch_alloc(&poff, sizeof(unsigned) * (size_t)(nslots + 1), st));
+        TRY(sa::scratch_alloc(&wbase, sizeof(int) * (size_t)(nr + 1), st));
+        TRY(sa::scratch_alloc(&runinfo, sizeof(unsigned) * 2 * (size_t)nr, st));
+        const unsigned pblocks = (unsigned)((patches + 3) / 4);
+        k_contrib_items<<<pblocks, 128, 0, st>>>(ca, false, pcnt, nullptr, nullptr);
+        TRY(cudaGetLastError());
+        TRY(cudaMemsetAsync(pcnt + nslots, 0, sizeof(unsigned), st));
+        TRY(cudaMemcpyAsync(poff, pcnt, sizeof(unsigned) * (size_t)(nslots + 1), cudaMemcpyDeviceToDevice, st));
+        TRY(exclusive_scan_u32(poff, nslots + 1, nullptr, st));
+        // per run: its first item and its count (run r's offsets start at slot r x patches)
+        std::vector<unsigned> h_off((size_t)nr + 1);
+        for (int r = 0; r <= nr; ++r)
+            TRY(cudaMemcpyAsync(&h_off[(size_t)r], poff + (size_t)r * patches, sizeof(unsigned),
+                                cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        const unsigned total = h_off[(size_t)nr];
+        TRY(sa::scratch_alloc(&items, sizeof(int) * ((size_t)total + 1), st));
+        k_contrib_items<<<pblocks, 128, 0, st>>>(ca, true, nullptr, poff, items);
+        TRY(cudaGetLastError());
+        std::vector<unsigned> h_run(2 * (size_t)nr);
+        std::vector<int> h_base((size_t)nr + 1, 0);
+        for (int r = 0; r < nr; ++r) {
+            h_run[(size_t)r] = h_off[(size_t)r];
+            h_run[(size_t)nr + r] = h_off[(size_t)r + 1] - h_off[(size_t)r];
+            h_base[(size_t)r + 1] = h_base[(size_t)r] + (int)((h_run[(size_t)nr + r] + 31u) / 32u);
+        }
+        TRY(cudaMemcpyAsync(runinfo, h_run.data(), sizeof(unsigned) * 2 * (size_t)nr, cudaMemcpyHostToDevice, st));
+        TRY(cudaMemcpyAsync(wbase, h_base.data(), sizeof(int) * (size_t)(nr + 1), cudaMemcpyHostToDevice, st));
+        ca.items = items; ca.item0 = runinfo; ca.n_items = runinfo + nr; ca.warp_base = wbase;
+        const long long warps = h_base[(size_t)nr];
+        if (warps > 0) {
             KernelTimer kt(KT_CONTRIB, st);
             k_building_contribution<<<(unsigned)((warps + kContribWarps - 1) / kContribWarps),
                                       32 * kContribWarps, 0, st>>>(ca);
@@ -406,7 +477,8 @@ cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, 
         stats_out[1] = h_cnt[2 * (size_t)B + 1];
     }
 done:
-    for (void* p : {(void*)masks, (void*)cnt, (void*)gross, (void*)run, (void*)dp, (void*)druns})
+    for (void* p : {(void*)masks, (void*)cnt, (void*)gross, (void*)run, (void*)dp, (void*)druns,
+                    (void*)items, (void*)pcnt, (void*)poff, (void*)runinfo, (void*)wbase})
         if (p) cudaFreeAsync(p, st);
     return e;
 #undef TRY

@@ -45,7 +45,8 @@ const char* check_site_name(int site) {
         "light-space map: binned triangle", "light-space map: binned receiver",
         "light-space map: receiver permutation", "light-space map: receiver mask",
         "building contribution: leaf triangle", "building contribution: escape link",
-        "building contribution: building id", "inverse map: leaf triangle",
+        "building contribution: building id", "building contribution: listed cell",
+        "inverse map: leaf triangle",
         "inverse map: escape link", "height adjoint: leaf triangle", "height adjoint: escape link"};
     return site >= 0 && site < CK_SITES ? names[site] : "unknown";
 }

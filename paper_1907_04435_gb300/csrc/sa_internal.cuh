@@ -25,7 +25,7 @@ namespace sa {
 enum CheckSite {
     CK_NONE = 0, CK_TRACE_LEAF, CK_TRACE_ESCAPE, CK_RASTER_BIN, CK_RASTER_CELL, CK_BIN_SLOT,
     CK_POINTS_TRI, CK_POINTS_RECV, CK_POINTS_PERM, CK_POINTS_MASK, CK_CONTRIB_LEAF,
-    CK_CONTRIB_ESCAPE, CK_CONTRIB_BUILDING, CK_IAM_LEAF, CK_IAM_ESCAPE, CK_ADJ_LEAF,
+    CK_CONTRIB_ESCAPE, CK_CONTRIB_BUILDING, CK_CONTRIB_CELL, CK_IAM_LEAF, CK_IAM_ESCAPE, CK_ADJ_LEAF,
     CK_ADJ_ESCAPE, CK_SITES
 };
 const char* check_site_name(int site);
