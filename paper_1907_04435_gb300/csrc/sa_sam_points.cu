@@ -32,8 +32,15 @@ namespace {
 
 constexpr int kRunMax = 32;
 constexpr float kLightSlack = 0.05f;    // absolute slack (m) of the light-space culls (rounding)
-constexpr int kTileThreads = 128;
-constexpr int kTriChunk = 128;
+// threads per light-space tile (a multiple of 32) and triangles staged per chunk (<= 256)
+#ifndef SA_TILE_THREADS
+#define SA_TILE_THREADS 128
+#endif
+#ifndef SA_TILE_CHUNK
+#define SA_TILE_CHUNK 128
+#endif
+constexpr int kTileThreads = SA_TILE_THREADS;
+constexpr int kTriChunk = SA_TILE_CHUNK;
 // side (m) of the light-space tiles
 #ifndef SA_LIGHT_TILE
 #define SA_LIGHT_TILE 32.f
