@@ -30,7 +30,12 @@ namespace {
 
 constexpr int kTile = 32;               // cells per tile side
 constexpr int kRasterThreads = 256;     // 8 warps x 4 rows each
-constexpr int kTriBatch = 64;           // triangles staged per batch
+// triangles staged per batch (<= 128: a unit index t x runs + run stays below 2^13, which
+// the float quotient that decodes it and the queue's 13 bits for it both need)
+#ifndef SA_RASTER_BATCH
+#define SA_RASTER_BATCH 64
+#endif
+constexpr int kTriBatch = SA_RASTER_BATCH;
 // resident CTAs per SM the raster kernels are compiled for (registers: 65536 / (256 x this))
 #ifndef SA_RASTER_CTAS
 #define SA_RASTER_CTAS 4
@@ -315,7 +320,7 @@ __device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int 
                                             unsigned long long& n_span) {
     const int lane = threadIdx.x & 31;
     // un = t nsub + sub; (un + 1/2) / nsub is at least 1 / (2 nsub) from an integer, far
-    // beyond the float quotient's rounding for un < 2^12
+    // beyond the float quotient's rounding (relative 2^-23) for un < 2^13
     const int t = (int)(((float)un + 0.5f) * sm.inv_nsub), sub = un - t * nsub;
     const int k0 = sm.run_k0[sub], kn = sm.run_k0[sub + 1] - k0;       // balanced runs
     const unsigned run_bits = (kn >= 32) ? 0xffffffffu : ((1u << kn) - 1u);
@@ -462,13 +467,13 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
     for (int base = 0; base < n; base += kTriBatch) {
         const int nt = min(kTriBatch, n - base);
         __syncthreads();
-        if (threadIdx.x < nt * 3) {
+        for (int i = threadIdx.x; i < nt * 3; i += kRasterThreads) {
             float4 v;
-            const bool ok = fetch(base + threadIdx.x / 3, threadIdx.x % 3, &v);
+            const bool ok = fetch(base + i / 3, i % 3, &v);
             v.x -= tox;
             v.y -= toy;
-            sm.tri[threadIdx.x] = v;
-            if (threadIdx.x % 3 == 0) sm.valid[threadIdx.x / 3] = ok ? 1 : 0;
+            sm.tri[i] = v;
+            if (i % 3 == 0) sm.valid[i / 3] = ok ? 1 : 0;
         }
         __syncthreads();
         if (threadIdx.x == 0) sm.next_unit = kWarpsRaster;
