@@ -364,15 +364,15 @@ sa_status sa_work_counters(const sa_scene* scene, const sa_receivers* recv, cons
 int32_t sa_checked_build(void);
 sa_status sa_check_status(int32_t* site, int64_t* index, int64_t* bound);
 
-/* Statistics of the library's scratch memory (diagnostics): stats uint64 [4] host gets
- *   [0] scratch allocations the library has made since it was loaded (all devices),
+/* Statistics of the library's device memory pool (diagnostics): stats uint64 [4] host gets
+ *   [0] allocations the library has made from its pool since it was loaded (all devices),
  *   [1] their bytes, summed,
- *   [2] bytes the current device's scratch pool holds reserved (0 before its first use),
+ *   [2] bytes the current device's pool holds reserved (0 before its first use),
  *   [3] the pool's high-water mark of bytes in use.
- * Scratch is taken from a stream-ordered pool per device inside each call and returned
- * before the call ends; the pool keeps up to 4 GiB reserved between calls.  Handles
- * (scene, sun, receivers, batch) hold their own device memory, not counted here.
- * Errors: SA_ERR_INVALID_ARG (NULL). */
+ * The pool is stream-ordered, one per device.  Calls take their scratch from it and return
+ * it before they end; scenes, sun tables and point receivers keep their arrays from it
+ * until they are destroyed (a batch uses cudaMalloc).  The pool keeps up to 4 GiB
+ * reserved between calls.  Errors: SA_ERR_INVALID_ARG (NULL). */
 sa_status sa_scratch_stats(uint64_t* stats);
 
 /* --------------------------------------------------- long periods: the direction graph

@@ -155,7 +155,7 @@ template <class T>
 cudaError_t upload(const void* src, size_t n, int device_ptrs, T** dst, cudaStream_t st) {
     *dst = nullptr;
     if (n == 0) return cudaSuccess;
-    cudaError_t e = cudaMalloc(dst, sizeof(T) * n);
+    cudaError_t e = sa::scratch_alloc(dst, sizeof(T) * n, st);
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(*dst, src, sizeof(T) * n,
                            device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
@@ -288,17 +288,17 @@ static cudaError_t rebuild_from_footprints(sa_scene* sc, cudaStream_t st) {
     int *dt = nullptr, *db = nullptr;
     cudaError_t e = cudaSuccess;
     if (fs.n_tris > 0) {
-        e = cudaMalloc(&dv, sizeof(float) * 3 * (size_t)fs.n_verts);
-        if (e == cudaSuccess) e = cudaMalloc(&dt, sizeof(int) * 3 * (size_t)fs.n_tris);
-        if (e == cudaSuccess) e = cudaMalloc(&db, sizeof(int) * (size_t)fs.n_tris);
+        e = sa::scratch_alloc(&dv, sizeof(float) * 3 * (size_t)fs.n_verts, st);
+        if (e == cudaSuccess) e = sa::scratch_alloc(&dt, sizeof(int) * 3 * (size_t)fs.n_tris, st);
+        if (e == cudaSuccess) e = sa::scratch_alloc(&db, sizeof(int) * (size_t)fs.n_tris, st);
         if (e == cudaSuccess) e = sa::extrude_footprints(fs, sc->d_heights, dv, dt, db, st);
     }
     sa::LbvhBuild nb{};
     if (e == cudaSuccess) e = sa::build_lbvh(dv, fs.n_verts, dt, fs.n_tris, db, &nb, st);
+    if (dv) cudaFreeAsync(dv, st);
+    if (dt) cudaFreeAsync(dt, st);
+    if (db) cudaFreeAsync(db, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (dv) cudaFree(dv);
-    if (dt) cudaFree(dt);
-    if (db) cudaFree(db);
     if (e != cudaSuccess) return e;
     if (sc->bvh.nodes) cudaFree(sc->bvh.nodes);
     if (sc->bvh.tris) cudaFree(sc->bvh.tris);
@@ -382,8 +382,8 @@ sa_status sa_scene_from_footprints(const float* xy, const int32_t* poly_off, int
     // one device block: xy (float2) | fp_off | bands | vert_off | tri_off
     const size_t b_xy = sizeof(float) * 2 * (size_t)std::max(nv, 1);
     const size_t b_i = sizeof(int) * (size_t)(n_buildings + 1);
-    cudaError_t e = cudaMalloc(&sc->d_fp_mem, b_xy + 4 * b_i);
-    if (e == cudaSuccess) e = cudaMalloc(&sc->d_heights, sizeof(float) * (size_t)std::max(n_buildings, 1));
+    cudaError_t e = sa::scratch_alloc_bytes(&sc->d_fp_mem, b_xy + 4 * b_i, st);
+    if (e == cudaSuccess) e = sa::scratch_alloc(&sc->d_heights, sizeof(float) * (size_t)std::max(n_buildings, 1), st);
     if (e == cudaSuccess) {
         char* base = static_cast<char*>(sc->d_fp_mem);
         float2* dxy = reinterpret_cast<float2*>(base);
@@ -731,9 +731,9 @@ sa_status sa_receivers_points(const float* pos, const float* normal, int64_t n,
         dp = sp;
         dn = normal ? sn : nullptr;
     }
-    if (e == cudaSuccess && n > 0) e = cudaMalloc(&r->d_orig, sizeof(float4) * (size_t)n);
-    if (e == cudaSuccess && n > 0) e = cudaMalloc(&r->d_perm, sizeof(int) * (size_t)n);
-    if (e == cudaSuccess && n > 0 && normal) e = cudaMalloc(&r->d_nrm, sizeof(float4) * (size_t)n);
+    if (e == cudaSuccess && n > 0) e = sa::scratch_alloc(&r->d_orig, sizeof(float4) * (size_t)n, st);
+    if (e == cudaSuccess && n > 0) e = sa::scratch_alloc(&r->d_perm, sizeof(int) * (size_t)n, st);
+    if (e == cudaSuccess && n > 0 && normal) e = sa::scratch_alloc(&r->d_nrm, sizeof(float4) * (size_t)n, st);
     long long bad[2] = {-1, -1};
     if (e == cudaSuccess)
         e = sa::sort_points(dp, dn, n, r->d_orig, r->d_nrm, r->d_perm, st, bad, r->box);

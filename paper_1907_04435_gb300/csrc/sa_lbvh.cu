@@ -228,8 +228,8 @@ cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, lo
     unsigned *cbox = nullptr, *keys = nullptr, *vals = nullptr, *flags = nullptr;
     int* ibuf = nullptr;
 #define TRY(x) do { e = (x); if (e != cudaSuccess) goto fail; } while (0)
-    TRY(cudaMalloc(&out->nodes, sizeof(float4) * 2 * (size_t)n_nodes));
-    TRY(cudaMalloc(&out->tris, sizeof(float4) * 3 * (size_t)n));
+    TRY(sa::scratch_alloc(&out->nodes, sizeof(float4) * 2 * (size_t)n_nodes, st));
+    TRY(sa::scratch_alloc(&out->tris, sizeof(float4) * 3 * (size_t)n, st));
     TRY(sa::scratch_alloc(&raw, sizeof(float4) * 3 * (size_t)n, st));
     TRY(sa::scratch_alloc(&cbox, sizeof(unsigned) * 6, st));
     TRY(sa::scratch_alloc(&keys, sizeof(unsigned) * (size_t)n, st));

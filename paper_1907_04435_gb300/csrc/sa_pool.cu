@@ -1,9 +1,11 @@
-// sa_pool.cu -- the library's stream-ordered scratch pool.
+// sa_pool.cu -- the library's stream-ordered memory pool.
 //
 // Scratch (bins, masks, sort buffers) is allocated and freed on the caller's stream within
-// each call.  The default pool would return that memory to the device at every
-// synchronisation, so a repeated call would map it again each time; this pool keeps up to
-// kKeep bytes reserved instead.
+// each call, and the handles' own arrays (BVH, sun tables, sorted receivers) come from the
+// same pool, freed when the handle is destroyed.  The default pool would return memory to
+// the device at every synchronisation, so a repeated call would map it again each time;
+// this pool keeps up to kKeep bytes reserved instead, and a handle built again (a scene
+// rebuilt every step) takes memory already mapped instead of paying cudaMalloc's latency.
 #include <atomic>
 #include <mutex>
 #include <vector>
