@@ -26,6 +26,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -688,8 +689,9 @@ def end_to_end(B, w, args, dev):
     """Same metric through the C ABI from pinned host buffers: every step copies the mesh,
     the sun table and the facade points to the device, builds the scene and its BVH, the
     sun table and the sorted receivers, accumulates, and copies the results back to pinned
-    host memory.  The facade receivers are sorted and accumulated on a second stream,
-    overlapping the ground's accumulation and its copy back."""
+    host memory.  The facade receivers are sorted on a second stream by a second host
+    thread while the scene is built, and accumulated on that stream, overlapping the
+    ground's accumulation and its copy back."""
     import torch
 
     def pinned(a):
@@ -712,10 +714,18 @@ def end_to_end(B, w, args, dev):
     Rg = g.R
 
     def once():
-        # ground on the current stream, facades on a second one once the scene and the sun
-        # table exist; each part's results go straight to its slice of the pinned output
-        # (gross | minutes | continuous, ground then facades), the ground's while the
-        # facades still run
+        # The facade points are sorted on a second stream by a second host thread while
+        # this one builds the scene and the sun table (the library's creation calls wait
+        # for their stream, and ctypes lets the other thread run meanwhile).  The ground
+        # accumulates on the current stream, the facades on the second one once the scene
+        # and the sun table exist; each part's results go straight to its slice of the
+        # pinned output (gross | minutes | continuous, ground then facades), the ground's
+        # while the facades still run.
+        fac_box = []
+        sorter = None
+        if fpos is not None:
+            sorter = threading.Thread(target=lambda: fac_box.append(B.Receivers.points(fpos, fnrm, stream=side)))
+            sorter.start()
         scene = B.Scene(verts, tris, tb, w.city.B, closed=True, stream=main)
         sun = B.Sun(dirs, day_start, args.block_len, stream=main)
         grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
@@ -723,11 +733,11 @@ def end_to_end(B, w, args, dev):
         gg, gm, gc = B.sa_accumulate(scene, grid, sun, st.step_minutes, "accrual_sam", stream=main)
         for q, t in enumerate((gg, gm.view(torch.int32), gc)):
             host_out[q * R:q * R + Rg].copy_(t, non_blocking=True)
-        if fpos is not None:
+        if sorter is not None:
+            sorter.join()
             side.wait_event(ready)
             with torch.cuda.stream(side):
-                fac = B.Receivers.points(fpos, fnrm, stream=side)
-                fg, fm, fc = B.sa_accumulate(scene, fac, sun, st.step_minutes, "accrual_sam", stream=side)
+                fg, fm, fc = B.sa_accumulate(scene, fac_box[0], sun, st.step_minutes, "accrual_sam", stream=side)
                 for q, t in enumerate((fg, fm.view(torch.int32), fc)):
                     host_out[q * R + Rg:(q + 1) * R].copy_(t, non_blocking=True)
         torch.cuda.synchronize()
