@@ -832,6 +832,40 @@ def run_only_graph(args):
                       "ms": statistics.median(ts), "kernel_times": kt}))
 
 
+def run_only_contrib(args):
+    """Profiling mode for the building contribution (Sec. 7.2): the district's scene and
+    sun, a square region of --contrib-n cells a side at the grid's centre; W warm-up and K
+    timed calls; prints one JSON line."""
+    import torch
+
+    from paper_1907_04435_gb300 import binding as B
+    from synth import configs
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = configs.district(n_facade=0)
+    g = w.ground
+    scene = B.Scene(w.mesh.verts, w.mesh.tris, w.mesh.tri_building, w.city.B, closed=True)
+    sun = B.Sun(w.sun.dirs, w.sun.day_start)
+    grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+    n = args.contrib_n
+    xa, ya = g.x0 + (g.nx - n) // 2 * g.dx, g.y0 + (g.ny - n) // 2 * g.dx
+    poly = np.array([[xa, ya], [xa + n * g.dx, ya], [xa + n * g.dx, ya + n * g.dx], [xa, ya + n * g.dx]],
+                    np.float32)
+    run = lambda: B.sa_building_contribution(scene, grid, sun, poly)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    print(json.dumps({"only_contrib": True, "region": f"{n}x{n} cells at the district grid's centre",
+                      "ms": statistics.median(ts)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -859,6 +893,9 @@ def main():
     ap.add_argument("--batch-variants", type=int, default=8)
     ap.add_argument("--batch-days", type=int, default=31)
     ap.add_argument("--baseline-steps", dest="baseline_steps", type=int, default=5)
+    ap.add_argument("--only-contrib", dest="only_contrib", action="store_true",
+                    help="profiling mode: the building contribution over a central region")
+    ap.add_argument("--contrib-n", dest="contrib_n", type=int, default=1024)
     ap.add_argument("--multi", default="problems", choices=["problems", "shard"],
                     help="under torchrun: a district per rank (weak) or one district split (strong)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -867,6 +904,8 @@ def main():
         run_reference(args)
     elif args.only_graph:
         run_only_graph(args)
+    elif args.only_contrib:
+        run_only_contrib(args)
     else:
         run_gpu(args)
 

@@ -110,14 +110,15 @@ __global__ void k_shadow_score(const int* __restrict__ steps, long long R, int n
 // with a shadowed step in it.  One warp then takes 32 listed cells of one run and walks
 // the depth-first node list once with the fan of the run's rays as its query (as the
 // ray-traced accrual does): every triangle in the fan is tested exactly (Plucker form,
-// with its distance) against the lane's shadowed steps it can reach.  Per lane and step the nearest hit (distance, building) is kept in shared
-// memory, and per lane and run a short list of (building, steps met) pairs; a lane whose
+// with its distance) against the lane's shadowed steps it can reach.  Per lane and step
+// the nearest hit (distance, building) is kept in shared memory, and per lane and run a
+// short list of kCastList (building, steps met) pairs; a lane whose
 // run meets more buildings than the list holds counts its casting again ray by ray, with
 // a list of kRayList buildings per ray.  Counts are integers, credited by atomics on
 // per-building totals (runs of equal nearest buildings are credited at once).
 constexpr int kContribWarps = 2;
 constexpr int kContribRun = 32;             // steps per fan traversal
-constexpr int kCastList = 16;               // buildings per lane and run in the fan pass
+constexpr int kCastList = 8;                // buildings per lane and run in the fan pass
 constexpr int kRayList = 2 * kContribRun;   // buildings per ray in the per-ray recount
 
 struct ContribArgs {
@@ -143,16 +144,24 @@ struct ContribArgs {
     const int* warp_base;             // [n_runs + 1] first warp of each run
 };
 
+// Per warp, in shared memory; Id is a 16-bit building id when the scene has fewer than
+// 65,536 buildings (the smaller footprint keeps more warps resident), else 32-bit.
+template <class Id>
 struct ContribWarpSmem {
     float t[kContribRun][32];         // nearest hit distance per step and lane
-    int b[kContribRun][32];           // its building
-    int cb[kCastList][32];            // casting list: building
+    Id b[kContribRun][32];            // its building
+    Id cb[kCastList][32];             // casting list: building
     unsigned cm[kCastList][32];       //               steps whose ray meets it
+};
+
+// what the kernel reads of a step: its direction and the direction's reciprocals
+struct ContribStep {
+    float dx, dy, dz, ix, iy, iz;
 };
 
 // Plucker test with the hit distance (t = ((a - o) . n) / (d . n)), the same decision as
 // plucker_hit.
-__device__ __forceinline__ bool plucker_hit_t(const PluckerTri& p, const StepConst& s, float tmin,
+__device__ __forceinline__ bool plucker_hit_t(const PluckerTri& p, const ContribStep& s, float tmin,
                                               float* t) {
     if (!plucker_hit(p, s.dx, s.dy, s.dz, tmin)) return false;
     const float nd = fmaf(s.dz, p.nz, fmaf(s.dy, p.ny, __fmul_rn(s.dx, p.nx)));
@@ -194,11 +203,12 @@ __global__ void k_contrib_items(ContribArgs a, bool fill, unsigned* __restrict__
     }
 }
 
+template <class Id>
 __global__ void __launch_bounds__(32 * kContribWarps)
 k_building_contribution(ContribArgs a) {
-    __shared__ ContribWarpSmem s_w[kContribWarps];
+    __shared__ ContribWarpSmem<Id> s_w[kContribWarps];
     __shared__ BlockConst s_bc[kContribWarps];
-    __shared__ StepConst s_st[kContribWarps][kContribRun];
+    __shared__ ContribStep s_st[kContribWarps][kContribRun];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int warp_id = (int)(blockIdx.x * kContribWarps + wib);
     if (warp_id >= a.warp_base[a.n_runs]) return;                       // whole warps
@@ -212,17 +222,19 @@ k_building_contribution(ContribArgs a) {
     o.x = __fadd_rn(a.x0, __fmul_rn(__fadd_rn((float)ix, 0.5f), a.dx));
     o.y = __fadd_rn(a.y0, __fmul_rn(__fadd_rn((float)iy, 0.5f), a.dx));
     o.z = 0.f;
-    ContribWarpSmem& w = s_w[wib];
+    ContribWarpSmem<Id>& w = s_w[wib];
     BlockConst& bc = s_bc[wib];
-    StepConst* ss = s_st[wib];
+    ContribStep* ss = s_st[wib];
     unsigned long long n_graze = 0, n_over = 0;
     {
         for (int q = lane; q < (int)(sizeof(BlockConst) / 4); q += 32)
             reinterpret_cast<int*>(&bc)[q] = reinterpret_cast<const int*>(&a.runs[r])[q];
         __syncwarp();
         const int K = bc.K;
-        for (int q = lane; q < K * (int)(sizeof(StepConst) / 4); q += 32)
-            reinterpret_cast<int*>(ss)[q] = reinterpret_cast<const int*>(&a.steps[bc.j0])[q];
+        if (lane < K) {
+            const StepConst& sk = a.steps[bc.j0 + lane];
+            ss[lane] = ContribStep{sk.dx, sk.dy, sk.dz, sk.ix, sk.iy, sk.iz};
+        }
         const unsigned run_bits = K >= 32 ? 0xffffffffu : ((1u << K) - 1u);
         unsigned m = 0u;
         if (live) m = (unsigned)(a.masks[(long long)bc.mask_block * a.R + cell] >> bc.mask_bit) & run_bits;
@@ -268,18 +280,18 @@ k_building_contribution(ContribArgs a) {
                             hits |= 1u << k;
                             if (t < w.t[k][lane]) {
                                 w.t[k][lane] = t;
-                                w.b[k][lane] = bid;
+                                w.b[k][lane] = (Id)bid;
                             }
                         }
                     }
                     if (hits) {
                         found |= hits;
                         int e = 0;
-                        while (e < n_list && w.cb[e][lane] != bid) ++e;
+                        while (e < n_list && (int)w.cb[e][lane] != bid) ++e;
                         if (e < n_list) {
                             w.cm[e][lane] |= hits;
                         } else if (n_list < kCastList) {
-                            w.cb[n_list][lane] = bid;
+                            w.cb[n_list][lane] = (Id)bid;
                             w.cm[n_list][lane] = hits;
                             ++n_list;
                         } else {
@@ -300,7 +312,7 @@ k_building_contribution(ContribArgs a) {
         while (rest) {
             const int k = __ffs(rest) - 1;
             rest &= rest - 1u;
-            const int bid = w.b[k][lane];
+            const int bid = (int)w.b[k][lane];
             if (bid != cur) {
                 if (cnt) atomicAdd(&a.near_cnt[cur], cnt);
                 cur = bid;
@@ -311,16 +323,18 @@ k_building_contribution(ContribArgs a) {
         if (cnt) atomicAdd(&a.near_cnt[cur], cnt);
         if (!ovf) {
             for (int e = 0; e < n_list; ++e)
-                atomicAdd(&a.cast_cnt[w.cb[e][lane]], (unsigned long long)__popc(w.cm[e][lane]));
+                atomicAdd(&a.cast_cnt[(int)w.cb[e][lane]], (unsigned long long)__popc(w.cm[e][lane]));
         }
         // more buildings than the list holds: casting again, ray by ray (each lane alone;
-        // the nearest arrays, no longer needed, hold the ray's list)
-        int* ids = reinterpret_cast<int*>(&w.t[0][0]);     // kRayList x 32 ints: t, then b
+        // the nearest arrays, no longer needed, hold the ray's list -- with 16-bit ids a
+        // lane's list spans other lanes' columns of t, hence the warp barrier)
+        __syncwarp();
+        Id* ids = reinterpret_cast<Id*>(&w.t[0][0]);       // kRayList x 32 ids over t (and b)
         unsigned todo = ovf ? (m & found) : 0u;
         while (todo) {
             const int k = __ffs(todo) - 1;
             todo &= todo - 1u;
-            const StepConst& s = ss[k];
+            const ContribStep& s = ss[k];
             int n_ids = 0;
             bool lost = false;
             for (int i = 0; i < a.sc.n_nodes;) {
@@ -338,9 +352,9 @@ k_building_contribution(ContribArgs a) {
                         if (plucker_hit(pt, s.dx, s.dy, s.dz, kGroundTmin)) {
                             const int bid = (int)SA_CHK(__float_as_int(ta.w), a.n_b, sa::CK_CONTRIB_BUILDING);
                             int e = 0;
-                            while (e < n_ids && ids[e * 32 + lane] != bid) ++e;
+                            while (e < n_ids && (int)ids[e * 32 + lane] != bid) ++e;
                             if (e == n_ids) {
-                                if (n_ids < kRayList) ids[(n_ids++) * 32 + lane] = bid;
+                                if (n_ids < kRayList) ids[(n_ids++) * 32 + lane] = (Id)bid;
                                 else lost = true;
                             }
                         }
@@ -350,7 +364,7 @@ k_building_contribution(ContribArgs a) {
                     i = in ? i + 1 : esc;
                 }
             }
-            for (int e = 0; e < n_ids; ++e) atomicAdd(&a.cast_cnt[ids[e * 32 + lane]], 1ull);
+            for (int e = 0; e < n_ids; ++e) atomicAdd(&a.cast_cnt[(int)ids[e * 32 + lane]], 1ull);
             if (lost) ++n_over;
         }
     }
@@ -460,8 +474,9 @@ cudaError_t launch_building_contribution(const DevScene& sc, const DevRecv& rc, 
         const long long warps = h_base[(size_t)nr];
         if (warps > 0) {
             KernelTimer kt(KT_CONTRIB, st);
-            k_building_contribution<<<(unsigned)((warps + kContribWarps - 1) / kContribWarps),
-                                      32 * kContribWarps, 0, st>>>(ca);
+            const unsigned ctas = (unsigned)((warps + kContribWarps - 1) / kContribWarps);
+            if (B <= 65535) k_building_contribution<unsigned short><<<ctas, 32 * kContribWarps, 0, st>>>(ca);
+            else k_building_contribution<int><<<ctas, 32 * kContribWarps, 0, st>>>(ca);
         }
         TRY(cudaGetLastError());
     }

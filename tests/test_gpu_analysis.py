@@ -249,3 +249,39 @@ def test_building_contribution_without_buildings_and_with_ragged_grids(cuda_lib)
     cnt_n = np.round(nearest / unit).astype(np.int64)
     assert np.all(np.abs(cnt_c - c_o) <= u_o) and np.abs(cnt_n - n_o).sum() <= 2 * u_any
     assert c_o.min() > 0 and over == 0
+
+
+@pytest.mark.parametrize("n_buildings", [20, 70000])
+def test_building_contribution_of_a_row_of_twenty_boxes(cuda_lib, n_buildings):
+    """Twenty thin boxes in a row toward a low sun: a ray from behind the row meets up to
+    twenty buildings, more than the per-run list holds, so the lanes recount ray by ray.
+    Counts agree with the oracle pair by pair, both with 16-bit building ids (20
+    buildings) and with 32-bit ones (70,000 declared, the rest crediting nothing)."""
+    B = cuda_lib
+    from synth import city as C
+    feet = [C.box_footprint(30.0 + 4.0 * k, 40.0, 31.5 + 4.0 * k, 60.0) for k in range(20)]
+    city = C.City(feet, np.full(20, 12.0, np.float32))
+    mesh = C.extrude(city)
+    el = np.radians(np.linspace(6.0, 9.0, 12))
+    az = np.radians(np.linspace(-4.0, 4.0, 12))
+    dirs = np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], 1).astype(np.float32)
+    day_start = np.array([0, 12], np.int32)
+    scene = B.Scene(mesh.verts, mesh.tris, mesh.tri_building, n_buildings, closed=True)
+    sun = B.Sun(dirs, day_start)
+    x0, y0, dx, nx, ny = 0.0, 30.0, 0.5, 60, 60
+    grid = B.Receivers.ground_grid(x0, y0, dx, nx, ny)
+    poly = np.array([[0.0, 30.0], [29.0, 30.0], [29.0, 60.0], [0.0, 60.0]], np.float32)
+    casting, nearest, (over, un) = B.sa_building_contribution(scene, grid, sun, poly)
+    assert casting.shape == (n_buildings,)
+    pos = _region_centres(SimpleNamespace(x0=x0, y0=y0, dx=dx, nx=nx, ny=ny), poly)
+    c_o, n_o, u_o, u_any = oracle.building_steps(mesh.tri9(), mesh.tri_building, pos, None, dirs,
+                                                 day_start, 20)
+    unit = dx * dx / 12
+    cnt_c = np.round(casting / unit).astype(np.int64)
+    cnt_n = np.round(nearest / unit).astype(np.int64)
+    assert not cnt_c[20:].any() and not cnt_n[20:].any()
+    cnt_c, cnt_n = cnt_c[:20], cnt_n[:20]
+    assert over == 0
+    assert (c_o > 0).sum() >= 12, c_o          # most of the row reaches the region
+    assert np.all(np.abs(cnt_c - c_o) <= u_o), (cnt_c, c_o, u_o)
+    assert np.abs(cnt_n - n_o).sum() <= 2 * u_any
