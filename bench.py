@@ -26,7 +26,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -689,9 +688,12 @@ def end_to_end(B, w, args, dev):
     """Same metric through the C ABI from pinned host buffers: every step copies the mesh,
     the sun table and the facade points to the device, builds the scene and its BVH, the
     sun table and the sorted receivers, accumulates, and copies the results back to pinned
-    host memory.  The facade receivers are sorted on a second stream by a second host
-    thread while the scene is built, and accumulated on that stream, overlapping the
-    ground's accumulation and its copy back."""
+    host memory.  Two worker threads, started once like the streams, build the sun table
+    and sort the facade receivers on streams of their own while this thread builds the
+    scene; the facades accumulate on a second stream, overlapping the ground's
+    accumulation and its copy back."""
+    import concurrent.futures as cf
+
     import torch
 
     def pinned(a):
@@ -711,33 +713,32 @@ def end_to_end(B, w, args, dev):
 
     main = torch.cuda.current_stream()
     side = torch.cuda.Stream()
+    sun_stream = torch.cuda.Stream()
     Rg = g.R
+    pool = cf.ThreadPoolExecutor(max_workers=2)
 
     def once():
-        # The facade points are sorted on a second stream by a second host thread while
-        # this one builds the scene and the sun table (the library's creation calls wait
-        # for their stream, and ctypes lets the other thread run meanwhile).  The ground
+        # The library's creation calls wait for their own stream before they return, and
+        # ctypes lets the other threads run meanwhile: the sun table and the sorted facade
+        # receivers are ready on the device once their futures resolve.  The ground
         # accumulates on the current stream, the facades on the second one once the scene
-        # and the sun table exist; each part's results go straight to its slice of the
-        # pinned output (gross | minutes | continuous, ground then facades), the ground's
-        # while the facades still run.
-        fac_box = []
-        sorter = None
-        if fpos is not None:
-            sorter = threading.Thread(target=lambda: fac_box.append(B.Receivers.points(fpos, fnrm, stream=side)))
-            sorter.start()
+        # exists; each part's results go straight to its slice of the pinned output
+        # (gross | minutes | continuous, ground then facades), the ground's while the
+        # facades still run.
+        sun_f = pool.submit(B.Sun, dirs, day_start, args.block_len, stream=sun_stream)
+        fac_f = None if fpos is None else pool.submit(B.Receivers.points, fpos, fnrm, stream=side)
         scene = B.Scene(verts, tris, tb, w.city.B, closed=True, stream=main)
-        sun = B.Sun(dirs, day_start, args.block_len, stream=main)
         grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
         ready = main.record_event()
+        sun = sun_f.result()
         gg, gm, gc = B.sa_accumulate(scene, grid, sun, st.step_minutes, "accrual_sam", stream=main)
         for q, t in enumerate((gg, gm.view(torch.int32), gc)):
             host_out[q * R:q * R + Rg].copy_(t, non_blocking=True)
-        if sorter is not None:
-            sorter.join()
+        if fac_f is not None:
+            fac = fac_f.result()
             side.wait_event(ready)
             with torch.cuda.stream(side):
-                fg, fm, fc = B.sa_accumulate(scene, fac_box[0], sun, st.step_minutes, "accrual_sam", stream=side)
+                fg, fm, fc = B.sa_accumulate(scene, fac, sun, st.step_minutes, "accrual_sam", stream=side)
                 for q, t in enumerate((fg, fm.view(torch.int32), fc)):
                     host_out[q * R + Rg:(q + 1) * R].copy_(t, non_blocking=True)
         torch.cuda.synchronize()
@@ -750,6 +751,7 @@ def end_to_end(B, w, args, dev):
         once()
         times.append(time.perf_counter() - t0)
     t = statistics.median(times)
+    pool.shutdown()
     # the overlapped results equal a sequential run on one stream, bit for bit
     scene = B.Scene(verts, tris, tb, w.city.B, closed=True)
     sun = B.Sun(dirs, day_start, args.block_len)

@@ -141,9 +141,14 @@ sa_status sa_kernel_times(double* ms, int64_t* launches, int32_t n);
  * On the device this builds a linear BVH: 30-bit Morton codes of the triangle
  * centroids, a least-significant-digit radix sort, Karras' (2012) radix-tree topology,
  * bottom-up box refit, and a depth-first node order whose escape links allow stackless
- * traversal.  Zero-area triangles are kept but never hit.
- * Errors: SA_ERR_INVALID_ARG (NULL pointers, index out of range, nt or nv < 0),
- * SA_ERR_DEGENERATE (non-finite vertex), SA_ERR_OOM, SA_ERR_CUDA.  nt = 0 is allowed. */
+ * traversal.  Zero-area triangles are kept but never hit.  Sizes and pointers are
+ * checked on the host; the contents on the device, while the BVH is built (an index out
+ * of range reads no memory), and the message names the first offending vertex or
+ * triangle.  The call synchronises the stream.
+ * Errors: SA_ERR_INVALID_ARG (NULL pointers, nt or nv < 0, nt > 2^30, n_buildings < 0,
+ * a vertex index outside [0, nv), a building id outside [0, max(n_buildings, 1))),
+ * SA_ERR_DEGENERATE (a non-finite coordinate of any vertex, used or not), SA_ERR_OOM,
+ * SA_ERR_CUDA.  nt = 0 is allowed. */
 sa_status sa_scene_from_mesh(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                              const int32_t* tri_building, int32_t n_buildings,
                              int32_t device_ptrs, void* stream, sa_scene** out);

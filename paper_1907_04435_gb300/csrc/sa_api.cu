@@ -198,42 +198,14 @@ sa_status sa_scene_from_mesh(const float* verts, int64_t nv, const int32_t* tris
     if ((nv > 0 && !verts) || (nt > 0 && !tris))
         return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: NULL buffer");
     if (n_buildings < 0) return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: n_buildings < 0");
-    // validation reads host memory in place (device inputs are copied to the host first)
-    std::vector<float> hv;
-    std::vector<int32_t> ht, hb;
-    const float* pv = verts;
-    const int32_t *pt = tris, *pb = tri_building;
-    if (device_ptrs) {
-        sa_status s = host_copy(verts, (size_t)nv * 3, 1, &hv);
-        if (s == SA_OK) s = host_copy(tris, (size_t)nt * 3, 1, &ht);
-        if (s == SA_OK && tri_building) s = host_copy(tri_building, (size_t)nt, 1, &hb);
-        if (s != SA_OK) return s;
-        pv = hv.data();
-        pt = ht.data();
-        pb = tri_building ? hb.data() : nullptr;
-    }
-    for (int64_t i = 0; i < 3 * nv; ++i)
-        if (!isfinite(pv[i])) return fail(SA_ERR_DEGENERATE, "sa_scene_from_mesh: non-finite vertex %lld", (long long)(i / 3));
-    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    const int32_t nb_max = std::max(n_buildings, 1);
-    for (int64_t t = 0; t < nt; ++t) {
-        for (int q = 0; q < 3; ++q) {
-            const int32_t ix = pt[3 * t + q];
-            if (ix < 0 || ix >= nv)
-                return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: triangle %lld indexes vertex %d", (long long)t, ix);
-            const float* v = pv + 3 * (size_t)ix;
-            for (int k = 0; k < 3; ++k) { lo[k] = std::min(lo[k], v[k]); hi[k] = std::max(hi[k], v[k]); }
-        }
-        if (pb && (pb[t] < 0 || pb[t] >= nb_max))
-            return fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: building id %d of triangle %lld", pb[t], (long long)t);
-    }
+    // The mesh is validated on the device while its BVH is built (non-finite vertices,
+    // vertex indices and building ids out of range), and the bounds of the referenced
+    // vertices come back with the checks.
     cudaStream_t st = as_stream(stream);
     sa_scene* sc = new (std::nothrow) sa_scene();
     if (!sc) return fail(SA_ERR_OOM, "sa_scene_from_mesh: host allocation");
     sc->T = nt;
     sc->n_buildings = n_buildings;
-    sc->min_z = nt > 0 ? lo[2] : 0.f;
-    for (int q = 0; q < 3; ++q) { sc->box[q] = nt > 0 ? lo[q] : 0.f; sc->box[3 + q] = nt > 0 ? hi[q] : 0.f; }
     // inputs to the device: device buffers are used in place, host buffers go through
     // stream-ordered staging (pinned host memory copies asynchronously)
     const float* dv = verts;
@@ -258,15 +230,45 @@ sa_status sa_scene_from_mesh(const float* verts, int64_t nv, const int32_t* tris
         dt = stt;
         db = tri_building ? sb : nullptr;
     }
-    if (e == cudaSuccess) e = sa::build_lbvh(dv, nv, dt, nt, db, &sc->bvh, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    sa::MeshCheck chk{};
+    if (e == cudaSuccess) e = sa::build_lbvh(dv, nv, dt, nt, db, &sc->bvh, st, std::max(n_buildings, 1), &chk);
+    // the failing triangle's indices, for the message (read before the staging is freed)
+    int32_t bad[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess && chk.bad_vertex < 0 && chk.bad_tri >= 0) {
+        const int32_t* src = device_ptrs ? dt : tris;
+        const int32_t* srcb = device_ptrs ? db : tri_building;
+        if (device_ptrs) {
+            e = cudaMemcpy(bad, src + 3 * chk.bad_tri, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && srcb) e = cudaMemcpy(bad + 3, srcb + chk.bad_tri, sizeof(int32_t), cudaMemcpyDeviceToHost);
+        } else {
+            memcpy(bad, src + 3 * chk.bad_tri, sizeof(int32_t) * 3);
+            if (srcb) bad[3] = srcb[chk.bad_tri];
+        }
+    }
     if (sv) cudaFreeAsync(sv, st);
     if (stt) cudaFreeAsync(stt, st);
     if (sb) cudaFreeAsync(sb, st);
+    sa_status verdict = SA_OK;
     if (e != cudaSuccess) {
-        delete sc;
-        return cuda_fail(e, "sa_scene_from_mesh");
+        verdict = cuda_fail(e, "sa_scene_from_mesh");
+    } else if (chk.bad_vertex >= 0) {
+        verdict = fail(SA_ERR_DEGENERATE, "sa_scene_from_mesh: non-finite vertex %lld", chk.bad_vertex);
+    } else if (chk.bad_tri >= 0) {
+        int q = 0;
+        while (q < 3 && bad[q] >= 0 && bad[q] < nv) ++q;
+        if (q < 3)
+            verdict = fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: triangle %lld indexes vertex %d", chk.bad_tri, bad[q]);
+        else
+            verdict = fail(SA_ERR_INVALID_ARG, "sa_scene_from_mesh: building id %d of triangle %lld", bad[3], chk.bad_tri);
     }
+    if (verdict != SA_OK) {
+        if (sc->bvh.nodes) cudaFreeAsync(sc->bvh.nodes, st);
+        if (sc->bvh.tris) cudaFreeAsync(sc->bvh.tris, st);
+        delete sc;
+        return verdict;
+    }
+    sc->min_z = chk.box[2];
+    for (int q = 0; q < 6; ++q) sc->box[q] = chk.box[q];
     *out = sc;
     return SA_OK;
 }

@@ -617,8 +617,21 @@ struct LbvhBuild {
     float4* tris;    // [3 * T]
     int n_nodes;
 };
+// Checks of an input mesh made on the device while its BVH is built: the first vertex
+// with a non-finite coordinate and the first triangle with a vertex index outside
+// [0, nv) or a building id outside [0, n_buildings) (-1: none), and the bounds (lo xyz,
+// hi xyz) of the vertices the triangles reference (zeros without triangles).
+struct MeshCheck {
+    long long bad_vertex;
+    long long bad_tri;
+    float box[6];
+};
+// Builds the BVH of nt triangles (synchronises st).  With `check`, the mesh is validated
+// as described above; a failed check still returns cudaSuccess with the BVH built from
+// the readable part, for the caller to free.  Without it the mesh is trusted.
 cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, long long nt,
-                       const int* d_tri_building, LbvhBuild* out, cudaStream_t st);
+                       const int* d_tri_building, LbvhBuild* out, cudaStream_t st,
+                       int n_buildings = 1, MeshCheck* check = nullptr);
 
 // Morton order of point receivers: fills perm (sorted -> input index) and sorted origins
 // (synchronises st).  bad_out[0] / [1]: first point with a non-finite position / normal

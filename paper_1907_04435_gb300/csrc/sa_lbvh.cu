@@ -43,33 +43,71 @@ __device__ __forceinline__ float o2f(unsigned u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
-// gather triangles, centroid bounds
-__global__ void k_gather(const float* __restrict__ verts, const int* __restrict__ tris,
-                         const int* __restrict__ tri_b, long long nt, float4* __restrict__ raw,
-                         unsigned* __restrict__ cbox /* 6: lo.xyz hi.xyz as ordered uint */) {
-    __shared__ unsigned s_lo[3], s_hi[3];
-    if (threadIdx.x < 3) { s_lo[threadIdx.x] = 0xffffffffu; s_hi[threadIdx.x] = 0u; }
+// Gather the triangles (three float4: vertex xyz, with the building id and the input
+// index in .w) and reduce the centroid bounds (cw[0..5], ordered uint).  With `check`, the
+// mesh is validated on the way: the first vertex with a non-finite coordinate (every
+// vertex, grid-stride; cw[14..15] as u64), the first triangle with a vertex index outside
+// [0, nv) or a building id outside [0, nb) (cw[12]), and the bounds of the referenced
+// vertices (cw[6..11]).  An index out of range reads no memory: its corner becomes the
+// origin, and the call that asked for the check fails once the results are read back.
+__global__ void k_gather(const float* __restrict__ verts, long long nv, const int* __restrict__ tris,
+                         const int* __restrict__ tri_b, long long nt, int nb, int check,
+                         float4* __restrict__ raw, unsigned* __restrict__ cw) {
+    __shared__ unsigned s_c[12];   // centroid lo xyz, hi xyz; vertex lo xyz, hi xyz
+    if (threadIdx.x < 12) s_c[threadIdx.x] = (threadIdx.x % 6) < 3 ? 0xffffffffu : 0u;
     __syncthreads();
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (check) {
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long v = t; v < nv; v += stride)
+            if (!(isfinite(verts[3 * v]) && isfinite(verts[3 * v + 1]) && isfinite(verts[3 * v + 2])))
+                atomicMin(reinterpret_cast<unsigned long long*>(cw + 14), (unsigned long long)v);
+    }
+    unsigned clo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, chi[3] = {0u, 0u, 0u};
+    unsigned vlo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, vhi[3] = {0u, 0u, 0u};
     if (t < nt) {
         float p[3][3];
+        bool ok = true;
         for (int v = 0; v < 3; ++v) {
-            long long vi = tris[3 * t + v];
-            for (int k = 0; k < 3; ++k) p[v][k] = verts[3 * vi + k];
+            const int vi = tris[3 * t + v];
+            const bool in = vi >= 0 && (long long)vi < nv;
+            ok = ok && in;
+            for (int k = 0; k < 3; ++k) p[v][k] = in ? verts[3 * (long long)vi + k] : 0.f;
         }
-        raw[3 * t + 0] = make_float4(p[0][0], p[0][1], p[0][2], __int_as_float(tri_b ? tri_b[t] : 0));
+        const int b = tri_b ? tri_b[t] : 0;
+        if (check && (!ok || b < 0 || b >= nb)) atomicMin(reinterpret_cast<int*>(cw + 12), (int)t);
+        raw[3 * t + 0] = make_float4(p[0][0], p[0][1], p[0][2], __int_as_float(b));
         raw[3 * t + 1] = make_float4(p[1][0], p[1][1], p[1][2], __int_as_float((int)t));
         raw[3 * t + 2] = make_float4(p[2][0], p[2][1], p[2][2], 0.f);
         for (int k = 0; k < 3; ++k) {
-            float c = (p[0][k] + p[1][k] + p[2][k]) * (1.f / 3.f);
-            atomicMin(&s_lo[k], f2o(c));
-            atomicMax(&s_hi[k], f2o(c));
+            const unsigned c = f2o((p[0][k] + p[1][k] + p[2][k]) * (1.f / 3.f));
+            clo[k] = c;
+            chi[k] = c;
+            for (int v = 0; v < 3; ++v) {
+                vlo[k] = min(vlo[k], f2o(p[v][k]));
+                vhi[k] = max(vhi[k], f2o(p[v][k]));
+            }
+        }
+    }
+    // warp reductions, then one shared atomic per warp and value
+    for (int k = 0; k < 3; ++k) {
+        clo[k] = __reduce_min_sync(0xffffffffu, clo[k]);
+        chi[k] = __reduce_max_sync(0xffffffffu, chi[k]);
+        vlo[k] = __reduce_min_sync(0xffffffffu, vlo[k]);
+        vhi[k] = __reduce_max_sync(0xffffffffu, vhi[k]);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&s_c[k], clo[k]);
+            atomicMax(&s_c[3 + k], chi[k]);
+            atomicMin(&s_c[6 + k], vlo[k]);
+            atomicMax(&s_c[9 + k], vhi[k]);
         }
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
-        atomicMin(&cbox[threadIdx.x], s_lo[threadIdx.x]);
-        atomicMax(&cbox[3 + threadIdx.x], s_hi[threadIdx.x]);
+    if (threadIdx.x < 12) {
+        if ((threadIdx.x % 6) < 3) atomicMin(&cw[threadIdx.x], s_c[threadIdx.x]);
+        else atomicMax(&cw[threadIdx.x], s_c[threadIdx.x]);
     }
 }
 
@@ -214,13 +252,48 @@ inline int nblk(long long n, int t = kThreads) { return (int)((n + t - 1) / t); 
 
 }  // namespace
 
+namespace {
+float o2f_host(unsigned u) {
+    const unsigned v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+    float f;
+    memcpy(&f, &v, sizeof(f));
+    return f;
+}
+
+// The mesh checks alone, for a mesh without triangles (its vertices are still checked).
+cudaError_t check_vertices_only(const float* d_verts, long long nv, MeshCheck* check, cudaStream_t st) {
+    unsigned* cw = nullptr;
+    cudaError_t e = sa::scratch_alloc(&cw, sizeof(unsigned) * 16, st);
+    unsigned h[16] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0xffffffffu, 0xffffffffu,
+                      0xffffffffu, 0u, 0u, 0u, 0x7fffffffu, 0u, 0xffffffffu, 0xffffffffu};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cw, h, sizeof(h), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && nv > 0) {
+        k_gather<<<(int)std::min<long long>(nblk(nv), 1024), kThreads, 0, st>>>(d_verts, nv, nullptr, nullptr,
+                                                                               0, 1, 1, nullptr, cw);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, cw, sizeof(h), cudaMemcpyDeviceToHost, st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2;
+    if (cw) cudaFreeAsync(cw, st);
+    if (e == cudaSuccess) {
+        unsigned long long bv;
+        memcpy(&bv, h + 14, sizeof(bv));
+        check->bad_vertex = bv == ~0ull ? -1 : (long long)bv;
+        check->bad_tri = -1;
+        for (int k = 0; k < 6; ++k) check->box[k] = 0.f;
+    }
+    return e;
+}
+}  // namespace
+
 cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, long long nt,
-                       const int* d_tri_b, LbvhBuild* out, cudaStream_t st) {
-    (void)nv;
+                       const int* d_tri_b, LbvhBuild* out, cudaStream_t st, int n_buildings,
+                       MeshCheck* check) {
     out->nodes = nullptr;
     out->tris = nullptr;
     out->n_nodes = 0;
-    if (nt == 0) return cudaSuccess;
+    if (nt == 0) return check ? check_vertices_only(d_verts, nv, check, st) : cudaSuccess;
     const int n = (int)nt;
     const int n_nodes = 2 * n - 1;
     cudaError_t e;
@@ -231,7 +304,7 @@ cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, lo
     TRY(sa::scratch_alloc(&out->nodes, sizeof(float4) * 2 * (size_t)n_nodes, st));
     TRY(sa::scratch_alloc(&out->tris, sizeof(float4) * 3 * (size_t)n, st));
     TRY(sa::scratch_alloc(&raw, sizeof(float4) * 3 * (size_t)n, st));
-    TRY(sa::scratch_alloc(&cbox, sizeof(unsigned) * 6, st));
+    TRY(sa::scratch_alloc(&cbox, sizeof(unsigned) * 16, st));   // bounds, checks (k_gather)
     TRY(sa::scratch_alloc(&keys, sizeof(unsigned) * (size_t)n, st));
     TRY(sa::scratch_alloc(&vals, sizeof(unsigned) * (size_t)n, st));
     TRY(sa::scratch_alloc(&blo, sizeof(float4) * (size_t)n_nodes, st));
@@ -245,11 +318,13 @@ cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, lo
         int* first = ibuf + 3 * n_nodes;
         int* last = ibuf + 4 * n_nodes;
         int* split = ibuf + 5 * n_nodes;
-        unsigned init[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+        unsigned init[16] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0xffffffffu, 0xffffffffu,
+                             0xffffffffu, 0u, 0u, 0u, 0x7fffffffu, 0u, 0xffffffffu, 0xffffffffu};
         TRY(cudaMemcpyAsync(cbox, init, sizeof(init), cudaMemcpyHostToDevice, st));
         TRY(cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)n, st));
         TRY(cudaMemsetAsync(ibuf, 0, sizeof(int) * 6 * (size_t)n_nodes, st));
-        k_gather<<<nblk(n), kThreads, 0, st>>>(d_verts, d_tris, d_tri_b, n, raw, cbox);
+        k_gather<<<nblk(n), kThreads, 0, st>>>(d_verts, nv, d_tris, d_tri_b, n, std::max(n_buildings, 1),
+                                               check ? 1 : 0, raw, cbox);
         k_morton<<<nblk(n), kThreads, 0, st>>>(raw, n, cbox, keys, vals);
         TRY(cudaGetLastError());
         TRY(radix_sort_pairs(keys, vals, n, st));
@@ -258,8 +333,18 @@ cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, lo
         k_refit<<<nblk(n), kThreads, 0, st>>>(out->tris, n, left, right, parent, blo, bhi, flags);
         k_emit<<<nblk(n_nodes), kThreads, 0, st>>>(n, left, parent, first, last, split, blo, bhi, out->nodes);
         TRY(cudaGetLastError());
-        // the initialisation copy reads host stack memory: finish before returning
+        // the checks come back with the build; the initialisation copy reads host stack
+        // memory, so the call finishes before returning either way
+        if (check) TRY(cudaMemcpyAsync(init, cbox, sizeof(init), cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
+        if (check) {
+            unsigned long long bv;
+            memcpy(&bv, init + 14, sizeof(bv));
+            check->bad_vertex = bv == ~0ull ? -1 : (long long)bv;
+            check->bad_tri = init[12] == 0x7fffffffu ? -1 : (long long)init[12];
+            // exact bounds of the referenced vertices; a zero bound is reported as +0
+            for (int k = 0; k < 6; ++k) check->box[k] = o2f_host(init[6 + k]) + 0.f;
+        }
     }
     out->n_nodes = n_nodes;
     cudaFreeAsync(raw, st); cudaFreeAsync(cbox, st); cudaFreeAsync(keys, st);
@@ -267,17 +352,10 @@ cudaError_t build_lbvh(const float* d_verts, long long nv, const int* d_tris, lo
     cudaFreeAsync(flags, st); cudaFreeAsync(ibuf, st);
     return cudaSuccess;
 fail:
+    for (void* q : {(void*)raw, (void*)cbox, (void*)keys, (void*)vals, (void*)blo, (void*)bhi,
+                    (void*)flags, (void*)ibuf, (void*)out->nodes, (void*)out->tris})
+        if (q) cudaFreeAsync(q, st);
     cudaStreamSynchronize(st);
-    if (raw) cudaFree(raw);
-    if (cbox) cudaFree(cbox);
-    if (keys) cudaFree(keys);
-    if (vals) cudaFree(vals);
-    if (blo) cudaFree(blo);
-    if (bhi) cudaFree(bhi);
-    if (flags) cudaFree(flags);
-    if (ibuf) cudaFree(ibuf);
-    if (out->nodes) cudaFree(out->nodes);
-    if (out->tris) cudaFree(out->tris);
     out->nodes = nullptr;
     out->tris = nullptr;
     return e;
@@ -357,15 +435,6 @@ __global__ void k_points_gather(const float4* __restrict__ o, const float* __res
     if (nout) nout[k] = make_float4(nrm[3ll * i], nrm[3ll * i + 1], nrm[3ll * i + 2], 0.f);
 }
 
-}  // namespace
-
-namespace {
-float o2f_host(unsigned u) {
-    const unsigned v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
-    float f;
-    memcpy(&f, &v, sizeof(f));
-    return f;
-}
 }  // namespace
 
 cudaError_t sort_points(const float* d_pos, const float* d_nrm, long long n, float4* d_orig,

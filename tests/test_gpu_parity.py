@@ -334,3 +334,72 @@ def test_scene_from_device_buffers_equals_scene_from_host_buffers(cuda_lib):
     assert L.sa_scene_from_mesh(ct.c_void_p(dv.data_ptr()), dv.shape[0], ct.c_void_p(bad.data_ptr()),
                                 bad.shape[0], None, 1, 1, stream, ct.byref(h2)) == -1
     assert b"triangle 5" in L.sa_last_error()
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_mesh_contents_are_checked_on_the_device(cuda_lib, on_device):
+    """A non-finite vertex (SA_ERR_DEGENERATE), a vertex index or a building id out of
+    range (SA_ERR_INVALID_ARG) fail the scene with the first offending vertex or triangle
+    named, from host or device buffers; a vertex no triangle uses still counts for the
+    finiteness check but not for the bounds, and the context stays usable."""
+    import ctypes as ct
+    B = cuda_lib
+    L = B.lib()
+    from synth import city as C
+    mesh = C.extrude(C.city_boxes(3, nx=3, ny=2))
+    v0 = np.concatenate([mesh.verts, np.array([[5.0, 5.0, -40.0]], np.float32)])   # unused vertex
+    t0, b0 = mesh.tris.copy(), mesh.tri_building.copy()
+    nb = int(b0.max()) + 1
+    stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    keep = []
+
+    def ptr(a):
+        a = np.ascontiguousarray(a)
+        if on_device:
+            a = torch.from_numpy(a).cuda()
+            keep.append(a)
+            return ct.c_void_p(a.data_ptr())
+        keep.append(a)
+        return a.ctypes.data_as(ct.c_void_p)
+
+    def make(v, t, b):
+        h = ct.c_void_p()
+        st = L.sa_scene_from_mesh(ptr(v), v.shape[0], ptr(t), t.shape[0], ptr(b), nb,
+                                  1 if on_device else 0, stream, ct.byref(h))
+        return st, L.sa_last_error().decode(), h
+
+    v = v0.copy()
+    v[17, 2] = np.nan
+    v[40, 0] = np.inf
+    st, msg, _ = make(v, t0, b0)
+    assert st == -5 and "non-finite vertex 17" in msg, msg
+    v = v0.copy()
+    v[-1, 1] = np.nan                       # unused, still checked
+    st, msg, _ = make(v, t0, b0)
+    assert st == -5 and f"non-finite vertex {v0.shape[0] - 1}" in msg, msg
+    t = t0.copy()
+    t[23, 1] = v0.shape[0]
+    t[30, 0] = -1
+    st, msg, _ = make(v0, t, b0)
+    assert st == -1 and f"triangle 23 indexes vertex {v0.shape[0]}" in msg, msg
+    b = b0.copy()
+    b[11] = nb
+    t = t0.copy()
+    t[12, 2] = -7
+    st, msg, _ = make(v0, t, b)
+    assert st == -1 and f"building id {nb} of triangle 11" in msg, msg
+    st, msg, h = make(v0, t0, b0)
+    assert st == 0, msg
+    sc = B.Scene.__new__(B.Scene)
+    sc.handle, sc.n_buildings = h, nb
+    info = sc.info()
+    assert info["n_tris"] == t0.shape[0] and info["n_buildings"] == nb
+    assert info["min_z"] == float(mesh.verts[t0.ravel(), 2].min())  # the unused vertex is not a bound
+    # the scene works: same counts as the binding's own scene of the plain mesh
+    ref = B.Scene(mesh.verts, mesh.tris, mesh.tri_building, nb)
+    st_ = configs.boxes16().sun
+    sun = B.Sun(st_.dirs, st_.day_start)
+    pts = B.Receivers.points(np.array([[x, y, 0.0] for x in range(0, 120, 7) for y in range(0, 80, 9)], np.float32))
+    a = B.sa_accumulate(ref, pts, sun, 2.0, "accrual_trace")[0]
+    c = B.sa_accumulate(sc, pts, sun, 2.0, "accrual_trace")[0]
+    assert torch.equal(a, c) and int(a.sum()) > 0
