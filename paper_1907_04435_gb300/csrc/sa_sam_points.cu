@@ -64,6 +64,9 @@ struct RunLight {
     // implies on each side: a ray point at height h above the receiver lies within
     // [-h da_hi, h da_lo] of it along e1 and [-h db_hi, h db_lo] along e2 (all >= 0)
     float da_hi, da_lo, db_hi, db_lo;
+    // every step direction of the run is d_m + alpha t + beta b + nu n (t, b, n: an FP32
+    // basis around d_m), with |alpha| <= ba, |beta| <= bb, |nu| <= bn
+    float dm[3], tv[3], bv[3], ba, bb, bn;
 };
 
 __device__ __forceinline__ void light_ab(const RunLight& rl, float x, float y, float z, float* a,
@@ -192,6 +195,20 @@ struct TileArgs {
 // Results are OR-ed into per-receiver masks in shared memory, then into the block masks.
 constexpr int kQueue = 64;
 
+// Bounds [lo, hi] on the FP32 value of d . v (in the rounding of the step tests) at every
+// step d of the run, for a vector v of the triangle: d . v = d_m . v + alpha (t . v) +
+// beta (b . v) + nu (n . v) exactly, n . v is within 2e-7 |v|_1 of d_m . v, and 2^-20 |v|_1
+// covers the roundings of the step test's value and of these bounds (each below 8 ulp of
+// |v|_1: every direction component is at most 1 in magnitude).
+__device__ __forceinline__ float2 run_dot_bounds(const RunLight& rl, float vx, float vy, float vz) {
+    const float c = fmaf(rl.dm[2], vz, fmaf(rl.dm[1], vy, rl.dm[0] * vx));
+    const float tv = fmaf(rl.tv[2], vz, fmaf(rl.tv[1], vy, rl.tv[0] * vx));
+    const float bv = fmaf(rl.bv[2], vz, fmaf(rl.bv[1], vy, rl.bv[0] * vx));
+    const float l1 = fabsf(vx) + fabsf(vy) + fabsf(vz);
+    const float r = fmaf(rl.ba, fabsf(tv), fmaf(rl.bb, fabsf(bv), fmaf(rl.bn, fabsf(c), 0x1p-20f * l1)));
+    return make_float2(c - r, c + r);
+}
+
 // Lines of a triangle's light-space projection, as unit inward normals and offsets: a point
 // x is inside iff n . x + c >= 0 for all three.  A ray of the run that meets the triangle at
 // height h above the receiver passes x = r + h delta, so r can be shadowed by it only if
@@ -279,9 +296,10 @@ k_sam_tile(TileArgs ta) {
     constexpr int kWarps = kTileThreads / 32;
     __shared__ float4 s_tri[kTriChunk * 3];
     __shared__ float4 s_n[kTriChunk];              // triangle normals (origin-independent set-up)
-    __shared__ float4 s_box[kTriChunk];            // light box (amin, amax, bmin, bmax)
-    __shared__ float4 s_edge[3][kTriChunk];        // light-space edge lines (nx, ny, c)
+    __shared__ float4 s_box[kTriChunk];            // light box (amin, amax, bmin, bmax), widened by the slack
+    __shared__ float4 s_edge[3][kTriChunk];        // light-space edge lines (nx, ny, c + slack, drift)
     __shared__ float s_ztop[kTriChunk];            // highest vertex z
+    __shared__ float2 s_nd[kTriChunk];             // bounds of d . normal over the run's steps
     __shared__ unsigned s_front[kTriChunk];
     __shared__ unsigned long long s_d2[kRunMax / 2][3];   // directions of steps (k, k + 1), k even
     __shared__ float4 s_o[kTileThreads];           // receiver origins (and t_min) of the pass
@@ -319,10 +337,16 @@ k_sam_tile(TileArgs ta) {
             light_ab(rl, a.x, a.y, a.z, &pa[0], &pb[0]);
             light_ab(rl, b.x, b.y, b.z, &pa[1], &pb[1]);
             light_ab(rl, c.x, c.y, c.z, &pa[2], &pb[2]);
-            s_box[i] = make_float4(fminf(pa[0], fminf(pa[1], pa[2])), fmaxf(pa[0], fmaxf(pa[1], pa[2])),
-                                   fminf(pb[0], fminf(pb[1], pb[2])), fmaxf(pb[0], fmaxf(pb[1], pb[2])));
+            // the box and the edge lines carry the culls' slack already
+            s_box[i] = make_float4(fminf(pa[0], fminf(pa[1], pa[2])) - kLightSlack,
+                                   fmaxf(pa[0], fmaxf(pa[1], pa[2])) + kLightSlack,
+                                   fminf(pb[0], fminf(pb[1], pb[2])) - kLightSlack,
+                                   fmaxf(pb[0], fmaxf(pb[1], pb[2])) + kLightSlack);
             light_edges(pa, pb, rl, s_edge[0][i], s_edge[1][i], s_edge[2][i]);
+#pragma unroll
+            for (int q3 = 0; q3 < 3; ++q3) s_edge[q3][i].z += kLightSlack;
             s_ztop[i] = fmaxf(a.z, fmaxf(b.z, c.z));
+            s_nd[i] = run_dot_bounds(rl, nrm.x, nrm.y, nrm.z);
             s_front[i] = run_front(a, b, c, ta.steps, rl, cull);
         }
         __syncthreads();
@@ -350,24 +374,17 @@ k_sam_tile(TileArgs ta) {
             }
             int nl = 0;
             for (int t0 = 0; t0 < nt; t0 += 32) {
-                const int t = t0 + lane;
-                bool near = false;
-                if (t < nt && s_front[t]) {
-                    const float rise = s_ztop[t] - wz;
-                    if (rise >= -0.01f) {
-                        const float h = fmaxf(rise, 0.f);
-                        const float4 bx = s_box[t];
-                        near = !(wa1 < bx.x - fmaf(h, rl.da_hi, kLightSlack) ||
-                                 wa0 > bx.y + fmaf(h, rl.da_lo, kLightSlack) ||
-                                 wb1 < bx.z - fmaf(h, rl.db_hi, kLightSlack) ||
-                                 wb0 > bx.w + fmaf(h, rl.db_lo, kLightSlack));
+                const int t = t0 + lane;           // < kTriChunk: the arrays are read in bounds
+                const float rise = s_ztop[t] - wz;
+                const float h = fmaxf(rise, 0.f);
+                const float4 bx = s_box[t];
+                bool near = (t < nt) & (s_front[t] != 0u) & (rise >= -0.01f);
+                near &= (fmaf(h, rl.da_hi, wa1) >= bx.x) & (fmaf(-h, rl.da_lo, wa0) <= bx.y) &
+                        (fmaf(h, rl.db_hi, wb1) >= bx.z) & (fmaf(-h, rl.db_lo, wb0) <= bx.w);
 #pragma unroll
-                        for (int q3 = 0; q3 < 3; ++q3) {
-                            const float4 e = s_edge[q3][t];
-                            near = near && fmaxf(e.x * wa0, e.x * wa1) + fmaxf(e.y * wb0, e.y * wb1) + e.z >=
-                                               -fmaf(h, e.w, kLightSlack);
-                        }
-                    }
+                for (int q3 = 0; q3 < 3; ++q3) {
+                    const float4 e = s_edge[q3][t];
+                    near &= fmaf(h, e.w, fmaxf(e.x * wa0, e.x * wa1) + fmaxf(e.y * wb0, e.y * wb1) + e.z) >= 0.f;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, near);
                 if (near) s_list[warp][nl + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)t;
@@ -375,26 +392,31 @@ k_sam_tile(TileArgs ta) {
             }
             int n = 0;
             __syncwarp();
+            // a lane without a receiver rises below every triangle
+            const float pz = live ? p.z : 3.4e38f;
             for (int j = 0; j < nl; ++j) {
                 const int t = s_list[warp][j];
-                bool pass = false;
-                if (live) {
-                    const float rise = s_ztop[t] - p.z;
-                    if (rise >= -0.01f) {
-                        const float h = fmaxf(rise, 0.f);
-                        const float4 bx = s_box[t];
-                        pass = !(la < bx.x - fmaf(h, rl.da_hi, kLightSlack) ||
-                                 la > bx.y + fmaf(h, rl.da_lo, kLightSlack) ||
-                                 lb < bx.z - fmaf(h, rl.db_hi, kLightSlack) ||
-                                 lb > bx.w + fmaf(h, rl.db_lo, kLightSlack));
-                        if (pass) {
+                const float rise = s_ztop[t] - pz;
+                const float h = fmaxf(rise, 0.f);
+                const float4 bx = s_box[t];
+                bool pass = (rise >= -0.01f) & (fmaf(h, rl.da_hi, la) >= bx.x) & (fmaf(-h, rl.da_lo, la) <= bx.y) &
+                            (fmaf(h, rl.db_hi, lb) >= bx.z) & (fmaf(-h, rl.db_lo, lb) <= bx.w);
+                if (pass) {
 #pragma unroll
-                            for (int q3 = 0; q3 < 3; ++q3) {
-                                const float4 e = s_edge[q3][t];
-                                pass = pass && fmaf(e.x, la, fmaf(e.y, lb, e.z)) >= -fmaf(h, e.w, kLightSlack);
-                            }
-                        }
+                    for (int q3 = 0; q3 < 3; ++q3) {
+                        const float4 e = s_edge[q3][t];
+                        pass &= fmaf(h, e.w, fmaf(e.x, la, fmaf(e.y, lb, e.z))) >= 0.f;
                     }
+                    // the receiver on the side of the triangle's plane that no ray of the run
+                    // leaves toward it: the step test's own distance check (a . n against
+                    // t_min d . n, same roundings) fails at every step
+                    const float4 v0 = s_tri[3 * t];
+                    const float4 nv = s_n[t];
+                    const float aon = fmaf(nv.z, __fsub_rn(v0.z, p.z),
+                                           fmaf(nv.y, __fsub_rn(v0.y, p.y), __fmul_rn(nv.x, __fsub_rn(v0.x, p.x))));
+                    const float2 nd = s_nd[t];
+                    if (nd.x > 0.f) pass &= aon > __fmul_rn(p.w, nd.x);
+                    else if (nd.y < 0.f) pass &= aon < __fmul_rn(p.w, nd.y);
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, pass);
                 if (pass) q[n + __popc(bal & ((1u << lane) - 1u))] =
@@ -512,6 +534,59 @@ void normalize3(double* v) {
     v[0] /= n; v[1] /= n; v[2] /= n;
 }
 
+// The run's middle direction d_m (as stored, FP32) and an FP32 orthonormal basis around
+// it: t along the run's motion, b = n x t, n = d_m / |d_m|; every step's d - d_m is solved
+// in that basis (Cramer's rule in double) and the largest |coefficients|, padded, bound
+// d . v - d_m . v over the run for any v (run_dot_bounds).
+void run_basis(const std::vector<StepConst>& h_steps, int j, int kn, int jm, const double* e1,
+               RunLight* rl) {
+    const float dmf[3] = {h_steps[jm].dx, h_steps[jm].dy, h_steps[jm].dz};
+    double n3[3] = {dmf[0], dmf[1], dmf[2]};
+    normalize3(n3);
+    const StepConst& sf = h_steps[j];
+    const StepConst& sl = h_steps[j + kn - 1];
+    double t3[3] = {(double)sl.dx - sf.dx, (double)sl.dy - sf.dy, (double)sl.dz - sf.dz};
+    const double tn = t3[0] * n3[0] + t3[1] * n3[1] + t3[2] * n3[2];
+    for (int q = 0; q < 3; ++q) t3[q] -= tn * n3[q];
+    if (t3[0] * t3[0] + t3[1] * t3[1] + t3[2] * t3[2] < 1e-24)
+        for (int q = 0; q < 3; ++q) t3[q] = e1[q];
+    normalize3(t3);
+    double b3[3] = {n3[1] * t3[2] - n3[2] * t3[1], n3[2] * t3[0] - n3[0] * t3[2], n3[0] * t3[1] - n3[1] * t3[0]};
+    normalize3(b3);
+    float tf[3], bf[3], nf[3];
+    for (int q = 0; q < 3; ++q) {
+        tf[q] = (float)t3[q];
+        bf[q] = (float)b3[q];
+        nf[q] = (float)n3[q];
+    }
+    const double M[3][3] = {{tf[0], bf[0], nf[0]}, {tf[1], bf[1], nf[1]}, {tf[2], bf[2], nf[2]}};
+    auto det3 = [](const double A[3][3]) {
+        return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+               A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+               A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    };
+    const double D = det3(M);
+    double mx[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < kn; ++k) {
+        const StepConst& s = h_steps[j + k];
+        const double dl[3] = {(double)s.dx - dmf[0], (double)s.dy - dmf[1], (double)s.dz - dmf[2]};
+        for (int col = 0; col < 3; ++col) {
+            double Mc[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) Mc[r][c] = c == col ? dl[r] : M[r][c];
+            mx[col] = std::max(mx[col], fabs(det3(Mc) / D));
+        }
+    }
+    for (int q = 0; q < 3; ++q) {
+        rl->dm[q] = dmf[q];
+        rl->tv[q] = tf[q];
+        rl->bv[q] = bf[q];
+    }
+    rl->ba = (float)(mx[0] * (1.0 + 1e-6) + 1e-12);
+    rl->bb = (float)(mx[1] * (1.0 + 1e-6) + 1e-12);
+    rl->bn = (float)(mx[2] * (1.0 + 1e-6) + 1e-12);
+}
+
 int g_point_run = 27;
 
 }  // namespace
@@ -595,6 +670,7 @@ cudaError_t launch_sam_points(const DevScene& sc, const float* scene_box, const 
                 rl.db_hi = (float)(db_hi * 1.0001 + pad);
                 rl.db_lo = (float)(-db_lo * 1.0001 + pad);
                 rl.zr = (float)zmin_r - 0.01f;
+                run_basis(h_steps, bc.j0 + k0, rl.kn, jm, e1, &rl);
                 for (int q = 0; q < 3; ++q) { rl.e1[q] = (float)e1[q]; rl.e2[q] = (float)e2[q]; rl.c[q] = (float)c[q]; }
                 // tile grid over the light-space box of the receivers
                 double amin = 1e30, amax = -1e30, bmin = 1e30, bmax = -1e30;
