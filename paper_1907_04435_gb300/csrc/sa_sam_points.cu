@@ -243,14 +243,23 @@ __device__ __forceinline__ void light_edges(const float* pa, const float* pb, co
 template <bool COUNT>
 __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int lane,
                                             const float4* s_tri, const float4* s_n,
-                                            const unsigned* s_front, const float4* s_o,
-                                            unsigned* s_m, const unsigned long long (*s_d2)[3],
-                                            int kn, unsigned long long& n_pair,
+                                            const float2* s_nd, const unsigned* s_front,
+                                            const float4* s_o, unsigned* s_m,
+                                            const unsigned long long (*s_d2)[3], int kn,
+                                            unsigned long long& n_pair,
                                             unsigned long long& n_test) {
-    if (lane >= n) return;
-    const unsigned e = q[lane];
+    const bool live = lane < n;
+    const unsigned e = live ? q[lane] : 0u;
     const int who = (int)(e >> 8), t = (int)(e & 0xffu);
     const float4 p = s_o[who];
+    const float2 ndb = s_nd[t];
+    // A receiver whose rays start at distance 0 (t_min = 0: the facade samples) with d . n
+    // of one sign at every step of the run: its pair passed the plane-side cull, so the
+    // distance check (a . n against 0 x d . n) holds at every step and only the inside
+    // test varies.  A warp whose pairs all are so skips the distance check.
+    const bool const_ahead = !live || (p.w == 0.f && (ndb.x > 0.f || ndb.y < 0.f));
+    const bool all_const = __all_sync(0xffffffffu, const_ahead);
+    if (!live) return;
     const float3 o = make_float3(p.x, p.y, p.z);
     const float4 a = s_tri[3 * t], b = s_tri[3 * t + 1], c = s_tri[3 * t + 2];
     const unsigned want = s_front[t];
@@ -260,29 +269,48 @@ __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int 
     // every step of the run is tested without branches, two steps per packed instruction
     // (the same roundings as plucker_hit_all); steps the triangle turns away from, and the
     // repeated step of an odd run's last pair, are masked off afterwards
-    unsigned long long M[3][3], N[3];
+    unsigned long long M[3][3];
 #pragma unroll
     for (int e = 0; e < 3; ++e)
 #pragma unroll
         for (int c = 0; c < 3; ++c) M[e][c] = f2_pack(pt.m[e][c], pt.m[e][c]);
-    N[0] = f2_pack(pt.nx, pt.nx); N[1] = f2_pack(pt.ny, pt.ny); N[2] = f2_pack(pt.nz, pt.nz);
     unsigned m = 0;
+    if (all_const) {
 #pragma unroll
-    for (int k = 0; k < kRunMax; k += 2) {
-        if (k >= kn) break;
-        const unsigned long long dx = s_d2[k >> 1][0], dy = s_d2[k >> 1][1], dz = s_d2[k >> 1][2];
-        float sv[3][2], nd[2];
+        for (int k = 0; k < kRunMax; k += 2) {
+            if (k >= kn) break;
+            const unsigned long long dx = s_d2[k >> 1][0], dy = s_d2[k >> 1][1], dz = s_d2[k >> 1][2];
+            float sv[3][2];
 #pragma unroll
-        for (int e = 0; e < 3; ++e)
-            f2_unpack(f2_fma(dz, M[e][2], f2_fma(dy, M[e][1], f2_mul(dx, M[e][0]))), sv[e][0], sv[e][1]);
-        f2_unpack(f2_fma(dz, N[2], f2_fma(dy, N[1], f2_mul(dx, N[0]))), nd[0], nd[1]);
+            for (int e = 0; e < 3; ++e)
+                f2_unpack(f2_fma(dz, M[e][2], f2_fma(dy, M[e][1], f2_mul(dx, M[e][0]))), sv[e][0], sv[e][1]);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const bool inside = min3f(sv[0][h], sv[1][h], sv[2][h]) >= 0.f ||
-                                max3f(sv[0][h], sv[1][h], sv[2][h]) <= 0.f;
-            const float lim = __fmul_rn(p.w, nd[h]);
-            const bool ahead = (nd[h] > 0.f && pt.aon > lim) || (nd[h] < 0.f && pt.aon < lim);
-            if (inside && ahead) m |= 1u << (k + h);
+            for (int h = 0; h < 2; ++h) {
+                const bool inside = min3f(sv[0][h], sv[1][h], sv[2][h]) >= 0.f ||
+                                    max3f(sv[0][h], sv[1][h], sv[2][h]) <= 0.f;
+                if (inside) m |= 1u << (k + h);
+            }
+        }
+    } else {
+        unsigned long long N[3];
+        N[0] = f2_pack(pt.nx, pt.nx); N[1] = f2_pack(pt.ny, pt.ny); N[2] = f2_pack(pt.nz, pt.nz);
+#pragma unroll
+        for (int k = 0; k < kRunMax; k += 2) {
+            if (k >= kn) break;
+            const unsigned long long dx = s_d2[k >> 1][0], dy = s_d2[k >> 1][1], dz = s_d2[k >> 1][2];
+            float sv[3][2], nd[2];
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+                f2_unpack(f2_fma(dz, M[e][2], f2_fma(dy, M[e][1], f2_mul(dx, M[e][0]))), sv[e][0], sv[e][1]);
+            f2_unpack(f2_fma(dz, N[2], f2_fma(dy, N[1], f2_mul(dx, N[0]))), nd[0], nd[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const bool inside = min3f(sv[0][h], sv[1][h], sv[2][h]) >= 0.f ||
+                                    max3f(sv[0][h], sv[1][h], sv[2][h]) <= 0.f;
+                const float lim = __fmul_rn(p.w, nd[h]);
+                const bool ahead = (nd[h] > 0.f && pt.aon > lim) || (nd[h] < 0.f && pt.aon < lim);
+                if (inside && ahead) m |= 1u << (k + h);
+            }
         }
     }
     m &= want;
@@ -424,14 +452,14 @@ k_sam_tile(TileArgs ta) {
                 n += __popc(bal);
                 if (n >= 32) {
                     __syncwarp();
-                    drain_pairs<COUNT>(q + (n - 32), 32, lane, s_tri, s_n, s_front, s_o, s_m, s_d2,
+                    drain_pairs<COUNT>(q + (n - 32), 32, lane, s_tri, s_n, s_nd, s_front, s_o, s_m, s_d2,
                                        kn, n_pair, n_test);
                     n -= 32;
                     __syncwarp();
                 }
             }
             __syncwarp();
-            drain_pairs<COUNT>(q, n, lane, s_tri, s_n, s_front, s_o, s_m, s_d2, kn, n_pair, n_test);
+            drain_pairs<COUNT>(q, n, lane, s_tri, s_n, s_nd, s_front, s_o, s_m, s_d2, kn, n_pair, n_test);
             __syncwarp();
             const unsigned m = s_m[threadIdx.x];
             if (live && m) atomicOr(&ta.masks[(long long)rl.blk * ta.R + s], (unsigned long long)m << rl.k0);
