@@ -422,9 +422,11 @@ k_sam_tile(TileArgs ta) {
             __syncwarp();
             // a lane without a receiver rises below every triangle
             const float pz = live ? p.z : 3.4e38f;
-            for (int j = 0; j < nl; ++j) {
-                const int t = s_list[warp][j];
-                const float rise = s_ztop[t] - pz;
+            // j == nl drains the queue's last pairs: one call site keeps the unrolled step
+            // tests in the instruction cache once
+            for (int j = 0; j <= nl; ++j) {
+                const int t = j < nl ? (int)s_list[warp][j] : 0;    // j == nl: nothing passes
+                const float rise = j < nl ? s_ztop[t] - pz : -3.4e38f;
                 const float h = fmaxf(rise, 0.f);
                 const float4 bx = s_box[t];
                 bool pass = (rise >= -0.01f) & (fmaf(h, rl.da_hi, la) >= bx.x) & (fmaf(-h, rl.da_lo, la) <= bx.y) &
@@ -450,16 +452,15 @@ k_sam_tile(TileArgs ta) {
                 if (pass) q[n + __popc(bal & ((1u << lane) - 1u))] =
                     (unsigned short)(((unsigned)threadIdx.x << 8) | (unsigned)t);
                 n += __popc(bal);
-                if (n >= 32) {
+                if (n >= 32 || (j == nl && n > 0)) {
+                    const int cnt = min(n, 32);
                     __syncwarp();
-                    drain_pairs<COUNT>(q + (n - 32), 32, lane, s_tri, s_n, s_nd, s_front, s_o, s_m, s_d2,
+                    drain_pairs<COUNT>(q + (n - cnt), cnt, lane, s_tri, s_n, s_nd, s_front, s_o, s_m, s_d2,
                                        kn, n_pair, n_test);
-                    n -= 32;
+                    n -= cnt;
                     __syncwarp();
                 }
             }
-            __syncwarp();
-            drain_pairs<COUNT>(q, n, lane, s_tri, s_n, s_nd, s_front, s_o, s_m, s_d2, kn, n_pair, n_test);
             __syncwarp();
             const unsigned m = s_m[threadIdx.x];
             if (live && m) atomicOr(&ta.masks[(long long)rl.blk * ta.R + s], (unsigned long long)m << rl.k0);
