@@ -185,10 +185,11 @@ struct EdgeRef {
 
 // The sign is folded into the edge vector: P, Qx and Qy are then the canonical values
 // times +-1, and since rounding to nearest is symmetric under negation every step's edge
-// value is the canonical one times +-1 exactly, up to the sign of a zero.  The step test
+// value is the canonical one times +-1 exactly, up to the sign of a zero.  The front test
 // takes +0 as inside and -0 as outside; where the two triangles of an edge both get a
 // zero, at least one of them gets +0 (a rounded sum of zeros is -0 only when both terms
 // are -0, and the other triangle's terms are then +0), so a cell on the edge is covered.
+// The back test takes both zeros as inside.
 __device__ __forceinline__ EdgeRef edge_ref(const float4& a, const float4& b) {
     const bool keep = a.x < b.x || (a.x == b.x && (a.y < b.y || (a.y == b.y && a.z < b.z)));
     const float4& v = keep ? a : b;
@@ -266,9 +267,10 @@ __device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeRef
     const unsigned long long* upx = sm.upx[k0 & 1] + (k0 >> 1);
     const unsigned long long* upy = sm.upy[k0 & 1] + (k0 >> 1);
     // Fully unrolled over the longest run.  A step covers the cell from the front when no
-    // edge value has its sign bit set (+0 counts as inside, -0 as outside), from the back
-    // when all three have; each step's bit is shifted in from the sign word, so the mask
-    // comes out in reverse step order.
+    // edge value has its sign bit set (+0 counts as inside, -0 as outside): that bit is
+    // shifted in from the sign word, so the front mask comes out in reverse step order.
+    // From the back (open scenes) all three values are <= 0, zeros of either sign
+    // included: two back faces sharing an edge may both get +0 there.
     unsigned hf = 0, hb = 0;
 #pragma unroll
     for (int k = 0; k < 32; k += 2) {
@@ -281,14 +283,13 @@ __device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeRef
         for (int h = 0; h < 2; ++h) {
             const unsigned a = __float_as_uint(f[0][h]), b = __float_as_uint(f[1][h]), c = __float_as_uint(f[2][h]);
             hf = __funnelshift_l(~(a | b | c), hf, 1);
-            if (!CULL) hb = __funnelshift_l(a & b & c, hb, 1);
+            if (!CULL && max3f(f[0][h], f[1][h], f[2][h]) <= 0.f) hb |= 1u << (k + h);
         }
     }
     // steps 0 .. K2 - 1 (an odd run's last pair repeats a step beyond it, which the masks
     // below drop) back in order: step k at bit k
     const int K2 = (kn + 1) & ~1;
     hf = __brev(hf) >> (32 - K2);
-    if (!CULL) hb = __brev(hb) >> (32 - K2);
     return CULL ? (hf & fr) : ((hf & fr) | (hb & bk));
 }
 

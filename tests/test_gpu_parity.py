@@ -403,3 +403,34 @@ def test_mesh_contents_are_checked_on_the_device(cuda_lib, on_device):
     a = B.sa_accumulate(ref, pts, sun, 2.0, "accrual_trace")[0]
     c = B.sa_accumulate(sc, pts, sun, 2.0, "accrual_trace")[0]
     assert torch.equal(a, c) and int(a.sum()) > 0
+
+
+@pytest.mark.parametrize("up", [True, False])
+@pytest.mark.parametrize("closed", [False, True])
+def test_cells_on_a_shared_edge_are_covered(cuda_lib, up, closed):
+    """A square roof of two triangles at z = 1 and a sun at azimuth 45 deg (d_x = d_y
+    exactly): the projected diagonal, the triangles' shared edge, passes exactly through
+    the cell centres (c, c), where the edge value is an exact zero in both triangles.
+    Every exact method still shadows those cells at every step, whichever way the
+    triangles face (open scene: the back-facing case too; a closed scene is declared
+    only with the faces up)."""
+    B = cuda_lib
+    if closed and not up:
+        pytest.skip("a closed scene's sun-facing faces point up")
+    v = np.array([[0, 0, 1], [4, 0, 1], [4, 4, 1], [0, 4, 1]], np.float32)
+    t = np.array([[0, 1, 2], [0, 2, 3]] if up else [[0, 2, 1], [0, 3, 2]], np.int32)
+    scene = B.Scene(v, t, None, 1, closed=closed)
+    el = np.radians(np.array([50.0, 55.0, 60.0, 65.0]))
+    h = (np.cos(el) / np.sqrt(2.0)).astype(np.float32)
+    dirs = np.stack([h, h, np.sin(el).astype(np.float32)], 1).astype(np.float32)
+    assert np.array_equal(dirs[:, 0], dirs[:, 1])
+    sun = B.Sun(dirs, np.array([0, 4], np.int32))
+    grid = B.Receivers.ground_grid(-2.0, -2.0, 1.0, 8, 8)
+    diag = [(c + 2) * 8 + (c + 2) for c in (0, 1, 2)]       # centres (0.5, 0.5) ... (2.5, 2.5)
+    for m in ("accrual_sam", "sweep_raster", "accrual_trace", "sweep_trace"):
+        g, _, _ = _run(B, scene, grid, sun, m)
+        assert (g[diag] == 4).all(), (m, g[diag])
+    pts = B.Receivers.points(np.array([[c, c, 0.0] for c in (0.5, 1.5, 2.5)], np.float32))
+    for m in POINT_METHODS:
+        g, _, _ = _run(B, scene, pts, sun, m)
+        assert (g == 4).all(), (m, g)
