@@ -334,8 +334,9 @@ int32_t sa_batch_affected_items(const sa_batch* b);
  * work runs as a CUDA graph (instantiated on the first call with these output pointers)
  * holding one persistent launch that drains a work queue. */
 sa_status sa_batch_run(sa_batch* b, int32_t* counts, int32_t* impact, void* stream);
-/* Autotuner: times 2, 3 or 4 persistent CTAs per SM x raster runs of 8, 16 or 24 steps on
- * an eighth of the work items and keeps the fastest; reports the choice. */
+/* Autotuner: times 2 to 6 persistent CTAs per SM (as many as the raster kernels are built
+ * to hold) x raster runs of 8, 16 or 24 steps on an eighth of the work items and keeps the
+ * fastest; reports the choice. */
 sa_status sa_batch_tune(sa_batch* b, int32_t* best_ctas, int32_t* best_run, void* stream);
 /* Work counters of one batch run (counters [2] cell set-ups, [3] cell-step tests). */
 sa_status sa_batch_work_counters(sa_batch* b, uint64_t* counters, void* stream);

@@ -50,6 +50,7 @@ int g_tile_skip = 1;
 }  // namespace
 void set_batch_tile_skip(int on) { g_tile_skip = on; }
 int get_batch_tile_skip() { return g_tile_skip; }
+int raster_ctas_per_sm();   // sa_raster.cu: the CTAs per SM its kernels are compiled for
 }  // namespace sa
 
 namespace {
@@ -365,7 +366,7 @@ sa_status sa_batch_tune(sa_batch* b, int32_t* best_ctas, int32_t* best_run, void
     float best = 3.4e38f;
     int bc = b->ctas, br = b->run;
     const int runs[3] = {8, 16, 24};
-    for (int c = 2; c <= 4 && e == cudaSuccess; ++c)
+    for (int c = 2; c <= sa::raster_ctas_per_sm() && e == cudaSuccess; ++c)
         for (int r : runs) {
             const sa::BatchLaunch bl = launch_of(b, scratch, nullptr, n, c * b->sms, r, nullptr);
             e = sa::launch_batch(bl, st);                                   // warm-up

@@ -36,9 +36,10 @@ constexpr int kRasterThreads = 256;     // 8 warps x 4 rows each
 #define SA_RASTER_BATCH 64
 #endif
 constexpr int kTriBatch = SA_RASTER_BATCH;
-// resident CTAs per SM the raster kernels are compiled for (registers: 65536 / (256 x this))
+// resident CTAs per SM the raster kernels are compiled for (registers: 65536 / (256 x this));
+// 6 is also what their 35.9 KB of shared memory allows
 #ifndef SA_RASTER_CTAS
-#define SA_RASTER_CTAS 4
+#define SA_RASTER_CTAS 6
 #endif
 
 struct TileGeom {
@@ -1035,6 +1036,8 @@ cudaError_t build_bins(const DevScene& sc, const DevRecv& rc, const DevSun& sun,
     }
     return e;
 }
+
+int raster_ctas_per_sm() { return SA_RASTER_CTAS; }
 
 cudaError_t launch_batch(const BatchLaunch& bl, cudaStream_t st) {
     BatchArgs ba;
