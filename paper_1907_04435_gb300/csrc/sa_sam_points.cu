@@ -243,7 +243,7 @@ __device__ __forceinline__ void light_edges(const float* pa, const float* pb, co
 template <bool COUNT>
 __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int lane,
                                             const float4* s_tri, const float4* s_n,
-                                            const float2* s_nd, const unsigned* s_front,
+                                            const unsigned* s_front,
                                             const float4* s_o, unsigned* s_m,
                                             const unsigned long long (*s_d2)[3], int kn,
                                             unsigned long long& n_pair,
@@ -252,7 +252,7 @@ __device__ __forceinline__ void drain_pairs(const unsigned short* q, int n, int 
     const unsigned e = live ? q[lane] : 0u;
     const int who = (int)(e >> 8), t = (int)(e & 0xffu);
     const float4 p = s_o[who];
-    const float2 ndb = s_nd[t];
+    const float2 ndb = make_float2(s_tri[3 * t + 1].w, s_tri[3 * t + 2].w);
     // A receiver whose rays start at distance 0 (t_min = 0: the facade samples) with d . n
     // of one sign at every step of the run: its pair passed the plane-side cull, so the
     // distance check (a . n against 0 x d . n) holds at every step and only the inside
@@ -323,11 +323,11 @@ __global__ void __launch_bounds__(kTileThreads, SA_TILE_CTAS)
 k_sam_tile(TileArgs ta) {
     constexpr int kWarps = kTileThreads / 32;
     __shared__ float4 s_tri[kTriChunk * 3];
-    __shared__ float4 s_n[kTriChunk];              // triangle normals (origin-independent set-up)
+    // staged triangles: vertices in .xyz; .w of the second and third vertex hold the
+    // bounds of d . n over the run's steps (run_dot_bounds)
+    __shared__ float4 s_n[kTriChunk];              // normals (origin-independent set-up), highest vertex z in .w
     __shared__ float4 s_box[kTriChunk];            // light box (amin, amax, bmin, bmax), widened by the slack
     __shared__ float4 s_edge[3][kTriChunk];        // light-space edge lines (nx, ny, c + slack, drift)
-    __shared__ float s_ztop[kTriChunk];            // highest vertex z
-    __shared__ float2 s_nd[kTriChunk];             // bounds of d . normal over the run's steps
     __shared__ unsigned s_front[kTriChunk];
     __shared__ unsigned long long s_d2[kRunMax / 2][3];   // directions of steps (k, k + 1), k even
     __shared__ float4 s_o[kTileThreads];           // receiver origins (and t_min) of the pass
@@ -360,7 +360,7 @@ k_sam_tile(TileArgs ta) {
                          c = __ldg(&ta.sc.tris[3 * t + 2]);
             s_tri[3 * i] = a; s_tri[3 * i + 1] = b; s_tri[3 * i + 2] = c;
             const float3 nrm = plucker_normal(a, b, c);
-            s_n[i] = make_float4(nrm.x, nrm.y, nrm.z, 0.f);
+            s_n[i] = make_float4(nrm.x, nrm.y, nrm.z, fmaxf(a.z, fmaxf(b.z, c.z)));
             float pa[3], pb[3];
             light_ab(rl, a.x, a.y, a.z, &pa[0], &pb[0]);
             light_ab(rl, b.x, b.y, b.z, &pa[1], &pb[1]);
@@ -373,8 +373,9 @@ k_sam_tile(TileArgs ta) {
             light_edges(pa, pb, rl, s_edge[0][i], s_edge[1][i], s_edge[2][i]);
 #pragma unroll
             for (int q3 = 0; q3 < 3; ++q3) s_edge[q3][i].z += kLightSlack;
-            s_ztop[i] = fmaxf(a.z, fmaxf(b.z, c.z));
-            s_nd[i] = run_dot_bounds(rl, nrm.x, nrm.y, nrm.z);
+            const float2 ndb = run_dot_bounds(rl, nrm.x, nrm.y, nrm.z);
+            s_tri[3 * i + 1].w = ndb.x;
+            s_tri[3 * i + 2].w = ndb.y;
             s_front[i] = run_front(a, b, c, ta.steps, rl, cull);
         }
         __syncthreads();
@@ -403,7 +404,7 @@ k_sam_tile(TileArgs ta) {
             int nl = 0;
             for (int t0 = 0; t0 < nt; t0 += 32) {
                 const int t = t0 + lane;           // < kTriChunk: the arrays are read in bounds
-                const float rise = s_ztop[t] - wz;
+                const float rise = s_n[t].w - wz;
                 const float h = fmaxf(rise, 0.f);
                 const float4 bx = s_box[t];
                 bool near = (t < nt) & (s_front[t] != 0u) & (rise >= -0.01f);
@@ -426,7 +427,7 @@ k_sam_tile(TileArgs ta) {
             // tests in the instruction cache once
             for (int j = 0; j <= nl; ++j) {
                 const int t = j < nl ? (int)s_list[warp][j] : 0;    // j == nl: nothing passes
-                const float rise = j < nl ? s_ztop[t] - pz : -3.4e38f;
+                const float rise = j < nl ? s_n[t].w - pz : -3.4e38f;
                 const float h = fmaxf(rise, 0.f);
                 const float4 bx = s_box[t];
                 bool pass = (rise >= -0.01f) & (fmaf(h, rl.da_hi, la) >= bx.x) & (fmaf(-h, rl.da_lo, la) <= bx.y) &
@@ -444,7 +445,7 @@ k_sam_tile(TileArgs ta) {
                     const float4 nv = s_n[t];
                     const float aon = fmaf(nv.z, __fsub_rn(v0.z, p.z),
                                            fmaf(nv.y, __fsub_rn(v0.y, p.y), __fmul_rn(nv.x, __fsub_rn(v0.x, p.x))));
-                    const float2 nd = s_nd[t];
+                    const float2 nd = make_float2(s_tri[3 * t + 1].w, s_tri[3 * t + 2].w);
                     if (nd.x > 0.f) pass &= aon > __fmul_rn(p.w, nd.x);
                     else if (nd.y < 0.f) pass &= aon < __fmul_rn(p.w, nd.y);
                 }
@@ -455,7 +456,7 @@ k_sam_tile(TileArgs ta) {
                 if (n >= 32 || (j == nl && n > 0)) {
                     const int cnt = min(n, 32);
                     __syncwarp();
-                    drain_pairs<COUNT>(q + (n - cnt), cnt, lane, s_tri, s_n, s_nd, s_front, s_o, s_m, s_d2,
+                    drain_pairs<COUNT>(q + (n - cnt), cnt, lane, s_tri, s_n, s_front, s_o, s_m, s_d2,
                                        kn, n_pair, n_test);
                     n -= cnt;
                     __syncwarp();
