@@ -711,7 +711,10 @@ def end_to_end(B, w, args, dev):
     h2d = sum(nbytes(t) for t in (verts, tris, tb, dirs, day_start, fpos, fnrm))
     d2h = 3 * R * 4
 
-    main = torch.cuda.current_stream()
+    # the scene build and the ground run on a high-priority stream: the build is a chain of
+    # small kernels, and the facade sort's wide kernels on the second stream would
+    # otherwise hold the SMs it waits for
+    main = torch.cuda.Stream(priority=-1)
     side = torch.cuda.Stream()
     sun_stream = torch.cuda.Stream()
     Rg = g.R
@@ -721,19 +724,20 @@ def end_to_end(B, w, args, dev):
         # The library's creation calls wait for their own stream before they return, and
         # ctypes lets the other threads run meanwhile: the sun table and the sorted facade
         # receivers are ready on the device once their futures resolve.  The ground
-        # accumulates on the current stream, the facades on the second one once the scene
-        # exists; each part's results go straight to its slice of the pinned output
+        # accumulates on the high-priority stream, the facades on the second one once the
+        # scene exists; each part's results go straight to its slice of the pinned output
         # (gross | minutes | continuous, ground then facades), the ground's while the
         # facades still run.
         sun_f = pool.submit(B.Sun, dirs, day_start, args.block_len, stream=sun_stream)
         fac_f = None if fpos is None else pool.submit(B.Receivers.points, fpos, fnrm, stream=side)
-        scene = B.Scene(verts, tris, tb, w.city.B, closed=True, stream=main)
-        grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
-        ready = main.record_event()
-        sun = sun_f.result()
-        gg, gm, gc = B.sa_accumulate(scene, grid, sun, st.step_minutes, "accrual_sam", stream=main)
-        for q, t in enumerate((gg, gm.view(torch.int32), gc)):
-            host_out[q * R:q * R + Rg].copy_(t, non_blocking=True)
+        with torch.cuda.stream(main):
+            scene = B.Scene(verts, tris, tb, w.city.B, closed=True, stream=main)
+            grid = B.Receivers.ground_grid(g.x0, g.y0, g.dx, g.nx, g.ny)
+            ready = main.record_event()
+            sun = sun_f.result()
+            gg, gm, gc = B.sa_accumulate(scene, grid, sun, st.step_minutes, "accrual_sam", stream=main)
+            for q, t in enumerate((gg, gm.view(torch.int32), gc)):
+                host_out[q * R:q * R + Rg].copy_(t, non_blocking=True)
         if fac_f is not None:
             fac = fac_f.result()
             side.wait_event(ready)
