@@ -36,6 +36,11 @@ constexpr int kRasterThreads = 256;     // 8 warps x 4 rows each
 #define SA_RASTER_BATCH 64
 #endif
 constexpr int kTriBatch = SA_RASTER_BATCH;
+// work units a warp claims at a time (<= 32: one lane each while their boxes are bounded)
+#ifndef SA_RASTER_CLAIM
+#define SA_RASTER_CLAIM 4
+#endif
+constexpr int kUnitClaim = SA_RASTER_CLAIM;
 // resident CTAs per SM the raster kernels are compiled for (registers: 65536 / (256 x this));
 // 6 is also what their 35.9 KB of shared memory allows
 #ifndef SA_RASTER_CTAS
@@ -321,121 +326,186 @@ __device__ __forceinline__ void drain_cells(TileSmem& sm, const unsigned* q, int
     if (hit) atomicOr(&sm.mask[SA_CHK(cell, kTile * kTile, sa::CK_RASTER_CELL)], (unsigned long long)hit << k0);
 }
 
-// One work unit: triangle t of the staged batch and run `sub` of the block.  The warp
-// bounds the run's swept projection, enumerates the covered cells row by row and tests
-// the run's steps per cell; step bits are ORed into sm.mask.
-template <bool COUNT, bool CULL>
-__device__ __forceinline__ void raster_unit(TileSmem& sm, int un, int nsub, int K,
-                                            float inv_dx, int& qn, unsigned long long& n_cell,
-                                            unsigned long long& n_test,
-                                            unsigned long long& n_unit,
-                                            unsigned long long& n_span) {
-    const int lane = threadIdx.x & 31;
-    // un = t nsub + sub; (un + 1/2) / nsub is at least 1 / (2 nsub) from an integer, far
-    // beyond the float quotient's rounding (relative 2^-23) for un < 2^13
-    const int t = (int)(((float)un + 0.5f) * sm.inv_nsub), sub = un - t * nsub;
-    const int k0 = sm.run_k0[sub], kn = sm.run_k0[sub + 1] - k0;       // balanced runs
+// A work unit is triangle t of the staged batch and run `sub` of the block, un = t nsub +
+// sub; (un + 1/2) / nsub is at least 1 / (2 nsub) from an integer, far beyond the float
+// quotient's rounding (relative 2^-23) for un < 2^13.
+struct UnitRun {
+    int t, sub, k0;
+    unsigned fr, bk;     // the run's steps the triangle faces (front; back, open scenes only)
+};
+
+template <bool CULL>
+__device__ __forceinline__ UnitRun unit_run(const TileSmem& sm, int un, int nsub) {
+    UnitRun u;
+    u.t = (int)(((float)un + 0.5f) * sm.inv_nsub);
+    u.sub = un - u.t * nsub;
+    u.k0 = sm.run_k0[u.sub];
+    const int kn = sm.run_k0[u.sub + 1] - u.k0;       // balanced runs
     const unsigned run_bits = (kn >= 32) ? 0xffffffffu : ((1u << kn) - 1u);
-    const unsigned fr = (unsigned)(sm.front[t] >> k0) & run_bits;
-    const unsigned bk = CULL ? 0u : ((unsigned)(sm.back[t] >> k0) & run_bits);
-    if ((fr | bk) == 0u) return;
-    const float4 a = sm.tri[3 * t], b = sm.tri[3 * t + 1], c = sm.tri[3 * t + 2];
-    // swept bounding box of the run's projections
-    const float4 ub = sm.ubox[sub];
+    u.fr = (unsigned)(sm.front[u.t] >> u.k0) & run_bits;
+    u.bk = CULL ? 0u : ((unsigned)(sm.back[u.t] >> u.k0) & run_bits);
+    return u;
+}
+
+// The cells of the tile whose centres (k + 0.5) dx fall in the swept bounding box of the
+// run's projections, with 0.01 cell of slack, as columns c0..c1 and rows r0..r1 packed
+// 5 bits each (c0 | c1 << 5 | r0 << 10 | r1 << 15); -1 when the unit reaches no cell.
+__device__ __forceinline__ int unit_box(const TileSmem& sm, const UnitRun& u, float inv_dx) {
+    if ((u.fr | u.bk) == 0u) return -1;
+    const float4 a = sm.tri[3 * u.t], b = sm.tri[3 * u.t + 1], c = sm.tri[3 * u.t + 2];
+    const float4 ub = sm.ubox[u.sub];
     const float uxlo = ub.x, uxhi = ub.y, uylo = ub.z, uyhi = ub.w;
     const float az = fmaxf(a.z, 0.f), bz = fmaxf(b.z, 0.f), cz = fmaxf(c.z, 0.f);
     const float xmin = fminf(a.x - az * uxhi, fminf(b.x - bz * uxhi, c.x - cz * uxhi));
     const float xmax = fmaxf(a.x - az * uxlo, fmaxf(b.x - bz * uxlo, c.x - cz * uxlo));
     const float ymin = fminf(a.y - az * uyhi, fminf(b.y - bz * uyhi, c.y - cz * uyhi));
     const float ymax = fmaxf(a.y - az * uylo, fmaxf(b.y - bz * uylo, c.y - cz * uylo));
-    // cells whose centres (k + 0.5) dx fall in the box, with 0.01 cell of slack
     const float fc0 = ceilf(xmin * inv_dx - 0.51f), fc1 = floorf(xmax * inv_dx - 0.49f);
     const float fr0 = ceilf(ymin * inv_dx - 0.51f), fr1 = floorf(ymax * inv_dx - 0.49f);
     if (fc1 < 0.f || fr1 < 0.f || fc0 > (float)(kTile - 1) || fr0 > (float)(kTile - 1) ||
-        fc0 > fc1 || fr0 > fr1) return;
+        fc0 > fc1 || fr0 > fr1) return -1;
     const int c0 = (int)fmaxf(fc0, 0.f), c1 = (int)fminf(fc1, (float)(kTile - 1));
     const int r0 = (int)fmaxf(fr0, 0.f), r1 = (int)fminf(fr1, (float)(kTile - 1));
-    // Row spans.  Each step's projection lies inside the projection for the run's
-    // middle slope u_m widened by (sx, sy) = z_max |u_hi - u_lo| / 2 (a vertex at
-    // height z moves by z (u_m - u_k)).  Lane j takes row r0 + j: the x-range of the
-    // middle projection over the band [y - sy, y + sy], widened by sx, bounds the
-    // row's covered cells (0.05 cell and 2 mm of slack absorb rounding).
-    const unsigned long long can = (unsigned long long)(fr | bk) << k0;
+    return c0 | (c1 << 5) | (r0 << 10) | (r1 << 15);
+}
+
+// Row span of a unit in tile row `row` (within its box): the cells cs .. cs + w - 1.
+// Each step's projection lies inside the projection for the run's middle slope u_m
+// widened by (sx, sy) = z_max |u_hi - u_lo| / 2 (a vertex at height z moves by
+// z (u_m - u_k)); the x-range of the middle projection over the band [y - sy, y + sy],
+// widened by sx, bounds the row's covered cells (0.05 cell and 2 mm of slack absorb
+// rounding).
+__device__ __forceinline__ void row_span(const TileSmem& sm, const UnitRun& u, int box, int row,
+                                         float inv_dx, int* cs, int* w) {
+    *cs = 0;
+    *w = 0;
+    const int c0 = box & 31, c1 = (box >> 5) & 31;
+    const float4 a = sm.tri[3 * u.t], b = sm.tri[3 * u.t + 1], c = sm.tri[3 * u.t + 2];
+    const float4 ub = sm.ubox[u.sub];
+    const float uxlo = ub.x, uxhi = ub.y, uylo = ub.z, uyhi = ub.w;
+    const float az = fmaxf(a.z, 0.f), bz = fmaxf(b.z, 0.f), cz = fmaxf(c.z, 0.f);
     const float umx = 0.5f * (uxlo + uxhi), umy = 0.5f * (uylo + uyhi);
     const float zm = fmaxf(az, fmaxf(bz, cz));
     const float slack = 0.05f + 2e-3f * inv_dx;                 // in cells
     const float sx = zm * (uxhi - uxlo) * 0.5f, sy = zm * (uyhi - uylo) * 0.5f;
     const float px[3] = {a.x - az * umx, b.x - bz * umx, c.x - cz * umx};
     const float py[3] = {a.y - az * umy, b.y - bz * umy, c.y - cz * umy};
-    int cs = 0, w = 0;
-    if (r0 + lane <= r1) {
-        const float y = sm.yl[r0 + lane];
-        const float band = sy + slack / inv_dx;
-        const float ya = y - band, yb = y + band;
-        float lo = 3.4e38f, hi = -3.4e38f;
+    const float y = sm.yl[row];
+    const float band = sy + slack / inv_dx;
+    const float ya = y - band, yb = y + band;
+    float lo = 3.4e38f, hi = -3.4e38f;
 #pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            if (py[v] >= ya && py[v] <= yb) { lo = fminf(lo, px[v]); hi = fmaxf(hi, px[v]); }
-            const int q = v == 2 ? 0 : v + 1;
-            const float dy = py[q] - py[v];
-            if (dy != 0.f) {
-                // the spans carry slack, so an approximate quotient suffices
-                const float slope = __fdividef(px[q] - px[v], dy);
-                const float e0 = fminf(py[v], py[q]), e1 = fmaxf(py[v], py[q]);
-                if (ya >= e0 && ya <= e1) {
-                    const float x = fmaf(ya - py[v], slope, px[v]);
-                    lo = fminf(lo, x); hi = fmaxf(hi, x);
-                }
-                if (yb >= e0 && yb <= e1) {
-                    const float x = fmaf(yb - py[v], slope, px[v]);
-                    lo = fminf(lo, x); hi = fmaxf(hi, x);
-                }
+    for (int v = 0; v < 3; ++v) {
+        if (py[v] >= ya && py[v] <= yb) { lo = fminf(lo, px[v]); hi = fmaxf(hi, px[v]); }
+        const int q = v == 2 ? 0 : v + 1;
+        const float dy = py[q] - py[v];
+        if (dy != 0.f) {
+            // the spans carry slack, so an approximate quotient suffices
+            const float slope = __fdividef(px[q] - px[v], dy);
+            const float e0 = fminf(py[v], py[q]), e1 = fmaxf(py[v], py[q]);
+            if (ya >= e0 && ya <= e1) {
+                const float x = fmaf(ya - py[v], slope, px[v]);
+                lo = fminf(lo, x); hi = fmaxf(hi, x);
             }
-        }
-        if (lo <= hi) {
-            const float f0 = fmaxf(ceilf((lo - sx) * inv_dx - 0.5f - slack), (float)c0);
-            const float f1 = fminf(floorf((hi + sx) * inv_dx - 0.5f + slack), (float)c1);
-            if (f0 <= f1) {
-                cs = (int)f0;
-                w = (int)f1 - cs + 1;
+            if (yb >= e0 && yb <= e1) {
+                const float x = fmaf(yb - py[v], slope, px[v]);
+                lo = fminf(lo, x); hi = fmaxf(hi, x);
             }
         }
     }
-    // lanes walk the spans' cells, 32 at a time; a binary search over the rows'
-    // inclusive prefix sums finds each cell's row
-    int incl = w;
+    if (lo <= hi) {
+        const float f0 = fmaxf(ceilf((lo - sx) * inv_dx - 0.5f - slack), (float)c0);
+        const float f1 = fminf(floorf((hi + sx) * inv_dx - 0.5f + slack), (float)c1);
+        if (f0 <= f1) {
+            *cs = (int)f0;
+            *w = (int)f1 - *cs + 1;
+        }
+    }
+}
+
+// Index of the lane whose inclusive prefix sum first exceeds idx (incl non-decreasing over
+// the lanes, idx < its value in lane 31).
+__device__ __forceinline__ int prefix_lane(int incl, int idx) {
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+        if (v <= idx) j += step;
+    }
+    return j;
+}
+
+__device__ __forceinline__ int lane_prefix(int x) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
+        const int v = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += v;
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (COUNT && lane == 0) { ++n_unit; n_span += (unsigned long long)total; }
-    const int excl = incl - w;
+    return x;
+}
+
+// Up to 32 work units un0 .. un0 + nu - 1, expanded level by level so that every lane
+// has work: one lane per unit bounds its swept box; one lane per covered row finds the
+// row's span; one lane per covered cell checks whether the cell is already shadowed at
+// every step its unit could set (a stale read only skips less) and queues the others,
+// (unit << 10) | cell, for the step tests, 32 at a time whichever unit they come from.
+template <bool COUNT, bool CULL>
+__device__ __forceinline__ void raster_units(TileSmem& sm, int un0, int nu, int nsub, float inv_dx,
+                                             int& qn, unsigned long long& n_cell,
+                                             unsigned long long& n_test,
+                                             unsigned long long& n_unit,
+                                             unsigned long long& n_span) {
+    const int lane = threadIdx.x & 31;
+    int box = -1;
+    if (lane < nu) box = unit_box(sm, unit_run<CULL>(sm, un0 + lane, nsub), inv_dx);
+    const int rows = box < 0 ? 0 : ((box >> 15) & 31) - ((box >> 10) & 31) + 1;
+    if (COUNT) {
+        const unsigned reach = __ballot_sync(0xffffffffu, rows > 0);
+        if (lane == 0) n_unit += (unsigned long long)__popc(reach);
+    }
+    const int rincl = lane_prefix(rows);
+    const int total_rows = __shfl_sync(0xffffffffu, rincl, 31);
     unsigned* q = sm.queue[threadIdx.x >> 5];
-    for (int base = 0; base < total; base += 32) {
-        const int idx = base + lane;
-        int j = 0;
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
-            if (v <= idx) j += step;
+    for (int rb = 0; rb < total_rows; rb += 32) {
+        // this lane's (unit, row)
+        const int ridx = rb + lane;
+        const int i = prefix_lane(rincl, ridx) & 31;
+        const int rex = __shfl_sync(0xffffffffu, rincl - rows, i);
+        const int ubox = __shfl_sync(0xffffffffu, box, i);
+        const int un = un0 + i;
+        int cs = 0, w = 0;
+        unsigned long long can = 0ull;
+        if (ridx < total_rows) {
+            const UnitRun u = unit_run<CULL>(sm, un, nsub);
+            const int row = ((ubox >> 10) & 31) + (ridx - rex);
+            row_span(sm, u, ubox, row, inv_dx, &cs, &w);
+            cs += row * kTile;                      // the row's first cell
+            can = (unsigned long long)(u.fr | u.bk) << u.k0;
         }
-        const int ex = __shfl_sync(0xffffffffu, excl, j & 31);
-        const int cj = __shfl_sync(0xffffffffu, cs, j & 31);
-        const int cell = (r0 + j) * kTile + cj + (idx - ex);
-        // a cell already shadowed at every step the unit could set has nothing to gain
-        // (a stale read only skips less); the others join the warp's queue
-        const bool need = idx < total &&
-                          (sm.mask[SA_CHK(cell, kTile * kTile, sa::CK_RASTER_CELL)] & can) != can;
-        const unsigned bal = __ballot_sync(0xffffffffu, need);
-        if (need) q[qn + __popc(bal & ((1u << lane) - 1u))] = ((unsigned)un << 10) | (unsigned)cell;
-        qn += __popc(bal);
-        if (qn >= 32) {
-            __syncwarp();
-            drain_cells<COUNT, CULL>(sm, q + (qn - 32), 32, nsub, n_cell, n_test);
-            qn -= 32;
-            __syncwarp();
+        const int cincl = lane_prefix(w);
+        const int total = __shfl_sync(0xffffffffu, cincl, 31);
+        if (COUNT && lane == 0) n_span += (unsigned long long)total;
+        const int cex = cincl - w;
+        for (int base = 0; base < total; base += 32) {
+            const int idx = base + lane;
+            const int j = prefix_lane(cincl, idx) & 31;
+            const int ex = __shfl_sync(0xffffffffu, cex, j);
+            const int cj = __shfl_sync(0xffffffffu, cs, j);
+            const int uj = __shfl_sync(0xffffffffu, un, j);
+            const unsigned long long cn = __shfl_sync(0xffffffffu, can, j);
+            const int cell = cj + (idx - ex);
+            const bool need = idx < total &&
+                              (sm.mask[SA_CHK(cell, kTile * kTile, sa::CK_RASTER_CELL)] & cn) != cn;
+            const unsigned bal = __ballot_sync(0xffffffffu, need);
+            if (need) q[qn + __popc(bal & ((1u << lane) - 1u))] = ((unsigned)uj << 10) | (unsigned)cell;
+            qn += __popc(bal);
+            if (qn >= 32) {
+                __syncwarp();
+                drain_cells<COUNT, CULL>(sm, q + (qn - 32), 32, nsub, n_cell, n_test);
+                qn -= 32;
+                __syncwarp();
+            }
         }
     }
 }
@@ -488,7 +558,7 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
             if (i % 3 == 0) sm.valid[i / 3] = ok ? 1 : 0;
         }
         __syncthreads();
-        if (threadIdx.x == 0) sm.next_unit = kWarpsRaster;
+        if (threadIdx.x == 0) sm.next_unit = kWarpsRaster * kUnitClaim;
         // sun-facing steps of each staged triangle: a warp per triangle, a lane per step
         for (int t = warp; t < nt; t += kWarpsRaster) {
             unsigned long long fr = 0, bk = 0;
@@ -526,15 +596,17 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
         }
         __syncthreads();
         const int units = nt * nsub;
-        // warps take units from a shared counter, so an expensive unit does not hold the
-        // warps that would otherwise wait for its warp at the next barrier
-        // (the next unit is claimed before this one is worked, hiding the atomic's latency)
-        int un = warp;
+        // warps take kUnitClaim units at a time from a shared counter, so an expensive
+        // group does not hold the warps that would otherwise wait for its warp at the next
+        // barrier (the next group is claimed before this one is worked, hiding the
+        // atomic's latency)
+        int un = warp * kUnitClaim;
         int qn = 0;
         while (un < units) {
             int nx = 0;
-            if (lane == 0) nx = atomicAdd(&sm.next_unit, 1);
-            raster_unit<COUNT, CULL>(sm, un, nsub, K, inv_dx, qn, n_cell, n_test, n_unit, n_span);
+            if (lane == 0) nx = atomicAdd(&sm.next_unit, kUnitClaim);
+            raster_units<COUNT, CULL>(sm, un, min(kUnitClaim, units - un), nsub, inv_dx, qn, n_cell, n_test,
+                                      n_unit, n_span);
             un = __shfl_sync(0xffffffffu, nx, 0);
         }
         // the queue's last cells, before the batch's triangles are replaced
