@@ -462,11 +462,11 @@ OPS_BOX, OPS_TRI = 12, 25
 # profile summary gives the command).  A figure is reported only while the kernel's
 # sources hash to the value they had when it was captured; otherwise traffic is null.
 TRAFFIC = {
-    "k_raster": {"bytes": 6998016 + 10662656, "workload": "district",
-                 "sources": ("sa_raster.cu", "sa_internal.cuh"), "sha256_16": "c45d7aa8cdb40fa5"},
-    "k_sam_tile": {"bytes": 155786752 + 26145280, "workload": "district",
+    "k_raster": {"bytes": 7003392 + 15011840, "workload": "district",
+                 "sources": ("sa_raster.cu", "sa_internal.cuh"), "sha256_16": "4e71a18b36820bae"},
+    "k_sam_tile": {"bytes": 155689216 + 26193152, "workload": "district",
                    "sources": ("sa_sam_points.cu", "sa_internal.cuh", "sa_handles.cuh"),
-                   "sha256_16": "5a77c76904fbdc48"},
+                   "sha256_16": "e9ff7eeb4764c3a4"},
 }
 
 
