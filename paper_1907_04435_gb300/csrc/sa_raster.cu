@@ -637,8 +637,8 @@ __device__ __forceinline__ void flush_raster_counts(unsigned long long* stats, u
 
 // One CTA per 32 x 32-cell tile, every block of the chunk in order; the gross /
 // continuous state of the thread's four cells stays in registers between blocks.
-template <bool COUNT, bool CULL>
-__global__ void __launch_bounds__(kRasterThreads, SA_RASTER_CTAS)
+template <bool COUNT, bool CULL, int CTAS>
+__global__ void __launch_bounds__(kRasterThreads, CTAS)
 k_raster(RasterArgs ra) {
     __shared__ TileSmem sm;
     __shared__ RunState s_st[kTile * kTile];       // gross / run / best of the tile's cells
@@ -836,14 +836,27 @@ __global__ void k_tile_order(const unsigned* __restrict__ counts, int nbc, int n
     for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) order[atomicAdd(&hist[bucket(t)], 1u)] = t;
 }
 
-void launch_k_raster(const RasterArgs& ra, int n_tiles, bool stats, cudaStream_t st) {
+template <int CTAS>
+void launch_k_raster_as(const RasterArgs& ra, int n_tiles, bool stats, cudaStream_t st) {
     if (ra.cull) {
-        if (stats) k_raster<true, true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
-        else k_raster<false, true><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        if (stats) k_raster<true, true, CTAS><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        else k_raster<false, true, CTAS><<<n_tiles, kRasterThreads, 0, st>>>(ra);
     } else {
-        if (stats) k_raster<true, false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
-        else k_raster<false, false><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        if (stats) k_raster<true, false, CTAS><<<n_tiles, kRasterThreads, 0, st>>>(ra);
+        else k_raster<false, false, CTAS><<<n_tiles, kRasterThreads, 0, st>>>(ra);
     }
+}
+
+// A launch of more tiles than 4 CTAs per SM hold takes the build for SA_RASTER_CTAS
+// resident CTAs per SM (fewer registers, more warps to hide latency); a smaller one, all of
+// whose tiles are resident at once anyway, takes the build for 4 (more registers, no
+// spills).
+void launch_k_raster(const RasterArgs& ra, int n_tiles, bool stats, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 0;
+    if (SA_RASTER_CTAS > 4 && n_tiles > 4 * sms) launch_k_raster_as<SA_RASTER_CTAS>(ra, n_tiles, stats, st);
+    else launch_k_raster_as<4>(ra, n_tiles, stats, st);
 }
 
 }  // namespace
