@@ -204,6 +204,26 @@ __device__ __forceinline__ EdgeRef edge_ref(const float4& a, const float4& b) {
     return EdgeRef{v.x, v.y, v.z, s * (w.x - v.x), s * (w.y - v.y), s * (w.z - v.z)};
 }
 
+// The edge's step-test terms as affine functions of the cell centre (x, y): with c = (x, y)
+// - v, P = e_x c_y - e_y c_x = pa y + pb x + pc, Q_x = -(v_z e_y + e_z c_y) = -ra y + qc and
+// Q_y = v_z e_x + e_z c_x = ra x + rc.  The constants are rounded once per staged triangle,
+// each from the edge vector in a way that an exactly negated edge vector negates exactly,
+// so the triangles sharing an edge still compute exactly negated values.
+struct EdgeLin {
+    float pa, pb, pc, ra, qc, rc;
+};
+
+__device__ __forceinline__ EdgeLin edge_lin(const EdgeRef& e) {
+    EdgeLin l;
+    l.pa = e.ex;
+    l.pb = -e.ey;
+    l.pc = -fmaf(l.pa, e.vy, l.pb * e.vx);
+    l.ra = e.ez;
+    l.qc = -fmaf(e.vz, e.ey, -(e.ez * e.vy));
+    l.rc = fmaf(e.vz, e.ex, -(e.ez * e.vx));
+    return l;
+}
+
 // Shared memory of one tile: staged triangles (xy tile-local), their sun-facing step
 // masks, the block's directions, ground slopes and per-run slope boxes, the tile's 64-bit
 // step masks and its cell centres.
@@ -212,8 +232,8 @@ struct TileSmem {
     unsigned long long front[kTriBatch];     // steps with n . d > 0
     unsigned long long back[kTriBatch];      // steps with n . d < 0 (open scenes only)
     int valid[kTriBatch];
-    // canonical edges (EdgeRef, 6 floats each) of the staged triangles, 20 floats apart so
-    // that a unit reads them as five float4
+    // the staged triangles' edge functions (EdgeLin, 6 floats each), 20 floats apart so
+    // that a cell's test reads them as five float4
     float edges[kTriBatch * 20];
     float2 u[kMaxBlock];
     // slopes of steps (k, k + 1) packed for the paired step tests: [0][i] starts at step
@@ -249,18 +269,17 @@ __device__ __forceinline__ void tile_setup(TileSmem& sm, const TileGeom& g, int 
 // The steps of one run (kn <= 32 steps from k0) that cover cell (x, y): bit k of the
 // result is step k0 + k.  CULL: closed scene, only front faces count.
 template <bool CULL>
-__device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeRef& E0,
-                                               const EdgeRef& E1, const EdgeRef& E2, float x,
+__device__ __forceinline__ unsigned cell_steps(const TileSmem& sm, const EdgeLin& E0,
+                                               const EdgeLin& E1, const EdgeLin& E2, float x,
                                                float y, int k0, int kn, unsigned fr, unsigned bk) {
     float P[3], QX[3], QY[3];
-    const EdgeRef* ee[3] = {&E0, &E1, &E2};
+    const EdgeLin* ee[3] = {&E0, &E1, &E2};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const EdgeRef& e = *ee[q];
-        const float cx = x - e.vx, cy = y - e.vy;
-        P[q] = __fsub_rn(__fmul_rn(e.ex, cy), __fmul_rn(e.ey, cx));
-        QX[q] = -fmaf(e.vz, e.ey, e.ez * cy);
-        QY[q] = fmaf(e.vz, e.ex, e.ez * cx);
+        const EdgeLin& e = *ee[q];
+        P[q] = fmaf(e.pa, y, fmaf(e.pb, x, e.pc));
+        QX[q] = fmaf(-e.ra, y, e.qc);
+        QY[q] = fmaf(e.ra, x, e.rc);
     }
     // steps in pairs: E = P + Qx u_x + Qy u_y for two steps per packed instruction
     unsigned long long P2[3], QX2[3], QY2[3];
@@ -317,9 +336,9 @@ __device__ __forceinline__ void drain_cells(TileSmem& sm, const unsigned* q, int
     const unsigned bk = CULL ? 0u : ((unsigned)(sm.back[t] >> k0) & run_bits);
     const float4* ef = reinterpret_cast<const float4*>(&sm.edges[20 * t]);
     const float4 f0 = ef[0], f1 = ef[1], f2 = ef[2], f3 = ef[3], f4 = ef[4];
-    const EdgeRef E0{f0.x, f0.y, f0.z, f0.w, f1.x, f1.y};
-    const EdgeRef E1{f1.z, f1.w, f2.x, f2.y, f2.z, f2.w};
-    const EdgeRef E2{f3.x, f3.y, f3.z, f3.w, f4.x, f4.y};
+    const EdgeLin E0{f0.x, f0.y, f0.z, f0.w, f1.x, f1.y};
+    const EdgeLin E1{f1.z, f1.w, f2.x, f2.y, f2.z, f2.w};
+    const EdgeLin E2{f3.x, f3.y, f3.z, f3.w, f4.x, f4.y};
     if (COUNT) { ++n_cell; n_test += kn; }
     const unsigned hit = cell_steps<CULL>(sm, E0, E1, E2, sm.xl[cell & (kTile - 1)],
                                           sm.yl[cell >> 5], k0, kn, fr, bk);
@@ -589,9 +608,9 @@ __device__ void raster_block(TileSmem& sm, const Fetch& fetch, int n, const Step
             if (lane < 3) {
                 const float4& p = sm.tri[3 * t + lane];
                 const float4& q = sm.tri[3 * t + (lane == 2 ? 0 : lane + 1)];
-                const EdgeRef e = edge_ref(p, q);
+                const EdgeLin e = edge_lin(edge_ref(p, q));
                 float* o = &sm.edges[20 * t + 6 * lane];
-                o[0] = e.vx; o[1] = e.vy; o[2] = e.vz; o[3] = e.ex; o[4] = e.ey; o[5] = e.ez;
+                o[0] = e.pa; o[1] = e.pb; o[2] = e.pc; o[3] = e.ra; o[4] = e.qc; o[5] = e.rc;
             }
         }
         __syncthreads();
