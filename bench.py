@@ -448,12 +448,13 @@ def B_option_run():
 
 
 # Algorithmic FP32 operations per unit of work (the method's own work, counted by the
-# library's instrumented counters): in the ground raster a cell set-up (three edges) 15
-# and a cell-step coverage test (three edge evaluations and compares) 9; in the light-space
+# library's instrumented counters): in the ground raster a cell set-up (P, Q_x and Q_y of
+# three edges from the triangle's affine edge constants, 4 FMAs each) 12 and a cell-step
+# coverage test (three edge evaluations and compares) 9; in the light-space
 # map of facades a receiver-triangle set-up (three Plücker edge moments, normal, distance)
 # 55 and a step test (three dot products, distance check) 15; in the ray-traced methods a
 # box test 12 and a watertight triangle test 25.
-OPS_CELL, OPS_TEST = 15, 9
+OPS_CELL, OPS_TEST = 12, 9
 OPS_PAIR, OPS_PTEST = 55, 15
 OPS_BOX, OPS_TRI = 12, 25
 
